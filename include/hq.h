@@ -1,0 +1,218 @@
+/*
+ * hq.h -- C ABI of the GB300 (sm_103a) quasi-orthogonal inverse-operator
+ * eigensolver: the discrete scheme Eq. (4.1) of Wang & Zhou, "A
+ * quasi-orthogonal method based on the inverse operator for Schroedinger
+ * eigenvalue problems" (arXiv 2605.25149), driven by Algorithm 1, for the N
+ * lowest eigenpairs of H = -Delta/2 + V on a 7-point finite-difference grid.
+ *
+ * Problem (Section 2.2): find U (n x N) and Lambda with <U,V>_a = <U Lambda,V>
+ * for all V, <U,U> = I.  Discretisation used by this library:
+ *   grid     m^3 interior nodes of [lo,hi]^3, h = (hi-lo)/(m+1), Dirichlet 0;
+ *            node (i,j,k) -> p = i + m*(j + m*k), x fastest, n = m^3;
+ *   blocks   n x N, point-major (U[p*N + c]); V is n values, same order;
+ *   product  <A,B> = h^3 A^T B (Section 2.1);
+ *   inverse  G = (H + sigma)^{-1} (Section 3.1) with a Garding shift sigma
+ *            (Section 2.2; automatic rule: sigma = 0 when
+ *            lambda_min(-Delta_h/2) + min V > 0, else 1 - that bound).
+ *
+ * Ownership: the caller allocates one device workspace of
+ * hq_workspace_bytes() bytes and passes a CUDA stream; the library never
+ * allocates device memory after hq_init and every kernel runs on that
+ * stream.  Pointers passed to a call are borrowed for the duration of the
+ * call only.  Arrays flagged on_device are device pointers, otherwise host
+ * pointers.  All arrays are FP64 unless stated.
+ *
+ * Errors: every function returns hq_status; hq_last_error() gives detail.
+ * After any status other than HQ_ERR_CUDA the context stays usable.  No C++
+ * exception crosses this boundary.  Device-side failures (CG breakdown, a
+ * singular small system) are reported through a status word read at the
+ * next synchronisation point; no kernel traps.
+ *
+ * Determinism: reductions run in a fixed order; identical inputs give
+ * bit-identical outputs.
+ */
+#ifndef HQ_H
+#define HQ_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hq_ctx hq_ctx;
+
+typedef enum {
+    HQ_OK = 0,
+    HQ_ERR_ARG = 1,            /* invalid argument (size, pointer, value)        */
+    HQ_ERR_STATE = 2,          /* call out of order (e.g. step before potential) */
+    HQ_ERR_CUDA = 3,           /* CUDA runtime error; the context is lost        */
+    HQ_ERR_NOMEM = 4,          /* workspace too small / host allocation failed   */
+    HQ_ERR_BREAKDOWN = 5,      /* inner CG: p^T A p <= 0 or not finite           */
+    HQ_ERR_SINGULAR = 6,       /* zero pivot in the predictor system             */
+    HQ_ERR_NOT_CONVERGED = 7,  /* inner CG or Algorithm 1 hit its iteration cap  */
+    HQ_ERR_TIMEOUT = 8,        /* wall-clock limit of hq_solve reached           */
+    HQ_ERR_NONFINITE = 9       /* NaN/Inf in an input or in the gradient norm    */
+} hq_status;
+
+typedef enum {
+    HQ_FP64 = 0,   /* every operation in IEEE FP64                               */
+    HQ_MIXED = 1   /* FP32 blocks, FP32 stencil / CG / multigrid, Gram products   */
+                   /* on tcgen05 tensor cores (3xTF32, FP32 accumulation),        */
+                   /* FP64 small solve, FP64 Rayleigh-Ritz refinement             */
+} hq_precision;
+
+typedef struct {
+    int m;               /* interior nodes per side (>= 3)                         */
+    double lo, hi;       /* box [lo,hi]^3                                          */
+    int nev;             /* N, number of eigenpairs (1 <= N <= min(n, 512))        */
+    double tau;          /* fixed time step tau_n of Algorithm 1 (> 0)             */
+    double shift;        /* sigma; NaN selects the automatic rule                  */
+    int precision;       /* hq_precision                                           */
+    double cg_rtol;      /* inner PCG: stop column j when ||r_j|| <= rtol ||b_j||  */
+    int cg_maxit;        /* inner PCG iteration cap                                */
+    int mg_nu1, mg_nu2;  /* damped-Jacobi pre/post sweeps per V-cycle level (>=1) */
+    int mg_coarsest;     /* coarsen m -> m/2 while m > mg_coarsest (1..4)          */
+    double mg_omega;     /* Jacobi damping                                         */
+    double timeout_s;    /* hq_solve wall-clock limit (<= 0: none)                 */
+} hq_config;
+
+/* Defaults: box [-6,6]^3, tau 0.4, automatic shift, FP64, cg_rtol 1e-10,
+ * cg_maxit 200, nu1 = nu2 = 2, coarsest 4, omega 0.8, no timeout.  m and nev
+ * are left 0 and must be set.                                              */
+void hq_default_config(hq_config *cfg);
+
+/* Bytes of device workspace hq_init needs for cfg (0 if cfg is invalid). */
+size_t hq_workspace_bytes(const hq_config *cfg);
+
+/* Creates a context on the current CUDA device.  d_workspace: device buffer
+ * of at least hq_workspace_bytes(cfg) bytes, 256-byte aligned, owned by the
+ * caller and kept alive until hq_destroy.  cuda_stream: a cudaStream_t (NULL
+ * = default stream).                                                        */
+hq_status hq_init(const hq_config *cfg, void *d_workspace, size_t bytes,
+                  void *cuda_stream, hq_ctx **out);
+
+/* Sets V (n values, unshifted) and rebuilds the multigrid hierarchy and the
+ * shift (setup of G, Section 3.1).  Resets the step counter and invalidates
+ * the iterate.  HQ_ERR_NONFINITE on NaN/Inf in V; HQ_ERR_ARG if a given shift
+ * leaves the coarsest operator indefinite.                                  */
+hq_status hq_set_potential(hq_ctx *ctx, const double *V, int on_device);
+
+/* Sets U0 (n x N, point-major) and rescales it by 1/sqrt(lambda_min(<U0,U0>))
+ * so that <U0,U0> >= I with equality in one direction: U0 enters the
+ * quasi-Stiefel set of Theorem 3.2 without being orthogonalised.            */
+hq_status hq_set_initial(hq_ctx *ctx, const double *U0, int on_device);
+
+/* Advances Eq. (4.1) nsteps times (predictor, corrector; two inner solves
+ * per step).  resid_out (nullable, host): the gradient norm
+ * ||G U - U <G U,U>|| (Remark 3.1) of the state at the start of the last
+ * step taken.                                                              */
+hq_status hq_step(hq_ctx *ctx, int nsteps, double *resid_out);
+
+/* Algorithm 1: steps until ||grad_G E_G(U_n)|| < eps (discrete L2 norm) or
+ * max_steps steps.  steps_out / resid_out (nullable, host) receive the steps
+ * taken in this call and the final gradient norm.  HQ_ERR_NOT_CONVERGED if
+ * max_steps was reached, HQ_ERR_TIMEOUT on the wall-clock limit.            */
+hq_status hq_solve(hq_ctx *ctx, double eps, long max_steps, long *steps_out,
+                   double *resid_out);
+
+/* Eigenpairs of the current iterate.  evals_paper (N, host, nullable): the
+ * eigenvalues of <G U,U>^{-1} shifted back by sigma (Section 5's
+ * definition), ascending.  evals_rr (N, host, nullable): FP64 Rayleigh-Ritz
+ * values of H on span(U), ascending.  evecs (n x N, point-major, nullable):
+ * Ritz vectors, <u_i,u_j> = delta_ij, largest-magnitude entry positive;
+ * device pointer if evecs_on_device else host.  resid (N, host, nullable):
+ * ||H u_i - lambda_i u_i|| in the discrete L2 norm.                        */
+hq_status hq_eigenpairs(hq_ctx *ctx, double *evals_paper, double *evals_rr,
+                        double *evecs, int evecs_on_device, double *resid);
+
+/* Checkpoint: copy U_n (n x N, FP64) and the step counter out / in.  Zwarm
+ * (nullable, n x N) is the inner solver's warm start, G Uh of the last step;
+ * restoring U together with Zwarm continues bit-identically to the
+ * uninterrupted run, restoring U alone within the inner-solve tolerance.
+ * hq_get_state with Zwarm before any step returns HQ_ERR_STATE.             */
+hq_status hq_get_state(hq_ctx *ctx, double *U, double *Zwarm, int on_device, long *step);
+hq_status hq_set_state(hq_ctx *ctx, const double *U, const double *Zwarm, int on_device,
+                       long step);
+
+/* Scalars of the configured problem (host outputs, nullable). */
+hq_status hq_problem_info(hq_ctx *ctx, double *h, double *sigma, int *levels,
+                          int *level_m /* up to 24 entries */);
+
+/* ---- operations of one step, on caller device buffers (point-major,
+ * ncol columns, FP64 in HQ_FP64 contexts, FP32 in HQ_MIXED contexts). ---- */
+
+/* y = (H + sigma) x on the finest grid (the operator G inverts). */
+hq_status hq_apply_operator(hq_ctx *ctx, const void *x, void *y, int ncol);
+
+/* z = M r: one multigrid V-cycle for (H + sigma) (symmetric when nu1 == nu2),
+ * the preconditioner of the inner solve.  ncol must equal N.                */
+hq_status hq_mg_vcycle(hq_ctx *ctx, const void *r, void *z);
+
+/* X = G B by block PCG, all N columns at once, column j stopped when
+ * ||r_j|| <= rtol ||b_j||; rtol = 0 runs exactly maxit iterations.  X holds
+ * the initial guess on entry.  iters (N ints, host, nullable).             */
+hq_status hq_block_pcg(hq_ctx *ctx, const void *B, void *X, double rtol, int maxit,
+                       int *iters);
+
+/* out = w A^T B (Na x Nb, row-major, FP64, device) for point-major blocks
+ * A (n x Na) and B (n x Nb) on the finest grid: the inner-product matrices
+ * <A,B> of Section 2.1 with w = h^3.  Na, Nb <= 2N.                        */
+hq_status hq_gram(hq_ctx *ctx, const void *A, int Na, const void *B, int Nb, double w,
+                  double *out);
+
+/* One step of Eq. (4.1) from the current iterate, exporting its
+ * intermediates to device buffers (each nullable): W = G U_n (n x N),
+ * gram = Gram of [U W] (2N x 2N, FP64), g (1 value, FP64), XY = [X; Y]
+ * (2N x N, FP64) with X = <U,Ut>, Y = <G U,Ut>, Uh (n x N), Shat = <Uh,Uh>
+ * (N x N, FP64), Z = G Uh (n x N), Unew = U_{n+1} (n x N).  Block outputs
+ * have the context's element type.  The iterate advances as in hq_step.    */
+hq_status hq_step_trace(hq_ctx *ctx, void *W, double *gram, double *g, double *XY,
+                        void *Uh, double *Shat, void *Z, void *Unew);
+
+/* Multigrid pieces on level l (0 = finest) for parity tests: one damped
+ * Jacobi sweep z_out = z_in + omega D^{-1}(r - A_l z_in); restriction
+ * rc = ((m_c+1)/(m_f+1))^3 P^T rf from level l to l+1; prolongation
+ * ef_out = ef_in + P ec from level l+1 to l; exact solve on the coarsest
+ * level.  ncol must equal N.                                               */
+hq_status hq_mg_smooth(hq_ctx *ctx, int level, const void *r, const void *z_in, void *z_out);
+hq_status hq_mg_restrict(hq_ctx *ctx, int level, const void *rf, void *rc);
+hq_status hq_mg_prolong(hq_ctx *ctx, int level, const void *ec, const void *ef_in,
+                        void *ef_out);
+hq_status hq_mg_coarse_solve(hq_ctx *ctx, const void *r, void *z);
+/* Level-l potential (n_l values, FP64, device). */
+hq_status hq_mg_level_potential(hq_ctx *ctx, int level, double *V_out);
+
+/* ---- instrumentation ---- */
+/* Kernel classes counted by the launch counters. */
+typedef enum {
+    HQ_K_STENCIL = 0,   /* 7-point operator (apply / residual)             */
+    HQ_K_SMOOTH,        /* damped-Jacobi sweeps                            */
+    HQ_K_TRANSFER,      /* restriction / prolongation                      */
+    HQ_K_COARSE,        /* coarsest-level solve                            */
+    HQ_K_VECTOR,        /* PCG vector updates, dots, conversions           */
+    HQ_K_REDUCE,        /* per-column / global finalising reductions       */
+    HQ_K_GRAM,          /* inner-product matrices <A,B>                    */
+    HQ_K_BLOCKGEMM,     /* block x small-matrix products (updates)         */
+    HQ_K_SMALL,         /* N x N / 2N x 2N FP64 algebra                    */
+    HQ_K_SETUP,         /* once-per-potential setup                        */
+    HQ_K_NCLASS
+} hq_kernel_class;
+
+/* Resets the per-class launch counters of this context; with timing != 0
+ * also brackets every kernel launch with CUDA events on the context's
+ * stream (adds host overhead; for measurement runs only).                  */
+hq_status hq_profile(hq_ctx *ctx, int timing);
+/* launches (HQ_K_NCLASS longs, host, nullable): kernels launched per class
+ * since the last hq_profile; ms (HQ_K_NCLASS doubles, host, nullable): summed
+ * event time per class (0 unless timing was on).  Synchronises the stream.  */
+hq_status hq_profile_read(hq_ctx *ctx, long *launches, double *ms);
+
+const char *hq_last_error(hq_ctx *ctx);
+const char *hq_status_string(hq_status s);
+void hq_destroy(hq_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HQ_H */

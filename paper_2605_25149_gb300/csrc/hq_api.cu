@@ -1,0 +1,1120 @@
+// libhq: host orchestration and the C ABI declared in include/hq.h.
+//
+// One step of the scheme Eq. (4.1) (Wang & Zhou, arXiv 2605.25149):
+//   A1  W = G U_n                   block PCG with a multigrid V-cycle
+//   A2  G2 = <[U W], [U W]>         split-K Gram, fixed-order reduction
+//   A3  g = || W - U <W,U> ||        Grassmann gradient (Remark 3.1), the
+//                                   quantity Algorithm 1 tests
+//   B1  [X; Y] from the 2N x 2N predictor system (LU, partial pivoting)
+//   B2  Uh = U (I - tau Y) + W (tau X)
+//   B3  Shat = <Uh,Uh> = C^T G2 C    (C = [I - tau Y; tau X]: the Gram of Uh
+//                                   by bilinearity, no extra pass over Uh)
+//   B4  Z = G Uh                    second block PCG
+//   B5  U_{n+1} = Uh - tau Z (Shat - I)
+// Every step runs on the caller's stream inside the caller's workspace; the
+// host reads back one scalar per PCG iteration (number of active columns) and
+// one per step (g) and never allocates device memory after hq_init.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hq.h"
+#include "hq_internal.cuh"
+
+using namespace hq;
+
+namespace {
+
+constexpr int MAXLEV = 24;
+
+struct Level {
+    int m = 0;
+    long n = 0;
+    double h = 0, c = 0;
+    double *V = nullptr, *D = nullptr, *wD = nullptr;   // FP64
+    void *Dt = nullptr, *wDt = nullptr;                 // working precision
+    void *r = nullptr, *z = nullptr, *t = nullptr;      // level buffers (l >= 1)
+    GridGeom g;
+};
+
+}  // namespace
+
+struct hq_ctx {
+    hq_config cfg;
+    bool mixed = false;
+    size_t esz = 8;
+    int m = 0, N = 0;
+    long n = 0;
+    double h = 0, h3 = 0, sigma = 0;
+    cudaStream_t st = nullptr;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    int L = 0;
+    Level lev[MAXLEV];
+    long nc = 0;
+    double *Acoarse = nullptr, *Ainv = nullptr;
+    // n x N blocks in the working precision
+    void *U = nullptr, *W = nullptr, *Uh = nullptr, *Z = nullptr;
+    void *R = nullptr, *Zp = nullptr, *P = nullptr, *Q = nullptr, *Tt = nullptr;
+    // FP64 n x N blocks for extraction / staging (aliases in FP64 mode)
+    double *E1 = nullptr, *E2 = nullptr, *E3 = nullptr;
+    PcgScalars sc;
+    double *part = nullptr, *part2 = nullptr;
+    GramPlan gplan_uw, gplan_max;
+    double *gpart = nullptr;
+    TallPlan tplan;
+    double *tpart = nullptr;   // gy x N
+    double *G2 = nullptr, *Mw = nullptr, *XY = nullptr, *C = nullptr, *T1 = nullptr;
+    double *Shat = nullptr, *Om = nullptr, *Msm = nullptr, *Ksm = nullptr, *Ssm = nullptr;
+    double *Lm = nullptr, *Cm = nullptr, *Ym = nullptr, *Cv = nullptr, *Cv2 = nullptr;
+    double *eigwork = nullptr, *evals = nullptr, *mu = nullptr, *lam_p = nullptr;
+    double *lam_r = nullptr, *resn = nullptr, *scal = nullptr, *signwork = nullptr;
+    int *status = nullptr;
+    // host state
+    bool have_V = false, have_U = false, w_valid = false, z_valid = false;
+    long step = 0;
+    double last_g = NAN;
+    std::string err;
+    // instrumentation
+    long launches[HQ_K_NCLASS] = {};
+    bool timing = false;
+    std::vector<cudaEvent_t> evpool;
+    size_t evused = 0;
+    std::vector<std::pair<int, size_t>> evrec;
+    size_t pending_start = 0;
+    ~hq_ctx() {
+        for (cudaEvent_t e : evpool) cudaEventDestroy(e);
+    }
+};
+
+namespace hq {
+namespace {
+thread_local hq_ctx *g_prof = nullptr;
+}
+void hook_before(int cls) {
+    (void)cls;
+    hq_ctx *x = g_prof;
+    if (!x || !x->timing) return;
+    while (x->evpool.size() < x->evused + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        x->evpool.push_back(e);
+    }
+    x->pending_start = x->evused;
+    cudaEventRecord(x->evpool[x->evused], x->st);
+    x->evused += 2;
+}
+void hook_after(int cls) {
+    hq_ctx *x = g_prof;
+    if (!x) return;
+    if (cls >= 0 && cls < HQ_K_NCLASS) x->launches[cls]++;
+    if (!x->timing || x->evused < 2) return;
+    cudaEventRecord(x->evpool[x->pending_start + 1], x->st);
+    x->evrec.emplace_back(cls, x->pending_start);
+}
+}  // namespace hq
+
+namespace {
+// binds the instrumentation hooks to a context for the duration of a call
+struct ProfScope {
+    hq_ctx *prev;
+    explicit ProfScope(hq_ctx *x) : prev(hq::g_prof) { hq::g_prof = x; }
+    ~ProfScope() { hq::g_prof = prev; }
+};
+}  // namespace
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// workspace carving (identical in the sizing pass and the real pass)
+// ---------------------------------------------------------------------------
+struct Carver {
+    char *base;
+    size_t off = 0;
+    template <typename P>
+    P *take(size_t bytes) {
+        off = (off + 255) & ~(size_t)255;
+        P *p = base ? reinterpret_cast<P *>(base + off) : nullptr;
+        off += bytes;
+        return p;
+    }
+};
+
+bool valid_config(const hq_config *c, std::string *why) {
+    auto fail = [&](const char *s) {
+        if (why) *why = s;
+        return false;
+    };
+    if (!c) return fail("null config");
+    if (c->m < 3) return fail("m must be >= 3");
+    if (c->m > 1024) return fail("m must be <= 1024");
+    long n = (long)c->m * c->m * c->m;
+    if (c->nev < 1 || c->nev > 512 || c->nev > n) return fail("nev must satisfy 1 <= N <= min(n, 512)");
+    if (!(c->hi > c->lo)) return fail("box: hi must exceed lo");
+    if (!(c->tau > 0.0) || !std::isfinite(c->tau)) return fail("tau must be positive and finite");
+    if (c->precision != HQ_FP64 && c->precision != HQ_MIXED) return fail("unknown precision");
+    if (!(c->cg_rtol >= 0.0)) return fail("cg_rtol must be >= 0");
+    if (c->cg_maxit < 1) return fail("cg_maxit must be >= 1");
+    if (c->mg_nu1 < 1 || c->mg_nu2 < 1 || c->mg_nu1 > 16 || c->mg_nu2 > 16)
+        return fail("mg_nu1, mg_nu2 must be in [1, 16]");
+    if (c->mg_coarsest < 1 || c->mg_coarsest > 4) return fail("mg_coarsest must be in [1, 4]");
+    if (!(c->mg_omega > 0.0 && c->mg_omega < 2.0)) return fail("mg_omega must be in (0, 2)");
+    return true;
+}
+
+int level_sizes(int m, int coarsest, int *ms) {
+    int L = 0;
+    ms[L++] = m;
+    while (ms[L - 1] > coarsest && ms[L - 1] >= 2 && L < MAXLEV) {
+        ms[L] = ms[L - 1] / 2;
+        L++;
+    }
+    return L;
+}
+
+size_t carve(hq_ctx *x, const hq_config *c, char *base) {
+    Carver cv{base};
+    const int m = c->m, N = c->nev;
+    const long n = (long)m * m * m;
+    const bool mixed = c->precision == HQ_MIXED;
+    const size_t esz = mixed ? 4 : 8;
+    const size_t blk = (size_t)n * N * esz;
+    int ms[MAXLEV];
+    const int L = level_sizes(m, c->mg_coarsest, ms);
+    void *U = cv.take<char>(blk), *W = cv.take<char>(blk), *Uh = cv.take<char>(blk),
+         *Z = cv.take<char>(blk), *R = cv.take<char>(blk), *Zp = cv.take<char>(blk),
+         *P = cv.take<char>(blk), *Q = cv.take<char>(blk), *Tt = cv.take<char>(blk);
+    double *E1, *E2, *E3;
+    if (mixed) {
+        E1 = cv.take<double>(sizeof(double) * n * N);
+        E2 = cv.take<double>(sizeof(double) * n * N);
+        E3 = cv.take<double>(sizeof(double) * n * N);
+    } else {
+        E1 = (double *)Q;
+        E2 = (double *)Tt;
+        E3 = (double *)Uh;
+    }
+    Level lev[MAXLEV];
+    for (int l = 0; l < L; l++) {
+        Level &v = lev[l];
+        v.m = ms[l];
+        v.n = (long)ms[l] * ms[l] * ms[l];
+        v.h = (c->hi - c->lo) / (ms[l] + 1);
+        v.c = 0.5 / (v.h * v.h);
+        v.g = make_geom(ms[l], N, (int)esz);
+        v.V = cv.take<double>(sizeof(double) * v.n);
+        v.D = cv.take<double>(sizeof(double) * v.n);
+        v.wD = cv.take<double>(sizeof(double) * v.n);
+        if (mixed) {
+            v.Dt = cv.take<float>(sizeof(float) * v.n);
+            v.wDt = cv.take<float>(sizeof(float) * v.n);
+        } else {
+            v.Dt = v.D;
+            v.wDt = v.wD;
+        }
+        if (l > 0) {
+            size_t lb = (size_t)v.n * N * esz;
+            v.r = cv.take<char>(lb);
+            v.z = cv.take<char>(lb);
+            v.t = cv.take<char>(lb);
+        } else {
+            v.r = R;
+            v.z = Zp;
+            v.t = Tt;
+        }
+    }
+    const long nc = lev[L - 1].n;
+    double *Acoarse = cv.take<double>(sizeof(double) * nc * nc);
+    double *Ainv = cv.take<double>(sizeof(double) * nc * nc);
+    PcgScalars sc;
+    sc.rz = cv.take<double>(sizeof(double) * N);
+    sc.alpha = cv.take<double>(sizeof(double) * N);
+    sc.beta = cv.take<double>(sizeof(double) * N);
+    sc.bnorm = cv.take<double>(sizeof(double) * N);
+    sc.rnorm = cv.take<double>(sizeof(double) * N);
+    sc.active = cv.take<int>(sizeof(int) * N);
+    sc.iters = cv.take<int>(sizeof(int) * N);
+    sc.num_active = cv.take<int>(sizeof(int) * 4);
+    sc.status = cv.take<int>(sizeof(int) * 4);
+    const int gy0 = lev[0].g.gy;
+    double *part = cv.take<double>(sizeof(double) * (size_t)gy0 * N);
+    double *part2 = cv.take<double>(sizeof(double) * (size_t)gy0 * N);
+    GramPlan guw = make_gram_plan(n, 2 * N, 2 * N, true);
+    GramPlan gmax = make_gram_plan(n, 2 * N, 2 * N, false);
+    double *gpart = cv.take<double>(std::max(gram_partial_bytes(guw), gram_partial_bytes(gmax)));
+    TallPlan tp = make_tall_plan(n, N, 2 * N, 0);
+    double *tpart = cv.take<double>(sizeof(double) * (size_t)tp.gy * std::max(N, tp.gx));
+    const size_t N2 = (size_t)N * N;
+    double *G2 = cv.take<double>(sizeof(double) * 4 * N2);
+    double *Mw = cv.take<double>(sizeof(double) * 4 * N2);
+    double *XY = cv.take<double>(sizeof(double) * 2 * N2);
+    double *Cc = cv.take<double>(sizeof(double) * 2 * N2);
+    double *T1 = cv.take<double>(sizeof(double) * 2 * N2);
+    double *Shat = cv.take<double>(sizeof(double) * N2);
+    double *Om = cv.take<double>(sizeof(double) * N2);
+    double *Msm = cv.take<double>(sizeof(double) * N2);
+    double *Ksm = cv.take<double>(sizeof(double) * N2);
+    double *Ssm = cv.take<double>(sizeof(double) * N2);
+    double *Lm = cv.take<double>(sizeof(double) * N2);
+    double *Cm = cv.take<double>(sizeof(double) * N2);
+    double *Ym = cv.take<double>(sizeof(double) * N2);
+    double *Cvv = cv.take<double>(sizeof(double) * N2);
+    double *Cv2 = cv.take<double>(sizeof(double) * N2);
+    const size_t P2 = (size_t)((N + 1) & ~1) * ((N + 1) & ~1);
+    double *eigwork = cv.take<double>(sizeof(double) * 2 * P2);
+    double *evals = cv.take<double>(sizeof(double) * N);
+    double *mu = cv.take<double>(sizeof(double) * N);
+    double *lam_p = cv.take<double>(sizeof(double) * N);
+    double *lam_r = cv.take<double>(sizeof(double) * N);
+    double *resn = cv.take<double>(sizeof(double) * N);
+    double *scal = cv.take<double>(sizeof(double) * 16);
+    double *signwork = cv.take<double>(sizeof(double) * 2 * 64 * N);
+    int *status = cv.take<int>(sizeof(int) * 4);
+    if (x) {
+        x->U = U; x->W = W; x->Uh = Uh; x->Z = Z; x->R = R; x->Zp = Zp; x->P = P; x->Q = Q;
+        x->Tt = Tt; x->E1 = E1; x->E2 = E2; x->E3 = E3;
+        x->L = L;
+        for (int l = 0; l < L; l++) x->lev[l] = lev[l];
+        x->nc = nc; x->Acoarse = Acoarse; x->Ainv = Ainv;
+        x->sc = sc; x->part = part; x->part2 = part2;
+        x->gplan_uw = guw; x->gplan_max = gmax; x->gpart = gpart;
+        x->tplan = tp; x->tpart = tpart;
+        x->G2 = G2; x->Mw = Mw; x->XY = XY; x->C = Cc; x->T1 = T1; x->Shat = Shat; x->Om = Om;
+        x->Msm = Msm; x->Ksm = Ksm; x->Ssm = Ssm; x->Lm = Lm; x->Cm = Cm; x->Ym = Ym;
+        x->Cv = Cvv; x->Cv2 = Cv2; x->eigwork = eigwork; x->evals = evals; x->mu = mu;
+        x->lam_p = lam_p; x->lam_r = lam_r; x->resn = resn; x->scal = scal;
+        x->signwork = signwork; x->status = status;
+    }
+    return cv.off + 256;
+}
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+#define HQ_CUDA(call)                                                          \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) {                                               \
+            x->err = std::string(#call) + ": " + cudaGetErrorString(e_);       \
+            return HQ_ERR_CUDA;                                                \
+        }                                                                      \
+    } while (0)
+
+#define HQ_TRY(expr)                    \
+    do {                                \
+        hq_status s_ = (expr);          \
+        if (s_ != HQ_OK) return s_;     \
+    } while (0)
+
+hq_status fail(hq_ctx *x, hq_status s, const std::string &msg) {
+    if (x) x->err = msg;
+    return s;
+}
+
+hq_status check_launch(hq_ctx *x) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(x, HQ_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return HQ_OK;
+}
+
+hq_status sync_status(hq_ctx *x, int *dev_status_word, const char *where) {
+    int st = 0;
+    HQ_CUDA(cudaMemcpyAsync(&st, dev_status_word, sizeof(int), cudaMemcpyDeviceToHost, x->st));
+    HQ_CUDA(cudaStreamSynchronize(x->st));
+    HQ_TRY(check_launch(x));
+    if (st & ST_BREAKDOWN) return fail(x, HQ_ERR_BREAKDOWN, std::string(where) + ": CG breakdown (p^T A p <= 0)");
+    if (st & ST_SINGULAR) return fail(x, HQ_ERR_SINGULAR, std::string(where) + ": singular small system");
+    if (st & ST_NONFINITE) return fail(x, HQ_ERR_NONFINITE, std::string(where) + ": non-finite value");
+    if (st & ST_GJ_FAIL) return fail(x, HQ_ERR_ARG, std::string(where) + ": coarsest operator not positive definite (shift too small)");
+    return HQ_OK;
+}
+
+hq_status clear_status(hq_ctx *x) {
+    HQ_CUDA(cudaMemsetAsync(x->sc.status, 0, sizeof(int), x->st));
+    HQ_CUDA(cudaMemsetAsync(x->status, 0, sizeof(int), x->st));
+    return HQ_OK;
+}
+
+// copy of an n x N block, count elements
+template <typename T>
+hq_status copy_blk(hq_ctx *x, T *dst, const T *src, size_t count) {
+    if (dst != src) HQ_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyDeviceToDevice, x->st));
+    return HQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// multigrid V-cycle
+// ---------------------------------------------------------------------------
+int cycle_writes(const hq_ctx *x) { return (x->cfg.mg_nu1 - 1) + 1 + x->cfg.mg_nu2; }
+
+template <typename T>
+T *first_target(hq_ctx *x, int l, T *Zfinal, T *Tbuf) {
+    (void)l;
+    return (cycle_writes(x) % 2 == 0) ? Zfinal : Tbuf;
+}
+
+template <typename T>
+hq_status vcycle(hq_ctx *x, int l, const T *r, T *Zf, T *Tb, bool first_done, double *part_final) {
+    Level &v = x->lev[l];
+    const T c = (T)v.c, omw = (T)(1.0 - x->cfg.mg_omega);
+    if (l == x->L - 1) {
+        launch_coarse_solve<T>(v.g, x->Ainv, r, Zf, x->st);
+        if (part_final) launch_dot<T>(v.g, r, Zf, part_final, x->st);
+        return HQ_OK;
+    }
+    T *cur = first_target<T>(x, l, Zf, Tb);
+    T *oth = (cur == Zf) ? Tb : Zf;
+    if (!first_done) launch_jacobi_first<T>(v.g, (const T *)v.wDt, r, cur, x->st);
+    for (int s = 1; s < x->cfg.mg_nu1; s++) {
+        launch_jacobi<T>(v.g, (const T *)v.Dt, (const T *)v.wDt, c, omw, r, cur, oth, nullptr, x->st);
+        std::swap(cur, oth);
+    }
+    launch_resid<T>(v.g, (const T *)v.Dt, c, cur, r, oth, nullptr, nullptr, x->st);
+    Level &w = x->lev[l + 1];
+    launch_restrict<T>(w.g, v.m, oth, (T *)w.r, x->st);
+    HQ_TRY(vcycle<T>(x, l + 1, (const T *)w.r, (T *)w.z, (T *)w.t, false, nullptr));
+    launch_prolong<T>(v.g, w.m, (const T *)w.z, cur, oth, x->st);
+    std::swap(cur, oth);
+    for (int s = 0; s < x->cfg.mg_nu2; s++) {
+        bool last = (s == x->cfg.mg_nu2 - 1);
+        launch_jacobi<T>(v.g, (const T *)v.Dt, (const T *)v.wDt, c, omw, r, cur, oth,
+                         last ? part_final : nullptr, x->st);
+        std::swap(cur, oth);
+    }
+    if (cur != Zf) HQ_TRY(copy_blk<T>(x, Zf, cur, (size_t)v.n * x->N));
+    return HQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// block PCG: X = G B, per-column stopping ||r_j|| <= rtol ||b_j||
+// ---------------------------------------------------------------------------
+template <typename T>
+hq_status pcg(hq_ctx *x, const T *B, T *X, double rtol, int maxit, int *iters_host) {
+    Level &v = x->lev[0];
+    const GridGeom &g = v.g;
+    const int N = x->N;
+    T *R = (T *)x->R, *Zp = (T *)x->Zp, *P = (T *)x->P, *Q = (T *)x->Q, *Tt = (T *)x->Tt;
+    const T c = (T)v.c;
+    PcgScalars sc = x->sc;
+    HQ_CUDA(cudaMemsetAsync(sc.num_active, 0, sizeof(int), x->st));
+    launch_resid<T>(g, (const T *)v.Dt, c, X, B, R, x->part, x->part2, x->st);
+    launch_finalize(FIN_BNORM_RNORM, N, g.gy, x->part, x->part2, sc, rtol, x->st);
+    int nact = 0;
+    HQ_CUDA(cudaMemcpyAsync(&nact, sc.num_active, sizeof(int), cudaMemcpyDeviceToHost, x->st));
+    HQ_CUDA(cudaStreamSynchronize(x->st));
+    hq_status st = HQ_OK;
+    if (nact > 0) {
+        HQ_TRY(vcycle<T>(x, 0, R, Zp, Tt, false, x->part));
+        launch_finalize(FIN_RZ, N, g.gy, x->part, nullptr, sc, rtol, x->st);
+        HQ_TRY(copy_blk<T>(x, P, Zp, (size_t)x->n * N));
+        T *zfirst = first_target<T>(x, 0, Zp, Tt);
+        const bool single = (x->L == 1);
+        int it = 0;
+        for (it = 1; it <= maxit; it++) {
+            launch_apply<T>(g, (const T *)v.Dt, c, P, Q, x->part, x->st);
+            launch_finalize(FIN_ALPHA, N, g.gy, x->part, nullptr, sc, rtol, x->st);
+            launch_pcg_xr<T>(g, sc.alpha, P, Q, X, R, x->part, (const T *)v.wDt,
+                             single ? nullptr : zfirst, x->st);
+            HQ_CUDA(cudaMemsetAsync(sc.num_active, 0, sizeof(int), x->st));
+            launch_finalize(FIN_RR, N, g.gy, x->part, nullptr, sc, rtol, x->st);
+            HQ_CUDA(cudaMemcpyAsync(&nact, sc.num_active, sizeof(int), cudaMemcpyDeviceToHost, x->st));
+            HQ_CUDA(cudaStreamSynchronize(x->st));
+            if (nact == 0) break;
+            HQ_TRY(vcycle<T>(x, 0, R, Zp, Tt, !single, x->part));
+            launch_finalize(FIN_BETA, N, g.gy, x->part, nullptr, sc, rtol, x->st);
+            launch_pcg_p<T>(g, sc.beta, Zp, P, x->st);
+        }
+        if (nact > 0 && rtol > 0.0) st = HQ_ERR_NOT_CONVERGED;
+    }
+    if (iters_host) HQ_CUDA(cudaMemcpyAsync(iters_host, sc.iters, sizeof(int) * N, cudaMemcpyDeviceToHost, x->st));
+    HQ_TRY(sync_status(x, sc.status, "inner PCG"));
+    if (st == HQ_ERR_NOT_CONVERGED) return fail(x, st, "inner PCG reached cg_maxit");
+    return HQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the scheme
+// ---------------------------------------------------------------------------
+// A1-A3: W = G U (warm start from the previous G Uh), Gram of [U W], g.
+template <typename T>
+hq_status phase_a(hq_ctx *x) {
+    const int N = x->N;
+    const size_t cnt = (size_t)x->n * N;
+    T *U = (T *)x->U, *W = (T *)x->W;
+    if (x->z_valid) HQ_TRY(copy_blk<T>(x, W, (const T *)x->Z, cnt));
+    else HQ_CUDA(cudaMemsetAsync(W, 0, cnt * sizeof(T), x->st));
+    HQ_TRY(pcg<T>(x, U, W, x->cfg.cg_rtol, x->cfg.cg_maxit, nullptr));
+    launch_gram<T>(x->gplan_uw, U, N, W, N, U, N, W, N, x->h3, x->gpart, x->G2, x->st);
+    // Msm = -Pwu (rows N..2N-1, columns 0..N-1 of G2); g = || W - U Pwu ||_h
+    launch_extract(N, N, -1.0, x->G2 + (size_t)N * 2 * N, 2 * N, x->Msm, N, x->st);
+    TallPlan tp = make_tall_plan(x->n, N, N, 0);
+    launch_tall_gemm<T>(tp, U, x->Msm, nullptr, nullptr, W, nullptr, x->tpart, x->st);
+    launch_sum_sqrt(tp.gy * tp.gx, x->tpart, x->h3, x->scal, x->st);
+    HQ_TRY(check_launch(x));
+    x->w_valid = true;
+    return HQ_OK;
+}
+
+hq_status read_g(hq_ctx *x, double *g) {
+    HQ_CUDA(cudaMemcpyAsync(g, x->scal, sizeof(double), cudaMemcpyDeviceToHost, x->st));
+    HQ_CUDA(cudaStreamSynchronize(x->st));
+    HQ_TRY(check_launch(x));
+    x->last_g = *g;
+    if (!std::isfinite(*g)) return fail(x, HQ_ERR_NONFINITE, "gradient norm is not finite");
+    return HQ_OK;
+}
+
+// B1-B5: predictor system, Uh, Shat, Z = G Uh, corrector (U <- U_{n+1}).
+template <typename T>
+hq_status phase_b(hq_ctx *x) {
+    const int N = x->N;
+    const size_t cnt = (size_t)x->n * N;
+    const double tau = x->cfg.tau;
+    T *U = (T *)x->U, *W = (T *)x->W, *Uh = (T *)x->Uh, *Z = (T *)x->Z;
+    launch_predictor_solve(N, tau, x->G2, x->Mw, x->XY, x->C, x->status, x->st);
+    TallPlan tp2 = make_tall_plan(x->n, N, N, N);
+    launch_tall_gemm<T>(tp2, U, x->C, W, x->C + (size_t)N * N, nullptr, Uh, nullptr, x->st);
+    // Shat = C^T G2 C, Om = Shat - I
+    launch_small_gemm(2 * N, N, 2 * N, 1.0, x->G2, 2 * N, false, x->C, N, false, 0.0, x->T1, N,
+                      x->st);
+    launch_small_gemm(N, N, 2 * N, 1.0, x->C, N, true, x->T1, N, false, 0.0, x->Shat, N, x->st);
+    // Om = -tau (Shat - I)
+    launch_extract(N, N, -tau, x->Shat, N, x->Om, N, x->st);
+    launch_add_diag(N, x->Om, tau, x->st);
+    HQ_TRY(sync_status(x, x->status, "predictor system"));
+    HQ_CUDA(cudaMemsetAsync(Z, 0, cnt * sizeof(T), x->st));
+    HQ_TRY(pcg<T>(x, Uh, Z, x->cfg.cg_rtol, x->cfg.cg_maxit, nullptr));
+    TallPlan tp1 = make_tall_plan(x->n, N, N, 0);
+    launch_tall_gemm<T>(tp1, Z, x->Om, nullptr, nullptr, Uh, U, nullptr, x->st);
+    HQ_TRY(check_launch(x));
+    x->w_valid = false;
+    x->z_valid = true;
+    x->step++;
+    return HQ_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+namespace {
+
+hq_status guard(hq_ctx *x) {
+    if (!x) return HQ_ERR_ARG;
+    return HQ_OK;
+}
+
+hq_status need_ready(hq_ctx *x) {
+    if (!x->have_V) return fail(x, HQ_ERR_STATE, "hq_set_potential has not been called");
+    if (!x->have_U) return fail(x, HQ_ERR_STATE, "hq_set_initial / hq_set_state has not been called");
+    return HQ_OK;
+}
+
+cudaMemcpyKind kind_in(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+cudaMemcpyKind kind_out(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+
+template <typename T>
+hq_status set_potential_impl(hq_ctx *x, const double *V, int on_device) {
+    Level &v0 = x->lev[0];
+    x->have_V = false;
+    HQ_TRY(clear_status(x));
+    HQ_CUDA(cudaMemcpyAsync(v0.V, V, sizeof(double) * x->n, kind_in(on_device), x->st));
+    launch_minmax(x->n, v0.V, x->scal + 2, x->st);
+    double mm[2] = {0, 0};
+    HQ_CUDA(cudaMemcpyAsync(mm, x->scal + 2, sizeof(mm), cudaMemcpyDeviceToHost, x->st));
+    HQ_CUDA(cudaStreamSynchronize(x->st));
+    HQ_TRY(check_launch(x));
+    if (mm[1] != 0.0) return fail(x, HQ_ERR_NONFINITE, "potential contains NaN or Inf");
+    const double PI = 3.14159265358979323846;
+    double s = std::sin(PI / (2.0 * (x->m + 1)));
+    double lb = 3.0 * (2.0 / (x->h * x->h)) * s * s + mm[0];
+    x->sigma = std::isnan(x->cfg.shift) ? (lb > 0.0 ? 0.0 : 1.0 - lb) : x->cfg.shift;
+    for (int l = 1; l < x->L; l++)
+        launch_coarse_potential(x->lev[l - 1].m, x->lev[l - 1].V, x->lev[l].m, x->lev[l].V, x->st);
+    for (int l = 0; l < x->L; l++) {
+        Level &v = x->lev[l];
+        launch_level_diag(v.n, v.V, x->sigma, v.c, x->cfg.mg_omega, v.D, v.wD, x->st);
+        if (x->mixed) {
+            launch_convert_d2f(v.n, v.D, (float *)v.Dt, x->st);
+            launch_convert_d2f(v.n, v.wD, (float *)v.wDt, x->st);
+        }
+    }
+    Level &vc = x->lev[x->L - 1];
+    launch_assemble_dense(vc.m, vc.c, vc.V, x->sigma, x->Acoarse, x->st);
+    launch_gauss_jordan((int)x->nc, x->Acoarse, x->Ainv, x->status, x->st);
+    HQ_TRY(sync_status(x, x->status, "potential setup"));
+    x->have_V = true;
+    x->w_valid = x->z_valid = false;
+    x->step = 0;
+    return HQ_OK;
+}
+
+template <typename T>
+hq_status load_block(hq_ctx *x, T *dst, const double *src, int on_device) {
+    const size_t cnt = (size_t)x->n * x->N;
+    if (!x->mixed) {
+        HQ_CUDA(cudaMemcpyAsync(dst, src, cnt * sizeof(double), kind_in(on_device), x->st));
+    } else {
+        const double *s64 = src;
+        if (!on_device) {
+            HQ_CUDA(cudaMemcpyAsync(x->E1, src, cnt * sizeof(double), cudaMemcpyHostToDevice, x->st));
+            s64 = x->E1;
+        }
+        launch_convert_d2f(cnt, s64, (float *)dst, x->st);
+    }
+    return check_launch(x);
+}
+
+template <typename T>
+hq_status store_block(hq_ctx *x, double *dst, const T *src, int on_device) {
+    const size_t cnt = (size_t)x->n * x->N;
+    if (!x->mixed) {
+        HQ_CUDA(cudaMemcpyAsync(dst, src, cnt * sizeof(double), kind_out(on_device), x->st));
+    } else {
+        double *d64 = on_device ? dst : x->E1;
+        launch_convert_f2d(cnt, (const float *)src, d64, x->st);
+        if (!on_device)
+            HQ_CUDA(cudaMemcpyAsync(dst, d64, cnt * sizeof(double), cudaMemcpyDeviceToHost, x->st));
+    }
+    return check_launch(x);
+}
+
+template <typename T>
+hq_status set_initial_impl(hq_ctx *x, const double *U0, int on_device) {
+    const int N = x->N;
+    x->have_U = false;
+    HQ_TRY(clear_status(x));
+    T *U = (T *)x->U;
+    HQ_TRY(load_block<T>(x, U, U0, on_device));
+    GramPlan gp = make_gram_plan(x->n, N, N, true);
+    launch_gram<T>(gp, U, N, nullptr, 0, U, N, nullptr, 0, x->h3, x->gpart, x->Ssm, x->st);
+    launch_sym_eig(N, x->Ssm, x->eigwork, x->evals, nullptr, x->st);
+    launch_inv_sqrt_first(x->evals, x->scal + 1, x->st);
+    double lmin = 0;
+    HQ_CUDA(cudaMemcpyAsync(&lmin, x->evals, sizeof(double), cudaMemcpyDeviceToHost, x->st));
+    HQ_CUDA(cudaStreamSynchronize(x->st));
+    HQ_TRY(check_launch(x));
+    if (!(lmin > 0.0) || !std::isfinite(lmin))
+        return fail(x, HQ_ERR_ARG, "initial block is rank deficient or not finite");
+    launch_scale<T>((size_t)x->n * N, x->scal + 1, U, x->st);
+    HQ_TRY(check_launch(x));
+    x->have_U = true;
+    x->w_valid = x->z_valid = false;
+    x->step = 0;
+    return HQ_OK;
+}
+
+template <typename T>
+hq_status step_impl(hq_ctx *x, int nsteps, double *resid_out) {
+    HQ_TRY(need_ready(x));
+    HQ_TRY(clear_status(x));
+    double g = NAN;
+    for (int s = 0; s < nsteps; s++) {
+        HQ_TRY(phase_a<T>(x));
+        HQ_TRY(read_g(x, &g));
+        HQ_TRY(phase_b<T>(x));
+    }
+    if (resid_out) *resid_out = g;
+    return HQ_OK;
+}
+
+template <typename T>
+hq_status solve_impl(hq_ctx *x, double eps, long max_steps, long *steps_out, double *resid_out) {
+    HQ_TRY(need_ready(x));
+    HQ_TRY(clear_status(x));
+    auto t0 = std::chrono::steady_clock::now();
+    long taken = 0;
+    double g = NAN;
+    hq_status st = HQ_OK;
+    for (;;) {
+        st = phase_a<T>(x);
+        if (st != HQ_OK) break;
+        st = read_g(x, &g);
+        if (st != HQ_OK) break;
+        if (g < eps) break;
+        if (taken >= max_steps) {
+            st = fail(x, HQ_ERR_NOT_CONVERGED, "Algorithm 1 reached max_steps");
+            break;
+        }
+        if (x->cfg.timeout_s > 0) {
+            double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (el > x->cfg.timeout_s) {
+                st = fail(x, HQ_ERR_TIMEOUT, "hq_solve wall-clock limit reached");
+                break;
+            }
+        }
+        st = phase_b<T>(x);
+        if (st != HQ_OK) break;
+        taken++;
+    }
+    if (steps_out) *steps_out = taken;
+    if (resid_out) *resid_out = g;
+    return st;
+}
+
+template <typename T>
+hq_status eigen_impl(hq_ctx *x, double *evals_paper, double *evals_rr, double *evecs,
+                     int evecs_on_device, double *resid) {
+    HQ_TRY(need_ready(x));
+    HQ_TRY(clear_status(x));
+    const int N = x->N;
+    const size_t cnt = (size_t)x->n * N;
+    if (!x->w_valid) HQ_TRY(phase_a<T>(x));
+    // eigenvalues of <G U, U>^{-1} (Section 5), shifted back
+    launch_extract(N, N, 1.0, x->G2 + (size_t)N * 2 * N, 2 * N, x->Ksm, N, x->st);
+    launch_sym_eig(N, x->Ksm, x->eigwork, x->mu, nullptr, x->st);
+    launch_paper_evals(N, x->mu, x->sigma, x->lam_p, x->st);
+    // FP64 Rayleigh-Ritz of H on span(U)
+    double *U64 = (double *)x->U;
+    if (x->mixed) {
+        launch_convert_f2d(cnt, (const float *)x->U, x->E1, x->st);
+        U64 = x->E1;
+    }
+    Level &v0 = x->lev[0];
+    GridGeom g64 = make_geom(x->m, N, 8);
+    launch_apply<double>(g64, v0.D, v0.c, U64, x->E2, nullptr, x->st);   // (H + sigma) U
+    GramPlan gk = make_gram_plan(x->n, N, N, false);
+    GramPlan gs = make_gram_plan(x->n, N, N, true);
+    launch_gram<double>(gk, U64, N, nullptr, 0, x->E2, N, nullptr, 0, x->h3, x->gpart, x->Ksm, x->st);
+    launch_gram<double>(gs, U64, N, nullptr, 0, U64, N, nullptr, 0, x->h3, x->gpart, x->Ssm, x->st);
+    launch_axpy_small(N * N, -x->sigma, x->Ssm, x->Ksm, x->st);   // <U, H U>
+    launch_rr_reduce(N, x->Ksm, x->Ssm, x->Lm, x->Cm, x->status, x->st);
+    HQ_TRY(sync_status(x, x->status, "Rayleigh-Ritz (Cholesky of <U,U>)"));
+    launch_sym_eig(N, x->Cm, x->eigwork, x->lam_r, x->Ym, x->st);
+    launch_rr_back(N, x->Lm, x->Ym, x->Cv, x->st);
+    TallPlan tp = make_tall_plan(x->n, N, N, N);
+    if (evecs || resid) {
+        double *X = (evecs && evecs_on_device) ? evecs : x->E3;
+        launch_tall_gemm<double>(tp, U64, x->Cv, nullptr, nullptr, nullptr, X, nullptr, x->st);
+        launch_fix_signs<double>(x->n, N, X, x->signwork, x->st);
+        if (evecs && !evecs_on_device)
+            HQ_CUDA(cudaMemcpyAsync(evecs, X, cnt * sizeof(double), cudaMemcpyDeviceToHost, x->st));
+        if (resid) {
+            launch_scale_cols(N, x->Cv, x->lam_r, x->sigma, x->Cv2, x->st);
+            launch_tall_gemm_colsq<double>(tp, x->E2, x->Cv, U64, x->Cv2, nullptr, nullptr,
+                                           x->tpart, x->st);
+            launch_colsum_sqrt(tp.gy, N, x->tpart, x->h3, x->resn, x->st);
+            HQ_CUDA(cudaMemcpyAsync(resid, x->resn, sizeof(double) * N, cudaMemcpyDeviceToHost, x->st));
+        }
+    }
+    if (evals_paper)
+        HQ_CUDA(cudaMemcpyAsync(evals_paper, x->lam_p, sizeof(double) * N, cudaMemcpyDeviceToHost, x->st));
+    if (evals_rr)
+        HQ_CUDA(cudaMemcpyAsync(evals_rr, x->lam_r, sizeof(double) * N, cudaMemcpyDeviceToHost, x->st));
+    HQ_CUDA(cudaStreamSynchronize(x->st));
+    return check_launch(x);
+}
+
+template <typename T>
+hq_status trace_impl(hq_ctx *x, void *W, double *gram, double *g, double *XY, void *Uh,
+                     double *Shat, void *Z, void *Unew) {
+    HQ_TRY(need_ready(x));
+    HQ_TRY(clear_status(x));
+    const int N = x->N;
+    const size_t cnt = (size_t)x->n * N;
+    HQ_TRY(phase_a<T>(x));
+    double gh;
+    HQ_TRY(read_g(x, &gh));
+    if (W) HQ_CUDA(cudaMemcpyAsync(W, x->W, cnt * sizeof(T), cudaMemcpyDeviceToDevice, x->st));
+    if (gram) HQ_CUDA(cudaMemcpyAsync(gram, x->G2, sizeof(double) * 4 * N * N, cudaMemcpyDeviceToDevice, x->st));
+    if (g) HQ_CUDA(cudaMemcpyAsync(g, x->scal, sizeof(double), cudaMemcpyDeviceToDevice, x->st));
+    HQ_TRY(phase_b<T>(x));
+    if (XY) HQ_CUDA(cudaMemcpyAsync(XY, x->XY, sizeof(double) * 2 * N * N, cudaMemcpyDeviceToDevice, x->st));
+    if (Uh) HQ_CUDA(cudaMemcpyAsync(Uh, x->Uh, cnt * sizeof(T), cudaMemcpyDeviceToDevice, x->st));
+    if (Shat) HQ_CUDA(cudaMemcpyAsync(Shat, x->Shat, sizeof(double) * N * N, cudaMemcpyDeviceToDevice, x->st));
+    if (Z) HQ_CUDA(cudaMemcpyAsync(Z, x->Z, cnt * sizeof(T), cudaMemcpyDeviceToDevice, x->st));
+    if (Unew) HQ_CUDA(cudaMemcpyAsync(Unew, x->U, cnt * sizeof(T), cudaMemcpyDeviceToDevice, x->st));
+    HQ_CUDA(cudaStreamSynchronize(x->st));
+    return check_launch(x);
+}
+
+template <typename T>
+hq_status level_check(hq_ctx *x, int level, bool need_next) {
+    if (!x->have_V) return fail(x, HQ_ERR_STATE, "hq_set_potential has not been called");
+    if (level < 0 || level >= x->L || (need_next && level + 1 >= x->L))
+        return fail(x, HQ_ERR_ARG, "multigrid level out of range");
+    return HQ_OK;
+}
+
+#define HQ_DISPATCH(x, fn, ...) ((x)->mixed ? fn<float>(__VA_ARGS__) : fn<double>(__VA_ARGS__))
+
+template <typename T>
+hq_status apply_impl(hq_ctx *x, const void *in, void *out, int ncol) {
+    Level &v = x->lev[0];
+    GridGeom g = make_geom(x->m, ncol, (int)sizeof(T));
+    launch_apply<T>(g, (const T *)v.Dt, (T)v.c, (const T *)in, (T *)out, nullptr, x->st);
+    return check_launch(x);
+}
+template <typename T>
+hq_status vcycle_impl(hq_ctx *x, const void *r, void *z) {
+    HQ_TRY(vcycle<T>(x, 0, (const T *)r, (T *)z, (T *)x->Tt, false, nullptr));
+    return check_launch(x);
+}
+template <typename T>
+hq_status pcg_impl(hq_ctx *x, const void *B, void *X, double rtol, int maxit, int *iters) {
+    HQ_TRY(clear_status(x));
+    return pcg<T>(x, (const T *)B, (T *)X, rtol, maxit, iters);
+}
+template <typename T>
+hq_status gram_impl(hq_ctx *x, const void *A, int Na, const void *B, int Nb, double w, double *out) {
+    GramPlan gp = make_gram_plan(x->n, Na, Nb, A == B && Na == Nb);
+    if (gram_partial_bytes(gp) > gram_partial_bytes(x->gplan_max) &&
+        gram_partial_bytes(gp) > gram_partial_bytes(x->gplan_uw))
+        return fail(x, HQ_ERR_ARG, "Gram shape exceeds the workspace plan");
+    launch_gram<T>(gp, (const T *)A, Na, nullptr, 0, (const T *)B, Nb, nullptr, 0, w, x->gpart, out, x->st);
+    return check_launch(x);
+}
+template <typename T>
+hq_status smooth_impl(hq_ctx *x, int l, const void *r, const void *zin, void *zout) {
+    Level &v = x->lev[l];
+    launch_jacobi<T>(v.g, (const T *)v.Dt, (const T *)v.wDt, (T)v.c, (T)(1.0 - x->cfg.mg_omega),
+                     (const T *)r, (const T *)zin, (T *)zout, nullptr, x->st);
+    return check_launch(x);
+}
+template <typename T>
+hq_status restrict_impl(hq_ctx *x, int l, const void *rf, void *rc) {
+    launch_restrict<T>(x->lev[l + 1].g, x->lev[l].m, (const T *)rf, (T *)rc, x->st);
+    return check_launch(x);
+}
+template <typename T>
+hq_status prolong_impl(hq_ctx *x, int l, const void *ec, const void *efin, void *efout) {
+    launch_prolong<T>(x->lev[l].g, x->lev[l + 1].m, (const T *)ec, (const T *)efin, (T *)efout, x->st);
+    return check_launch(x);
+}
+template <typename T>
+hq_status coarse_impl(hq_ctx *x, const void *r, void *z) {
+    launch_coarse_solve<T>(x->lev[x->L - 1].g, x->Ainv, (const T *)r, (T *)z, x->st);
+    return check_launch(x);
+}
+template <typename T>
+hq_status get_state_impl(hq_ctx *x, double *U, double *Zw, int on_device) {
+    if (U) HQ_TRY(store_block<T>(x, U, (const T *)x->U, on_device));
+    if (Zw) {
+        if (!x->z_valid) return fail(x, HQ_ERR_STATE, "no warm-start block yet (no step taken)");
+        HQ_TRY(store_block<T>(x, Zw, (const T *)x->Z, on_device));
+    }
+    HQ_CUDA(cudaStreamSynchronize(x->st));
+    return HQ_OK;
+}
+template <typename T>
+hq_status set_state_impl(hq_ctx *x, const double *U, const double *Zw, int on_device) {
+    HQ_TRY(load_block<T>(x, (T *)x->U, U, on_device));
+    x->have_U = true;
+    x->w_valid = false;
+    x->z_valid = false;
+    if (Zw) {
+        HQ_TRY(load_block<T>(x, (T *)x->Z, Zw, on_device));
+        x->z_valid = true;
+    }
+    HQ_CUDA(cudaStreamSynchronize(x->st));
+    return HQ_OK;
+}
+
+}  // namespace
+
+#define HQ_API_BEGIN try {
+#define HQ_API_END                                                   \
+    }                                                                \
+    catch (...) {                                                    \
+        return HQ_ERR_NOMEM;                                         \
+    }
+
+extern "C" {
+
+void hq_default_config(hq_config *c) {
+    if (!c) return;
+    std::memset(c, 0, sizeof(*c));
+    c->m = 0;
+    c->lo = -6.0;
+    c->hi = 6.0;
+    c->nev = 0;
+    c->tau = 0.4;
+    c->shift = NAN;
+    c->precision = HQ_FP64;
+    c->cg_rtol = 1e-10;
+    c->cg_maxit = 200;
+    c->mg_nu1 = 2;
+    c->mg_nu2 = 2;
+    c->mg_coarsest = 4;
+    c->mg_omega = 0.8;
+    c->timeout_s = 0.0;
+}
+
+size_t hq_workspace_bytes(const hq_config *cfg) {
+    if (!valid_config(cfg, nullptr)) return 0;
+    try {
+        return carve(nullptr, cfg, nullptr);
+    } catch (...) {
+        return 0;
+    }
+}
+
+hq_status hq_init(const hq_config *cfg, void *d_workspace, size_t bytes, void *cuda_stream,
+                  hq_ctx **out) {
+    HQ_API_BEGIN
+    if (!out) return HQ_ERR_ARG;
+    *out = nullptr;
+    std::string why;
+    if (!valid_config(cfg, &why)) return HQ_ERR_ARG;
+    size_t need = carve(nullptr, cfg, nullptr);
+    if (!d_workspace || bytes < need) return HQ_ERR_NOMEM;
+    if (((uintptr_t)d_workspace & 255u) != 0) return HQ_ERR_ARG;
+    hq_ctx *x = new hq_ctx();
+    x->cfg = *cfg;
+    x->mixed = cfg->precision == HQ_MIXED;
+    x->esz = x->mixed ? 4 : 8;
+    x->m = cfg->m;
+    x->N = cfg->nev;
+    x->n = (long)cfg->m * cfg->m * cfg->m;
+    x->h = (cfg->hi - cfg->lo) / (cfg->m + 1);
+    x->h3 = x->h * x->h * x->h;
+    x->st = (cudaStream_t)cuda_stream;
+    x->ws = (char *)d_workspace;
+    x->ws_bytes = bytes;
+    carve(x, cfg, x->ws);
+    // the status words start cleared
+    cudaError_t e = cudaMemsetAsync(x->sc.status, 0, sizeof(int), x->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(x->status, 0, sizeof(int), x->st);
+    if (e != cudaSuccess) {
+        delete x;
+        return HQ_ERR_CUDA;
+    }
+    *out = x;
+    return HQ_OK;
+    HQ_API_END
+}
+
+hq_status hq_set_potential(hq_ctx *x, const double *V, int on_device) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    if (!V) return fail(x, HQ_ERR_ARG, "V is null");
+    return HQ_DISPATCH(x, set_potential_impl, x, V, on_device);
+    HQ_API_END
+}
+
+hq_status hq_set_initial(hq_ctx *x, const double *U0, int on_device) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    if (!U0) return fail(x, HQ_ERR_ARG, "U0 is null");
+    return HQ_DISPATCH(x, set_initial_impl, x, U0, on_device);
+    HQ_API_END
+}
+
+hq_status hq_step(hq_ctx *x, int nsteps, double *resid_out) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    if (nsteps < 0) return fail(x, HQ_ERR_ARG, "nsteps < 0");
+    return HQ_DISPATCH(x, step_impl, x, nsteps, resid_out);
+    HQ_API_END
+}
+
+hq_status hq_solve(hq_ctx *x, double eps, long max_steps, long *steps_out, double *resid_out) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    if (!(eps > 0.0) || max_steps < 0) return fail(x, HQ_ERR_ARG, "eps must be > 0, max_steps >= 0");
+    return HQ_DISPATCH(x, solve_impl, x, eps, max_steps, steps_out, resid_out);
+    HQ_API_END
+}
+
+hq_status hq_eigenpairs(hq_ctx *x, double *evals_paper, double *evals_rr, double *evecs,
+                        int evecs_on_device, double *resid) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    return HQ_DISPATCH(x, eigen_impl, x, evals_paper, evals_rr, evecs, evecs_on_device, resid);
+    HQ_API_END
+}
+
+hq_status hq_get_state(hq_ctx *x, double *U, double *Zwarm, int on_device, long *step) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    if (!x->have_U) return fail(x, HQ_ERR_STATE, "no iterate");
+    HQ_TRY(HQ_DISPATCH(x, get_state_impl, x, U, Zwarm, on_device));
+    if (step) *step = x->step;
+    return HQ_OK;
+    HQ_API_END
+}
+
+hq_status hq_set_state(hq_ctx *x, const double *U, const double *Zwarm, int on_device, long step) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    if (!U || step < 0) return fail(x, HQ_ERR_ARG, "U is null or step < 0");
+    HQ_TRY(HQ_DISPATCH(x, set_state_impl, x, U, Zwarm, on_device));
+    x->step = step;
+    return HQ_OK;
+    HQ_API_END
+}
+
+hq_status hq_problem_info(hq_ctx *x, double *h, double *sigma, int *levels, int *level_m) {
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    if (h) *h = x->h;
+    if (sigma) *sigma = x->sigma;
+    if (levels) *levels = x->L;
+    if (level_m)
+        for (int l = 0; l < x->L; l++) level_m[l] = x->lev[l].m;
+    return HQ_OK;
+}
+
+hq_status hq_apply_operator(hq_ctx *x, const void *in, void *out, int ncol) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    if (!x->have_V) return fail(x, HQ_ERR_STATE, "hq_set_potential has not been called");
+    if (!in || !out || ncol < 1 || ncol > x->N) return fail(x, HQ_ERR_ARG, "bad operand");
+    return HQ_DISPATCH(x, apply_impl, x, in, out, ncol);
+    HQ_API_END
+}
+
+hq_status hq_mg_vcycle(hq_ctx *x, const void *r, void *z) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    if (!x->have_V) return fail(x, HQ_ERR_STATE, "hq_set_potential has not been called");
+    if (!r || !z) return fail(x, HQ_ERR_ARG, "null operand");
+    return HQ_DISPATCH(x, vcycle_impl, x, r, z);
+    HQ_API_END
+}
+
+hq_status hq_block_pcg(hq_ctx *x, const void *B, void *X, double rtol, int maxit, int *iters) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    if (!x->have_V) return fail(x, HQ_ERR_STATE, "hq_set_potential has not been called");
+    if (!B || !X || maxit < 0 || !(rtol >= 0.0)) return fail(x, HQ_ERR_ARG, "bad operand");
+    return HQ_DISPATCH(x, pcg_impl, x, B, X, rtol, maxit, iters);
+    HQ_API_END
+}
+
+hq_status hq_gram(hq_ctx *x, const void *A, int Na, const void *B, int Nb, double w, double *out) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    if (!A || !B || !out || Na < 1 || Nb < 1 || Na > 2 * x->N || Nb > 2 * x->N)
+        return fail(x, HQ_ERR_ARG, "bad operand");
+    return HQ_DISPATCH(x, gram_impl, x, A, Na, B, Nb, w, out);
+    HQ_API_END
+}
+
+hq_status hq_step_trace(hq_ctx *x, void *W, double *gram, double *g, double *XY, void *Uh,
+                        double *Shat, void *Z, void *Unew) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    return HQ_DISPATCH(x, trace_impl, x, W, gram, g, XY, Uh, Shat, Z, Unew);
+    HQ_API_END
+}
+
+hq_status hq_mg_smooth(hq_ctx *x, int level, const void *r, const void *z_in, void *z_out) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    HQ_TRY(HQ_DISPATCH(x, level_check, x, level, false));
+    if (!r || !z_in || !z_out || z_in == z_out) return fail(x, HQ_ERR_ARG, "bad operand");
+    return HQ_DISPATCH(x, smooth_impl, x, level, r, z_in, z_out);
+    HQ_API_END
+}
+
+hq_status hq_mg_restrict(hq_ctx *x, int level, const void *rf, void *rc) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    HQ_TRY(HQ_DISPATCH(x, level_check, x, level, true));
+    if (!rf || !rc) return fail(x, HQ_ERR_ARG, "bad operand");
+    return HQ_DISPATCH(x, restrict_impl, x, level, rf, rc);
+    HQ_API_END
+}
+
+hq_status hq_mg_prolong(hq_ctx *x, int level, const void *ec, const void *ef_in, void *ef_out) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    HQ_TRY(HQ_DISPATCH(x, level_check, x, level, true));
+    if (!ec || !ef_in || !ef_out) return fail(x, HQ_ERR_ARG, "bad operand");
+    return HQ_DISPATCH(x, prolong_impl, x, level, ec, ef_in, ef_out);
+    HQ_API_END
+}
+
+hq_status hq_mg_coarse_solve(hq_ctx *x, const void *r, void *z) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    if (!x->have_V) return fail(x, HQ_ERR_STATE, "hq_set_potential has not been called");
+    if (!r || !z) return fail(x, HQ_ERR_ARG, "bad operand");
+    return HQ_DISPATCH(x, coarse_impl, x, r, z);
+    HQ_API_END
+}
+
+hq_status hq_mg_level_potential(hq_ctx *x, int level, double *V_out) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    HQ_TRY(HQ_DISPATCH(x, level_check, x, level, false));
+    if (!V_out) return fail(x, HQ_ERR_ARG, "bad operand");
+    HQ_CUDA(cudaMemcpyAsync(V_out, x->lev[level].V, sizeof(double) * x->lev[level].n,
+                            cudaMemcpyDeviceToDevice, x->st));
+    return HQ_OK;
+    HQ_API_END
+}
+
+hq_status hq_profile(hq_ctx *x, int timing) {
+    HQ_TRY(guard(x));
+    for (int i = 0; i < HQ_K_NCLASS; i++) x->launches[i] = 0;
+    x->timing = timing != 0;
+    x->evused = 0;
+    x->evrec.clear();
+    return HQ_OK;
+}
+
+hq_status hq_profile_read(hq_ctx *x, long *launches, double *ms) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    HQ_CUDA(cudaStreamSynchronize(x->st));
+    if (launches)
+        for (int i = 0; i < HQ_K_NCLASS; i++) launches[i] = x->launches[i];
+    if (ms) {
+        for (int i = 0; i < HQ_K_NCLASS; i++) ms[i] = 0.0;
+        for (auto &r : x->evrec) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, x->evpool[r.second], x->evpool[r.second + 1]) == cudaSuccess)
+                ms[r.first] += t;
+        }
+    }
+    return HQ_OK;
+    HQ_API_END
+}
+
+const char *hq_last_error(hq_ctx *x) { return x ? x->err.c_str() : "null context"; }
+
+const char *hq_status_string(hq_status s) {
+    switch (s) {
+    case HQ_OK: return "ok";
+    case HQ_ERR_ARG: return "invalid argument";
+    case HQ_ERR_STATE: return "call out of order";
+    case HQ_ERR_CUDA: return "CUDA error";
+    case HQ_ERR_NOMEM: return "insufficient workspace or host memory";
+    case HQ_ERR_BREAKDOWN: return "inner CG breakdown";
+    case HQ_ERR_SINGULAR: return "singular predictor system";
+    case HQ_ERR_NOT_CONVERGED: return "not converged";
+    case HQ_ERR_TIMEOUT: return "timeout";
+    case HQ_ERR_NONFINITE: return "non-finite value";
+    }
+    return "unknown status";
+}
+
+void hq_destroy(hq_ctx *x) { delete x; }
+
+}  // extern "C"

@@ -1,0 +1,193 @@
+// Internal declarations shared by the CUDA translation units of libhq.
+// Layout conventions: an n x N block is point-major (element (p, c) at
+// p*N + c); grid node (i, j, k) of an m^3 grid is p = i + m*(j + m*k).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "../../include/hq.h"
+#include <stdint.h>
+#include <stddef.h>
+
+namespace hq {
+
+// launch instrumentation: every kernel launch is bracketed by these hooks,
+// which count launches per class and optionally record CUDA events.
+void hook_before(int cls);
+void hook_after(int cls);
+#define HQ_LAUNCH(cls, ...)          \
+    do {                             \
+        ::hq::hook_before(cls);      \
+        __VA_ARGS__;                 \
+        ::hq::hook_after(cls);       \
+    } while (0)
+
+// ----------------------------------------------------------------------------
+// launch geometry of the point-major grid kernels
+// ----------------------------------------------------------------------------
+struct GridGeom {
+    int m;          // nodes per side
+    long n;         // m^3
+    int N;          // columns (= leading dimension)
+    int vec;        // columns per thread (vector width)
+    int tx, ty;     // block shape: tx column-vectors x ty points
+    int gx, gy;     // grid shape
+    int ppt;        // points per thread (consecutive slabs of ty points)
+};
+GridGeom make_geom(int m, int N, int elem_bytes);
+
+// per-column PCG scalars, all device arrays of length N (FP64)
+struct PcgScalars {
+    double *rz, *alpha, *beta, *bnorm, *rnorm;
+    int *active, *iters;
+    int *num_active;   // 1 int
+    int *status;       // 1 int, sticky error flags (bit 0: breakdown)
+};
+
+enum { ST_BREAKDOWN = 1, ST_SINGULAR = 2, ST_NONFINITE = 4, ST_GJ_FAIL = 8 };
+
+// ----------------------------------------------------------------------------
+// grid kernels (k_grid.cu); T = double or float
+// ----------------------------------------------------------------------------
+// y = A x with A = (H + sigma) on a level: A x = D x - c * (sum of 6 nbrs).
+// Optional per-column partial of x.y (part_xy, gy x N) .
+template <typename T>
+void launch_apply(const GridGeom &g, const T *D, T c, const T *x, T *y, double *part_xy,
+                  cudaStream_t s);
+// y = b - A x, partials of y.y and b.b (nullable)
+template <typename T>
+void launch_resid(const GridGeom &g, const T *D, T c, const T *x, const T *b, T *y,
+                  double *part_yy, double *part_bb, cudaStream_t s);
+// x += alpha p, r -= alpha q (per-column alpha), partial r.r; if zf != null also
+// zf = wD * r (first damped-Jacobi sweep from zero).
+template <typename T>
+void launch_pcg_xr(const GridGeom &g, const double *alpha, const T *p, const T *q, T *x, T *r,
+                   double *part_rr, const T *wD, T *zf, cudaStream_t s);
+// p = z + beta p
+template <typename T>
+void launch_pcg_p(const GridGeom &g, const double *beta, const T *z, T *p, cudaStream_t s);
+// z_out = z_in + wD (r - A z_in); partial r.z_out (nullable)
+template <typename T>
+void launch_jacobi(const GridGeom &g, const T *D, const T *wD, T c, T one_minus_omega,
+                   const T *r, const T *zin, T *zout, double *part_rz, cudaStream_t s);
+// z = wD * r
+template <typename T>
+void launch_jacobi_first(const GridGeom &g, const T *wD, const T *r, T *z, cudaStream_t s);
+// rc = ((mc+1)/(mf+1))^3 P^T rf
+template <typename T>
+void launch_restrict(const GridGeom &gc, int mf, const T *rf, T *rc, cudaStream_t s);
+// ef_out = ef_in + P ec
+template <typename T>
+void launch_prolong(const GridGeom &gf, int mc, const T *ec, const T *efin, T *efout,
+                    cudaStream_t s);
+// z = Ainv r on the coarsest level (Ainv nc x nc, FP64)
+template <typename T>
+void launch_coarse_solve(const GridGeom &g, const double *Ainv, const T *r, T *z,
+                         cudaStream_t s);
+// partial of x.y per column
+template <typename T>
+void launch_dot(const GridGeom &g, const T *x, const T *y, double *part, cudaStream_t s);
+
+// per-column reduction of gy partials + PCG scalar logic
+enum FinMode { FIN_BNORM_RNORM = 0, FIN_ALPHA = 1, FIN_RR = 2, FIN_BETA = 3, FIN_RZ = 4 };
+void launch_finalize(int mode, int N, int gy, const double *part, const double *part2,
+                     PcgScalars sc, double rtol, cudaStream_t s);
+
+// setup
+void launch_coarse_potential(int mf, const double *Vf, int mc, double *Vc, cudaStream_t s);
+void launch_level_diag(long n, const double *V, double sigma, double c, double omega,
+                       double *D, double *wD, cudaStream_t s);
+void launch_assemble_dense(int mc, double c, const double *V, double sigma, double *A,
+                           cudaStream_t s);
+void launch_gauss_jordan(int nc, double *A, double *Ainv, int *status, cudaStream_t s);
+void launch_minmax(long n, const double *V, double *out2 /* [min, max-abs-nonfinite flag] */,
+                   cudaStream_t s);
+void launch_convert_d2f(size_t count, const double *in, float *out, cudaStream_t s);
+void launch_convert_f2d(size_t count, const float *in, double *out, cudaStream_t s);
+template <typename T>
+void launch_scale(size_t count, const double *factor, T *x, cudaStream_t s);
+
+// ----------------------------------------------------------------------------
+// dense kernels (k_dense.cu)
+// ----------------------------------------------------------------------------
+// Gram of logical blocks A = [A1 A2] (n x (na1+na2)) and B = [B1 B2]:
+// out = w A^T B  (FP64, row-major).  If sym, A == B and only the upper tiles
+// are computed (mirrored).  partials: workspace of gram_partial_bytes().
+struct GramPlan {
+    long n;
+    int na, nb, tiles_a, tiles_b, ntiles, chunks;
+    long chunk_rows;
+    bool sym;
+};
+GramPlan make_gram_plan(long n, int na, int nb, bool sym);
+size_t gram_partial_bytes(const GramPlan &p);
+template <typename T>
+void launch_gram(const GramPlan &p, const T *A1, int na1, const T *A2, int na2, const T *B1,
+                 int nb1, const T *B2, int nb2, double w, double *partials, double *out,
+                 cudaStream_t s);
+
+// Out = A1 M1 (+ A2 M2) (+ Cin), M's are FP64 K x Ncol row-major; optional
+// partial sum of squares of Out (one double per CTA, npart entries).
+struct TallPlan {
+    long n;
+    int ncol, k1, k2;
+    int gx, gy;
+};
+TallPlan make_tall_plan(long n, int ncol, int k1, int k2);
+template <typename T>
+void launch_tall_gemm(const TallPlan &p, const T *A1, const double *M1, const T *A2,
+                      const double *M2, const T *Cin, T *Out, double *part_sq,
+                      cudaStream_t s);
+// same with per-column partial sums of squares (gy x ncol)
+template <typename T>
+void launch_tall_gemm_colsq(const TallPlan &p, const T *A1, const double *M1, const T *A2,
+                            const double *M2, const T *Cin, T *Out, double *part_sq,
+                            cudaStream_t s);
+// dst (rows x cols, ld ldd) = alpha * src (ld lds)
+void launch_extract(int rows, int cols, double alpha, const double *src, int lds, double *dst,
+                    int ldd, cudaStream_t s);
+// out[i][j] = -Cv[i][j] * (lam[j] + add)   (N x N)
+void launch_scale_cols(int N, const double *Cv, const double *lam, double add, double *out,
+                       cudaStream_t s);
+// out[0] = sqrt(w * sum(part[0..np)))
+void launch_sum_sqrt(int np, const double *part, double w, double *out, cudaStream_t s);
+// per-column version: part is np x ncol, out[c] = sqrt(w * sum_i part[i*ncol+c])
+void launch_colsum_sqrt(int np, int ncol, const double *part, double w, double *out,
+                        cudaStream_t s);
+
+// C = alpha op(A) op(B) + beta C (FP64, row-major, small)
+void launch_small_gemm(int M, int Ncol, int K, double alpha, const double *A, int lda, bool ta,
+                       const double *B, int ldb, bool tb, double beta, double *C, int ldc,
+                       cudaStream_t s);
+// predictor system of Eq. (4.1): from the 2N x 2N Gram of [U W] build
+//   [I - tau/2 Puw, tau/2 S; -tau/2 Q, I + tau/2 Pwu] [X;Y] = [S; Pwu]
+// and solve by LU with partial pivoting.  Mwork: 4N^2, XY: 2N x N.  Then
+// C = [I - tau Y; tau X] (2N x N).
+void launch_predictor_solve(int N, double tau, const double *G2, double *Mwork, double *XY,
+                            double *C, int *status, cudaStream_t s);
+// A += v I (N x N) in place
+void launch_add_diag(int N, double *A, double v, cudaStream_t s);
+// out = alpha * in  (count values)
+void launch_dscale(int count, double alpha, const double *in, double *out, cudaStream_t s);
+// symmetric eigen (cyclic Jacobi, one CTA): ascending evals, evecs columns (N x N)
+void launch_sym_eig(int N, const double *A, double *work, double *evals, double *evecs,
+                    cudaStream_t s);
+// Rayleigh-Ritz reduction: given K (N x N, symmetrised inside) and S (SPD),
+// Cm = L^{-1} K L^{-T} with S = L L^T; Linv kept in L (lower).  One CTA.
+void launch_rr_reduce(int N, const double *K, const double *S, double *L, double *Cm,
+                      int *status, cudaStream_t s);
+// c = L^{-T} y  (columns of Y), Cv output N x N
+void launch_rr_back(int N, const double *L, const double *Y, double *Cv, cudaStream_t s);
+// scale factor 1/sqrt(evals[0]) -> out
+void launch_inv_sqrt_first(const double *evals, double *out, cudaStream_t s);
+// lam_paper[i] = 1/mu[N-1-i] - sigma
+void launch_paper_evals(int N, const double *mu, double sigma, double *lam, cudaStream_t s);
+// subtract sigma from each of N values
+void launch_add_scalar(int N, const double *in, double add, double *out, cudaStream_t s);
+// K -= sigma * S (elementwise N x N)
+void launch_axpy_small(int count, double a, const double *x, double *y, cudaStream_t s);
+// Ritz-vector sign: flip column c if its largest-magnitude entry is negative
+template <typename T>
+void launch_fix_signs(long n, int N, T *U, double *work /* gx*N*2 */, cudaStream_t s);
+// M3 = C1 + Msmall C2 etc. are done with small_gemm.
+
+}  // namespace hq

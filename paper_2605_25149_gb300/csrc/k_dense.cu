@@ -1,0 +1,783 @@
+// Dense kernels of the scheme: inner-product matrices <A,B> = w A^T B of
+// tall-skinny blocks (split over grid points, fixed-order reduction), the
+// block x small-matrix products of the predictor / corrector updates, and
+// the small FP64 algebra (predictor system of Eq. (4.1) by LU with partial
+// pivoting, cyclic Jacobi eigensolver, Rayleigh-Ritz reduction).
+#include "hq_internal.cuh"
+
+#include <algorithm>
+
+namespace hq {
+
+// ---------------------------------------------------------------------------
+// Gram: out = w [A1 A2]^T [B1 B2], tiles of 64 x 64, split over point chunks.
+// ---------------------------------------------------------------------------
+constexpr int GT = 64;   // tile edge
+constexpr int GK = 16;   // points per smem stage
+
+GramPlan make_gram_plan(long n, int na, int nb, bool sym) {
+    GramPlan p;
+    p.n = n;
+    p.na = na;
+    p.nb = nb;
+    p.sym = sym;
+    p.tiles_a = (na + GT - 1) / GT;
+    p.tiles_b = (nb + GT - 1) / GT;
+    p.ntiles = sym ? p.tiles_a * (p.tiles_a + 1) / 2 : p.tiles_a * p.tiles_b;
+    long target = std::max(1L, (long)(2 * 152) / p.ntiles);
+    long maxchunks = std::max(1L, (n + GT - 1) / GT);
+    long chunks = std::min(target, maxchunks);
+    long rows = (n + chunks - 1) / chunks;
+    rows = (rows + GK - 1) / GK * GK;
+    p.chunk_rows = rows;
+    p.chunks = (int)((n + rows - 1) / rows);
+    return p;
+}
+
+size_t gram_partial_bytes(const GramPlan &p) {
+    return sizeof(double) * (size_t)p.chunks * p.ntiles * GT * GT;
+}
+
+__device__ __forceinline__ void tile_of(int t, int tiles_a, bool sym, int &ta, int &tb) {
+    if (!sym) {
+        ta = t % tiles_a;
+        tb = t / tiles_a;
+        return;
+    }
+    // upper triangle, row-major over (ta <= tb)
+    int r = 0, rem = t;
+    while (rem >= tiles_a - r) {
+        rem -= tiles_a - r;
+        r++;
+    }
+    ta = r;
+    tb = r + rem;
+}
+
+template <typename T>
+__device__ __forceinline__ T gat(const T *X1, int n1, const T *X2, int n2, long p, int c) {
+    return c < n1 ? X1[(size_t)p * n1 + c] : X2[(size_t)p * n2 + (c - n1)];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gram_partial(GramPlan P, const T *A1, int na1,
+                                                      const T *A2, int na2, const T *B1,
+                                                      int nb1, const T *B2, int nb2,
+                                                      double *partials) {
+    __shared__ T As[GK][GT + 1];
+    __shared__ T Bs[GK][GT + 1];
+    const int tile = blockIdx.x, chunk = blockIdx.y;
+    int ta, tb;
+    tile_of(tile, P.tiles_a, P.sym, ta, tb);
+    const int a0 = ta * GT, b0 = tb * GT;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const long r0 = (long)chunk * P.chunk_rows;
+    const long r1 = (P.n < r0 + P.chunk_rows) ? P.n : r0 + P.chunk_rows;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = T(0);
+    for (long p0 = r0; p0 < r1; p0 += GK) {
+        for (int idx = threadIdx.x; idx < GK * GT; idx += 256) {
+            int kk = idx / GT, c = idx % GT;
+            long p = p0 + kk;
+            int ca = a0 + c, cb = b0 + c;
+            As[kk][c] = (p < r1 && ca < P.na) ? gat(A1, na1, A2, na2, p, ca) : T(0);
+            Bs[kk][c] = (p < r1 && cb < P.nb) ? gat(B1, nb1, B2, nb2, p, cb) : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GK; kk++) {
+            T a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; j++) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+    double *dst = partials + ((size_t)chunk * P.ntiles + tile) * GT * GT;
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) dst[(ty + 16 * i) * GT + tx + 16 * j] = (double)acc[i][j];
+}
+
+__global__ void k_gram_reduce(GramPlan P, const double *partials, double w, double *out) {
+    const int tile = blockIdx.x;
+    int ta, tb;
+    tile_of(tile, P.tiles_a, P.sym, ta, tb);
+    for (int e = threadIdx.x; e < GT * GT; e += blockDim.x) {
+        int la = e / GT, lb = e % GT;
+        int a = ta * GT + la, b = tb * GT + lb;
+        if (a >= P.na || b >= P.nb) continue;
+        double s = 0.0;
+        for (int c = 0; c < P.chunks; c++)
+            s += partials[((size_t)c * P.ntiles + tile) * GT * GT + e];
+        s *= w;
+        out[(size_t)a * P.nb + b] = s;
+        if (P.sym && ta != tb) out[(size_t)b * P.nb + a] = s;
+    }
+}
+
+template <typename T>
+void launch_gram(const GramPlan &p, const T *A1, int na1, const T *A2, int na2, const T *B1,
+                 int nb1, const T *B2, int nb2, double w, double *partials, double *out,
+                 cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_GRAM, k_gram_partial<T><<<dim3(p.ntiles, p.chunks), 256, 0, s>>>(p, A1, na1, A2, na2, B1, nb1,
+                                                               B2, nb2, partials));
+    HQ_LAUNCH(HQ_K_GRAM, k_gram_reduce<<<p.ntiles, 256, 0, s>>>(p, partials, w, out));
+}
+
+// ---------------------------------------------------------------------------
+// Tall GEMM: Out = A1 M1 + A2 M2 + Cin (64 x 64 output tiles)
+// ---------------------------------------------------------------------------
+constexpr int TBP = 64, TBN = 64, TKC = 16;
+
+TallPlan make_tall_plan(long n, int ncol, int k1, int k2) {
+    TallPlan p;
+    p.n = n;
+    p.ncol = ncol;
+    p.k1 = k1;
+    p.k2 = k2;
+    p.gx = (ncol + TBN - 1) / TBN;
+    p.gy = (int)((n + TBP - 1) / TBP);
+    return p;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_tall_gemm(TallPlan P, const T *A1, const double *M1,
+                                                   const T *A2, const double *M2, const T *Cin,
+                                                   T *Out, double *part_sq, int colwise) {
+    __shared__ T As[TBP][TKC + 1];
+    __shared__ T Ms[TKC][TBN + 1];
+    __shared__ double red[256];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const long p0 = (long)blockIdx.y * TBP;
+    const int c0 = blockIdx.x * TBN;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = T(0);
+    for (int pass = 0; pass < 2; pass++) {
+        const T *A = pass == 0 ? A1 : A2;
+        const double *M = pass == 0 ? M1 : M2;
+        const int K = pass == 0 ? P.k1 : P.k2;
+        if (A == nullptr || K == 0) continue;
+        for (int k0 = 0; k0 < K; k0 += TKC) {
+            for (int idx = threadIdx.x; idx < TBP * TKC; idx += 256) {
+                int r = idx / TKC, kk = idx % TKC;
+                long p = p0 + r;
+                As[r][kk] = (p < P.n && k0 + kk < K) ? A[(size_t)p * K + k0 + kk] : T(0);
+            }
+            for (int idx = threadIdx.x; idx < TKC * TBN; idx += 256) {
+                int kk = idx / TBN, c = idx % TBN;
+                Ms[kk][c] = (k0 + kk < K && c0 + c < P.ncol)
+                                ? (T)M[(size_t)(k0 + kk) * P.ncol + c0 + c]
+                                : T(0);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < TKC; kk++) {
+                T a[4], b[4];
+#pragma unroll
+                for (int i = 0; i < 4; i++) a[i] = As[ty + 16 * i][kk];
+#pragma unroll
+                for (int j = 0; j < 4; j++) b[j] = Ms[kk][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+#pragma unroll
+                    for (int j = 0; j < 4; j++) acc[i][j] += a[i] * b[j];
+            }
+            __syncthreads();
+        }
+    }
+    double sq = 0.0;
+    double sqc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        long p = p0 + ty + 16 * i;
+        if (p >= P.n) continue;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            int c = c0 + tx + 16 * j;
+            if (c >= P.ncol) continue;
+            size_t e = (size_t)p * P.ncol + c;
+            T v = acc[i][j];
+            if (Cin) v = Cin[e] + v;
+            if (Out) Out[e] = v;
+            double dv = (double)v;
+            sq += dv * dv;
+            sqc[j] += dv * dv;
+        }
+    }
+    if (part_sq) {
+        if (!colwise) {
+            red[threadIdx.x] = sq;
+            __syncthreads();
+            for (int w = 128; w > 0; w >>= 1) {
+                if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) part_sq[(size_t)blockIdx.y * P.gx + blockIdx.x] = red[0];
+        } else {
+            // per column: reduce over ty (16 rows of threads) in order
+            for (int j = 0; j < 4; j++) {
+                red[threadIdx.x] = sqc[j];
+                __syncthreads();
+                if (ty == 0) {
+                    double s = 0.0;
+                    for (int y = 0; y < 16; y++) s += red[y * 16 + tx];
+                    int c = c0 + tx + 16 * j;
+                    if (c < P.ncol) part_sq[(size_t)blockIdx.y * P.ncol + c] = s;
+                }
+                __syncthreads();
+            }
+        }
+    }
+}
+
+template <typename T>
+void launch_tall_gemm(const TallPlan &p, const T *A1, const double *M1, const T *A2,
+                      const double *M2, const T *Cin, T *Out, double *part_sq,
+                      cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_BLOCKGEMM, k_tall_gemm<T><<<dim3(p.gx, p.gy), 256, 0, s>>>(p, A1, M1, A2, M2, Cin, Out, part_sq, 0));
+}
+template <typename T>
+void launch_tall_gemm_colsq(const TallPlan &p, const T *A1, const double *M1, const T *A2,
+                            const double *M2, const T *Cin, T *Out, double *part_sq,
+                            cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_BLOCKGEMM, k_tall_gemm<T><<<dim3(p.gx, p.gy), 256, 0, s>>>(p, A1, M1, A2, M2, Cin, Out, part_sq, 1));
+}
+
+__global__ void k_sum_sqrt(int np, const double *part, double w, double *out) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < np; i += 256) s += part[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sqrt(w * red[0]);
+}
+void launch_sum_sqrt(int np, const double *part, double w, double *out, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_REDUCE, k_sum_sqrt<<<1, 256, 0, s>>>(np, part, w, out));
+}
+
+__global__ void k_colsum_sqrt(int np, int ncol, const double *part, double w, double *out) {
+    __shared__ double red[128];
+    const int c = blockIdx.x;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < np; i += 128) s += part[(size_t)i * ncol + c];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = 64; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = sqrt(w * red[0]);
+}
+void launch_colsum_sqrt(int np, int ncol, const double *part, double w, double *out,
+                        cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_REDUCE, k_colsum_sqrt<<<ncol, 128, 0, s>>>(np, ncol, part, w, out));
+}
+
+// ---------------------------------------------------------------------------
+// small FP64 algebra
+// ---------------------------------------------------------------------------
+__global__ void k_small_gemm(int M, int Nc, int K, double alpha, const double *A, int lda,
+                             int ta, const double *B, int ldb, int tb, double beta, double *C,
+                             int ldc) {
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < (long)M * Nc;
+         idx += (long)gridDim.x * blockDim.x) {
+        int i = (int)(idx / Nc), j = (int)(idx % Nc);
+        double s = 0.0;
+        for (int k = 0; k < K; k++) {
+            double a = ta ? A[(size_t)k * lda + i] : A[(size_t)i * lda + k];
+            double b = tb ? B[(size_t)j * ldb + k] : B[(size_t)k * ldb + j];
+            s += a * b;
+        }
+        double c = beta == 0.0 ? 0.0 : beta * C[(size_t)i * ldc + j];
+        C[(size_t)i * ldc + j] = c + alpha * s;
+    }
+}
+void launch_small_gemm(int M, int Ncol, int K, double alpha, const double *A, int lda, bool ta,
+                       const double *B, int ldb, bool tb, double beta, double *C, int ldc,
+                       cudaStream_t s) {
+    long tot = (long)M * Ncol;
+    int blocks = (int)std::min<long>((tot + 255) / 256, 1024);
+    HQ_LAUNCH(HQ_K_SMALL, k_small_gemm<<<blocks, 256, 0, s>>>(M, Ncol, K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc));
+}
+
+// Predictor system of Eq. (4.1) (one CTA).
+__global__ void __launch_bounds__(1024) k_predictor_solve(int N, double tau, const double *G2,
+                                                          double *Mw, double *XY, double *C,
+                                                          int *status) {
+    extern __shared__ double sh[];
+    double *lcol = sh;                       // 2N
+    double *rv = sh + 2 * N;                 // 1024 reduction values
+    int *ri = (int *)(rv + 1024);            // 1024 reduction indices
+    const int nn = 2 * N, ld2 = 2 * N;
+    const int T = blockDim.x, tid = threadIdx.x;
+    const double ht = 0.5 * tau;
+    // build [I - tau/2 Puw, tau/2 S; -tau/2 Q, I + tau/2 Pwu] and [S; Pwu]
+    for (long idx = tid; idx < (long)nn * nn; idx += T) {
+        int i = (int)(idx / nn), j = (int)(idx % nn);
+        double d = (i == j) ? 1.0 : 0.0;   // G2 rows / columns: [U W]
+        double v;
+        if (i < N && j < N) v = ht * G2[(size_t)i * ld2 + N + j] * -1.0 + d;     // I - tau/2 Puw
+        else if (i < N) v = ht * G2[(size_t)i * ld2 + (j - N)];                  // tau/2 S
+        else if (j < N) v = -ht * G2[(size_t)i * ld2 + N + j];                   // -tau/2 Q
+        else v = d + ht * G2[(size_t)i * ld2 + (j - N)];                         // I + tau/2 Pwu
+        Mw[idx] = v;
+    }
+    for (long idx = tid; idx < (long)nn * N; idx += T) {
+        int i = (int)(idx / N), j = (int)(idx % N);
+        XY[idx] = G2[(size_t)i * ld2 + j];   // rows 0..N-1: S; rows N..2N-1: Pwu
+    }
+    __syncthreads();
+    for (int k = 0; k < nn; k++) {
+        // pivot: max |M[i][k]|, i >= k, first index on ties
+        double best = -1.0;
+        int bi = nn;
+        for (int i = k + tid; i < nn; i += T) {
+            double v = fabs(Mw[(size_t)i * nn + k]);
+            if (v > best) { best = v; bi = i; }
+        }
+        rv[tid] = best;
+        ri[tid] = bi;
+        __syncthreads();
+        for (int w = T / 2; w > 0; w >>= 1) {
+            if (tid < w) {
+                double v2 = rv[tid + w];
+                int i2 = ri[tid + w];
+                if (v2 > rv[tid] || (v2 == rv[tid] && i2 < ri[tid])) { rv[tid] = v2; ri[tid] = i2; }
+            }
+            __syncthreads();
+        }
+        const int piv = ri[0];
+        const double pval = rv[0];
+        __syncthreads();
+        if (!(pval > 0.0) || !isfinite(pval)) {
+            if (tid == 0) atomicOr(status, ST_SINGULAR);
+            return;
+        }
+        if (piv != k) {
+            for (int j = tid; j < nn; j += T) {
+                double t = Mw[(size_t)k * nn + j];
+                Mw[(size_t)k * nn + j] = Mw[(size_t)piv * nn + j];
+                Mw[(size_t)piv * nn + j] = t;
+            }
+            for (int j = tid; j < N; j += T) {
+                double t = XY[(size_t)k * N + j];
+                XY[(size_t)k * N + j] = XY[(size_t)piv * N + j];
+                XY[(size_t)piv * N + j] = t;
+            }
+        }
+        __syncthreads();
+        const double dkk = Mw[(size_t)k * nn + k];
+        for (int i = k + 1 + tid; i < nn; i += T) {
+            double f = Mw[(size_t)i * nn + k] / dkk;
+            Mw[(size_t)i * nn + k] = f;
+            lcol[i] = f;
+        }
+        __syncthreads();
+        const int rows = nn - k - 1, cols = nn - k - 1 + N;
+        for (long idx = tid; idx < (long)rows * cols; idx += T) {
+            int i = k + 1 + (int)(idx / cols);
+            int c = (int)(idx % cols);
+            double f = lcol[i];
+            if (c < nn - k - 1) {
+                int j = k + 1 + c;
+                Mw[(size_t)i * nn + j] -= f * Mw[(size_t)k * nn + j];
+            } else {
+                int j = c - (nn - k - 1);
+                XY[(size_t)i * N + j] -= f * XY[(size_t)k * N + j];
+            }
+        }
+        __syncthreads();
+    }
+    // back substitution (column-oriented)
+    for (int i = nn - 1; i >= 0; i--) {
+        const double dii = Mw[(size_t)i * nn + i];
+        for (int j = tid; j < N; j += T) XY[(size_t)i * N + j] /= dii;
+        __syncthreads();
+        for (long idx = tid; idx < (long)i * N; idx += T) {
+            int r = (int)(idx / N), j = (int)(idx % N);
+            XY[(size_t)r * N + j] -= Mw[(size_t)r * nn + i] * XY[(size_t)i * N + j];
+        }
+        __syncthreads();
+    }
+    // C = [I - tau Y; tau X]
+    for (long idx = tid; idx < (long)N * N; idx += T) {
+        int i = (int)(idx / N), j = (int)(idx % N);
+        C[idx] = ((i == j) ? 1.0 : 0.0) - tau * XY[(size_t)(N + i) * N + j];
+        C[(size_t)(N + i) * N + j] = tau * XY[idx];
+    }
+}
+
+void launch_predictor_solve(int N, double tau, const double *G2, double *Mwork, double *XY,
+                            double *C, int *status, cudaStream_t s) {
+    size_t shm = sizeof(double) * (2 * N + 1024) + sizeof(int) * 1024;
+    HQ_LAUNCH(HQ_K_SMALL, k_predictor_solve<<<1, 1024, shm, s>>>(N, tau, G2, Mwork, XY, C, status));
+}
+
+__global__ void k_add_diag(int N, double *A, double v) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        A[(size_t)i * N + i] += v;
+}
+void launch_add_diag(int N, double *A, double v, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_SMALL, k_add_diag<<<(N + 255) / 256, 256, 0, s>>>(N, A, v));
+}
+
+__global__ void k_dscale(int count, double alpha, const double *in, double *out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+        out[i] = alpha * in[i];
+}
+void launch_dscale(int count, double alpha, const double *in, double *out, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_SMALL, k_dscale<<<std::min((count + 255) / 256, 1024), 256, 0, s>>>(count, alpha, in, out));
+}
+
+__global__ void k_axpy_small(int count, double a, const double *x, double *y) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+        y[i] += a * x[i];
+}
+void launch_axpy_small(int count, double a, const double *x, double *y, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_SMALL, k_axpy_small<<<std::min((count + 255) / 256, 1024), 256, 0, s>>>(count, a, x, y));
+}
+
+// Cyclic Jacobi with a parallel (round-robin) ordering, one CTA.  work: 2 N^2
+// (+ padding to even order).  Rotation: theta = (a_qq - a_pp) / (2 a_pq),
+// t = sign(theta) / (|theta| + sqrt(theta^2 + 1)), c = 1/sqrt(t^2 + 1), s = t c,
+// A <- J^T A J, V <- V J with J = [c s; -s c] on (p, q).
+__global__ void __launch_bounds__(1024) k_sym_eig(int N, const double *Ain, double *work,
+                                                  double *evals, double *evecs) {
+    extern __shared__ double sh[];
+    const int P = (N + 1) & ~1;          // even order (index N is a dummy when N is odd)
+    double *A = work;                    // P x P
+    double *Vv = work + (size_t)P * P;   // P x P
+    double *cs = sh;                     // P/2 c
+    double *sn = sh + P / 2;             // P/2 s
+    int *pp = (int *)(sh + P);           // P/2
+    int *qq = pp + P / 2;                // P/2
+    double *red = (double *)(pp + P);    // 1024 (pp + P is 8-byte aligned: P even)
+    const int tid = threadIdx.x, T = blockDim.x;
+    for (long idx = tid; idx < (long)P * P; idx += T) {
+        int i = (int)(idx / P), j = (int)(idx % P);
+        double v = 0.0;
+        if (i < N && j < N) v = 0.5 * (Ain[(size_t)i * N + j] + Ain[(size_t)j * N + i]);
+        A[idx] = v;
+        Vv[idx] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    double fro;
+    {
+        double s = 0.0;
+        for (long idx = tid; idx < (long)P * P; idx += T) s += A[idx] * A[idx];
+        red[tid] = s;
+        __syncthreads();
+        for (int w = T / 2; w > 0; w >>= 1) {
+            if (tid < w) red[tid] += red[tid + w];
+            __syncthreads();
+        }
+        fro = sqrt(red[0]);
+        __syncthreads();
+    }
+    for (int sweep = 0; sweep < 100; sweep++) {
+        double s = 0.0;
+        for (long idx = tid; idx < (long)P * P; idx += T) {
+            int i = (int)(idx / P), j = (int)(idx % P);
+            if (i < j) s += A[idx] * A[idx];
+        }
+        red[tid] = s;
+        __syncthreads();
+        for (int w = T / 2; w > 0; w >>= 1) {
+            if (tid < w) red[tid] += red[tid + w];
+            __syncthreads();
+        }
+        double off = red[0];
+        __syncthreads();
+        if (sqrt(off) <= 1e-15 * fro || off == 0.0) break;
+        for (int r = 0; r < P - 1; r++) {
+            for (int k = tid; k < P / 2; k += T) {
+                int a, b;
+                if (k == 0) { a = P - 1; b = r; }
+                else { a = (r + k) % (P - 1); b = (r - k + (P - 1)) % (P - 1); }
+                int p = a < b ? a : b, q = a < b ? b : a;
+                pp[k] = p;
+                qq[k] = q;
+                double c = 1.0, sv = 0.0;
+                if (q < N) {
+                    double apq = A[(size_t)p * P + q];
+                    if (apq != 0.0) {
+                        double app = A[(size_t)p * P + p], aqq = A[(size_t)q * P + q];
+                        double theta = (aqq - app) / (2.0 * apq);
+                        double t = (theta >= 0.0 ? 1.0 : -1.0) /
+                                   (fabs(theta) + sqrt(theta * theta + 1.0));
+                        c = 1.0 / sqrt(t * t + 1.0);
+                        sv = t * c;
+                    }
+                }
+                cs[k] = c;
+                sn[k] = sv;
+            }
+            __syncthreads();
+            // rows: A <- J^T A
+            for (long idx = tid; idx < (long)(P / 2) * P; idx += T) {
+                int k = (int)(idx / P), j = (int)(idx % P);
+                double c = cs[k], sv = sn[k];
+                if (sv == 0.0) continue;
+                int p = pp[k], q = qq[k];
+                double apj = A[(size_t)p * P + j], aqj = A[(size_t)q * P + j];
+                A[(size_t)p * P + j] = c * apj - sv * aqj;
+                A[(size_t)q * P + j] = sv * apj + c * aqj;
+            }
+            __syncthreads();
+            // columns: A <- A J, V <- V J
+            for (long idx = tid; idx < (long)(P / 2) * P; idx += T) {
+                int k = (int)(idx / P), i = (int)(idx % P);
+                double c = cs[k], sv = sn[k];
+                if (sv == 0.0) continue;
+                int p = pp[k], q = qq[k];
+                double aip = A[(size_t)i * P + p], aiq = A[(size_t)i * P + q];
+                A[(size_t)i * P + p] = c * aip - sv * aiq;
+                A[(size_t)i * P + q] = sv * aip + c * aiq;
+                double vip = Vv[(size_t)i * P + p], viq = Vv[(size_t)i * P + q];
+                Vv[(size_t)i * P + p] = c * vip - sv * viq;
+                Vv[(size_t)i * P + q] = sv * vip + c * viq;
+            }
+            __syncthreads();
+            for (int k = tid; k < P / 2; k += T) {
+                if (sn[k] != 0.0) {
+                    A[(size_t)pp[k] * P + qq[k]] = 0.0;
+                    A[(size_t)qq[k] * P + pp[k]] = 0.0;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // sort ascending (rank sort, ties by index)
+    for (int i = tid; i < N; i += T) {
+        double di = A[(size_t)i * P + i];
+        int rank = 0;
+        for (int j = 0; j < N; j++) {
+            double dj = A[(size_t)j * P + j];
+            if (dj < di || (dj == di && j < i)) rank++;
+        }
+        evals[rank] = di;
+        if (evecs)
+            for (int k = 0; k < N; k++) evecs[(size_t)k * N + rank] = Vv[(size_t)k * P + i];
+    }
+}
+
+void launch_sym_eig(int N, const double *A, double *work, double *evals, double *evecs,
+                    cudaStream_t s) {
+    int P = (N + 1) & ~1;
+    size_t shm = sizeof(double) * (P + 1024) + sizeof(int) * (P + 2) + 16;
+    HQ_LAUNCH(HQ_K_SMALL, k_sym_eig<<<1, 1024, shm, s>>>(N, A, work, evals, evecs));
+}
+
+// Rayleigh-Ritz reduction: S = L L^T, Cm = L^{-1} sym(K) L^{-T}.  One CTA.
+__global__ void __launch_bounds__(1024) k_rr_reduce(int N, const double *K, const double *S,
+                                                    double *L, double *Cm, int *status) {
+    const int tid = threadIdx.x, T = blockDim.x;
+    for (long idx = tid; idx < (long)N * N; idx += T) L[idx] = S[idx];
+    __syncthreads();
+    for (int k = 0; k < N; k++) {
+        double d = L[(size_t)k * N + k];
+        if (!(d > 0.0)) {
+            if (tid == 0) atomicOr(status, ST_SINGULAR);
+            return;
+        }
+        d = sqrt(d);
+        __syncthreads();
+        for (int i = k + tid; i < N; i += T) L[(size_t)i * N + k] = (i == k) ? d : L[(size_t)i * N + k] / d;
+        __syncthreads();
+        const int r = N - k - 1;
+        for (long idx = tid; idx < (long)r * r; idx += T) {
+            int i = k + 1 + (int)(idx / r), j = k + 1 + (int)(idx % r);
+            if (j > i) continue;
+            L[(size_t)i * N + j] -= L[(size_t)i * N + k] * L[(size_t)j * N + k];
+        }
+        __syncthreads();
+    }
+    for (long idx = tid; idx < (long)N * N; idx += T) {
+        int i = (int)(idx / N), j = (int)(idx % N);
+        if (j > i) L[idx] = 0.0;
+    }
+    __syncthreads();
+    // T1 = L^{-1} sym(K) into Cm (column j by thread), then Cm = L^{-1} T1^T
+    for (int j = tid; j < N; j += T) {
+        for (int i = 0; i < N; i++) {
+            double s = 0.5 * (K[(size_t)i * N + j] + K[(size_t)j * N + i]);
+            for (int k = 0; k < i; k++) s -= L[(size_t)i * N + k] * Cm[(size_t)k * N + j];
+            Cm[(size_t)i * N + j] = s / L[(size_t)i * N + i];
+        }
+    }
+    __syncthreads();
+    // transpose in place
+    for (long idx = tid; idx < (long)N * N; idx += T) {
+        int i = (int)(idx / N), j = (int)(idx % N);
+        if (i < j) {
+            double a = Cm[idx], b = Cm[(size_t)j * N + i];
+            Cm[idx] = b;
+            Cm[(size_t)j * N + i] = a;
+        }
+    }
+    __syncthreads();
+    for (int j = tid; j < N; j += T) {
+        for (int i = 0; i < N; i++) {
+            double s = Cm[(size_t)i * N + j];
+            for (int k = 0; k < i; k++) s -= L[(size_t)i * N + k] * Cm[(size_t)k * N + j];
+            Cm[(size_t)i * N + j] = s / L[(size_t)i * N + i];
+        }
+    }
+}
+void launch_rr_reduce(int N, const double *K, const double *S, double *L, double *Cm,
+                      int *status, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_SMALL, k_rr_reduce<<<1, 1024, 0, s>>>(N, K, S, L, Cm, status));
+}
+
+__global__ void k_rr_back(int N, const double *L, const double *Y, double *Cv) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N; e += gridDim.x * blockDim.x) {
+        for (int i = N - 1; i >= 0; i--) {
+            double s = Y[(size_t)i * N + e];
+            for (int k = i + 1; k < N; k++) s -= L[(size_t)k * N + i] * Cv[(size_t)k * N + e];
+            Cv[(size_t)i * N + e] = s / L[(size_t)i * N + i];
+        }
+    }
+}
+void launch_rr_back(int N, const double *L, const double *Y, double *Cv, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_SMALL, k_rr_back<<<(N + 127) / 128, 128, 0, s>>>(N, L, Y, Cv));
+}
+
+__global__ void k_inv_sqrt_first(const double *ev, double *out) { out[0] = 1.0 / sqrt(ev[0]); }
+void launch_inv_sqrt_first(const double *evals, double *out, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_SMALL, k_inv_sqrt_first<<<1, 1, 0, s>>>(evals, out));
+}
+
+__global__ void k_paper_evals(int N, const double *mu, double sigma, double *lam) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) lam[i] = 1.0 / mu[N - 1 - i] - sigma;
+}
+void launch_paper_evals(int N, const double *mu, double sigma, double *lam, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_SMALL, k_paper_evals<<<1, 256, 0, s>>>(N, mu, sigma, lam));
+}
+
+__global__ void k_add_scalar(int N, const double *in, double add, double *out) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) out[i] = in[i] + add;
+}
+void launch_add_scalar(int N, const double *in, double add, double *out, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_SMALL, k_add_scalar<<<1, 256, 0, s>>>(N, in, add, out));
+}
+
+// Ritz-vector sign: per column, entry of largest magnitude (first on ties)
+// made positive.  Pass 1: per-CTA (max, index) over a slab of points.
+template <typename T>
+__global__ void k_sign_pass1(long n, int N, const T *U, long rows, double *work) {
+    __shared__ double bv[256];
+    __shared__ long bi[256];
+    const int c = blockIdx.x;
+    const long r0 = (long)blockIdx.y * rows, r1 = min(n, r0 + rows);
+    double best = -1.0;
+    long idx = -1;
+    for (long p = r0 + threadIdx.x; p < r1; p += blockDim.x) {
+        double v = fabs((double)U[(size_t)p * N + c]);
+        if (v > best) { best = v; idx = p; }
+    }
+    bv[threadIdx.x] = best;
+    bi[threadIdx.x] = idx;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            double v2 = bv[threadIdx.x + w];
+            long i2 = bi[threadIdx.x + w];
+            if (v2 > bv[threadIdx.x] || (v2 == bv[threadIdx.x] && i2 >= 0 && (bi[threadIdx.x] < 0 || i2 < bi[threadIdx.x]))) {
+                bv[threadIdx.x] = v2;
+                bi[threadIdx.x] = i2;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        work[((size_t)blockIdx.y * N + c) * 2] = bv[0];
+        work[((size_t)blockIdx.y * N + c) * 2 + 1] = (double)bi[0];
+    }
+}
+template <typename T>
+__global__ void k_sign_pass2(long n, int N, T *U, int gy, const double *work) {
+    const int c = blockIdx.x;
+    __shared__ double sgn;
+    if (threadIdx.x == 0) {
+        double best = -1.0;
+        long idx = -1;
+        for (int y = 0; y < gy; y++) {
+            double v = work[((size_t)y * N + c) * 2];
+            long i = (long)work[((size_t)y * N + c) * 2 + 1];
+            if (v > best) { best = v; idx = i; }
+        }
+        sgn = (idx >= 0 && U[(size_t)idx * N + c] < T(0)) ? -1.0 : 1.0;
+    }
+    __syncthreads();
+    if (sgn > 0) return;
+    for (long p = threadIdx.x; p < n; p += blockDim.x) U[(size_t)p * N + c] = -U[(size_t)p * N + c];
+}
+template <typename T>
+void launch_fix_signs(long n, int N, T *U, double *work, cudaStream_t s) {
+    int gy = (int)std::min<long>(64, (n + 1023) / 1024);
+    long rows = (n + gy - 1) / gy;
+    HQ_LAUNCH(HQ_K_SMALL, k_sign_pass1<T><<<dim3(N, gy), 256, 0, s>>>(n, N, U, rows, work));
+    HQ_LAUNCH(HQ_K_SMALL, k_sign_pass2<T><<<N, 256, 0, s>>>(n, N, U, gy, work));
+}
+
+__global__ void k_extract(int rows, int cols, double alpha, const double *src, int lds,
+                          double *dst, int ldd) {
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < rows * cols;
+         idx += gridDim.x * blockDim.x) {
+        int i = idx / cols, j = idx % cols;
+        dst[(size_t)i * ldd + j] = alpha * src[(size_t)i * lds + j];
+    }
+}
+void launch_extract(int rows, int cols, double alpha, const double *src, int lds, double *dst,
+                    int ldd, cudaStream_t s) {
+    int tot = rows * cols;
+    HQ_LAUNCH(HQ_K_SMALL, k_extract<<<std::min((tot + 255) / 256, 1024), 256, 0, s>>>(rows, cols, alpha, src, lds, dst,
+                                                                ldd));
+}
+
+__global__ void k_scale_cols(int N, const double *Cv, const double *lam, double add,
+                             double *out) {
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N * N;
+         idx += gridDim.x * blockDim.x) {
+        int j = idx % N;
+        out[idx] = -Cv[idx] * (lam[j] + add);
+    }
+}
+void launch_scale_cols(int N, const double *Cv, const double *lam, double add, double *out,
+                       cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_SMALL, k_scale_cols<<<std::min((N * N + 255) / 256, 1024), 256, 0, s>>>(N, Cv, lam, add, out));
+}
+
+#define HQ_DINST(T)                                                                          \
+    template void launch_gram<T>(const GramPlan &, const T *, int, const T *, int, const T *, \
+                                 int, const T *, int, double, double *, double *,            \
+                                 cudaStream_t);                                              \
+    template void launch_tall_gemm<T>(const TallPlan &, const T *, const double *, const T *, \
+                                      const double *, const T *, T *, double *,              \
+                                      cudaStream_t);                                         \
+    template void launch_tall_gemm_colsq<T>(const TallPlan &, const T *, const double *,      \
+                                            const T *, const double *, const T *, T *,        \
+                                            double *, cudaStream_t);                         \
+    template void launch_fix_signs<T>(long, int, T *, double *, cudaStream_t);
+
+HQ_DINST(double)
+HQ_DINST(float)
+
+}  // namespace hq

@@ -1,0 +1,852 @@
+// Grid kernels of the inner solve: 7-point operator, block-PCG vector
+// updates, damped-Jacobi smoothing, trilinear transfer operators, coarsest
+// solve and the per-column reductions that drive the PCG recurrences.
+//
+// All blocks are point-major (n x N, columns fastest), so each stencil tap is
+// a contiguous N-vector: a thread owns VEC consecutive columns of one point
+// and every load/store is a 16-byte (or 8-byte) vector access, coalesced
+// across the threads of a warp.  Reductions are per CTA in a fixed order,
+// then over CTAs in a fixed order (deterministic, bit-reproducible).
+#include "hq_internal.cuh"
+
+#include <algorithm>
+
+namespace hq {
+
+template <typename T, int V>
+struct alignas(sizeof(T) * V) VT {
+    T v[V];
+};
+
+template <typename T, int V>
+__device__ __forceinline__ VT<T, V> ldv(const T *p) {
+    return *reinterpret_cast<const VT<T, V> *>(p);
+}
+template <typename T, int V>
+__device__ __forceinline__ void stv(T *p, const VT<T, V> &x) {
+    *reinterpret_cast<VT<T, V> *>(p) = x;
+}
+
+GridGeom make_geom(int m, int N, int elem_bytes) {
+    GridGeom g;
+    g.m = m;
+    g.n = (long)m * m * m;
+    g.N = N;
+    if (elem_bytes == 8)
+        g.vec = (N % 2 == 0) ? 2 : 1;
+    else
+        g.vec = (N % 4 == 0) ? 4 : ((N % 2 == 0) ? 2 : 1);
+    int tpr = N / g.vec;
+    g.tx = tpr <= 32 ? tpr : 32;
+    g.ty = std::max(1, 256 / g.tx);
+    g.gx = (tpr + g.tx - 1) / g.tx;
+    long target_gy = std::max(1L, 152L * 16 / g.gx);
+    long ppt = (g.n + (long)g.ty * target_gy - 1) / ((long)g.ty * target_gy);
+    g.ppt = (int)std::max(1L, ppt);
+    g.gy = (int)((g.n + (long)g.ty * g.ppt - 1) / ((long)g.ty * g.ppt));
+    return g;
+}
+
+// Per-column partial sums: each thread holds acc[V] for its columns; reduce
+// over threadIdx.y in order and store one row of the partial array.
+template <int V, typename A>
+__device__ __forceinline__ void block_col_reduce(A (&acc)[V], double *red, double *part,
+                                                 int N, int col, bool cv) {
+    const int tx = threadIdx.x, ty = threadIdx.y, TX = blockDim.x, TY = blockDim.y;
+#pragma unroll
+    for (int v = 0; v < V; v++) red[(ty * TX + tx) * V + v] = (double)acc[v];
+    __syncthreads();
+    if (ty == 0 && cv && part) {
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            double s = 0.0;
+            for (int y = 0; y < TY; y++) s += red[(y * TX + tx) * V + v];
+            part[(size_t)blockIdx.y * N + col + v] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// 7-point operator.  MODE 0: y = A x (+ x.y);  MODE 1: y = b - A x (+ y.y, b.b)
+// A x = D x - c (x_w + x_e + x_s + x_n + x_b + x_t),  D = 6c + V + sigma.
+// ---------------------------------------------------------------------------
+template <typename T, int V, int MODE>
+__global__ void __launch_bounds__(256) k_stencil(int m, long n, int N, int ppt,
+                                                 const T *__restrict__ D, T c,
+                                                 const T *__restrict__ x,
+                                                 const T *__restrict__ b, T *__restrict__ y,
+                                                 double *part1, double *part2) {
+    __shared__ double red[1024];
+    const int TY = blockDim.y;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int col = t * V;
+    const bool cv = col < N;
+    T a1[V], a2[V];   // per-thread partials in the working precision
+#pragma unroll
+    for (int v = 0; v < V; v++) a1[v] = a2[v] = T(0);
+    const size_t sx = (size_t)N, sy = (size_t)m * N, sz = (size_t)m * m * N;
+    const long base = (long)blockIdx.y * TY * ppt;
+    for (int k = 0; k < ppt; k++) {
+        long p = base + (long)k * TY + threadIdx.y;
+        if (!cv || p >= n) continue;
+        int i = (int)(p % m);
+        long q = p / m;
+        int j = (int)(q % m);
+        int kk = (int)(q / m);
+        size_t e = (size_t)p * N + col;
+        VT<T, V> xc = ldv<T, V>(x + e), s;
+#pragma unroll
+        for (int v = 0; v < V; v++) s.v[v] = T(0);
+        if (i > 0) { VT<T, V> a = ldv<T, V>(x + e - sx); for (int v = 0; v < V; v++) s.v[v] += a.v[v]; }
+        if (i < m - 1) { VT<T, V> a = ldv<T, V>(x + e + sx); for (int v = 0; v < V; v++) s.v[v] += a.v[v]; }
+        if (j > 0) { VT<T, V> a = ldv<T, V>(x + e - sy); for (int v = 0; v < V; v++) s.v[v] += a.v[v]; }
+        if (j < m - 1) { VT<T, V> a = ldv<T, V>(x + e + sy); for (int v = 0; v < V; v++) s.v[v] += a.v[v]; }
+        if (kk > 0) { VT<T, V> a = ldv<T, V>(x + e - sz); for (int v = 0; v < V; v++) s.v[v] += a.v[v]; }
+        if (kk < m - 1) { VT<T, V> a = ldv<T, V>(x + e + sz); for (int v = 0; v < V; v++) s.v[v] += a.v[v]; }
+        T d = D[p];
+        VT<T, V> o;
+#pragma unroll
+        for (int v = 0; v < V; v++) o.v[v] = d * xc.v[v] - c * s.v[v];
+        if (MODE == 1) {
+            VT<T, V> bb = ldv<T, V>(b + e);
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                o.v[v] = bb.v[v] - o.v[v];
+                a1[v] += o.v[v] * o.v[v];
+                a2[v] += bb.v[v] * bb.v[v];
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; v++) a1[v] += xc.v[v] * o.v[v];
+        }
+        stv<T, V>(y + e, o);
+    }
+    if (part1) block_col_reduce<V, T>(a1, red, part1, N, col, cv);
+    if (MODE == 1 && part2) block_col_reduce<V, T>(a2, red, part2, N, col, cv);
+}
+
+// x += alpha p; r -= alpha q; partial r.r; optional zf = wD r
+template <typename T, int V>
+__global__ void __launch_bounds__(256) k_pcg_xr(int m, long n, int N, int ppt,
+                                                const double *__restrict__ alpha,
+                                                const T *__restrict__ p_, const T *__restrict__ q_,
+                                                T *__restrict__ x, T *__restrict__ r,
+                                                double *part, const T *__restrict__ wD,
+                                                T *__restrict__ zf) {
+    __shared__ double red[1024];
+    const int TY = blockDim.y;
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    const bool cv = col < N;
+    T acc[V];
+    T a[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+        acc[v] = T(0);
+        a[v] = cv ? (T)alpha[col + v] : T(0);
+    }
+    const long base = (long)blockIdx.y * TY * ppt;
+    for (int k = 0; k < ppt; k++) {
+        long p = base + (long)k * TY + threadIdx.y;
+        if (!cv || p >= n) continue;
+        size_t e = (size_t)p * N + col;
+        VT<T, V> pv = ldv<T, V>(p_ + e), qv = ldv<T, V>(q_ + e), xv = ldv<T, V>(x + e),
+                 rv = ldv<T, V>(r + e);
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            xv.v[v] += a[v] * pv.v[v];
+            rv.v[v] -= a[v] * qv.v[v];
+            acc[v] += rv.v[v] * rv.v[v];
+        }
+        stv<T, V>(x + e, xv);
+        stv<T, V>(r + e, rv);
+        if (zf) {
+            T w = wD[p];
+            VT<T, V> zv;
+#pragma unroll
+            for (int v = 0; v < V; v++) zv.v[v] = w * rv.v[v];
+            stv<T, V>(zf + e, zv);
+        }
+    }
+    block_col_reduce<V, T>(acc, red, part, N, col, cv);
+}
+
+template <typename T, int V>
+__global__ void __launch_bounds__(256) k_pcg_p(long n, int N, int ppt,
+                                               const double *__restrict__ beta,
+                                               const T *__restrict__ z, T *__restrict__ p_) {
+    const int TY = blockDim.y;
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    if (col >= N) return;
+    T bt[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) bt[v] = (T)beta[col + v];
+    const long base = (long)blockIdx.y * TY * ppt;
+    for (int k = 0; k < ppt; k++) {
+        long p = base + (long)k * TY + threadIdx.y;
+        if (p >= n) continue;
+        size_t e = (size_t)p * N + col;
+        VT<T, V> zv = ldv<T, V>(z + e), pv = ldv<T, V>(p_ + e);
+#pragma unroll
+        for (int v = 0; v < V; v++) pv.v[v] = zv.v[v] + bt[v] * pv.v[v];
+        stv<T, V>(p_ + e, pv);
+    }
+}
+
+// z_out = z_in + wD (r - A z_in) = (1 - omega) z_in + wD (r + c * nbrsum(z_in))
+// (wD = omega / D, so wD * D = omega); optional partial r.z_out.
+template <typename T, int V>
+__global__ void __launch_bounds__(256) k_jacobi(int m, long n, int N, int ppt,
+                                                const T *__restrict__ wD, T c, T omw,
+                                                const T *__restrict__ r,
+                                                const T *__restrict__ zin,
+                                                T *__restrict__ zout, double *part) {
+    __shared__ double red[1024];
+    const int TY = blockDim.y;
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    const bool cv = col < N;
+    T acc[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) acc[v] = T(0);
+    const size_t sx = (size_t)N, sy = (size_t)m * N, sz = (size_t)m * m * N;
+    const long base = (long)blockIdx.y * TY * ppt;
+    for (int k = 0; k < ppt; k++) {
+        long p = base + (long)k * TY + threadIdx.y;
+        if (!cv || p >= n) continue;
+        int i = (int)(p % m);
+        long q = p / m;
+        int j = (int)(q % m);
+        int kk = (int)(q / m);
+        size_t e = (size_t)p * N + col;
+        VT<T, V> zc = ldv<T, V>(zin + e), s, rv = ldv<T, V>(r + e);
+#pragma unroll
+        for (int v = 0; v < V; v++) s.v[v] = T(0);
+        if (i > 0) { VT<T, V> a = ldv<T, V>(zin + e - sx); for (int v = 0; v < V; v++) s.v[v] += a.v[v]; }
+        if (i < m - 1) { VT<T, V> a = ldv<T, V>(zin + e + sx); for (int v = 0; v < V; v++) s.v[v] += a.v[v]; }
+        if (j > 0) { VT<T, V> a = ldv<T, V>(zin + e - sy); for (int v = 0; v < V; v++) s.v[v] += a.v[v]; }
+        if (j < m - 1) { VT<T, V> a = ldv<T, V>(zin + e + sy); for (int v = 0; v < V; v++) s.v[v] += a.v[v]; }
+        if (kk > 0) { VT<T, V> a = ldv<T, V>(zin + e - sz); for (int v = 0; v < V; v++) s.v[v] += a.v[v]; }
+        if (kk < m - 1) { VT<T, V> a = ldv<T, V>(zin + e + sz); for (int v = 0; v < V; v++) s.v[v] += a.v[v]; }
+        T w = wD[p];
+        VT<T, V> o;
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            o.v[v] = omw * zc.v[v] + w * (rv.v[v] + c * s.v[v]);
+            acc[v] += rv.v[v] * o.v[v];
+        }
+        stv<T, V>(zout + e, o);
+    }
+    if (part) block_col_reduce<V, T>(acc, red, part, N, col, cv);
+}
+
+template <typename T, int V>
+__global__ void __launch_bounds__(256) k_jacobi_first(long n, int N, int ppt,
+                                                      const T *__restrict__ wD,
+                                                      const T *__restrict__ r,
+                                                      T *__restrict__ z) {
+    const int TY = blockDim.y;
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    if (col >= N) return;
+    const long base = (long)blockIdx.y * TY * ppt;
+    for (int k = 0; k < ppt; k++) {
+        long p = base + (long)k * TY + threadIdx.y;
+        if (p >= n) continue;
+        size_t e = (size_t)p * N + col;
+        T w = wD[p];
+        VT<T, V> rv = ldv<T, V>(r + e), o;
+#pragma unroll
+        for (int v = 0; v < V; v++) o.v[v] = w * rv.v[v];
+        stv<T, V>(z + e, o);
+    }
+}
+
+template <typename T, int V>
+__global__ void __launch_bounds__(256) k_dot(long n, int N, int ppt, const T *__restrict__ x,
+                                             const T *__restrict__ y, double *part) {
+    __shared__ double red[1024];
+    const int TY = blockDim.y;
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    const bool cv = col < N;
+    T acc[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) acc[v] = T(0);
+    const long base = (long)blockIdx.y * TY * ppt;
+    for (int k = 0; k < ppt; k++) {
+        long p = base + (long)k * TY + threadIdx.y;
+        if (!cv || p >= n) continue;
+        size_t e = (size_t)p * N + col;
+        VT<T, V> xv = ldv<T, V>(x + e), yv = ldv<T, V>(y + e);
+#pragma unroll
+        for (int v = 0; v < V; v++) acc[v] += xv.v[v] * yv.v[v];
+    }
+    block_col_reduce<V, T>(acc, red, part, N, col, cv);
+}
+
+// ---------------------------------------------------------------------------
+// Transfer operators between a grid of mf and one of mc nodes per side on the
+// same box.  Fine node f (1-based) has coarse coordinate f (mc+1)/(mf+1);
+// every weight is a ratio of two integers, so both sides of any comparison
+// obtain the same doubles.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double hat_weight(int f, int c1, int mf, int mc) {
+    long den = mf + 1;
+    long num = (long)f * (mc + 1) - (long)c1 * den;
+    long a = num < 0 ? -num : num;
+    return a < den ? (double)(den - a) / (double)den : 0.0;
+}
+
+// 1-D list of fine nodes (1-based) feeding coarse node c1, with weights
+__device__ __forceinline__ int restrict_list(int c1, int mf, int mc, int *fi, double *fw) {
+    long den = mf + 1, mcp = mc + 1;
+    long lo = ((long)(c1 - 1) * den) / mcp;
+    long hi = ((long)(c1 + 1) * den + mcp - 1) / mcp;
+    if (lo < 1) lo = 1;
+    if (hi > mf) hi = mf;
+    int cnt = 0;
+    for (long f = lo; f <= hi && cnt < 8; f++) {
+        double w = hat_weight((int)f, c1, mf, mc);
+        if (w > 0.0) {
+            fi[cnt] = (int)f;
+            fw[cnt] = w;
+            cnt++;
+        }
+    }
+    return cnt;
+}
+
+template <typename T, int V>
+__global__ void __launch_bounds__(256) k_restrict(int mc, long nc, int N, int ppt, int mf,
+                                                  double scale, const T *__restrict__ rf,
+                                                  T *__restrict__ rc) {
+    const int TY = blockDim.y;
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    if (col >= N) return;
+    const long base = (long)blockIdx.y * TY * ppt;
+    for (int k = 0; k < ppt; k++) {
+        long p = base + (long)k * TY + threadIdx.y;
+        if (p >= nc) continue;
+        int ci = (int)(p % mc);
+        long q = p / mc;
+        int cj = (int)(q % mc);
+        int ck = (int)(q / mc);
+        int fx[8], fy[8], fz[8];
+        double wx[8], wy[8], wz[8];
+        int nx = restrict_list(ci + 1, mf, mc, fx, wx);
+        int ny = restrict_list(cj + 1, mf, mc, fy, wy);
+        int nz = restrict_list(ck + 1, mf, mc, fz, wz);
+        T acc[V];
+#pragma unroll
+        for (int v = 0; v < V; v++) acc[v] = T(0);
+        for (int c = 0; c < nz; c++)
+            for (int b = 0; b < ny; b++) {
+                double wzy = wz[c] * wy[b];
+                size_t rowbase = ((size_t)(fz[c] - 1) * mf + (fy[b] - 1)) * mf;
+                for (int a = 0; a < nx; a++) {
+                    T w = (T)(wzy * wx[a]);
+                    VT<T, V> rv = ldv<T, V>(rf + (rowbase + fx[a] - 1) * N + col);
+#pragma unroll
+                    for (int v = 0; v < V; v++) acc[v] += w * rv.v[v];
+                }
+            }
+        VT<T, V> o;
+#pragma unroll
+        for (int v = 0; v < V; v++) o.v[v] = (T)scale * acc[v];
+        stv<T, V>(rc + (size_t)p * N + col, o);
+    }
+}
+
+template <typename T, int V>
+__global__ void __launch_bounds__(256) k_prolong(int mf, long nf, int N, int ppt, int mc,
+                                                 const T *__restrict__ ec,
+                                                 const T *__restrict__ efin,
+                                                 T *__restrict__ efout) {
+    const int TY = blockDim.y;
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    if (col >= N) return;
+    const long den = mf + 1, mcp = mc + 1;
+    const long base = (long)blockIdx.y * TY * ppt;
+    for (int k = 0; k < ppt; k++) {
+        long p = base + (long)k * TY + threadIdx.y;
+        if (p >= nf) continue;
+        int f[3];
+        f[0] = (int)(p % mf) + 1;
+        long q = p / mf;
+        f[1] = (int)(q % mf) + 1;
+        f[2] = (int)(q / mf) + 1;
+        int s0[3];
+        double w[3][2];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            long num = (long)f[d] * mcp;
+            s0[d] = (int)(num / den);
+            long rem = num % den;
+            w[d][1] = (double)rem / (double)den;
+            w[d][0] = (double)(den - rem) / (double)den;
+        }
+        size_t e = (size_t)p * N + col;
+        VT<T, V> o = ldv<T, V>(efin + e);
+        T acc[V];
+#pragma unroll
+        for (int v = 0; v < V; v++) acc[v] = T(0);
+#pragma unroll
+        for (int cz = 0; cz < 2; cz++) {
+            int kz = s0[2] + cz;
+            if (kz < 1 || kz > mc || w[2][cz] == 0.0) continue;
+#pragma unroll
+            for (int cy = 0; cy < 2; cy++) {
+                int ky = s0[1] + cy;
+                if (ky < 1 || ky > mc || w[1][cy] == 0.0) continue;
+#pragma unroll
+                for (int cx = 0; cx < 2; cx++) {
+                    int kx = s0[0] + cx;
+                    if (kx < 1 || kx > mc || w[0][cx] == 0.0) continue;
+                    T wt = (T)(w[0][cx] * w[1][cy] * w[2][cz]);
+                    size_t ce = (((size_t)(kz - 1) * mc + (ky - 1)) * mc + (kx - 1)) * N + col;
+                    VT<T, V> ev = ldv<T, V>(ec + ce);
+#pragma unroll
+                    for (int v = 0; v < V; v++) acc[v] += wt * ev.v[v];
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < V; v++) o.v[v] = o.v[v] + acc[v];
+        stv<T, V>(efout + e, o);
+    }
+}
+
+template <typename T, int V>
+__global__ void __launch_bounds__(256) k_coarse_solve(long nc, int N, int ppt,
+                                                      const double *__restrict__ Ainv,
+                                                      const T *__restrict__ r,
+                                                      T *__restrict__ z) {
+    const int TY = blockDim.y;
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    if (col >= N) return;
+    const long base = (long)blockIdx.y * TY * ppt;
+    for (int k = 0; k < ppt; k++) {
+        long p = base + (long)k * TY + threadIdx.y;
+        if (p >= nc) continue;
+        double acc[V];
+#pragma unroll
+        for (int v = 0; v < V; v++) acc[v] = 0.0;
+        for (long qq = 0; qq < nc; qq++) {
+            double a = Ainv[p * nc + qq];
+            VT<T, V> rv = ldv<T, V>(r + (size_t)qq * N + col);
+#pragma unroll
+            for (int v = 0; v < V; v++) acc[v] += a * (double)rv.v[v];
+        }
+        VT<T, V> o;
+#pragma unroll
+        for (int v = 0; v < V; v++) o.v[v] = (T)acc[v];
+        stv<T, V>(z + (size_t)p * N + col, o);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-column finalisation of the PCG recurrences (one block per column)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_finalize(int mode, int N, int gy, const double *part,
+                                                  const double *part2, PcgScalars sc,
+                                                  double rtol) {
+    __shared__ double red[2][128];
+    const int col = blockIdx.x;
+    double s = 0.0, s2 = 0.0;
+    for (int i = threadIdx.x; i < gy; i += blockDim.x) {
+        s += part[(size_t)i * N + col];
+        if (part2) s2 += part2[(size_t)i * N + col];
+    }
+    red[0][threadIdx.x] = s;
+    red[1][threadIdx.x] = s2;
+    __syncthreads();
+    for (int w = 64; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + w];
+            red[1][threadIdx.x] += red[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    s = red[0][0];
+    s2 = red[1][0];
+    switch (mode) {
+    case FIN_BNORM_RNORM: {
+        double rn = sqrt(s), bn = sqrt(s2);
+        sc.rnorm[col] = rn;
+        sc.bnorm[col] = bn;
+        sc.iters[col] = 0;
+        if (!isfinite(rn) || !isfinite(bn)) atomicOr(sc.status, ST_NONFINITE);
+        int act = (rn > rtol * bn) ? 1 : 0;
+        sc.active[col] = act;
+        if (act) atomicAdd(sc.num_active, 1);
+        break;
+    }
+    case FIN_RZ:
+        sc.rz[col] = s;
+        break;
+    case FIN_ALPHA: {
+        double a = 0.0;
+        if (sc.active[col]) {
+            if (!(s > 0.0) || !isfinite(s)) {
+                atomicOr(sc.status, ST_BREAKDOWN);
+                sc.active[col] = 0;
+            } else {
+                a = sc.rz[col] / s;
+            }
+        }
+        sc.alpha[col] = a;
+        break;
+    }
+    case FIN_RR: {
+        double rn = sqrt(s);
+        sc.rnorm[col] = rn;
+        if (!isfinite(rn)) atomicOr(sc.status, ST_NONFINITE);
+        if (sc.active[col]) {
+            sc.iters[col] += 1;
+            if (rn <= rtol * sc.bnorm[col] || !isfinite(rn))
+                sc.active[col] = 0;
+            else
+                atomicAdd(sc.num_active, 1);
+        }
+        break;
+    }
+    case FIN_BETA: {
+        double b = 0.0;
+        if (sc.active[col]) {
+            b = s / sc.rz[col];
+            sc.rz[col] = s;
+        }
+        sc.beta[col] = b;
+        break;
+    }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// setup kernels (once per potential)
+// ---------------------------------------------------------------------------
+__global__ void k_coarse_potential(int mf, const double *__restrict__ Vf, int mc,
+                                   double *__restrict__ Vc) {
+    long nc = (long)mc * mc * mc;
+    for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < nc;
+         p += (long)gridDim.x * blockDim.x) {
+        int t[3];
+        t[0] = (int)(p % mc) + 1;
+        long q = p / mc;
+        t[1] = (int)(q % mc) + 1;
+        t[2] = (int)(q / mc) + 1;
+        int s0[3];
+        double w[3][2];
+        for (int d = 0; d < 3; d++) {
+            long num = (long)t[d] * (mf + 1), den = mc + 1;
+            s0[d] = (int)(num / den);
+            long rem = num % den;
+            w[d][1] = (double)rem / (double)den;
+            w[d][0] = (double)(den - rem) / (double)den;
+        }
+        double v = 0.0;
+        for (int c = 0; c < 8; c++) {
+            int a = c & 1, b = (c >> 1) & 1, e = (c >> 2) & 1;
+            double wt = w[0][a] * w[1][b] * w[2][e];
+            if (wt == 0.0) continue;
+            int fi = s0[0] + a, fj = s0[1] + b, fk = s0[2] + e;
+            if (fi < 1 || fi > mf || fj < 1 || fj > mf || fk < 1 || fk > mf) continue;
+            v += wt * Vf[(fi - 1) + (long)mf * ((fj - 1) + (long)mf * (fk - 1))];
+        }
+        Vc[p] = v;
+    }
+}
+
+__global__ void k_level_diag(long n, const double *V, double sigma, double c, double omega,
+                             double *D, double *wD) {
+    for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < n;
+         p += (long)gridDim.x * blockDim.x) {
+        double d = 6.0 * c + V[p] + sigma;
+        D[p] = d;
+        wD[p] = omega / d;
+    }
+}
+
+__global__ void k_assemble_dense(int mc, double c, const double *V, double sigma, double *A) {
+    long nc = (long)mc * mc * mc;
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < nc * nc;
+         idx += (long)gridDim.x * blockDim.x) {
+        long p = idx / nc, q = idx % nc;
+        double a = 0.0;
+        if (p == q) {
+            a = 6.0 * c + V[p] + sigma;
+        } else {
+            int pi = p % mc, pj = (p / mc) % mc, pk = p / (mc * mc);
+            int qi = q % mc, qj = (q / mc) % mc, qk = q / (mc * mc);
+            int d = abs(pi - qi) + abs(pj - qj) + abs(pk - qk);
+            if (d == 1) a = -c;
+        }
+        A[idx] = a;
+    }
+}
+
+// Gauss-Jordan inverse of an SPD matrix (no pivoting needed), one CTA.
+__global__ void __launch_bounds__(256) k_gauss_jordan(int nc, double *A, double *Ainv,
+                                                      int *status) {
+    extern __shared__ double fcol[];
+    const long n2 = (long)nc * nc;
+    for (long i = threadIdx.x; i < n2; i += blockDim.x)
+        Ainv[i] = (i / nc == i % nc) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int k = 0; k < nc; k++) {
+        double piv = A[(long)k * nc + k];
+        if (!(piv > 0.0) || !isfinite(piv)) {
+            if (threadIdx.x == 0) atomicOr(status, ST_GJ_FAIL);
+            return;  // uniform: every thread reads the same pivot
+        }
+        __syncthreads();
+        double inv = 1.0 / piv;
+        for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+            A[(long)k * nc + j] *= inv;
+            Ainv[(long)k * nc + j] *= inv;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nc; i += blockDim.x) fcol[i] = A[(long)i * nc + k];
+        __syncthreads();
+        for (long idx = threadIdx.x; idx < n2; idx += blockDim.x) {
+            int i = (int)(idx / nc), j = (int)(idx % nc);
+            if (i == k) continue;
+            double f = fcol[i];
+            A[idx] -= f * A[(long)k * nc + j];
+            Ainv[idx] -= f * Ainv[(long)k * nc + j];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_minmax(long n, const double *V, double *out) {
+    __shared__ double mn[256];
+    __shared__ int bad[256];
+    double m = INFINITY;
+    int b = 0;
+    for (long p = threadIdx.x; p < n; p += blockDim.x) {
+        double v = V[p];
+        if (!isfinite(v)) b = 1;
+        else m = fmin(m, v);
+    }
+    mn[threadIdx.x] = m;
+    bad[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            mn[threadIdx.x] = fmin(mn[threadIdx.x], mn[threadIdx.x + w]);
+            bad[threadIdx.x] |= bad[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = mn[0];
+        out[1] = bad[0] ? 1.0 : 0.0;
+    }
+}
+
+__global__ void k_d2f(size_t count, const double *in, float *out) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+__global__ void k_f2d(size_t count, const float *in, double *out) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+template <typename T>
+__global__ void k_scale(size_t count, const double *factor, T *x) {
+    T f = (T)factor[0];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+         i += (size_t)gridDim.x * blockDim.x)
+        x[i] *= f;
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static inline dim3 blk(const GridGeom &g) { return dim3(g.tx, g.ty); }
+static inline dim3 grd(const GridGeom &g) { return dim3(g.gx, g.gy); }
+
+#define HQ_VEC_DISPATCH(T, g, KERNEL, ...)                                       \
+    do {                                                                         \
+        if ((g).vec == 4) KERNEL<T, (sizeof(T) == 4 ? 4 : 2)>(__VA_ARGS__);       \
+        else if ((g).vec == 2) KERNEL<T, 2>(__VA_ARGS__);                         \
+        else KERNEL<T, 1>(__VA_ARGS__);                                           \
+    } while (0)
+
+template <typename T, int V>
+static void run_apply(const GridGeom &g, const T *D, T c, const T *x, T *y, double *part,
+                      cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_STENCIL, k_stencil<T, V, 0><<<grd(g), blk(g), 0, s>>>(g.m, g.n, g.N, g.ppt, D, c, x, nullptr, y,
+                                                  part, nullptr));
+}
+template <typename T>
+void launch_apply(const GridGeom &g, const T *D, T c, const T *x, T *y, double *part_xy,
+                  cudaStream_t s) {
+    HQ_VEC_DISPATCH(T, g, run_apply, g, D, c, x, y, part_xy, s);
+}
+
+template <typename T, int V>
+static void run_resid(const GridGeom &g, const T *D, T c, const T *x, const T *b, T *y,
+                      double *p1, double *p2, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_STENCIL, k_stencil<T, V, 1><<<grd(g), blk(g), 0, s>>>(g.m, g.n, g.N, g.ppt, D, c, x, b, y, p1, p2));
+}
+template <typename T>
+void launch_resid(const GridGeom &g, const T *D, T c, const T *x, const T *b, T *y,
+                  double *part_yy, double *part_bb, cudaStream_t s) {
+    HQ_VEC_DISPATCH(T, g, run_resid, g, D, c, x, b, y, part_yy, part_bb, s);
+}
+
+template <typename T, int V>
+static void run_pcg_xr(const GridGeom &g, const double *alpha, const T *p, const T *q, T *x,
+                       T *r, double *part, const T *wD, T *zf, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_VECTOR, k_pcg_xr<T, V><<<grd(g), blk(g), 0, s>>>(g.m, g.n, g.N, g.ppt, alpha, p, q, x, r, part, wD,
+                                             zf));
+}
+template <typename T>
+void launch_pcg_xr(const GridGeom &g, const double *alpha, const T *p, const T *q, T *x, T *r,
+                   double *part_rr, const T *wD, T *zf, cudaStream_t s) {
+    HQ_VEC_DISPATCH(T, g, run_pcg_xr, g, alpha, p, q, x, r, part_rr, wD, zf, s);
+}
+
+template <typename T, int V>
+static void run_pcg_p(const GridGeom &g, const double *beta, const T *z, T *p, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_VECTOR, k_pcg_p<T, V><<<grd(g), blk(g), 0, s>>>(g.n, g.N, g.ppt, beta, z, p));
+}
+template <typename T>
+void launch_pcg_p(const GridGeom &g, const double *beta, const T *z, T *p, cudaStream_t s) {
+    HQ_VEC_DISPATCH(T, g, run_pcg_p, g, beta, z, p, s);
+}
+
+template <typename T, int V>
+static void run_jacobi(const GridGeom &g, const T *wD, T c, T omw, const T *r, const T *zin,
+                       T *zout, double *part, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_SMOOTH, k_jacobi<T, V><<<grd(g), blk(g), 0, s>>>(g.m, g.n, g.N, g.ppt, wD, c, omw, r, zin, zout,
+                                             part));
+}
+template <typename T>
+void launch_jacobi(const GridGeom &g, const T *D, const T *wD, T c, T omw, const T *r,
+                   const T *zin, T *zout, double *part_rz, cudaStream_t s) {
+    (void)D;
+    HQ_VEC_DISPATCH(T, g, run_jacobi, g, wD, c, omw, r, zin, zout, part_rz, s);
+}
+
+template <typename T, int V>
+static void run_jacobi_first(const GridGeom &g, const T *wD, const T *r, T *z, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_SMOOTH, k_jacobi_first<T, V><<<grd(g), blk(g), 0, s>>>(g.n, g.N, g.ppt, wD, r, z));
+}
+template <typename T>
+void launch_jacobi_first(const GridGeom &g, const T *wD, const T *r, T *z, cudaStream_t s) {
+    HQ_VEC_DISPATCH(T, g, run_jacobi_first, g, wD, r, z, s);
+}
+
+template <typename T, int V>
+static void run_restrict(const GridGeom &gc, int mf, const T *rf, T *rc, cudaStream_t s) {
+    double q = (double)(gc.m + 1) / (double)(mf + 1);
+    HQ_LAUNCH(HQ_K_TRANSFER, k_restrict<T, V><<<grd(gc), blk(gc), 0, s>>>(gc.m, gc.n, gc.N, gc.ppt, mf, q * q * q, rf,
+                                                 rc));
+}
+template <typename T>
+void launch_restrict(const GridGeom &gc, int mf, const T *rf, T *rc, cudaStream_t s) {
+    HQ_VEC_DISPATCH(T, gc, run_restrict, gc, mf, rf, rc, s);
+}
+
+template <typename T, int V>
+static void run_prolong(const GridGeom &gf, int mc, const T *ec, const T *efin, T *efout,
+                        cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_TRANSFER, k_prolong<T, V><<<grd(gf), blk(gf), 0, s>>>(gf.m, gf.n, gf.N, gf.ppt, mc, ec, efin, efout));
+}
+template <typename T>
+void launch_prolong(const GridGeom &gf, int mc, const T *ec, const T *efin, T *efout,
+                    cudaStream_t s) {
+    HQ_VEC_DISPATCH(T, gf, run_prolong, gf, mc, ec, efin, efout, s);
+}
+
+template <typename T, int V>
+static void run_coarse_solve(const GridGeom &g, const double *Ainv, const T *r, T *z,
+                             cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_COARSE, k_coarse_solve<T, V><<<grd(g), blk(g), 0, s>>>(g.n, g.N, g.ppt, Ainv, r, z));
+}
+template <typename T>
+void launch_coarse_solve(const GridGeom &g, const double *Ainv, const T *r, T *z,
+                         cudaStream_t s) {
+    HQ_VEC_DISPATCH(T, g, run_coarse_solve, g, Ainv, r, z, s);
+}
+
+template <typename T, int V>
+static void run_dot(const GridGeom &g, const T *x, const T *y, double *part, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_VECTOR, k_dot<T, V><<<grd(g), blk(g), 0, s>>>(g.n, g.N, g.ppt, x, y, part));
+}
+template <typename T>
+void launch_dot(const GridGeom &g, const T *x, const T *y, double *part, cudaStream_t s) {
+    HQ_VEC_DISPATCH(T, g, run_dot, g, x, y, part, s);
+}
+
+void launch_finalize(int mode, int N, int gy, const double *part, const double *part2,
+                     PcgScalars sc, double rtol, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_REDUCE, k_finalize<<<N, 128, 0, s>>>(mode, N, gy, part, part2, sc, rtol));
+}
+
+void launch_coarse_potential(int mf, const double *Vf, int mc, double *Vc, cudaStream_t s) {
+    long nc = (long)mc * mc * mc;
+    int blocks = (int)std::min<long>((nc + 255) / 256, 4096);
+    HQ_LAUNCH(HQ_K_SETUP, k_coarse_potential<<<blocks, 256, 0, s>>>(mf, Vf, mc, Vc));
+}
+void launch_level_diag(long n, const double *V, double sigma, double c, double omega,
+                       double *D, double *wD, cudaStream_t s) {
+    int blocks = (int)std::min<long>((n + 255) / 256, 4096);
+    HQ_LAUNCH(HQ_K_SETUP, k_level_diag<<<blocks, 256, 0, s>>>(n, V, sigma, c, omega, D, wD));
+}
+void launch_assemble_dense(int mc, double c, const double *V, double sigma, double *A,
+                           cudaStream_t s) {
+    long nc = (long)mc * mc * mc;
+    int blocks = (int)std::min<long>((nc * nc + 255) / 256, 4096);
+    HQ_LAUNCH(HQ_K_SETUP, k_assemble_dense<<<blocks, 256, 0, s>>>(mc, c, V, sigma, A));
+}
+void launch_gauss_jordan(int nc, double *A, double *Ainv, int *status, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_SETUP, k_gauss_jordan<<<1, 256, sizeof(double) * nc, s>>>(nc, A, Ainv, status));
+}
+void launch_minmax(long n, const double *V, double *out2, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_REDUCE, k_minmax<<<1, 256, 0, s>>>(n, V, out2));
+}
+void launch_convert_d2f(size_t count, const double *in, float *out, cudaStream_t s) {
+    int blocks = (int)std::min<size_t>((count + 255) / 256, 152 * 16);
+    if (count) HQ_LAUNCH(HQ_K_VECTOR, k_d2f<<<blocks, 256, 0, s>>>(count, in, out));
+}
+void launch_convert_f2d(size_t count, const float *in, double *out, cudaStream_t s) {
+    int blocks = (int)std::min<size_t>((count + 255) / 256, 152 * 16);
+    if (count) HQ_LAUNCH(HQ_K_VECTOR, k_f2d<<<blocks, 256, 0, s>>>(count, in, out));
+}
+template <typename T>
+void launch_scale(size_t count, const double *factor, T *x, cudaStream_t s) {
+    int blocks = (int)std::min<size_t>((count + 255) / 256, 152 * 16);
+    if (count) HQ_LAUNCH(HQ_K_VECTOR, k_scale<T><<<blocks, 256, 0, s>>>(count, factor, x));
+}
+
+#define HQ_INST(T)                                                                           \
+    template void launch_apply<T>(const GridGeom &, const T *, T, const T *, T *, double *,   \
+                                  cudaStream_t);                                             \
+    template void launch_resid<T>(const GridGeom &, const T *, T, const T *, const T *, T *,  \
+                                  double *, double *, cudaStream_t);                         \
+    template void launch_pcg_xr<T>(const GridGeom &, const double *, const T *, const T *,    \
+                                   T *, T *, double *, const T *, T *, cudaStream_t);        \
+    template void launch_pcg_p<T>(const GridGeom &, const double *, const T *, T *,           \
+                                  cudaStream_t);                                             \
+    template void launch_jacobi<T>(const GridGeom &, const T *, const T *, T, T, const T *,   \
+                                   const T *, T *, double *, cudaStream_t);                  \
+    template void launch_jacobi_first<T>(const GridGeom &, const T *, const T *, T *,         \
+                                         cudaStream_t);                                      \
+    template void launch_restrict<T>(const GridGeom &, int, const T *, T *, cudaStream_t);    \
+    template void launch_prolong<T>(const GridGeom &, int, const T *, const T *, T *,         \
+                                    cudaStream_t);                                           \
+    template void launch_coarse_solve<T>(const GridGeom &, const double *, const T *, T *,    \
+                                         cudaStream_t);                                      \
+    template void launch_dot<T>(const GridGeom &, const T *, const T *, double *,             \
+                                cudaStream_t);                                               \
+    template void launch_scale<T>(size_t, const double *, T *, cudaStream_t);
+
+HQ_INST(double)
+HQ_INST(float)
+
+}  // namespace hq

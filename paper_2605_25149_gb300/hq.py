@@ -1,0 +1,362 @@
+"""ctypes binding of libhq (include/hq.h): argument marshalling only.
+
+Every step of the eigensolver runs in libhq's CUDA kernels; PyTorch provides
+the device workspace (one uint8 tensor) and the CUDA stream.  Importing this
+module loads the in-tree ``_build/libhq.so`` and raises if it is missing:
+there is no CPU fallback.
+
+Host arrays are numpy FP64 arrays; device arrays are CUDA torch tensors of
+the context's element type (float64 for ``precision="fp64"``, float32 for
+``precision="mixed"`` where a call takes the working precision, float64 where
+the header says FP64).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhq.so")
+
+OK = 0
+STATUS_NAMES = {
+    0: "HQ_OK", 1: "HQ_ERR_ARG", 2: "HQ_ERR_STATE", 3: "HQ_ERR_CUDA", 4: "HQ_ERR_NOMEM",
+    5: "HQ_ERR_BREAKDOWN", 6: "HQ_ERR_SINGULAR", 7: "HQ_ERR_NOT_CONVERGED",
+    8: "HQ_ERR_TIMEOUT", 9: "HQ_ERR_NONFINITE",
+}
+FP64, MIXED = 0, 1
+
+EXPORTED = [
+    "hq_default_config", "hq_workspace_bytes", "hq_init", "hq_set_potential", "hq_set_initial",
+    "hq_step", "hq_solve", "hq_eigenpairs", "hq_get_state", "hq_set_state", "hq_problem_info",
+    "hq_apply_operator", "hq_mg_vcycle", "hq_block_pcg", "hq_gram", "hq_step_trace",
+    "hq_mg_smooth", "hq_mg_restrict", "hq_mg_prolong", "hq_mg_coarse_solve",
+    "hq_mg_level_potential", "hq_profile", "hq_profile_read", "hq_last_error",
+    "hq_status_string", "hq_destroy",
+]
+KERNEL_CLASSES = ["stencil", "smooth", "transfer", "coarse", "vector", "reduce", "gram",
+                  "blockgemm", "small", "setup"]
+
+
+class HQError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("m", ctypes.c_int), ("lo", ctypes.c_double), ("hi", ctypes.c_double),
+        ("nev", ctypes.c_int), ("tau", ctypes.c_double), ("shift", ctypes.c_double),
+        ("precision", ctypes.c_int), ("cg_rtol", ctypes.c_double), ("cg_maxit", ctypes.c_int),
+        ("mg_nu1", ctypes.c_int), ("mg_nu2", ctypes.c_int), ("mg_coarsest", ctypes.c_int),
+        ("mg_omega", ctypes.c_double), ("timeout_s", ctypes.c_double),
+    ]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_L = ctypes.c_long
+_lib = None
+
+
+def load():
+    """Load libhq.so (built by paper_2605_25149_gb300.build); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libhq.so is not built (%s); run "
+                           "paper_2605_25149_gb300.build.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "hq_default_config": (None, [_P]),
+        "hq_workspace_bytes": (ctypes.c_size_t, [_P]),
+        "hq_init": (_I, [_P, _P, ctypes.c_size_t, _P, _P]),
+        "hq_set_potential": (_I, [_P, _P, _I]),
+        "hq_set_initial": (_I, [_P, _P, _I]),
+        "hq_step": (_I, [_P, _I, _P]),
+        "hq_solve": (_I, [_P, _D, _L, _P, _P]),
+        "hq_eigenpairs": (_I, [_P, _P, _P, _P, _I, _P]),
+        "hq_get_state": (_I, [_P, _P, _P, _I, _P]),
+        "hq_set_state": (_I, [_P, _P, _P, _I, _L]),
+        "hq_problem_info": (_I, [_P, _P, _P, _P, _P]),
+        "hq_apply_operator": (_I, [_P, _P, _P, _I]),
+        "hq_mg_vcycle": (_I, [_P, _P, _P]),
+        "hq_block_pcg": (_I, [_P, _P, _P, _D, _I, _P]),
+        "hq_gram": (_I, [_P, _P, _I, _P, _I, _D, _P]),
+        "hq_step_trace": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
+        "hq_mg_smooth": (_I, [_P, _I, _P, _P, _P]),
+        "hq_mg_restrict": (_I, [_P, _I, _P, _P]),
+        "hq_mg_prolong": (_I, [_P, _I, _P, _P, _P]),
+        "hq_mg_coarse_solve": (_I, [_P, _P, _P]),
+        "hq_mg_level_potential": (_I, [_P, _I, _P]),
+        "hq_profile": (_I, [_P, _I]),
+        "hq_profile_read": (_I, [_P, _P, _P]),
+        "hq_last_error": (ctypes.c_char_p, [_P]),
+        "hq_status_string": (ctypes.c_char_p, [_I]),
+        "hq_destroy": (None, [_P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def default_config(m, nev, **kw) -> Config:
+    c = Config()
+    load().hq_default_config(ctypes.byref(c))
+    c.m, c.nev = m, nev
+    if "precision" in kw and isinstance(kw["precision"], str):
+        kw["precision"] = {"fp64": FP64, "mixed": MIXED}[kw["precision"]]
+    for k, v in kw.items():
+        if v is None:
+            continue
+        setattr(c, k, v)
+    return c
+
+
+def workspace_bytes(cfg: Config) -> int:
+    return int(load().hq_workspace_bytes(ctypes.byref(cfg)))
+
+
+def _dptr(t):
+    """Device pointer of a contiguous CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Solver:
+    """One eigenproblem context (C handle hq_ctx) on the current CUDA device."""
+
+    def __init__(self, m, nev, stream=None, **cfg_kw):
+        import torch
+        self._torch = torch
+        self.lib = load()
+        self.cfg = default_config(m, nev, **cfg_kw)
+        nbytes = workspace_bytes(self.cfg)
+        if nbytes == 0:
+            raise HQError(1, "invalid configuration")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self.workspace.data_ptr()
+        off = (-base) % 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._ctx = ctypes.c_void_p()
+        st = self.lib.hq_init(ctypes.byref(self.cfg), ctypes.c_void_p(base + off), nbytes,
+                              ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self._ctx))
+        if st != OK:
+            raise HQError(st, "hq_init failed")
+        self.m, self.N = m, nev
+        self.n = m ** 3
+        self.dtype = torch.float64 if self.cfg.precision == FP64 else torch.float32
+
+    # -- plumbing ---------------------------------------------------------
+    def _check(self, st, what):
+        if st != OK:
+            msg = self.lib.hq_last_error(self._ctx)
+            raise HQError(st, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            self.lib.hq_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _host_f64(a, shape):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        if a.size != int(np.prod(shape)):
+            raise ValueError("expected %s values" % (shape,))
+        return a
+
+    def _buf(self, a, shape):
+        """(pointer, on_device, keepalive) for an FP64 host array or CUDA tensor."""
+        if hasattr(a, "is_cuda") and a.is_cuda:
+            if a.dtype != self._torch.float64 or a.numel() != int(np.prod(shape)):
+                raise ValueError("expected a float64 CUDA tensor of %s values" % (shape,))
+            return _dptr(a), 1, a
+        h = self._host_f64(a, shape)
+        return _hptr(h), 0, h
+
+    # -- the five calls of the problem statement ---------------------------
+    def set_potential(self, V):
+        p, dev, keep = self._buf(V, (self.n,))
+        self._check(self.lib.hq_set_potential(self._ctx, p, dev), "hq_set_potential")
+
+    def set_initial(self, U0):
+        p, dev, keep = self._buf(U0, (self.n, self.N))
+        self._check(self.lib.hq_set_initial(self._ctx, p, dev), "hq_set_initial")
+
+    def step(self, nsteps=1):
+        g = ctypes.c_double()
+        self._check(self.lib.hq_step(self._ctx, nsteps, ctypes.byref(g)), "hq_step")
+        return g.value
+
+    def solve(self, eps, max_steps, raise_on_unconverged=True):
+        steps, g = ctypes.c_long(), ctypes.c_double()
+        st = self.lib.hq_solve(self._ctx, eps, max_steps, ctypes.byref(steps), ctypes.byref(g))
+        if st == 7 and not raise_on_unconverged:
+            return steps.value, g.value
+        self._check(st, "hq_solve")
+        return steps.value, g.value
+
+    def eigenpairs(self, vectors=False, vectors_on_device=False):
+        N = self.N
+        lp, lr, res = np.empty(N), np.empty(N), np.empty(N)
+        vec = None
+        vptr = None
+        if vectors:
+            if vectors_on_device:
+                vec = self._torch.empty((self.n, N), dtype=self._torch.float64, device="cuda")
+                vptr = _dptr(vec)
+            else:
+                vec = np.empty((self.n, N))
+                vptr = _hptr(vec)
+        self._check(self.lib.hq_eigenpairs(self._ctx, _hptr(lp), _hptr(lr), vptr,
+                                           1 if vectors_on_device else 0, _hptr(res)),
+                    "hq_eigenpairs")
+        return dict(lam_paper=lp, lam_rr=lr, vectors=vec, residuals=res)
+
+    def get_state(self, with_warm_start=False):
+        U = np.empty((self.n, self.N))
+        Z = np.empty((self.n, self.N)) if with_warm_start else None
+        step = ctypes.c_long()
+        self._check(self.lib.hq_get_state(self._ctx, _hptr(U), _hptr(Z), 0, ctypes.byref(step)),
+                    "hq_get_state")
+        return U, Z, step.value
+
+    def set_state(self, U, step, Z=None):
+        U = self._host_f64(U, (self.n, self.N))
+        Zh = None if Z is None else self._host_f64(Z, (self.n, self.N))
+        self._check(self.lib.hq_set_state(self._ctx, _hptr(U), _hptr(Zh), 0, step),
+                    "hq_set_state")
+
+    def info(self):
+        h, s, L = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        ms = (ctypes.c_int * 24)()
+        self._check(self.lib.hq_problem_info(self._ctx, ctypes.byref(h), ctypes.byref(s),
+                                             ctypes.byref(L), ms), "hq_problem_info")
+        return dict(h=h.value, sigma=s.value, levels=[ms[i] for i in range(L.value)])
+
+    # -- kernel-level operations on device tensors -------------------------
+    def _dev(self, t, rows, cols=None):
+        cols = self.N if cols is None else cols
+        if t.dtype != self.dtype or t.numel() != rows * cols:
+            raise ValueError("expected %s tensor with %d x %d values" % (self.dtype, rows, cols))
+        return _dptr(t)
+
+    def apply_operator(self, x, ncol=None):
+        ncol = self.N if ncol is None else ncol
+        y = self._torch.empty_like(x)
+        self._check(self.lib.hq_apply_operator(self._ctx, self._dev(x, self.n, ncol),
+                                               _dptr(y), ncol), "hq_apply_operator")
+        return y
+
+    def mg_vcycle(self, r):
+        z = self._torch.empty_like(r)
+        self._check(self.lib.hq_mg_vcycle(self._ctx, self._dev(r, self.n), _dptr(z)),
+                    "hq_mg_vcycle")
+        return z
+
+    def block_pcg(self, B, X0=None, rtol=1e-10, maxit=200):
+        X = self._torch.zeros_like(B) if X0 is None else X0.clone()
+        its = np.zeros(self.N, dtype=np.int32)
+        self._check(self.lib.hq_block_pcg(self._ctx, self._dev(B, self.n), _dptr(X), rtol, maxit,
+                                          _hptr(its)), "hq_block_pcg")
+        return X, its
+
+    def gram(self, A, B, w):
+        Na, Nb = A.shape[1], B.shape[1]
+        out = self._torch.empty((Na, Nb), dtype=self._torch.float64, device="cuda")
+        self._check(self.lib.hq_gram(self._ctx, self._dev(A, self.n, Na), Na,
+                                     self._dev(B, self.n, Nb), Nb, w, _dptr(out)), "hq_gram")
+        return out
+
+    def step_trace(self):
+        t = self._torch
+        n, N = self.n, self.N
+        o = dict(W=t.empty((n, N), dtype=self.dtype, device="cuda"),
+                 gram=t.empty((2 * N, 2 * N), dtype=t.float64, device="cuda"),
+                 g=t.empty(1, dtype=t.float64, device="cuda"),
+                 XY=t.empty((2 * N, N), dtype=t.float64, device="cuda"),
+                 Uh=t.empty((n, N), dtype=self.dtype, device="cuda"),
+                 Shat=t.empty((N, N), dtype=t.float64, device="cuda"),
+                 Z=t.empty((n, N), dtype=self.dtype, device="cuda"),
+                 Unew=t.empty((n, N), dtype=self.dtype, device="cuda"))
+        self._check(self.lib.hq_step_trace(self._ctx, *[_dptr(o[k]) for k in
+                                                        ("W", "gram", "g", "XY", "Uh", "Shat",
+                                                         "Z", "Unew")]), "hq_step_trace")
+        return o
+
+    def profile(self, timing=False):
+        """Reset the launch counters; timing=True brackets launches with events."""
+        self._check(self.lib.hq_profile(self._ctx, 1 if timing else 0), "hq_profile")
+
+    def profile_read(self):
+        """{class: (launches, ms)} since the last profile() call."""
+        n = len(KERNEL_CLASSES)
+        la = (ctypes.c_long * n)()
+        ms = (ctypes.c_double * n)()
+        self._check(self.lib.hq_profile_read(self._ctx, la, ms), "hq_profile_read")
+        return {k: (la[i], ms[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+    def levels(self):
+        return self.info()["levels"]
+
+    def mg_smooth(self, level, r, zin):
+        m = self.levels()[level]
+        zout = self._torch.empty_like(zin)
+        self._check(self.lib.hq_mg_smooth(self._ctx, level, self._dev(r, m ** 3),
+                                          self._dev(zin, m ** 3), _dptr(zout)), "hq_mg_smooth")
+        return zout
+
+    def mg_restrict(self, level, rf):
+        ms = self.levels()
+        rc = self._torch.empty((ms[level + 1] ** 3, self.N), dtype=self.dtype, device="cuda")
+        self._check(self.lib.hq_mg_restrict(self._ctx, level, self._dev(rf, ms[level] ** 3),
+                                            _dptr(rc)), "hq_mg_restrict")
+        return rc
+
+    def mg_prolong(self, level, ec, efin):
+        ms = self.levels()
+        efout = self._torch.empty_like(efin)
+        self._check(self.lib.hq_mg_prolong(self._ctx, level, self._dev(ec, ms[level + 1] ** 3),
+                                           self._dev(efin, ms[level] ** 3), _dptr(efout)),
+                    "hq_mg_prolong")
+        return efout
+
+    def mg_coarse_solve(self, r):
+        mc = self.levels()[-1]
+        z = self._torch.empty_like(r)
+        self._check(self.lib.hq_mg_coarse_solve(self._ctx, self._dev(r, mc ** 3), _dptr(z)),
+                    "hq_mg_coarse_solve")
+        return z
+
+    def mg_level_potential(self, level):
+        m = self.levels()[level]
+        out = self._torch.empty(m ** 3, dtype=self._torch.float64, device="cuda")
+        self._check(self.lib.hq_mg_level_potential(self._ctx, level, _dptr(out)),
+                    "hq_mg_level_potential")
+        return out
+
+
+def status_string(st: int) -> str:
+    return load().hq_status_string(st).decode()

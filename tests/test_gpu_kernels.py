@@ -1,0 +1,107 @@
+"""GPU parity of the hot-path operations against the CPU oracle, element by
+element, through the C ABI (FP64 contexts unless stated).  Sizes span several
+CTAs with ragged tails (odd m, odd N) and the degenerate cases (N = 1,
+single-level multigrid)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2605_25149_gb300 import inputs
+from tests.gpu_common import dev, host, make, oracle_mg, rel, torch_mod
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.mark.parametrize("m,N", [(5, 1), (8, 3), (13, 17), (16, 8), (24, 64)])
+def test_operator_matches_oracle(m, N):
+    torch = torch_mod()
+    s, V, _ = make(m, N)
+    rng = np.random.default_rng(m * 7 + N)
+    X = rng.standard_normal((m ** 3, N))
+    Y = host(s.apply_operator(dev(X)))
+    Yo = O.apply_h(m, inputs.grid_h(m), V, s.info()["sigma"], X)
+    assert rel(Y, Yo) < TOL64
+
+
+@pytest.mark.parametrize("m,N", [(9, 2), (16, 5), (20, 8)])
+def test_multigrid_pieces_match_oracle(m, N):
+    s, V, _ = make(m, N)
+    mg = oracle_mg(s, V)
+    assert s.levels() == mg.levels
+    rng = np.random.default_rng(m + N)
+    for l, ml in enumerate(mg.levels):
+        np.testing.assert_allclose(host(s.mg_level_potential(l)), mg.level_potential(l),
+                                   rtol=1e-14, atol=1e-14)
+        r = rng.standard_normal((ml ** 3, N))
+        z = rng.standard_normal((ml ** 3, N))
+        assert rel(host(s.mg_smooth(l, dev(r), dev(z))), mg.smooth(l, r, z)) < TOL64
+        if l + 1 < len(mg.levels):
+            mc = mg.levels[l + 1]
+            assert rel(host(s.mg_restrict(l, dev(r))), O.restrict(ml, mc, r)) < TOL64
+            ec = rng.standard_normal((mc ** 3, N))
+            assert rel(host(s.mg_prolong(l, dev(ec), dev(z))), O.prolong_add(mc, ml, ec, z)) < TOL64
+    mc = mg.levels[-1]
+    r = rng.standard_normal((mc ** 3, N))
+    assert rel(host(s.mg_coarse_solve(dev(r))), mg.coarse_solve(r)) < 1e-11
+
+
+@pytest.mark.parametrize("m,N", [(3, 2), (16, 4), (21, 9)])
+def test_vcycle_matches_oracle(m, N):
+    s, V, _ = make(m, N)
+    mg = oracle_mg(s, V)
+    r = np.random.default_rng(5).standard_normal((m ** 3, N))
+    assert rel(host(s.mg_vcycle(dev(r))), mg.vcycle(r)) < 1e-11
+
+
+@pytest.mark.parametrize("m,N,k", [(12, 3, 1), (16, 8, 4), (19, 5, 6)])
+def test_pcg_recurrence_matches_oracle_iteration_by_iteration(m, N, k):
+    """rtol = 0: both sides run exactly k PCG iterations of the same recurrence."""
+    s, V, _ = make(m, N)
+    mg = oracle_mg(s, V)
+    B = np.random.default_rng(7).standard_normal((m ** 3, N))
+    X, its = s.block_pcg(dev(B), rtol=0.0, maxit=k)
+    Xo, itso = mg.pcg(B, rtol=0.0, maxit=k)
+    assert (its == k).all() and (itso == k).all()
+    assert rel(host(X), Xo) < 1e-10
+
+
+def test_pcg_converges_to_inverse_operator():
+    m, N = 24, 6
+    s, V, _ = make(m, N)
+    sigma = s.info()["sigma"]
+    B = np.random.default_rng(8).standard_normal((m ** 3, N))
+    X, its = s.block_pcg(dev(B), rtol=1e-11, maxit=100)
+    X = host(X)
+    res = np.linalg.norm(B - O.apply_h(m, inputs.grid_h(m), V, sigma, X), axis=0)
+    assert (res <= 1e-11 * np.linalg.norm(B, axis=0) * 1.0001).all()
+    Xo, _ = O.cg(m, inputs.grid_h(m), V, sigma, B, rtol=1e-13)
+    assert rel(X, Xo) < 1e-8
+    mg = oracle_mg(s, V)
+    _, itso = mg.pcg(B, rtol=1e-11, maxit=100)
+    np.testing.assert_array_equal(its, itso)
+
+
+@pytest.mark.parametrize("m,Na,Nb", [(10, 3, 3), (16, 16, 9), (17, 70, 128), (12, 1, 5)])
+def test_gram_matches_oracle(m, Na, Nb):
+    N = max(Na, Nb)
+    s, V, _ = make(m, (N + 1) // 2 if N > 1 else 1)
+    rng = np.random.default_rng(Na * 31 + Nb)
+    A = rng.standard_normal((m ** 3, Na))
+    B = rng.standard_normal((m ** 3, Nb))
+    w = inputs.grid_h(m) ** 3
+    out = host(s.gram(dev(A), dev(B), w))
+    assert rel(out, O.gram(A, B, w)) < TOL64
+    outs = host(s.gram(dev(A), dev(A), w))     # symmetric path
+    assert rel(outs, O.gram(A, A, w)) < TOL64
+
+
+def test_determinism_bitwise():
+    m, N = 16, 8
+    outs = []
+    for _ in range(2):
+        s, V, U0 = make(m, N)
+        s.step(2)
+        outs.append(s.get_state()[0])
+    np.testing.assert_array_equal(outs[0], outs[1])

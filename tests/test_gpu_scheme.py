@@ -1,0 +1,130 @@
+"""GPU parity of the scheme (Eq. (4.1)), Algorithm 1 and extraction against
+the CPU oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2605_25149_gb300 import hq, inputs
+from tests.gpu_common import dev, host, make, rel, torch_mod
+from tests.helpers import separable_levels
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_from_gpu_start(s, U0):
+    h3 = inputs.grid_h(s.m) ** 3
+    Uo, _ = O.scale_initial(U0, h3)
+    return Uo
+
+
+@pytest.mark.parametrize("m,N,pot", [(10, 4, "wells"), (13, 7, "harmonic"), (16, 8, "wells")])
+def test_step_intermediates_match_oracle(m, N, pot):
+    tau = 0.4
+    s, V, U0 = make(m, N, potential=pot, tau=tau, cg_rtol=1e-13, cg_maxit=400)
+    sigma = s.info()["sigma"]
+    Ug0, _, _ = s.get_state()
+    Uo = _oracle_from_gpu_start(s, U0)
+    assert rel(Ug0, Uo) < 1e-13
+    tr = s.step_trace()
+    o = O.scheme_step(m, V, sigma, Ug0, tau)
+    assert rel(host(tr["W"]), o["W"]) < 1e-10
+    assert rel(host(tr["gram"]), o["gram"]) < 1e-10
+    assert abs(host(tr["g"])[0] - o["g"]) <= 1e-9 * o["g"]
+    assert rel(host(tr["XY"]), o["XY"]) < 1e-9
+    assert rel(host(tr["Uh"]), o["Uh"]) < 1e-9
+    assert rel(host(tr["Shat"]), o["Shat"]) < 1e-10
+    assert rel(host(tr["Z"]), o["Z"]) < 1e-9
+    assert rel(host(tr["Unew"]), o["Unew"]) < 1e-9
+
+
+def test_trajectory_matches_oracle_for_20_steps():
+    m, N, tau = 12, 6, 0.4
+    s, V, U0 = make(m, N, tau=tau, cg_rtol=1e-13, cg_maxit=400)
+    sigma = s.info()["sigma"]
+    Uo = s.get_state()[0]
+    for n in range(20):
+        s.step(1)
+        Uo = O.scheme_step(m, V, sigma, Uo, tau)["Unew"]
+        assert rel(s.get_state()[0], Uo) < 1e-9, n
+
+
+def test_harmonic16_N8_converges_to_closed_form():
+    """The 16^3, N = 8 harmonic workload run to residual 1e-8 (Algorithm 1):
+    FP64 Rayleigh-Ritz values equal the 1D-sum closed form to 1e-10."""
+    m, N = 16, 8
+    s, V, U0 = make(m, N, potential="harmonic", useed=1, tau=0.5, cg_rtol=1e-10)
+    steps, g = s.solve(1e-8, 10000)
+    assert g < 1e-8
+    ev = s.eigenpairs(vectors=True)
+    lv = separable_levels(m, -6.0, 6.0, N)
+    np.testing.assert_allclose(ev["lam_rr"], lv, rtol=1e-10)
+    np.testing.assert_allclose(ev["lam_paper"], lv, rtol=1e-8)
+    assert ev["residuals"].max() < 1e-6
+    h3 = inputs.grid_h(m) ** 3
+    u = ev["vectors"]
+    np.testing.assert_allclose(h3 * u.T @ u, np.eye(N), atol=1e-9)
+
+
+def test_wells_solve_matches_oracle_solve():
+    m, N, tau = 10, 5, 0.4
+    s, V, U0 = make(m, N, tau=tau, cg_rtol=1e-12)
+    sigma = s.info()["sigma"]
+    steps, g = s.solve(1e-9, 20000)
+    ev = s.eigenpairs(vectors=True)
+    Uo = _oracle_from_gpu_start(s, U0)
+    Ue, We, so, go, _ = O.solve(m, V, sigma, Uo, tau, 1e-9, 20000)
+    exo = O.extract(m, V, sigma, Ue, We)
+    np.testing.assert_allclose(ev["lam_rr"], exo["lam_rr"], rtol=1e-10)
+    np.testing.assert_allclose(ev["lam_paper"], exo["lam_paper"], rtol=1e-8)
+    assert abs(steps - so) <= 2
+    # Ritz vectors: sign-fixed, compare where the spectrum is simple
+    lam = exo["lam_rr"]
+    gaps = np.minimum(np.diff(np.r_[-np.inf, lam]), np.diff(np.r_[lam, np.inf]))
+    for i in np.nonzero(gaps > 1e-3)[0]:
+        assert rel(ev["vectors"][:, i], exo["vectors"][:, i]) < 1e-5
+
+
+def test_checkpoint_resume_is_bit_identical():
+    m, N = 12, 4
+    s, V, U0 = make(m, N)
+    s.step(3)
+    U, Z, st = s.get_state(with_warm_start=True)
+    s.step(2)
+    ref = s.get_state()[0]
+    s2, _, _ = make(m, N)
+    s2.set_state(U, st, Z=Z)
+    s2.step(2)
+    np.testing.assert_array_equal(s2.get_state()[0], ref)
+    assert s2.get_state()[2] == st + 2
+
+
+def test_error_paths_report_status():
+    torch_mod()
+    s = hq.Solver(8, 4)
+    with pytest.raises(hq.HQError) as e:
+        s.step(1)
+    assert e.value.status == 2           # HQ_ERR_STATE
+    V = inputs.harmonic(8)
+    V[5] = np.nan
+    with pytest.raises(hq.HQError) as e:
+        s.set_potential(V)
+    assert e.value.status == 9           # HQ_ERR_NONFINITE
+    s.set_potential(inputs.harmonic(8))
+    with pytest.raises(hq.HQError) as e:
+        s.set_initial(np.zeros((8 ** 3, 4)))
+    assert e.value.status == 1           # rank-deficient U0
+    # a given shift that makes H + sigma indefinite: coarsest factorisation fails
+    s2 = hq.Solver(8, 4, shift=-50.0)
+    with pytest.raises(hq.HQError) as e:
+        s2.set_potential(inputs.harmonic(8))
+    assert e.value.status == 1
+    # the context stays usable after errors
+    s.set_initial(inputs.initial_block(8, 4, 3))
+    s.step(1)
+
+
+def test_solve_reports_not_converged_and_keeps_state():
+    s, V, U0 = make(10, 4)
+    steps, g = s.solve(1e-12, 3, raise_on_unconverged=False)
+    assert steps == 3 and g > 1e-12
+    s.step(1)
