@@ -186,7 +186,8 @@ hq_status hq_mg_level_potential(hq_ctx *ctx, int level, double *V_out);
 /* ---- instrumentation ---- */
 /* Kernel classes counted by the launch counters. */
 typedef enum {
-    HQ_K_STENCIL = 0,   /* 7-point operator (apply / residual)             */
+    HQ_K_STENCIL = 0,   /* 7-point operator y = (H + sigma) x              */
+    HQ_K_RESIDUAL,      /* residual r - (H + sigma) z                      */
     HQ_K_SMOOTH,        /* damped-Jacobi sweeps                            */
     HQ_K_TRANSFER,      /* restriction / prolongation                      */
     HQ_K_COARSE,        /* coarsest-level solve                            */
@@ -205,8 +206,10 @@ typedef enum {
 hq_status hq_profile(hq_ctx *ctx, int timing);
 /* launches (HQ_K_NCLASS longs, host, nullable): kernels launched per class
  * since the last hq_profile; ms (HQ_K_NCLASS doubles, host, nullable): summed
- * event time per class (0 unless timing was on).  Synchronises the stream.  */
-hq_status hq_profile_read(hq_ctx *ctx, long *launches, double *ms);
+ * event time per class (0 unless timing was on); elements (HQ_K_NCLASS
+ * doubles, host, nullable): grid point-columns written by the grid kernels
+ * of each class (0 for the dense classes).  Synchronises the stream.        */
+hq_status hq_profile_read(hq_ctx *ctx, long *launches, double *ms, double *elements);
 
 const char *hq_last_error(hq_ctx *ctx);
 const char *hq_status_string(hq_status s);

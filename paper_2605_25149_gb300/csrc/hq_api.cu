@@ -40,6 +40,7 @@ struct Level {
     double *V = nullptr, *D = nullptr, *wD = nullptr;   // FP64
     void *Dt = nullptr, *wDt = nullptr;                 // working precision
     void *r = nullptr, *z = nullptr, *t = nullptr;      // level buffers (l >= 1)
+    XferTab tab{};                                       // transfer tables to level l + 1
     GridGeom g;
 };
 
@@ -59,6 +60,7 @@ struct hq_ctx {
     Level lev[MAXLEV];
     long nc = 0;
     double *Acoarse = nullptr, *Ainv = nullptr;
+    void *xt1 = nullptr, *xt2 = nullptr;   // transfer-pass scratch
     // n x N blocks in the working precision
     void *U = nullptr, *W = nullptr, *Uh = nullptr, *Z = nullptr;
     void *R = nullptr, *Zp = nullptr, *P = nullptr, *Q = nullptr, *Tt = nullptr;
@@ -68,6 +70,7 @@ struct hq_ctx {
     double *part = nullptr, *part2 = nullptr;
     GramPlan gplan_uw, gplan_max;
     double *gpart = nullptr;
+    float *tcpart = nullptr;   // tensor-core Gram partials (HQ_MIXED)
     TallPlan tplan;
     double *tpart = nullptr;   // gy x N
     double *G2 = nullptr, *Mw = nullptr, *XY = nullptr, *C = nullptr, *T1 = nullptr;
@@ -83,6 +86,7 @@ struct hq_ctx {
     std::string err;
     // instrumentation
     long launches[HQ_K_NCLASS] = {};
+    double work[HQ_K_NCLASS] = {};
     bool timing = false;
     std::vector<cudaEvent_t> evpool;
     size_t evused = 0;
@@ -110,10 +114,13 @@ void hook_before(int cls) {
     cudaEventRecord(x->evpool[x->evused], x->st);
     x->evused += 2;
 }
-void hook_after(int cls) {
+void hook_after(int cls, double work) {
     hq_ctx *x = g_prof;
     if (!x) return;
-    if (cls >= 0 && cls < HQ_K_NCLASS) x->launches[cls]++;
+    if (cls >= 0 && cls < HQ_K_NCLASS) {
+        x->launches[cls]++;
+        x->work[cls] += work;
+    }
     if (!x->timing || x->evused < 2) return;
     cudaEventRecord(x->evpool[x->pending_start + 1], x->st);
     x->evrec.emplace_back(cls, x->pending_start);
@@ -229,6 +236,20 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
             v.t = Tt;
         }
     }
+    for (int l = 0; l + 1 < L; l++) {
+        const int mc = ms[l + 1], mf = ms[l];
+        lev[l].tab.ridx = cv.take<int>(sizeof(int) * mc * XFER_RTAPS);
+        lev[l].tab.rw = cv.take<double>(sizeof(double) * mc * XFER_RTAPS);
+        lev[l].tab.rwf = cv.take<float>(sizeof(float) * mc * XFER_RTAPS);
+        lev[l].tab.pidx = cv.take<int>(sizeof(int) * mf * 2);
+        lev[l].tab.pw = cv.take<double>(sizeof(double) * mf * 2);
+        lev[l].tab.pwf = cv.take<float>(sizeof(float) * mf * 2);
+    }
+    // scratch of the separable transfers: (mf^2 mc + mf mc^2) x N elements on the finest level
+    const size_t xs = (L > 1) ? (size_t)ms[0] * ms[0] * ms[1] : 1;
+    const size_t xs2 = (L > 1) ? (size_t)ms[0] * ms[1] * ms[1] : 1;
+    void *xt1 = cv.take<char>(xs * N * esz);
+    void *xt2 = cv.take<char>(xs2 * N * esz);
     const long nc = lev[L - 1].n;
     double *Acoarse = cv.take<double>(sizeof(double) * nc * nc);
     double *Ainv = cv.take<double>(sizeof(double) * nc * nc);
@@ -245,6 +266,7 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
     const int gy0 = lev[0].g.gy;
     double *part = cv.take<double>(sizeof(double) * (size_t)gy0 * N);
     double *part2 = cv.take<double>(sizeof(double) * (size_t)gy0 * N);
+    float *tcpart = mixed ? cv.take<float>(gram_tc_partial_bytes(n, 2 * N)) : nullptr;
     GramPlan guw = make_gram_plan(n, 2 * N, 2 * N, true);
     GramPlan gmax = make_gram_plan(n, 2 * N, 2 * N, false);
     double *gpart = cv.take<double>(std::max(gram_partial_bytes(guw), gram_partial_bytes(gmax)));
@@ -281,9 +303,9 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
         x->Tt = Tt; x->E1 = E1; x->E2 = E2; x->E3 = E3;
         x->L = L;
         for (int l = 0; l < L; l++) x->lev[l] = lev[l];
-        x->nc = nc; x->Acoarse = Acoarse; x->Ainv = Ainv;
+        x->nc = nc; x->Acoarse = Acoarse; x->Ainv = Ainv; x->xt1 = xt1; x->xt2 = xt2;
         x->sc = sc; x->part = part; x->part2 = part2;
-        x->gplan_uw = guw; x->gplan_max = gmax; x->gpart = gpart;
+        x->gplan_uw = guw; x->gplan_max = gmax; x->gpart = gpart; x->tcpart = tcpart;
         x->tplan = tp; x->tpart = tpart;
         x->G2 = G2; x->Mw = Mw; x->XY = XY; x->C = Cc; x->T1 = T1; x->Shat = Shat; x->Om = Om;
         x->Msm = Msm; x->Ksm = Ksm; x->Ssm = Ssm; x->Lm = Lm; x->Cm = Cm; x->Ym = Ym;
@@ -377,9 +399,10 @@ hq_status vcycle(hq_ctx *x, int l, const T *r, T *Zf, T *Tb, bool first_done, do
     }
     launch_resid<T>(v.g, (const T *)v.Dt, c, cur, r, oth, nullptr, nullptr, x->st);
     Level &w = x->lev[l + 1];
-    launch_restrict<T>(w.g, v.m, oth, (T *)w.r, x->st);
+    launch_restrict<T>(v.m, w.m, x->N, v.tab, oth, (T *)x->xt1, (T *)x->xt2, (T *)w.r, x->st);
     HQ_TRY(vcycle<T>(x, l + 1, (const T *)w.r, (T *)w.z, (T *)w.t, false, nullptr));
-    launch_prolong<T>(v.g, w.m, (const T *)w.z, cur, oth, x->st);
+    launch_prolong<T>(v.m, w.m, x->N, v.tab, (const T *)w.z, (T *)x->xt1, (T *)x->xt2, cur, oth,
+                      x->st);
     std::swap(cur, oth);
     for (int s = 0; s < x->cfg.mg_nu2; s++) {
         bool last = (s == x->cfg.mg_nu2 - 1);
@@ -438,6 +461,20 @@ hq_status pcg(hq_ctx *x, const T *B, T *X, double rtol, int maxit, int *iters_ho
     return HQ_OK;
 }
 
+// Symmetric Gram of [X1 X2] into out (FP64): SIMT FP64 in HQ_FP64 contexts,
+// tcgen05 3xTF32 in HQ_MIXED contexts.
+template <typename T>
+void gram_sym(hq_ctx *x, const T *X1, int n1, const T *X2, int n2, double *out);
+template <>
+void gram_sym<double>(hq_ctx *x, const double *X1, int n1, const double *X2, int n2, double *out) {
+    GramPlan gp = make_gram_plan(x->n, n1 + n2, n1 + n2, true);
+    launch_gram<double>(gp, X1, n1, X2, n2, X1, n1, X2, n2, x->h3, x->gpart, out, x->st);
+}
+template <>
+void gram_sym<float>(hq_ctx *x, const float *X1, int n1, const float *X2, int n2, double *out) {
+    launch_gram_tc(x->n, X1, n1, X2, n2, x->h3, x->tcpart, out, x->status, x->st);
+}
+
 // ---------------------------------------------------------------------------
 // the scheme
 // ---------------------------------------------------------------------------
@@ -450,7 +487,7 @@ hq_status phase_a(hq_ctx *x) {
     if (x->z_valid) HQ_TRY(copy_blk<T>(x, W, (const T *)x->Z, cnt));
     else HQ_CUDA(cudaMemsetAsync(W, 0, cnt * sizeof(T), x->st));
     HQ_TRY(pcg<T>(x, U, W, x->cfg.cg_rtol, x->cfg.cg_maxit, nullptr));
-    launch_gram<T>(x->gplan_uw, U, N, W, N, U, N, W, N, x->h3, x->gpart, x->G2, x->st);
+    gram_sym<T>(x, U, N, W, N, x->G2);
     // Msm = -Pwu (rows N..2N-1, columns 0..N-1 of G2); g = || W - U Pwu ||_h
     launch_extract(N, N, -1.0, x->G2 + (size_t)N * 2 * N, 2 * N, x->Msm, N, x->st);
     TallPlan tp = make_tall_plan(x->n, N, N, 0);
@@ -536,8 +573,10 @@ hq_status set_potential_impl(hq_ctx *x, const double *V, int on_device) {
     double s = std::sin(PI / (2.0 * (x->m + 1)));
     double lb = 3.0 * (2.0 / (x->h * x->h)) * s * s + mm[0];
     x->sigma = std::isnan(x->cfg.shift) ? (lb > 0.0 ? 0.0 : 1.0 - lb) : x->cfg.shift;
-    for (int l = 1; l < x->L; l++)
+    for (int l = 1; l < x->L; l++) {
         launch_coarse_potential(x->lev[l - 1].m, x->lev[l - 1].V, x->lev[l].m, x->lev[l].V, x->st);
+        launch_xfer_tables(x->lev[l - 1].m, x->lev[l].m, x->lev[l - 1].tab, x->st);
+    }
     for (int l = 0; l < x->L; l++) {
         Level &v = x->lev[l];
         launch_level_diag(v.n, v.V, x->sigma, v.c, x->cfg.mg_omega, v.D, v.wD, x->st);
@@ -593,8 +632,7 @@ hq_status set_initial_impl(hq_ctx *x, const double *U0, int on_device) {
     HQ_TRY(clear_status(x));
     T *U = (T *)x->U;
     HQ_TRY(load_block<T>(x, U, U0, on_device));
-    GramPlan gp = make_gram_plan(x->n, N, N, true);
-    launch_gram<T>(gp, U, N, nullptr, 0, U, N, nullptr, 0, x->h3, x->gpart, x->Ssm, x->st);
+    gram_sym<T>(x, U, N, (const T *)nullptr, 0, x->Ssm);
     launch_sym_eig(N, x->Ssm, x->eigwork, x->evals, nullptr, x->st);
     launch_inv_sqrt_first(x->evals, x->scal + 1, x->st);
     double lmin = 0;
@@ -764,6 +802,12 @@ hq_status pcg_impl(hq_ctx *x, const void *B, void *X, double rtol, int maxit, in
 }
 template <typename T>
 hq_status gram_impl(hq_ctx *x, const void *A, int Na, const void *B, int Nb, double w, double *out) {
+    if (x->mixed && A == B && Na == Nb) {
+        // symmetric case of a mixed context: the tensor-core path of the step
+        launch_gram_tc(x->n, (const float *)A, Na, nullptr, 0, w, x->tcpart, out, x->status, x->st);
+        HQ_TRY(check_launch(x));
+        return sync_status(x, x->status, "tensor-core Gram");
+    }
     GramPlan gp = make_gram_plan(x->n, Na, Nb, A == B && Na == Nb);
     if (gram_partial_bytes(gp) > gram_partial_bytes(x->gplan_max) &&
         gram_partial_bytes(gp) > gram_partial_bytes(x->gplan_uw))
@@ -780,12 +824,14 @@ hq_status smooth_impl(hq_ctx *x, int l, const void *r, const void *zin, void *zo
 }
 template <typename T>
 hq_status restrict_impl(hq_ctx *x, int l, const void *rf, void *rc) {
-    launch_restrict<T>(x->lev[l + 1].g, x->lev[l].m, (const T *)rf, (T *)rc, x->st);
+    launch_restrict<T>(x->lev[l].m, x->lev[l + 1].m, x->N, x->lev[l].tab, (const T *)rf,
+                       (T *)x->xt1, (T *)x->xt2, (T *)rc, x->st);
     return check_launch(x);
 }
 template <typename T>
 hq_status prolong_impl(hq_ctx *x, int l, const void *ec, const void *efin, void *efout) {
-    launch_prolong<T>(x->lev[l].g, x->lev[l + 1].m, (const T *)ec, (const T *)efin, (T *)efout, x->st);
+    launch_prolong<T>(x->lev[l].m, x->lev[l + 1].m, x->N, x->lev[l].tab, (const T *)ec,
+                      (T *)x->xt1, (T *)x->xt2, (const T *)efin, (T *)efout, x->st);
     return check_launch(x);
 }
 template <typename T>
@@ -1072,19 +1118,24 @@ hq_status hq_mg_level_potential(hq_ctx *x, int level, double *V_out) {
 
 hq_status hq_profile(hq_ctx *x, int timing) {
     HQ_TRY(guard(x));
-    for (int i = 0; i < HQ_K_NCLASS; i++) x->launches[i] = 0;
+    for (int i = 0; i < HQ_K_NCLASS; i++) {
+        x->launches[i] = 0;
+        x->work[i] = 0.0;
+    }
     x->timing = timing != 0;
     x->evused = 0;
     x->evrec.clear();
     return HQ_OK;
 }
 
-hq_status hq_profile_read(hq_ctx *x, long *launches, double *ms) {
+hq_status hq_profile_read(hq_ctx *x, long *launches, double *ms, double *elements) {
     HQ_API_BEGIN
     HQ_TRY(guard(x));
     HQ_CUDA(cudaStreamSynchronize(x->st));
     if (launches)
         for (int i = 0; i < HQ_K_NCLASS; i++) launches[i] = x->launches[i];
+    if (elements)
+        for (int i = 0; i < HQ_K_NCLASS; i++) elements[i] = x->work[i];
     if (ms) {
         for (int i = 0; i < HQ_K_NCLASS; i++) ms[i] = 0.0;
         for (auto &r : x->evrec) {

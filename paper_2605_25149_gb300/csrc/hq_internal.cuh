@@ -13,13 +13,14 @@ namespace hq {
 // launch instrumentation: every kernel launch is bracketed by these hooks,
 // which count launches per class and optionally record CUDA events.
 void hook_before(int cls);
-void hook_after(int cls);
-#define HQ_LAUNCH(cls, ...)          \
-    do {                             \
-        ::hq::hook_before(cls);      \
-        __VA_ARGS__;                 \
-        ::hq::hook_after(cls);       \
+void hook_after(int cls, double work);
+#define HQ_LAUNCH_W(cls, work, ...)                 \
+    do {                                            \
+        ::hq::hook_before(cls);                     \
+        __VA_ARGS__;                                \
+        ::hq::hook_after(cls, (double)(work));      \
     } while (0)
+#define HQ_LAUNCH(cls, ...) HQ_LAUNCH_W(cls, 0, __VA_ARGS__)
 
 // ----------------------------------------------------------------------------
 // launch geometry of the point-major grid kernels
@@ -43,7 +44,7 @@ struct PcgScalars {
     int *status;       // 1 int, sticky error flags (bit 0: breakdown)
 };
 
-enum { ST_BREAKDOWN = 1, ST_SINGULAR = 2, ST_NONFINITE = 4, ST_GJ_FAIL = 8 };
+enum { ST_BREAKDOWN = 1, ST_SINGULAR = 2, ST_NONFINITE = 4, ST_GJ_FAIL = 8, ST_TC_TIMEOUT = 16 };
 
 // ----------------------------------------------------------------------------
 // grid kernels (k_grid.cu); T = double or float
@@ -72,13 +73,29 @@ void launch_jacobi(const GridGeom &g, const T *D, const T *wD, T c, T one_minus_
 // z = wD * r
 template <typename T>
 void launch_jacobi_first(const GridGeom &g, const T *wD, const T *r, T *z, cudaStream_t s);
-// rc = ((mc+1)/(mf+1))^3 P^T rf
+// 1-D transfer tables between grids of mf and mc nodes per side:
+// restriction taps (fine node, weight) per coarse node, XFER_RTAPS each;
+// prolongation taps (coarse node, weight) per fine node, 2 each; index -1 =
+// no tap.  Built once per potential by launch_xfer_tables.
+constexpr int XFER_RTAPS = 6;
+struct XferTab {
+    int *ridx;
+    double *rw;
+    float *rwf;
+    int *pidx;
+    double *pw;
+    float *pwf;
+};
+void launch_xfer_tables(int mf, int mc, const XferTab &t, cudaStream_t s);
+// rc = ((mc+1)/(mf+1))^3 P^T rf, three 1-D passes through tmp1 (mf*mf*mc*N)
+// and tmp2 (mf*mc*mc*N)
 template <typename T>
-void launch_restrict(const GridGeom &gc, int mf, const T *rf, T *rc, cudaStream_t s);
-// ef_out = ef_in + P ec
+void launch_restrict(int mf, int mc, int N, const XferTab &t, const T *rf, T *tmp1, T *tmp2,
+                     T *rc, cudaStream_t s);
+// ef_out = ef_in + P ec, three 1-D passes through tmp2 and tmp1
 template <typename T>
-void launch_prolong(const GridGeom &gf, int mc, const T *ec, const T *efin, T *efout,
-                    cudaStream_t s);
+void launch_prolong(int mf, int mc, int N, const XferTab &t, const T *ec, T *tmp1, T *tmp2,
+                    const T *efin, T *efout, cudaStream_t s);
 // z = Ainv r on the coarsest level (Ainv nc x nc, FP64)
 template <typename T>
 void launch_coarse_solve(const GridGeom &g, const double *Ainv, const T *r, T *z,
@@ -124,6 +141,14 @@ template <typename T>
 void launch_gram(const GramPlan &p, const T *A1, int na1, const T *A2, int na2, const T *B1,
                  int nb1, const T *B2, int nb2, double w, double *partials, double *out,
                  cudaStream_t s);
+
+// Symmetric Gram out = w [X1 X2]^T [X1 X2] of FP32 blocks on tcgen05 tensor
+// cores (kind::tf32, 3xTF32 split, FP32 accumulation in TMEM, FP64 chunk
+// reduction).  partials: gram_tc_partial_bytes(n, n1 + n2) bytes.
+size_t gram_tc_partial_bytes(long n, int na);
+size_t gram_tc_smem_bytes();
+void launch_gram_tc(long n, const float *X1, int n1, const float *X2, int n2, double w,
+                    float *partials, double *out, int *status, cudaStream_t s);
 
 // Out = A1 M1 (+ A2 M2) (+ Cin), M's are FP64 K x Ncol row-major; optional
 // partial sum of squares of Out (one double per CTA, npart entries).

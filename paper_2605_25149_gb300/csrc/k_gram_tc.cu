@@ -1,0 +1,357 @@
+// Inner-product matrices <A,B> = w A^T A of FP32 tall-skinny blocks on the
+// 5th-generation tensor cores (tcgen05, kind::tf32), FP32-accurate by the
+// 3xTF32 split: each FP32 value a = hi + lo with hi = rna_tf32(a) and
+// lo = rna_tf32(a - hi), and A^T A ~ hi^T hi + hi^T lo + lo^T hi (the dropped
+// lo^T lo term is below 2^-22 relative).
+//
+// Work decomposition: the (na x na) symmetric output is cut into 128 x 128
+// tiles (upper triangle only) and the n grid points into chunks; one CTA
+// computes one tile over one chunk, accumulating in TMEM (128 lanes x 128
+// FP32 columns), and writes its partial tile; a second kernel reduces the
+// chunk partials in FP64 in a fixed order (deterministic).
+//
+// Per 32-point K-slice the 128 threads load the tile columns of 32 point rows
+// (coalesced along the columns of the point-major block), split them into
+// tf32 hi/lo and store them K-major with the 128-byte swizzle into a
+// double-buffered shared-memory stage; one thread issues 12 MMAs
+// (4 K-steps of 8 x 3 products, M = N = 128) and commits them to the stage's
+// mbarrier, so the loads of the next slice overlap the MMAs of this one.
+// Every wait is bounded: on expiry the CTA sets an error flag, stops issuing
+// and still releases its TMEM.
+#include "hq_internal.cuh"
+
+#include <algorithm>
+
+namespace hq {
+
+constexpr int TC_T = 128;        // output tile edge (M = N = 128)
+constexpr int TC_K = 32;         // points per slice (128 bytes of tf32 per row)
+constexpr int TC_THREADS = 128;  // 4 warps: each owns 32 TMEM lanes in the epilogue
+constexpr int TC_TILE_BYTES = TC_T * TC_K * 4;   // 16 KB: one operand, one of hi / lo
+constexpr unsigned TC_WAIT_LIMIT = 1u << 28;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm volatile("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// byte offset of element (row r, k) in a 128-row x 32-k K-major tile with the
+// 128-byte swizzle (8-row atoms of 1024 bytes; 16-byte chunk c of row r is
+// stored at chunk c ^ (r & 7)).
+__device__ __forceinline__ uint32_t sw128_offset(int r, int k) {
+    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 2) ^ (r & 7)) & 7) << 4) +
+                      ((k & 3) << 2));
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, SBO = 1024 B
+__device__ __forceinline__ uint64_t make_desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);          // start address
+    d |= (uint64_t)(1) << 16;                         // leading byte offset (unused, swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                           // descriptor version (sm_100 family)
+    d |= (uint64_t)2 << 61;                           // swizzle mode: 128 B
+    return d;
+}
+
+// instruction descriptor: D f32, A/B tf32, both K-major, M = N = 128
+__host__ __device__ constexpr uint32_t idesc_tf32_128x128() {
+    return (1u << 4)                 // D format: F32
+           | (2u << 7)               // A format: TF32
+           | (2u << 10)              // B format: TF32
+           | ((uint32_t)(TC_T >> 3) << 17)   // N / 8
+           | ((uint32_t)(TC_T >> 4) << 24);  // M / 16
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// bounded wait for completion of the phase with the given parity
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+    uint32_t a = smem_u32(bar);
+    for (unsigned it = 0; it < TC_WAIT_LIMIT; it++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+template <int NC>
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[NC]);
+
+template <>
+__device__ __forceinline__ void tmem_ld32<32>(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcPlan {
+    long n;
+    int na, tiles, ntiles, chunks;
+    long chunk_rows;
+};
+
+__device__ __forceinline__ void tc_tile_of(int t, int tiles, int &ta, int &tb) {
+    int r = 0, rem = t;
+    while (rem >= tiles - r) {
+        rem -= tiles - r;
+        r++;
+    }
+    ta = r;
+    tb = r + rem;
+}
+
+__device__ __forceinline__ float tc_gat(const float *X1, int n1, const float *X2, int n2, long p,
+                                        int c) {
+    return c < n1 ? X1[(size_t)p * n1 + c] : X2[(size_t)p * n2 + (c - n1)];
+}
+
+// Stage layout (bytes): [A_hi | A_lo | B_hi | B_lo], 16 KB each, 1024-aligned.
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_gram_tf32x3(TcPlan P, const float *__restrict__ X1, int n1, const float *__restrict__ X2,
+                  int n2, float *__restrict__ partials, int *status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ uint64_t mbar[2];
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int ta, tb;
+    tc_tile_of(blockIdx.x, P.tiles, ta, tb);
+    const bool diag = (ta == tb);
+    const int a0 = ta * TC_T, b0 = tb * TC_T;
+    const long r0 = (long)blockIdx.y * P.chunk_rows;
+    const long r1 = (P.n < r0 + P.chunk_rows) ? P.n : r0 + P.chunk_rows;
+    const int nslices = (int)((r1 - r0 + TC_K - 1) / TC_K);
+
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_sh)),
+                     "r"(TC_T)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sh;
+
+    // each thread loads column-quads of 32 point rows: 32 rows x 128 cols =
+    // 1024 float4; thread t takes float4 index q = t + 128 j (j = 0..7):
+    // row = q / 32, column quad = q % 32.
+    float4 ra[8], rb[8];
+    const bool vec4 = (n1 % 4 == 0) && (n2 % 4 == 0) &&
+                      (((uintptr_t)X1 & 15) == 0) && (X2 == nullptr || ((uintptr_t)X2 & 15) == 0);
+    auto load_slice = [&](int s, float4 (&dst)[8], int c0) {
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            int q = tid + TC_THREADS * j;
+            int row = q >> 5, cq = (q & 31) * 4;
+            long p = r0 + (long)s * TC_K + row;
+            const int c = c0 + cq;
+            if (p < r1 && vec4 && c + 3 < P.na) {
+                const float *src = c < n1 ? X1 + (size_t)p * n1 + c : X2 + (size_t)p * n2 + (c - n1);
+                dst[j] = *reinterpret_cast<const float4 *>(src);
+            } else {
+                float v[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    v[u] = (p < r1 && c + u < P.na) ? tc_gat(X1, n1, X2, n2, p, c + u) : 0.f;
+                dst[j] = make_float4(v[0], v[1], v[2], v[3]);
+            }
+        }
+    };
+    // store: element (point row k, column i) -> K-major tile row i, k
+    auto store_slice = [&](unsigned char *hi, unsigned char *lo, const float4 (&src)[8]) {
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            int q = tid + TC_THREADS * j;
+            int k = q >> 5, cq = (q & 31) * 4;
+            float v[4] = {src[j].x, src[j].y, src[j].z, src[j].w};
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                float h = tf32_rna(v[u]);
+                float l = tf32_rna(v[u] - h);
+                uint32_t off = sw128_offset(cq + u, k);
+                *reinterpret_cast<float *>(hi + off) = h;
+                *reinterpret_cast<float *>(lo + off) = l;
+            }
+        }
+    };
+
+    const uint32_t idesc = idesc_tf32_128x128();
+    if (nslices > 0) {
+        load_slice(0, ra, a0);
+        if (!diag) load_slice(0, rb, b0);
+    }
+    for (int s = 0; s < nslices; s++) {
+        const int st = s & 1;
+        unsigned char *base = smem + st * 4 * TC_TILE_BYTES;
+        unsigned char *Ahi = base, *Alo = base + TC_TILE_BYTES;
+        unsigned char *Bhi = diag ? Ahi : base + 2 * TC_TILE_BYTES;
+        unsigned char *Blo = diag ? Alo : base + 3 * TC_TILE_BYTES;
+        if (s >= 2) {
+            if (!mbar_wait(&mbar[st], (unsigned)(((s - 2) >> 1) & 1))) atomicExch(&abort_sh, 1);
+        }
+        __syncthreads();
+        if (abort_sh) break;
+        store_slice(Ahi, Alo, ra);
+        if (!diag) store_slice(Bhi, Blo, rb);
+        if (s + 1 < nslices) {
+            load_slice(s + 1, ra, a0);
+            if (!diag) load_slice(s + 1, rb, b0);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ahi = smem_u32(Ahi), alo = smem_u32(Alo);
+            const uint32_t bhi = smem_u32(Bhi), blo = smem_u32(Blo);
+#pragma unroll
+            for (int kk = 0; kk < TC_K / 8; kk++) {
+                const uint32_t ko = kk * 32;   // 8 tf32 = 32 bytes along K
+                const uint64_t dah = make_desc_sw128(ahi + ko), dal = make_desc_sw128(alo + ko);
+                const uint64_t dbh = make_desc_sw128(bhi + ko), dbl = make_desc_sw128(blo + ko);
+                mma_tf32(tmem, dah, dbh, idesc, (s > 0 || kk > 0) ? 1u : 0u);
+                mma_tf32(tmem, dah, dbl, idesc, 1u);
+                mma_tf32(tmem, dal, dbh, idesc, 1u);
+            }
+            mma_commit(&mbar[st]);
+        }
+    }
+    // wait for the last two commits (they complete in issue order)
+    bool ok = !abort_sh;
+    if (ok && nslices >= 1) {
+        int s = nslices - 1;
+        ok = mbar_wait(&mbar[s & 1], (unsigned)((s >> 1) & 1));
+        if (ok && nslices >= 2) {
+            s = nslices - 2;
+            ok = mbar_wait(&mbar[s & 1], (unsigned)((s >> 1) & 1));
+        }
+    }
+    if (!ok) atomicExch(&abort_sh, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (abort_sh) {
+        if (tid == 0) atomicOr(status, ST_TC_TIMEOUT);
+    } else if (nslices > 0) {
+        // epilogue: warp w reads TMEM lanes 32w..32w+31 (tile rows), 32 columns at a time
+        float *dst = partials + ((size_t)blockIdx.y * P.ntiles + blockIdx.x) * TC_T * TC_T;
+        const int row = warp * 32 + lane;
+        for (int cb = 0; cb < TC_T; cb += 32) {
+            float v[32];
+            tmem_ld32<32>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+#pragma unroll
+            for (int j = 0; j < 32; j++) dst[(size_t)row * TC_T + cb + j] = v[j];
+        }
+    } else {
+        float *dst = partials + ((size_t)blockIdx.y * P.ntiles + blockIdx.x) * TC_T * TC_T;
+        for (int e = tid; e < TC_T * TC_T; e += TC_THREADS) dst[e] = 0.f;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_T)
+                     : "memory");
+}
+
+__global__ void k_gram_tc_reduce(TcPlan P, const float *partials, double w, double *out) {
+    const int tile = blockIdx.x;
+    int ta, tb;
+    tc_tile_of(tile, P.tiles, ta, tb);
+    for (int e = threadIdx.x; e < TC_T * TC_T; e += blockDim.x) {
+        int la = e / TC_T, lb = e % TC_T;
+        int a = ta * TC_T + la, b = tb * TC_T + lb;
+        if (a >= P.na || b >= P.na) continue;
+        // within a diagonal tile the MMA accumulates (i,j) and (j,i) in
+        // different orders: keep the upper entry and mirror it
+        if (ta == tb && la > lb) continue;
+        double s = 0.0;
+        for (int c = 0; c < P.chunks; c++)
+            s += (double)partials[((size_t)c * P.ntiles + tile) * TC_T * TC_T + e];
+        s *= w;
+        out[(size_t)a * P.na + b] = s;
+        if (a != b) out[(size_t)b * P.na + a] = s;
+    }
+}
+
+TcPlan make_tc_plan(long n, int na) {
+    TcPlan p;
+    p.n = n;
+    p.na = na;
+    p.tiles = (na + TC_T - 1) / TC_T;
+    p.ntiles = p.tiles * (p.tiles + 1) / 2;
+    long target = std::max(1L, (long)(2 * 152) / p.ntiles);
+    long maxchunks = std::max(1L, (n + 4 * TC_K - 1) / (4 * TC_K));
+    long chunks = std::min(target, maxchunks);
+    long rows = (n + chunks - 1) / chunks;
+    rows = (rows + TC_K - 1) / TC_K * TC_K;
+    p.chunk_rows = rows;
+    p.chunks = (int)((n + rows - 1) / rows);
+    return p;
+}
+
+size_t gram_tc_partial_bytes(long n, int na) {
+    TcPlan p = make_tc_plan(n, na);
+    return sizeof(float) * (size_t)p.chunks * p.ntiles * TC_T * TC_T;
+}
+
+size_t gram_tc_smem_bytes() { return 2 * 4 * TC_TILE_BYTES + 1024; }
+
+void launch_gram_tc(long n, const float *X1, int n1, const float *X2, int n2, double w,
+                    float *partials, double *out, int *status, cudaStream_t s) {
+    TcPlan p = make_tc_plan(n, n1 + n2);
+    const int smem = (int)gram_tc_smem_bytes();
+    cudaFuncSetAttribute(k_gram_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    HQ_LAUNCH(HQ_K_GRAM, k_gram_tf32x3<<<dim3(p.ntiles, p.chunks), TC_THREADS, smem, s>>>(
+                             p, X1, n1, X2, n2, partials, status));
+    HQ_LAUNCH(HQ_K_GRAM, k_gram_tc_reduce<<<p.ntiles, 256, 0, s>>>(p, partials, w, out));
+}
+
+}  // namespace hq

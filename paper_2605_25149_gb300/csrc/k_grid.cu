@@ -284,133 +284,118 @@ __global__ void __launch_bounds__(256) k_dot(long n, int N, int ppt, const T *__
 
 // ---------------------------------------------------------------------------
 // Transfer operators between a grid of mf and one of mc nodes per side on the
-// same box.  Fine node f (1-based) has coarse coordinate f (mc+1)/(mf+1);
-// every weight is a ratio of two integers, so both sides of any comparison
-// obtain the same doubles.
+// same box.  Fine node f (1-based) has coarse coordinate f (mc+1)/(mf+1); the
+// 1-D hat weight of coarse node c for fine node f is
+//   w(f, c) = (den - |f (mc+1) - c den|) / den,  den = mf + 1,
+// a ratio of two integers, so every implementation obtains the same doubles.
+// P = Pz (x) Py (x) Px and R = ((mc+1)/(mf+1))^3 P^T are tensor products, so
+// both are applied as three 1-D passes (x, y, z), each reading its weights
+// from small per-level tables built once per potential.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double hat_weight(int f, int c1, int mf, int mc) {
-    long den = mf + 1;
-    long num = (long)f * (mc + 1) - (long)c1 * den;
-    long a = num < 0 ? -num : num;
-    return a < den ? (double)(den - a) / (double)den : 0.0;
-}
-
-// 1-D list of fine nodes (1-based) feeding coarse node c1, with weights
-__device__ __forceinline__ int restrict_list(int c1, int mf, int mc, int *fi, double *fw) {
-    long den = mf + 1, mcp = mc + 1;
-    long lo = ((long)(c1 - 1) * den) / mcp;
-    long hi = ((long)(c1 + 1) * den + mcp - 1) / mcp;
-    if (lo < 1) lo = 1;
-    if (hi > mf) hi = mf;
-    int cnt = 0;
-    for (long f = lo; f <= hi && cnt < 8; f++) {
-        double w = hat_weight((int)f, c1, mf, mc);
-        if (w > 0.0) {
-            fi[cnt] = (int)f;
-            fw[cnt] = w;
-            cnt++;
-        }
-    }
-    return cnt;
-}
-
-template <typename T, int V>
-__global__ void __launch_bounds__(256) k_restrict(int mc, long nc, int N, int ppt, int mf,
-                                                  double scale, const T *__restrict__ rf,
-                                                  T *__restrict__ rc) {
-    const int TY = blockDim.y;
-    const int col = (blockIdx.x * blockDim.x + threadIdx.x) * V;
-    if (col >= N) return;
-    const long base = (long)blockIdx.y * TY * ppt;
-    for (int k = 0; k < ppt; k++) {
-        long p = base + (long)k * TY + threadIdx.y;
-        if (p >= nc) continue;
-        int ci = (int)(p % mc);
-        long q = p / mc;
-        int cj = (int)(q % mc);
-        int ck = (int)(q / mc);
-        int fx[8], fy[8], fz[8];
-        double wx[8], wy[8], wz[8];
-        int nx = restrict_list(ci + 1, mf, mc, fx, wx);
-        int ny = restrict_list(cj + 1, mf, mc, fy, wy);
-        int nz = restrict_list(ck + 1, mf, mc, fz, wz);
-        T acc[V];
-#pragma unroll
-        for (int v = 0; v < V; v++) acc[v] = T(0);
-        for (int c = 0; c < nz; c++)
-            for (int b = 0; b < ny; b++) {
-                double wzy = wz[c] * wy[b];
-                size_t rowbase = ((size_t)(fz[c] - 1) * mf + (fy[b] - 1)) * mf;
-                for (int a = 0; a < nx; a++) {
-                    T w = (T)(wzy * wx[a]);
-                    VT<T, V> rv = ldv<T, V>(rf + (rowbase + fx[a] - 1) * N + col);
-#pragma unroll
-                    for (int v = 0; v < V; v++) acc[v] += w * rv.v[v];
-                }
-            }
-        VT<T, V> o;
-#pragma unroll
-        for (int v = 0; v < V; v++) o.v[v] = (T)scale * acc[v];
-        stv<T, V>(rc + (size_t)p * N + col, o);
-    }
-}
-
-template <typename T, int V>
-__global__ void __launch_bounds__(256) k_prolong(int mf, long nf, int N, int ppt, int mc,
-                                                 const T *__restrict__ ec,
-                                                 const T *__restrict__ efin,
-                                                 T *__restrict__ efout) {
-    const int TY = blockDim.y;
-    const int col = (blockIdx.x * blockDim.x + threadIdx.x) * V;
-    if (col >= N) return;
+__global__ void k_xfer_tables(int mf, int mc, int *ridx, double *rw, float *rwf, int *pidx,
+                              double *pw, float *pwf) {
     const long den = mf + 1, mcp = mc + 1;
+    for (int c = threadIdx.x; c < mc; c += blockDim.x) {
+        const int c1 = c + 1;
+        long lo = ((long)(c1 - 1) * den) / mcp, hi = ((long)(c1 + 1) * den + mcp - 1) / mcp;
+        if (lo < 1) lo = 1;
+        if (hi > mf) hi = mf;
+        int cnt = 0;
+        for (long f = lo; f <= hi && cnt < XFER_RTAPS; f++) {
+            long a = f * mcp - (long)c1 * den;
+            if (a < 0) a = -a;
+            if (a < den) {
+                double w = (double)(den - a) / (double)den;
+                ridx[c * XFER_RTAPS + cnt] = (int)(f - 1);
+                rw[c * XFER_RTAPS + cnt] = w;
+                rwf[c * XFER_RTAPS + cnt] = (float)w;
+                cnt++;
+            }
+        }
+        for (; cnt < XFER_RTAPS; cnt++) {
+            ridx[c * XFER_RTAPS + cnt] = -1;
+            rw[c * XFER_RTAPS + cnt] = 0.0;
+            rwf[c * XFER_RTAPS + cnt] = 0.f;
+        }
+    }
+    for (int f = threadIdx.x; f < mf; f += blockDim.x) {
+        const long num = (long)(f + 1) * mcp;
+        const int s0 = (int)(num / den);
+        const long rem = num % den;
+        const double w1 = (double)rem / (double)den, w0 = (double)(den - rem) / (double)den;
+        const int c0 = s0, c1 = s0 + 1;   // 1-based coarse nodes
+        const bool v0 = c0 >= 1 && c0 <= mc && w0 > 0.0, v1 = c1 >= 1 && c1 <= mc && w1 > 0.0;
+        pidx[f * 2] = v0 ? c0 - 1 : -1;
+        pw[f * 2] = v0 ? w0 : 0.0;
+        pwf[f * 2] = v0 ? (float)w0 : 0.f;
+        pidx[f * 2 + 1] = v1 ? c1 - 1 : -1;
+        pw[f * 2 + 1] = v1 ? w1 : 0.0;
+        pwf[f * 2 + 1] = v1 ? (float)w1 : 0.f;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ const T *wsel(const double *wd, const float *wf);
+template <>
+__device__ __forceinline__ const double *wsel<double>(const double *wd, const float *) { return wd; }
+template <>
+__device__ __forceinline__ const float *wsel<float>(const double *, const float *wf) { return wf; }
+
+// One 1-D pass along `axis` (0 = x, fastest; 1 = y; 2 = z).  Output dims
+// (o2, o1, o0), input dims equal except along the axis (ilen).  Output index
+// o along the axis takes taps idx[o*NT + t] (input index, -1 = none) with
+// weights w[o*NT + t]:  out = scale * sum_t w in (+ add).
+template <typename T, int V, int NT>
+__global__ void __launch_bounds__(256) k_axis_pass(int o2, int o1, int o0, int ilen, int axis,
+                                                   int N, int ppt, const int *__restrict__ idx,
+                                                   const double *__restrict__ wd,
+                                                   const float *__restrict__ wf, T scale,
+                                                   const T *__restrict__ in,
+                                                   const T *__restrict__ add,
+                                                   T *__restrict__ out) {
+    const int TY = blockDim.y;
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    if (col >= N) return;
+    const T *w = wsel<T>(wd, wf);
+    const long nout = (long)o2 * o1 * o0;
+    const int d0 = axis == 0 ? ilen : o0;
+    const int d1 = axis == 1 ? ilen : o1;
+    const size_t s0 = (size_t)N, s1 = (size_t)d0 * N, s2 = (size_t)d1 * d0 * N;
+    const size_t sa = axis == 0 ? s0 : (axis == 1 ? s1 : s2);
     const long base = (long)blockIdx.y * TY * ppt;
     for (int k = 0; k < ppt; k++) {
         long p = base + (long)k * TY + threadIdx.y;
-        if (p >= nf) continue;
-        int f[3];
-        f[0] = (int)(p % mf) + 1;
-        long q = p / mf;
-        f[1] = (int)(q % mf) + 1;
-        f[2] = (int)(q / mf) + 1;
-        int s0[3];
-        double w[3][2];
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-            long num = (long)f[d] * mcp;
-            s0[d] = (int)(num / den);
-            long rem = num % den;
-            w[d][1] = (double)rem / (double)den;
-            w[d][0] = (double)(den - rem) / (double)den;
-        }
-        size_t e = (size_t)p * N + col;
-        VT<T, V> o = ldv<T, V>(efin + e);
+        if (p >= nout) continue;
+        const int i0 = (int)(p % o0);
+        const long q = p / o0;
+        const int i1 = (int)(q % o1);
+        const int i2 = (int)(q / o1);
+        const int oa = axis == 0 ? i0 : (axis == 1 ? i1 : i2);
+        const size_t ib = (axis == 0 ? 0 : (size_t)i0 * s0) + (axis == 1 ? 0 : (size_t)i1 * s1) +
+                          (axis == 2 ? 0 : (size_t)i2 * s2) + col;
         T acc[V];
 #pragma unroll
         for (int v = 0; v < V; v++) acc[v] = T(0);
 #pragma unroll
-        for (int cz = 0; cz < 2; cz++) {
-            int kz = s0[2] + cz;
-            if (kz < 1 || kz > mc || w[2][cz] == 0.0) continue;
+        for (int t = 0; t < NT; t++) {
+            const int ii = idx[oa * NT + t];
+            if (ii < 0) continue;
+            const T wt = w[oa * NT + t];
+            VT<T, V> a = ldv<T, V>(in + ib + (size_t)ii * sa);
 #pragma unroll
-            for (int cy = 0; cy < 2; cy++) {
-                int ky = s0[1] + cy;
-                if (ky < 1 || ky > mc || w[1][cy] == 0.0) continue;
-#pragma unroll
-                for (int cx = 0; cx < 2; cx++) {
-                    int kx = s0[0] + cx;
-                    if (kx < 1 || kx > mc || w[0][cx] == 0.0) continue;
-                    T wt = (T)(w[0][cx] * w[1][cy] * w[2][cz]);
-                    size_t ce = (((size_t)(kz - 1) * mc + (ky - 1)) * mc + (kx - 1)) * N + col;
-                    VT<T, V> ev = ldv<T, V>(ec + ce);
-#pragma unroll
-                    for (int v = 0; v < V; v++) acc[v] += wt * ev.v[v];
-                }
-            }
+            for (int v = 0; v < V; v++) acc[v] += wt * a.v[v];
         }
+        const size_t oe = (size_t)p * N + col;
+        VT<T, V> o;
+        if (add) {
+            VT<T, V> a = ldv<T, V>(add + oe);
 #pragma unroll
-        for (int v = 0; v < V; v++) o.v[v] = o.v[v] + acc[v];
-        stv<T, V>(efout + e, o);
+            for (int v = 0; v < V; v++) o.v[v] = a.v[v] + scale * acc[v];
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; v++) o.v[v] = scale * acc[v];
+        }
+        stv<T, V>(out + oe, o);
     }
 }
 
@@ -678,7 +663,7 @@ static inline dim3 grd(const GridGeom &g) { return dim3(g.gx, g.gy); }
 template <typename T, int V>
 static void run_apply(const GridGeom &g, const T *D, T c, const T *x, T *y, double *part,
                       cudaStream_t s) {
-    HQ_LAUNCH(HQ_K_STENCIL, k_stencil<T, V, 0><<<grd(g), blk(g), 0, s>>>(g.m, g.n, g.N, g.ppt, D, c, x, nullptr, y,
+    HQ_LAUNCH_W(HQ_K_STENCIL, (double)g.n * g.N, k_stencil<T, V, 0><<<grd(g), blk(g), 0, s>>>(g.m, g.n, g.N, g.ppt, D, c, x, nullptr, y,
                                                   part, nullptr));
 }
 template <typename T>
@@ -690,7 +675,7 @@ void launch_apply(const GridGeom &g, const T *D, T c, const T *x, T *y, double *
 template <typename T, int V>
 static void run_resid(const GridGeom &g, const T *D, T c, const T *x, const T *b, T *y,
                       double *p1, double *p2, cudaStream_t s) {
-    HQ_LAUNCH(HQ_K_STENCIL, k_stencil<T, V, 1><<<grd(g), blk(g), 0, s>>>(g.m, g.n, g.N, g.ppt, D, c, x, b, y, p1, p2));
+    HQ_LAUNCH_W(HQ_K_RESIDUAL, (double)g.n * g.N, k_stencil<T, V, 1><<<grd(g), blk(g), 0, s>>>(g.m, g.n, g.N, g.ppt, D, c, x, b, y, p1, p2));
 }
 template <typename T>
 void launch_resid(const GridGeom &g, const T *D, T c, const T *x, const T *b, T *y,
@@ -701,7 +686,7 @@ void launch_resid(const GridGeom &g, const T *D, T c, const T *x, const T *b, T 
 template <typename T, int V>
 static void run_pcg_xr(const GridGeom &g, const double *alpha, const T *p, const T *q, T *x,
                        T *r, double *part, const T *wD, T *zf, cudaStream_t s) {
-    HQ_LAUNCH(HQ_K_VECTOR, k_pcg_xr<T, V><<<grd(g), blk(g), 0, s>>>(g.m, g.n, g.N, g.ppt, alpha, p, q, x, r, part, wD,
+    HQ_LAUNCH_W(HQ_K_VECTOR, (double)g.n * g.N, k_pcg_xr<T, V><<<grd(g), blk(g), 0, s>>>(g.m, g.n, g.N, g.ppt, alpha, p, q, x, r, part, wD,
                                              zf));
 }
 template <typename T>
@@ -712,7 +697,7 @@ void launch_pcg_xr(const GridGeom &g, const double *alpha, const T *p, const T *
 
 template <typename T, int V>
 static void run_pcg_p(const GridGeom &g, const double *beta, const T *z, T *p, cudaStream_t s) {
-    HQ_LAUNCH(HQ_K_VECTOR, k_pcg_p<T, V><<<grd(g), blk(g), 0, s>>>(g.n, g.N, g.ppt, beta, z, p));
+    HQ_LAUNCH_W(HQ_K_VECTOR, (double)g.n * g.N, k_pcg_p<T, V><<<grd(g), blk(g), 0, s>>>(g.n, g.N, g.ppt, beta, z, p));
 }
 template <typename T>
 void launch_pcg_p(const GridGeom &g, const double *beta, const T *z, T *p, cudaStream_t s) {
@@ -722,7 +707,7 @@ void launch_pcg_p(const GridGeom &g, const double *beta, const T *z, T *p, cudaS
 template <typename T, int V>
 static void run_jacobi(const GridGeom &g, const T *wD, T c, T omw, const T *r, const T *zin,
                        T *zout, double *part, cudaStream_t s) {
-    HQ_LAUNCH(HQ_K_SMOOTH, k_jacobi<T, V><<<grd(g), blk(g), 0, s>>>(g.m, g.n, g.N, g.ppt, wD, c, omw, r, zin, zout,
+    HQ_LAUNCH_W(HQ_K_SMOOTH, (double)g.n * g.N, k_jacobi<T, V><<<grd(g), blk(g), 0, s>>>(g.m, g.n, g.N, g.ppt, wD, c, omw, r, zin, zout,
                                              part));
 }
 template <typename T>
@@ -734,39 +719,74 @@ void launch_jacobi(const GridGeom &g, const T *D, const T *wD, T c, T omw, const
 
 template <typename T, int V>
 static void run_jacobi_first(const GridGeom &g, const T *wD, const T *r, T *z, cudaStream_t s) {
-    HQ_LAUNCH(HQ_K_SMOOTH, k_jacobi_first<T, V><<<grd(g), blk(g), 0, s>>>(g.n, g.N, g.ppt, wD, r, z));
+    HQ_LAUNCH_W(HQ_K_VECTOR, (double)g.n * g.N, k_jacobi_first<T, V><<<grd(g), blk(g), 0, s>>>(g.n, g.N, g.ppt, wD, r, z));
 }
 template <typename T>
 void launch_jacobi_first(const GridGeom &g, const T *wD, const T *r, T *z, cudaStream_t s) {
     HQ_VEC_DISPATCH(T, g, run_jacobi_first, g, wD, r, z, s);
 }
 
-template <typename T, int V>
-static void run_restrict(const GridGeom &gc, int mf, const T *rf, T *rc, cudaStream_t s) {
-    double q = (double)(gc.m + 1) / (double)(mf + 1);
-    HQ_LAUNCH(HQ_K_TRANSFER, k_restrict<T, V><<<grd(gc), blk(gc), 0, s>>>(gc.m, gc.n, gc.N, gc.ppt, mf, q * q * q, rf,
-                                                 rc));
-}
-template <typename T>
-void launch_restrict(const GridGeom &gc, int mf, const T *rf, T *rc, cudaStream_t s) {
-    HQ_VEC_DISPATCH(T, gc, run_restrict, gc, mf, rf, rc, s);
+GridGeom make_geom_pts(long npts, int N, int elem_bytes) {
+    GridGeom g = make_geom(1, N, elem_bytes);
+    g.m = 0;
+    g.n = npts;
+    long target_gy = std::max(1L, 152L * 16 / g.gx);
+    long ppt = (npts + (long)g.ty * target_gy - 1) / ((long)g.ty * target_gy);
+    g.ppt = (int)std::max(1L, ppt);
+    g.gy = (int)((npts + (long)g.ty * g.ppt - 1) / ((long)g.ty * g.ppt));
+    return g;
 }
 
-template <typename T, int V>
-static void run_prolong(const GridGeom &gf, int mc, const T *ec, const T *efin, T *efout,
-                        cudaStream_t s) {
-    HQ_LAUNCH(HQ_K_TRANSFER, k_prolong<T, V><<<grd(gf), blk(gf), 0, s>>>(gf.m, gf.n, gf.N, gf.ppt, mc, ec, efin, efout));
+template <typename T, int V, int NT>
+static void run_axis(const GridGeom &g, int o2, int o1, int o0, int ilen, int axis,
+                     const int *idx, const double *wd, const float *wf, T scale, const T *in,
+                     const T *add, T *out, cudaStream_t s) {
+    HQ_LAUNCH_W(HQ_K_TRANSFER, (double)g.n * g.N,
+                k_axis_pass<T, V, NT><<<grd(g), blk(g), 0, s>>>(o2, o1, o0, ilen, axis, g.N, g.ppt,
+                                                                idx, wd, wf, scale, in, add, out));
 }
+
+template <typename T, int NT>
+static void axis_pass(int o2, int o1, int o0, int ilen, int axis, int N, const int *idx,
+                      const double *wd, const float *wf, T scale, const T *in, const T *add, T *out,
+                      cudaStream_t s) {
+    GridGeom g = make_geom_pts((long)o2 * o1 * o0, N, (int)sizeof(T));
+    if (g.vec == 4) run_axis<T, (sizeof(T) == 4 ? 4 : 2), NT>(g, o2, o1, o0, ilen, axis, idx, wd, wf, scale, in, add, out, s);
+    else if (g.vec == 2) run_axis<T, 2, NT>(g, o2, o1, o0, ilen, axis, idx, wd, wf, scale, in, add, out, s);
+    else run_axis<T, 1, NT>(g, o2, o1, o0, ilen, axis, idx, wd, wf, scale, in, add, out, s);
+}
+
+void launch_xfer_tables(int mf, int mc, const XferTab &t, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_SETUP, k_xfer_tables<<<1, 256, 0, s>>>(mf, mc, t.ridx, t.rw, t.rwf, t.pidx,
+                                                           t.pw, t.pwf));
+}
+
+// rc = ((mc+1)/(mf+1))^3 (Rz Ry Rx) rf : x pass (mf,mf,mf)->(mf,mf,mc),
+// y pass ->(mf,mc,mc), z pass (scaled) ->(mc,mc,mc)
 template <typename T>
-void launch_prolong(const GridGeom &gf, int mc, const T *ec, const T *efin, T *efout,
-                    cudaStream_t s) {
-    HQ_VEC_DISPATCH(T, gf, run_prolong, gf, mc, ec, efin, efout, s);
+void launch_restrict(int mf, int mc, int N, const XferTab &t, const T *rf, T *tmp1, T *tmp2,
+                     T *rc, cudaStream_t s) {
+    const double q = (double)(mc + 1) / (double)(mf + 1);
+    axis_pass<T, XFER_RTAPS>(mf, mf, mc, mf, 0, N, t.ridx, t.rw, t.rwf, T(1), rf, nullptr, tmp1, s);
+    axis_pass<T, XFER_RTAPS>(mf, mc, mc, mf, 1, N, t.ridx, t.rw, t.rwf, T(1), tmp1, nullptr, tmp2, s);
+    axis_pass<T, XFER_RTAPS>(mc, mc, mc, mf, 2, N, t.ridx, t.rw, t.rwf, (T)(q * q * q), tmp2,
+                             nullptr, rc, s);
+}
+
+// ef_out = ef_in + (Pz Py Px) ec : z pass (mc,mc,mc)->(mf,mc,mc), y pass
+// ->(mf,mf,mc), x pass with the add ->(mf,mf,mf)
+template <typename T>
+void launch_prolong(int mf, int mc, int N, const XferTab &t, const T *ec, T *tmp1, T *tmp2,
+                    const T *efin, T *efout, cudaStream_t s) {
+    axis_pass<T, 2>(mf, mc, mc, mc, 2, N, t.pidx, t.pw, t.pwf, T(1), ec, nullptr, tmp2, s);
+    axis_pass<T, 2>(mf, mf, mc, mc, 1, N, t.pidx, t.pw, t.pwf, T(1), tmp2, nullptr, tmp1, s);
+    axis_pass<T, 2>(mf, mf, mf, mc, 0, N, t.pidx, t.pw, t.pwf, T(1), tmp1, efin, efout, s);
 }
 
 template <typename T, int V>
 static void run_coarse_solve(const GridGeom &g, const double *Ainv, const T *r, T *z,
                              cudaStream_t s) {
-    HQ_LAUNCH(HQ_K_COARSE, k_coarse_solve<T, V><<<grd(g), blk(g), 0, s>>>(g.n, g.N, g.ppt, Ainv, r, z));
+    HQ_LAUNCH_W(HQ_K_COARSE, (double)g.n * g.N, k_coarse_solve<T, V><<<grd(g), blk(g), 0, s>>>(g.n, g.N, g.ppt, Ainv, r, z));
 }
 template <typename T>
 void launch_coarse_solve(const GridGeom &g, const double *Ainv, const T *r, T *z,
@@ -776,7 +796,7 @@ void launch_coarse_solve(const GridGeom &g, const double *Ainv, const T *r, T *z
 
 template <typename T, int V>
 static void run_dot(const GridGeom &g, const T *x, const T *y, double *part, cudaStream_t s) {
-    HQ_LAUNCH(HQ_K_VECTOR, k_dot<T, V><<<grd(g), blk(g), 0, s>>>(g.n, g.N, g.ppt, x, y, part));
+    HQ_LAUNCH_W(HQ_K_VECTOR, (double)g.n * g.N, k_dot<T, V><<<grd(g), blk(g), 0, s>>>(g.n, g.N, g.ppt, x, y, part));
 }
 template <typename T>
 void launch_dot(const GridGeom &g, const T *x, const T *y, double *part, cudaStream_t s) {
@@ -837,9 +857,10 @@ void launch_scale(size_t count, const double *factor, T *x, cudaStream_t s) {
                                    const T *, T *, double *, cudaStream_t);                  \
     template void launch_jacobi_first<T>(const GridGeom &, const T *, const T *, T *,         \
                                          cudaStream_t);                                      \
-    template void launch_restrict<T>(const GridGeom &, int, const T *, T *, cudaStream_t);    \
-    template void launch_prolong<T>(const GridGeom &, int, const T *, const T *, T *,         \
-                                    cudaStream_t);                                           \
+    template void launch_restrict<T>(int, int, int, const XferTab &, const T *, T *, T *, T *, \
+                                     cudaStream_t);                                          \
+    template void launch_prolong<T>(int, int, int, const XferTab &, const T *, T *, T *,      \
+                                    const T *, T *, cudaStream_t);                           \
     template void launch_coarse_solve<T>(const GridGeom &, const double *, const T *, T *,    \
                                          cudaStream_t);                                      \
     template void launch_dot<T>(const GridGeom &, const T *, const T *, double *,             \

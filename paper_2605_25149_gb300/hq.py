@@ -37,7 +37,7 @@ EXPORTED = [
     "hq_mg_level_potential", "hq_profile", "hq_profile_read", "hq_last_error",
     "hq_status_string", "hq_destroy",
 ]
-KERNEL_CLASSES = ["stencil", "smooth", "transfer", "coarse", "vector", "reduce", "gram",
+KERNEL_CLASSES = ["stencil", "residual", "smooth", "transfer", "coarse", "vector", "reduce", "gram",
                   "blockgemm", "small", "setup"]
 
 
@@ -96,7 +96,7 @@ def load():
         "hq_mg_coarse_solve": (_I, [_P, _P, _P]),
         "hq_mg_level_potential": (_I, [_P, _I, _P]),
         "hq_profile": (_I, [_P, _I]),
-        "hq_profile_read": (_I, [_P, _P, _P]),
+        "hq_profile_read": (_I, [_P, _P, _P, _P]),
         "hq_last_error": (ctypes.c_char_p, [_P]),
         "hq_status_string": (ctypes.c_char_p, [_I]),
         "hq_destroy": (None, [_P]),
@@ -311,12 +311,13 @@ class Solver:
         self._check(self.lib.hq_profile(self._ctx, 1 if timing else 0), "hq_profile")
 
     def profile_read(self):
-        """{class: (launches, ms)} since the last profile() call."""
+        """{class: (launches, ms, point-columns)} since the last profile() call."""
         n = len(KERNEL_CLASSES)
         la = (ctypes.c_long * n)()
         ms = (ctypes.c_double * n)()
-        self._check(self.lib.hq_profile_read(self._ctx, la, ms), "hq_profile_read")
-        return {k: (la[i], ms[i]) for i, k in enumerate(KERNEL_CLASSES)}
+        el = (ctypes.c_double * n)()
+        self._check(self.lib.hq_profile_read(self._ctx, la, ms, el), "hq_profile_read")
+        return {k: (la[i], ms[i], el[i]) for i, k in enumerate(KERNEL_CLASSES)}
 
     def levels(self):
         return self.info()["levels"]

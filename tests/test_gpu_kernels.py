@@ -105,3 +105,39 @@ def test_determinism_bitwise():
         s.step(2)
         outs.append(s.get_state()[0])
     np.testing.assert_array_equal(outs[0], outs[1])
+
+
+# ---------------------------------------------------------------------------
+# mixed precision (FP32 blocks, tcgen05 3xTF32 Gram)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("m,N,Na", [(16, 4, 8), (16, 32, 64), (17, 65, 130), (24, 128, 256)])
+def test_tensor_core_gram_matches_oracle(m, N, Na):
+    """Symmetric Gram of an FP32 block on tcgen05 (kind::tf32, 3xTF32 split):
+    relative error at FP32 level against the FP64 oracle of the same data."""
+    torch = torch_mod()
+    s, V, _ = make(m, N, precision="mixed", cg_rtol=1e-6)
+    rng = np.random.default_rng(Na)
+    A = rng.standard_normal((m ** 3, Na)).astype(np.float32)
+    w = inputs.grid_h(m) ** 3
+    Ad = dev(A)
+    out = host(s.gram(Ad, Ad, w))          # same tensor twice: the tensor-core path
+    ref = O.gram(A.astype(np.float64), A.astype(np.float64), w)
+    err = np.abs(out - ref).max() / np.abs(ref).max()
+    assert err < 2e-6, err
+    np.testing.assert_array_equal(out, out.T)
+    # a second call is bit-identical (fixed-order reduction)
+    np.testing.assert_array_equal(host(s.gram(Ad, Ad, w)), out)
+
+
+@pytest.mark.parametrize("m,N", [(8, 3), (16, 8)])
+def test_mixed_operator_and_vcycle_match_oracle(m, N):
+    s, V, _ = make(m, N, precision="mixed", cg_rtol=1e-6)
+    torch = torch_mod()
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((m ** 3, N)).astype(np.float32)
+    Y = host(s.apply_operator(dev(X)))
+    Yo = O.apply_h(m, inputs.grid_h(m), V, s.info()["sigma"], X.astype(np.float64))
+    assert rel(Y, Yo) < 1e-6
+    mg = oracle_mg(s, V)
+    Z = host(s.mg_vcycle(dev(X)))
+    assert rel(Z, mg.vcycle(X.astype(np.float64))) < 1e-5

@@ -128,3 +128,27 @@ def test_solve_reports_not_converged_and_keeps_state():
     steps, g = s.solve(1e-12, 3, raise_on_unconverged=False)
     assert steps == 3 and g > 1e-12
     s.step(1)
+
+
+def test_mixed_step_tracks_fp64_oracle():
+    m, N, tau = 12, 6, 0.4
+    s, V, U0 = make(m, N, precision="mixed", tau=tau, cg_rtol=1e-7, cg_maxit=400)
+    sigma = s.info()["sigma"]
+    Ug0 = s.get_state()[0]
+    tr = s.step_trace()
+    o = O.scheme_step(m, V, sigma, Ug0, tau)
+    assert rel(host(tr["gram"]), o["gram"]) < 1e-5
+    assert rel(host(tr["Unew"]), o["Unew"]) < 1e-5
+
+
+def test_mixed_solve_eigenvalues_within_1e6_of_fp64():
+    """Mixed precision run to its FP32 floor, then FP64 Rayleigh-Ritz: on the
+    16^3 harmonic grid with N = 10 (three complete shells plus the ground
+    state) the eigenvalues agree with the closed-form 1D sums to 1e-6."""
+    m, N, tau = 16, 10, 0.5
+    s, V, U0 = make(m, N, potential="harmonic", precision="mixed", tau=tau, cg_rtol=1e-6)
+    steps, g = s.solve(2e-5, 5000, raise_on_unconverged=False)
+    ev = s.eigenpairs()
+    lam = separable_levels(m, -6.0, 6.0, N)
+    err = np.abs(ev["lam_rr"] - lam) / np.abs(lam)
+    assert err.max() < 1e-6, (err, steps, g)
