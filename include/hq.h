@@ -183,6 +183,29 @@ hq_status hq_mg_coarse_solve(hq_ctx *ctx, const void *r, void *z);
 /* Level-l potential (n_l values, FP64, device). */
 hq_status hq_mg_level_potential(hq_ctx *ctx, int level, double *V_out);
 
+/* ---- allocation-free variant ----
+ * hq_gram_static: out = w A^T B (Na x Nb, row-major, FP64, device) for
+ * point-major FP64 device blocks A (n x Na) and B (n x Nb), with no context
+ * and no workspace.  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory -- code that runs inside a
+ * stream capture whose allocation policy forbids cudaMalloc, plugin hosts
+ * that only hand out pre-registered buffers, and real-time loops that must
+ * not allocate after start-up.  Its split-K partial sums live in one fixed
+ * file-scope device array of 2^19 doubles (4 MiB) that every GPU which loads
+ * this library keeps until the process exits; it calls no cudaMalloc,
+ * cudaFree or allocating library routine.
+ * Limits: 1 <= Na, Nb <= 512, n >= 1; anything else returns HQ_ERR_ARG.
+ * The first call on each device (with that device current) looks up the
+ * array's device address; make that first call before any stream capture.
+ * All calls share the one array, which keeps the previous call's contents
+ * (every partial is written before it is read, so nothing needs clearing):
+ * calls that can overlap on the GPU -- on different streams, or from
+ * different host threads -- race and must be serialised by the caller.
+ * cuda_stream: a cudaStream_t (NULL = default stream); the call is
+ * asynchronous on it.  Returns HQ_ERR_CUDA on a runtime error.             */
+hq_status hq_gram_static(const double *A, int Na, const double *B, int Nb, long n, double w,
+                         double *out, void *cuda_stream);
+
 /* ---- instrumentation ---- */
 /* Kernel classes counted by the launch counters. */
 typedef enum {

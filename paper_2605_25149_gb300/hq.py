@@ -34,7 +34,7 @@ EXPORTED = [
     "hq_step", "hq_solve", "hq_eigenpairs", "hq_get_state", "hq_set_state", "hq_problem_info",
     "hq_apply_operator", "hq_mg_vcycle", "hq_block_pcg", "hq_gram", "hq_step_trace",
     "hq_mg_smooth", "hq_mg_restrict", "hq_mg_prolong", "hq_mg_coarse_solve",
-    "hq_mg_level_potential", "hq_profile", "hq_profile_read", "hq_last_error",
+    "hq_mg_level_potential", "hq_gram_static", "hq_profile", "hq_profile_read", "hq_last_error",
     "hq_status_string", "hq_destroy",
 ]
 KERNEL_CLASSES = ["stencil", "residual", "smooth", "transfer", "coarse", "vector", "reduce", "gram",
@@ -95,6 +95,7 @@ def load():
         "hq_mg_prolong": (_I, [_P, _I, _P, _P, _P]),
         "hq_mg_coarse_solve": (_I, [_P, _P, _P]),
         "hq_mg_level_potential": (_I, [_P, _I, _P]),
+        "hq_gram_static": (_I, [_P, _I, _P, _I, _L, _D, _P, _P]),
         "hq_profile": (_I, [_P, _I]),
         "hq_profile_read": (_I, [_P, _P, _P, _P]),
         "hq_last_error": (ctypes.c_char_p, [_P]),
