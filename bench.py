@@ -44,9 +44,12 @@ FP64_PEAK_GFLOPS = 2 * 152 * 2.07 * 2
 #   stencil  y = D x - c s: 5 add + mul + fma = 8 flops; 2 words
 #   residual b - (D x - c s): 9 flops; 3 words
 ALGO = {"smooth": (10.0, 3.0), "stencil": (8.0, 2.0), "residual": (9.0, 3.0)}
-# DRAM bytes per point-column of the smooth kernel measured by ncu (see
-# profiles/); None until a capture of the current kernel exists.
-TRAFFIC_PER_ELEMENT = {("smooth", "f64"): None, ("smooth", "f32"): None}
+# DRAM bytes per point-column of the finest-level smooth kernel measured by
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum of one launch / 16.78 M
+# point-columns, profiles/k_jacobi_wells64_N64.md); set to None whenever the
+# kernel changes until it is captured again.
+TRAFFIC_PER_ELEMENT = {("smooth", "f64"): (278.660352e6 + 112.328704e6) / 16777216,
+                       ("smooth", "f32"): (135.338240e6 + 44.317696e6) / 16777216}
 
 
 def peaks():
@@ -222,18 +225,14 @@ def run_hq(args):
     # step, state and gradient norm back to pinned host memory
     Uh_host = torch.empty((m ** 3, N), dtype=torch.float64, pin_memory=True).numpy()
     Zh_host = torch.empty((m ** 3, N), dtype=torch.float64, pin_memory=True).numpy()
-    Uc, Zc, stp = s.get_state(with_warm_start=True)
-    Uh_host[:] = Uc
-    Zh_host[:] = Zc
+    _, _, stp = s.get_state(with_warm_start=True, U_out=Uh_host, Z_out=Zh_host)
     barrier(ws)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(K):
         s.set_state(Uh_host, stp, Z=Zh_host)
         s.step(1)
-        Uo, Zo, stp = s.get_state(with_warm_start=True)
-        Uh_host[:] = Uo
-        Zh_host[:] = Zo
+        _, _, stp = s.get_state(with_warm_start=True, U_out=Uh_host, Z_out=Zh_host)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / max(K, 1)
     barrier(ws)
