@@ -126,13 +126,21 @@ def barrier(ws):
 
 
 def max_over_ranks(ws, x):
+    """Maximum of a per-rank scalar over all ranks (the slowest replica)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(ws, ms_per_step_max):
+    """Whole-job steps/s: every rank advances its own replica by one step in
+    ms_per_step_max (the slowest rank's time)."""
+    return ws * 1000.0 / ms_per_step_max
 
 
 def time_steps(torch, s, K, ws):
@@ -180,6 +188,13 @@ def roofline(prof, dtype_tag, hbm_peak, hbm_kind):
     return out
 
 
+def breakdown(prof, K):
+    """Per kernel class: launches and event-timed ms per step, share."""
+    tot = sum(v[1] for v in prof.values()) or 1.0
+    return {k: {"launches_per_step": v[0] / K, "ms_per_step": v[1] / K,
+                "share": v[1] / tot} for k, v in prof.items() if v[0] > 0}
+
+
 def run_hq(args):
     import numpy as np
     import torch
@@ -221,6 +236,7 @@ def run_hq(args):
     prof = s.profile_read()
     s.profile(timing=False)
     roof = roofline(prof, "f64", hbm_peak, hbm_kind)
+    brk = breakdown(prof, K)
     # end to end through host buffers: state in from pinned host memory,
     # step, state and gradient norm back to pinned host memory
     Uh_host = torch.empty((m ** 3, N), dtype=torch.float64, pin_memory=True).numpy()
@@ -279,10 +295,11 @@ def run_hq(args):
         time_steps(torch, sm, K, ws)
         prof_m = sm.profile_read()
         sm.profile(timing=False)
-        mixed = {"value": ws * 1000.0 / ms_m, "unit": "steps/s", "ms_per_step": ms_m,
+        mixed = {"value": job_value(ws, ms_m), "unit": "steps/s", "ms_per_step": ms_m,
                  "speedup_vs_fp64": ms / ms_m, "dtype": "f32 (FP64 small solve / extraction)",
                  "cg_rtol": args.mixed_rtol,
-                 "roofline": roofline(prof_m, "f32", hbm_peak, hbm_kind)}
+                 "roofline": roofline(prof_m, "f32", hbm_peak, hbm_kind),
+                 "breakdown": breakdown(prof_m, K)}
         if fp64_lam is not None and args.ttr_steps > 0:
             sm2 = hq.Solver(m, N, tau=w["tau"], cg_rtol=args.mixed_rtol, precision="mixed",
                             timeout_s=args.ttr_timeout)
@@ -311,7 +328,7 @@ def run_hq(args):
     if ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(V, U0, w, steps=1)
 
-    value = ws * 1000.0 / ms
+    value = job_value(ws, ms)
     out = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": K,
         "warmup": W, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -326,6 +343,7 @@ def run_hq(args):
         "clocks": clocks,
         "gpu_launches": int(launches),
         "ms_per_step_instrumented": ms_instr,
+        "breakdown": brk,
         "e2e": {"value": ws / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": 2 * blk_bytes,
                 "d2h_bytes_per_step": 2 * blk_bytes + 8,
                 "how": "hq_set_state from pinned host (U and warm start), hq_step, "

@@ -220,6 +220,8 @@ typedef enum {
     HQ_K_BLOCKGEMM,     /* block x small-matrix products (updates)         */
     HQ_K_SMALL,         /* N x N / 2N x 2N FP64 algebra                    */
     HQ_K_SETUP,         /* once-per-potential setup                        */
+    HQ_K_COARSE_GRIDS,  /* grid kernels on multigrid levels >= 1 (the      */
+                        /* classes above count the finest level only)      */
     HQ_K_NCLASS
 } hq_kernel_class;
 

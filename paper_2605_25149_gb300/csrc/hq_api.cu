@@ -46,6 +46,20 @@ struct Level {
 
 }  // namespace
 
+namespace {
+constexpr int MAXGRAPH = 4;
+// a captured PCG loop (conditional WHILE node) for one solution block
+struct PcgGraph {
+    const void *X = nullptr;
+    double rtol = 0.0;
+    int maxit = 0;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long body_launches[HQ_K_NCLASS] = {};
+    bool ok = false;
+};
+}  // namespace
+
 struct hq_ctx {
     hq_config cfg;
     bool mixed = false;
@@ -92,19 +106,31 @@ struct hq_ctx {
     size_t evused = 0;
     std::vector<std::pair<int, size_t>> evrec;
     size_t pending_start = 0;
+    // captured PCG loops
+    bool use_graphs = true, capturing = false;
+    long *cap_counts = nullptr;
+    PcgGraph pgraph[MAXGRAPH];
+    int npgraph = 0;
+    cudaStream_t cap = nullptr;
     ~hq_ctx() {
         for (cudaEvent_t e : evpool) cudaEventDestroy(e);
+        for (int i = 0; i < npgraph; i++) {
+            if (pgraph[i].exec) cudaGraphExecDestroy(pgraph[i].exec);
+            if (pgraph[i].g) cudaGraphDestroy(pgraph[i].g);
+        }
+        if (cap) cudaStreamDestroy(cap);
     }
 };
 
 namespace hq {
 namespace {
 thread_local hq_ctx *g_prof = nullptr;
+thread_local int g_level = 0;   // multigrid level of the launches being issued
 }
 void hook_before(int cls) {
     (void)cls;
     hq_ctx *x = g_prof;
-    if (!x || !x->timing) return;
+    if (!x || !x->timing || x->capturing) return;
     while (x->evpool.size() < x->evused + 2) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) return;
@@ -117,6 +143,13 @@ void hook_before(int cls) {
 void hook_after(int cls, double work) {
     hq_ctx *x = g_prof;
     if (!x) return;
+    if (g_level > 0 && (cls == HQ_K_STENCIL || cls == HQ_K_RESIDUAL || cls == HQ_K_SMOOTH ||
+                        cls == HQ_K_TRANSFER || cls == HQ_K_VECTOR))
+        cls = HQ_K_COARSE_GRIDS;
+    if (x->capturing) {
+        if (x->cap_counts && cls >= 0 && cls < HQ_K_NCLASS) x->cap_counts[cls]++;
+        return;
+    }
     if (cls >= 0 && cls < HQ_K_NCLASS) {
         x->launches[cls]++;
         x->work[cls] += work;
@@ -128,6 +161,13 @@ void hook_after(int cls, double work) {
 }  // namespace hq
 
 namespace {
+// tags the launches issued in its lifetime with a multigrid level
+struct LevelScope {
+    int prev;
+    explicit LevelScope(int l) : prev(hq::g_level) { hq::g_level = l; }
+    ~LevelScope() { hq::g_level = prev; }
+};
+
 // binds the instrumentation hooks to a context for the duration of a call
 struct ProfScope {
     hq_ctx *prev;
@@ -383,6 +423,7 @@ T *first_target(hq_ctx *x, int l, T *Zfinal, T *Tbuf) {
 
 template <typename T>
 hq_status vcycle(hq_ctx *x, int l, const T *r, T *Zf, T *Tb, bool first_done, double *part_final) {
+    LevelScope lvl_(l);
     Level &v = x->lev[l];
     const T c = (T)v.c, omw = (T)(1.0 - x->cfg.mg_omega);
     if (l == x->L - 1) {
@@ -416,13 +457,126 @@ hq_status vcycle(hq_ctx *x, int l, const T *r, T *Zf, T *Tb, bool first_done, do
 
 // ---------------------------------------------------------------------------
 // block PCG: X = G B, per-column stopping ||r_j|| <= rtol ||b_j||
+//
+// Per column (columns that have stopped are frozen by alpha = beta = 0):
+//   r = b - A x, z = M r, p = z, rz = r.z
+//   iterate: q = A p, alpha = rz / p.q, x += alpha p, r -= alpha q,
+//            stop if ||r|| <= rtol ||b||; z = M r, beta = (r.z)/rz, p = z + beta p
+// The first iteration runs from the host; the remaining ones run as the body
+// of a CUDA graph with a conditional WHILE node (body: V-cycle, beta, p, A p,
+// alpha, x / r update, stopping test, and a kernel that sets the loop
+// condition from the number of active columns and the iteration count), so
+// a whole solve costs two host round trips.  With per-launch event timing on,
+// the same body is launched from the host instead.
 // ---------------------------------------------------------------------------
+template <typename T>
+hq_status pcg_body(hq_ctx *x, T *X, double rtol) {
+    Level &v = x->lev[0];
+    const GridGeom &g = v.g;
+    const int N = x->N;
+    T *R = (T *)x->R, *Zp = (T *)x->Zp, *P = (T *)x->P, *Q = (T *)x->Q, *Tt = (T *)x->Tt;
+    PcgScalars sc = x->sc;
+    const bool single = (x->L == 1);
+    HQ_TRY(vcycle<T>(x, 0, R, Zp, Tt, !single, x->part));
+    launch_finalize(FIN_BETA, N, g.gy, x->part, nullptr, sc, rtol, x->st);
+    launch_pcg_p<T>(g, sc.beta, Zp, P, x->st);
+    return HQ_OK;
+}
+
+template <typename T>
+hq_status pcg_half(hq_ctx *x, T *X, double rtol) {
+    Level &v = x->lev[0];
+    const GridGeom &g = v.g;
+    const int N = x->N;
+    T *R = (T *)x->R, *Zp = (T *)x->Zp, *P = (T *)x->P, *Q = (T *)x->Q, *Tt = (T *)x->Tt;
+    PcgScalars sc = x->sc;
+    const bool single = (x->L == 1);
+    T *zfirst = first_target<T>(x, 0, Zp, Tt);
+    launch_apply<T>(g, (const T *)v.Dt, (T)v.c, P, Q, x->part, x->st);
+    launch_finalize(FIN_ALPHA, N, g.gy, x->part, nullptr, sc, rtol, x->st);
+    launch_pcg_xr<T>(g, sc.alpha, P, Q, X, R, x->part, (const T *)v.wDt,
+                     single ? nullptr : zfirst, x->st);
+    HQ_CUDA(cudaMemsetAsync(sc.num_active, 0, sizeof(int), x->st));
+    launch_finalize(FIN_RR, N, g.gy, x->part, nullptr, sc, rtol, x->st);
+    return HQ_OK;
+}
+
+void destroy_graph(PcgGraph &pg) {
+    if (pg.exec) cudaGraphExecDestroy(pg.exec);
+    if (pg.g) cudaGraphDestroy(pg.g);
+    pg = PcgGraph();
+}
+
+template <typename T>
+PcgGraph *pcg_graph(hq_ctx *x, T *X, double rtol, int maxit) {
+    for (int i = 0; i < x->npgraph; i++) {
+        PcgGraph &pg = x->pgraph[i];
+        if (pg.X == X && pg.rtol == rtol && pg.maxit == maxit) return pg.ok ? &pg : nullptr;
+    }
+    if (x->npgraph == MAXGRAPH) {
+        destroy_graph(x->pgraph[0]);
+        for (int i = 1; i < MAXGRAPH; i++) x->pgraph[i - 1] = x->pgraph[i];
+        x->pgraph[MAXGRAPH - 1] = PcgGraph();
+        x->npgraph--;
+    }
+    PcgGraph &pg = x->pgraph[x->npgraph++];
+    pg.X = X;
+    pg.rtol = rtol;
+    pg.maxit = maxit;
+    pg.ok = false;
+    if (!x->cap && cudaStreamCreateWithFlags(&x->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        x->cap = nullptr;
+        return nullptr;
+    }
+    cudaGraphConditionalHandle h;
+    if (cudaGraphCreate(&pg.g, 0) != cudaSuccess) return nullptr;
+    if (cudaGraphConditionalHandleCreate(&h, pg.g, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+        return nullptr;
+    // zero-initialised node parameters (the struct has no default constructor)
+    alignas(cudaGraphNodeParams) unsigned char npbuf[sizeof(cudaGraphNodeParams)];
+    std::memset(npbuf, 0, sizeof(npbuf));
+    cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(npbuf);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, pg.g, nullptr, nullptr, 0, &np) != cudaSuccess) return nullptr;
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(x->cap, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return nullptr;
+    cudaStream_t saved = x->st;
+    x->st = x->cap;
+    x->capturing = true;
+    for (int i = 0; i < HQ_K_NCLASS; i++) pg.body_launches[i] = 0;
+    x->cap_counts = pg.body_launches;
+    hq_status st = pcg_body<T>(x, X, rtol);
+    if (st == HQ_OK) st = pcg_half<T>(x, X, rtol);
+    if (st == HQ_OK) launch_pcg_cond(x->sc.num_active, x->sc.num_active + 1, maxit, h, x->st);
+    x->capturing = false;
+    x->cap_counts = nullptr;
+    x->st = saved;
+    cudaGraph_t out = nullptr;
+    cudaError_t e = cudaStreamEndCapture(x->cap, &out);
+    if (st != HQ_OK || e != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (cudaGraphInstantiate(&pg.exec, pg.g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    pg.ok = true;
+    return &pg;
+}
+
 template <typename T>
 hq_status pcg(hq_ctx *x, const T *B, T *X, double rtol, int maxit, int *iters_host) {
     Level &v = x->lev[0];
     const GridGeom &g = v.g;
     const int N = x->N;
-    T *R = (T *)x->R, *Zp = (T *)x->Zp, *P = (T *)x->P, *Q = (T *)x->Q, *Tt = (T *)x->Tt;
+    T *R = (T *)x->R, *Zp = (T *)x->Zp, *P = (T *)x->P, *Tt = (T *)x->Tt;
     const T c = (T)v.c;
     PcgScalars sc = x->sc;
     HQ_CUDA(cudaMemsetAsync(sc.num_active, 0, sizeof(int), x->st));
@@ -432,26 +586,33 @@ hq_status pcg(hq_ctx *x, const T *B, T *X, double rtol, int maxit, int *iters_ho
     HQ_CUDA(cudaMemcpyAsync(&nact, sc.num_active, sizeof(int), cudaMemcpyDeviceToHost, x->st));
     HQ_CUDA(cudaStreamSynchronize(x->st));
     hq_status st = HQ_OK;
-    if (nact > 0) {
+    if (nact > 0 && maxit > 0) {
         HQ_TRY(vcycle<T>(x, 0, R, Zp, Tt, false, x->part));
         launch_finalize(FIN_RZ, N, g.gy, x->part, nullptr, sc, rtol, x->st);
         HQ_TRY(copy_blk<T>(x, P, Zp, (size_t)x->n * N));
-        T *zfirst = first_target<T>(x, 0, Zp, Tt);
-        const bool single = (x->L == 1);
-        int it = 0;
-        for (it = 1; it <= maxit; it++) {
-            launch_apply<T>(g, (const T *)v.Dt, c, P, Q, x->part, x->st);
-            launch_finalize(FIN_ALPHA, N, g.gy, x->part, nullptr, sc, rtol, x->st);
-            launch_pcg_xr<T>(g, sc.alpha, P, Q, X, R, x->part, (const T *)v.wDt,
-                             single ? nullptr : zfirst, x->st);
-            HQ_CUDA(cudaMemsetAsync(sc.num_active, 0, sizeof(int), x->st));
-            launch_finalize(FIN_RR, N, g.gy, x->part, nullptr, sc, rtol, x->st);
-            HQ_CUDA(cudaMemcpyAsync(&nact, sc.num_active, sizeof(int), cudaMemcpyDeviceToHost, x->st));
-            HQ_CUDA(cudaStreamSynchronize(x->st));
-            if (nact == 0) break;
-            HQ_TRY(vcycle<T>(x, 0, R, Zp, Tt, !single, x->part));
-            launch_finalize(FIN_BETA, N, g.gy, x->part, nullptr, sc, rtol, x->st);
-            launch_pcg_p<T>(g, sc.beta, Zp, P, x->st);
+        HQ_TRY(pcg_half<T>(x, X, rtol));   // iteration 1
+        HQ_CUDA(cudaMemcpyAsync(&nact, sc.num_active, sizeof(int), cudaMemcpyDeviceToHost, x->st));
+        HQ_CUDA(cudaStreamSynchronize(x->st));
+        if (nact > 0 && maxit > 1) {
+            PcgGraph *pg = (x->use_graphs && !x->timing) ? pcg_graph<T>(x, X, rtol, maxit) : nullptr;
+            if (pg) {
+                int it[2] = {nact, 1};
+                HQ_CUDA(cudaMemcpyAsync(sc.num_active, it, sizeof(it), cudaMemcpyHostToDevice, x->st));
+                HQ_CUDA(cudaGraphLaunch(pg->exec, x->st));
+                HQ_CUDA(cudaMemcpyAsync(it, sc.num_active, sizeof(it), cudaMemcpyDeviceToHost, x->st));
+                HQ_CUDA(cudaStreamSynchronize(x->st));
+                nact = it[0];
+                for (int i = 0; i < HQ_K_NCLASS; i++)
+                    x->launches[i] += pg->body_launches[i] * (long)(it[1] - 1);
+            } else {
+                for (int it = 2; it <= maxit; it++) {
+                    HQ_TRY(pcg_body<T>(x, X, rtol));
+                    HQ_TRY(pcg_half<T>(x, X, rtol));
+                    HQ_CUDA(cudaMemcpyAsync(&nact, sc.num_active, sizeof(int), cudaMemcpyDeviceToHost, x->st));
+                    HQ_CUDA(cudaStreamSynchronize(x->st));
+                    if (nact == 0) break;
+                }
+            }
         }
         if (nact > 0 && rtol > 0.0) st = HQ_ERR_NOT_CONVERGED;
     }
@@ -924,6 +1085,10 @@ hq_status hq_init(const hq_config *cfg, void *d_workspace, size_t bytes, void *c
     x->st = (cudaStream_t)cuda_stream;
     x->ws = (char *)d_workspace;
     x->ws_bytes = bytes;
+    {
+        const char *e = std::getenv("HQ_NO_GRAPHS");
+        x->use_graphs = !(e && e[0] == '1');
+    }
     carve(x, cfg, x->ws);
     // the status words start cleared
     cudaError_t e = cudaMemsetAsync(x->sc.status, 0, sizeof(int), x->st);

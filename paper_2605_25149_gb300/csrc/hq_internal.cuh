@@ -109,6 +109,11 @@ enum FinMode { FIN_BNORM_RNORM = 0, FIN_ALPHA = 1, FIN_RR = 2, FIN_BETA = 3, FIN
 void launch_finalize(int mode, int N, int gy, const double *part, const double *part2,
                      PcgScalars sc, double rtol, cudaStream_t s);
 
+// sets the WHILE condition of a captured PCG loop (num_active[0] > 0 and
+// ++iter[0] < maxit)
+void launch_pcg_cond(const int *num_active, int *iter, int maxit, cudaGraphConditionalHandle h,
+                     cudaStream_t s);
+
 // setup
 void launch_coarse_potential(int mf, const double *Vf, int mc, double *Vc, cudaStream_t s);
 void launch_level_diag(long n, const double *V, double sigma, double c, double omega,

@@ -506,6 +506,15 @@ __global__ void __launch_bounds__(128) k_finalize(int mode, int N, int gy, const
     }
 }
 
+// loop condition of the captured PCG: one more iteration was completed;
+// continue while columns are active and the cap is not reached
+__global__ void k_pcg_cond(const int *num_active, int *iter, int maxit,
+                           cudaGraphConditionalHandle h) {
+    const int it = iter[0] + 1;
+    iter[0] = it;
+    cudaGraphSetConditional(h, (num_active[0] > 0 && it < maxit) ? 1u : 0u);
+}
+
 // ---------------------------------------------------------------------------
 // setup kernels (once per potential)
 // ---------------------------------------------------------------------------
@@ -806,6 +815,11 @@ void launch_dot(const GridGeom &g, const T *x, const T *y, double *part, cudaStr
 void launch_finalize(int mode, int N, int gy, const double *part, const double *part2,
                      PcgScalars sc, double rtol, cudaStream_t s) {
     HQ_LAUNCH(HQ_K_REDUCE, k_finalize<<<N, 128, 0, s>>>(mode, N, gy, part, part2, sc, rtol));
+}
+
+void launch_pcg_cond(const int *num_active, int *iter, int maxit, cudaGraphConditionalHandle h,
+                     cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_REDUCE, k_pcg_cond<<<1, 1, 0, s>>>(num_active, iter, maxit, h));
 }
 
 void launch_coarse_potential(int mf, const double *Vf, int mc, double *Vc, cudaStream_t s) {

@@ -38,7 +38,7 @@ EXPORTED = [
     "hq_status_string", "hq_destroy",
 ]
 KERNEL_CLASSES = ["stencil", "residual", "smooth", "transfer", "coarse", "vector", "reduce", "gram",
-                  "blockgemm", "small", "setup"]
+                  "blockgemm", "small", "setup", "coarse_grids"]
 
 
 class HQError(RuntimeError):
@@ -236,9 +236,17 @@ class Solver:
                     "hq_eigenpairs")
         return dict(lam_paper=lp, lam_rr=lr, vectors=vec, residuals=res)
 
-    def get_state(self, with_warm_start=False):
-        U = np.empty((self.n, self.N))
-        Z = np.empty((self.n, self.N)) if with_warm_start else None
+    def get_state(self, with_warm_start=False, U_out=None, Z_out=None):
+        """(U, Z or None, step).  U_out / Z_out: optional preallocated host
+        FP64 arrays (e.g. pinned) to copy into."""
+        U = np.empty((self.n, self.N)) if U_out is None else U_out
+        Z = None
+        if with_warm_start:
+            Z = np.empty((self.n, self.N)) if Z_out is None else Z_out
+        for a in (U, Z):
+            if a is not None and (a.dtype != np.float64 or not a.flags.c_contiguous or
+                                  a.size != self.n * self.N):
+                raise ValueError("expected a C-contiguous float64 array of n x N values")
         step = ctypes.c_long()
         self._check(self.lib.hq_get_state(self._ctx, _hptr(U), _hptr(Z), 0, ctypes.byref(step)),
                     "hq_get_state")
