@@ -234,6 +234,7 @@ def run_hq(args):
     s.profile(timing=True)
     ms_instr, _ = time_steps(torch, s, K, ws)
     prof = s.profile_read()
+    pcg_solves, pcg_iters = s.pcg_stats()
     s.profile(timing=False)
     roof = roofline(prof, "f64", hbm_peak, hbm_kind)
     brk = breakdown(prof, K)
@@ -343,6 +344,7 @@ def run_hq(args):
         "clocks": clocks,
         "gpu_launches": int(launches),
         "ms_per_step_instrumented": ms_instr,
+        "pcg_iterations_per_solve": pcg_iters / max(pcg_solves, 1),
         "breakdown": brk,
         "e2e": {"value": ws / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": 2 * blk_bytes,
                 "d2h_bytes_per_step": 2 * blk_bytes + 8,

@@ -75,11 +75,19 @@ typedef struct {
     int mg_coarsest;     /* coarsen m -> m/2 while m > mg_coarsest (1..4)          */
     double mg_omega;     /* Jacobi damping                                         */
     double timeout_s;    /* hq_solve wall-clock limit (<= 0: none)                 */
+    int z_warm_start;    /* 1: start the corrector solve G Uh from W (C1 + S^-1 Puw C2), */
+                         /* exact when span(U) is G-invariant; 0: from zero          */
+    int adaptive_tau;    /* 0: tau_n = tau.  1: tau_n = min(tau_max, 0.8 lam / s_max,  */
+                         /* 1.05 tau_{n-1}) with lam = 1/(largest Ritz value of G on  */
+                         /* span(U)), s_max = max_i sum_j |<U,U>_ij| (a bound on its  */
+                         /* largest eigenvalue); the first step starts from the       */
+                         /* closed-form lower bound of lambda_1(H + sigma)            */
+    double tau_max;      /* delta_T of Algorithm 1 for adaptive_tau (<= 0: no cap)    */
 } hq_config;
 
 /* Defaults: box [-6,6]^3, tau 0.4, automatic shift, FP64, cg_rtol 1e-10,
- * cg_maxit 200, nu1 = nu2 = 2, coarsest 4, omega 0.8, no timeout.  m and nev
- * are left 0 and must be set.                                              */
+ * cg_maxit 200, nu1 = nu2 = 2, coarsest 4, omega 0.8, no timeout, warm start
+ * of the corrector solve on.  m and nev are left 0 and must be set.         */
 void hq_default_config(hq_config *cfg);
 
 /* Bytes of device workspace hq_init needs for cfg (0 if cfg is invalid). */
@@ -126,6 +134,37 @@ hq_status hq_solve(hq_ctx *ctx, double eps, long max_steps, long *steps_out,
 hq_status hq_eigenpairs(hq_ctx *ctx, double *evals_paper, double *evals_rr,
                         double *evecs, int evecs_on_device, double *resid);
 
+/* Monitoring of the current iterate (all host outputs, nullable), in FP64:
+ * energy = E(U) = (1/2)(U,U)_a = (1/2) h^3 tr(U^T H U) with the unshifted H
+ * (Section 2.2; decays along the scheme, Theorem 4.5), onorm = ||<U,U> - I||_F
+ * (the orthogonality error of Theorem 4.6), smin / smax = extreme
+ * eigenvalues of <U,U> (quasi-Stiefel membership, Theorem 4.3).            */
+hq_status hq_monitor(hq_ctx *ctx, double *energy, double *onorm, double *smin, double *smax);
+
+/* ---- differentiation (HQ_FP64 contexts; the iterate should be converged) ----
+ * The Ritz vectors u_i and values lambda_i of hq_eigenpairs define
+ * rho = sum_i u_i^2 (the density, n values).                               */
+/* rho_out (n, FP64): the density of the current Ritz vectors.               */
+hq_status hq_density(hq_ctx *ctx, double *rho_out, int on_device);
+/* dV = sum_i w_i d lambda_i / dV = h^3 sum_i w_i u_i^2 (Hellmann-Feynman for
+ * the discrete operator; w: N host weights, NULL = all ones, giving
+ * d(sum lambda_i)/dV).  dV: n values.                                      */
+hq_status hq_grad_eigs(hq_ctx *ctx, const double *w, double *dV, int on_device);
+/* Adjoint of the density: for a loss L(rho) with G = dL/drho (n values),
+ *   dL/dV = -2 sum_i u_i o xi_i,  (H - lambda_i) xi_i = P (G o u_i),  xi_i in range(P),
+ * P = I - u (h^3 u^T) the projector onto the complement of span(u_1..u_N)
+ * (first-order perturbation of the eigenvectors; components inside the span
+ * leave rho unchanged).  The N systems are solved together by block PCG on
+ * the projected, column-shifted operator with the multigrid V-cycle of
+ * H + sigma as preconditioner (symmetric positive definite on range(P) when
+ * lambda_N < lambda_{N+1}), each to ||r_i|| <= rtol ||P(G o u_i)||.
+ * If rho_target is non-null, G is ignored and the loss
+ * L = (1/2) h^3 sum (rho - rho_target)^2 is used (G = h^3 (rho - rho_target));
+ * *loss (host, nullable) receives L.  iters (host, nullable): PCG
+ * iterations taken.                                                        */
+hq_status hq_grad_density(hq_ctx *ctx, const double *G, const double *rho_target, int on_device,
+                          double rtol, int maxit, double *dV, double *loss, int *iters);
+
 /* Checkpoint: copy U_n (n x N, FP64) and the step counter out / in.  Zwarm
  * (nullable, n x N) is the inner solver's warm start, G Uh of the last step;
  * restoring U together with Zwarm continues bit-identically to the
@@ -134,6 +173,9 @@ hq_status hq_eigenpairs(hq_ctx *ctx, double *evals_paper, double *evals_rr,
 hq_status hq_get_state(hq_ctx *ctx, double *U, double *Zwarm, int on_device, long *step);
 hq_status hq_set_state(hq_ctx *ctx, const double *U, const double *Zwarm, int on_device,
                        long step);
+
+/* Time step tau_n used by the last step taken (host output). */
+hq_status hq_time_step(hq_ctx *ctx, double *tau);
 
 /* Scalars of the configured problem (host outputs, nullable). */
 hq_status hq_problem_info(hq_ctx *ctx, double *h, double *sigma, int *levels,
@@ -160,6 +202,16 @@ hq_status hq_block_pcg(hq_ctx *ctx, const void *B, void *X, double rtol, int max
  * <A,B> of Section 2.1 with w = h^3.  Na, Nb <= 2N.                        */
 hq_status hq_gram(hq_ctx *ctx, const void *A, int Na, const void *B, int Nb, double w,
                   double *out);
+
+/* Out = A1 M1 + A2 M2 (+ Cin): the block x small-matrix products of the
+ * updates of Eq. (4.1) (Uh = U C1 + W C2, U+ = Uh - tau Z (<Uh,Uh> - I)).
+ * A1 (n x k1), A2 (n x k2; nullable with k2 = 0), Cin (nullable) and Out are
+ * point-major device blocks of the context's element type with N columns
+ * (Out, Cin) and 1 <= k1, 0 <= k2 <= N; M1 (k1 x N), M2 (k2 x N) are FP64
+ * row-major device matrices.  FP64 SIMT in HQ_FP64 contexts, tcgen05 3xTF32
+ * (FP32 accumulation) in HQ_MIXED contexts.                                */
+hq_status hq_block_gemm(hq_ctx *ctx, const void *A1, int k1, const double *M1, const void *A2,
+                        int k2, const double *M2, const void *Cin, void *Out);
 
 /* One step of Eq. (4.1) from the current iterate, exporting its
  * intermediates to device buffers (each nullable): W = G U_n (n x N),
@@ -235,6 +287,9 @@ hq_status hq_profile(hq_ctx *ctx, int timing);
  * doubles, host, nullable): grid point-columns written by the grid kernels
  * of each class (0 for the dense classes).  Synchronises the stream.        */
 hq_status hq_profile_read(hq_ctx *ctx, long *launches, double *ms, double *elements);
+/* Inner-solve statistics since the last hq_profile: block-PCG solves run and
+ * PCG iterations summed over them (host outputs, nullable).                 */
+hq_status hq_pcg_stats(hq_ctx *ctx, long *solves, long *iterations);
 
 const char *hq_last_error(hq_ctx *ctx);
 const char *hq_status_string(hq_status s);

@@ -86,6 +86,9 @@ def _sig(lib):
         "orc_solve": (_I, [_I, _D, _D, _P, _D, _I, _D, _D, _I, _D, _L, _P, _P,
                            _P, _P, _P]),
         "orc_extract": (_I, [_I, _D, _D, _P, _D, _I, _P, _P, _P, _P, _P, _P]),
+        "orc_lambda1_lower_bound": (_D, [_I, _D, _D, _P, _D]),
+        "orc_solve_adaptive": (_I, [_I, _D, _D, _P, _D, _I, _D, _D, _I, _D, _L, _P, _P, _P,
+                                    _P, _P, _P]),
         "orc_energy": (_D, [_I, _D, _D, _P, _D, _I, _P]),
     }
     for name, (res, args) in spec.items():
@@ -339,6 +342,31 @@ def solve(m, V, sigma, U0, tau, eps, max_steps, lo=-6.0, hi=6.0, cg_rtol=1e-13,
     if not (allow_unconverged and st == ERR_NOT_CONVERGED):
         _check(st, "orc_solve")
     return U, W, steps.value, g.value, hist[: steps.value + 1]
+
+
+def lambda1_lower_bound(m, V, sigma, lo=-6.0, hi=6.0):
+    """Closed-form lower bound of the smallest eigenvalue of H_h + sigma."""
+    return lib().orc_lambda1_lower_bound(m, lo, hi, _ptr(_f64(V).ravel()), sigma)
+
+
+def solve_adaptive(m, V, sigma, U0, tau_max, eps, max_steps, lo=-6.0, hi=6.0, cg_rtol=1e-13,
+                   cg_maxit=20000, allow_unconverged=False):
+    """Algorithm 1 with the adaptive time step (tau_n <= tau_max = delta_T):
+    tau_n = min(delta_T, 0.8 lam_hat / lambda_max<U,U>, 1.05 tau_{n-1}).
+    Returns (U_end, W_end, steps, g_end, g_history, tau_history)."""
+    V = _f64(V).ravel()
+    U = _f64(U0).copy()
+    W = np.empty_like(U)
+    steps = ctypes.c_long()
+    g = ctypes.c_double()
+    hist = np.full(max_steps + 1, np.nan)
+    th = np.full(max_steps + 1, np.nan)
+    st = lib().orc_solve_adaptive(m, lo, hi, _ptr(V), sigma, U.shape[1], tau_max, cg_rtol,
+                                  cg_maxit, eps, max_steps, _ptr(U), _ptr(W), ctypes.byref(steps),
+                                  ctypes.byref(g), _ptr(hist), _ptr(th))
+    if not (allow_unconverged and st == ERR_NOT_CONVERGED):
+        _check(st, "orc_solve_adaptive")
+    return U, W, steps.value, g.value, hist[: steps.value + 1], th[: steps.value]
 
 
 def extract(m, V, sigma, U, W, lo=-6.0, hi=6.0, want_vectors=True):

@@ -710,12 +710,83 @@ double orc_scale_initial(long n, int N, double h3, double *U)
 /* Outputs (any may be NULL): W = G U, gram (2N x 2N Gram of [U W]), g,      */
 /*          XY (2N x N), Uh, Shat = <Uh,Uh>, Z = G Uh, Unew.                 */
 /* ------------------------------------------------------------------------ */
-int orc_scheme_step(int m, double lo, double hi, const double *V, double sigma, int N,
-                    double tau, double cg_rtol, int cg_maxit,
-                    const double *U, const double *W0, const double *Z0,
-                    double *W_out, double *gram_out, double *g_out, double *XY_out,
-                    double *Uh_out, double *Shat_out, double *Z_out, double *Unew_out,
-                    int *cg_iters /* 2*N or NULL */)
+/* Adaptive time step (an extension: Algorithm 1 allows any tau_n <= delta_T
+ * and the paper leaves adaptive stepping as future work).  From the Gram of
+ * [U W] of step n:
+ *   lam_hat = 1 / mu_max, mu_max the largest Ritz value of G on span(U), i.e.
+ *             the largest eigenvalue of the pencil (sym <W,U>, <U,U>) -- an
+ *             upper estimate of the smallest eigenvalue lambda'_1 of H + sigma;
+ *   s_max   = max_i sum_j |<U,U>_ij| (Gershgorin bound on lambda_max(<U,U>));
+ *   tau_n   = min(delta_T, c lam_hat / s_max, gamma tau_{n-1}),
+ * with c = 0.8, gamma = 1.05 and, for the first step, tau_{-1} chosen so that
+ * tau_0 <= c lb / s_max where lb <= lambda'_1 is the closed-form lower bound.
+ * Near convergence the orthogonality error of eigenpair 1 is multiplied by
+ * 1 - 2 tau / lambda'_1 per step, so tau < lambda'_1 keeps it contracting.  */
+typedef struct {
+    double tau_max, c, gamma, lb, tau_prev;
+    int first;
+} orc_adapt;
+
+/* Cm = L^{-1} sym(K) L^{-T} with <U,U> = S = L L^T (all N x N, row-major). */
+static int rr_matrix(int N, const double *K, const double *S, double *L, double *Cm, double *T)
+{
+    memcpy(L, S, sizeof(double) * N * N);
+    int st = cholesky(N, L);
+    if (st != ORC_OK) return st;
+    for (int j = 0; j < N; j++)
+        for (int i = 0; i < N; i++) {
+            double v = 0.5 * (K[i * N + j] + K[j * N + i]);
+            for (int k = 0; k < i; k++) v -= L[i * N + k] * T[k * N + j];
+            T[i * N + j] = v / L[i * N + i];
+        }
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++) {
+            double v = T[i * N + j];
+            for (int k = 0; k < j; k++) v -= Cm[i * N + k] * L[j * N + k];
+            Cm[i * N + j] = v / L[j * N + j];
+        }
+    return ORC_OK;
+}
+
+static double adaptive_tau(int N, const double *G2, orc_adapt *ad)
+{
+    int N2 = 2 * N;
+    double *S = malloc(sizeof(double) * N * N), *P = malloc(sizeof(double) * N * N),
+           *L = malloc(sizeof(double) * N * N), *Cm = malloc(sizeof(double) * N * N),
+           *T = malloc(sizeof(double) * N * N), *ev = malloc(sizeof(double) * N);
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++) {
+            S[i * N + j] = G2[(long)i * N2 + j];
+            P[i * N + j] = G2[(long)(N + i) * N2 + j];
+        }
+    /* s_max: Gershgorin bound max_i sum_j |S_ij| >= lambda_max(<U,U>) */
+    double smax = 0.0;
+    for (int i = 0; i < N; i++) {
+        double r = 0.0;
+        for (int j = 0; j < N; j++) r += fabs(S[i * N + j]);
+        if (r > smax) smax = r;
+    }
+    double tau = ad->tau_max;
+    if (rr_matrix(N, P, S, L, Cm, T) == ORC_OK) {
+        orc_sym_eig(N, Cm, ev, NULL);
+        double cap = ad->c * (1.0 / ev[N - 1]) / smax;
+        if (cap < tau) tau = cap;
+    }
+    double prev = ad->first ? ad->c * ad->lb / (ad->gamma * smax) : ad->tau_prev;
+    if (ad->gamma * prev < tau) tau = ad->gamma * prev;
+    ad->tau_prev = tau;
+    ad->first = 0;
+    free(S); free(P); free(L); free(Cm); free(T); free(ev);
+    return tau;
+}
+
+static int scheme_step_impl(int m, double lo, double hi, const double *V, double sigma, int N,
+                            double tau, orc_adapt *ad, double *tau_used,
+                            double cg_rtol, int cg_maxit,
+                            const double *U, const double *W0, const double *Z0,
+                            double *W_out, double *gram_out, double *g_out, double *XY_out,
+                            double *Uh_out, double *Shat_out, double *Z_out, double *Unew_out,
+                            int *cg_iters)
 {
     long n = cube(m);
     double h = orc_grid_h(m, lo, hi), h3 = h * h * h;
@@ -755,7 +826,9 @@ int orc_scheme_step(int m, double lo, double hi, const double *V, double sigma, 
         *g_out = sqrt(h3 * kval(&k));
     }
 
-    /* 4. predictor system */
+    /* 4. predictor system (time step fixed, or from the adaptive rule) */
+    if (ad) tau = adaptive_tau(N, G2, ad);
+    if (tau_used) *tau_used = tau;
     for (int i = 0; i < N; i++)
         for (int j = 0; j < N; j++) {
             double d = (i == j) ? 1.0 : 0.0;
@@ -809,6 +882,28 @@ done:
     return st;
 }
 
+int orc_scheme_step(int m, double lo, double hi, const double *V, double sigma, int N,
+                    double tau, double cg_rtol, int cg_maxit,
+                    const double *U, const double *W0, const double *Z0,
+                    double *W_out, double *gram_out, double *g_out, double *XY_out,
+                    double *Uh_out, double *Shat_out, double *Z_out, double *Unew_out,
+                    int *cg_iters /* 2*N or NULL */)
+{
+    return scheme_step_impl(m, lo, hi, V, sigma, N, tau, NULL, NULL, cg_rtol, cg_maxit, U, W0,
+                            Z0, W_out, gram_out, g_out, XY_out, Uh_out, Shat_out, Z_out,
+                            Unew_out, cg_iters);
+}
+
+/* Closed-form lower bound of the smallest eigenvalue of H + sigma. */
+double orc_lambda1_lower_bound(int m, double lo, double hi, const double *V, double sigma)
+{
+    double h = orc_grid_h(m, lo, hi);
+    double s = sin(ORC_PI / (2.0 * (m + 1)));
+    double vmin = V[0];
+    for (long p = 1; p < cube(m); p++) if (V[p] < vmin) vmin = V[p];
+    return 3.0 * (2.0 / (h * h)) * s * s + vmin + sigma;
+}
+
 /* Gradient norm alone: W = G U by CG, g = || W - U <W,U> ||_h. */
 int orc_grad_norm(int m, double lo, double hi, const double *V, double sigma, int N,
                   double cg_rtol, int cg_maxit, const double *U, double *W_io, double *g_out)
@@ -855,6 +950,38 @@ int orc_solve(int m, double lo, double hi, const double *V, double sigma, int N,
         if (st != ORC_OK) break;
         if (g_hist) g_hist[step] = g;
         if (g < eps || step >= max_steps) break;
+        memcpy(U, Un, sizeof(double) * n * N);
+        have_z = 1;
+        step++;
+    }
+    if (st == ORC_OK && !(g < eps)) st = ORC_ERR_NOT_CONVERGED;
+    *steps_out = step;
+    *g_out = g;
+    free(Z); free(Un);
+    return st;
+}
+
+/* Algorithm 1 with the adaptive time step above (delta_T = tau_max).
+ * tau_hist (max_steps entries or NULL) receives tau_0, tau_1, ...            */
+int orc_solve_adaptive(int m, double lo, double hi, const double *V, double sigma, int N,
+                       double tau_max, double cg_rtol, int cg_maxit, double eps, long max_steps,
+                       double *U, double *W, long *steps_out, double *g_out, double *g_hist,
+                       double *tau_hist)
+{
+    long n = cube(m);
+    double *Z = malloc(sizeof(double) * n * N), *Un = malloc(sizeof(double) * n * N);
+    orc_adapt ad = {tau_max, 0.8, 1.05, orc_lambda1_lower_bound(m, lo, hi, V, sigma), 0.0, 1};
+    int have_z = 0, st = ORC_OK;
+    long step = 0;
+    double g = INFINITY, tau_used = 0.0;
+    for (;;) {
+        st = scheme_step_impl(m, lo, hi, V, sigma, N, tau_max, &ad, &tau_used, cg_rtol, cg_maxit,
+                              U, have_z ? Z : NULL, NULL, W, NULL, &g, NULL, NULL, NULL, Z, Un,
+                              NULL);
+        if (st != ORC_OK) break;
+        if (g_hist) g_hist[step] = g;
+        if (g < eps || step >= max_steps) break;
+        if (tau_hist) tau_hist[step] = tau_used;
         memcpy(U, Un, sizeof(double) * n * N);
         have_z = 1;
         step++;

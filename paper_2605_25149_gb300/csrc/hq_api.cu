@@ -16,6 +16,7 @@
 // one per step (g) and never allocates device memory after hq_init.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -85,6 +86,7 @@ struct hq_ctx {
     GramPlan gplan_uw, gplan_max;
     double *gpart = nullptr;
     float *tcpart = nullptr;   // tensor-core Gram partials (HQ_MIXED)
+    unsigned char *tcimg = nullptr;   // split small matrix of the tensor-core block products
     TallPlan tplan;
     double *tpart = nullptr;   // gy x N
     double *G2 = nullptr, *Mw = nullptr, *XY = nullptr, *C = nullptr, *T1 = nullptr;
@@ -93,14 +95,18 @@ struct hq_ctx {
     double *eigwork = nullptr, *evals = nullptr, *mu = nullptr, *lam_p = nullptr;
     double *lam_r = nullptr, *resn = nullptr, *scal = nullptr, *signwork = nullptr;
     int *status = nullptr;
+    double *vn[3] = {nullptr, nullptr, nullptr};   // FP64 n-vectors (density, adjoint)
+    double *pvec = nullptr;                        // power-iteration vector (N)
     // host state
     bool have_V = false, have_U = false, w_valid = false, z_valid = false;
     long step = 0;
     double last_g = NAN;
+    double lambda1_lb = 0.0;   // closed-form lower bound of lambda_1(H + sigma)
     std::string err;
     // instrumentation
     long launches[HQ_K_NCLASS] = {};
     double work[HQ_K_NCLASS] = {};
+    long stat_solves = 0, stat_iters = 0;
     bool timing = false;
     std::vector<cudaEvent_t> evpool;
     size_t evused = 0;
@@ -303,10 +309,13 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
     sc.iters = cv.take<int>(sizeof(int) * N);
     sc.num_active = cv.take<int>(sizeof(int) * 4);
     sc.status = cv.take<int>(sizeof(int) * 4);
-    const int gy0 = lev[0].g.gy;
+    // partial rows: the working-precision geometry of the finest level, or the
+    // FP64 geometry used by the FP64 extraction / monitoring kernels
+    const int gy0 = std::max(lev[0].g.gy, make_geom(m, N, 8).gy);
     double *part = cv.take<double>(sizeof(double) * (size_t)gy0 * N);
     double *part2 = cv.take<double>(sizeof(double) * (size_t)gy0 * N);
     float *tcpart = mixed ? cv.take<float>(gram_tc_partial_bytes(n, 2 * N)) : nullptr;
+    unsigned char *tcimg = mixed ? cv.take<unsigned char>(tall_tc_image_bytes(N, N, N)) : nullptr;
     GramPlan guw = make_gram_plan(n, 2 * N, 2 * N, true);
     GramPlan gmax = make_gram_plan(n, 2 * N, 2 * N, false);
     double *gpart = cv.take<double>(std::max(gram_partial_bytes(guw), gram_partial_bytes(gmax)));
@@ -338,14 +347,20 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
     double *scal = cv.take<double>(sizeof(double) * 16);
     double *signwork = cv.take<double>(sizeof(double) * 2 * 64 * N);
     int *status = cv.take<int>(sizeof(int) * 4);
+    double *vn0 = cv.take<double>(sizeof(double) * n);
+    double *vn1 = cv.take<double>(sizeof(double) * n);
+    double *vn2 = cv.take<double>(sizeof(double) * n);
+    double *pvec = cv.take<double>(sizeof(double) * N);
     if (x) {
+        x->pvec = pvec;
+        x->vn[0] = vn0; x->vn[1] = vn1; x->vn[2] = vn2;
         x->U = U; x->W = W; x->Uh = Uh; x->Z = Z; x->R = R; x->Zp = Zp; x->P = P; x->Q = Q;
         x->Tt = Tt; x->E1 = E1; x->E2 = E2; x->E3 = E3;
         x->L = L;
         for (int l = 0; l < L; l++) x->lev[l] = lev[l];
         x->nc = nc; x->Acoarse = Acoarse; x->Ainv = Ainv; x->xt1 = xt1; x->xt2 = xt2;
         x->sc = sc; x->part = part; x->part2 = part2;
-        x->gplan_uw = guw; x->gplan_max = gmax; x->gpart = gpart; x->tcpart = tcpart;
+        x->gplan_uw = guw; x->gplan_max = gmax; x->gpart = gpart; x->tcpart = tcpart; x->tcimg = tcimg;
         x->tplan = tp; x->tpart = tpart;
         x->G2 = G2; x->Mw = Mw; x->XY = XY; x->C = Cc; x->T1 = T1; x->Shat = Shat; x->Om = Om;
         x->Msm = Msm; x->Ksm = Ksm; x->Ssm = Ssm; x->Lm = Lm; x->Cm = Cm; x->Ym = Ym;
@@ -586,11 +601,13 @@ hq_status pcg(hq_ctx *x, const T *B, T *X, double rtol, int maxit, int *iters_ho
     HQ_CUDA(cudaMemcpyAsync(&nact, sc.num_active, sizeof(int), cudaMemcpyDeviceToHost, x->st));
     HQ_CUDA(cudaStreamSynchronize(x->st));
     hq_status st = HQ_OK;
+    long it_done = 0;
     if (nact > 0 && maxit > 0) {
         HQ_TRY(vcycle<T>(x, 0, R, Zp, Tt, false, x->part));
         launch_finalize(FIN_RZ, N, g.gy, x->part, nullptr, sc, rtol, x->st);
         HQ_TRY(copy_blk<T>(x, P, Zp, (size_t)x->n * N));
         HQ_TRY(pcg_half<T>(x, X, rtol));   // iteration 1
+        it_done = 1;
         HQ_CUDA(cudaMemcpyAsync(&nact, sc.num_active, sizeof(int), cudaMemcpyDeviceToHost, x->st));
         HQ_CUDA(cudaStreamSynchronize(x->st));
         if (nact > 0 && maxit > 1) {
@@ -602,12 +619,14 @@ hq_status pcg(hq_ctx *x, const T *B, T *X, double rtol, int maxit, int *iters_ho
                 HQ_CUDA(cudaMemcpyAsync(it, sc.num_active, sizeof(it), cudaMemcpyDeviceToHost, x->st));
                 HQ_CUDA(cudaStreamSynchronize(x->st));
                 nact = it[0];
+                it_done = it[1];
                 for (int i = 0; i < HQ_K_NCLASS; i++)
                     x->launches[i] += pg->body_launches[i] * (long)(it[1] - 1);
             } else {
                 for (int it = 2; it <= maxit; it++) {
                     HQ_TRY(pcg_body<T>(x, X, rtol));
                     HQ_TRY(pcg_half<T>(x, X, rtol));
+                    it_done = it;
                     HQ_CUDA(cudaMemcpyAsync(&nact, sc.num_active, sizeof(int), cudaMemcpyDeviceToHost, x->st));
                     HQ_CUDA(cudaStreamSynchronize(x->st));
                     if (nact == 0) break;
@@ -616,6 +635,8 @@ hq_status pcg(hq_ctx *x, const T *B, T *X, double rtol, int maxit, int *iters_ho
         }
         if (nact > 0 && rtol > 0.0) st = HQ_ERR_NOT_CONVERGED;
     }
+    x->stat_solves++;
+    x->stat_iters += it_done;
     if (iters_host) HQ_CUDA(cudaMemcpyAsync(iters_host, sc.iters, sizeof(int) * N, cudaMemcpyDeviceToHost, x->st));
     HQ_TRY(sync_status(x, sc.status, "inner PCG"));
     if (st == HQ_ERR_NOT_CONVERGED) return fail(x, st, "inner PCG reached cg_maxit");
@@ -636,6 +657,27 @@ void gram_sym<float>(hq_ctx *x, const float *X1, int n1, const float *X2, int n2
     launch_gram_tc(x->n, X1, n1, X2, n2, x->h3, x->tcpart, out, x->status, x->st);
 }
 
+// Out = A1 M1 (+ A2 M2) (+ Cin) (n x N); part_sq: sum of squares of Out into
+// x->tpart and the number of partials into *np.  FP64: SIMT register-tiled;
+// HQ_MIXED: tcgen05 3xTF32.
+template <typename T>
+void block_gemm(hq_ctx *x, const T *A1, int k1, const double *M1, const T *A2, int k2,
+                const double *M2, const T *Cin, T *Out, bool sq, int *np);
+template <>
+void block_gemm<double>(hq_ctx *x, const double *A1, int k1, const double *M1, const double *A2,
+                        int k2, const double *M2, const double *Cin, double *Out, bool sq, int *np) {
+    TallPlan tp = make_tall_plan(x->n, x->N, k1, k2);
+    launch_tall_gemm<double>(tp, A1, M1, A2, M2, Cin, Out, sq ? x->tpart : nullptr, x->st);
+    if (np) *np = tp.gy * tp.gx;
+}
+template <>
+void block_gemm<float>(hq_ctx *x, const float *A1, int k1, const double *M1, const float *A2,
+                       int k2, const double *M2, const float *Cin, float *Out, bool sq, int *np) {
+    launch_tall_tc(x->n, A1, k1, M1, A2, k2, M2, x->N, Cin, Out, sq ? x->tpart : nullptr, x->tcimg,
+                   x->status, x->st);
+    if (np) *np = tall_tc_partials(x->n, x->N);
+}
+
 // ---------------------------------------------------------------------------
 // the scheme
 // ---------------------------------------------------------------------------
@@ -651,11 +693,20 @@ hq_status phase_a(hq_ctx *x) {
     gram_sym<T>(x, U, N, W, N, x->G2);
     // Msm = -Pwu (rows N..2N-1, columns 0..N-1 of G2); g = || W - U Pwu ||_h
     launch_extract(N, N, -1.0, x->G2 + (size_t)N * 2 * N, 2 * N, x->Msm, N, x->st);
-    TallPlan tp = make_tall_plan(x->n, N, N, 0);
-    launch_tall_gemm<T>(tp, U, x->Msm, nullptr, nullptr, W, nullptr, x->tpart, x->st);
-    launch_sum_sqrt(tp.gy * tp.gx, x->tpart, x->h3, x->scal, x->st);
+    int np = 0;
+    block_gemm<T>(x, U, N, x->Msm, nullptr, 0, nullptr, W, nullptr, true, &np);
+    launch_sum_sqrt(np, x->tpart, x->h3, x->scal, x->st);
     HQ_TRY(check_launch(x));
     x->w_valid = true;
+    return HQ_OK;
+}
+
+// restart the adaptive time step (first step from the lower bound)
+hq_status reset_tau(hq_ctx *x) {
+    double st[3] = {x->cfg.tau, x->cfg.tau, 1.0};
+    HQ_CUDA(cudaMemcpyAsync(x->scal + 8, st, sizeof(st), cudaMemcpyHostToDevice, x->st));
+    HQ_CUDA(cudaMemsetAsync(x->pvec, 0, sizeof(double) * x->N, x->st));
+    HQ_CUDA(cudaStreamSynchronize(x->st));
     return HQ_OK;
 }
 
@@ -675,21 +726,43 @@ hq_status phase_b(hq_ctx *x) {
     const size_t cnt = (size_t)x->n * N;
     const double tau = x->cfg.tau;
     T *U = (T *)x->U, *W = (T *)x->W, *Uh = (T *)x->Uh, *Z = (T *)x->Z;
-    launch_predictor_solve(N, tau, x->G2, x->Mw, x->XY, x->C, x->status, x->st);
-    TallPlan tp2 = make_tall_plan(x->n, N, N, N);
-    launch_tall_gemm<T>(tp2, U, x->C, W, x->C + (size_t)N * N, nullptr, Uh, nullptr, x->st);
+    const double *tau_dev = nullptr;
+    if (x->cfg.adaptive_tau) {
+        // tau_n from the Gram of step n (Ritz estimate of lambda_1, lambda_max<U,U>)
+        launch_extract(N, N, 1.0, x->G2, 2 * N, x->Ssm, N, x->st);
+        launch_extract(N, N, 1.0, x->G2 + (size_t)N * 2 * N, 2 * N, x->Ksm, N, x->st);
+        launch_rr_reduce(N, x->Ksm, x->Ssm, x->Lm, x->Cm, x->status, x->st);
+        launch_top_eig(N, x->Cm, N, x->pvec, x->scal + 12, x->st);
+        launch_gersh(N, x->Ssm, N, x->scal + 13, x->st);
+        const double tmax = x->cfg.tau_max > 0.0 ? x->cfg.tau_max : 1e300;
+        launch_adapt_tau(x->scal + 12, x->scal + 13, tmax, 0.8, 1.05, x->lambda1_lb, x->scal + 8,
+                         x->st);
+        tau_dev = x->scal + 8;
+    }
+    launch_predictor_solve(N, tau, x->G2, x->Mw, x->XY, x->C, x->status, x->st, tau_dev);
+    block_gemm<T>(x, U, N, x->C, W, N, x->C + (size_t)N * N, nullptr, Uh, false, nullptr);
     // Shat = C^T G2 C, Om = Shat - I
     launch_small_gemm(2 * N, N, 2 * N, 1.0, x->G2, 2 * N, false, x->C, N, false, 0.0, x->T1, N,
                       x->st);
     launch_small_gemm(N, N, 2 * N, 1.0, x->C, N, true, x->T1, N, false, 0.0, x->Shat, N, x->st);
     // Om = -tau (Shat - I)
-    launch_extract(N, N, -tau, x->Shat, N, x->Om, N, x->st);
-    launch_add_diag(N, x->Om, tau, x->st);
+    launch_corrector_matrix(N, x->Shat, tau_dev, tau, x->Om, x->st);
+    if (x->cfg.z_warm_start) {
+        // G Uh = W C1 + G W C2 and G W ~ W M with M = S^{-1} Puw (exact when
+        // span(U) is G-invariant): start from Z0 = W (C1 + M C2)
+        launch_chol_solve(N, x->G2, 2 * N, x->G2 + N, 2 * N, x->Lm, x->Ym, x->status, x->st);
+        launch_extract(N, N, 1.0, x->C, N, x->Cm, N, x->st);
+        launch_small_gemm(N, N, N, 1.0, x->Ym, N, false, x->C + (size_t)N * N, N, false, 1.0,
+                          x->Cm, N, x->st);
+    }
     HQ_TRY(sync_status(x, x->status, "predictor system"));
-    HQ_CUDA(cudaMemsetAsync(Z, 0, cnt * sizeof(T), x->st));
+    if (x->cfg.z_warm_start) {
+        block_gemm<T>(x, W, N, x->Cm, nullptr, 0, nullptr, nullptr, Z, false, nullptr);
+    } else {
+        HQ_CUDA(cudaMemsetAsync(Z, 0, cnt * sizeof(T), x->st));
+    }
     HQ_TRY(pcg<T>(x, Uh, Z, x->cfg.cg_rtol, x->cfg.cg_maxit, nullptr));
-    TallPlan tp1 = make_tall_plan(x->n, N, N, 0);
-    launch_tall_gemm<T>(tp1, Z, x->Om, nullptr, nullptr, Uh, U, nullptr, x->st);
+    block_gemm<T>(x, Z, N, x->Om, nullptr, 0, nullptr, Uh, U, false, nullptr);
     HQ_TRY(check_launch(x));
     x->w_valid = false;
     x->z_valid = true;
@@ -734,6 +807,7 @@ hq_status set_potential_impl(hq_ctx *x, const double *V, int on_device) {
     double s = std::sin(PI / (2.0 * (x->m + 1)));
     double lb = 3.0 * (2.0 / (x->h * x->h)) * s * s + mm[0];
     x->sigma = std::isnan(x->cfg.shift) ? (lb > 0.0 ? 0.0 : 1.0 - lb) : x->cfg.shift;
+    x->lambda1_lb = lb + x->sigma;
     for (int l = 1; l < x->L; l++) {
         launch_coarse_potential(x->lev[l - 1].m, x->lev[l - 1].V, x->lev[l].m, x->lev[l].V, x->st);
         launch_xfer_tables(x->lev[l - 1].m, x->lev[l].m, x->lev[l - 1].tab, x->st);
@@ -753,7 +827,7 @@ hq_status set_potential_impl(hq_ctx *x, const double *V, int on_device) {
     x->have_V = true;
     x->w_valid = x->z_valid = false;
     x->step = 0;
-    return HQ_OK;
+    return reset_tau(x);
 }
 
 template <typename T>
@@ -807,7 +881,7 @@ hq_status set_initial_impl(hq_ctx *x, const double *U0, int on_device) {
     x->have_U = true;
     x->w_valid = x->z_valid = false;
     x->step = 0;
-    return HQ_OK;
+    return reset_tau(x);
 }
 
 template <typename T>
@@ -912,6 +986,45 @@ hq_status eigen_impl(hq_ctx *x, double *evals_paper, double *evals_rr, double *e
 }
 
 template <typename T>
+hq_status monitor_impl(hq_ctx *x, double *energy, double *onorm, double *smin, double *smax) {
+    HQ_TRY(need_ready(x));
+    HQ_TRY(clear_status(x));
+    const int N = x->N;
+    const size_t cnt = (size_t)x->n * N;
+    double *U64 = (double *)x->U;
+    if (x->mixed) {
+        launch_convert_f2d(cnt, (const float *)x->U, x->E1, x->st);
+        U64 = x->E1;
+    }
+    Level &v0 = x->lev[0];
+    GridGeom g64 = make_geom(x->m, N, 8);
+    // tr(U^T (H + sigma) U) as per-column partial dots, fused into the operator
+    launch_apply<double>(g64, v0.D, v0.c, U64, x->E2, x->part, x->st);
+    GramPlan gs = make_gram_plan(x->n, N, N, true);
+    launch_gram<double>(gs, U64, N, nullptr, 0, U64, N, nullptr, 0, x->h3, x->gpart, x->Ssm, x->st);
+    launch_monitor_finish(g64.gy * N, x->part, x->h3, N, x->Ssm, x->scal + 4, x->st);
+    launch_sym_eig(N, x->Ssm, x->eigwork, x->evals, nullptr, x->st);
+    double e2[2], ev_lo = 0, ev_hi = 0;
+    HQ_CUDA(cudaMemcpyAsync(e2, x->scal + 4, sizeof(e2), cudaMemcpyDeviceToHost, x->st));
+    HQ_CUDA(cudaMemcpyAsync(&ev_lo, x->evals, sizeof(double), cudaMemcpyDeviceToHost, x->st));
+    HQ_CUDA(cudaMemcpyAsync(&ev_hi, x->evals + N - 1, sizeof(double), cudaMemcpyDeviceToHost, x->st));
+    HQ_CUDA(cudaStreamSynchronize(x->st));
+    HQ_TRY(check_launch(x));
+    // (1/2) h^3 tr(U^T H U) = (1/2) (h^3 tr(U^T (H + sigma) U) - sigma tr<U,U>)
+    double trS = 0.0;
+    {
+        std::vector<double> S((size_t)N * N);
+        HQ_CUDA(cudaMemcpy(S.data(), x->Ssm, sizeof(double) * N * N, cudaMemcpyDeviceToHost));
+        for (int i = 0; i < N; i++) trS += S[(size_t)i * N + i];
+    }
+    if (energy) *energy = 0.5 * (e2[0] - x->sigma * trS);
+    if (onorm) *onorm = e2[1];
+    if (smin) *smin = ev_lo;
+    if (smax) *smax = ev_hi;
+    return HQ_OK;
+}
+
+template <typename T>
 hq_status trace_impl(hq_ctx *x, void *W, double *gram, double *g, double *XY, void *Uh,
                      double *Shat, void *Z, void *Unew) {
     HQ_TRY(need_ready(x));
@@ -940,6 +1053,137 @@ hq_status level_check(hq_ctx *x, int level, bool need_next) {
     if (level < 0 || level >= x->L || (need_next && level + 1 >= x->L))
         return fail(x, HQ_ERR_ARG, "multigrid level out of range");
     return HQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// differentiation (FP64 contexts)
+// ---------------------------------------------------------------------------
+// y <- P y = y - u (h^3 u^T y), u = Ritz vectors (in Uh)
+hq_status project(hq_ctx *x, double *y) {
+    const int N = x->N;
+    const double *u = (const double *)x->Uh;
+    GramPlan gp = make_gram_plan(x->n, N, N, false);
+    launch_gram<double>(gp, u, N, nullptr, 0, y, N, nullptr, 0, x->h3, x->gpart, x->Ksm, x->st);
+    launch_extract(N, N, -1.0, x->Ksm, N, x->Msm, N, x->st);
+    block_gemm<double>(x, u, N, x->Msm, nullptr, 0, nullptr, y, y, false, nullptr);
+    return check_launch(x);
+}
+
+hq_status need_fp64(hq_ctx *x) {
+    if (x->mixed) return fail(x, HQ_ERR_STATE, "differentiation needs an HQ_FP64 context");
+    return need_ready(x);
+}
+
+// Ritz vectors into Uh, Ritz values into lam_r (device)
+hq_status ritz(hq_ctx *x) {
+    return eigen_impl<double>(x, nullptr, nullptr, (double *)x->Uh, 1, nullptr);
+}
+
+hq_status density_impl(hq_ctx *x, double *rho_out, int on_device) {
+    HQ_TRY(need_fp64(x));
+    HQ_TRY(ritz(x));
+    launch_rowreduce(0, x->n, x->N, (const double *)x->Uh, nullptr, nullptr, 1.0, x->vn[0], x->st);
+    HQ_CUDA(cudaMemcpyAsync(rho_out, x->vn[0], sizeof(double) * x->n, kind_out(on_device), x->st));
+    HQ_CUDA(cudaStreamSynchronize(x->st));
+    return check_launch(x);
+}
+
+hq_status grad_eigs_impl(hq_ctx *x, const double *w, double *dV, int on_device) {
+    HQ_TRY(need_fp64(x));
+    HQ_TRY(ritz(x));
+    const double *wd = nullptr;
+    if (w) {
+        HQ_CUDA(cudaMemcpyAsync(x->mu, w, sizeof(double) * x->N, cudaMemcpyHostToDevice, x->st));
+        wd = x->mu;
+    }
+    launch_rowreduce(0, x->n, x->N, (const double *)x->Uh, nullptr, wd, x->h3, x->vn[0], x->st);
+    HQ_CUDA(cudaMemcpyAsync(dV, x->vn[0], sizeof(double) * x->n, kind_out(on_device), x->st));
+    HQ_CUDA(cudaStreamSynchronize(x->st));
+    return check_launch(x);
+}
+
+hq_status grad_density_impl(hq_ctx *x, const double *G, const double *rho_target, int on_device,
+                            double rtol, int maxit, double *dV, double *loss, int *iters) {
+    HQ_TRY(need_fp64(x));
+    HQ_TRY(clear_status(x));
+    HQ_TRY(ritz(x));
+    const int N = x->N;
+    const long n = x->n;
+    const size_t cnt = (size_t)n * N;
+    const double *u = (const double *)x->Uh;
+    double *Gd = x->vn[1];
+    if (rho_target) {
+        // G = h^3 (rho - rho_target), L = (1/2) h^3 sum (rho - rho_target)^2
+        launch_rowreduce(0, n, N, u, nullptr, nullptr, 1.0, x->vn[0], x->st);
+        HQ_CUDA(cudaMemcpyAsync(x->vn[2], rho_target, sizeof(double) * n, kind_in(on_device), x->st));
+        int np = launch_diff_sq(n, x->vn[0], x->vn[2], Gd, x->tpart, x->st);
+        launch_monitor_finish(np, x->tpart, 0.5 * x->h3, 0, nullptr, x->scal + 6, x->st);
+        launch_dscale((int)n, x->h3, Gd, Gd, x->st);
+    } else {
+        if (!G) return fail(x, HQ_ERR_ARG, "G and rho_target are both null");
+        HQ_CUDA(cudaMemcpyAsync(Gd, G, sizeof(double) * n, kind_in(on_device), x->st));
+    }
+    // right-hand sides b_i = P (G o u_i) in Z; shifts s_i = lambda_i + sigma
+    double *b = (double *)x->Z, *xi = (double *)x->W;
+    launch_scale_rows(n, N, Gd, u, b, x->st);
+    HQ_TRY(project(x, b));
+    launch_add_scalar(N, x->lam_r, x->sigma, x->mu, x->st);
+    // projected block PCG on (A - s_i) with preconditioner P M P
+    Level &v = x->lev[0];
+    const GridGeom &g = v.g;
+    double *R = (double *)x->R, *Zp = (double *)x->Zp, *P = (double *)x->P, *Q = (double *)x->Q,
+           *Tt = (double *)x->Tt;
+    PcgScalars sc = x->sc;
+    HQ_CUDA(cudaMemsetAsync(xi, 0, cnt * sizeof(double), x->st));
+    HQ_TRY(copy_blk<double>(x, R, b, cnt));
+    HQ_CUDA(cudaMemsetAsync(sc.num_active, 0, sizeof(int), x->st));
+    launch_dot<double>(g, R, R, x->part, x->st);
+    launch_dot<double>(g, b, b, x->part2, x->st);
+    launch_finalize(FIN_BNORM_RNORM, N, g.gy, x->part, x->part2, sc, rtol, x->st);
+    int nact = 0, it = 0;
+    HQ_CUDA(cudaMemcpyAsync(&nact, sc.num_active, sizeof(int), cudaMemcpyDeviceToHost, x->st));
+    HQ_CUDA(cudaStreamSynchronize(x->st));
+    if (nact > 0) {
+        HQ_TRY(vcycle<double>(x, 0, R, Zp, Tt, false, nullptr));
+        HQ_TRY(project(x, Zp));
+        launch_dot<double>(g, R, Zp, x->part, x->st);
+        launch_finalize(FIN_RZ, N, g.gy, x->part, nullptr, sc, rtol, x->st);
+        HQ_TRY(copy_blk<double>(x, P, Zp, cnt));
+        for (it = 1; it <= maxit; it++) {
+            launch_apply<double>(g, v.D, v.c, P, Q, nullptr, x->st);
+            launch_shift_cols(n, N, x->mu, P, Q, x->st);
+            HQ_TRY(project(x, Q));
+            launch_dot<double>(g, P, Q, x->part, x->st);
+            launch_finalize(FIN_ALPHA, N, g.gy, x->part, nullptr, sc, rtol, x->st);
+            launch_pcg_xr<double>(g, sc.alpha, P, Q, xi, R, x->part, v.wD, nullptr, x->st);
+            HQ_CUDA(cudaMemsetAsync(sc.num_active, 0, sizeof(int), x->st));
+            launch_finalize(FIN_RR, N, g.gy, x->part, nullptr, sc, rtol, x->st);
+            HQ_CUDA(cudaMemcpyAsync(&nact, sc.num_active, sizeof(int), cudaMemcpyDeviceToHost, x->st));
+            HQ_CUDA(cudaStreamSynchronize(x->st));
+            if (nact == 0) break;
+            HQ_TRY(vcycle<double>(x, 0, R, Zp, Tt, false, nullptr));
+            HQ_TRY(project(x, Zp));
+            launch_dot<double>(g, R, Zp, x->part, x->st);
+            launch_finalize(FIN_BETA, N, g.gy, x->part, nullptr, sc, rtol, x->st);
+            launch_pcg_p<double>(g, sc.beta, Zp, P, x->st);
+        }
+    }
+    HQ_TRY(sync_status(x, sc.status, "adjoint PCG"));
+    if (nact > 0) return fail(x, HQ_ERR_NOT_CONVERGED, "adjoint PCG reached maxit");
+    // dL/dV = -2 sum_i u_i o xi_i
+    launch_rowreduce(1, n, N, u, xi, nullptr, -2.0, x->vn[0], x->st);
+    HQ_CUDA(cudaMemcpyAsync(dV, x->vn[0], sizeof(double) * n, kind_out(on_device), x->st));
+    if (loss) {
+        *loss = 0.0;
+        if (rho_target)
+            HQ_CUDA(cudaMemcpyAsync(loss, x->scal + 6, sizeof(double), cudaMemcpyDeviceToHost, x->st));
+    }
+    if (iters) *iters = it;
+    HQ_CUDA(cudaStreamSynchronize(x->st));
+    // the step buffers W and Z now hold adjoint data
+    x->w_valid = false;
+    x->z_valid = false;
+    return check_launch(x);
 }
 
 #define HQ_DISPATCH(x, fn, ...) ((x)->mixed ? fn<float>(__VA_ARGS__) : fn<double>(__VA_ARGS__))
@@ -976,6 +1220,16 @@ hq_status gram_impl(hq_ctx *x, const void *A, int Na, const void *B, int Nb, dou
     launch_gram<T>(gp, (const T *)A, Na, nullptr, 0, (const T *)B, Nb, nullptr, 0, w, x->gpart, out, x->st);
     return check_launch(x);
 }
+template <typename T>
+hq_status block_gemm_impl(hq_ctx *x, const void *A1, int k1, const double *M1, const void *A2,
+                          int k2, const double *M2, const void *Cin, void *Out) {
+    HQ_TRY(clear_status(x));
+    block_gemm<T>(x, (const T *)A1, k1, M1, (const T *)A2, k2, M2, (const T *)Cin, (T *)Out, false,
+                  nullptr);
+    HQ_TRY(check_launch(x));
+    return sync_status(x, x->status, "block gemm");
+}
+
 template <typename T>
 hq_status smooth_impl(hq_ctx *x, int l, const void *r, const void *zin, void *zout) {
     Level &v = x->lev[l];
@@ -1052,6 +1306,9 @@ void hq_default_config(hq_config *c) {
     c->mg_coarsest = 4;
     c->mg_omega = 0.8;
     c->timeout_s = 0.0;
+    c->z_warm_start = 1;
+    c->adaptive_tau = 0;
+    c->tau_max = 0.0;
 }
 
 size_t hq_workspace_bytes(const hq_config *cfg) {
@@ -1147,6 +1404,42 @@ hq_status hq_eigenpairs(hq_ctx *x, double *evals_paper, double *evals_rr, double
     HQ_API_END
 }
 
+hq_status hq_monitor(hq_ctx *x, double *energy, double *onorm, double *smin, double *smax) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    return HQ_DISPATCH(x, monitor_impl, x, energy, onorm, smin, smax);
+    HQ_API_END
+}
+
+hq_status hq_density(hq_ctx *x, double *rho_out, int on_device) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    if (!rho_out) return fail(x, HQ_ERR_ARG, "rho_out is null");
+    return density_impl(x, rho_out, on_device);
+    HQ_API_END
+}
+
+hq_status hq_grad_eigs(hq_ctx *x, const double *w, double *dV, int on_device) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    if (!dV) return fail(x, HQ_ERR_ARG, "dV is null");
+    return grad_eigs_impl(x, w, dV, on_device);
+    HQ_API_END
+}
+
+hq_status hq_grad_density(hq_ctx *x, const double *G, const double *rho_target, int on_device,
+                          double rtol, int maxit, double *dV, double *loss, int *iters) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    if (!dV || !(rtol > 0.0) || maxit < 1) return fail(x, HQ_ERR_ARG, "bad argument");
+    return grad_density_impl(x, G, rho_target, on_device, rtol, maxit, dV, loss, iters);
+    HQ_API_END
+}
+
 hq_status hq_get_state(hq_ctx *x, double *U, double *Zwarm, int on_device, long *step) {
     HQ_API_BEGIN
     HQ_TRY(guard(x));
@@ -1165,6 +1458,20 @@ hq_status hq_set_state(hq_ctx *x, const double *U, const double *Zwarm, int on_d
     if (!U || step < 0) return fail(x, HQ_ERR_ARG, "U is null or step < 0");
     HQ_TRY(HQ_DISPATCH(x, set_state_impl, x, U, Zwarm, on_device));
     x->step = step;
+    return HQ_OK;
+    HQ_API_END
+}
+
+hq_status hq_time_step(hq_ctx *x, double *tau) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    if (!tau) return fail(x, HQ_ERR_ARG, "tau is null");
+    if (!x->cfg.adaptive_tau) {
+        *tau = x->cfg.tau;
+        return HQ_OK;
+    }
+    HQ_CUDA(cudaMemcpyAsync(tau, x->scal + 8, sizeof(double), cudaMemcpyDeviceToHost, x->st));
+    HQ_CUDA(cudaStreamSynchronize(x->st));
     return HQ_OK;
     HQ_API_END
 }
@@ -1217,6 +1524,18 @@ hq_status hq_gram(hq_ctx *x, const void *A, int Na, const void *B, int Nb, doubl
     if (!A || !B || !out || Na < 1 || Nb < 1 || Na > 2 * x->N || Nb > 2 * x->N)
         return fail(x, HQ_ERR_ARG, "bad operand");
     return HQ_DISPATCH(x, gram_impl, x, A, Na, B, Nb, w, out);
+    HQ_API_END
+}
+
+hq_status hq_block_gemm(hq_ctx *x, const void *A1, int k1, const double *M1, const void *A2,
+                        int k2, const double *M2, const void *Cin, void *Out) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    if (!A1 || !M1 || !Out || k1 < 1 || k1 > x->N || k2 < 0 || k2 > x->N || (k2 > 0 && (!A2 || !M2)))
+        return fail(x, HQ_ERR_ARG, "bad operand");
+    return HQ_DISPATCH(x, block_gemm_impl, x, A1, k1, M1, k2 > 0 ? A2 : nullptr, k2,
+                       k2 > 0 ? M2 : nullptr, Cin, Out);
     HQ_API_END
 }
 
@@ -1287,6 +1606,7 @@ hq_status hq_profile(hq_ctx *x, int timing) {
         x->launches[i] = 0;
         x->work[i] = 0.0;
     }
+    x->stat_solves = x->stat_iters = 0;
     x->timing = timing != 0;
     x->evused = 0;
     x->evrec.clear();
@@ -1311,6 +1631,13 @@ hq_status hq_profile_read(hq_ctx *x, long *launches, double *ms, double *element
     }
     return HQ_OK;
     HQ_API_END
+}
+
+hq_status hq_pcg_stats(hq_ctx *x, long *solves, long *iterations) {
+    HQ_TRY(guard(x));
+    if (solves) *solves = x->stat_solves;
+    if (iterations) *iterations = x->stat_iters;
+    return HQ_OK;
 }
 
 const char *hq_last_error(hq_ctx *x) { return x ? x->err.c_str() : "null context"; }

@@ -114,6 +114,17 @@ void launch_finalize(int mode, int N, int gy, const double *part, const double *
 void launch_pcg_cond(const int *num_active, int *iter, int maxit, cudaGraphConditionalHandle h,
                      cudaStream_t s);
 
+// adjoint row kernels (FP64): mode 0 out[p] = scale sum_c w_c u_pc^2,
+// mode 1 out[p] = scale sum_c u_pc v_pc
+void launch_rowreduce(int mode, long n, int N, const double *u, const double *v, const double *w,
+                      double scale, double *out, cudaStream_t s);
+void launch_scale_rows(long n, int N, const double *g, const double *u, double *y, cudaStream_t s);
+void launch_shift_cols(long n, int N, const double *sft, const double *x, double *y,
+                       cudaStream_t s);
+// d = a - b, returns the number of partial sums of d^2 written to part
+int launch_diff_sq(long n, const double *a, const double *b, double *d, double *part,
+                   cudaStream_t s);
+
 // setup
 void launch_coarse_potential(int mf, const double *Vf, int mc, double *Vc, cudaStream_t s);
 void launch_level_diag(long n, const double *V, double sigma, double c, double omega,
@@ -155,6 +166,16 @@ size_t gram_tc_smem_bytes();
 void launch_gram_tc(long n, const float *X1, int n1, const float *X2, int n2, double w,
                     float *partials, double *out, int *status, cudaStream_t s);
 
+// FP32 block x small-matrix product on tcgen05 (3xTF32):
+// Out (n x ncol) = A1 (n x k1) M1 (k1 x ncol) + A2 M2 (+ Cin); M1, M2 FP64
+// row-major, split into the swizzled tf32 hi/lo image (tall_tc_image_bytes);
+// part_sq (nullable): tall_tc_partials(n, ncol) partial sums of squares of Out.
+size_t tall_tc_image_bytes(int k1, int k2, int ncol);
+int tall_tc_partials(long n, int ncol);
+void launch_tall_tc(long n, const float *A1, int k1, const double *M1, const float *A2, int k2,
+                    const double *M2, int ncol, const float *Cin, float *Out, double *part_sq,
+                    unsigned char *image, int *status, cudaStream_t s);
+
 // Out = A1 M1 (+ A2 M2) (+ Cin), M's are FP64 K x Ncol row-major; optional
 // partial sum of squares of Out (one double per CTA, npart entries).
 struct TallPlan {
@@ -178,6 +199,9 @@ void launch_extract(int rows, int cols, double alpha, const double *src, int lds
 // out[i][j] = -Cv[i][j] * (lam[j] + add)   (N x N)
 void launch_scale_cols(int N, const double *Cv, const double *lam, double add, double *out,
                        cudaStream_t s);
+// out[0] = w * sum(part[0..np)); out[1] = ||A - I||_F for N x N A (nullable)
+void launch_monitor_finish(int np, const double *part, double w, int N, const double *A,
+                           double *out, cudaStream_t s);
 // out[0] = sqrt(w * sum(part[0..np)))
 void launch_sum_sqrt(int np, const double *part, double w, double *out, cudaStream_t s);
 // per-column version: part is np x ncol, out[c] = sqrt(w * sum_i part[i*ncol+c])
@@ -193,7 +217,20 @@ void launch_small_gemm(int M, int Ncol, int K, double alpha, const double *A, in
 // and solve by LU with partial pivoting.  Mwork: 4N^2, XY: 2N x N.  Then
 // C = [I - tau Y; tau X] (2N x N).
 void launch_predictor_solve(int N, double tau, const double *G2, double *Mwork, double *XY,
-                            double *C, int *status, cudaStream_t s);
+                            double *C, int *status, cudaStream_t s,
+                            const double *tau_dev = nullptr);
+// largest eigenvalue of sym(A) (N x N, leading dimension lda) -> out[0];
+// vec (N): warm-start vector, updated (all zero: fixed start)
+void launch_top_eig(int N, const double *A, int lda, double *vec, double *out, cudaStream_t s);
+// out[0] = max_i sum_j |A_ij|
+void launch_gersh(int N, const double *A, int lda, double *out, cudaStream_t s);
+// adaptive time step (see hq_config.adaptive_tau): st[0] = tau_n, st[1] = tau_{n-1},
+// st[2] = first-step flag
+void launch_adapt_tau(const double *mm, const double *sm, double tau_max, double c, double gamma,
+                      double lb, double *st, cudaStream_t s);
+// Om = -tau (Shat - I), tau from tau_dev when non-null
+void launch_corrector_matrix(int N, const double *Shat, const double *tau_dev, double tau,
+                             double *Om, cudaStream_t s);
 // A += v I (N x N) in place
 void launch_add_diag(int N, double *A, double v, cudaStream_t s);
 // out = alpha * in  (count values)
@@ -205,6 +242,9 @@ void launch_sym_eig(int N, const double *A, double *work, double *evals, double 
 // Cm = L^{-1} K L^{-T} with S = L L^T; Linv kept in L (lower).  One CTA.
 void launch_rr_reduce(int N, const double *K, const double *S, double *L, double *Cm,
                       int *status, cudaStream_t s);
+// X = A^{-1} B for SPD A by Cholesky (one CTA); L: N x N work
+void launch_chol_solve(int N, const double *A, int lda, const double *B, int ldb, double *L,
+                       double *X, int *status, cudaStream_t s);
 // c = L^{-T} y  (columns of Y), Cv output N x N
 void launch_rr_back(int N, const double *L, const double *Y, double *Cv, cudaStream_t s);
 // scale factor 1/sqrt(evals[0]) -> out

@@ -318,9 +318,10 @@ void launch_small_gemm(int M, int Ncol, int K, double alpha, const double *A, in
 }
 
 // Predictor system of Eq. (4.1) (one CTA).
-__global__ void __launch_bounds__(1024) k_predictor_solve(int N, double tau, const double *G2,
+__global__ void __launch_bounds__(1024) k_predictor_solve(int N, double tau_arg, const double *G2,
                                                           double *Mw, double *XY, double *C,
-                                                          int *status) {
+                                                          int *status, const double *tau_dev) {
+    const double tau = tau_dev ? tau_dev[0] : tau_arg;
     extern __shared__ double sh[];
     double *lcol = sh;                       // 2N
     double *rv = sh + 2 * N;                 // 1024 reduction values
@@ -425,9 +426,127 @@ __global__ void __launch_bounds__(1024) k_predictor_solve(int N, double tau, con
 }
 
 void launch_predictor_solve(int N, double tau, const double *G2, double *Mwork, double *XY,
-                            double *C, int *status, cudaStream_t s) {
+                            double *C, int *status, cudaStream_t s, const double *tau_dev) {
     size_t shm = sizeof(double) * (2 * N + 1024) + sizeof(int) * 1024;
-    HQ_LAUNCH(HQ_K_SMALL, k_predictor_solve<<<1, 1024, shm, s>>>(N, tau, G2, Mwork, XY, C, status));
+    HQ_LAUNCH(HQ_K_SMALL, k_predictor_solve<<<1, 1024, shm, s>>>(N, tau, G2, Mwork, XY, C, status,
+                                                                  tau_dev));
+}
+
+// Largest eigenvalue of the symmetric part of A (N x N, leading dimension
+// lda) by power iteration with Rayleigh quotients, one CTA; out[0] = value.
+// vec (N, device): start vector on entry (all zero: a fixed start), final
+// iterate on exit, so successive calls on slowly changing matrices restart
+// close to the answer.
+__global__ void __launch_bounds__(256) k_top_eig(int N, const double *A, int lda, double *vec,
+                                                 double *out) {
+    extern __shared__ double sh[];
+    double *v = sh, *w = sh + N, *red = sh + 2 * N;
+    const int tid = threadIdx.x;
+    __shared__ int fresh;
+    if (tid == 0) {
+        double nv = 0.0;
+        for (int i = 0; i < N; i++) nv += vec[i] * vec[i];
+        fresh = !(nv > 0.0);
+    }
+    __syncthreads();
+    for (int i = tid; i < N; i += blockDim.x) v[i] = fresh ? 1.0 + 0.125 * (double)(i % 7) : vec[i];
+    __syncthreads();
+    double mu = 0.0, mu_prev = 0.0;
+    for (int it = 0; it < 1000; it++) {
+        for (int i = tid; i < N; i += blockDim.x) {
+            double acc = 0.0;
+            for (int j = 0; j < N; j++)
+                acc += 0.5 * (A[(size_t)i * lda + j] + A[(size_t)j * lda + i]) * v[j];
+            w[i] = acc;
+        }
+        __syncthreads();
+        double vw = 0.0, vv = 0.0, ww = 0.0;
+        for (int i = tid; i < N; i += blockDim.x) {
+            vw += v[i] * w[i];
+            vv += v[i] * v[i];
+            ww += w[i] * w[i];
+        }
+        red[tid] = vw;
+        red[256 + tid] = vv;
+        red[512 + tid] = ww;
+        __syncthreads();
+        for (int k = 128; k > 0; k >>= 1) {
+            if (tid < k) {
+                red[tid] += red[tid + k];
+                red[256 + tid] += red[256 + tid + k];
+                red[512 + tid] += red[512 + tid + k];
+            }
+            __syncthreads();
+        }
+        mu = red[0] / red[256];
+        const double nw = sqrt(red[512]);
+        __syncthreads();
+        if (!(nw > 0.0)) break;
+        for (int i = tid; i < N; i += blockDim.x) v[i] = w[i] / nw;
+        __syncthreads();
+        if (it > 1 && fabs(mu - mu_prev) <= 1e-14 * fabs(mu)) break;
+        mu_prev = mu;
+    }
+    for (int i = tid; i < N; i += blockDim.x) vec[i] = v[i];
+    if (tid == 0) out[0] = mu;
+}
+void launch_top_eig(int N, const double *A, int lda, double *vec, double *out, cudaStream_t s) {
+    size_t shm = sizeof(double) * (2 * N + 768);
+    HQ_LAUNCH(HQ_K_SMALL, k_top_eig<<<1, 256, shm, s>>>(N, A, lda, vec, out));
+}
+
+// out[0] = max_i sum_j |A_ij| (N x N, leading dimension lda): Gershgorin bound
+__global__ void k_gersh(int N, const double *A, int lda, double *out) {
+    __shared__ double red[256];
+    double best = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        double r = 0.0;
+        for (int j = 0; j < N; j++) r += fabs(A[(size_t)i * lda + j]);
+        best = fmax(best, r);
+    }
+    red[threadIdx.x] = best;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + k]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0];
+}
+void launch_gersh(int N, const double *A, int lda, double *out, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_SMALL, k_gersh<<<1, 256, 0, s>>>(N, A, lda, out));
+}
+
+// Adaptive time step: st[0] = tau_n written from mu_max = mm[0] (largest Ritz
+// value of G), smax = sm[0] (lambda_max<U,U>) and the previous tau st[1];
+// st[2] != 0 marks the first step (tau_{-1} from the lower bound lb).
+__global__ void k_adapt_tau(const double *mm, const double *sm, double tau_max, double c,
+                            double gamma, double lb, double *st) {
+    const double smax = sm[0];
+    double tau = tau_max;
+    const double cap = c * (1.0 / mm[0]) / smax;
+    if (mm[0] > 0.0 && cap < tau) tau = cap;
+    const double prev = (st[2] != 0.0) ? c * lb / (gamma * smax) : st[1];
+    if (gamma * prev < tau) tau = gamma * prev;
+    st[0] = tau;
+    st[1] = tau;
+    st[2] = 0.0;
+}
+void launch_adapt_tau(const double *mm, const double *sm, double tau_max, double c, double gamma,
+                      double lb, double *st, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_SMALL, k_adapt_tau<<<1, 1, 0, s>>>(mm, sm, tau_max, c, gamma, lb, st));
+}
+
+// Om = -tau (Shat - I) with tau from device memory
+__global__ void k_corrector_matrix(int N, const double *Shat, const double *tau_dev, double tau,
+                                   double *Om) {
+    const double t = tau_dev ? tau_dev[0] : tau;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N * N; i += gridDim.x * blockDim.x)
+        Om[i] = -t * (Shat[i] - ((i / N == i % N) ? 1.0 : 0.0));
+}
+void launch_corrector_matrix(int N, const double *Shat, const double *tau_dev, double tau,
+                             double *Om, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_SMALL, k_corrector_matrix<<<std::min((N * N + 255) / 256, 1024), 256, 0, s>>>(
+                              N, Shat, tau_dev, tau, Om));
 }
 
 __global__ void k_add_diag(int N, double *A, double v) {
@@ -646,6 +765,55 @@ void launch_rr_reduce(int N, const double *K, const double *S, double *L, double
     HQ_LAUNCH(HQ_K_SMALL, k_rr_reduce<<<1, 1024, 0, s>>>(N, K, S, L, Cm, status));
 }
 
+// X = A^{-1} B for SPD A (N x N, leading dimension lda) and N right-hand
+// sides B (leading dimension ldb) by Cholesky; L: N x N work.  One CTA.
+__global__ void __launch_bounds__(1024) k_chol_solve(int N, const double *A, int lda,
+                                                     const double *B, int ldb, double *L,
+                                                     double *X, int *status) {
+    const int tid = threadIdx.x, T = blockDim.x;
+    for (long idx = tid; idx < (long)N * N; idx += T) {
+        int i = (int)(idx / N), j = (int)(idx % N);
+        L[idx] = A[(size_t)i * lda + j];
+        X[idx] = B[(size_t)i * ldb + j];
+    }
+    __syncthreads();
+    for (int k = 0; k < N; k++) {
+        double d = L[(size_t)k * N + k];
+        if (!(d > 0.0)) {
+            if (tid == 0) atomicOr(status, ST_SINGULAR);
+            return;
+        }
+        d = sqrt(d);
+        __syncthreads();
+        for (int i = k + tid; i < N; i += T) L[(size_t)i * N + k] = (i == k) ? d : L[(size_t)i * N + k] / d;
+        __syncthreads();
+        const int r = N - k - 1;
+        for (long idx = tid; idx < (long)r * r; idx += T) {
+            int i = k + 1 + (int)(idx / r), j = k + 1 + (int)(idx % r);
+            if (j > i) continue;
+            L[(size_t)i * N + j] -= L[(size_t)i * N + k] * L[(size_t)j * N + k];
+        }
+        __syncthreads();
+    }
+    // forward then backward substitution, one right-hand side per thread
+    for (int c = tid; c < N; c += T) {
+        for (int i = 0; i < N; i++) {
+            double s = X[(size_t)i * N + c];
+            for (int k = 0; k < i; k++) s -= L[(size_t)i * N + k] * X[(size_t)k * N + c];
+            X[(size_t)i * N + c] = s / L[(size_t)i * N + i];
+        }
+        for (int i = N - 1; i >= 0; i--) {
+            double s = X[(size_t)i * N + c];
+            for (int k = i + 1; k < N; k++) s -= L[(size_t)k * N + i] * X[(size_t)k * N + c];
+            X[(size_t)i * N + c] = s / L[(size_t)i * N + i];
+        }
+    }
+}
+void launch_chol_solve(int N, const double *A, int lda, const double *B, int ldb, double *L,
+                       double *X, int *status, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_SMALL, k_chol_solve<<<1, 1024, 0, s>>>(N, A, lda, B, ldb, L, X, status));
+}
+
 __global__ void k_rr_back(int N, const double *L, const double *Y, double *Cv) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N; e += gridDim.x * blockDim.x) {
         for (int i = N - 1; i >= 0; i--) {
@@ -763,6 +931,43 @@ __global__ void k_scale_cols(int N, const double *Cv, const double *lam, double 
 void launch_scale_cols(int N, const double *Cv, const double *lam, double add, double *out,
                        cudaStream_t s) {
     HQ_LAUNCH(HQ_K_SMALL, k_scale_cols<<<std::min((N * N + 255) / 256, 1024), 256, 0, s>>>(N, Cv, lam, add, out));
+}
+
+// out[0] = w * sum of all np*ncol partials (fixed order); out[1] = ||A - I||_F
+// of the N x N matrix A (nullable)
+__global__ void k_monitor_finish(int np, const double *part, double w, int N, const double *A,
+                                 double *out) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < np; i += 256) s += part[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    double tot = red[0];
+    __syncthreads();
+    double o = 0.0;
+    if (A)
+        for (int i = threadIdx.x; i < N * N; i += 256) {
+            double d = A[i] - ((i / N == i % N) ? 1.0 : 0.0);
+            o += d * d;
+        }
+    red[threadIdx.x] = o;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = w * tot;
+        out[1] = sqrt(red[0]);
+    }
+}
+void launch_monitor_finish(int np, const double *part, double w, int N, const double *A,
+                           double *out, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_REDUCE, k_monitor_finish<<<1, 256, 0, s>>>(np, part, w, N, A, out));
 }
 
 #define HQ_DINST(T)                                                                          \

@@ -354,4 +354,291 @@ void launch_gram_tc(long n, const float *X1, int n1, const float *X2, int n2, do
     HQ_LAUNCH(HQ_K_GRAM, k_gram_tc_reduce<<<p.ntiles, 256, 0, s>>>(p, partials, w, out));
 }
 
+
+
+// ===========================================================================
+// Block x small-matrix products on tcgen05:
+//   Out (n x ncol) = [A1 A2] (n x (k1 + k2)) [M1; M2] (+ Cin), FP32 blocks,
+//   FP64 small matrices, 3xTF32.
+// D = A B with M = 128 grid points per CTA (tile rows), N = NT output columns
+// (NT = min(256, ncol rounded up to 16)), K = the block's columns in slices
+// of 32.  The point rows of a point-major block are already K-major, so an A
+// slice (128 points x 32 columns) is loaded, split into tf32 hi / lo and
+// stored with the 128-byte swizzle exactly as in the Gram kernel.  The small
+// matrix is split once per call by k_split_small into the same swizzled
+// shared-memory image (per column tile and K slice), which each CTA copies
+// with plain 16-byte loads.  Accumulators: TMEM, 128 lanes x NT columns.
+// ===========================================================================
+constexpr int TT_M = 128;
+
+struct TallTcPlan {
+    long n;
+    int k1, k2, kpad, nslices, ncol, nt, ctiles;
+};
+
+TallTcPlan make_tall_tc_plan(long n, int k1, int k2, int ncol) {
+    TallTcPlan p;
+    p.n = n;
+    p.k1 = k1;
+    p.k2 = k2;
+    p.kpad = (k1 + k2 + TC_K - 1) / TC_K * TC_K;
+    p.nslices = p.kpad / TC_K;
+    p.ncol = ncol;
+    // instantiated tile widths (multiples of 16 up to the M = 128 limit of 256)
+    const int widths[6] = {16, 32, 48, 64, 128, 256};
+    p.nt = 256;
+    for (int i = 0; i < 6; i++)
+        if (widths[i] >= ncol) {
+            p.nt = widths[i];
+            break;
+        }
+    p.ctiles = (ncol + p.nt - 1) / p.nt;
+    return p;
+}
+
+size_t tall_tc_image_bytes(int k1, int k2, int ncol) {
+    TallTcPlan p = make_tall_tc_plan(1, k1, k2, ncol);
+    return (size_t)p.ctiles * p.nslices * 2 * p.nt * 128;
+}
+
+// image[(ct * nslices + s)] = { hi: nt rows x 128 B, lo: nt rows x 128 B },
+// row = output column c (within the tile), 32 k values per row, swizzled.
+__global__ void k_split_small(TallTcPlan P, const double *M1, const double *M2,
+                              unsigned char *image) {
+    const long total = (long)P.ctiles * P.nt * P.kpad;
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long)gridDim.x * blockDim.x) {
+        const int k = (int)(idx % P.kpad);
+        const long q = idx / P.kpad;
+        const int r = (int)(q % P.nt);
+        const int ct = (int)(q / P.nt);
+        const int c = ct * P.nt + r;
+        double v = 0.0;
+        if (c < P.ncol) {
+            if (k < P.k1) v = M1[(size_t)k * P.ncol + c];
+            else if (k < P.k1 + P.k2) v = M2[(size_t)(k - P.k1) * P.ncol + c];
+        }
+        const float f = (float)v;
+        const float h = tf32_rna(f);
+        const float l = tf32_rna(f - h);
+        const int s = k / TC_K, kk = k % TC_K;
+        unsigned char *blk = image + ((size_t)ct * P.nslices + s) * 2 * P.nt * 128;
+        const uint32_t off = sw128_offset(r, kk);
+        *reinterpret_cast<float *>(blk + off) = h;
+        *reinterpret_cast<float *>(blk + (size_t)P.nt * 128 + off) = l;
+    }
+}
+
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_tall_tf32x3(TallTcPlan P, const float *__restrict__ A1, const float *__restrict__ A2,
+                  const unsigned char *__restrict__ image, const float *__restrict__ Cin,
+                  float *__restrict__ Out, double *part_sq, int *status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ uint64_t mbar[2];
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;
+    __shared__ double red[TC_THREADS];
+    constexpr int ABYTES = TT_M * 128;           // one operand half (hi or lo): 16 KB
+    constexpr int BBYTES = NT * 128;             // 32 KB for NT = 256
+    constexpr int STAGE = 2 * ABYTES + 2 * BBYTES;
+    constexpr uint32_t TCOLS = NT < 32 ? 32 : (NT <= 32 ? 32 : (NT <= 64 ? 64 : (NT <= 128 ? 128 : 256)));
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long r0 = (long)blockIdx.x * TT_M;
+    const int ct = blockIdx.y;
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_sh)),
+                     "r"(TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sh;
+    const bool vec4 = (P.k1 % 4 == 0) && (P.k2 % 4 == 0) && (((uintptr_t)A1 & 15) == 0) &&
+                      (A2 == nullptr || ((uintptr_t)A2 & 15) == 0);
+
+    // A slice: 128 points x 32 columns; thread t takes float4 q = t + 128 j:
+    // row = q / 8, column quad = (q % 8) * 4
+    float4 ra[8];
+    auto load_a = [&](int s) {
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const int q = tid + TC_THREADS * j;
+            const int row = q >> 3, kq = (q & 7) * 4;
+            const long p = r0 + row;
+            const int k = s * TC_K + kq;
+            if (p < P.n && vec4 && k + 3 < P.k1 + P.k2) {
+                const float *src = k < P.k1 ? A1 + (size_t)p * P.k1 + k
+                                            : A2 + (size_t)p * P.k2 + (k - P.k1);
+                ra[j] = *reinterpret_cast<const float4 *>(src);
+            } else {
+                float v[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int kk = k + u;
+                    v[u] = 0.f;
+                    if (p < P.n && kk < P.k1) v[u] = A1[(size_t)p * P.k1 + kk];
+                    else if (p < P.n && kk < P.k1 + P.k2) v[u] = A2[(size_t)p * P.k2 + (kk - P.k1)];
+                }
+                ra[j] = make_float4(v[0], v[1], v[2], v[3]);
+            }
+        }
+    };
+    auto store_a = [&](unsigned char *hi, unsigned char *lo) {
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const int q = tid + TC_THREADS * j;
+            const int row = q >> 3, kq = (q & 7) * 4;
+            const float v[4] = {ra[j].x, ra[j].y, ra[j].z, ra[j].w};
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const float h = tf32_rna(v[u]);
+                const float l = tf32_rna(v[u] - h);
+                const uint32_t off = sw128_offset(row, kq + u);
+                *reinterpret_cast<float *>(hi + off) = h;
+                *reinterpret_cast<float *>(lo + off) = l;
+            }
+        }
+    };
+    auto copy_b = [&](int s, unsigned char *dst) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(
+            image + ((size_t)ct * P.nslices + s) * 2 * (size_t)BBYTES);
+        uint4 *d = reinterpret_cast<uint4 *>(dst);
+        for (int i = tid; i < 2 * BBYTES / 16; i += TC_THREADS) d[i] = src[i];
+    };
+
+    const uint32_t idesc = idesc_tf32(TT_M, NT);
+    if (P.nslices > 0) load_a(0);
+    for (int s = 0; s < P.nslices; s++) {
+        const int st = s & 1;
+        unsigned char *base = smem + st * STAGE;
+        unsigned char *Ahi = base, *Alo = base + ABYTES, *Bhi = base + 2 * ABYTES,
+                      *Blo = base + 2 * ABYTES + BBYTES;
+        if (s >= 2) {
+            if (!mbar_wait(&mbar[st], (unsigned)(((s - 2) >> 1) & 1))) atomicExch(&abort_sh, 1);
+        }
+        __syncthreads();
+        if (abort_sh) break;
+        store_a(Ahi, Alo);
+        copy_b(s, Bhi);
+        if (s + 1 < P.nslices) load_a(s + 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ahi = smem_u32(Ahi), alo = smem_u32(Alo);
+            const uint32_t bhi = smem_u32(Bhi), blo = smem_u32(Blo);
+#pragma unroll
+            for (int kk = 0; kk < TC_K / 8; kk++) {
+                const uint32_t ko = kk * 32;
+                const uint64_t dah = make_desc_sw128(ahi + ko), dal = make_desc_sw128(alo + ko);
+                const uint64_t dbh = make_desc_sw128(bhi + ko), dbl = make_desc_sw128(blo + ko);
+                mma_tf32(tmem, dah, dbh, idesc, (s > 0 || kk > 0) ? 1u : 0u);
+                mma_tf32(tmem, dah, dbl, idesc, 1u);
+                mma_tf32(tmem, dal, dbh, idesc, 1u);
+            }
+            mma_commit(&mbar[st]);
+        }
+    }
+    bool ok = !abort_sh;
+    if (ok && P.nslices >= 1) {
+        int s = P.nslices - 1;
+        ok = mbar_wait(&mbar[s & 1], (unsigned)((s >> 1) & 1));
+        if (ok && P.nslices >= 2) {
+            s = P.nslices - 2;
+            ok = mbar_wait(&mbar[s & 1], (unsigned)((s >> 1) & 1));
+        }
+    }
+    if (!ok) atomicExch(&abort_sh, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    double sq = 0.0;
+    if (abort_sh) {
+        if (tid == 0) atomicOr(status, ST_TC_TIMEOUT);
+    } else {
+        // epilogue: thread = one point row (TMEM lane), 32 columns per load
+        const long p = r0 + warp * 32 + lane;
+        for (int cb = 0; cb < NT; cb += 32) {
+            float v[32];
+            tmem_ld32<32>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+            if (p < P.n) {
+#pragma unroll
+                for (int j = 0; j < 32; j++) {
+                    const int c = ct * NT + cb + j;
+                    if (cb + j >= NT || c >= P.ncol) continue;
+                    const size_t e = (size_t)p * P.ncol + c;
+                    float o = v[j];
+                    if (Cin) o += Cin[e];
+                    if (Out) Out[e] = o;
+                    sq += (double)o * (double)o;
+                }
+            }
+        }
+    }
+    if (part_sq) {
+        red[tid] = sq;
+        __syncthreads();
+        for (int k = TC_THREADS / 2; k > 0; k >>= 1) {
+            if (tid < k) red[tid] += red[tid + k];
+            __syncthreads();
+        }
+        if (tid == 0) part_sq[(size_t)blockIdx.x * gridDim.y + blockIdx.y] = red[0];
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS)
+                     : "memory");
+}
+
+template <int NT>
+static void run_tall_tc(const TallTcPlan &p, const float *A1, const float *A2,
+                        const unsigned char *image, const float *Cin, float *Out, double *part_sq,
+                        int *status, cudaStream_t s) {
+    const int smem = 2 * (2 * TT_M * 128 + 2 * NT * 128) + 1024;
+    cudaFuncSetAttribute(k_tall_tf32x3<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const unsigned gx = (unsigned)((p.n + TT_M - 1) / TT_M);
+    HQ_LAUNCH(HQ_K_BLOCKGEMM,
+              k_tall_tf32x3<NT><<<dim3(gx, p.ctiles), TC_THREADS, smem, s>>>(p, A1, A2, image, Cin,
+                                                                             Out, part_sq, status));
+}
+
+int tall_tc_partials(long n, int ncol) {
+    TallTcPlan p = make_tall_tc_plan(n, 4, 0, ncol);
+    return (int)(((n + TT_M - 1) / TT_M) * p.ctiles);
+}
+
+void launch_tall_tc(long n, const float *A1, int k1, const double *M1, const float *A2, int k2,
+                    const double *M2, int ncol, const float *Cin, float *Out, double *part_sq,
+                    unsigned char *image, int *status, cudaStream_t s) {
+    TallTcPlan p = make_tall_tc_plan(n, k1, k2, ncol);
+    const long total = (long)p.ctiles * p.nt * p.kpad;
+    HQ_LAUNCH(HQ_K_BLOCKGEMM, k_split_small<<<(int)std::min<long>((total + 255) / 256, 4096), 256, 0,
+                                             s>>>(p, M1, A2 ? M2 : nullptr, image));
+    switch (p.nt) {
+    case 16: run_tall_tc<16>(p, A1, A2, image, Cin, Out, part_sq, status, s); break;
+    case 32: run_tall_tc<32>(p, A1, A2, image, Cin, Out, part_sq, status, s); break;
+    case 48: run_tall_tc<48>(p, A1, A2, image, Cin, Out, part_sq, status, s); break;
+    case 64: run_tall_tc<64>(p, A1, A2, image, Cin, Out, part_sq, status, s); break;
+    case 128: run_tall_tc<128>(p, A1, A2, image, Cin, Out, part_sq, status, s); break;
+    case 256: run_tall_tc<256>(p, A1, A2, image, Cin, Out, part_sq, status, s); break;
+    }
+}
+
 }  // namespace hq

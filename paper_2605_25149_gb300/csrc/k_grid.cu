@@ -67,6 +67,26 @@ __device__ __forceinline__ void block_col_reduce(A (&acc)[V], double *red, doubl
     __syncthreads();
 }
 
+// Sum of the six neighbours of element e (point (i, j, k) of an m^3 grid) with
+// zero Dirichlet values outside.  Every load uses a clamped, always valid
+// address and is masked afterwards by a select, so the compiler can issue all
+// six loads back to back (no branch between them).
+template <typename T, int V>
+__device__ __forceinline__ VT<T, V> nbr_sum(const T *__restrict__ x, size_t e, int i, int j, int kk,
+                                            int m, size_t sx, size_t sy, size_t sz) {
+    const bool bw = i > 0, be = i < m - 1, bs = j > 0, bn = j < m - 1, bb = kk > 0, bt = kk < m - 1;
+    VT<T, V> a0 = ldv<T, V>(x + (bw ? e - sx : e)), a1 = ldv<T, V>(x + (be ? e + sx : e));
+    VT<T, V> a2 = ldv<T, V>(x + (bs ? e - sy : e)), a3 = ldv<T, V>(x + (bn ? e + sy : e));
+    VT<T, V> a4 = ldv<T, V>(x + (bb ? e - sz : e)), a5 = ldv<T, V>(x + (bt ? e + sz : e));
+    VT<T, V> s;
+#pragma unroll
+    for (int v = 0; v < V; v++)
+        s.v[v] = (((bw ? a0.v[v] : T(0)) + (be ? a1.v[v] : T(0))) +
+                  ((bs ? a2.v[v] : T(0)) + (bn ? a3.v[v] : T(0)))) +
+                 ((bb ? a4.v[v] : T(0)) + (bt ? a5.v[v] : T(0)));
+    return s;
+}
+
 // ---------------------------------------------------------------------------
 // 7-point operator.  MODE 0: y = A x (+ x.y);  MODE 1: y = b - A x (+ y.y, b.b)
 // A x = D x - c (x_w + x_e + x_s + x_n + x_b + x_t),  D = 6c + V + sigma.
@@ -95,15 +115,8 @@ __global__ void __launch_bounds__(256) k_stencil(int m, long n, int N, int ppt,
         int j = (int)(q % m);
         int kk = (int)(q / m);
         size_t e = (size_t)p * N + col;
-        VT<T, V> xc = ldv<T, V>(x + e), s;
-#pragma unroll
-        for (int v = 0; v < V; v++) s.v[v] = T(0);
-        if (i > 0) { VT<T, V> a = ldv<T, V>(x + e - sx); for (int v = 0; v < V; v++) s.v[v] += a.v[v]; }
-        if (i < m - 1) { VT<T, V> a = ldv<T, V>(x + e + sx); for (int v = 0; v < V; v++) s.v[v] += a.v[v]; }
-        if (j > 0) { VT<T, V> a = ldv<T, V>(x + e - sy); for (int v = 0; v < V; v++) s.v[v] += a.v[v]; }
-        if (j < m - 1) { VT<T, V> a = ldv<T, V>(x + e + sy); for (int v = 0; v < V; v++) s.v[v] += a.v[v]; }
-        if (kk > 0) { VT<T, V> a = ldv<T, V>(x + e - sz); for (int v = 0; v < V; v++) s.v[v] += a.v[v]; }
-        if (kk < m - 1) { VT<T, V> a = ldv<T, V>(x + e + sz); for (int v = 0; v < V; v++) s.v[v] += a.v[v]; }
+        VT<T, V> xc = ldv<T, V>(x + e);
+        VT<T, V> s = nbr_sum<T, V>(x, e, i, j, kk, m, sx, sy, sz);
         T d = D[p];
         VT<T, V> o;
 #pragma unroll
@@ -218,15 +231,8 @@ __global__ void __launch_bounds__(256) k_jacobi(int m, long n, int N, int ppt,
         int j = (int)(q % m);
         int kk = (int)(q / m);
         size_t e = (size_t)p * N + col;
-        VT<T, V> zc = ldv<T, V>(zin + e), s, rv = ldv<T, V>(r + e);
-#pragma unroll
-        for (int v = 0; v < V; v++) s.v[v] = T(0);
-        if (i > 0) { VT<T, V> a = ldv<T, V>(zin + e - sx); for (int v = 0; v < V; v++) s.v[v] += a.v[v]; }
-        if (i < m - 1) { VT<T, V> a = ldv<T, V>(zin + e + sx); for (int v = 0; v < V; v++) s.v[v] += a.v[v]; }
-        if (j > 0) { VT<T, V> a = ldv<T, V>(zin + e - sy); for (int v = 0; v < V; v++) s.v[v] += a.v[v]; }
-        if (j < m - 1) { VT<T, V> a = ldv<T, V>(zin + e + sy); for (int v = 0; v < V; v++) s.v[v] += a.v[v]; }
-        if (kk > 0) { VT<T, V> a = ldv<T, V>(zin + e - sz); for (int v = 0; v < V; v++) s.v[v] += a.v[v]; }
-        if (kk < m - 1) { VT<T, V> a = ldv<T, V>(zin + e + sz); for (int v = 0; v < V; v++) s.v[v] += a.v[v]; }
+        VT<T, V> zc = ldv<T, V>(zin + e), rv = ldv<T, V>(r + e);
+        VT<T, V> s = nbr_sum<T, V>(zin, e, i, j, kk, m, sx, sy, sz);
         T w = wD[p];
         VT<T, V> o;
 #pragma unroll
@@ -504,6 +510,78 @@ __global__ void __launch_bounds__(128) k_finalize(int mode, int N, int gy, const
         break;
     }
     }
+}
+
+// Row-wise kernels of the adjoint (FP64, point-major n x N blocks):
+//   mode 0: out[p] = scale * sum_c w[c] u[p][c]^2            (w nullable: 1)
+//   mode 1: out[p] = scale * sum_c u[p][c] v[p][c]
+__global__ void k_rowreduce(int mode, long n, int N, const double *u, const double *v,
+                            const double *w, double scale, double *out) {
+    for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < n;
+         p += (long)gridDim.x * blockDim.x) {
+        const double *ur = u + (size_t)p * N;
+        double s = 0.0;
+        if (mode == 0) {
+            for (int c = 0; c < N; c++) s += (w ? w[c] : 1.0) * ur[c] * ur[c];
+        } else {
+            const double *vr = v + (size_t)p * N;
+            for (int c = 0; c < N; c++) s += ur[c] * vr[c];
+        }
+        out[p] = scale * s;
+    }
+}
+void launch_rowreduce(int mode, long n, int N, const double *u, const double *v, const double *w,
+                      double scale, double *out, cudaStream_t s) {
+    int blocks = (int)std::min<long>((n + 255) / 256, 152 * 8);
+    HQ_LAUNCH(HQ_K_VECTOR, k_rowreduce<<<blocks, 256, 0, s>>>(mode, n, N, u, v, w, scale, out));
+}
+
+//   y[p][c] = g[p] * u[p][c]               (scale rows)
+__global__ void k_scale_rows(long n, int N, const double *g, const double *u, double *y) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * N;
+         e += (size_t)gridDim.x * blockDim.x)
+        y[e] = g[e / N] * u[e];
+}
+void launch_scale_rows(long n, int N, const double *g, const double *u, double *y, cudaStream_t s) {
+    int blocks = (int)std::min<size_t>(((size_t)n * N + 255) / 256, 152 * 16);
+    HQ_LAUNCH(HQ_K_VECTOR, k_scale_rows<<<blocks, 256, 0, s>>>(n, N, g, u, y));
+}
+
+//   y[p][c] -= s[c] * x[p][c]              (per-column shift)
+__global__ void k_shift_cols(long n, int N, const double *sft, const double *x, double *y) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * N;
+         e += (size_t)gridDim.x * blockDim.x)
+        y[e] -= sft[e % N] * x[e];
+}
+void launch_shift_cols(long n, int N, const double *sft, const double *x, double *y,
+                       cudaStream_t s) {
+    int blocks = (int)std::min<size_t>(((size_t)n * N + 255) / 256, 152 * 16);
+    HQ_LAUNCH(HQ_K_VECTOR, k_shift_cols<<<blocks, 256, 0, s>>>(n, N, sft, x, y));
+}
+
+// d[p] = a[p] - b[p]; part[block] = sum of d^2 (one partial per block)
+__global__ void k_diff_sq(long n, const double *a, const double *b, double *d, double *part) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < n;
+         p += (long)gridDim.x * blockDim.x) {
+        const double v = a[p] - b[p];
+        d[p] = v;
+        s += v * v;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+int launch_diff_sq(long n, const double *a, const double *b, double *d, double *part,
+                   cudaStream_t s) {
+    int blocks = (int)std::min<long>((n + 255) / 256, 512);
+    HQ_LAUNCH(HQ_K_VECTOR, k_diff_sq<<<blocks, 256, 0, s>>>(n, a, b, d, part));
+    return blocks;
 }
 
 // loop condition of the captured PCG: one more iteration was completed;

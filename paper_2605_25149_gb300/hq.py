@@ -31,10 +31,13 @@ FP64, MIXED = 0, 1
 
 EXPORTED = [
     "hq_default_config", "hq_workspace_bytes", "hq_init", "hq_set_potential", "hq_set_initial",
-    "hq_step", "hq_solve", "hq_eigenpairs", "hq_get_state", "hq_set_state", "hq_problem_info",
-    "hq_apply_operator", "hq_mg_vcycle", "hq_block_pcg", "hq_gram", "hq_step_trace",
+    "hq_step", "hq_solve", "hq_eigenpairs", "hq_monitor", "hq_time_step", "hq_density",
+    "hq_grad_eigs", "hq_grad_density", "hq_get_state", "hq_set_state", "hq_problem_info",
+    "hq_apply_operator", "hq_mg_vcycle", "hq_block_pcg", "hq_gram", "hq_block_gemm",
+    "hq_step_trace",
     "hq_mg_smooth", "hq_mg_restrict", "hq_mg_prolong", "hq_mg_coarse_solve",
-    "hq_mg_level_potential", "hq_gram_static", "hq_profile", "hq_profile_read", "hq_last_error",
+    "hq_mg_level_potential", "hq_gram_static", "hq_profile", "hq_profile_read", "hq_pcg_stats",
+    "hq_last_error",
     "hq_status_string", "hq_destroy",
 ]
 KERNEL_CLASSES = ["stencil", "residual", "smooth", "transfer", "coarse", "vector", "reduce", "gram",
@@ -54,6 +57,8 @@ class Config(ctypes.Structure):
         ("precision", ctypes.c_int), ("cg_rtol", ctypes.c_double), ("cg_maxit", ctypes.c_int),
         ("mg_nu1", ctypes.c_int), ("mg_nu2", ctypes.c_int), ("mg_coarsest", ctypes.c_int),
         ("mg_omega", ctypes.c_double), ("timeout_s", ctypes.c_double),
+        ("z_warm_start", ctypes.c_int), ("adaptive_tau", ctypes.c_int),
+        ("tau_max", ctypes.c_double),
     ]
 
 
@@ -82,6 +87,11 @@ def load():
         "hq_step": (_I, [_P, _I, _P]),
         "hq_solve": (_I, [_P, _D, _L, _P, _P]),
         "hq_eigenpairs": (_I, [_P, _P, _P, _P, _I, _P]),
+        "hq_monitor": (_I, [_P, _P, _P, _P, _P]),
+        "hq_time_step": (_I, [_P, _P]),
+        "hq_density": (_I, [_P, _P, _I]),
+        "hq_grad_eigs": (_I, [_P, _P, _P, _I]),
+        "hq_grad_density": (_I, [_P, _P, _P, _I, _D, _I, _P, _P, _P]),
         "hq_get_state": (_I, [_P, _P, _P, _I, _P]),
         "hq_set_state": (_I, [_P, _P, _P, _I, _L]),
         "hq_problem_info": (_I, [_P, _P, _P, _P, _P]),
@@ -89,6 +99,7 @@ def load():
         "hq_mg_vcycle": (_I, [_P, _P, _P]),
         "hq_block_pcg": (_I, [_P, _P, _P, _D, _I, _P]),
         "hq_gram": (_I, [_P, _P, _I, _P, _I, _D, _P]),
+        "hq_block_gemm": (_I, [_P, _P, _I, _P, _P, _I, _P, _P, _P]),
         "hq_step_trace": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
         "hq_mg_smooth": (_I, [_P, _I, _P, _P, _P]),
         "hq_mg_restrict": (_I, [_P, _I, _P, _P]),
@@ -98,6 +109,7 @@ def load():
         "hq_gram_static": (_I, [_P, _I, _P, _I, _L, _D, _P, _P]),
         "hq_profile": (_I, [_P, _I]),
         "hq_profile_read": (_I, [_P, _P, _P, _P]),
+        "hq_pcg_stats": (_I, [_P, _P, _P]),
         "hq_last_error": (ctypes.c_char_p, [_P]),
         "hq_status_string": (ctypes.c_char_p, [_I]),
         "hq_destroy": (None, [_P]),
@@ -236,6 +248,45 @@ class Solver:
                     "hq_eigenpairs")
         return dict(lam_paper=lp, lam_rr=lr, vectors=vec, residuals=res)
 
+    def density(self):
+        """rho = sum_i u_i^2 of the Ritz vectors (host FP64 array)."""
+        rho = np.empty(self.n)
+        self._check(self.lib.hq_density(self._ctx, _hptr(rho), 0), "hq_density")
+        return rho
+
+    def grad_eigs(self, w=None):
+        """sum_i w_i d lambda_i / dV (w = None: d(sum lambda)/dV)."""
+        dV = np.empty(self.n)
+        wh = None if w is None else self._host_f64(w, (self.N,))
+        self._check(self.lib.hq_grad_eigs(self._ctx, _hptr(wh), _hptr(dV), 0), "hq_grad_eigs")
+        return dV
+
+    def grad_density(self, G=None, rho_target=None, rtol=1e-10, maxit=500):
+        """dL/dV for a density loss: G = dL/drho, or the L2 mismatch to
+        rho_target; returns (dV, loss, iterations)."""
+        dV = np.empty(self.n)
+        loss = ctypes.c_double()
+        its = ctypes.c_int()
+        Gh = None if G is None else self._host_f64(G, (self.n,))
+        Th = None if rho_target is None else self._host_f64(rho_target, (self.n,))
+        self._check(self.lib.hq_grad_density(self._ctx, _hptr(Gh), _hptr(Th), 0, rtol, maxit,
+                                             _hptr(dV), ctypes.byref(loss), ctypes.byref(its)),
+                    "hq_grad_density")
+        return dV, loss.value, its.value
+
+    def time_step(self):
+        """tau_n of the last step taken."""
+        t = ctypes.c_double()
+        self._check(self.lib.hq_time_step(self._ctx, ctypes.byref(t)), "hq_time_step")
+        return t.value
+
+    def monitor(self):
+        """Energy E(U), ||<U,U> - I||_F, extreme eigenvalues of <U,U>."""
+        e, o, lo, hi = (ctypes.c_double() for _ in range(4))
+        self._check(self.lib.hq_monitor(self._ctx, ctypes.byref(e), ctypes.byref(o),
+                                        ctypes.byref(lo), ctypes.byref(hi)), "hq_monitor")
+        return dict(energy=e.value, onorm=o.value, smin=lo.value, smax=hi.value)
+
     def get_state(self, with_warm_start=False, U_out=None, Z_out=None):
         """(U, Z or None, step).  U_out / Z_out: optional preallocated host
         FP64 arrays (e.g. pinned) to copy into."""
@@ -299,6 +350,17 @@ class Solver:
                                      self._dev(B, self.n, Nb), Nb, w, _dptr(out)), "hq_gram")
         return out
 
+    def block_gemm(self, A1, M1, A2=None, M2=None, Cin=None):
+        """Out = A1 M1 + A2 M2 (+ Cin) (device tensors; M's FP64)."""
+        k1 = A1.shape[1]
+        k2 = 0 if A2 is None else A2.shape[1]
+        Out = self._torch.empty((self.n, self.N), dtype=self.dtype, device="cuda")
+        self._check(self.lib.hq_block_gemm(
+            self._ctx, self._dev(A1, self.n, k1), k1, _dptr(M1),
+            None if A2 is None else self._dev(A2, self.n, k2), k2, _dptr(M2),
+            None if Cin is None else self._dev(Cin, self.n), _dptr(Out)), "hq_block_gemm")
+        return Out
+
     def step_trace(self):
         t = self._torch
         n, N = self.n, self.N
@@ -327,6 +389,13 @@ class Solver:
         el = (ctypes.c_double * n)()
         self._check(self.lib.hq_profile_read(self._ctx, la, ms, el), "hq_profile_read")
         return {k: (la[i], ms[i], el[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+    def pcg_stats(self):
+        """(solves, iterations) of the inner block PCG since profile()."""
+        a, b = ctypes.c_long(), ctypes.c_long()
+        self._check(self.lib.hq_pcg_stats(self._ctx, ctypes.byref(a), ctypes.byref(b)),
+                    "hq_pcg_stats")
+        return a.value, b.value
 
     def levels(self):
         return self.info()["levels"]

@@ -141,3 +141,30 @@ def test_mixed_operator_and_vcycle_match_oracle(m, N):
     mg = oracle_mg(s, V)
     Z = host(s.mg_vcycle(dev(X)))
     assert rel(Z, mg.vcycle(X.astype(np.float64))) < 1e-5
+
+
+@pytest.mark.parametrize("prec,m,N,k1,k2,tol", [("fp64", 12, 8, 8, 8, 1e-13), ("fp64", 13, 17, 5, 0, 1e-13),
+                                               ("mixed", 16, 64, 64, 64, 2e-6),
+                                               ("mixed", 13, 24, 24, 7, 2e-6),
+                                               ("mixed", 12, 80, 80, 0, 2e-6)])
+def test_block_gemm_matches_numpy(prec, m, N, k1, k2, tol):
+    """Out = A1 M1 + A2 M2 + Cin, the products of the predictor / corrector
+    updates: SIMT FP64, or tcgen05 3xTF32 in mixed precision (ragged tile
+    widths and K not a multiple of 32 included)."""
+    torch = torch_mod()
+    s, V, _ = make(m, N, precision=prec, cg_rtol=1e-10 if prec == "fp64" else 1e-6)
+    rng = np.random.default_rng(N + k1 + k2)
+    dt = np.float64 if prec == "fp64" else np.float32
+    n = m ** 3
+    A1 = rng.standard_normal((n, k1)).astype(dt)
+    M1 = rng.standard_normal((k1, N))
+    A2 = rng.standard_normal((n, k2)).astype(dt) if k2 else None
+    M2 = rng.standard_normal((k2, N)) if k2 else None
+    Cin = rng.standard_normal((n, N)).astype(dt)
+    out = host(s.block_gemm(dev(A1), dev(M1), None if A2 is None else dev(A2),
+                            None if M2 is None else dev(M2), dev(Cin)))
+    ref = A1.astype(np.float64) @ M1 + Cin.astype(np.float64)
+    if k2:
+        ref += A2.astype(np.float64) @ M2
+    err = np.abs(out - ref).max() / np.abs(ref).max()
+    assert err < tol, err

@@ -152,3 +152,40 @@ def test_mixed_solve_eigenvalues_within_1e6_of_fp64():
     lam = separable_levels(m, -6.0, 6.0, N)
     err = np.abs(ev["lam_rr"] - lam) / np.abs(lam)
     assert err.max() < 1e-6, (err, steps, g)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("mixed", 1e-6)])
+def test_monitor_matches_oracle(prec, tol):
+    """Energy E(U) (Section 2.2), ||<U,U> - I||_F and the extreme eigenvalues
+    of <U,U> of the current iterate, against the oracle on the same state."""
+    m, N = 12, 5
+    s, V, U0 = make(m, N, precision=prec, cg_rtol=1e-10 if prec == "fp64" else 1e-6)
+    s.step(3)
+    U = s.get_state()[0]
+    mon = s.monitor()
+    h3 = inputs.grid_h(m) ** 3
+    E = O.energy(m, V, U)
+    S = h3 * U.T @ U
+    lam = np.linalg.eigvalsh(S)
+    assert mon["energy"] == pytest.approx(E, rel=tol)
+    assert mon["onorm"] == pytest.approx(np.linalg.norm(S - np.eye(N)), rel=max(tol, 1e-9), abs=1e-12)
+    assert mon["smin"] == pytest.approx(lam[0], rel=max(tol, 1e-11))
+    assert mon["smax"] == pytest.approx(lam[-1], rel=max(tol, 1e-11))
+
+
+def test_adaptive_tau_trajectory_matches_oracle():
+    """Adaptive time step: the GPU's tau_n (power iteration on one CTA) and
+    iterate follow the oracle's (Jacobi eigenvalues) for 20 steps."""
+    m, N, tmax = 10, 4, 5.0
+    s, V, U0 = make(m, N, adaptive_tau=1, tau_max=tmax, cg_rtol=1e-13, cg_maxit=400)
+    sigma = s.info()["sigma"]
+    Uo = s.get_state()[0]
+    taus = []
+    for _ in range(20):
+        s.step(1)
+        taus.append(s.time_step())
+    Ue, _, steps, _, _, th = O.solve_adaptive(m, V, sigma, Uo, tmax, 1e-30, 20,
+                                              allow_unconverged=True)
+    assert steps == 20
+    np.testing.assert_allclose(taus, th, rtol=1e-9)
+    assert rel(s.get_state()[0], Ue) < 1e-8
