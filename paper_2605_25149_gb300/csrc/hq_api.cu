@@ -61,6 +61,19 @@ struct PcgGraph {
 };
 }  // namespace
 
+// a captured phase of the scheme (A: W = G U, Gram, g; B: predictor,
+// updates, Z = G Uh, corrector) with its PCG loop as a conditional WHILE node
+struct StepGraph {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool ok = false, tried = false;
+    long fixed[HQ_K_NCLASS] = {};   // launches outside the PCG loop
+    long part1[HQ_K_NCLASS] = {};   // per loop iteration
+    long part2[HQ_K_NCLASS] = {};   // per executed IF body (V-cycle, beta, p)
+    long launches = 0;              // graph launches not yet folded into the counters
+    long long seen[2] = {0, 0};     // device counters already folded
+};
+
 struct hq_ctx {
     hq_config cfg;
     bool mixed = false;
@@ -118,6 +131,10 @@ struct hq_ctx {
     PcgGraph pgraph[MAXGRAPH];
     int npgraph = 0;
     cudaStream_t cap = nullptr;
+    // whole-phase graphs
+    StepGraph sg[2];
+    cudaStream_t capA = nullptr, capB = nullptr, capC = nullptr;
+    long long *dcount = nullptr;   // device counters: [2 per phase graph]
     ~hq_ctx() {
         for (cudaEvent_t e : evpool) cudaEventDestroy(e);
         for (int i = 0; i < npgraph; i++) {
@@ -125,6 +142,13 @@ struct hq_ctx {
             if (pgraph[i].g) cudaGraphDestroy(pgraph[i].g);
         }
         if (cap) cudaStreamDestroy(cap);
+        for (int i = 0; i < 2; i++) {
+            if (sg[i].exec) cudaGraphExecDestroy(sg[i].exec);
+            if (sg[i].g) cudaGraphDestroy(sg[i].g);
+        }
+        if (capA) cudaStreamDestroy(capA);
+        if (capB) cudaStreamDestroy(capB);
+        if (capC) cudaStreamDestroy(capC);
     }
 };
 
@@ -351,8 +375,10 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
     double *vn1 = cv.take<double>(sizeof(double) * n);
     double *vn2 = cv.take<double>(sizeof(double) * n);
     double *pvec = cv.take<double>(sizeof(double) * N);
+    long long *dcount = cv.take<long long>(sizeof(long long) * 8);
     if (x) {
         x->pvec = pvec;
+        x->dcount = dcount;
         x->vn[0] = vn0; x->vn[1] = vn1; x->vn[2] = vn2;
         x->U = U; x->W = W; x->Uh = Uh; x->Z = Z; x->R = R; x->Zp = Zp; x->P = P; x->Q = Q;
         x->Tt = Tt; x->E1 = E1; x->E2 = E2; x->E3 = E3;
@@ -409,6 +435,8 @@ hq_status sync_status(hq_ctx *x, int *dev_status_word, const char *where) {
     if (st & ST_SINGULAR) return fail(x, HQ_ERR_SINGULAR, std::string(where) + ": singular small system");
     if (st & ST_NONFINITE) return fail(x, HQ_ERR_NONFINITE, std::string(where) + ": non-finite value");
     if (st & ST_GJ_FAIL) return fail(x, HQ_ERR_ARG, std::string(where) + ": coarsest operator not positive definite (shift too small)");
+    if (st & ST_TC_TIMEOUT) return fail(x, HQ_ERR_TIMEOUT, std::string(where) + ": tensor-core wait expired");
+    if (st & ST_PCG_MAXIT) return fail(x, HQ_ERR_NOT_CONVERGED, std::string(where) + ": inner PCG reached cg_maxit");
     return HQ_OK;
 }
 
@@ -681,21 +709,263 @@ void block_gemm<float>(hq_ctx *x, const float *A1, int k1, const double *M1, con
 // ---------------------------------------------------------------------------
 // the scheme
 // ---------------------------------------------------------------------------
-// A1-A3: W = G U (warm start from the previous G Uh), Gram of [U W], g.
+// Appends a conditional node with handle h to the capture sequence of s and
+// returns its body graph; the capture continues after the node.
+bool add_cond_node(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                   cudaGraph_t *body) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *ed = nullptr;
+    size_t nd = 0;
+    if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &ed, &nd) != cudaSuccess ||
+        cs != cudaStreamCaptureStatusActive)
+        return false;
+    alignas(cudaGraphNodeParams) unsigned char npbuf[sizeof(cudaGraphNodeParams)];
+    std::memset(npbuf, 0, sizeof(npbuf));
+    cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(npbuf);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = type;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, g, deps, ed, nd, &np) != cudaSuccess) return false;
+    if (cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies) !=
+        cudaSuccess)
+        return false;
+    *body = np.conditional.phGraph_out[0];
+    return true;
+}
+
+bool capture_graph_of(cudaStream_t s, cudaGraph_t *g) {
+    cudaStreamCaptureStatus cs;
+    return cudaStreamGetCaptureInfo(s, &cs, nullptr, g, nullptr, nullptr, nullptr) == cudaSuccess &&
+           cs == cudaStreamCaptureStatusActive;
+}
+
+// Block PCG recorded into the phase graph being captured on x->st: the
+// prologue, then WHILE(active && it < maxit) { q = A p, alpha, x / r update,
+// stopping test, IF(active) { z = M r, beta, p = z + beta p } }.  The
+// operation sequence equals that of pcg(); nothing is read back on the host.
 template <typename T>
-hq_status phase_a(hq_ctx *x) {
+hq_status pcg_device(hq_ctx *x, const T *B, T *X, double rtol, int maxit, StepGraph &sgr,
+                     long long *counters) {
+    Level &v = x->lev[0];
+    const GridGeom &g = v.g;
+    const int N = x->N;
+    T *R = (T *)x->R, *Zp = (T *)x->Zp, *P = (T *)x->P, *Tt = (T *)x->Tt;
+    PcgScalars sc = x->sc;
+    cudaStream_t main = x->st;
+    HQ_CUDA(cudaMemsetAsync(sc.num_active, 0, 2 * sizeof(int), main));
+    launch_resid<T>(g, (const T *)v.Dt, (T)v.c, X, B, R, x->part, x->part2, main);
+    launch_finalize(FIN_BNORM_RNORM, N, g.gy, x->part, x->part2, sc, rtol, main);
+    HQ_TRY(vcycle<T>(x, 0, R, Zp, Tt, false, x->part));
+    launch_finalize(FIN_RZ, N, g.gy, x->part, nullptr, sc, rtol, main);
+    HQ_TRY(copy_blk<T>(x, P, Zp, (size_t)x->n * N));
+    cudaGraph_t gmain;
+    if (!capture_graph_of(main, &gmain)) return fail(x, HQ_ERR_CUDA, "capture state");
+    cudaGraphConditionalHandle hw, hif;
+    if (cudaGraphConditionalHandleCreate(&hw, gmain, 0, cudaGraphCondAssignDefault) != cudaSuccess)
+        return fail(x, HQ_ERR_CUDA, "conditional handle");
+    launch_pcg_cond_init(sc.num_active, maxit, hw, main);
+    cudaGraph_t body;
+    if (!add_cond_node(main, hw, cudaGraphCondTypeWhile, &body))
+        return fail(x, HQ_ERR_CUDA, "WHILE node");
+    // loop body, captured on capB
+    x->st = x->capB;
+    if (cudaStreamBeginCaptureToGraph(x->capB, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        x->st = main;
+        return fail(x, HQ_ERR_CUDA, "body capture");
+    }
+    x->cap_counts = sgr.part1;
+    hq_status st = pcg_half<T>(x, X, rtol);
+    cudaGraph_t ifbody = nullptr;
+    bool ok = st == HQ_OK &&
+              cudaGraphConditionalHandleCreate(&hif, body, 0, cudaGraphCondAssignDefault) ==
+                  cudaSuccess;
+    if (ok) {
+        launch_pcg_cond2(sc.num_active, sc.num_active + 1, maxit, hw, hif, counters, sc.status,
+                         rtol > 0.0 ? 1 : 0, x->st);
+        ok = add_cond_node(x->capB, hif, cudaGraphCondTypeIf, &ifbody);
+    }
+    if (ok) {
+        x->st = x->capC;
+        ok = cudaStreamBeginCaptureToGraph(x->capC, ifbody, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            x->cap_counts = sgr.part2;
+            st = pcg_body<T>(x, X, rtol);
+            cudaGraph_t tmp;
+            if (cudaStreamEndCapture(x->capC, &tmp) != cudaSuccess) ok = false;
+        }
+        x->st = x->capB;
+    }
+    cudaGraph_t tmpb;
+    if (cudaStreamEndCapture(x->capB, &tmpb) != cudaSuccess) ok = false;
+    x->st = main;
+    x->cap_counts = sgr.fixed;
+    if (!ok || st != HQ_OK) return fail(x, HQ_ERR_CUDA, "PCG loop capture");
+    return HQ_OK;
+}
+
+// A1-A3: W = G U (warm start from the previous G Uh), Gram of [U W], g.
+// sgr == nullptr: host-driven PCG; otherwise recorded into a phase graph.
+template <typename T>
+hq_status enqueue_a(hq_ctx *x, StepGraph *sgr) {
     const int N = x->N;
     const size_t cnt = (size_t)x->n * N;
     T *U = (T *)x->U, *W = (T *)x->W;
-    if (x->z_valid) HQ_TRY(copy_blk<T>(x, W, (const T *)x->Z, cnt));
+    if (x->z_valid || sgr) HQ_TRY(copy_blk<T>(x, W, (const T *)x->Z, cnt));
     else HQ_CUDA(cudaMemsetAsync(W, 0, cnt * sizeof(T), x->st));
-    HQ_TRY(pcg<T>(x, U, W, x->cfg.cg_rtol, x->cfg.cg_maxit, nullptr));
+    if (sgr) HQ_TRY(pcg_device<T>(x, U, W, x->cfg.cg_rtol, x->cfg.cg_maxit, *sgr, x->dcount));
+    else HQ_TRY(pcg<T>(x, U, W, x->cfg.cg_rtol, x->cfg.cg_maxit, nullptr));
     gram_sym<T>(x, U, N, W, N, x->G2);
     // Msm = -Pwu (rows N..2N-1, columns 0..N-1 of G2); g = || W - U Pwu ||_h
     launch_extract(N, N, -1.0, x->G2 + (size_t)N * 2 * N, 2 * N, x->Msm, N, x->st);
     int np = 0;
     block_gemm<T>(x, U, N, x->Msm, nullptr, 0, nullptr, W, nullptr, true, &np);
     launch_sum_sqrt(np, x->tpart, x->h3, x->scal, x->st);
+    return HQ_OK;
+}
+
+// B1-B5: predictor system, Uh, Shat, Z = G Uh, corrector (U <- U_{n+1}).
+template <typename T>
+hq_status enqueue_b(hq_ctx *x, StepGraph *sgr) {
+    const int N = x->N;
+    const size_t cnt = (size_t)x->n * N;
+    const double tau = x->cfg.tau;
+    T *U = (T *)x->U, *W = (T *)x->W, *Uh = (T *)x->Uh, *Z = (T *)x->Z;
+    const double *tau_dev = nullptr;
+    if (x->cfg.adaptive_tau) {
+        // tau_n from the Gram of step n (Ritz estimate of lambda_1, bound on lambda_max<U,U>)
+        launch_extract(N, N, 1.0, x->G2, 2 * N, x->Ssm, N, x->st);
+        launch_extract(N, N, 1.0, x->G2 + (size_t)N * 2 * N, 2 * N, x->Ksm, N, x->st);
+        launch_rr_reduce(N, x->Ksm, x->Ssm, x->Lm, x->Cm, x->status, x->st);
+        launch_top_eig(N, x->Cm, N, x->pvec, x->scal + 12, x->st);
+        launch_gersh(N, x->Ssm, N, x->scal + 13, x->st);
+        const double tmax = x->cfg.tau_max > 0.0 ? x->cfg.tau_max : 1e300;
+        launch_adapt_tau(x->scal + 12, x->scal + 13, tmax, 0.8, 1.05, x->lambda1_lb, x->scal + 8,
+                         x->st);
+        tau_dev = x->scal + 8;
+    }
+    launch_predictor_solve(N, tau, x->G2, x->Mw, x->XY, x->C, x->status, x->st, tau_dev);
+    block_gemm<T>(x, U, N, x->C, W, N, x->C + (size_t)N * N, nullptr, Uh, false, nullptr);
+    // Shat = C^T G2 C, Om = -tau (Shat - I)
+    launch_small_gemm(2 * N, N, 2 * N, 1.0, x->G2, 2 * N, false, x->C, N, false, 0.0, x->T1, N,
+                      x->st);
+    launch_small_gemm(N, N, 2 * N, 1.0, x->C, N, true, x->T1, N, false, 0.0, x->Shat, N, x->st);
+    launch_corrector_matrix(N, x->Shat, tau_dev, tau, x->Om, x->st);
+    if (x->cfg.z_warm_start) {
+        // G Uh = W C1 + G W C2 and G W ~ W M with M = S^{-1} Puw (exact when
+        // span(U) is G-invariant): start from Z0 = W (C1 + M C2)
+        launch_chol_solve(N, x->G2, 2 * N, x->G2 + N, 2 * N, x->Lm, x->Ym, x->status, x->st);
+        launch_extract(N, N, 1.0, x->C, N, x->Cm, N, x->st);
+        launch_small_gemm(N, N, N, 1.0, x->Ym, N, false, x->C + (size_t)N * N, N, false, 1.0,
+                          x->Cm, N, x->st);
+    }
+    if (!sgr) HQ_TRY(sync_status(x, x->status, "predictor system"));
+    if (x->cfg.z_warm_start) {
+        block_gemm<T>(x, W, N, x->Cm, nullptr, 0, nullptr, nullptr, Z, false, nullptr);
+    } else {
+        HQ_CUDA(cudaMemsetAsync(Z, 0, cnt * sizeof(T), x->st));
+    }
+    if (sgr) HQ_TRY(pcg_device<T>(x, Uh, Z, x->cfg.cg_rtol, x->cfg.cg_maxit, *sgr, x->dcount + 2));
+    else HQ_TRY(pcg<T>(x, Uh, Z, x->cfg.cg_rtol, x->cfg.cg_maxit, nullptr));
+    block_gemm<T>(x, Z, N, x->Om, nullptr, 0, nullptr, Uh, U, false, nullptr);
+    return HQ_OK;
+}
+
+// Captures phase `which` (0: A, 1: B) once; later calls replay it.
+template <typename T>
+StepGraph *phase_graph(hq_ctx *x, int which) {
+    StepGraph &sgr = x->sg[which];
+    if (sgr.tried) return sgr.ok ? &sgr : nullptr;
+    sgr.tried = true;
+    for (cudaStream_t *c : {&x->capA, &x->capB, &x->capC})
+        if (!*c && cudaStreamCreateWithFlags(c, cudaStreamNonBlocking) != cudaSuccess) {
+            *c = nullptr;
+            return nullptr;
+        }
+    if (cudaStreamSynchronize(x->st) != cudaSuccess) return nullptr;
+    cudaStream_t saved = x->st;
+    x->st = x->capA;
+    if (cudaStreamBeginCapture(x->capA, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        x->st = saved;
+        return nullptr;
+    }
+    x->capturing = true;
+    x->cap_counts = sgr.fixed;
+    hq_status st = which == 0 ? enqueue_a<T>(x, &sgr) : enqueue_b<T>(x, &sgr);
+    x->capturing = false;
+    x->cap_counts = nullptr;
+    x->st = saved;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(x->capA, &g);
+    if (st != HQ_OK || e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        x->err.clear();
+        return nullptr;
+    }
+    sgr.g = g;
+    if (cudaGraphInstantiate(&sgr.exec, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    sgr.ok = true;
+    return &sgr;
+}
+
+// adds the launches of the replayed phase graphs to the counters
+hq_status fold_graph_counts(hq_ctx *x) {
+    if (!x->sg[0].launches && !x->sg[1].launches) return HQ_OK;
+    long long c[4];
+    HQ_CUDA(cudaMemcpyAsync(c, x->dcount, sizeof(c), cudaMemcpyDeviceToHost, x->st));
+    HQ_CUDA(cudaStreamSynchronize(x->st));
+    for (int w = 0; w < 2; w++) {
+        StepGraph &sgr = x->sg[w];
+        const long long it = c[2 * w] - sgr.seen[0], ifs = c[2 * w + 1] - sgr.seen[1];
+        sgr.seen[0] = c[2 * w];
+        sgr.seen[1] = c[2 * w + 1];
+        for (int k = 0; k < HQ_K_NCLASS; k++)
+            x->launches[k] += sgr.fixed[k] * sgr.launches + sgr.part1[k] * it + sgr.part2[k] * ifs;
+        // each replay runs one solve of 1 + (loop iterations) PCG iterations
+        x->stat_solves += sgr.launches;
+        x->stat_iters += (long)it;
+        sgr.launches = 0;
+    }
+    return HQ_OK;
+}
+
+// Graphs hold the shift constants and the lower bound of lambda_1 by value:
+// a new potential discards them (after folding their launch counts).
+hq_status drop_graphs(hq_ctx *x) {
+    HQ_TRY(fold_graph_counts(x));
+    for (int i = 0; i < x->npgraph; i++) destroy_graph(x->pgraph[i]);
+    x->npgraph = 0;
+    for (StepGraph &sgr : x->sg) {
+        if (sgr.exec) cudaGraphExecDestroy(sgr.exec);
+        if (sgr.g) cudaGraphDestroy(sgr.g);
+        const long long s0 = sgr.seen[0], s1 = sgr.seen[1];
+        sgr = StepGraph();
+        sgr.seen[0] = s0;
+        sgr.seen[1] = s1;
+    }
+    return HQ_OK;
+}
+
+bool use_phase_graphs(hq_ctx *x) { return x->use_graphs && !x->timing && x->z_valid; }
+
+template <typename T>
+hq_status phase_a(hq_ctx *x) {
+    StepGraph *sgr = use_phase_graphs(x) ? phase_graph<T>(x, 0) : nullptr;
+    if (sgr) {
+        HQ_CUDA(cudaGraphLaunch(sgr->exec, x->st));
+        sgr->launches++;
+    } else {
+        HQ_TRY(enqueue_a<T>(x, nullptr));
+    }
     HQ_TRY(check_launch(x));
     x->w_valid = true;
     return HQ_OK;
@@ -719,55 +989,27 @@ hq_status read_g(hq_ctx *x, double *g) {
     return HQ_OK;
 }
 
-// B1-B5: predictor system, Uh, Shat, Z = G Uh, corrector (U <- U_{n+1}).
 template <typename T>
 hq_status phase_b(hq_ctx *x) {
-    const int N = x->N;
-    const size_t cnt = (size_t)x->n * N;
-    const double tau = x->cfg.tau;
-    T *U = (T *)x->U, *W = (T *)x->W, *Uh = (T *)x->Uh, *Z = (T *)x->Z;
-    const double *tau_dev = nullptr;
-    if (x->cfg.adaptive_tau) {
-        // tau_n from the Gram of step n (Ritz estimate of lambda_1, lambda_max<U,U>)
-        launch_extract(N, N, 1.0, x->G2, 2 * N, x->Ssm, N, x->st);
-        launch_extract(N, N, 1.0, x->G2 + (size_t)N * 2 * N, 2 * N, x->Ksm, N, x->st);
-        launch_rr_reduce(N, x->Ksm, x->Ssm, x->Lm, x->Cm, x->status, x->st);
-        launch_top_eig(N, x->Cm, N, x->pvec, x->scal + 12, x->st);
-        launch_gersh(N, x->Ssm, N, x->scal + 13, x->st);
-        const double tmax = x->cfg.tau_max > 0.0 ? x->cfg.tau_max : 1e300;
-        launch_adapt_tau(x->scal + 12, x->scal + 13, tmax, 0.8, 1.05, x->lambda1_lb, x->scal + 8,
-                         x->st);
-        tau_dev = x->scal + 8;
-    }
-    launch_predictor_solve(N, tau, x->G2, x->Mw, x->XY, x->C, x->status, x->st, tau_dev);
-    block_gemm<T>(x, U, N, x->C, W, N, x->C + (size_t)N * N, nullptr, Uh, false, nullptr);
-    // Shat = C^T G2 C, Om = Shat - I
-    launch_small_gemm(2 * N, N, 2 * N, 1.0, x->G2, 2 * N, false, x->C, N, false, 0.0, x->T1, N,
-                      x->st);
-    launch_small_gemm(N, N, 2 * N, 1.0, x->C, N, true, x->T1, N, false, 0.0, x->Shat, N, x->st);
-    // Om = -tau (Shat - I)
-    launch_corrector_matrix(N, x->Shat, tau_dev, tau, x->Om, x->st);
-    if (x->cfg.z_warm_start) {
-        // G Uh = W C1 + G W C2 and G W ~ W M with M = S^{-1} Puw (exact when
-        // span(U) is G-invariant): start from Z0 = W (C1 + M C2)
-        launch_chol_solve(N, x->G2, 2 * N, x->G2 + N, 2 * N, x->Lm, x->Ym, x->status, x->st);
-        launch_extract(N, N, 1.0, x->C, N, x->Cm, N, x->st);
-        launch_small_gemm(N, N, N, 1.0, x->Ym, N, false, x->C + (size_t)N * N, N, false, 1.0,
-                          x->Cm, N, x->st);
-    }
-    HQ_TRY(sync_status(x, x->status, "predictor system"));
-    if (x->cfg.z_warm_start) {
-        block_gemm<T>(x, W, N, x->Cm, nullptr, 0, nullptr, nullptr, Z, false, nullptr);
+    StepGraph *sgr = use_phase_graphs(x) ? phase_graph<T>(x, 1) : nullptr;
+    if (sgr) {
+        HQ_CUDA(cudaGraphLaunch(sgr->exec, x->st));
+        sgr->launches++;
     } else {
-        HQ_CUDA(cudaMemsetAsync(Z, 0, cnt * sizeof(T), x->st));
+        HQ_TRY(enqueue_b<T>(x, nullptr));
     }
-    HQ_TRY(pcg<T>(x, Uh, Z, x->cfg.cg_rtol, x->cfg.cg_maxit, nullptr));
-    block_gemm<T>(x, Z, N, x->Om, nullptr, 0, nullptr, Uh, U, false, nullptr);
     HQ_TRY(check_launch(x));
     x->w_valid = false;
     x->z_valid = true;
     x->step++;
     return HQ_OK;
+}
+
+// status words of the replayed graphs (read at the end of hq_step / each
+// hq_solve iteration)
+hq_status graph_status(hq_ctx *x) {
+    HQ_TRY(sync_status(x, x->sc.status, "inner PCG"));
+    return sync_status(x, x->status, "step");
 }
 
 }  // namespace
@@ -795,6 +1037,7 @@ template <typename T>
 hq_status set_potential_impl(hq_ctx *x, const double *V, int on_device) {
     Level &v0 = x->lev[0];
     x->have_V = false;
+    HQ_TRY(drop_graphs(x));
     HQ_TRY(clear_status(x));
     HQ_CUDA(cudaMemcpyAsync(v0.V, V, sizeof(double) * x->n, kind_in(on_device), x->st));
     launch_minmax(x->n, v0.V, x->scal + 2, x->st);
@@ -891,9 +1134,10 @@ hq_status step_impl(hq_ctx *x, int nsteps, double *resid_out) {
     double g = NAN;
     for (int s = 0; s < nsteps; s++) {
         HQ_TRY(phase_a<T>(x));
-        HQ_TRY(read_g(x, &g));
+        if (s == nsteps - 1 || !use_phase_graphs(x)) HQ_TRY(read_g(x, &g));
         HQ_TRY(phase_b<T>(x));
     }
+    HQ_TRY(graph_status(x));
     if (resid_out) *resid_out = g;
     return HQ_OK;
 }
@@ -927,6 +1171,7 @@ hq_status solve_impl(hq_ctx *x, double eps, long max_steps, long *steps_out, dou
         if (st != HQ_OK) break;
         taken++;
     }
+    if (st == HQ_OK) st = graph_status(x);
     if (steps_out) *steps_out = taken;
     if (resid_out) *resid_out = g;
     return st;
@@ -1014,7 +1259,8 @@ hq_status monitor_impl(hq_ctx *x, double *energy, double *onorm, double *smin, d
     double trS = 0.0;
     {
         std::vector<double> S((size_t)N * N);
-        HQ_CUDA(cudaMemcpy(S.data(), x->Ssm, sizeof(double) * N * N, cudaMemcpyDeviceToHost));
+        HQ_CUDA(cudaMemcpyAsync(S.data(), x->Ssm, sizeof(double) * N * N, cudaMemcpyDeviceToHost, x->st));
+        HQ_CUDA(cudaStreamSynchronize(x->st));
         for (int i = 0; i < N; i++) trS += S[(size_t)i * N + i];
     }
     if (energy) *energy = 0.5 * (e2[0] - x->sigma * trS);
@@ -1347,9 +1593,12 @@ hq_status hq_init(const hq_config *cfg, void *d_workspace, size_t bytes, void *c
         x->use_graphs = !(e && e[0] == '1');
     }
     carve(x, cfg, x->ws);
-    // the status words start cleared
+    // the status words and counters start cleared
     cudaError_t e = cudaMemsetAsync(x->sc.status, 0, sizeof(int), x->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(x->status, 0, sizeof(int), x->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(x->dcount, 0, sizeof(long long) * 8, x->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(x->st);
+    if (x->mixed) hq::tc_prepare();
     if (e != cudaSuccess) {
         delete x;
         return HQ_ERR_CUDA;
@@ -1602,6 +1851,7 @@ hq_status hq_mg_level_potential(hq_ctx *x, int level, double *V_out) {
 
 hq_status hq_profile(hq_ctx *x, int timing) {
     HQ_TRY(guard(x));
+    HQ_TRY(fold_graph_counts(x));
     for (int i = 0; i < HQ_K_NCLASS; i++) {
         x->launches[i] = 0;
         x->work[i] = 0.0;
@@ -1616,6 +1866,7 @@ hq_status hq_profile(hq_ctx *x, int timing) {
 hq_status hq_profile_read(hq_ctx *x, long *launches, double *ms, double *elements) {
     HQ_API_BEGIN
     HQ_TRY(guard(x));
+    HQ_TRY(fold_graph_counts(x));
     HQ_CUDA(cudaStreamSynchronize(x->st));
     if (launches)
         for (int i = 0; i < HQ_K_NCLASS; i++) launches[i] = x->launches[i];
@@ -1635,6 +1886,7 @@ hq_status hq_profile_read(hq_ctx *x, long *launches, double *ms, double *element
 
 hq_status hq_pcg_stats(hq_ctx *x, long *solves, long *iterations) {
     HQ_TRY(guard(x));
+    HQ_TRY(fold_graph_counts(x));
     if (solves) *solves = x->stat_solves;
     if (iterations) *iterations = x->stat_iters;
     return HQ_OK;

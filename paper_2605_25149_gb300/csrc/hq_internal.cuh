@@ -44,7 +44,8 @@ struct PcgScalars {
     int *status;       // 1 int, sticky error flags (bit 0: breakdown)
 };
 
-enum { ST_BREAKDOWN = 1, ST_SINGULAR = 2, ST_NONFINITE = 4, ST_GJ_FAIL = 8, ST_TC_TIMEOUT = 16 };
+enum { ST_BREAKDOWN = 1, ST_SINGULAR = 2, ST_NONFINITE = 4, ST_GJ_FAIL = 8, ST_TC_TIMEOUT = 16,
+       ST_PCG_MAXIT = 32 };
 
 // ----------------------------------------------------------------------------
 // grid kernels (k_grid.cu); T = double or float
@@ -113,6 +114,18 @@ void launch_finalize(int mode, int N, int gy, const double *part, const double *
 // ++iter[0] < maxit)
 void launch_pcg_cond(const int *num_active, int *iter, int maxit, cudaGraphConditionalHandle h,
                      cudaStream_t s);
+// whole-step graphs: hw = (num_active[0] > 0 && maxit > 0) before the loop;
+// in the loop body: ++iter[0], counters[0] += 1, counters[1] += active,
+// hif = active, hw = active && iter < maxit, and ST_PCG_MAXIT in status when
+// columns are still active at the cap (check_maxit)
+void launch_pcg_cond_init(const int *num_active, int maxit, cudaGraphConditionalHandle hw,
+                          cudaStream_t s);
+void launch_pcg_cond2(const int *num_active, int *iter, int maxit, cudaGraphConditionalHandle hw,
+                      cudaGraphConditionalHandle hif, long long *counters, int *status,
+                      int check_maxit, cudaStream_t s);
+// sets the dynamic shared-memory limits of the tensor-core kernels (call once,
+// outside any stream capture)
+void tc_prepare();
 
 // adjoint row kernels (FP64): mode 0 out[p] = scale sum_c w_c u_pc^2,
 // mode 1 out[p] = scale sum_c u_pc v_pc

@@ -348,7 +348,7 @@ void launch_gram_tc(long n, const float *X1, int n1, const float *X2, int n2, do
                     float *partials, double *out, int *status, cudaStream_t s) {
     TcPlan p = make_tc_plan(n, n1 + n2);
     const int smem = (int)gram_tc_smem_bytes();
-    cudaFuncSetAttribute(k_gram_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    tc_prepare();
     HQ_LAUNCH(HQ_K_GRAM, k_gram_tf32x3<<<dim3(p.ntiles, p.chunks), TC_THREADS, smem, s>>>(
                              p, X1, n1, X2, n2, partials, status));
     HQ_LAUNCH(HQ_K_GRAM, k_gram_tc_reduce<<<p.ntiles, 256, 0, s>>>(p, partials, w, out));
@@ -612,11 +612,31 @@ static void run_tall_tc(const TallTcPlan &p, const float *A1, const float *A2,
                         const unsigned char *image, const float *Cin, float *Out, double *part_sq,
                         int *status, cudaStream_t s) {
     const int smem = 2 * (2 * TT_M * 128 + 2 * NT * 128) + 1024;
-    cudaFuncSetAttribute(k_tall_tf32x3<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    tc_prepare();
     const unsigned gx = (unsigned)((p.n + TT_M - 1) / TT_M);
     HQ_LAUNCH(HQ_K_BLOCKGEMM,
               k_tall_tf32x3<NT><<<dim3(gx, p.ctiles), TC_THREADS, smem, s>>>(p, A1, A2, image, Cin,
                                                                              Out, part_sq, status));
+}
+
+template <int NT>
+static void prep_tall() {
+    const int smem = 2 * (2 * TT_M * 128 + 2 * NT * 128) + 1024;
+    cudaFuncSetAttribute(k_tall_tf32x3<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+void tc_prepare() {
+    static bool done = false;
+    if (done) return;
+    cudaFuncSetAttribute(k_gram_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)gram_tc_smem_bytes());
+    prep_tall<16>();
+    prep_tall<32>();
+    prep_tall<48>();
+    prep_tall<64>();
+    prep_tall<128>();
+    prep_tall<256>();
+    done = true;
 }
 
 int tall_tc_partials(long n, int ncol) {

@@ -593,6 +593,24 @@ __global__ void k_pcg_cond(const int *num_active, int *iter, int maxit,
     cudaGraphSetConditional(h, (num_active[0] > 0 && it < maxit) ? 1u : 0u);
 }
 
+__global__ void k_pcg_cond_init(const int *num_active, int maxit, cudaGraphConditionalHandle hw) {
+    cudaGraphSetConditional(hw, (num_active[0] > 0 && maxit > 0) ? 1u : 0u);
+}
+
+__global__ void k_pcg_cond2(const int *num_active, int *iter, int maxit,
+                            cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hif,
+                            long long *counters, int *status, int check_maxit) {
+    const int it = iter[0] + 1;
+    iter[0] = it;
+    const bool act = num_active[0] > 0;
+    const bool more = act && it < maxit;
+    counters[0] += 1;
+    if (more) counters[1] += 1;
+    if (act && it >= maxit && check_maxit) atomicOr(status, ST_PCG_MAXIT);
+    cudaGraphSetConditional(hif, more ? 1u : 0u);
+    cudaGraphSetConditional(hw, more ? 1u : 0u);
+}
+
 // ---------------------------------------------------------------------------
 // setup kernels (once per potential)
 // ---------------------------------------------------------------------------
@@ -898,6 +916,17 @@ void launch_finalize(int mode, int N, int gy, const double *part, const double *
 void launch_pcg_cond(const int *num_active, int *iter, int maxit, cudaGraphConditionalHandle h,
                      cudaStream_t s) {
     HQ_LAUNCH(HQ_K_REDUCE, k_pcg_cond<<<1, 1, 0, s>>>(num_active, iter, maxit, h));
+}
+
+void launch_pcg_cond_init(const int *num_active, int maxit, cudaGraphConditionalHandle hw,
+                          cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_REDUCE, k_pcg_cond_init<<<1, 1, 0, s>>>(num_active, maxit, hw));
+}
+void launch_pcg_cond2(const int *num_active, int *iter, int maxit, cudaGraphConditionalHandle hw,
+                      cudaGraphConditionalHandle hif, long long *counters, int *status,
+                      int check_maxit, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_REDUCE, k_pcg_cond2<<<1, 1, 0, s>>>(num_active, iter, maxit, hw, hif, counters,
+                                                        status, check_maxit));
 }
 
 void launch_coarse_potential(int mf, const double *Vf, int mc, double *Vc, cudaStream_t s) {
