@@ -83,6 +83,9 @@ typedef struct {
                          /* largest eigenvalue); the first step starts from the       */
                          /* closed-form lower bound of lambda_1(H + sigma)            */
     double tau_max;      /* delta_T of Algorithm 1 for adaptive_tau (<= 0: no cap)    */
+    int grid_block;      /* threads per CTA of the grid kernels: 0 (= 256), 64, 128, 256 */
+    int grid_ctas;       /* target CTAs per SM of the grid kernels: 0 (= 16) .. 64;     */
+                         /* both set the launch shape only (hq_tune picks them)      */
 } hq_config;
 
 /* Defaults: box [-6,6]^3, tau 0.4, automatic shift, FP64, cg_rtol 1e-10,
@@ -294,6 +297,64 @@ hq_status hq_pcg_stats(hq_ctx *ctx, long *solves, long *iterations);
 const char *hq_last_error(hq_ctx *ctx);
 const char *hq_status_string(hq_status s);
 void hq_destroy(hq_ctx *ctx);
+
+/* ------------------------------------------------------------------------
+ * Launch-shape autotuner (no counterpart in the paper).  For cfg's m, nev and
+ * precision it times a 10-iteration multigrid-preconditioned block PCG (the
+ * inner solve of Eq. (4.1); harmonic potential, pseudo-random right-hand
+ * side) under each candidate grid_block in {64, 128, 256} x grid_ctas in
+ * {4, 8, 16, 32} and writes cfg with the fastest pair into *tuned.  The launch
+ * shape changes only the order of the per-column reductions, so results agree
+ * with the default shape to rounding.  workspace: device buffer of at least
+ * hq_tune_workspace_bytes(cfg) bytes (256-byte aligned), scratch for the call
+ * only.  ms_out: the fastest time per PCG iteration in ms (nullable).
+ * Synchronises cuda_stream.  Errors: HQ_ERR_ARG (invalid cfg or null
+ * pointer), HQ_ERR_NOMEM (workspace too small), HQ_ERR_CUDA.
+ * ------------------------------------------------------------------------ */
+size_t hq_tune_workspace_bytes(const hq_config *cfg);
+hq_status hq_tune(const hq_config *cfg, void *d_workspace, size_t bytes, void *cuda_stream,
+                  hq_config *tuned, double *ms_out);
+
+/* ------------------------------------------------------------------------
+ * Batched form: many independent problems (contexts of any m, N and
+ * precision, each with its own potential and U0) advanced by Algorithm 1
+ * (Section 5) in ONE CUDA-graph launch per call.  The graph holds the time
+ * loop as a conditional WHILE node; inside it every problem is an IF node
+ * (skipped once that problem has stopped) holding its two phases of
+ * Eq. (4.1), each with its inner block PCG as nested WHILE / IF nodes.  The
+ * problems' kernels run concurrently; nothing returns to the host until all
+ * problems have stopped.  Each problem follows the trajectory that
+ * hq_solve / hq_step of its context would produce, bit for bit.
+ * ------------------------------------------------------------------------ */
+typedef struct hq_batch hq_batch;
+
+/* ctxs: count (1..64) distinct contexts on the current device, borrowed: they
+ * must outlive the batch and must not be used by another thread during a
+ * batch call.  cuda_stream: the stream the batch graph is launched on (NULL:
+ * legacy default stream).  The graph is captured at the first hq_batch_solve
+ * / hq_batch_step and again after any member's hq_set_potential.  *out is
+ * freed with hq_batch_destroy.  Errors: HQ_ERR_ARG (count, null or repeated
+ * context).                                                                */
+hq_status hq_batch_create(hq_ctx *const *ctxs, int count, void *cuda_stream, hq_batch **out);
+/* Algorithm 1 for every member: problem k stops when its g < eps[k] (eps:
+ * count host doubles, > 0) or after max_steps steps; timeout_s > 0 bounds the
+ * wall-clock time of the whole batch on the device (0: none).  Outputs (host,
+ * count entries each, nullable): steps taken, last g, per-problem status
+ * (HQ_OK, HQ_ERR_NOT_CONVERGED, HQ_ERR_TIMEOUT, or the error a member hit;
+ * its message is in hq_last_error of that context).  Returns HQ_OK when every
+ * problem converged, else the first non-OK per-problem status (message in
+ * hq_batch_last_error).  Synchronises the batch stream.                    */
+hq_status hq_batch_solve(hq_batch *b, const double *eps, long max_steps, double timeout_s,
+                         long *steps_out, double *resid_out, int *status_out);
+/* nsteps steps of Eq. (4.1) for every member, as hq_step(ctx, nsteps).
+ * resid_out / status_out: as in hq_batch_solve (nullable).                 */
+hq_status hq_batch_step(hq_batch *b, long nsteps, double *resid_out, int *status_out);
+/* batch-level kernels launched (loop control; the members' kernels are
+ * counted in their contexts, see hq_profile_read) and time-loop iterations
+ * run, since creation (host outputs, nullable).                            */
+hq_status hq_batch_launches(const hq_batch *b, long *batch_kernels, long *loop_iterations);
+const char *hq_batch_last_error(const hq_batch *b);
+void hq_batch_destroy(hq_batch *b);
 
 #ifdef __cplusplus
 }

@@ -108,6 +108,7 @@ struct hq_ctx {
     double *eigwork = nullptr, *evals = nullptr, *mu = nullptr, *lam_p = nullptr;
     double *lam_r = nullptr, *resn = nullptr, *scal = nullptr, *signwork = nullptr;
     int *status = nullptr;
+    int *ipiv = nullptr;   // pivots of the blocked predictor elimination (2N)
     double *vn[3] = {nullptr, nullptr, nullptr};   // FP64 n-vectors (density, adjoint)
     double *pvec = nullptr;                        // power-iteration vector (N)
     // host state
@@ -133,8 +134,14 @@ struct hq_ctx {
     cudaStream_t cap = nullptr;
     // whole-phase graphs
     StepGraph sg[2];
-    cudaStream_t capA = nullptr, capB = nullptr, capC = nullptr;
-    long long *dcount = nullptr;   // device counters: [2 per phase graph]
+    cudaStream_t capA = nullptr, capB = nullptr, capC = nullptr, capD = nullptr;
+    // device words: [0..3] PCG loop counters of the phase graphs, [4..7] the
+    // same in batch graphs, [8..16] the batch time-loop state (BS_*)
+    long long *dcount = nullptr;
+    // batched form: launch counts of the phases as captured in a batch graph
+    StepGraph bsg[2];
+    long long bseen[4] = {0, 0, 0, 0};
+    int gen = 0;   // incremented whenever the captured graphs are dropped
     ~hq_ctx() {
         for (cudaEvent_t e : evpool) cudaEventDestroy(e);
         for (int i = 0; i < npgraph; i++) {
@@ -149,6 +156,7 @@ struct hq_ctx {
         if (capA) cudaStreamDestroy(capA);
         if (capB) cudaStreamDestroy(capB);
         if (capC) cudaStreamDestroy(capC);
+        if (capD) cudaStreamDestroy(capD);
     }
 };
 
@@ -242,6 +250,9 @@ bool valid_config(const hq_config *c, std::string *why) {
         return fail("mg_nu1, mg_nu2 must be in [1, 16]");
     if (c->mg_coarsest < 1 || c->mg_coarsest > 4) return fail("mg_coarsest must be in [1, 4]");
     if (!(c->mg_omega > 0.0 && c->mg_omega < 2.0)) return fail("mg_omega must be in (0, 2)");
+    if (c->grid_block != 0 && c->grid_block != 64 && c->grid_block != 128 && c->grid_block != 256)
+        return fail("grid_block must be 0, 64, 128 or 256");
+    if (c->grid_ctas < 0 || c->grid_ctas > 64) return fail("grid_ctas must be in [0, 64]");
     return true;
 }
 
@@ -284,7 +295,7 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
         v.n = (long)ms[l] * ms[l] * ms[l];
         v.h = (c->hi - c->lo) / (ms[l] + 1);
         v.c = 0.5 / (v.h * v.h);
-        v.g = make_geom(ms[l], N, (int)esz);
+        v.g = make_geom(ms[l], N, (int)esz, c->grid_block, c->grid_ctas);
         v.V = cv.take<double>(sizeof(double) * v.n);
         v.D = cv.take<double>(sizeof(double) * v.n);
         v.wD = cv.take<double>(sizeof(double) * v.n);
@@ -349,6 +360,7 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
     double *G2 = cv.take<double>(sizeof(double) * 4 * N2);
     double *Mw = cv.take<double>(sizeof(double) * 4 * N2);
     double *XY = cv.take<double>(sizeof(double) * 2 * N2);
+    int *ipiv = cv.take<int>(sizeof(int) * 2 * N);
     double *Cc = cv.take<double>(sizeof(double) * 2 * N2);
     double *T1 = cv.take<double>(sizeof(double) * 2 * N2);
     double *Shat = cv.take<double>(sizeof(double) * N2);
@@ -375,7 +387,7 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
     double *vn1 = cv.take<double>(sizeof(double) * n);
     double *vn2 = cv.take<double>(sizeof(double) * n);
     double *pvec = cv.take<double>(sizeof(double) * N);
-    long long *dcount = cv.take<long long>(sizeof(long long) * 8);
+    long long *dcount = cv.take<long long>(sizeof(long long) * 24);
     if (x) {
         x->pvec = pvec;
         x->dcount = dcount;
@@ -388,6 +400,7 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
         x->sc = sc; x->part = part; x->part2 = part2;
         x->gplan_uw = guw; x->gplan_max = gmax; x->gpart = gpart; x->tcpart = tcpart; x->tcimg = tcimg;
         x->tplan = tp; x->tpart = tpart;
+        x->ipiv = ipiv;
         x->G2 = G2; x->Mw = Mw; x->XY = XY; x->C = Cc; x->T1 = T1; x->Shat = Shat; x->Om = Om;
         x->Msm = Msm; x->Ksm = Ksm; x->Ssm = Ssm; x->Lm = Lm; x->Cm = Cm; x->Ym = Ym;
         x->Cv = Cvv; x->Cv2 = Cv2; x->eigwork = eigwork; x->evals = evals; x->mu = mu;
@@ -812,13 +825,13 @@ hq_status pcg_device(hq_ctx *x, const T *B, T *X, double rtol, int maxit, StepGr
 // A1-A3: W = G U (warm start from the previous G Uh), Gram of [U W], g.
 // sgr == nullptr: host-driven PCG; otherwise recorded into a phase graph.
 template <typename T>
-hq_status enqueue_a(hq_ctx *x, StepGraph *sgr) {
+hq_status enqueue_a(hq_ctx *x, StepGraph *sgr, long long *counters) {
     const int N = x->N;
     const size_t cnt = (size_t)x->n * N;
     T *U = (T *)x->U, *W = (T *)x->W;
     if (x->z_valid || sgr) HQ_TRY(copy_blk<T>(x, W, (const T *)x->Z, cnt));
     else HQ_CUDA(cudaMemsetAsync(W, 0, cnt * sizeof(T), x->st));
-    if (sgr) HQ_TRY(pcg_device<T>(x, U, W, x->cfg.cg_rtol, x->cfg.cg_maxit, *sgr, x->dcount));
+    if (sgr) HQ_TRY(pcg_device<T>(x, U, W, x->cfg.cg_rtol, x->cfg.cg_maxit, *sgr, counters));
     else HQ_TRY(pcg<T>(x, U, W, x->cfg.cg_rtol, x->cfg.cg_maxit, nullptr));
     gram_sym<T>(x, U, N, W, N, x->G2);
     // Msm = -Pwu (rows N..2N-1, columns 0..N-1 of G2); g = || W - U Pwu ||_h
@@ -831,7 +844,7 @@ hq_status enqueue_a(hq_ctx *x, StepGraph *sgr) {
 
 // B1-B5: predictor system, Uh, Shat, Z = G Uh, corrector (U <- U_{n+1}).
 template <typename T>
-hq_status enqueue_b(hq_ctx *x, StepGraph *sgr) {
+hq_status enqueue_b(hq_ctx *x, StepGraph *sgr, long long *counters) {
     const int N = x->N;
     const size_t cnt = (size_t)x->n * N;
     const double tau = x->cfg.tau;
@@ -849,7 +862,7 @@ hq_status enqueue_b(hq_ctx *x, StepGraph *sgr) {
                          x->st);
         tau_dev = x->scal + 8;
     }
-    launch_predictor_solve(N, tau, x->G2, x->Mw, x->XY, x->C, x->status, x->st, tau_dev);
+    launch_predictor_solve(N, tau, x->G2, x->Mw, x->XY, x->C, x->status, x->st, tau_dev, x->ipiv);
     block_gemm<T>(x, U, N, x->C, W, N, x->C + (size_t)N * N, nullptr, Uh, false, nullptr);
     // Shat = C^T G2 C, Om = -tau (Shat - I)
     launch_small_gemm(2 * N, N, 2 * N, 1.0, x->G2, 2 * N, false, x->C, N, false, 0.0, x->T1, N,
@@ -859,7 +872,8 @@ hq_status enqueue_b(hq_ctx *x, StepGraph *sgr) {
     if (x->cfg.z_warm_start) {
         // G Uh = W C1 + G W C2 and G W ~ W M with M = S^{-1} Puw (exact when
         // span(U) is G-invariant): start from Z0 = W (C1 + M C2)
-        launch_chol_solve(N, x->G2, 2 * N, x->G2 + N, 2 * N, x->Lm, x->Ym, x->status, x->st);
+        launch_spd_solve(N, x->G2, 2 * N, x->G2 + N, 2 * N, x->Mw, x->Lm, x->Ym, x->ipiv,
+                         x->status, x->st);
         launch_extract(N, N, 1.0, x->C, N, x->Cm, N, x->st);
         launch_small_gemm(N, N, N, 1.0, x->Ym, N, false, x->C + (size_t)N * N, N, false, 1.0,
                           x->Cm, N, x->st);
@@ -870,10 +884,20 @@ hq_status enqueue_b(hq_ctx *x, StepGraph *sgr) {
     } else {
         HQ_CUDA(cudaMemsetAsync(Z, 0, cnt * sizeof(T), x->st));
     }
-    if (sgr) HQ_TRY(pcg_device<T>(x, Uh, Z, x->cfg.cg_rtol, x->cfg.cg_maxit, *sgr, x->dcount + 2));
+    if (sgr) HQ_TRY(pcg_device<T>(x, Uh, Z, x->cfg.cg_rtol, x->cfg.cg_maxit, *sgr, counters + 2));
     else HQ_TRY(pcg<T>(x, Uh, Z, x->cfg.cg_rtol, x->cfg.cg_maxit, nullptr));
     block_gemm<T>(x, Z, N, x->Om, nullptr, 0, nullptr, Uh, U, false, nullptr);
     return HQ_OK;
+}
+
+// the private streams the captures of a context are recorded on
+bool ensure_cap_streams(hq_ctx *x) {
+    for (cudaStream_t *c : {&x->capA, &x->capB, &x->capC, &x->capD})
+        if (!*c && cudaStreamCreateWithFlags(c, cudaStreamNonBlocking) != cudaSuccess) {
+            *c = nullptr;
+            return false;
+        }
+    return true;
 }
 
 // Captures phase `which` (0: A, 1: B) once; later calls replay it.
@@ -882,11 +906,7 @@ StepGraph *phase_graph(hq_ctx *x, int which) {
     StepGraph &sgr = x->sg[which];
     if (sgr.tried) return sgr.ok ? &sgr : nullptr;
     sgr.tried = true;
-    for (cudaStream_t *c : {&x->capA, &x->capB, &x->capC})
-        if (!*c && cudaStreamCreateWithFlags(c, cudaStreamNonBlocking) != cudaSuccess) {
-            *c = nullptr;
-            return nullptr;
-        }
+    if (!ensure_cap_streams(x)) return nullptr;
     if (cudaStreamSynchronize(x->st) != cudaSuccess) return nullptr;
     cudaStream_t saved = x->st;
     x->st = x->capA;
@@ -896,7 +916,7 @@ StepGraph *phase_graph(hq_ctx *x, int which) {
     }
     x->capturing = true;
     x->cap_counts = sgr.fixed;
-    hq_status st = which == 0 ? enqueue_a<T>(x, &sgr) : enqueue_b<T>(x, &sgr);
+    hq_status st = which == 0 ? enqueue_a<T>(x, &sgr, x->dcount) : enqueue_b<T>(x, &sgr, x->dcount);
     x->capturing = false;
     x->cap_counts = nullptr;
     x->st = saved;
@@ -942,6 +962,7 @@ hq_status fold_graph_counts(hq_ctx *x) {
 // a new potential discards them (after folding their launch counts).
 hq_status drop_graphs(hq_ctx *x) {
     HQ_TRY(fold_graph_counts(x));
+    x->gen++;
     for (int i = 0; i < x->npgraph; i++) destroy_graph(x->pgraph[i]);
     x->npgraph = 0;
     for (StepGraph &sgr : x->sg) {
@@ -964,7 +985,7 @@ hq_status phase_a(hq_ctx *x) {
         HQ_CUDA(cudaGraphLaunch(sgr->exec, x->st));
         sgr->launches++;
     } else {
-        HQ_TRY(enqueue_a<T>(x, nullptr));
+        HQ_TRY(enqueue_a<T>(x, nullptr, nullptr));
     }
     HQ_TRY(check_launch(x));
     x->w_valid = true;
@@ -996,7 +1017,7 @@ hq_status phase_b(hq_ctx *x) {
         HQ_CUDA(cudaGraphLaunch(sgr->exec, x->st));
         sgr->launches++;
     } else {
-        HQ_TRY(enqueue_b<T>(x, nullptr));
+        HQ_TRY(enqueue_b<T>(x, nullptr, nullptr));
     }
     HQ_TRY(check_launch(x));
     x->w_valid = false;
@@ -1010,6 +1031,312 @@ hq_status phase_b(hq_ctx *x) {
 hq_status graph_status(hq_ctx *x) {
     HQ_TRY(sync_status(x, x->sc.status, "inner PCG"));
     return sync_status(x, x->status, "step");
+}
+
+}  // namespace
+
+// ===========================================================================
+// Batched form: the time loop of Algorithm 1 for many contexts in one graph.
+//
+//   init (steps, flags, start time)
+//   WHILE (some problem running) {
+//     arm: h_k = problem k running
+//     IF (h_k) { phase A_k; check g_k / cap / errors; IF (running) { phase B_k; ++steps } }
+//     ... one IF node per problem, all in parallel ...
+//     cond: wall-clock limit, loop condition
+//   }
+// Each phase holds its PCG loop as nested WHILE / IF nodes (pcg_device), so a
+// whole batched solve is one graph launch and one host synchronisation.
+// Phases of different problems share no buffers and run concurrently.
+// ===========================================================================
+struct hq_batch {
+    std::vector<hq_ctx *> ctx;
+    std::vector<int> gen;
+    cudaStream_t st = nullptr;                      // caller's stream
+    cudaStream_t capT = nullptr, capW = nullptr;    // captures: top graph, loop body
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::string err;
+    long launches = 0;   // batch-level kernels (init, arm, cond)
+    long loop_iters = 0;
+    ~hq_batch() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (g) cudaGraphDestroy(g);
+        if (capT) cudaStreamDestroy(capT);
+        if (capW) cudaStreamDestroy(capW);
+    }
+};
+
+namespace {
+
+hq_status bfail(hq_batch *b, hq_status st, const std::string &msg) {
+    b->err = msg;
+    return st;
+}
+
+long long *slot_of(hq_ctx *x) { return x->dcount + 8; }
+
+// Records problem x (phase A, the stopping test, phase B under an IF node)
+// into `body`, the IF body graph of this problem in the time-loop body.
+template <typename T>
+hq_status capture_problem(hq_ctx *x, cudaGraph_t body) {
+    ProfScope ps_(x);
+    for (StepGraph &c : x->bsg) c = StepGraph();
+    cudaStream_t saved = x->st;
+    x->st = x->capA;
+    if (cudaStreamBeginCaptureToGraph(x->capA, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        x->st = saved;
+        return fail(x, HQ_ERR_CUDA, "batch capture");
+    }
+    x->capturing = true;
+    x->cap_counts = x->bsg[0].fixed;
+    hq_status st = enqueue_a<T>(x, &x->bsg[0], x->dcount + 4);
+    bool ok = st == HQ_OK;
+    cudaGraph_t gA = nullptr, bodyB = nullptr;
+    cudaGraphConditionalHandle hB;
+    ok = ok && capture_graph_of(x->capA, &gA) &&
+         cudaGraphConditionalHandleCreate(&hB, gA, 0, 0) == cudaSuccess;
+    if (ok) {
+        launch_batch_check(slot_of(x), x->scal, x->status, x->sc.status, hB, x->capA);
+        ok = add_cond_node(x->capA, hB, cudaGraphCondTypeIf, &bodyB);
+    }
+    if (ok) {
+        x->st = x->capD;
+        ok = cudaStreamBeginCaptureToGraph(x->capD, bodyB, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            x->cap_counts = x->bsg[1].fixed;
+            st = enqueue_b<T>(x, &x->bsg[1], x->dcount + 4);
+            launch_batch_count(slot_of(x), x->capD);
+            cudaGraph_t tmp;
+            if (cudaStreamEndCapture(x->capD, &tmp) != cudaSuccess) ok = false;
+        }
+        x->st = x->capA;
+    }
+    cudaGraph_t tmpA;
+    if (cudaStreamEndCapture(x->capA, &tmpA) != cudaSuccess) ok = false;
+    x->st = saved;
+    x->capturing = false;
+    x->cap_counts = nullptr;
+    if (!ok || st != HQ_OK) {
+        cudaGetLastError();
+        return fail(x, HQ_ERR_CUDA, "batch capture of a problem");
+    }
+    return HQ_OK;
+}
+
+void batch_drop(hq_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->g) cudaGraphDestroy(b->g);
+    b->exec = nullptr;
+    b->g = nullptr;
+}
+
+hq_status batch_build(hq_batch *b) {
+    batch_drop(b);
+    const int K = (int)b->ctx.size();
+    for (hq_ctx *x : b->ctx)
+        if (!ensure_cap_streams(x)) return bfail(b, HQ_ERR_CUDA, "stream creation");
+    for (cudaStream_t *c : {&b->capT, &b->capW})
+        if (!*c && cudaStreamCreateWithFlags(c, cudaStreamNonBlocking) != cudaSuccess) {
+            *c = nullptr;
+            return bfail(b, HQ_ERR_CUDA, "stream creation");
+        }
+    BatchArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.count = K;
+    for (int k = 0; k < K; k++) a.slot[k] = slot_of(b->ctx[k]);
+    if (cudaStreamBeginCapture(b->capT, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return bfail(b, HQ_ERR_CUDA, "batch capture");
+    bool ok = true;
+    cudaGraph_t top = nullptr, wbody = nullptr;
+    cudaGraphConditionalHandle hT;
+    std::vector<cudaGraph_t> bodies(K, nullptr);
+    ok = capture_graph_of(b->capT, &top) &&
+         cudaGraphConditionalHandleCreate(&hT, top, 0, 0) == cudaSuccess;
+    if (ok) {
+        launch_batch_init(a, hT, b->capT);
+        ok = add_cond_node(b->capT, hT, cudaGraphCondTypeWhile, &wbody);
+    }
+    if (ok) {
+        ok = cudaStreamBeginCaptureToGraph(b->capW, wbody, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            for (int k = 0; k < K && ok; k++)
+                ok = cudaGraphConditionalHandleCreate(&a.h[k], wbody, 0, 0) == cudaSuccess;
+            if (ok) launch_batch_arm(a, b->capW);
+            // one IF node per problem, all depending on the arm kernel only
+            cudaStreamCaptureStatus cs;
+            cudaGraph_t gW = nullptr;
+            const cudaGraphNode_t *deps = nullptr;
+            const cudaGraphEdgeData *ed = nullptr;
+            size_t nd = 0;
+            ok = ok && cudaStreamGetCaptureInfo(b->capW, &cs, nullptr, &gW, &deps, &ed, &nd) ==
+                           cudaSuccess &&
+                 cs == cudaStreamCaptureStatusActive;
+            std::vector<cudaGraphNode_t> dv, ifn(K);
+            std::vector<cudaGraphEdgeData> ev;
+            if (ok) {
+                dv.assign(deps, deps + nd);
+                if (ed) ev.assign(ed, ed + nd);
+            }
+            for (int k = 0; k < K && ok; k++) {
+                alignas(cudaGraphNodeParams) unsigned char npbuf[sizeof(cudaGraphNodeParams)];
+                std::memset(npbuf, 0, sizeof(npbuf));
+                cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(npbuf);
+                np.type = cudaGraphNodeTypeConditional;
+                np.conditional.handle = a.h[k];
+                np.conditional.type = cudaGraphCondTypeIf;
+                np.conditional.size = 1;
+                ok = cudaGraphAddNode(&ifn[k], gW, dv.data(), ed ? ev.data() : nullptr, nd, &np) ==
+                     cudaSuccess;
+                if (ok) bodies[k] = np.conditional.phGraph_out[0];
+            }
+            ok = ok && cudaStreamUpdateCaptureDependencies(b->capW, ifn.data(), nullptr, K,
+                                                           cudaStreamSetCaptureDependencies) ==
+                           cudaSuccess;
+            if (ok) launch_batch_cond(a, hT, b->capW);
+            cudaGraph_t tmp;
+            if (cudaStreamEndCapture(b->capW, &tmp) != cudaSuccess) ok = false;
+        }
+    }
+    hq_status st = HQ_OK;
+    for (int k = 0; k < K && ok; k++) {
+        hq_ctx *x = b->ctx[k];
+        st = x->mixed ? capture_problem<float>(x, bodies[k]) : capture_problem<double>(x, bodies[k]);
+        if (st != HQ_OK) {
+            ok = false;
+            b->err = "problem " + std::to_string(k) + ": " + x->err;
+        }
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->capT, &g);
+    if (!ok || e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        if (b->err.empty()) b->err = "batch graph capture failed";
+        return st != HQ_OK ? st : HQ_ERR_CUDA;
+    }
+    b->g = g;
+    if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        batch_drop(b);
+        return bfail(b, HQ_ERR_CUDA, "batch graph instantiation failed");
+    }
+    for (int k = 0; k < K; k++) b->gen[k] = b->ctx[k]->gen;
+    return HQ_OK;
+}
+
+// mode 0: Algorithm 1 per problem (stop at g < eps[k] or max_steps);
+// mode 1: max_steps steps per problem
+hq_status batch_run(hq_batch *b, int mode, const double *eps, long max_steps, double timeout_s,
+                    long *steps_out, double *resid_out, int *status_out) {
+    const int K = (int)b->ctx.size();
+    b->err.clear();
+    for (int k = 0; k < K; k++) {
+        hq_ctx *x = b->ctx[k];
+        if (!x->have_V || !x->have_U)
+            return bfail(b, HQ_ERR_STATE, "problem " + std::to_string(k) +
+                                              ": potential or initial block not set");
+    }
+    bool stale = !b->exec;
+    for (int k = 0; k < K; k++) stale = stale || b->gen[k] != b->ctx[k]->gen;
+    // the contexts' own streams may still hold work (uploads)
+    for (hq_ctx *x : b->ctx)
+        if (cudaStreamSynchronize(x->st) != cudaSuccess) return bfail(b, HQ_ERR_CUDA, "sync");
+    if (stale) HQ_TRY(batch_build(b));
+    for (int k = 0; k < K; k++) {
+        hq_ctx *x = b->ctx[k];
+        if (!x->z_valid) {
+            // a zero warm start of W = G U, as the host path uses before the first step
+            if (cudaMemsetAsync(x->Z, 0, (size_t)x->n * x->N * x->esz, b->st) != cudaSuccess)
+                return bfail(b, HQ_ERR_CUDA, "memset");
+            x->z_valid = true;
+        }
+        long long w[9];
+        const double e = mode == 0 ? eps[k] : 0.0;
+        std::memcpy(&w[BS_EPS], &e, sizeof(double));
+        w[BS_STEPS] = 0;
+        w[BS_DONE] = 0;
+        w[BS_AEXEC] = 0;
+        w[BS_MODE] = mode;
+        w[BS_MAXSTEPS] = max_steps;
+        w[BS_T0] = 0;
+        w[BS_TIMEOUT] = (k == 0 && timeout_s > 0) ? (long long)(timeout_s * 1e9) : 0;
+        w[BS_ITERS] = 0;
+        if (cudaMemcpyAsync(slot_of(x), w, sizeof(w), cudaMemcpyHostToDevice, b->st) != cudaSuccess ||
+            cudaMemsetAsync(x->status, 0, sizeof(int), b->st) != cudaSuccess ||
+            cudaMemsetAsync(x->sc.status, 0, sizeof(int), b->st) != cudaSuccess)
+            return bfail(b, HQ_ERR_CUDA, "batch staging");
+    }
+    if (cudaGraphLaunch(b->exec, b->st) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, HQ_ERR_CUDA, "batch graph launch failed");
+    }
+    // read back: loop state, PCG counters, g
+    std::vector<long long> words((size_t)K * 13);
+    std::vector<double> g(K);
+    for (int k = 0; k < K; k++) {
+        hq_ctx *x = b->ctx[k];
+        if (cudaMemcpyAsync(&words[(size_t)k * 13], x->dcount + 4, 13 * sizeof(long long),
+                            cudaMemcpyDeviceToHost, b->st) != cudaSuccess ||
+            cudaMemcpyAsync(&g[k], x->scal, sizeof(double), cudaMemcpyDeviceToHost, b->st) !=
+                cudaSuccess)
+            return bfail(b, HQ_ERR_CUDA, "batch read-back");
+    }
+    cudaError_t ce = cudaStreamSynchronize(b->st);
+    if (ce != cudaSuccess) return bfail(b, HQ_ERR_CUDA, cudaGetErrorString(ce));
+    hq_status first = HQ_OK;
+    long iters = 0;
+    for (int k = 0; k < K; k++) {
+        hq_ctx *x = b->ctx[k];
+        const long long *c = &words[(size_t)k * 13];   // c[0..3] PCG counters, c[4..12] slot
+        const long long *sl = c + 4;
+        const long steps = (long)sl[BS_STEPS], aexec = (long)sl[BS_AEXEC];
+        if (k == 0) iters = (long)sl[BS_ITERS];
+        x->step += steps;
+        x->w_valid = aexec > steps;
+        x->last_g = g[k];
+        // launch accounting (see fold_graph_counts)
+        long long d[4];
+        for (int i = 0; i < 4; i++) {
+            d[i] = c[i] - x->bseen[i];
+            x->bseen[i] = c[i];
+        }
+        for (int cl = 0; cl < HQ_K_NCLASS; cl++)
+            x->launches[cl] += x->bsg[0].fixed[cl] * aexec + x->bsg[1].fixed[cl] * steps +
+                               x->bsg[0].part1[cl] * d[0] + x->bsg[0].part2[cl] * d[1] +
+                               x->bsg[1].part1[cl] * d[2] + x->bsg[1].part2[cl] * d[3];
+        x->stat_solves += aexec + steps;
+        x->stat_iters += (long)(d[0] + d[2]);
+        hq_status stk = HQ_OK;
+        switch (sl[BS_DONE]) {
+            case BD_CONVERGED: stk = HQ_OK; break;
+            case BD_MAXSTEPS:
+                stk = mode == 0 ? fail(x, HQ_ERR_NOT_CONVERGED, "Algorithm 1 reached max_steps")
+                                : HQ_OK;
+                break;
+            case BD_TIMEOUT: stk = fail(x, HQ_ERR_TIMEOUT, "batch wall-clock limit reached"); break;
+            default: {
+                stk = graph_status(x);
+                if (stk == HQ_OK)
+                    stk = std::isfinite(g[k]) ? fail(x, HQ_ERR_STATE, "batch loop ended early")
+                                              : fail(x, HQ_ERR_NONFINITE, "gradient norm is not finite");
+            }
+        }
+        if (stk == HQ_OK && sl[BS_DONE] != BD_ERROR) stk = graph_status(x);
+        if (steps_out) steps_out[k] = steps;
+        if (resid_out) resid_out[k] = g[k];
+        if (status_out) status_out[k] = stk;
+        if (stk != HQ_OK && first == HQ_OK) {
+            first = stk;
+            b->err = "problem " + std::to_string(k) + ": " + x->err;
+        }
+    }
+    b->loop_iters += iters;
+    b->launches += 1 + 2 * iters;
+    return first;
 }
 
 }  // namespace
@@ -1596,9 +1923,10 @@ hq_status hq_init(const hq_config *cfg, void *d_workspace, size_t bytes, void *c
     // the status words and counters start cleared
     cudaError_t e = cudaMemsetAsync(x->sc.status, 0, sizeof(int), x->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(x->status, 0, sizeof(int), x->st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(x->dcount, 0, sizeof(long long) * 8, x->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(x->dcount, 0, sizeof(long long) * 24, x->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(x->st);
     if (x->mixed) hq::tc_prepare();
+    hq::lu_prepare();
     if (e != cudaSuccess) {
         delete x;
         return HQ_ERR_CUDA;
@@ -1911,5 +2239,157 @@ const char *hq_status_string(hq_status s) {
 }
 
 void hq_destroy(hq_ctx *x) { delete x; }
+
+// ---------------------------------------------------------------------------
+// launch-shape autotuner
+// ---------------------------------------------------------------------------
+static const int TUNE_BLOCKS[] = {64, 128, 256};
+static const int TUNE_CTAS[] = {4, 8, 16, 32};
+
+size_t hq_tune_workspace_bytes(const hq_config *cfg) {
+    if (!valid_config(cfg, nullptr)) return 0;
+    size_t need = 0;
+    try {
+        for (int b : TUNE_BLOCKS)
+            for (int c : TUNE_CTAS) {
+                hq_config t = *cfg;
+                t.grid_block = b;
+                t.grid_ctas = c;
+                need = std::max(need, carve(nullptr, &t, nullptr));
+            }
+    } catch (...) {
+        return 0;
+    }
+    return need;
+}
+
+hq_status hq_tune(const hq_config *cfg, void *d_workspace, size_t bytes, void *cuda_stream,
+                  hq_config *tuned, double *ms_out) {
+    HQ_API_BEGIN
+    if (!cfg || !tuned) return HQ_ERR_ARG;
+    const size_t need = hq_tune_workspace_bytes(cfg);
+    if (need == 0) return HQ_ERR_ARG;
+    if (!d_workspace || bytes < need) return HQ_ERR_NOMEM;
+    const int m = cfg->m;
+    const long n = (long)m * m * m;
+    // harmonic potential on the configured box (timing input)
+    std::vector<double> V((size_t)n);
+    const double h = (cfg->hi - cfg->lo) / (m + 1);
+    for (int k = 0; k < m; k++)
+        for (int j = 0; j < m; j++)
+            for (int i = 0; i < m; i++) {
+                const double xx = cfg->lo + h * (i + 1), yy = cfg->lo + h * (j + 1),
+                             zz = cfg->lo + h * (k + 1);
+                V[(size_t)i + (size_t)m * (j + (size_t)m * k)] = 0.5 * (xx * xx + yy * yy + zz * zz);
+            }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return HQ_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return HQ_ERR_CUDA;
+    }
+    const int iters = 10;
+    double best = 1e300;
+    hq_config best_cfg = *cfg;
+    hq_status st = HQ_OK;
+    for (int b : TUNE_BLOCKS) {
+        for (int c : TUNE_CTAS) {
+            hq_config t = *cfg;
+            t.grid_block = b;
+            t.grid_ctas = c;
+            hq_ctx *x = nullptr;
+            st = hq_init(&t, d_workspace, bytes, cuda_stream, &x);
+            if (st != HQ_OK) break;
+            {
+                ProfScope ps_(x);
+                st = hq_set_potential(x, V.data(), 0);
+                const size_t cnt = (size_t)n * x->N;
+                if (st == HQ_OK) {
+                    if (x->mixed) launch_fill_hash<float>((long)cnt, 12345u, (float *)x->U, s);
+                    else launch_fill_hash<double>((long)cnt, 12345u, (double *)x->U, s);
+                    if (cudaMemsetAsync(x->W, 0, cnt * x->esz, s) != cudaSuccess) st = HQ_ERR_CUDA;
+                }
+                // one untimed solve (captures the PCG graph), then the timed one
+                float ms = 0.f;
+                for (int rep = 0; rep < 2 && st == HQ_OK; rep++) {
+                    if (rep == 1 && cudaEventRecord(e0, s) != cudaSuccess) st = HQ_ERR_CUDA;
+                    if (st == HQ_OK)
+                        st = x->mixed ? pcg<float>(x, (const float *)x->U, (float *)x->W, 0.0, iters, nullptr)
+                                      : pcg<double>(x, (const double *)x->U, (double *)x->W, 0.0, iters, nullptr);
+                    if (rep == 1 && st == HQ_OK) {
+                        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                            st = HQ_ERR_CUDA;
+                    }
+                }
+                if (st == HQ_OK && ms / iters < best) {
+                    best = ms / iters;
+                    best_cfg = t;
+                }
+            }
+            hq_destroy(x);
+            if (st != HQ_OK) break;
+        }
+        if (st != HQ_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != HQ_OK) return st;
+    *tuned = best_cfg;
+    if (ms_out) *ms_out = best;
+    return HQ_OK;
+    HQ_API_END
+}
+
+hq_status hq_batch_create(hq_ctx *const *ctxs, int count, void *cuda_stream, hq_batch **out) {
+    HQ_API_BEGIN
+    if (!out) return HQ_ERR_ARG;
+    *out = nullptr;
+    if (!ctxs || count < 1 || count > BATCH_MAX) return HQ_ERR_ARG;
+    for (int i = 0; i < count; i++) {
+        if (!ctxs[i]) return HQ_ERR_ARG;
+        for (int j = 0; j < i; j++)
+            if (ctxs[j] == ctxs[i]) return HQ_ERR_ARG;
+    }
+    hq_batch *b = new hq_batch();
+    b->ctx.assign(ctxs, ctxs + count);
+    b->gen.assign(count, -1);
+    b->st = (cudaStream_t)cuda_stream;
+    *out = b;
+    return HQ_OK;
+    HQ_API_END
+}
+
+hq_status hq_batch_solve(hq_batch *b, const double *eps, long max_steps, double timeout_s,
+                         long *steps_out, double *resid_out, int *status_out) {
+    HQ_API_BEGIN
+    if (!b) return HQ_ERR_ARG;
+    if (!eps || max_steps < 0 || timeout_s < 0 || !std::isfinite(timeout_s))
+        return bfail(b, HQ_ERR_ARG, "bad argument");
+    for (size_t k = 0; k < b->ctx.size(); k++)
+        if (!(eps[k] > 0.0)) return bfail(b, HQ_ERR_ARG, "eps must be > 0");
+    return batch_run(b, 0, eps, max_steps, timeout_s, steps_out, resid_out, status_out);
+    HQ_API_END
+}
+
+hq_status hq_batch_step(hq_batch *b, long nsteps, double *resid_out, int *status_out) {
+    HQ_API_BEGIN
+    if (!b) return HQ_ERR_ARG;
+    if (nsteps < 0) return bfail(b, HQ_ERR_ARG, "nsteps must be >= 0");
+    return batch_run(b, 1, nullptr, nsteps, 0.0, nullptr, resid_out, status_out);
+    HQ_API_END
+}
+
+hq_status hq_batch_launches(const hq_batch *b, long *batch_kernels, long *loop_iterations) {
+    if (!b) return HQ_ERR_ARG;
+    if (batch_kernels) *batch_kernels = b->launches;
+    if (loop_iterations) *loop_iterations = b->loop_iters;
+    return HQ_OK;
+}
+
+const char *hq_batch_last_error(const hq_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+void hq_batch_destroy(hq_batch *b) { delete b; }
 
 }  // extern "C"

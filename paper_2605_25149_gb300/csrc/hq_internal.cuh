@@ -34,7 +34,9 @@ struct GridGeom {
     int gx, gy;     // grid shape
     int ppt;        // points per thread (consecutive slabs of ty points)
 };
-GridGeom make_geom(int m, int N, int elem_bytes);
+// block: threads per CTA (0: 256); ctas_per_sm: target CTAs per SM of the
+// grid (0: 16) -- the two launch-shape parameters the autotuner searches
+GridGeom make_geom(int m, int N, int elem_bytes, int block = 0, int ctas_per_sm = 0);
 
 // per-column PCG scalars, all device arrays of length N (FP64)
 struct PcgScalars {
@@ -115,17 +117,51 @@ void launch_finalize(int mode, int N, int gy, const double *part, const double *
 void launch_pcg_cond(const int *num_active, int *iter, int maxit, cudaGraphConditionalHandle h,
                      cudaStream_t s);
 // whole-step graphs: hw = (num_active[0] > 0 && maxit > 0) before the loop;
-// in the loop body: ++iter[0], counters[0] += 1, counters[1] += active,
-// hif = active, hw = active && iter < maxit, and ST_PCG_MAXIT in status when
+// in the loop body: ++iter[0], more = active && iter < maxit, counters[0] += 1,
+// counters[1] += more, hif = hw = more, and ST_PCG_MAXIT in status when
 // columns are still active at the cap (check_maxit)
 void launch_pcg_cond_init(const int *num_active, int maxit, cudaGraphConditionalHandle hw,
                           cudaStream_t s);
 void launch_pcg_cond2(const int *num_active, int *iter, int maxit, cudaGraphConditionalHandle hw,
                       cudaGraphConditionalHandle hif, long long *counters, int *status,
                       int check_maxit, cudaStream_t s);
+// out[i] = pseudo-random value in [-1, 1) from a hash of (seed, i)
+template <typename T>
+void launch_fill_hash(long count, unsigned long long seed, T *out, cudaStream_t s);
 // sets the dynamic shared-memory limits of the tensor-core kernels (call once,
 // outside any stream capture)
 void tc_prepare();
+
+// ----------------------------------------------------------------------------
+// batched form (k_batch.cu): device state of the time loop of one problem in
+// a batch graph, nine 64-bit words in the problem's workspace (T0, TIMEOUT
+// and ITERS are used in the first problem's words only)
+// ----------------------------------------------------------------------------
+enum { BS_STEPS = 0, BS_DONE = 1, BS_AEXEC = 2, BS_MODE = 3, BS_MAXSTEPS = 4, BS_EPS = 5,
+       BS_T0 = 6, BS_TIMEOUT = 7, BS_ITERS = 8 };
+// BS_DONE codes
+enum { BD_RUNNING = 0, BD_CONVERGED = 1, BD_MAXSTEPS = 2, BD_ERROR = 3, BD_TIMEOUT = 4 };
+constexpr int BATCH_MAX = 64;
+struct BatchArgs {
+    int count;
+    long long *slot[BATCH_MAX];
+    cudaGraphConditionalHandle h[BATCH_MAX];   // per-problem IF handles (arm)
+};
+// before the time loop: steps, done and A-executions cleared, start time
+// stamped in slot[0], hT = (count > 0)
+void launch_batch_init(const BatchArgs &a, cudaGraphConditionalHandle hT, cudaStream_t s);
+// start of each time-loop iteration: a problem in step mode that has taken
+// its steps is done; h[k] = !done
+void launch_batch_arm(const BatchArgs &a, cudaStream_t s);
+// after phase A of one problem: stop on error, nonfinite g, g < eps (solve
+// mode) or the step cap; hB = still running
+void launch_batch_check(long long *slot, const double *g, const int *st1, const int *st2,
+                        cudaGraphConditionalHandle hB, cudaStream_t s);
+// after phase B of one problem: ++steps
+void launch_batch_count(long long *slot, cudaStream_t s);
+// end of each time-loop iteration: ++ITERS, wall-clock limit (slot[0] T0 /
+// TIMEOUT), hT = any problem still running
+void launch_batch_cond(const BatchArgs &a, cudaGraphConditionalHandle hT, cudaStream_t s);
 
 // adjoint row kernels (FP64): mode 0 out[p] = scale sum_c w_c u_pc^2,
 // mode 1 out[p] = scale sum_c u_pc v_pc
@@ -229,9 +265,11 @@ void launch_small_gemm(int M, int Ncol, int K, double alpha, const double *A, in
 //   [I - tau/2 Puw, tau/2 S; -tau/2 Q, I + tau/2 Pwu] [X;Y] = [S; Pwu]
 // and solve by LU with partial pivoting.  Mwork: 4N^2, XY: 2N x N.  Then
 // C = [I - tau Y; tau X] (2N x N).
+// ipiv: 2N ints of scratch for the blocked elimination used when 2N > 64
+// (nullptr: always the one-CTA kernel)
 void launch_predictor_solve(int N, double tau, const double *G2, double *Mwork, double *XY,
                             double *C, int *status, cudaStream_t s,
-                            const double *tau_dev = nullptr);
+                            const double *tau_dev = nullptr, int *ipiv = nullptr);
 // largest eigenvalue of sym(A) (N x N, leading dimension lda) -> out[0];
 // vec (N): warm-start vector, updated (all zero: fixed start)
 void launch_top_eig(int N, const double *A, int lda, double *vec, double *out, cudaStream_t s);
@@ -256,6 +294,18 @@ void launch_sym_eig(int N, const double *A, double *work, double *evals, double 
 void launch_rr_reduce(int N, const double *K, const double *S, double *L, double *Cm,
                       int *status, cudaStream_t s);
 // X = A^{-1} B for SPD A by Cholesky (one CTA); L: N x N work
+// sets the shared-memory limit of the blocked elimination's panel kernel
+// (call once, outside any stream capture)
+void lu_prepare();
+// in place: XY (nn x nrhs) <- Mw^-1 XY, Mw (nn x nn) overwritten; blocked
+// elimination with partial pivoting (ipiv: nn ints of scratch)
+void launch_lu_solve(int nn, int nrhs, double *Mw, double *XY, int *ipiv, int *status,
+                     cudaStream_t s);
+// X = A^-1 B, A N x N symmetric positive definite (lda), B N x N (ldb): the
+// one-CTA Cholesky kernel (factor into L) for N <= 32 or ipiv == nullptr,
+// else the blocked elimination in the N x N scratch Mw
+void launch_spd_solve(int N, const double *A, int lda, const double *B, int ldb, double *Mw,
+                      double *L, double *X, int *ipiv, int *status, cudaStream_t s);
 void launch_chol_solve(int N, const double *A, int lda, const double *B, int ldb, double *L,
                        double *X, int *status, cudaStream_t s);
 // c = L^{-T} y  (columns of Y), Cv output N x N

@@ -108,21 +108,21 @@ __global__ void __launch_bounds__(256) k_gram_partial(GramPlan P, const T *A1, i
         for (int j = 0; j < 4; j++) dst[(ty + 16 * i) * GT + tx + 16 * j] = (double)acc[i][j];
 }
 
+// one thread per tile entry (grid: tiles x entry blocks), chunks summed in order
 __global__ void k_gram_reduce(GramPlan P, const double *partials, double w, double *out) {
     const int tile = blockIdx.x;
     int ta, tb;
     tile_of(tile, P.tiles_a, P.sym, ta, tb);
-    for (int e = threadIdx.x; e < GT * GT; e += blockDim.x) {
-        int la = e / GT, lb = e % GT;
-        int a = ta * GT + la, b = tb * GT + lb;
-        if (a >= P.na || b >= P.nb) continue;
-        double s = 0.0;
-        for (int c = 0; c < P.chunks; c++)
-            s += partials[((size_t)c * P.ntiles + tile) * GT * GT + e];
-        s *= w;
-        out[(size_t)a * P.nb + b] = s;
-        if (P.sym && ta != tb) out[(size_t)b * P.nb + a] = s;
-    }
+    const int e = blockIdx.y * blockDim.x + threadIdx.x;
+    if (e >= GT * GT) return;
+    const int la = e / GT, lb = e % GT;
+    const int a = ta * GT + la, b = tb * GT + lb;
+    if (a >= P.na || b >= P.nb) return;
+    double s = 0.0;
+    for (int c = 0; c < P.chunks; c++) s += partials[((size_t)c * P.ntiles + tile) * GT * GT + e];
+    s *= w;
+    out[(size_t)a * P.nb + b] = s;
+    if (P.sym && ta != tb) out[(size_t)b * P.nb + a] = s;
 }
 
 template <typename T>
@@ -131,7 +131,8 @@ void launch_gram(const GramPlan &p, const T *A1, int na1, const T *A2, int na2, 
                  cudaStream_t s) {
     HQ_LAUNCH(HQ_K_GRAM, k_gram_partial<T><<<dim3(p.ntiles, p.chunks), 256, 0, s>>>(p, A1, na1, A2, na2, B1, nb1,
                                                                B2, nb2, partials));
-    HQ_LAUNCH(HQ_K_GRAM, k_gram_reduce<<<p.ntiles, 256, 0, s>>>(p, partials, w, out));
+    HQ_LAUNCH(HQ_K_GRAM, k_gram_reduce<<<dim3(p.ntiles, (GT * GT + 255) / 256), 256, 0, s>>>(
+                             p, partials, w, out));
 }
 
 // ---------------------------------------------------------------------------
@@ -425,11 +426,340 @@ __global__ void __launch_bounds__(1024) k_predictor_solve(int N, double tau_arg,
     }
 }
 
-void launch_predictor_solve(int N, double tau, const double *G2, double *Mwork, double *XY,
-                            double *C, int *status, cudaStream_t s, const double *tau_dev) {
-    size_t shm = sizeof(double) * (2 * N + 1024) + sizeof(int) * 1024;
-    HQ_LAUNCH(HQ_K_SMALL, k_predictor_solve<<<1, 1024, shm, s>>>(N, tau, G2, Mwork, XY, C, status,
-                                                                  tau_dev));
+// ---------------------------------------------------------------------------
+// Dense FP64 solve A X = B (A nn x nn, B nn x nrhs, both row-major and
+// contiguous, overwritten): Gaussian elimination with partial pivoting on the
+// augmented matrix [A | B] in panels of PB columns (pivot: largest |entry| in
+// the column, first row on ties, as in the one-CTA kernels), then blocked
+// back substitution.  Per panel: the panel factorisation (one CTA), row swaps
+// + unit-lower triangular solve of the panel rows for every column to the
+// right (one thread per column), the trailing update (64 x 64 tiles over many
+// CTAs); per block of the back substitution: the diagonal triangle (one
+// thread per right-hand side) and the update of the rows above (tiles).
+// ---------------------------------------------------------------------------
+constexpr int PB = 32;
+
+__global__ void k_pred_build(int N, double tau_arg, const double *tau_dev, const double *G2,
+                             double *Mw, double *XY) {
+    const double tau = tau_dev ? tau_dev[0] : tau_arg;
+    const double ht = 0.5 * tau;
+    const int nn = 2 * N, ld2 = 2 * N;
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < (long)nn * nn + (long)nn * N;
+         idx += (long)gridDim.x * blockDim.x) {
+        if (idx < (long)nn * nn) {
+            int i = (int)(idx / nn), j = (int)(idx % nn);
+            double d = (i == j) ? 1.0 : 0.0;
+            double v;
+            if (i < N && j < N) v = ht * G2[(size_t)i * ld2 + N + j] * -1.0 + d;
+            else if (i < N) v = ht * G2[(size_t)i * ld2 + (j - N)];
+            else if (j < N) v = -ht * G2[(size_t)i * ld2 + N + j];
+            else v = d + ht * G2[(size_t)i * ld2 + (j - N)];
+            Mw[idx] = v;
+        } else {
+            long r = idx - (long)nn * nn;
+            int i = (int)(r / N), j = (int)(r % N);
+            XY[r] = G2[(size_t)i * ld2 + j];
+        }
+    }
+}
+
+// factorise columns [k0, k0 + nb) of rows [k0, nn): the panel is staged in
+// shared memory (row stride nb + 1), pivots into ipiv
+__global__ void __launch_bounds__(512) k_lu_panel(int nn, int k0, int nb, double *Mw, int *ipiv,
+                                                  int *status) {
+    extern __shared__ double P[];
+    __shared__ double wv[16];
+    __shared__ int wi[16];
+    __shared__ int piv_s;
+    __shared__ double pval_s;
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int R = nn - k0, ld = nb + 1;
+    for (int idx = tid; idx < R * nb; idx += T) {
+        const int r = idx / nb, c = idx % nb;
+        P[r * ld + c] = Mw[(size_t)(k0 + r) * nn + k0 + c];
+    }
+    __syncthreads();
+    bool singular = false;
+    for (int jj = 0; jj < nb; jj++) {
+        // pivot: largest |P[i][jj]|, i >= jj, first row on ties
+        double best = -1.0;
+        int bi = R;
+        for (int r = jj + tid; r < R; r += T) {
+            const double v = fabs(P[r * ld + jj]);
+            if (v > best) { best = v; bi = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double v2 = __shfl_down_sync(0xffffffffu, best, o);
+            const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
+            if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
+        }
+        if (lane == 0) { wv[warp] = best; wi[warp] = bi; }
+        __syncthreads();
+        if (warp == 0) {
+            const int nw = T >> 5;
+            best = lane < nw ? wv[lane] : -1.0;
+            bi = lane < nw ? wi[lane] : R;
+            for (int o = 16; o > 0; o >>= 1) {
+                const double v2 = __shfl_down_sync(0xffffffffu, best, o);
+                const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
+                if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
+            }
+            if (lane == 0) { piv_s = bi; pval_s = best; }
+        }
+        __syncthreads();
+        const int piv = piv_s;
+        const double pval = pval_s;
+        if (!(pval > 0.0) || !isfinite(pval)) {
+            if (tid == 0) {
+                atomicOr(status, ST_SINGULAR);
+                for (int t = jj; t < nb; t++) ipiv[k0 + t] = k0 + t;
+            }
+            singular = true;
+            break;
+        }
+        if (tid == 0) ipiv[k0 + jj] = k0 + piv;
+        if (piv != jj && tid < nb) {
+            const double t = P[jj * ld + tid];
+            P[jj * ld + tid] = P[piv * ld + tid];
+            P[piv * ld + tid] = t;
+        }
+        __syncthreads();
+        const double djj = P[jj * ld + jj];
+        for (int r = jj + 1 + tid; r < R; r += T) {
+            const double l = P[r * ld + jj] / djj;
+            P[r * ld + jj] = l;
+            for (int c = jj + 1; c < nb; c++) P[r * ld + c] -= l * P[jj * ld + c];
+        }
+        __syncthreads();
+    }
+    (void)singular;
+    __syncthreads();
+    for (int idx = tid; idx < R * nb; idx += T) {
+        const int r = idx / nb, c = idx % nb;
+        Mw[(size_t)(k0 + r) * nn + k0 + c] = P[r * ld + c];
+    }
+}
+
+size_t lu_panel_smem(int nn, int nb) { return sizeof(double) * (size_t)nn * (nb + 1); }
+int lu_block(int nn) { return nn > 768 ? 16 : PB; }
+
+// columns right of the panel (matrix columns [k0+nb, nn), then the N RHS
+// columns): the panel's row swaps in order, then the unit-lower solve with
+// the panel's L11 staged in shared memory
+__global__ void __launch_bounds__(128) k_lu_trsm(int nn, int N, int k0, int nb, double *Mw,
+                                                 double *XY, const int *ipiv) {
+    __shared__ double L[PB][PB + 1];
+    for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+        const int r = idx / nb, q = idx % nb;
+        L[r][q] = Mw[(size_t)(k0 + r) * nn + k0 + q];
+    }
+    __syncthreads();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ncm = nn - k0 - nb;
+    if (t >= ncm + N) return;
+    double *col;
+    size_t ld;
+    if (t < ncm) { col = Mw + k0 + nb + t; ld = nn; }
+    else { col = XY + (t - ncm); ld = N; }
+    for (int j = 0; j < nb; j++) {
+        const int piv = ipiv[k0 + j];
+        if (piv != k0 + j) {
+            double a = col[(size_t)(k0 + j) * ld], b = col[(size_t)piv * ld];
+            col[(size_t)(k0 + j) * ld] = b;
+            col[(size_t)piv * ld] = a;
+        }
+    }
+    double x[PB];
+#pragma unroll
+    for (int r = 0; r < PB; r++) {
+        if (r < nb) {
+            double v = col[(size_t)(k0 + r) * ld];
+#pragma unroll
+            for (int q = 0; q < r; q++) v -= L[r][q] * x[q];
+            x[r] = v;
+            col[(size_t)(k0 + r) * ld] = v;
+        }
+    }
+}
+
+// trailing update: rows [k0+nb, nn) of every column right of the panel
+// (matrix and RHS) -= L21 (rows x nb) * U12 (nb x cols); 64 x 64 tiles
+__global__ void __launch_bounds__(256) k_lu_update(int nn, int N, int k0, int nb, double *Mw,
+                                                     double *XY) {
+    __shared__ double Ls[64][PB + 1];
+    __shared__ double Us[PB][64 + 1];
+    const int r0 = k0 + nb + blockIdx.y * 64;
+    const int ncm = nn - k0 - nb;
+    const int c0 = blockIdx.x * 64;   // index over [matrix cols right of panel | RHS cols]
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < 64 * PB; idx += 256) {
+        const int rr = idx / PB, q = idx % PB;
+        const int row = r0 + rr;
+        Ls[rr][q] = (row < nn && q < nb) ? Mw[(size_t)row * nn + k0 + q] : 0.0;
+    }
+    for (int idx = tid; idx < PB * 64; idx += 256) {
+        const int q = idx / 64, cc = idx % 64;
+        const int t = c0 + cc;
+        double v = 0.0;
+        if (q < nb && t < ncm + N)
+            v = t < ncm ? Mw[(size_t)(k0 + q) * nn + k0 + nb + t] : XY[(size_t)(k0 + q) * N + (t - ncm)];
+        Us[q][cc] = v;
+    }
+    __syncthreads();
+    const int tx = tid & 15, ty = tid >> 4;
+    for (int a = 0; a < 4; a++) {
+        const int rr = ty * 4 + a, row = r0 + rr;
+        if (row >= nn) continue;
+        for (int b = 0; b < 4; b++) {
+            const int cc = tx * 4 + b, t = c0 + cc;
+            if (t >= ncm + N) continue;
+            double acc = 0.0;
+            for (int q = 0; q < nb; q++) acc += Ls[rr][q] * Us[q][cc];
+            double *dst = t < ncm ? &Mw[(size_t)row * nn + k0 + nb + t] : &XY[(size_t)row * N + (t - ncm)];
+            *dst -= acc;
+        }
+    }
+}
+
+// back substitution, diagonal block [k0, k0+nb): X_b = U_bb^-1 Y_b (one thread
+// per RHS column, U_bb staged in shared memory)
+__global__ void __launch_bounds__(128) k_lu_back_diag(int nn, int N, int k0, int nb,
+                                                      const double *Mw, double *XY) {
+    __shared__ double Ub[PB][PB + 1];
+    for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+        const int r = idx / nb, q = idx % nb;
+        Ub[r][q] = Mw[(size_t)(k0 + r) * nn + k0 + q];
+    }
+    __syncthreads();
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    double x[PB];
+#pragma unroll
+    for (int r = PB - 1; r >= 0; r--) {
+        if (r < nb) {
+            double v = XY[(size_t)(k0 + r) * N + c];
+#pragma unroll
+            for (int q = r + 1; q < PB; q++)
+                if (q < nb) v -= Ub[r][q] * x[q];
+            x[r] = v / Ub[r][r];
+            XY[(size_t)(k0 + r) * N + c] = x[r];
+        }
+    }
+}
+
+// rows [0, k0): Y -= U[0:k0, k0:k0+nb] X_b (64 x 64 tiles)
+__global__ void __launch_bounds__(256) k_lu_back_update(int nn, int N, int k0, int nb,
+                                                          const double *Mw, double *XY) {
+    __shared__ double Ls[64][PB + 1];
+    __shared__ double Xs[PB][64 + 1];
+    const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64, tid = threadIdx.x;
+    for (int idx = tid; idx < 64 * PB; idx += 256) {
+        const int rr = idx / PB, q = idx % PB, row = r0 + rr;
+        Ls[rr][q] = (row < k0 && q < nb) ? Mw[(size_t)row * nn + k0 + q] : 0.0;
+    }
+    for (int idx = tid; idx < PB * 64; idx += 256) {
+        const int q = idx / 64, cc = idx % 64, c = c0 + cc;
+        Xs[q][cc] = (q < nb && c < N) ? XY[(size_t)(k0 + q) * N + c] : 0.0;
+    }
+    __syncthreads();
+    const int tx = tid & 15, ty = tid >> 4;
+    for (int a = 0; a < 4; a++) {
+        const int row = r0 + ty * 4 + a;
+        if (row >= k0) continue;
+        for (int b = 0; b < 4; b++) {
+            const int c = c0 + tx * 4 + b;
+            if (c >= N) continue;
+            double acc = 0.0;
+            for (int q = 0; q < nb; q++) acc += Ls[ty * 4 + a][q] * Xs[q][tx * 4 + b];
+            XY[(size_t)row * N + c] -= acc;
+        }
+    }
+}
+
+// C = [I - tau Y; tau X]
+__global__ void k_pred_c(int N, double tau_arg, const double *tau_dev, const double *XY,
+                         double *C) {
+    const double tau = tau_dev ? tau_dev[0] : tau_arg;
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < (long)N * N;
+         idx += (long)gridDim.x * blockDim.x) {
+        int i = (int)(idx / N), j = (int)(idx % N);
+        C[idx] = ((i == j) ? 1.0 : 0.0) - tau * XY[(size_t)(N + i) * N + j];
+        C[(size_t)(N + i) * N + j] = tau * XY[idx];
+    }
+}
+
+void lu_prepare() {
+    static bool done = false;
+    if (done) return;
+    cudaFuncSetAttribute(k_lu_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)lu_panel_smem(768, PB));
+    done = true;
+}
+
+void launch_lu_solve(int nn, int N, double *Mw, double *XY, int *ipiv, int *status,
+                     cudaStream_t s) {
+    const int bs = lu_block(nn);
+    for (int k0 = 0; k0 < nn; k0 += bs) {
+        const int nb = std::min(bs, nn - k0);
+        HQ_LAUNCH(HQ_K_SMALL, k_lu_panel<<<1, 512, lu_panel_smem(nn - k0, nb), s>>>(nn, k0, nb, Mw,
+                                                                                   ipiv, status));
+        const int ncols = nn - k0 - nb + N;
+        HQ_LAUNCH(HQ_K_SMALL, k_lu_trsm<<<(ncols + 127) / 128, 128, 0, s>>>(nn, N, k0, nb, Mw, XY,
+                                                                             ipiv));
+        const int rows = nn - k0 - nb;
+        if (rows > 0)
+            HQ_LAUNCH(HQ_K_SMALL, k_lu_update<<<dim3((ncols + 63) / 64, (rows + 63) / 64), 256, 0, s>>>(
+                                      nn, N, k0, nb, Mw, XY));
+    }
+    for (int k0 = ((nn - 1) / bs) * bs; k0 >= 0; k0 -= bs) {
+        const int nb = std::min(bs, nn - k0);
+        HQ_LAUNCH(HQ_K_SMALL, k_lu_back_diag<<<(N + 127) / 128, 128, 0, s>>>(nn, N, k0, nb, Mw, XY));
+        if (k0 > 0)
+            HQ_LAUNCH(HQ_K_SMALL, k_lu_back_update<<<dim3((N + 63) / 64, (k0 + 63) / 64), 256, 0, s>>>(
+                                      nn, N, k0, nb, Mw, XY));
+    }
+}
+
+void launch_predictor_solve(int N, double tau, const double *G2, double *Mw, double *XY,
+                            double *C, int *status, cudaStream_t s, const double *tau_dev,
+                            int *ipiv) {
+    const int nn = 2 * N;
+    if (nn <= 64 || !ipiv) {
+        size_t shm = sizeof(double) * (2 * N + 1024) + sizeof(int) * 1024;
+        HQ_LAUNCH(HQ_K_SMALL, k_predictor_solve<<<1, 1024, shm, s>>>(N, tau, G2, Mw, XY, C, status,
+                                                                      tau_dev));
+        return;
+    }
+    const long tot = (long)nn * nn + (long)nn * N;
+    HQ_LAUNCH(HQ_K_SMALL, k_pred_build<<<(int)std::min<long>((tot + 255) / 256, 1024), 256, 0, s>>>(
+                              N, tau, tau_dev, G2, Mw, XY));
+    launch_lu_solve(nn, N, Mw, XY, ipiv, status, s);
+    HQ_LAUNCH(HQ_K_SMALL, k_pred_c<<<(int)std::min<long>(((long)N * N + 255) / 256, 1024), 256, 0, s>>>(
+                              N, tau, tau_dev, XY, C));
+}
+
+// X = A^-1 B for an N x N matrix A and N right-hand sides (leading dimensions
+// lda, ldb); Mw: N x N scratch.  Blocked elimination for N > 32, else the
+// one-CTA Cholesky kernel (A symmetric positive definite there).
+__global__ void k_copy2(int N, const double *A, int lda, const double *B, int ldb, double *Mw,
+                        double *X) {
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < 2L * N * N;
+         idx += (long)gridDim.x * blockDim.x) {
+        const long e = idx % ((long)N * N);
+        const int i = (int)(e / N), j = (int)(e % N);
+        if (idx < (long)N * N) Mw[e] = A[(size_t)i * lda + j];
+        else X[e] = B[(size_t)i * ldb + j];
+    }
+}
+void launch_spd_solve(int N, const double *A, int lda, const double *B, int ldb, double *Mw,
+                      double *L, double *X, int *ipiv, int *status, cudaStream_t s) {
+    if (N <= 32 || !ipiv) {
+        launch_chol_solve(N, A, lda, B, ldb, L, X, status, s);
+        return;
+    }
+    HQ_LAUNCH(HQ_K_SMALL, k_copy2<<<(int)std::min<long>((2L * N * N + 255) / 256, 1024), 256, 0, s>>>(
+                              N, A, lda, B, ldb, Mw, X));
+    launch_lu_solve(N, N, Mw, X, ipiv, status, s);
 }
 
 // Largest eigenvalue of the symmetric part of A (N x N, leading dimension

@@ -301,24 +301,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                      : "memory");
 }
 
+// one thread per tile entry (grid: tiles x entry blocks), chunks summed in
+// order in FP64
 __global__ void k_gram_tc_reduce(TcPlan P, const float *partials, double w, double *out) {
     const int tile = blockIdx.x;
     int ta, tb;
     tc_tile_of(tile, P.tiles, ta, tb);
-    for (int e = threadIdx.x; e < TC_T * TC_T; e += blockDim.x) {
-        int la = e / TC_T, lb = e % TC_T;
-        int a = ta * TC_T + la, b = tb * TC_T + lb;
-        if (a >= P.na || b >= P.na) continue;
-        // within a diagonal tile the MMA accumulates (i,j) and (j,i) in
-        // different orders: keep the upper entry and mirror it
-        if (ta == tb && la > lb) continue;
-        double s = 0.0;
-        for (int c = 0; c < P.chunks; c++)
-            s += (double)partials[((size_t)c * P.ntiles + tile) * TC_T * TC_T + e];
-        s *= w;
-        out[(size_t)a * P.na + b] = s;
-        if (a != b) out[(size_t)b * P.na + a] = s;
-    }
+    const int e = blockIdx.y * blockDim.x + threadIdx.x;
+    if (e >= TC_T * TC_T) return;
+    const int la = e / TC_T, lb = e % TC_T;
+    const int a = ta * TC_T + la, b = tb * TC_T + lb;
+    if (a >= P.na || b >= P.na) return;
+    // within a diagonal tile the MMA accumulates (i,j) and (j,i) in different
+    // orders: keep the upper entry and mirror it
+    if (ta == tb && la > lb) return;
+    double s = 0.0;
+    for (int c = 0; c < P.chunks; c++)
+        s += (double)partials[((size_t)c * P.ntiles + tile) * TC_T * TC_T + e];
+    s *= w;
+    out[(size_t)a * P.na + b] = s;
+    if (a != b) out[(size_t)b * P.na + a] = s;
 }
 
 TcPlan make_tc_plan(long n, int na) {
@@ -351,7 +353,8 @@ void launch_gram_tc(long n, const float *X1, int n1, const float *X2, int n2, do
     tc_prepare();
     HQ_LAUNCH(HQ_K_GRAM, k_gram_tf32x3<<<dim3(p.ntiles, p.chunks), TC_THREADS, smem, s>>>(
                              p, X1, n1, X2, n2, partials, status));
-    HQ_LAUNCH(HQ_K_GRAM, k_gram_tc_reduce<<<p.ntiles, 256, 0, s>>>(p, partials, w, out));
+    HQ_LAUNCH(HQ_K_GRAM, k_gram_tc_reduce<<<dim3(p.ntiles, (TC_T * TC_T + 255) / 256), 256, 0, s>>>(
+                             p, partials, w, out));
 }
 
 

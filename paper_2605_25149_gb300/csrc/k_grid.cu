@@ -27,20 +27,22 @@ __device__ __forceinline__ void stv(T *p, const VT<T, V> &x) {
     *reinterpret_cast<VT<T, V> *>(p) = x;
 }
 
-GridGeom make_geom(int m, int N, int elem_bytes) {
+GridGeom make_geom(int m, int N, int elem_bytes, int block, int ctas_per_sm) {
     GridGeom g;
     g.m = m;
     g.n = (long)m * m * m;
     g.N = N;
+    if (block <= 0) block = 256;
+    if (ctas_per_sm <= 0) ctas_per_sm = 16;
     if (elem_bytes == 8)
         g.vec = (N % 2 == 0) ? 2 : 1;
     else
         g.vec = (N % 4 == 0) ? 4 : ((N % 2 == 0) ? 2 : 1);
     int tpr = N / g.vec;
     g.tx = tpr <= 32 ? tpr : 32;
-    g.ty = std::max(1, 256 / g.tx);
+    g.ty = std::max(1, block / g.tx);
     g.gx = (tpr + g.tx - 1) / g.tx;
-    long target_gy = std::max(1L, 152L * 16 / g.gx);
+    long target_gy = std::max(1L, 152L * ctas_per_sm / g.gx);
     long ppt = (g.n + (long)g.ty * target_gy - 1) / ((long)g.ty * target_gy);
     g.ppt = (int)std::max(1L, ppt);
     g.gy = (int)((g.n + (long)g.ty * g.ppt - 1) / ((long)g.ty * g.ppt));
@@ -65,6 +67,27 @@ __device__ __forceinline__ void block_col_reduce(A (&acc)[V], double *red, doubl
         }
     }
     __syncthreads();
+}
+
+// Grid coordinates of point p (p = i + m (j + m k), n = m^3 < 2^31): one 32-bit
+// decomposition per thread, then an increment per visited point (the loops
+// below step p by the block height), which keeps integer division out of the
+// per-point work.
+__device__ __forceinline__ void grid_decomp(unsigned p, unsigned m, int &i, int &j, int &kk) {
+    const unsigned q = p / m;
+    i = (int)(p - q * m);
+    kk = (int)(q / m);
+    j = (int)(q - (unsigned)kk * m);
+}
+__device__ __forceinline__ void grid_advance(int d, int m, int &i, int &j, int &kk) {
+    i += d;
+    while (i >= m) {
+        i -= m;
+        if (++j == m) {
+            j = 0;
+            ++kk;
+        }
+    }
 }
 
 // Sum of the six neighbours of element e (point (i, j, k) of an m^3 grid) with
@@ -107,13 +130,11 @@ __global__ void __launch_bounds__(256) k_stencil(int m, long n, int N, int ppt,
     for (int v = 0; v < V; v++) a1[v] = a2[v] = T(0);
     const size_t sx = (size_t)N, sy = (size_t)m * N, sz = (size_t)m * m * N;
     const long base = (long)blockIdx.y * TY * ppt;
-    for (int k = 0; k < ppt; k++) {
-        long p = base + (long)k * TY + threadIdx.y;
+    long p = base + threadIdx.y;
+    int i, j, kk;
+    grid_decomp((unsigned)p, (unsigned)m, i, j, kk);
+    for (int k = 0; k < ppt; k++, p += TY, grid_advance(TY, m, i, j, kk)) {
         if (!cv || p >= n) continue;
-        int i = (int)(p % m);
-        long q = p / m;
-        int j = (int)(q % m);
-        int kk = (int)(q / m);
         size_t e = (size_t)p * N + col;
         VT<T, V> xc = ldv<T, V>(x + e);
         VT<T, V> s = nbr_sum<T, V>(x, e, i, j, kk, m, sx, sy, sz);
@@ -223,13 +244,11 @@ __global__ void __launch_bounds__(256) k_jacobi(int m, long n, int N, int ppt,
     for (int v = 0; v < V; v++) acc[v] = T(0);
     const size_t sx = (size_t)N, sy = (size_t)m * N, sz = (size_t)m * m * N;
     const long base = (long)blockIdx.y * TY * ppt;
-    for (int k = 0; k < ppt; k++) {
-        long p = base + (long)k * TY + threadIdx.y;
+    long p = base + threadIdx.y;
+    int i, j, kk;
+    grid_decomp((unsigned)p, (unsigned)m, i, j, kk);
+    for (int k = 0; k < ppt; k++, p += TY, grid_advance(TY, m, i, j, kk)) {
         if (!cv || p >= n) continue;
-        int i = (int)(p % m);
-        long q = p / m;
-        int j = (int)(q % m);
-        int kk = (int)(q / m);
         size_t e = (size_t)p * N + col;
         VT<T, V> zc = ldv<T, V>(zin + e), rv = ldv<T, V>(r + e);
         VT<T, V> s = nbr_sum<T, V>(zin, e, i, j, kk, m, sx, sy, sz);
@@ -593,10 +612,28 @@ __global__ void k_pcg_cond(const int *num_active, int *iter, int maxit,
     cudaGraphSetConditional(h, (num_active[0] > 0 && it < maxit) ? 1u : 0u);
 }
 
+// deterministic pseudo-random values in [-1, 1) (a 64-bit integer hash of
+// the index; timing inputs of the autotuner, no part of the method)
+template <typename T>
+__global__ void k_fill_hash(long count, unsigned long long seed, T *out) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count;
+         i += (long)gridDim.x * blockDim.x) {
+        unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(i + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        out[i] = (T)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+    }
+}
+
+// whole-phase graphs: enter the WHILE node only if a column is active
 __global__ void k_pcg_cond_init(const int *num_active, int maxit, cudaGraphConditionalHandle hw) {
     cudaGraphSetConditional(hw, (num_active[0] > 0 && maxit > 0) ? 1u : 0u);
 }
 
+// whole-phase graphs, end of a loop iteration (x / r update and stopping
+// test done): the IF node that follows (z = M r, beta, p) and the next
+// iteration run only while columns are active and the cap is not reached
 __global__ void k_pcg_cond2(const int *num_active, int *iter, int maxit,
                             cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hif,
                             long long *counters, int *status, int check_maxit) {
@@ -912,6 +949,14 @@ void launch_finalize(int mode, int N, int gy, const double *part, const double *
                      PcgScalars sc, double rtol, cudaStream_t s) {
     HQ_LAUNCH(HQ_K_REDUCE, k_finalize<<<N, 128, 0, s>>>(mode, N, gy, part, part2, sc, rtol));
 }
+
+template <typename T>
+void launch_fill_hash(long count, unsigned long long seed, T *out, cudaStream_t s) {
+    const int blocks = (int)std::min<long>((count + 255) / 256, 152L * 8);
+    HQ_LAUNCH(HQ_K_SETUP, k_fill_hash<T><<<blocks, 256, 0, s>>>(count, seed, out));
+}
+template void launch_fill_hash<float>(long, unsigned long long, float *, cudaStream_t);
+template void launch_fill_hash<double>(long, unsigned long long, double *, cudaStream_t);
 
 void launch_pcg_cond(const int *num_active, int *iter, int maxit, cudaGraphConditionalHandle h,
                      cudaStream_t s) {

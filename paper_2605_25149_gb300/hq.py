@@ -39,6 +39,9 @@ EXPORTED = [
     "hq_mg_level_potential", "hq_gram_static", "hq_profile", "hq_profile_read", "hq_pcg_stats",
     "hq_last_error",
     "hq_status_string", "hq_destroy",
+    "hq_tune_workspace_bytes", "hq_tune",
+    "hq_batch_create", "hq_batch_solve", "hq_batch_step", "hq_batch_launches",
+    "hq_batch_last_error", "hq_batch_destroy",
 ]
 KERNEL_CLASSES = ["stencil", "residual", "smooth", "transfer", "coarse", "vector", "reduce", "gram",
                   "blockgemm", "small", "setup", "coarse_grids"]
@@ -58,7 +61,7 @@ class Config(ctypes.Structure):
         ("mg_nu1", ctypes.c_int), ("mg_nu2", ctypes.c_int), ("mg_coarsest", ctypes.c_int),
         ("mg_omega", ctypes.c_double), ("timeout_s", ctypes.c_double),
         ("z_warm_start", ctypes.c_int), ("adaptive_tau", ctypes.c_int),
-        ("tau_max", ctypes.c_double),
+        ("tau_max", ctypes.c_double), ("grid_block", ctypes.c_int), ("grid_ctas", ctypes.c_int),
     ]
 
 
@@ -113,6 +116,14 @@ def load():
         "hq_last_error": (ctypes.c_char_p, [_P]),
         "hq_status_string": (ctypes.c_char_p, [_I]),
         "hq_destroy": (None, [_P]),
+        "hq_tune_workspace_bytes": (ctypes.c_size_t, [_P]),
+        "hq_tune": (_I, [_P, _P, ctypes.c_size_t, _P, _P, _P]),
+        "hq_batch_create": (_I, [_P, _I, _P, _P]),
+        "hq_batch_solve": (_I, [_P, _P, _L, _D, _P, _P, _P]),
+        "hq_batch_step": (_I, [_P, _L, _P, _P]),
+        "hq_batch_launches": (_I, [_P, _P, _P]),
+        "hq_batch_last_error": (ctypes.c_char_p, [_P]),
+        "hq_batch_destroy": (None, [_P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -137,6 +148,57 @@ def default_config(m, nev, **kw) -> Config:
 
 def workspace_bytes(cfg: Config) -> int:
     return int(load().hq_workspace_bytes(ctypes.byref(cfg)))
+
+
+def tune(cfg: Config, stream=None):
+    """hq_tune: (grid_block, grid_ctas, ms per PCG iteration) for cfg."""
+    import torch
+    lib = load()
+    nbytes = int(lib.hq_tune_workspace_bytes(ctypes.byref(cfg)))
+    if nbytes == 0:
+        raise HQError(1, "invalid configuration")
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    base = ws.data_ptr()
+    off = (-base) % 256
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    out = Config()
+    ms = ctypes.c_double()
+    st = lib.hq_tune(ctypes.byref(cfg), ctypes.c_void_p(base + off), nbytes,
+                     ctypes.c_void_p(stream.cuda_stream), ctypes.byref(out), ctypes.byref(ms))
+    del ws
+    if st != OK:
+        raise HQError(st, "hq_tune failed")
+    return out.grid_block, out.grid_ctas, ms.value
+
+
+def tuned_shape(m, nev, precision="fp64", cache=None, **cfg_kw):
+    """(grid_block, grid_ctas) for this problem shape on this GPU: from the JSON
+    cache (path `cache`, else $HQ_TUNE_CACHE, else ~/.cache/hq_tune.json), or
+    measured by hq_tune and stored there."""
+    import json
+    import torch
+    path = cache or os.environ.get("HQ_TUNE_CACHE") or os.path.join(
+        os.path.expanduser("~"), ".cache", "hq_tune.json")
+    key = "%s|m=%d|N=%d|%s" % (torch.cuda.get_device_name(), m, nev, precision)
+    try:
+        with open(path) as f:
+            table = json.load(f)
+    except (OSError, ValueError):
+        table = {}
+    if key in table:
+        e = table[key]
+        return int(e["grid_block"]), int(e["grid_ctas"])
+    b, c, ms = tune(default_config(m, nev, precision=precision, **cfg_kw))
+    table[key] = {"grid_block": b, "grid_ctas": c, "ms_per_pcg_iteration": ms}
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + ".tmp%d" % os.getpid()
+        with open(tmp, "w") as f:
+            json.dump(table, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return b, c
 
 
 def _dptr(t):
@@ -435,6 +497,72 @@ class Solver:
         self._check(self.lib.hq_mg_level_potential(self._ctx, level, _dptr(out)),
                     "hq_mg_level_potential")
         return out
+
+
+class Batch:
+    """Several Solver contexts advanced together in one CUDA-graph launch per
+    call (hq_batch_*).  The solvers must outlive the batch."""
+
+    def __init__(self, solvers, stream=None):
+        import torch
+        self.lib = load()
+        self.solvers = list(solvers)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        arr = (ctypes.c_void_p * len(self.solvers))(*[s._ctx.value for s in self.solvers])
+        self._b = ctypes.c_void_p()
+        st = self.lib.hq_batch_create(arr, len(self.solvers),
+                                      ctypes.c_void_p(self.stream.cuda_stream),
+                                      ctypes.byref(self._b))
+        if st != OK:
+            raise HQError(st, "hq_batch_create failed")
+
+    def _check(self, st, what):
+        if st != OK:
+            msg = self.lib.hq_batch_last_error(self._b)
+            raise HQError(st, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    def solve(self, eps, max_steps, timeout_s=0.0, raise_on_error=True):
+        """Algorithm 1 for every member; returns (steps, g, status) arrays."""
+        K = len(self.solvers)
+        e = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, dtype=np.float64), (K,)))
+        steps = np.zeros(K, dtype=np.int64)
+        g = np.zeros(K)
+        stat = np.zeros(K, dtype=np.int32)
+        st = self.lib.hq_batch_solve(self._b, _hptr(e), max_steps, timeout_s,
+                                     steps.ctypes.data_as(ctypes.c_void_p), _hptr(g),
+                                     stat.ctypes.data_as(ctypes.c_void_p))
+        if raise_on_error:
+            self._check(st, "hq_batch_solve")
+        return steps, g, stat
+
+    def step(self, nsteps=1, raise_on_error=True):
+        """nsteps steps for every member; returns (g, status) arrays."""
+        K = len(self.solvers)
+        g = np.zeros(K)
+        stat = np.zeros(K, dtype=np.int32)
+        st = self.lib.hq_batch_step(self._b, nsteps, _hptr(g),
+                                    stat.ctypes.data_as(ctypes.c_void_p))
+        if raise_on_error:
+            self._check(st, "hq_batch_step")
+        return g, stat
+
+    def launches(self):
+        """(batch-level kernels, time-loop iterations) since creation."""
+        a, b = ctypes.c_long(), ctypes.c_long()
+        self._check(self.lib.hq_batch_launches(self._b, ctypes.byref(a), ctypes.byref(b)),
+                    "hq_batch_launches")
+        return a.value, b.value
+
+    def close(self):
+        if getattr(self, "_b", None) and self._b.value:
+            self.lib.hq_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def status_string(st: int) -> str:

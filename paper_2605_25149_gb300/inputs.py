@@ -88,3 +88,24 @@ def workload(name: str):
     V = potential(w["potential"], w["m"])
     U0 = initial_block(w["m"], w["N"], w["u0_seed"])
     return V, U0, w
+
+
+# The batched workload: 32 independent problems, grid sides and block widths
+# drawn uniformly from these sets by default_rng(4) (sides first, then widths),
+# wells potential k from default_rng(1000 + k), U0 k from default_rng(2000 + k),
+# tau = 0.4, mixed precision.
+BATCH_SIDES = (32, 48, 64, 96)
+BATCH_WIDTHS = (16, 32, 64, 128)
+
+
+def batch_shapes(count: int = 32, seed: int = 4):
+    """[(m_k, N_k)] of the batched workload."""
+    rng = np.random.default_rng(seed)
+    ms = rng.choice(BATCH_SIDES, count)
+    Ns = rng.choice(BATCH_WIDTHS, count)
+    return [(int(m), int(N)) for m, N in zip(ms, Ns)]
+
+
+def batch_problem(k: int, m: int, N: int):
+    """(V, U0) of problem k of the batched workload."""
+    return wells(m, 1000 + k), initial_block(m, N, 2000 + k)

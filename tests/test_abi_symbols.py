@@ -56,3 +56,32 @@ def test_init_rejects_null_workspace_without_touching_a_device():
     ctx = ctypes.c_void_p()
     st = lib.hq_init(ctypes.byref(c), None, 0, None, ctypes.byref(ctx))
     assert st == 4 and not ctx.value
+
+
+def test_batch_create_rejects_bad_arguments_without_touching_a_device():
+    lib = hq.load()
+    out = ctypes.c_void_p()
+    assert lib.hq_batch_create(None, 1, None, ctypes.byref(out)) == 1 and not out.value
+    fake = (ctypes.c_void_p * 2)(0x1000, 0x1000)          # repeated context
+    assert lib.hq_batch_create(fake, 2, None, ctypes.byref(out)) == 1 and not out.value
+    assert lib.hq_batch_create(fake, 0, None, ctypes.byref(out)) == 1
+    assert lib.hq_batch_create(fake, 65, None, ctypes.byref(out)) == 1
+    assert lib.hq_batch_last_error(None) == b"null batch"
+
+
+def test_launch_shape_fields_and_tuner_workspace():
+    lib = hq.load()
+    c = hq.default_config(32, 16, precision="mixed")
+    assert c.grid_block == 0 and c.grid_ctas == 0
+    base = hq.workspace_bytes(c)
+    tune_ws = int(lib.hq_tune_workspace_bytes(ctypes.byref(c)))
+    assert tune_ws >= base > 0
+    for b in (64, 128, 256):
+        for k in (4, 8, 16, 32):
+            t = hq.default_config(32, 16, precision="mixed", grid_block=b, grid_ctas=k)
+            assert 0 < hq.workspace_bytes(t) <= tune_ws
+    assert hq.workspace_bytes(hq.default_config(32, 16, grid_block=96)) == 0
+    assert hq.workspace_bytes(hq.default_config(32, 16, grid_block=512)) == 0
+    assert hq.workspace_bytes(hq.default_config(32, 16, grid_ctas=65)) == 0
+    out = hq.Config()
+    assert lib.hq_tune(ctypes.byref(c), None, 0, None, ctypes.byref(out), None) == 4

@@ -17,7 +17,10 @@ def _oracle_from_gpu_start(s, U0):
     return Uo
 
 
-@pytest.mark.parametrize("m,N,pot", [(10, 4, "wells"), (13, 7, "harmonic"), (16, 8, "wells")])
+# N = 40 and 70: 2N > 64 takes the blocked predictor elimination (panels of
+# 32 columns, the last one ragged)
+@pytest.mark.parametrize("m,N,pot", [(10, 4, "wells"), (13, 7, "harmonic"), (16, 8, "wells"),
+                                     (12, 40, "wells"), (14, 70, "harmonic")])
 def test_step_intermediates_match_oracle(m, N, pot):
     tau = 0.4
     s, V, U0 = make(m, N, potential=pot, tau=tau, cg_rtol=1e-13, cg_maxit=400)
