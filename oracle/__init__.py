@@ -90,6 +90,8 @@ def _sig(lib):
         "orc_solve_adaptive": (_I, [_I, _D, _D, _P, _D, _I, _D, _D, _I, _D, _L, _P, _P, _P,
                                     _P, _P, _P]),
         "orc_energy": (_D, [_I, _D, _D, _P, _D, _I, _P]),
+        "orc_grad_eigs": (_I, [_I, _D, _D, _I, _P, _P, _P]),
+        "orc_grad_density": (_I, [_I, _D, _D, _P, _I, _P, _P, _P, _D, _I, _P, _P, _P]),
     }
     for name, (res, args) in spec.items():
         f = getattr(lib, name)
@@ -392,3 +394,36 @@ def energy(m, V, U, shift=0.0, lo=-6.0, hi=6.0):
     V = _f64(V).ravel()
     U = _f64(U)
     return lib().orc_energy(m, lo, hi, _ptr(V), shift, U.shape[1], _ptr(U))
+
+
+# --------------------------------------------------------------------------
+# differentiation through converged eigenpairs (not in the paper; the
+# derivations are in the comments of orc_grad_eigs / orc_grad_density)
+# --------------------------------------------------------------------------
+def grad_eigs(m, U, w=None, lo=-6.0, hi=6.0):
+    """d(sum_i w_i lambda_i)/dV = h^3 sum_i w_i u_i^2 for eigenvectors U
+    (point-major n x N, <u_i,u_j> = delta_ij)."""
+    U = _f64(U)
+    n, N = U.shape
+    wv = None if w is None else _f64(w).ravel()
+    dV = np.empty(n)
+    _check(lib().orc_grad_eigs(m, lo, hi, N, _ptr(U), _ptr(wv), _ptr(dV)), "orc_grad_eigs")
+    return dV
+
+
+def grad_density(m, V, U, lam, rho_target, rtol=1e-12, maxit=20000, lo=-6.0, hi=6.0):
+    """Loss L = (1/2) h^3 |rho - rho_target|^2 with rho = sum_i u_i^2 and its
+    gradient dL/dV by the adjoint solves (H - lambda_i) xi_i = Q (g u_i).
+    Returns (dV, L, largest CG iteration count)."""
+    V = _f64(V).ravel()
+    U = _f64(U)
+    n, N = U.shape
+    lam = _f64(lam).ravel()
+    rt = _f64(rho_target).ravel()
+    dV = np.empty(n)
+    L = ctypes.c_double()
+    its = ctypes.c_int()
+    st = lib().orc_grad_density(m, lo, hi, _ptr(V), N, _ptr(U), _ptr(lam), _ptr(rt), rtol, maxit,
+                                _ptr(dV), ctypes.byref(L), ctypes.byref(its))
+    _check(st, "orc_grad_density")
+    return dV, L.value, its.value

@@ -1087,3 +1087,107 @@ double orc_energy(int m, double lo, double hi, const double *V, double shift, in
     free(HU);
     return 0.5 * h3 * kval(&k);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Differentiation through converged eigenpairs (not in the paper).         */
+/* Input: eigenpairs (lam_i, u_i), i < N, of H = -Delta_h/2 + V with         */
+/* <u_i,u_j> = h^3 u_i^T u_j = delta_ij, and lam_N < lam_{N+1}.              */
+/*                                                                          */
+/* Sum of eigenvalues: d lam_i / d V_p = <u_i, e_p u_i> = h^3 u_i(p)^2       */
+/* (first-order perturbation of a simple eigenvalue), so                    */
+/*   dV_p = h^3 sum_i w_i u_i(p)^2.                                         */
+/*                                                                          */
+/* Density loss: rho = sum_i u_i^2 (pointwise), L = (1/2) h^3 |rho - rho*|^2. */
+/* A perturbation dV moves u_i by du_i = -(H - lam_i)^{-1} Q (dV u_i) with   */
+/* Q = I - sum_j u_j <u_j, .> (components along the other occupied u_j      */
+/* cancel in rho), and (H - lam_i) is SPD on range(Q).  With g = rho - rho*  */
+/* dL = <g, d rho> = 2 sum_i <g u_i, du_i>, and the operator Q(H-lam_i)^{-1}Q */
+/* is self-adjoint, so                                                      */
+/*   dL/dV_p = -2 h^3 sum_i xi_i(p) u_i(p),  (H - lam_i) xi_i = Q (g u_i),  */
+/* xi_i in range(Q), solved by CG with Q applied after every operator       */
+/* application (the Krylov space stays in range(Q)).                        */
+/* ------------------------------------------------------------------------ */
+int orc_grad_eigs(int m, double lo, double hi, int N, const double *U, const double *w,
+                  double *dV)
+{
+    long n = cube(m);
+    double h = orc_grid_h(m, lo, hi), h3 = h * h * h;
+    for (long p = 0; p < n; p++) {
+        double s = 0.0;
+        for (int i = 0; i < N; i++) s += (w ? w[i] : 1.0) * U[p * N + i] * U[p * N + i];
+        dV[p] = h3 * s;
+    }
+    return ORC_OK;
+}
+
+/* x <- Q x = x - sum_j u_j h^3 (u_j^T x) for one column x */
+static void project_out(long n, int N, double h3, const double *U, double *x)
+{
+    for (int j = 0; j < N; j++) {
+        double s = 0.0;
+        for (long p = 0; p < n; p++) s += U[p * N + j] * x[p];
+        s *= h3;
+        for (long p = 0; p < n; p++) x[p] -= s * U[p * N + j];
+    }
+}
+
+int orc_grad_density(int m, double lo, double hi, const double *V, int N, const double *U,
+                     const double *lam, const double *rho_target, double rtol, int maxit,
+                     double *dV, double *loss, int *iters)
+{
+    long n = cube(m);
+    double h = orc_grid_h(m, lo, hi), h3 = h * h * h;
+    double *g = malloc(sizeof(double) * n);
+    double *xi = calloc((size_t)n * N, sizeof(double));
+    ksum L = {0.0, 0.0};
+    for (long p = 0; p < n; p++) {
+        double rho = 0.0;
+        for (int i = 0; i < N; i++) rho += U[p * N + i] * U[p * N + i];
+        g[p] = rho - rho_target[p];
+        kadd(&L, g[p] * g[p]);
+    }
+    *loss = 0.5 * h3 * kval(&L);
+    int status = ORC_OK, itmax = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < N; i++) {
+        double *b = malloc(sizeof(double) * n), *x = calloc(n, sizeof(double));
+        double *r = malloc(sizeof(double) * n), *pp = malloc(sizeof(double) * n),
+               *q = malloc(sizeof(double) * n);
+        for (long p = 0; p < n; p++) b[p] = g[p] * U[p * N + i];
+        project_out(n, N, h3, U, b);
+        /* CG on (H - lam_i) restricted to range(Q), x0 = 0 */
+        double bn = sqrt(dot(n, b, b));
+        for (long p = 0; p < n; p++) { r[p] = b[p]; pp[p] = b[p]; }
+        double rr = dot(n, r, r);
+        int st = (sqrt(rr) <= rtol * bn) ? ORC_OK : ORC_ERR_NOT_CONVERGED, it = 0;
+        while (st != ORC_OK && it < maxit) {
+            apply_col(m, h, V, -lam[i], pp, q);
+            project_out(n, N, h3, U, q);
+            double pq = dot(n, pp, q);
+            if (!(pq > 0.0)) { st = ORC_ERR_BREAKDOWN; break; }
+            double alpha = rr / pq;
+            for (long p = 0; p < n; p++) { x[p] += alpha * pp[p]; r[p] -= alpha * q[p]; }
+            double rr1 = dot(n, r, r);
+            it++;
+            if (sqrt(rr1) <= rtol * bn) { st = ORC_OK; break; }
+            double beta = rr1 / rr;
+            for (long p = 0; p < n; p++) pp[p] = r[p] + beta * pp[p];
+            rr = rr1;
+        }
+        for (long p = 0; p < n; p++) xi[p * N + i] = x[p];
+#pragma omp critical
+        {
+            if (st != ORC_OK && status == ORC_OK) status = st;
+            if (it > itmax) itmax = it;
+        }
+        free(b); free(x); free(r); free(pp); free(q);
+    }
+    for (long p = 0; p < n; p++) {
+        double s = 0.0;
+        for (int i = 0; i < N; i++) s += xi[p * N + i] * U[p * N + i];
+        dV[p] = -2.0 * h3 * s;
+    }
+    if (iters) *iters = itmax;
+    free(g); free(xi);
+    return status;
+}

@@ -108,7 +108,9 @@ struct hq_ctx {
     double *eigwork = nullptr, *evals = nullptr, *mu = nullptr, *lam_p = nullptr;
     double *lam_r = nullptr, *resn = nullptr, *scal = nullptr, *signwork = nullptr;
     int *status = nullptr;
-    int *ipiv = nullptr;   // pivots of the blocked predictor elimination (2N)
+    int *ipiv = nullptr;   // pivots of the small eliminations (2N)
+    float *lu32 = nullptr;  // FP32 factors of the small systems (mixed precision)
+    double *pB = nullptr, *pR = nullptr;   // predictor right-hand side / residual
     double *vn[3] = {nullptr, nullptr, nullptr};   // FP64 n-vectors (density, adjoint)
     double *pvec = nullptr;                        // power-iteration vector (N)
     // host state
@@ -349,6 +351,8 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
     const int gy0 = std::max(lev[0].g.gy, make_geom(m, N, 8).gy);
     double *part = cv.take<double>(sizeof(double) * (size_t)gy0 * N);
     double *part2 = cv.take<double>(sizeof(double) * (size_t)gy0 * N);
+    sc.fpart = cv.take<double>(sizeof(double) * 2 * (size_t)finalize_chunks(gy0) * N);
+    sc.fcount = cv.take<unsigned>(sizeof(unsigned) * 16);
     float *tcpart = mixed ? cv.take<float>(gram_tc_partial_bytes(n, 2 * N)) : nullptr;
     unsigned char *tcimg = mixed ? cv.take<unsigned char>(tall_tc_image_bytes(N, N, N)) : nullptr;
     GramPlan guw = make_gram_plan(n, 2 * N, 2 * N, true);
@@ -361,6 +365,11 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
     double *Mw = cv.take<double>(sizeof(double) * 4 * N2);
     double *XY = cv.take<double>(sizeof(double) * 2 * N2);
     int *ipiv = cv.take<int>(sizeof(int) * 2 * N);
+    // mixed-precision small solves: FP32 factors and FP64 right-hand side /
+    // residual of the predictor system
+    float *lu32 = mixed ? cv.take<float>(sizeof(float) * 4 * N2) : nullptr;
+    double *pB = mixed ? cv.take<double>(sizeof(double) * 2 * N2) : nullptr;
+    double *pR = mixed ? cv.take<double>(sizeof(double) * 2 * N2) : nullptr;
     double *Cc = cv.take<double>(sizeof(double) * 2 * N2);
     double *T1 = cv.take<double>(sizeof(double) * 2 * N2);
     double *Shat = cv.take<double>(sizeof(double) * N2);
@@ -401,6 +410,9 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
         x->gplan_uw = guw; x->gplan_max = gmax; x->gpart = gpart; x->tcpart = tcpart; x->tcimg = tcimg;
         x->tplan = tp; x->tpart = tpart;
         x->ipiv = ipiv;
+        x->lu32 = lu32;
+        x->pB = pB;
+        x->pR = pR;
         x->G2 = G2; x->Mw = Mw; x->XY = XY; x->C = Cc; x->T1 = T1; x->Shat = Shat; x->Om = Om;
         x->Msm = Msm; x->Ksm = Ksm; x->Ssm = Ssm; x->Lm = Lm; x->Cm = Cm; x->Ym = Ym;
         x->Cv = Cvv; x->Cv2 = Cv2; x->eigwork = eigwork; x->evals = evals; x->mu = mu;
@@ -862,7 +874,8 @@ hq_status enqueue_b(hq_ctx *x, StepGraph *sgr, long long *counters) {
                          x->st);
         tau_dev = x->scal + 8;
     }
-    launch_predictor_solve(N, tau, x->G2, x->Mw, x->XY, x->C, x->status, x->st, tau_dev, x->ipiv);
+    launch_predictor_solve(N, tau, x->G2, x->Mw, x->XY, x->C, x->status, x->st, tau_dev, x->ipiv,
+                           x->lu32, x->pB, x->pR);
     block_gemm<T>(x, U, N, x->C, W, N, x->C + (size_t)N * N, nullptr, Uh, false, nullptr);
     // Shat = C^T G2 C, Om = -tau (Shat - I)
     launch_small_gemm(2 * N, N, 2 * N, 1.0, x->G2, 2 * N, false, x->C, N, false, 0.0, x->T1, N,
@@ -873,7 +886,7 @@ hq_status enqueue_b(hq_ctx *x, StepGraph *sgr, long long *counters) {
         // G Uh = W C1 + G W C2 and G W ~ W M with M = S^{-1} Puw (exact when
         // span(U) is G-invariant): start from Z0 = W (C1 + M C2)
         launch_spd_solve(N, x->G2, 2 * N, x->G2 + N, 2 * N, x->Mw, x->Lm, x->Ym, x->ipiv,
-                         x->status, x->st);
+                         x->status, x->st, x->lu32);
         launch_extract(N, N, 1.0, x->C, N, x->Cm, N, x->st);
         launch_small_gemm(N, N, N, 1.0, x->Ym, N, false, x->C + (size_t)N * N, N, false, 1.0,
                           x->Cm, N, x->st);
@@ -1924,9 +1937,11 @@ hq_status hq_init(const hq_config *cfg, void *d_workspace, size_t bytes, void *c
     cudaError_t e = cudaMemsetAsync(x->sc.status, 0, sizeof(int), x->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(x->status, 0, sizeof(int), x->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(x->dcount, 0, sizeof(long long) * 24, x->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(x->sc.fcount, 0, sizeof(unsigned) * 16, x->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(x->st);
     if (x->mixed) hq::tc_prepare();
     hq::lu_prepare();
+    if (x->mixed) hq::lu32_prepare();
     if (e != cudaSuccess) {
         delete x;
         return HQ_ERR_CUDA;

@@ -44,6 +44,8 @@ struct PcgScalars {
     int *active, *iters;
     int *num_active;   // 1 int
     int *status;       // 1 int, sticky error flags (bit 0: breakdown)
+    double *fpart;     // 2 x ceil(gy / 128) x N: row-chunk sums of the finalisation
+    unsigned *fcount;  // ceil(N / 32) arrival counters of the finalisation (start at 0)
 };
 
 enum { ST_BREAKDOWN = 1, ST_SINGULAR = 2, ST_NONFINITE = 4, ST_GJ_FAIL = 8, ST_TC_TIMEOUT = 16,
@@ -109,6 +111,8 @@ void launch_dot(const GridGeom &g, const T *x, const T *y, double *part, cudaStr
 
 // per-column reduction of gy partials + PCG scalar logic
 enum FinMode { FIN_BNORM_RNORM = 0, FIN_ALPHA = 1, FIN_RR = 2, FIN_BETA = 3, FIN_RZ = 4 };
+// row chunks of the finalisation for gy partial rows (sizes PcgScalars::fpart)
+int finalize_chunks(int gy);
 void launch_finalize(int mode, int N, int gy, const double *part, const double *part2,
                      PcgScalars sc, double rtol, cudaStream_t s);
 
@@ -267,9 +271,16 @@ void launch_small_gemm(int M, int Ncol, int K, double alpha, const double *A, in
 // C = [I - tau Y; tau X] (2N x N).
 // ipiv: 2N ints of scratch for the blocked elimination used when 2N > 64
 // (nullptr: always the one-CTA kernel)
+// lu32 (4N^2 floats), pB, pR (2N x N doubles): scratch of the mixed-precision
+// variant (FP32 elimination + FP64 iterative refinement), used when all are
+// non-null and the system fits one CTA's shared memory
 void launch_predictor_solve(int N, double tau, const double *G2, double *Mwork, double *XY,
                             double *C, int *status, cudaStream_t s,
-                            const double *tau_dev = nullptr, int *ipiv = nullptr);
+                            const double *tau_dev = nullptr, int *ipiv = nullptr,
+                            float *lu32 = nullptr, double *pB = nullptr, double *pR = nullptr);
+// sets the shared-memory limits of the FP32 elimination kernels (call once,
+// outside any stream capture)
+void lu32_prepare();
 // largest eigenvalue of sym(A) (N x N, leading dimension lda) -> out[0];
 // vec (N): warm-start vector, updated (all zero: fixed start)
 void launch_top_eig(int N, const double *A, int lda, double *vec, double *out, cudaStream_t s);
@@ -301,11 +312,13 @@ void lu_prepare();
 // elimination with partial pivoting (ipiv: nn ints of scratch)
 void launch_lu_solve(int nn, int nrhs, double *Mw, double *XY, int *ipiv, int *status,
                      cudaStream_t s);
-// X = A^-1 B, A N x N symmetric positive definite (lda), B N x N (ldb): the
-// one-CTA Cholesky kernel (factor into L) for N <= 32 or ipiv == nullptr,
-// else the blocked elimination in the N x N scratch Mw
+// X = A^-1 B, A N x N symmetric positive definite (lda), B N x N (ldb): with
+// lu32 (N^2 floats) an FP32 elimination in one CTA (no refinement: used for a
+// warm start), else the one-CTA Cholesky kernel (factor into L) for N <= 32
+// or ipiv == nullptr, else the blocked elimination in the N x N scratch Mw
 void launch_spd_solve(int N, const double *A, int lda, const double *B, int ldb, double *Mw,
-                      double *L, double *X, int *ipiv, int *status, cudaStream_t s);
+                      double *L, double *X, int *ipiv, int *status, cudaStream_t s,
+                      float *lu32 = nullptr);
 void launch_chol_solve(int N, const double *A, int lda, const double *B, int ldb, double *L,
                        double *X, int *status, cudaStream_t s);
 // c = L^{-T} y  (columns of Y), Cv output N x N

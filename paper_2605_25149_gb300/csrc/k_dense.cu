@@ -329,6 +329,7 @@ __global__ void __launch_bounds__(1024) k_predictor_solve(int N, double tau_arg,
     int *ri = (int *)(rv + 1024);            // 1024 reduction indices
     const int nn = 2 * N, ld2 = 2 * N;
     const int T = blockDim.x, tid = threadIdx.x;
+    const int lx = tid & 31, wy = tid >> 5, NW = T >> 5;
     const double ht = 0.5 * tau;
     // build [I - tau/2 Puw, tau/2 S; -tau/2 Q, I + tau/2 Pwu] and [S; Pwu]
     for (long idx = tid; idx < (long)nn * nn; idx += T) {
@@ -392,18 +393,11 @@ __global__ void __launch_bounds__(1024) k_predictor_solve(int N, double tau_arg,
             lcol[i] = f;
         }
         __syncthreads();
-        const int rows = nn - k - 1, cols = nn - k - 1 + N;
-        for (long idx = tid; idx < (long)rows * cols; idx += T) {
-            int i = k + 1 + (int)(idx / cols);
-            int c = (int)(idx % cols);
-            double f = lcol[i];
-            if (c < nn - k - 1) {
-                int j = k + 1 + c;
-                Mw[(size_t)i * nn + j] -= f * Mw[(size_t)k * nn + j];
-            } else {
-                int j = c - (nn - k - 1);
-                XY[(size_t)i * N + j] -= f * XY[(size_t)k * N + j];
-            }
+        // trailing update: rows by warp, columns by lane
+        for (int i = k + 1 + wy; i < nn; i += NW) {
+            const double f = lcol[i];
+            for (int j = k + 1 + lx; j < nn; j += 32) Mw[(size_t)i * nn + j] -= f * Mw[(size_t)k * nn + j];
+            for (int j = lx; j < N; j += 32) XY[(size_t)i * N + j] -= f * XY[(size_t)k * N + j];
         }
         __syncthreads();
     }
@@ -412,9 +406,9 @@ __global__ void __launch_bounds__(1024) k_predictor_solve(int N, double tau_arg,
         const double dii = Mw[(size_t)i * nn + i];
         for (int j = tid; j < N; j += T) XY[(size_t)i * N + j] /= dii;
         __syncthreads();
-        for (long idx = tid; idx < (long)i * N; idx += T) {
-            int r = (int)(idx / N), j = (int)(idx % N);
-            XY[(size_t)r * N + j] -= Mw[(size_t)r * nn + i] * XY[(size_t)i * N + j];
+        for (int r = wy; r < i; r += NW) {
+            const double u = Mw[(size_t)r * nn + i];
+            for (int j = lx; j < N; j += 32) XY[(size_t)r * N + j] -= u * XY[(size_t)i * N + j];
         }
         __syncthreads();
     }
@@ -720,10 +714,219 @@ void launch_lu_solve(int nn, int N, double *Mw, double *XY, int *ipiv, int *stat
     }
 }
 
+// ---------------------------------------------------------------------------
+// Small solves of the mixed-precision path: FP32 Gaussian elimination with
+// partial pivoting in one CTA's shared memory, followed by FP64 iterative
+// refinement (residual in FP64 over many CTAs, correction with the stored
+// FP32 factors).  GB300 issues about two FP64 lane operations per clock per
+// SM, so a one-SM FP64 elimination is bound by that rate; FP32 runs 64x
+// faster per SM and the FP64 residuals restore FP64 accuracy (each
+// refinement multiplies the error by about cond(A) * 2^-24).
+// ---------------------------------------------------------------------------
+constexpr int LU32_THREADS = 1024;
+
+size_t lu32_smem(int nn, int nr) { return sizeof(float) * ((size_t)nn * (nn + 1) + (size_t)nn * nr); }
+bool lu32_fits(int nn, int nr) { return lu32_smem(nn, nr) <= 200 * 1024; }
+
+__device__ __forceinline__ void lu32_argmax(float v, int i, float *wv, int *wi, int *piv_s,
+                                            float *pval_s) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        const float v2 = __shfl_down_sync(0xffffffffu, v, o);
+        const int i2 = __shfl_down_sync(0xffffffffu, i, o);
+        if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
+    }
+    if (lane == 0) { wv[warp] = v; wi[warp] = i; }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        v = lane < nw ? wv[lane] : -1.0f;
+        i = lane < nw ? wi[lane] : 0x7fffffff;
+        for (int o = 16; o > 0; o >>= 1) {
+            const float v2 = __shfl_down_sync(0xffffffffu, v, o);
+            const int i2 = __shfl_down_sync(0xffffffffu, i, o);
+            if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
+        }
+        if (lane == 0) { *piv_s = i; *pval_s = v; }
+    }
+    __syncthreads();
+}
+
+// A (nn x nn, lda) and B (nn x nr, ldb) in FP64; factors LU (nn x nn FP32,
+// L unit lower below the diagonal, rows permuted) and ipiv to global memory;
+// X (nn x nr, FP64) = the FP32 solution.  Work is mapped row = warp, column =
+// lane (no integer division in the loops).
+__global__ void __launch_bounds__(LU32_THREADS) k_lu32_factor_solve(int nn, int nr, const double *A,
+                                                                  int lda, const double *B, int ldb,
+                                                                  float *LU, int *ipiv, double *X,
+                                                                  int *status) {
+    extern __shared__ float sm32[];
+    float *sA = sm32;                          // nn x (nn + 1)
+    float *sB = sm32 + (size_t)nn * (nn + 1);  // nn x nr
+    __shared__ float wv[32];
+    __shared__ int wi[32];
+    __shared__ int piv_s;
+    __shared__ float pval_s;
+    const int T = blockDim.x, tid = threadIdx.x, la = nn + 1;
+    const int lx = tid & 31, wy = tid >> 5, NW = T >> 5;
+    for (int r = wy; r < nn; r += NW) {
+        for (int c = lx; c < nn; c += 32) sA[r * la + c] = (float)A[(size_t)r * lda + c];
+        for (int c = lx; c < nr; c += 32) sB[r * nr + c] = (float)B[(size_t)r * ldb + c];
+    }
+    __syncthreads();
+    for (int k = 0; k < nn; k++) {
+        float best = -1.0f;
+        int bi = 0x7fffffff;
+        for (int r = k + tid; r < nn; r += T) {
+            const float v = fabsf(sA[r * la + k]);
+            if (v > best) { best = v; bi = r; }
+        }
+        lu32_argmax(best, bi, wv, wi, &piv_s, &pval_s);
+        const int piv = piv_s;
+        if (!(pval_s > 0.0f) || !isfinite(pval_s)) {
+            if (tid == 0) atomicOr(status, ST_SINGULAR);
+            for (int t = k + tid; t < nn; t += T) ipiv[t] = t;
+            return;
+        }
+        if (tid == 0) ipiv[k] = piv;
+        if (piv != k) {
+            for (int c = tid; c < nn; c += T) {
+                const float t = sA[k * la + c];
+                sA[k * la + c] = sA[piv * la + c];
+                sA[piv * la + c] = t;
+            }
+            for (int c = tid; c < nr; c += T) {
+                const float t = sB[k * nr + c];
+                sB[k * nr + c] = sB[piv * nr + c];
+                sB[piv * nr + c] = t;
+            }
+        }
+        __syncthreads();
+        const float inv = 1.0f / sA[k * la + k];
+        for (int r = k + 1 + wy; r < nn; r += NW) {
+            const float l = sA[r * la + k] * inv;   // every lane of the warp computes it
+            for (int c = k + 1 + lx; c < nn; c += 32) sA[r * la + c] -= l * sA[k * la + c];
+            for (int c = lx; c < nr; c += 32) sB[r * nr + c] -= l * sB[k * nr + c];
+        }
+        __syncthreads();
+        for (int r = k + 1 + tid; r < nn; r += T) sA[r * la + k] *= inv;
+        // (column k below the diagonal is read by no later step of this loop)
+    }
+    __syncthreads();
+    for (int k = nn - 1; k >= 0; k--) {
+        const float inv = 1.0f / sA[k * la + k];
+        for (int r = wy; r < k; r += NW) {
+            const float u = sA[r * la + k] * inv;
+            for (int c = lx; c < nr; c += 32) sB[r * nr + c] -= u * sB[k * nr + c];
+        }
+        __syncthreads();
+        for (int c = tid; c < nr; c += T) sB[k * nr + c] *= inv;
+        // row k is read by no later step
+    }
+    __syncthreads();
+    for (int r = wy; r < nn; r += NW) {
+        for (int c = lx; c < nn; c += 32) LU[(size_t)r * nn + c] = sA[r * la + c];
+        for (int c = lx; c < nr; c += 32) X[(size_t)r * nr + c] = (double)sB[r * nr + c];
+    }
+}
+
+// R = B - A X in FP64 (one thread per entry of R, 64-thread CTAs)
+__global__ void __launch_bounds__(64) k_resid64(int nn, int nr, const double *A, int lda,
+                                                const double *B, int ldb, const double *X,
+                                                double *R) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nn * nr) return;
+    const int r = e / nr, c = e % nr;
+    double s = B[(size_t)r * ldb + c];
+    for (int k = 0; k < nn; k++) s -= A[(size_t)r * lda + k] * X[(size_t)k * nr + c];
+    R[e] = s;
+}
+
+// X += (LU)^-1 P R with the stored FP32 factors
+__global__ void __launch_bounds__(LU32_THREADS) k_lu32_resolve(int nn, int nr, const float *LU,
+                                                             const int *ipiv, const double *R,
+                                                             double *X) {
+    extern __shared__ float sm32[];
+    float *sA = sm32;
+    float *sB = sm32 + (size_t)nn * (nn + 1);
+    const int T = blockDim.x, tid = threadIdx.x, la = nn + 1;
+    const int lx = tid & 31, wy = tid >> 5, NW = T >> 5;
+    for (int r = wy; r < nn; r += NW) {
+        for (int c = lx; c < nn; c += 32) sA[r * la + c] = LU[(size_t)r * nn + c];
+        for (int c = lx; c < nr; c += 32) sB[r * nr + c] = (float)R[(size_t)r * nr + c];
+    }
+    __syncthreads();
+    // row swaps in elimination order, one thread per right-hand side
+    for (int c = tid; c < nr; c += T)
+        for (int k = 0; k < nn; k++) {
+            const int p = ipiv[k];
+            if (p != k) {
+                const float t = sB[k * nr + c];
+                sB[k * nr + c] = sB[p * nr + c];
+                sB[p * nr + c] = t;
+            }
+        }
+    __syncthreads();
+    for (int k = 0; k < nn - 1; k++) {
+        for (int r = k + 1 + wy; r < nn; r += NW) {
+            const float l = sA[r * la + k];
+            for (int c = lx; c < nr; c += 32) sB[r * nr + c] -= l * sB[k * nr + c];
+        }
+        __syncthreads();
+    }
+    for (int k = nn - 1; k >= 0; k--) {
+        const float inv = 1.0f / sA[k * la + k];
+        for (int r = wy; r < k; r += NW) {
+            const float u = sA[r * la + k] * inv;
+            for (int c = lx; c < nr; c += 32) sB[r * nr + c] -= u * sB[k * nr + c];
+        }
+        __syncthreads();
+        for (int c = tid; c < nr; c += T) sB[k * nr + c] *= inv;
+    }
+    __syncthreads();
+    for (int r = wy; r < nn; r += NW)
+        for (int c = lx; c < nr; c += 32) X[(size_t)r * nr + c] += (double)sB[r * nr + c];
+}
+
+void lu32_prepare() {
+    static bool done = false;
+    if (done) return;
+    const int lim = 200 * 1024;
+    cudaFuncSetAttribute(k_lu32_factor_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_lu32_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    done = true;
+}
+
+// X = A^-1 B (A nn x nn, B nn x nr, FP64 in and out) by FP32 elimination and
+// `refine` FP64 refinement steps; LU (nn^2 floats), ipiv (nn) and R (nn x nr
+// doubles) are scratch.  Requires lu32_fits(nn, nr).
+void launch_solve32_refined(int nn, int nr, const double *A, int lda, const double *B, int ldb,
+                            double *X, float *LU, int *ipiv, double *R, int refine, int *status,
+                            cudaStream_t s) {
+    const size_t shm = lu32_smem(nn, nr);
+    HQ_LAUNCH(HQ_K_SMALL, k_lu32_factor_solve<<<1, LU32_THREADS, shm, s>>>(nn, nr, A, lda, B, ldb,
+                                                                          LU, ipiv, X, status));
+    for (int it = 0; it < refine; it++) {
+        HQ_LAUNCH(HQ_K_SMALL, k_resid64<<<(nn * nr + 63) / 64, 64, 0, s>>>(nn, nr, A, lda, B, ldb,
+                                                                          X, R));
+        HQ_LAUNCH(HQ_K_SMALL, k_lu32_resolve<<<1, LU32_THREADS, shm, s>>>(nn, nr, LU, ipiv, R, X));
+    }
+}
+
 void launch_predictor_solve(int N, double tau, const double *G2, double *Mw, double *XY,
                             double *C, int *status, cudaStream_t s, const double *tau_dev,
-                            int *ipiv) {
+                            int *ipiv, float *lu32, double *pB, double *pR) {
     const int nn = 2 * N;
+    if (lu32 && pB && pR && ipiv && lu32_fits(nn, N)) {
+        // mixed-precision path: FP32 elimination + 2 FP64 refinement steps
+        const long tot = (long)nn * nn + (long)nn * N;
+        HQ_LAUNCH(HQ_K_SMALL, k_pred_build<<<(int)std::min<long>((tot + 255) / 256, 1024), 256, 0, s>>>(
+                                  N, tau, tau_dev, G2, Mw, pB));
+        launch_solve32_refined(nn, N, Mw, nn, pB, N, XY, lu32, ipiv, pR, 2, status, s);
+        HQ_LAUNCH(HQ_K_SMALL, k_pred_c<<<(int)std::min<long>(((long)N * N + 255) / 256, 1024), 256, 0, s>>>(
+                                  N, tau, tau_dev, XY, C));
+        return;
+    }
     if (nn <= 64 || !ipiv) {
         size_t shm = sizeof(double) * (2 * N + 1024) + sizeof(int) * 1024;
         HQ_LAUNCH(HQ_K_SMALL, k_predictor_solve<<<1, 1024, shm, s>>>(N, tau, G2, Mw, XY, C, status,
@@ -752,7 +955,13 @@ __global__ void k_copy2(int N, const double *A, int lda, const double *B, int ld
     }
 }
 void launch_spd_solve(int N, const double *A, int lda, const double *B, int ldb, double *Mw,
-                      double *L, double *X, int *ipiv, int *status, cudaStream_t s) {
+                      double *L, double *X, int *ipiv, int *status, cudaStream_t s, float *lu32) {
+    if (lu32 && ipiv && lu32_fits(N, N)) {
+        // mixed-precision path (a warm start only needs FP32 accuracy)
+        HQ_LAUNCH(HQ_K_SMALL, k_lu32_factor_solve<<<1, LU32_THREADS, lu32_smem(N, N), s>>>(
+                                  N, N, A, lda, B, ldb, lu32, ipiv, X, status));
+        return;
+    }
     if (N <= 32 || !ipiv) {
         launch_chol_solve(N, A, lda, B, ldb, L, X, status, s);
         return;
@@ -1050,11 +1259,10 @@ __global__ void __launch_bounds__(1024) k_rr_reduce(int N, const double *K, cons
         __syncthreads();
         for (int i = k + tid; i < N; i += T) L[(size_t)i * N + k] = (i == k) ? d : L[(size_t)i * N + k] / d;
         __syncthreads();
-        const int r = N - k - 1;
-        for (long idx = tid; idx < (long)r * r; idx += T) {
-            int i = k + 1 + (int)(idx / r), j = k + 1 + (int)(idx % r);
-            if (j > i) continue;
-            L[(size_t)i * N + j] -= L[(size_t)i * N + k] * L[(size_t)j * N + k];
+        for (int i = k + 1 + (tid >> 5); i < N; i += (T >> 5)) {
+            const double lik = L[(size_t)i * N + k];
+            for (int j = k + 1 + (tid & 31); j <= i; j += 32)
+                L[(size_t)i * N + j] -= lik * L[(size_t)j * N + k];
         }
         __syncthreads();
     }
@@ -1117,11 +1325,10 @@ __global__ void __launch_bounds__(1024) k_chol_solve(int N, const double *A, int
         __syncthreads();
         for (int i = k + tid; i < N; i += T) L[(size_t)i * N + k] = (i == k) ? d : L[(size_t)i * N + k] / d;
         __syncthreads();
-        const int r = N - k - 1;
-        for (long idx = tid; idx < (long)r * r; idx += T) {
-            int i = k + 1 + (int)(idx / r), j = k + 1 + (int)(idx % r);
-            if (j > i) continue;
-            L[(size_t)i * N + j] -= L[(size_t)i * N + k] * L[(size_t)j * N + k];
+        for (int i = k + 1 + (tid >> 5); i < N; i += (T >> 5)) {
+            const double lik = L[(size_t)i * N + k];
+            for (int j = k + 1 + (tid & 31); j <= i; j += 32)
+                L[(size_t)i * N + j] -= lik * L[(size_t)j * N + k];
         }
         __syncthreads();
     }

@@ -453,31 +453,58 @@ __global__ void __launch_bounds__(256) k_coarse_solve(long nc, int N, int ppt,
 }
 
 // ---------------------------------------------------------------------------
-// per-column finalisation of the PCG recurrences (one block per column)
+// per-column finalisation of the PCG recurrences.  Grid: ceil(N/32) column
+// tiles x ceil(gy/FIN_ROWS) row chunks; lanes are columns (coalesced reads of
+// the gy x N partials), warps split a chunk's rows.  Each CTA stores its chunk
+// sums; the last CTA of a column tile to arrive (arrival counter) adds the
+// chunk sums in chunk order, so the result does not depend on scheduling,
+// applies the PCG update for its 32 columns and resets the counter.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_finalize(int mode, int N, int gy, const double *part,
+constexpr int FIN_ROWS = 128;
+
+__global__ void __launch_bounds__(256) k_finalize(int mode, int N, int gy, const double *part,
                                                   const double *part2, PcgScalars sc,
                                                   double rtol) {
-    __shared__ double red[2][128];
-    const int col = blockIdx.x;
+    __shared__ double red[2][8][32];
+    __shared__ int last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int col = blockIdx.x * 32 + lane;
+    const int R = gridDim.y, y0 = blockIdx.y * FIN_ROWS;
+    const int y1 = min(gy, y0 + FIN_ROWS);
     double s = 0.0, s2 = 0.0;
-    for (int i = threadIdx.x; i < gy; i += blockDim.x) {
-        s += part[(size_t)i * N + col];
-        if (part2) s2 += part2[(size_t)i * N + col];
-    }
-    red[0][threadIdx.x] = s;
-    red[1][threadIdx.x] = s2;
-    __syncthreads();
-    for (int w = 64; w > 0; w >>= 1) {
-        if (threadIdx.x < w) {
-            red[0][threadIdx.x] += red[0][threadIdx.x + w];
-            red[1][threadIdx.x] += red[1][threadIdx.x + w];
+    if (col < N)
+        for (int i = y0 + warp; i < y1; i += 8) {
+            s += part[(size_t)i * N + col];
+            if (part2) s2 += part2[(size_t)i * N + col];
         }
-        __syncthreads();
+    red[0][warp][lane] = s;
+    red[1][warp][lane] = s2;
+    __syncthreads();
+    if (warp == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < 8; w++) {
+            a += red[0][w][lane];
+            b += red[1][w][lane];
+        }
+        if (col < N) {
+            sc.fpart[(size_t)blockIdx.y * N + col] = a;
+            sc.fpart[(size_t)(R + blockIdx.y) * N + col] = b;
+        }
+        __threadfence();
     }
-    if (threadIdx.x != 0) return;
-    s = red[0][0];
-    s2 = red[1][0];
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(&sc.fcount[blockIdx.x], 1u) == (unsigned)(R - 1));
+    __syncthreads();
+    if (!last || warp != 0) return;
+    __threadfence();
+    if (lane == 0) sc.fcount[blockIdx.x] = 0u;
+    if (col >= N) return;
+    s = 0.0;
+    s2 = 0.0;
+    for (int c = 0; c < R; c++) {
+        s += __ldcg(&sc.fpart[(size_t)c * N + col]);
+        s2 += __ldcg(&sc.fpart[(size_t)(R + c) * N + col]);
+    }
     switch (mode) {
     case FIN_BNORM_RNORM: {
         double rn = sqrt(s), bn = sqrt(s2);
@@ -928,7 +955,11 @@ void launch_prolong(int mf, int mc, int N, const XferTab &t, const T *ec, T *tmp
 template <typename T, int V>
 static void run_coarse_solve(const GridGeom &g, const double *Ainv, const T *r, T *z,
                              cudaStream_t s) {
-    HQ_LAUNCH_W(HQ_K_COARSE, (double)g.n * g.N, k_coarse_solve<T, V><<<grd(g), blk(g), 0, s>>>(g.n, g.N, g.ppt, Ainv, r, z));
+    // one coarse point per CTA row: the FP64 products of the dense inverse
+    // are spread over nc CTAs (GB300's per-SM FP64 rate is low)
+    HQ_LAUNCH_W(HQ_K_COARSE, (double)g.n * g.N,
+                k_coarse_solve<T, V><<<dim3(g.gx, (unsigned)g.n), dim3(g.tx, 1), 0, s>>>(
+                    g.n, g.N, 1, Ainv, r, z));
 }
 template <typename T>
 void launch_coarse_solve(const GridGeom &g, const double *Ainv, const T *r, T *z,
@@ -945,9 +976,12 @@ void launch_dot(const GridGeom &g, const T *x, const T *y, double *part, cudaStr
     HQ_VEC_DISPATCH(T, g, run_dot, g, x, y, part, s);
 }
 
+int finalize_chunks(int gy) { return (gy + FIN_ROWS - 1) / FIN_ROWS; }
+
 void launch_finalize(int mode, int N, int gy, const double *part, const double *part2,
                      PcgScalars sc, double rtol, cudaStream_t s) {
-    HQ_LAUNCH(HQ_K_REDUCE, k_finalize<<<N, 128, 0, s>>>(mode, N, gy, part, part2, sc, rtol));
+    const dim3 grid((N + 31) / 32, finalize_chunks(gy));
+    HQ_LAUNCH(HQ_K_REDUCE, k_finalize<<<grid, 256, 0, s>>>(mode, N, gy, part, part2, sc, rtol));
 }
 
 template <typename T>

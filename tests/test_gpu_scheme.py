@@ -192,3 +192,22 @@ def test_adaptive_tau_trajectory_matches_oracle():
     assert steps == 20
     np.testing.assert_allclose(taus, th, rtol=1e-9)
     assert rel(s.get_state()[0], Ue) < 1e-8
+
+
+@pytest.mark.parametrize("m,N", [(12, 8), (12, 40), (14, 90)])
+def test_mixed_predictor_system_is_solved_to_fp64_accuracy(m, N):
+    """Mixed precision solves the 2N x 2N predictor system of Eq. (4.1) by FP32
+    elimination plus FP64 iterative refinement: the FP64 residual of the
+    equations, re-evaluated from the step's Gram G2 and its X, Y, is at the
+    FP64 rounding level (FP32 alone would leave ~1e-7)."""
+    tau = 0.4
+    s, V, U0 = make(m, N, precision="mixed", tau=tau, cg_rtol=1e-6)
+    tr = s.step_trace()
+    G2, XY = host(tr["gram"]), host(tr["XY"])
+    S, Puw = G2[:N, :N], G2[:N, N:]
+    Pwu, Q = G2[N:, :N], G2[N:, N:]
+    I = np.eye(N)
+    Mm = np.block([[I - tau / 2 * Puw, tau / 2 * S], [-tau / 2 * Q, I + tau / 2 * Pwu]])
+    rhs = np.vstack([S, Pwu])
+    res = np.abs(Mm @ XY - rhs).max() / np.abs(rhs).max()
+    assert res < 1e-13, res
