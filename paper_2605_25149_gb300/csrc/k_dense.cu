@@ -213,9 +213,11 @@ __global__ void __launch_bounds__(256) k_tall_gemm(TallPlan P, const T *A1, cons
             T v = acc[i][j];
             if (Cin) v = Cin[e] + v;
             if (Out) Out[e] = v;
-            double dv = (double)v;
-            sq += dv * dv;
-            sqc[j] += dv * dv;
+            if (part_sq) {
+                double dv = (double)v;
+                sq += dv * dv;
+                sqc[j] += dv * dv;
+            }
         }
     }
     if (part_sq) {

@@ -575,23 +575,47 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (abort_sh) {
         if (tid == 0) atomicOr(status, ST_TC_TIMEOUT);
     } else {
-        // epilogue: thread = one point row (TMEM lane), 32 columns per load
+        // epilogue: thread = one point row (TMEM lane), 32 columns per load;
+        // 16-byte loads / stores where the row segment allows, squares summed
+        // in FP32 per 32 columns and in FP64 across segments (only when the
+        // sum of squares is requested)
         const long p = r0 + warp * 32 + lane;
+        const bool v4 = (P.ncol % 4 == 0) && (((uintptr_t)Out & 15) == 0) &&
+                        (((uintptr_t)Cin & 15) == 0);
         for (int cb = 0; cb < NT; cb += 32) {
             float v[32];
             tmem_ld32<32>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
-            if (p < P.n) {
+            if (p >= P.n) continue;
+            const int c0 = ct * NT + cb;
+            float sqf = 0.f;
+            if (v4 && cb + 32 <= NT && c0 + 32 <= P.ncol) {
+                const size_t e0 = (size_t)p * P.ncol + c0;
+#pragma unroll
+                for (int j = 0; j < 32; j += 4) {
+                    float4 o = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    if (Cin) {
+                        const float4 ci = *reinterpret_cast<const float4 *>(Cin + e0 + j);
+                        o.x += ci.x;
+                        o.y += ci.y;
+                        o.z += ci.z;
+                        o.w += ci.w;
+                    }
+                    if (Out) *reinterpret_cast<float4 *>(Out + e0 + j) = o;
+                    if (part_sq) sqf += (o.x * o.x + o.y * o.y) + (o.z * o.z + o.w * o.w);
+                }
+            } else {
 #pragma unroll
                 for (int j = 0; j < 32; j++) {
-                    const int c = ct * NT + cb + j;
+                    const int c = c0 + j;
                     if (cb + j >= NT || c >= P.ncol) continue;
                     const size_t e = (size_t)p * P.ncol + c;
                     float o = v[j];
                     if (Cin) o += Cin[e];
                     if (Out) Out[e] = o;
-                    sq += (double)o * (double)o;
+                    if (part_sq) sqf += o * o;
                 }
             }
+            if (part_sq) sq += (double)sqf;
         }
     }
     if (part_sq) {
