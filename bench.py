@@ -48,8 +48,8 @@ ALGO = {"smooth": (10.0, 3.0), "stencil": (8.0, 2.0), "residual": (9.0, 3.0)}
 # ncu (dram__bytes_read.sum + dram__bytes_write.sum of one launch / 16.78 M
 # point-columns, profiles/k_jacobi_wells64_N64.md); set to None whenever the
 # kernel changes until it is captured again.
-TRAFFIC_PER_ELEMENT = {("smooth", "f64"): (278.660352e6 + 112.328704e6) / 16777216,
-                       ("smooth", "f32"): (135.338240e6 + 44.317696e6) / 16777216}
+TRAFFIC_PER_ELEMENT = {("smooth", "f64"): (288.253952e6 + 111.722752e6) / 16777216,
+                       ("smooth", "f32"): (136.215040e6 + 44.029440e6) / 16777216}
 
 
 # Recorded by `python bench.py --ttr` on a GB300 (profiles/ttr_wells64_N64.md):
@@ -200,6 +200,63 @@ def roofline(prof, dtype_tag, hbm_peak, hbm_kind):
                "peak_source": hbm_kind}
     out.update({"launches": launches, "ms_per_launch": ms / launches,
                 "elements_per_launch": per_launch_elems, "share": ms / sum(v[1] for v in prof.values())})
+    return out
+
+
+def smooth_alone(torch, hq, s, reps=40):
+    """The finest-level damped-Jacobi sweep (the dominant kernel class) timed
+    alone: `reps` back-to-back launches through hq_mg_smooth on n x N blocks
+    of the context's working precision (ping-pong z_in / z_out; the three
+    blocks exceed L2, so every sweep streams from HBM), CUDA events on the
+    context's stream around the whole sequence.  Returns ms per launch."""
+    import ctypes
+    n, N = s.n, s.N
+    g = torch.Generator(device="cuda").manual_seed(7)
+    r = torch.rand((n, N), generator=g, device="cuda", dtype=s.dtype)
+    za = torch.rand((n, N), generator=g, device="cuda", dtype=s.dtype)
+    zb = torch.empty_like(za)
+    st = s.stream
+    lib = s.lib
+    args = [(ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(za.data_ptr()),
+             ctypes.c_void_p(zb.data_ptr())),
+            (ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(zb.data_ptr()),
+             ctypes.c_void_p(za.data_ptr()))]
+    for i in range(4):
+        s._check(lib.hq_mg_smooth(s._ctx, 0, *args[i & 1]), "hq_mg_smooth")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for i in range(reps):
+        s._check(lib.hq_mg_smooth(s._ctx, 0, *args[i & 1]), "hq_mg_smooth")
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def roofline_alone(ms_launch, n_el, dtype_tag, hbm_peak, hbm_kind, in_step):
+    """Roofline entry of the smooth kernel from its stand-alone launch time."""
+    flops_e, words_e = ALGO["smooth"]
+    w = 8 if dtype_tag == "f64" else 4
+    t = ms_launch / 1e3
+    tr = TRAFFIC_PER_ELEMENT.get(("smooth", dtype_tag))
+    traffic = None if tr is None else tr * n_el
+    out = {"kernel": "smooth (k_jacobi, finest level)", "timing": "alone: back-to-back "
+           "launches on the step's block shape, CUDA events; inputs exceed L2",
+           "ms_per_launch": ms_launch, "elements_per_launch": n_el, "traffic": traffic,
+           "algorithmic_bytes": words_e * w * n_el, "algorithmic_flops": flops_e * n_el}
+    if dtype_tag == "f64":
+        achieved = flops_e * n_el / t / 1e12
+        peak = FP64_PEAK_GFLOPS / 1e3
+        out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak,
+                    "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz",
+                    "hbm_gbs": words_e * w * n_el / t / 1e9})
+    else:
+        achieved = words_e * w * n_el / t / 1e9
+        out.update({"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "peak_source": hbm_kind})
+    out["in_step"] = in_step
     return out
 
 
@@ -488,7 +545,8 @@ def run_hq(args):
     prof = s.profile_read()
     pcg_solves, pcg_iters = s.pcg_stats()
     s.profile(timing=False)
-    roof = roofline(prof, "f64", hbm_peak, hbm_kind)
+    roof = roofline_alone(smooth_alone(torch, hq, s), m ** 3 * N, "f64", hbm_peak, hbm_kind,
+                          roofline(prof, "f64", hbm_peak, hbm_kind))
     brk = breakdown(prof, K)
     # end to end through host buffers: state in from pinned host memory,
     # step, state and gradient norm back to pinned host memory
@@ -545,7 +603,9 @@ def run_hq(args):
                      "how": "recorded (%s); same step count, so the speedup at error 1e-6 "
                             "equals the per-step ratio" % TTR_STEPS[WORKLOAD]["command"]},
                  "cg_rtol": args.mixed_rtol,
-                 "roofline": roofline(prof_m, "f32", hbm_peak, hbm_kind),
+                 "roofline": roofline_alone(smooth_alone(torch, hq, sm), m ** 3 * N, "f32",
+                                            hbm_peak, hbm_kind,
+                                            roofline(prof_m, "f32", hbm_peak, hbm_kind)),
                  "breakdown": breakdown(prof_m, K)}
         del sm
         torch.cuda.empty_cache()
