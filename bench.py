@@ -504,6 +504,43 @@ def bench_batched(torch, hq, inputs, K, W, tune=True):
     return res
 
 
+def bench_large(torch, hq, inputs, K, W, hbm_peak, hbm_kind, shape=(128, 256)):
+    """The 128^3, N = 256 wells workload in mixed precision (FP32 blocks of
+    2.15 GB: every grid kernel streams from HBM): ms per step, the smooth
+    sweep timed alone against the HBM roofline, and the per-class split of
+    an instrumented pass.  `shape` = (m, N) overrides the size (same
+    potential family and seeds), e.g. for a profiler capture of a smaller
+    case."""
+    V, U0, w = inputs.workload("wells128_N256")
+    if tuple(shape) != (w["m"], w["N"]):
+        w = dict(w, m=shape[0], N=shape[1])
+        V = inputs.wells(w["m"], w["potential"][1])
+        U0 = inputs.initial_block(w["m"], w["N"], w["u0_seed"])
+    m, N = w["m"], w["N"]
+    s = hq.Solver(m, N, tau=w["tau"], cg_rtol=w["cg_rtol"], precision="mixed")
+    s.set_potential(V)
+    s.set_initial(U0)
+    del U0
+    for _ in range(W):
+        s.step(1)
+    ms, _ = time_steps(torch, s, K, 1, "large_timed")
+    s.profile(timing=True)
+    time_steps(torch, s, 1, 1)
+    prof = s.profile_read()
+    s.profile(timing=False)
+    ms_sm = smooth_alone(torch, hq, s, reps=10)
+    roof = roofline_alone(ms_sm, m ** 3 * N, "f32", hbm_peak, hbm_kind, None)
+    roof["traffic"] = None
+    out = {"workload": "wells: %d^3 grid, V=|x|^2/2 + 8 wells (default_rng(3)), "
+                       "N=%d, tau=0.4, mixed, PCG rtol 1e-6" % (m, N),
+           "ms_per_step": ms, "value": 1000.0 / ms, "unit": "steps/s", "roofline": roof,
+           "breakdown": breakdown(prof, 1),
+           "workspace_gb": s.workspace.numel() / 1e9}
+    del s
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_hq(args):
     import numpy as np
     import torch
@@ -610,6 +647,12 @@ def run_hq(args):
         del sm
         torch.cuda.empty_cache()
 
+    # ---- 128^3, N = 256 in mixed precision ---------------------------------------
+    large = None
+    if not args.no_large:
+        large = bench_large(torch, hq, inputs, max(1, min(K, 3)), max(1, min(W, 2)), hbm_peak,
+                            hbm_kind, tuple(args.large_shape))
+
     # ---- batched form ---------------------------------------------------------
     batched = None
     if not args.no_batch:
@@ -645,6 +688,7 @@ def run_hq(args):
                 "how": "hq_set_state from pinned host (U and warm start), hq_step, "
                        "hq_get_state to pinned host, every step"},
         "mixed": mixed,
+        "large": large,
         "batched": batched,
         "cpu_baseline": cpu,
         "gradient_norm_last": g,
@@ -736,6 +780,9 @@ def main():
     ap.add_argument("--tau-max", type=float, default=10.0)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
+    ap.add_argument("--no-large", action="store_true", help="skip the 128^3, N = 256 workload")
+    ap.add_argument("--large-shape", type=int, nargs=2, default=[128, 256], metavar=("M", "N"),
+                    help="grid side and block width of the large mixed workload")
     ap.add_argument("--no-tune", action="store_true",
                     help="batched workload with the default launch shape only")
     ap.add_argument("--mixed-rtol", type=float, default=1e-6)

@@ -86,11 +86,17 @@ typedef struct {
     int grid_block;      /* threads per CTA of the grid kernels: 0 (= 256), 64, 128, 256 */
     int grid_ctas;       /* target CTAs per SM of the grid kernels: 0 (= 16) .. 64;     */
                          /* both set the launch shape only (hq_tune picks them)      */
+    int fp64_tc;         /* HQ_FP64 only: 1 = the n x N block products (Uh, U_{n+1},   */
+                         /* the gradient residual, the warm start) on tensor cores by */
+                         /* exact integer slicing of the FP64 values (error below    */
+                         /* 2^-53 of |row max| |column max| per term, FP64 results), */
+                         /* for K <= 128 columns; 0 = FP64 SIMT products             */
 } hq_config;
 
 /* Defaults: box [-6,6]^3, tau 0.4, automatic shift, FP64, cg_rtol 1e-10,
  * cg_maxit 200, nu1 = nu2 = 2, coarsest 4, omega 0.8, no timeout, warm start
- * of the corrector solve on.  m and nev are left 0 and must be set.         */
+ * of the corrector solve on, fp64_tc on.  m and nev are left 0 and must be
+ * set.                                                                      */
 void hq_default_config(hq_config *cfg);
 
 /* Bytes of device workspace hq_init needs for cfg (0 if cfg is invalid). */

@@ -110,6 +110,7 @@ struct hq_ctx {
     int *status = nullptr;
     int *ipiv = nullptr;   // pivots of the small eliminations (2N)
     float *lu32 = nullptr;  // FP32 factors of the small systems (mixed precision)
+    unsigned char *ozimg = nullptr;   // FP64 tensor-core block products: digit planes
     double *pB = nullptr, *pR = nullptr;   // predictor right-hand side / residual
     double *vn[3] = {nullptr, nullptr, nullptr};   // FP64 n-vectors (density, adjoint)
     double *pvec = nullptr;                        // power-iteration vector (N)
@@ -255,6 +256,7 @@ bool valid_config(const hq_config *c, std::string *why) {
     if (c->grid_block != 0 && c->grid_block != 64 && c->grid_block != 128 && c->grid_block != 256)
         return fail("grid_block must be 0, 64, 128 or 256");
     if (c->grid_ctas < 0 || c->grid_ctas > 64) return fail("grid_ctas must be in [0, 64]");
+    if (c->fp64_tc != 0 && c->fp64_tc != 1) return fail("fp64_tc must be 0 or 1");
     return true;
 }
 
@@ -368,6 +370,10 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
     // mixed-precision small solves: FP32 factors and FP64 right-hand side /
     // residual of the predictor system
     float *lu32 = mixed ? cv.take<float>(sizeof(float) * 4 * N2) : nullptr;
+    // digit planes of the small matrices of the FP64 tensor-core block products
+    unsigned char *ozimg = (!mixed && c->fp64_tc && tall_oz_supported(2 * N, 0))
+                               ? cv.take<unsigned char>(tall_oz_image_bytes(n, 2 * N, N))
+                               : nullptr;
     double *pB = mixed ? cv.take<double>(sizeof(double) * 2 * N2) : nullptr;
     double *pR = mixed ? cv.take<double>(sizeof(double) * 2 * N2) : nullptr;
     double *Cc = cv.take<double>(sizeof(double) * 2 * N2);
@@ -411,6 +417,7 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
         x->tplan = tp; x->tpart = tpart;
         x->ipiv = ipiv;
         x->lu32 = lu32;
+        x->ozimg = ozimg;
         x->pB = pB;
         x->pR = pR;
         x->G2 = G2; x->Mw = Mw; x->XY = XY; x->C = Cc; x->T1 = T1; x->Shat = Shat; x->Om = Om;
@@ -719,6 +726,12 @@ void block_gemm(hq_ctx *x, const T *A1, int k1, const double *M1, const T *A2, i
 template <>
 void block_gemm<double>(hq_ctx *x, const double *A1, int k1, const double *M1, const double *A2,
                         int k2, const double *M2, const double *Cin, double *Out, bool sq, int *np) {
+    if (x->ozimg && tall_oz_supported(k1, A2 ? k2 : 0)) {
+        launch_tall_oz(x->n, A1, k1, M1, A2, k2, M2, x->N, Cin, Out, sq ? x->tpart : nullptr,
+                       x->ozimg, x->status, x->st);
+        if (np) *np = tall_oz_partials(x->n, x->N);
+        return;
+    }
     TallPlan tp = make_tall_plan(x->n, x->N, k1, k2);
     launch_tall_gemm<double>(tp, A1, M1, A2, M2, Cin, Out, sq ? x->tpart : nullptr, x->st);
     if (np) *np = tp.gy * tp.gx;
@@ -1894,6 +1907,7 @@ void hq_default_config(hq_config *c) {
     c->timeout_s = 0.0;
     c->z_warm_start = 1;
     c->adaptive_tau = 0;
+    c->fp64_tc = 1;
     c->tau_max = 0.0;
 }
 
@@ -1942,6 +1956,7 @@ hq_status hq_init(const hq_config *cfg, void *d_workspace, size_t bytes, void *c
     if (x->mixed) hq::tc_prepare();
     hq::lu_prepare();
     if (x->mixed) hq::lu32_prepare();
+    if (x->ozimg) hq::oz_prepare();
     if (e != cudaSuccess) {
         delete x;
         return HQ_ERR_CUDA;

@@ -132,6 +132,17 @@ void launch_pcg_cond2(const int *num_active, int *iter, int maxit, cudaGraphCond
 // out[i] = pseudo-random value in [-1, 1) from a hash of (seed, i)
 template <typename T>
 void launch_fill_hash(long count, unsigned long long seed, T *out, cudaStream_t s);
+// FP64 block products on tensor cores by exact integer slicing (k_tall_oz.cu):
+// Out = A1 M1 (+ A2 M2) (+ Cin), FP64, for K = k1 + k2 <= 128; image: scratch
+// of tall_oz_image_bytes(n, K, ncol); part_sq: tall_oz_partials(n, ncol) sums of
+// squares of Out (nullable)
+bool tall_oz_supported(int k1, int k2);
+size_t tall_oz_image_bytes(long n, int K, int ncol);
+int tall_oz_partials(long n, int ncol);
+void oz_prepare();
+void launch_tall_oz(long n, const double *A1, int k1, const double *M1, const double *A2, int k2,
+                    const double *M2, int ncol, const double *Cin, double *Out, double *part_sq,
+                    unsigned char *image, int *status, cudaStream_t s);
 // sets the dynamic shared-memory limits of the tensor-core kernels (call once,
 // outside any stream capture)
 void tc_prepare();

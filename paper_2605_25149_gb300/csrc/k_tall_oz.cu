@@ -1,0 +1,365 @@
+// FP64 block x small-matrix products on the tcgen05 tensor cores by exact
+// integer slicing (the splitting idea of Ozaki, Ogita, Oishi and Rump, 2012).
+//
+//   Out (n x ncol) = [A1 A2] (n x K) [M1; M2] (K x ncol) (+ Cin), all FP64.
+//
+// GB300 retires about two FP64 lane operations per clock per SM, so the FP64
+// SIMT form of these products is bound by the FP64 pipe.  Here every value is
+// written as a scaled sum of 8 signed 7-bit integer digits:
+//   A[p][k] = 2^(e_p) * sgn * sum_{i=1..8} a_i 2^(-7i)   (+ below 2^-56 |row max|),
+// with e_p taken from the largest exponent of row p (points) of [A1 A2], and
+// likewise for each column c of [M1; M2].  Digits are integers 0..127, exact
+// in bf16.  Products of digit pairs with the same i + j = t share the scale
+// 2^(-7t) and are accumulated by kind::f16 MMAs into one FP32 TMEM
+// accumulator D_t; every partial sum is an integer below
+// 8 * K * 127^2 < 2^24 for K <= 128, so the accumulation is exact.  Pairs with
+// t <= 9 are kept (the dropped ones are below 2^-53 of |row max| |column max|
+// per term).  The epilogue combines D_2..D_9 in 64-bit fixed point, converts
+// once to FP64, applies 2^(e_p + f_c), adds Cin and optionally sums squares.
+//
+// CTA = 128 points x 64 output columns, all K; per 64-wide K chunk the 128
+// threads convert the FP64 rows into 8 digit planes (K-major, 128-byte
+// swizzle) and copy the 8 digit planes of the small matrix prepared once per
+// call by k_oz_split; one thread issues 36 MMAs per K step of 16.  TMEM:
+// 8 accumulators x 64 columns = 512 columns.  Every wait is bounded.
+#include "hq_internal.cuh"
+#include "tc_common.cuh"
+
+#include <algorithm>
+
+namespace hq {
+
+namespace {
+
+constexpr int OZ_M = 128;                 // points per CTA (TMEM lanes)
+constexpr int OZ_NT = 64;                 // output columns per CTA
+constexpr int OZ_KC = 64;                 // K per chunk: 128 bytes of bf16 per row
+constexpr int OZ_S = 8;                   // digits per value
+constexpr int OZ_BITS = 7;                // bits per digit
+constexpr int OZ_THREADS = 256;           // 8 warps: warp w reads TMEM lanes 32 (w % 4)..
+constexpr int OZ_APLANE = OZ_M * 128;     // one digit plane of the point rows: 16 KB
+constexpr int OZ_BPLANE = OZ_NT * 128;    // one digit plane of the small matrix: 8 KB
+constexpr int OZ_SMEM = OZ_S * (OZ_APLANE + OZ_BPLANE) + 1024;
+constexpr int OZ_EBAD = 0x7FF;            // biased exponent of Inf / NaN
+constexpr int OZ_FRAC = 40;               // fraction bits of the fixed-point combination
+
+// byte offset of 16-bit element (row r, k) in a K-major tile of 64-element
+// rows with the 128-byte swizzle (16-byte chunk c of row r at c ^ (r & 7))
+__device__ __forceinline__ uint32_t sw128_offset16(int r, int k) {
+    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 3) ^ (r & 7)) & 7) << 4) +
+                      ((k & 7) << 1));
+}
+
+// instruction descriptor: D f32, A/B bf16, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ int biased_exp(double x) {
+    return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+
+// the 8 digits of x relative to the biased exponent emax of its row / column,
+// as bf16 bit patterns of the signed integers
+__device__ __forceinline__ void oz_digits(double x, int emax, uint16_t (&dg)[OZ_S]) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    unsigned long long f = 0ull;   // |x| / 2^(emax - 1022) with 62 fraction bits
+    if (ex != 0 && ex != OZ_EBAD && emax != OZ_EBAD) {
+        const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        const int sh = 9 + ex - emax;   // <= 9 since ex <= emax
+        f = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> (-sh)) : 0ull);
+    }
+    const uint16_t sgn = (uint16_t)((b >> 48) & 0x8000u);
+#pragma unroll
+    for (int i = 0; i < OZ_S; i++) {
+        const unsigned d = (unsigned)(f >> (62 - OZ_BITS * (i + 1))) & 127u;
+        // float(d) exactly, via the 2^23 bias; bf16 = its upper 16 bits
+        const float fd = __uint_as_float(0x4B000000u | d) - 8388608.0f;
+        dg[i] = (uint16_t)(__float_as_uint(fd) >> 16) | (d ? sgn : (uint16_t)0);
+    }
+}
+
+__device__ __forceinline__ double pow2(int e) {
+    // 2^e for |e| <= 2000 as a product of two normal powers of two
+    const int e1 = e / 2, e2 = e - e1;
+    return __longlong_as_double((long long)(e1 + 1023) << 52) *
+           __longlong_as_double((long long)(e2 + 1023) << 52);
+}
+
+// Digit planes of the small matrix [M1; M2] (K x ncol) in the layout the MMA
+// reads: image[((ct * kchunks + ch) * 8 + j) * 8 KB] holds digit j of rows =
+// output columns ct*64 .. +63 and K = ch*64 .. +63; fexp[c] = the column's
+// largest biased exponent.  One thread per output column of a tile.
+__global__ void __launch_bounds__(OZ_NT) k_oz_split(int K, int k1, int ncol, int kchunks,
+                                                    const double *M1, const double *M2,
+                                                    unsigned char *image, int *fexp) {
+    const int ct = blockIdx.x, cl = threadIdx.x, c = ct * OZ_NT + cl;
+    auto val = [&](int k) -> double {
+        if (c >= ncol || k >= K) return 0.0;
+        return k < k1 ? M1[(size_t)k * ncol + c] : M2[(size_t)(k - k1) * ncol + c];
+    };
+    int em = 0;
+    for (int k = 0; k < K; k++) em = max(em, biased_exp(val(k)));
+    if (c < ncol) fexp[c] = em;
+    for (int ch = 0; ch < kchunks; ch++) {
+        unsigned char *base = image + (size_t)(ct * kchunks + ch) * OZ_S * OZ_BPLANE;
+        for (int kl = 0; kl < OZ_KC; kl++) {
+            uint16_t dg[OZ_S];
+            oz_digits(val(ch * OZ_KC + kl), em, dg);
+            const uint32_t off = sw128_offset16(cl, kl);
+#pragma unroll
+            for (int j = 0; j < OZ_S; j++)
+                *reinterpret_cast<uint16_t *>(base + (size_t)j * OZ_BPLANE + off) = dg[j];
+        }
+    }
+}
+
+// largest biased exponent of every point row of [A1 A2] (one warp per row)
+__global__ void __launch_bounds__(256) k_oz_rowexp(long n, int k1, int k2, const double *A1,
+                                                   const double *A2, int *erow) {
+    const int lane = threadIdx.x & 31;
+    const long p = (long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (p >= n) return;
+    int em = 0;
+    for (int k = lane; k < k1; k += 32) em = max(em, biased_exp(A1[(size_t)p * k1 + k]));
+    for (int k = lane; k < k2; k += 32) em = max(em, biased_exp(A2[(size_t)p * k2 + k]));
+    for (int o = 16; o > 0; o >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
+    if (lane == 0) erow[p] = em;
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    k_tall_oz(long n, int k1, int k2, int ncol, int kchunks, const double *__restrict__ A1,
+              const double *__restrict__ A2, const unsigned char *__restrict__ image,
+              const int *__restrict__ fexp, const int *__restrict__ erow_g,
+              const double *__restrict__ Cin, double *__restrict__ Out, double *part_sq,
+              int *status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *planesA = smem;
+    unsigned char *planesB = smem + OZ_S * OZ_APLANE;
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int erow[OZ_M];
+    __shared__ int abort_sh;
+    __shared__ double red[OZ_THREADS];
+    constexpr uint32_t TCOLS = OZ_S * OZ_NT;   // 512
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long r0 = (long)blockIdx.x * OZ_M;
+    const int ct = blockIdx.y;
+    const int K = k1 + k2;
+    if (tid == 0) {
+        mbar_init(&mbar, 1);
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_sh)),
+                     "r"(TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    auto aval = [&](long p, int k) -> double {
+        return k < k1 ? A1[(size_t)p * k1 + k] : A2[(size_t)p * k2 + (k - k1)];
+    };
+    for (int r = tid; r < OZ_M; r += OZ_THREADS) erow[r] = (r0 + r < n) ? erow_g[r0 + r] : 0;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sh;
+    const uint32_t idesc = idesc_bf16(OZ_M, OZ_NT);
+
+    for (int ch = 0; ch < kchunks; ch++) {
+        if (ch > 0 && tid == 0) {
+            if (!mbar_wait(&mbar, (unsigned)((ch - 1) & 1))) abort_sh = 1;
+        }
+        __syncthreads();
+        if (abort_sh) break;
+        // digit planes of the point rows for K = ch*64 .. ch*64+63: a warp owns
+        // 16 rows; all 32 loads of a batch of 16 are issued before converting
+        {
+            constexpr int RPW = OZ_M / (OZ_THREADS / 32);   // rows per warp
+            double xv[RPW][2];
+#pragma unroll
+            for (int q = 0; q < RPW; q++) {
+                const int r = warp * RPW + q;
+                const long p = r0 + r;
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const int kg = ch * OZ_KC + lane + 32 * h;
+                    xv[q][h] = (p < n && kg < K) ? aval(p, kg) : 0.0;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < RPW; q++) {
+                const int r = warp * RPW + q;
+                const int em = erow[r];
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    uint16_t dg[OZ_S];
+                    oz_digits(xv[q][h], em, dg);
+                    const uint32_t off = sw128_offset16(r, lane + 32 * h);
+#pragma unroll
+                    for (int i = 0; i < OZ_S; i++)
+                        *reinterpret_cast<uint16_t *>(planesA + i * OZ_APLANE + off) = dg[i];
+                }
+            }
+        }
+        // digit planes of the small matrix (prepared by k_oz_split)
+        {
+            const uint4 *src = reinterpret_cast<const uint4 *>(
+                image + (size_t)(ct * kchunks + ch) * OZ_S * OZ_BPLANE);
+            uint4 *dst = reinterpret_cast<uint4 *>(planesB);
+            for (int i = tid; i < OZ_S * OZ_BPLANE / 16; i += OZ_THREADS) dst[i] = src[i];
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int ks = 0; ks < OZ_KC / 16; ks++) {
+                const uint32_t ko = ks * 32;
+#pragma unroll
+                for (int t = 2; t <= OZ_S + 1; t++) {
+                    const int ilo = t - OZ_S > 1 ? t - OZ_S : 1;
+                    const int ihi = t - 1 < OZ_S ? t - 1 : OZ_S;
+                    for (int i = ilo; i <= ihi; i++) {
+                        const int j = t - i;
+                        const uint64_t da = make_desc_sw128(smem_u32(planesA + (i - 1) * OZ_APLANE) + ko);
+                        const uint64_t db = make_desc_sw128(smem_u32(planesB + (j - 1) * OZ_BPLANE) + ko);
+                        const uint32_t acc = (ch > 0 || ks > 0 || i > ilo) ? 1u : 0u;
+                        mma_bf16(tmem + (uint32_t)((t - 2) * OZ_NT), da, db, idesc, acc);
+                    }
+                }
+            }
+            mma_commit(&mbar);
+        }
+    }
+    if (!abort_sh && tid == 0) {
+        if (!mbar_wait(&mbar, (unsigned)((kchunks - 1) & 1))) abort_sh = 1;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    double sq = 0.0;
+    if (abort_sh) {
+        if (tid == 0) atomicOr(status, ST_TC_TIMEOUT);
+    } else {
+        // epilogue: thread = one point row (TMEM lane 32 (warp % 4) + lane) and
+        // one half of the 64 output columns (warp / 4)
+        const int r = (warp & 3) * 32 + lane;
+        const long p = r0 + r;
+        const int em = erow[r];
+        {
+            const int cb = (warp >> 2) * 32;
+            // sum_t D_t 2^(-7(t-2)) as a 64-bit fixed-point integer with 40
+            // fraction bits (|D_2| < 2^21: no overflow; the two smallest
+            // scales lose at most 2^-39), so the FP64 pipe sees one
+            // conversion per output instead of a Horner chain
+            long long acc[32];
+#pragma unroll
+            for (int j = 0; j < 32; j++) acc[j] = 0;
+#pragma unroll
+            for (int t = 2; t <= OZ_S + 1; t++) {
+                float v[32];
+                tmem_ld32<32>(tmem + ((uint32_t)((warp & 3) * 32) << 16) +
+                                  (uint32_t)((t - 2) * OZ_NT + cb), v);
+                const int sh = OZ_FRAC - OZ_BITS * (t - 2);
+#pragma unroll
+                for (int j = 0; j < 32; j++) {
+                    const long long d = (long long)__float2int_rn(v[j]);
+                    acc[j] += sh >= 0 ? (d << sh) : (d >> (-sh));
+                }
+            }
+            if (p < n) {
+#pragma unroll
+            for (int j = 0; j < 32; j++) {
+                const int c = ct * OZ_NT + cb + j;
+                if (c >= ncol) continue;
+                const int fc = fexp[c];
+                const int es = (em - 1022) + (fc - 1022) - 2 * OZ_BITS - OZ_FRAC;
+                const double a = (double)acc[j];
+                double o;
+                if (em == OZ_EBAD || fc == OZ_EBAD)
+                    o = __longlong_as_double(0x7FF8000000000000ll);
+                else if (es >= -1022 && es <= 1023)
+                    o = a * __longlong_as_double((long long)(es + 1023) << 52);
+                else
+                    o = a * pow2(es);
+                const size_t e = (size_t)p * ncol + c;
+                if (Cin) o += Cin[e];
+                if (Out) Out[e] = o;
+                if (part_sq) sq = fma(o, o, sq);
+            }
+            }
+        }
+    }
+    if (part_sq) {
+        red[tid] = sq;
+        __syncthreads();
+        for (int k = OZ_THREADS / 2; k > 0; k >>= 1) {
+            if (tid < k) red[tid] += red[tid + k];
+            __syncthreads();
+        }
+        if (tid == 0) part_sq[(size_t)blockIdx.x * gridDim.y + blockIdx.y] = red[0];
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS)
+                     : "memory");
+}
+
+}  // namespace
+
+bool tall_oz_supported(int k1, int k2) { return k1 + k2 >= 1 && k1 + k2 <= 128; }
+
+size_t tall_oz_image_bytes(long n, int K, int ncol) {
+    const int kchunks = (K + OZ_KC - 1) / OZ_KC;
+    const int ctiles = (ncol + OZ_NT - 1) / OZ_NT;
+    return (size_t)ctiles * kchunks * OZ_S * OZ_BPLANE + sizeof(int) * (size_t)(ncol + 64 + n);
+}
+
+int tall_oz_partials(long n, int ncol) {
+    return (int)(((n + OZ_M - 1) / OZ_M) * ((ncol + OZ_NT - 1) / OZ_NT));
+}
+
+void oz_prepare() {
+    static bool done = false;
+    if (done) return;
+    cudaFuncSetAttribute(k_tall_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+    done = true;
+}
+
+void launch_tall_oz(long n, const double *A1, int k1, const double *M1, const double *A2, int k2,
+                    const double *M2, int ncol, const double *Cin, double *Out, double *part_sq,
+                    unsigned char *image, int *status, cudaStream_t s) {
+    if (!A2) k2 = 0;
+    const int K = k1 + k2;
+    const int kchunks = (K + OZ_KC - 1) / OZ_KC;
+    const int ctiles = (ncol + OZ_NT - 1) / OZ_NT;
+    int *fexp = reinterpret_cast<int *>(image + (size_t)ctiles * kchunks * OZ_S * OZ_BPLANE);
+    int *erow = fexp + ncol + 64;
+    HQ_LAUNCH(HQ_K_BLOCKGEMM, k_oz_split<<<ctiles, OZ_NT, 0, s>>>(K, k1, ncol, kchunks, M1,
+                                                                   k2 ? M2 : nullptr, image, fexp));
+    HQ_LAUNCH(HQ_K_BLOCKGEMM, k_oz_rowexp<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(
+                                  n, k1, k2, A1, k2 ? A2 : nullptr, erow));
+    const unsigned gx = (unsigned)((n + OZ_M - 1) / OZ_M);
+    HQ_LAUNCH(HQ_K_BLOCKGEMM,
+              k_tall_oz<<<dim3(gx, ctiles), OZ_THREADS, OZ_SMEM, s>>>(
+                  n, k1, k2, ncol, kchunks, A1, k2 ? A2 : nullptr, image, fexp, erow, Cin, Out,
+                  part_sq, status));
+}
+
+}  // namespace hq

@@ -168,3 +168,35 @@ def test_block_gemm_matches_numpy(prec, m, N, k1, k2, tol):
         ref += A2.astype(np.float64) @ M2
     err = np.abs(out - ref).max() / np.abs(ref).max()
     assert err < tol, err
+
+
+@pytest.mark.parametrize("m,N,k1,k2", [(13, 64, 64, 64), (12, 40, 40, 0), (13, 17, 17, 9)])
+def test_fp64_tensor_core_products_match_fp64(m, N, k1, k2):
+    """FP64 block products on tensor cores (exact integer digit slicing) against
+    numpy FP64 and the FP64 SIMT kernel: rows spanning 1e-9..1e3 in scale, a
+    zero row, ragged point count and column tiles.  The error bound of the
+    slicing is 2^-53 |row max| |column max| per term."""
+    torch = torch_mod()
+    rng = np.random.default_rng(m * N + k1 + k2)
+    n = m ** 3
+    A1 = rng.standard_normal((n, k1)) * np.exp(rng.uniform(-20, 7, (n, 1)))
+    A1[5] = 0.0
+    M1 = rng.standard_normal((k1, N)) * np.exp(rng.uniform(-3, 3, (1, N)))
+    A2 = rng.standard_normal((n, k2)) * np.exp(rng.uniform(-20, 7, (n, 1))) if k2 else None
+    M2 = rng.standard_normal((k2, N)) if k2 else None
+    Cin = rng.standard_normal((n, N))
+    ref = A1 @ M1 + Cin + (A2 @ M2 if k2 else 0.0)
+    outs = []
+    for tc in (1, 0):
+        s, _, _ = make(m, N, fp64_tc=tc)
+        outs.append(host(s.block_gemm(dev(A1), dev(M1), None if A2 is None else dev(A2),
+                                      None if M2 is None else dev(M2), dev(Cin))))
+    rowmax = np.abs(A1).max(axis=1, keepdims=True)
+    colmax = np.abs(M1).max(axis=0, keepdims=True)
+    if k2:
+        rowmax = np.maximum(rowmax, np.abs(A2).max(axis=1, keepdims=True))
+        colmax = np.maximum(colmax, np.abs(M2).max(axis=0, keepdims=True))
+    bound = 4 * 2.0 ** -53 * (k1 + k2) * rowmax * colmax + 4 * 2.0 ** -53 * np.abs(ref)
+    for out in outs:
+        assert np.all(np.abs(out - ref) <= bound)
+    assert np.array_equal(outs[0][5], (Cin + (A2 @ M2 if k2 else 0.0))[5]) or k2
