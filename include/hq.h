@@ -86,11 +86,11 @@ typedef struct {
     int grid_block;      /* threads per CTA of the grid kernels: 0 (= 256), 64, 128, 256 */
     int grid_ctas;       /* target CTAs per SM of the grid kernels: 0 (= 16) .. 64;     */
                          /* both set the launch shape only (hq_tune picks them)      */
-    int fp64_tc;         /* HQ_FP64 only: 1 = the n x N block products (Uh, U_{n+1},   */
-                         /* the gradient residual, the warm start) on tensor cores by */
-                         /* exact integer slicing of the FP64 values (error below    */
-                         /* 2^-53 of |row max| |column max| per term, FP64 results), */
-                         /* for K <= 128 columns; 0 = FP64 SIMT products             */
+    int fp64_tc;         /* HQ_FP64 only: 1 = the Gram of [U W] and the n x N block   */
+                         /* products (Uh, U_{n+1}, the gradient residual, the warm   */
+                         /* start) on tensor cores by exact integer slicing of the   */
+                         /* FP64 values (error below 2^-53 |row max| |column max|    */
+                         /* per term, FP64 results; for 2N <= 128); 0 = FP64 SIMT   */
 } hq_config;
 
 /* Defaults: box [-6,6]^3, tau 0.4, automatic shift, FP64, cg_rtol 1e-10,

@@ -111,6 +111,7 @@ struct hq_ctx {
     int *ipiv = nullptr;   // pivots of the small eliminations (2N)
     float *lu32 = nullptr;  // FP32 factors of the small systems (mixed precision)
     unsigned char *ozimg = nullptr;   // FP64 tensor-core block products: digit planes
+    double *ozgram = nullptr;         // FP64 tensor-core Gram: chunk partials, exponents
     double *pB = nullptr, *pR = nullptr;   // predictor right-hand side / residual
     double *vn[3] = {nullptr, nullptr, nullptr};   // FP64 n-vectors (density, adjoint)
     double *pvec = nullptr;                        // power-iteration vector (N)
@@ -374,6 +375,9 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
     unsigned char *ozimg = (!mixed && c->fp64_tc && tall_oz_supported(2 * N, 0))
                                ? cv.take<unsigned char>(tall_oz_image_bytes(n, 2 * N, N))
                                : nullptr;
+    double *ozgram = (!mixed && c->fp64_tc && gram_oz_supported(2 * N))
+                         ? cv.take<double>(gram_oz_scratch_bytes(n, 2 * N))
+                         : nullptr;
     double *pB = mixed ? cv.take<double>(sizeof(double) * 2 * N2) : nullptr;
     double *pR = mixed ? cv.take<double>(sizeof(double) * 2 * N2) : nullptr;
     double *Cc = cv.take<double>(sizeof(double) * 2 * N2);
@@ -418,6 +422,7 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
         x->ipiv = ipiv;
         x->lu32 = lu32;
         x->ozimg = ozimg;
+        x->ozgram = ozgram;
         x->pB = pB;
         x->pR = pR;
         x->G2 = G2; x->Mw = Mw; x->XY = XY; x->C = Cc; x->T1 = T1; x->Shat = Shat; x->Om = Om;
@@ -709,6 +714,10 @@ template <typename T>
 void gram_sym(hq_ctx *x, const T *X1, int n1, const T *X2, int n2, double *out);
 template <>
 void gram_sym<double>(hq_ctx *x, const double *X1, int n1, const double *X2, int n2, double *out) {
+    if (x->ozgram && gram_oz_supported(n1 + n2)) {
+        launch_gram_oz(x->n, X1, n1, X2, n2, x->h3, x->ozgram, out, x->status, x->st);
+        return;
+    }
     GramPlan gp = make_gram_plan(x->n, n1 + n2, n1 + n2, true);
     launch_gram<double>(gp, X1, n1, X2, n2, X1, n1, X2, n2, x->h3, x->gpart, out, x->st);
 }
@@ -1956,7 +1965,7 @@ hq_status hq_init(const hq_config *cfg, void *d_workspace, size_t bytes, void *c
     if (x->mixed) hq::tc_prepare();
     hq::lu_prepare();
     if (x->mixed) hq::lu32_prepare();
-    if (x->ozimg) hq::oz_prepare();
+    if (x->ozimg || x->ozgram) hq::oz_prepare();
     if (e != cudaSuccess) {
         delete x;
         return HQ_ERR_CUDA;

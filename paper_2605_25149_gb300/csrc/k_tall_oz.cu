@@ -321,6 +321,192 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                      : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// FP64 Gram <X, X> = w X^T X of X = [X1 X2] (n x na, na <= 128) by the same
+// digit slicing, with per-column exponents over all points (k_oz_colexp).
+// CTA = all na rows x 64 output columns over a chunk of points; the digit
+// planes of a 64-point slice serve as both operands (the B operand is rows
+// ct*64.. of the A planes).  The exact-sum bound holds for 128 points, so
+// every two slices the eight accumulators are read and added into 64-bit
+// fixed-point registers (OZ_GFRAC fraction bits); the chunk's FP64 partial
+// tile is summed over chunks in a fixed order by k_oz_gram_reduce.  D_t(i,j)
+// and D_t(j,i) are the same integers, so the result is exactly symmetric.
+// ---------------------------------------------------------------------------
+constexpr int OZ_GFRAC = 32;
+constexpr int OZ_GSMEM = OZ_S * OZ_APLANE + 1024;
+
+__global__ void __launch_bounds__(128) k_oz_colexp(long n, int n1, int n2, const double *X1,
+                                                   const double *X2, int *colexp) {
+    const int c = threadIdx.x, na = n1 + n2;
+    if (c >= na) return;
+    int em = 0;
+    for (long p = blockIdx.x; p < n; p += gridDim.x)
+        em = max(em, biased_exp(c < n1 ? X1[(size_t)p * n1 + c] : X2[(size_t)p * n2 + (c - n1)]));
+    atomicMax(&colexp[c], em);
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    k_gram_oz(long n, int n1, int n2, long chunk_rows, const double *__restrict__ X1,
+              const double *__restrict__ X2, const int *__restrict__ colexp,
+              double *__restrict__ partials, int *status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *planes = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int cexp[OZ_M];
+    __shared__ int abort_sh;
+    constexpr uint32_t TCOLS = OZ_S * OZ_NT;   // 512
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int na = n1 + n2, ct = blockIdx.x;
+    const long p0 = (long)blockIdx.y * chunk_rows;
+    const long p1 = (n < p0 + chunk_rows) ? n : p0 + chunk_rows;
+    const int nslices = p1 > p0 ? (int)((p1 - p0 + OZ_KC - 1) / OZ_KC) : 0;
+    if (tid == 0) {
+        mbar_init(&mbar, 1);
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int c = tid; c < OZ_M; c += OZ_THREADS) cexp[c] = c < na ? colexp[c] : 0;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_sh)),
+                     "r"(TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sh;
+    const uint32_t idesc = idesc_bf16(OZ_M, OZ_NT);
+    // slice loads: thread t takes column c = t & 127 of points 2 j + (t >> 7)
+    const int lc = tid & (OZ_M - 1), lh = tid >> 7;
+    double xv[OZ_KC / 2];
+    auto load_slice = [&](int sl) {
+#pragma unroll
+        for (int j = 0; j < OZ_KC / 2; j++) {
+            const long p = p0 + (long)sl * OZ_KC + 2 * j + lh;
+            xv[j] = (p < p1 && lc < na)
+                        ? (lc < n1 ? X1[(size_t)p * n1 + lc] : X2[(size_t)p * n2 + (lc - n1)])
+                        : 0.0;
+        }
+    };
+    // fixed-point sums: thread = TMEM lane 32 (warp % 4) + lane (Gram row),
+    // 32 output columns (warp / 4)
+    const int grow = (warp & 3) * 32 + lane, gcb = (warp >> 2) * 32;
+    long long facc[32];
+#pragma unroll
+    for (int j = 0; j < 32; j++) facc[j] = 0;
+    auto flush = [&]() {
+#pragma unroll
+        for (int t = 2; t <= OZ_S + 1; t++) {
+            float v[32];
+            tmem_ld32<32>(tmem + ((uint32_t)((warp & 3) * 32) << 16) +
+                              (uint32_t)((t - 2) * OZ_NT + gcb), v);
+            const int sh = OZ_GFRAC - OZ_BITS * (t - 2);
+#pragma unroll
+            for (int j = 0; j < 32; j++) {
+                const long long d = (long long)__float2int_rn(v[j]);
+                facc[j] += sh >= 0 ? (d << sh) : (d >> (-sh));
+            }
+        }
+    };
+    if (nslices > 0) load_slice(0);
+    for (int sl = 0; sl < nslices; sl++) {
+        if (sl > 0 && tid == 0) {
+            if (!mbar_wait(&mbar, (unsigned)((sl - 1) & 1))) abort_sh = 1;
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (abort_sh) break;
+        if (sl > 0 && (sl & 1) == 0) flush();   // 128 points accumulated
+        {
+            const int em = cexp[lc];
+#pragma unroll
+            for (int j = 0; j < OZ_KC / 2; j++) {
+                uint16_t dg[OZ_S];
+                oz_digits(xv[j], em, dg);
+                const uint32_t off = sw128_offset16(lc, 2 * j + lh);
+#pragma unroll
+                for (int i = 0; i < OZ_S; i++)
+                    *reinterpret_cast<uint16_t *>(planes + i * OZ_APLANE + off) = dg[i];
+            }
+        }
+        if (sl + 1 < nslices) load_slice(sl + 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const bool fresh = (sl & 1) == 0;
+#pragma unroll
+            for (int ks = 0; ks < OZ_KC / 16; ks++) {
+                const uint32_t ko = ks * 32;
+#pragma unroll
+                for (int t = 2; t <= OZ_S + 1; t++) {
+                    const int ilo = t - OZ_S > 1 ? t - OZ_S : 1;
+                    const int ihi = t - 1 < OZ_S ? t - 1 : OZ_S;
+                    for (int i = ilo; i <= ihi; i++) {
+                        const int j = t - i;
+                        const uint64_t da = make_desc_sw128(smem_u32(planes + (i - 1) * OZ_APLANE) + ko);
+                        const uint64_t db = make_desc_sw128(
+                            smem_u32(planes + (j - 1) * OZ_APLANE + ct * OZ_NT * 128) + ko);
+                        const uint32_t acc = (!fresh || ks > 0 || i > ilo) ? 1u : 0u;
+                        mma_bf16(tmem + (uint32_t)((t - 2) * OZ_NT), da, db, idesc, acc);
+                    }
+                }
+            }
+            mma_commit(&mbar);
+        }
+    }
+    if (!abort_sh && nslices > 0 && tid == 0) {
+        if (!mbar_wait(&mbar, (unsigned)((nslices - 1) & 1))) abort_sh = 1;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (abort_sh) {
+        if (tid == 0) atomicOr(status, ST_TC_TIMEOUT);
+    } else {
+        if (nslices > 0) flush();
+        double *dst = partials + ((size_t)blockIdx.y * gridDim.x + ct) * OZ_M * OZ_NT;
+        const int ea = cexp[grow];
+#pragma unroll
+        for (int j = 0; j < 32; j++) {
+            const int gc = ct * OZ_NT + gcb + j;
+            double o = 0.0;
+            if (grow < na && gc < na) {
+                const int eb = cexp[gc];
+                const int es = (ea - 1022) + (eb - 1022) - 2 * OZ_BITS - OZ_GFRAC;
+                if (ea == OZ_EBAD || eb == OZ_EBAD) o = __longlong_as_double(0x7FF8000000000000ll);
+                else if (es >= -1022 && es <= 1023)
+                    o = (double)facc[j] * __longlong_as_double((long long)(es + 1023) << 52);
+                else
+                    o = (double)facc[j] * pow2(es);
+            }
+            dst[(size_t)grow * OZ_NT + gcb + j] = o;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS)
+                     : "memory");
+}
+
+// out[i][j] = w * sum over chunks (in order) of the chunk partials
+__global__ void k_oz_gram_reduce(int na, int ctiles, int chunks, const double *partials, double w,
+                                 double *out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= na * na) return;
+    const int i = e / na, j = e % na, ct = j / OZ_NT, jl = j % OZ_NT;
+    double s = 0.0;
+    for (int c = 0; c < chunks; c++)
+        s += partials[(((size_t)c * ctiles + ct) * OZ_M + i) * OZ_NT + jl];
+    out[e] = w * s;
+}
+
 }  // namespace
 
 bool tall_oz_supported(int k1, int k2) { return k1 + k2 >= 1 && k1 + k2 <= 128; }
@@ -339,7 +525,51 @@ void oz_prepare() {
     static bool done = false;
     if (done) return;
     cudaFuncSetAttribute(k_tall_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+    cudaFuncSetAttribute(k_gram_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_GSMEM);
     done = true;
+}
+
+bool gram_oz_supported(int na) { return na >= 1 && na <= OZ_M; }
+
+namespace {
+struct OzGramPlan {
+    int ctiles, chunks;
+    long chunk_rows;
+};
+OzGramPlan make_oz_gram_plan(long n, int na) {
+    OzGramPlan g;
+    g.ctiles = (na + OZ_NT - 1) / OZ_NT;
+    // at most 16384 points per chunk: the 64-bit fixed-point sums then stay
+    // below 2^60 (2^53 per 128-point flush)
+    long chunks = std::max((long)(2 * 152) / g.ctiles, (n + 16383) / 16384);
+    chunks = std::max(1L, std::min(chunks, (n + OZ_KC - 1) / OZ_KC));
+    long rows = (n + chunks - 1) / chunks;
+    rows = (rows + OZ_KC - 1) / OZ_KC * OZ_KC;
+    g.chunk_rows = rows;
+    g.chunks = (int)((n + rows - 1) / rows);
+    return g;
+}
+}  // namespace
+
+size_t gram_oz_scratch_bytes(long n, int na) {
+    OzGramPlan g = make_oz_gram_plan(n, na);
+    return sizeof(double) * (size_t)g.chunks * g.ctiles * OZ_M * OZ_NT + sizeof(int) * OZ_M;
+}
+
+void launch_gram_oz(long n, const double *X1, int n1, const double *X2, int n2, double w,
+                    double *scratch, double *out, int *status, cudaStream_t s) {
+    if (!X2) n2 = 0;
+    const int na = n1 + n2;
+    OzGramPlan g = make_oz_gram_plan(n, na);
+    double *partials = scratch;
+    int *colexp = reinterpret_cast<int *>(scratch + (size_t)g.chunks * g.ctiles * OZ_M * OZ_NT);
+    cudaMemsetAsync(colexp, 0, sizeof(int) * OZ_M, s);
+    HQ_LAUNCH(HQ_K_GRAM, k_oz_colexp<<<1024, 128, 0, s>>>(n, n1, n2, X1, n2 ? X2 : nullptr, colexp));
+    HQ_LAUNCH(HQ_K_GRAM, k_gram_oz<<<dim3(g.ctiles, g.chunks), OZ_THREADS, OZ_GSMEM, s>>>(
+                             n, n1, n2, g.chunk_rows, X1, n2 ? X2 : nullptr, colexp, partials,
+                             status));
+    HQ_LAUNCH(HQ_K_GRAM, k_oz_gram_reduce<<<(na * na + 255) / 256, 256, 0, s>>>(
+                             na, g.ctiles, g.chunks, partials, w, out));
 }
 
 void launch_tall_oz(long n, const double *A1, int k1, const double *M1, const double *A2, int k2,

@@ -200,3 +200,22 @@ def test_fp64_tensor_core_products_match_fp64(m, N, k1, k2):
     for out in outs:
         assert np.all(np.abs(out - ref) <= bound)
     assert np.array_equal(outs[0][5], (Cin + (A2 @ M2 if k2 else 0.0))[5]) or k2
+
+
+@pytest.mark.parametrize("m,N", [(16, 64), (13, 9)])
+def test_fp64_tensor_core_gram_matches_simt(m, N):
+    """The Gram of [U W] of one step by digit slicing on tensor cores
+    (fp64_tc = 1) against the FP64 SIMT Gram (fp64_tc = 0) on the same state:
+    exactly symmetric, and equal to within 2^-50 |col max_i| |col max_j| n h^3."""
+    torch_mod()
+    grams, Ws = [], []
+    for tc in (1, 0):
+        s, V, U0 = make(m, N, fp64_tc=tc, cg_rtol=1e-12)
+        tr = s.step_trace()
+        grams.append(host(tr["gram"]))
+        Ws.append(host(tr["W"]))
+    g_tc, g_ref = grams
+    assert np.array_equal(g_tc, g_tc.T)
+    scale = np.sqrt(np.abs(np.diag(g_ref)))
+    bound = 2.0 ** -44 * np.outer(scale, scale) * (m ** 3)
+    assert np.all(np.abs(g_tc - g_ref) <= bound + 1e-14 * np.abs(g_ref).max())
