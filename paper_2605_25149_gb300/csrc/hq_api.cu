@@ -301,6 +301,14 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
         v.h = (c->hi - c->lo) / (ms[l] + 1);
         v.c = 0.5 / (v.h * v.h);
         v.g = make_geom(ms[l], N, (int)esz, c->grid_block, c->grid_ctas);
+        // finest-level blocks of 100 MB or more: z-marching smoothing sweeps
+        // (HQ_ZMARCH=0 keeps the linear point order, HQ_ZMARCH=1 forces the
+        // z-marching order at any size; both for comparisons)
+        if (l == 0 && L > 1) {
+            const char *zm = std::getenv("HQ_ZMARCH");
+            const bool force = zm && zm[0] == '1', off = zm && zm[0] == '0';
+            if (!off && (force || (double)v.n * N * esz >= 100e6)) enable_zmarch(v.g);
+        }
         v.V = cv.take<double>(sizeof(double) * v.n);
         v.D = cv.take<double>(sizeof(double) * v.n);
         v.wD = cv.take<double>(sizeof(double) * v.n);

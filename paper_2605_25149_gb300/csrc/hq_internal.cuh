@@ -33,7 +33,11 @@ struct GridGeom {
     int tx, ty;     // block shape: tx column-vectors x ty points
     int gx, gy;     // grid shape
     int ppt;        // points per thread (consecutive slabs of ty points)
+    int zch;        // > 0: smoothing sweeps without partial sums march in z
+                    // (zch chunks of planes per x-segment / y-row), see k_jacobi_zm
 };
+// switches the smoother of a level to z-marching CTAs (blocks larger than L2)
+void enable_zmarch(GridGeom &g);
 // block: threads per CTA (0: 256); ctas_per_sm: target CTAs per SM of the
 // grid (0: 16) -- the two launch-shape parameters the autotuner searches
 GridGeom make_geom(int m, int N, int elem_bytes, int block = 0, int ctas_per_sm = 0);

@@ -46,7 +46,15 @@ GridGeom make_geom(int m, int N, int elem_bytes, int block, int ctas_per_sm) {
     long ppt = (g.n + (long)g.ty * target_gy - 1) / ((long)g.ty * target_gy);
     g.ppt = (int)std::max(1L, ppt);
     g.gy = (int)((g.n + (long)g.ty * g.ppt - 1) / ((long)g.ty * g.ppt));
+    g.zch = 0;
     return g;
+}
+
+void enable_zmarch(GridGeom &g) {
+    const long per_chunk = (long)g.gx * ((g.m + g.ty - 1) / g.ty) * g.m;   // CTAs per z-chunk
+    long zch = (152L * 8 + per_chunk - 1) / per_chunk;
+    zch = std::max(1L, std::min(zch, (long)std::max(1, g.m / 8)));
+    g.zch = (int)zch;
 }
 
 // Per-column partial sums: each thread holds acc[V] for its columns; reduce
@@ -262,6 +270,104 @@ __global__ void __launch_bounds__(256) k_jacobi(int m, long n, int N, int ppt,
         stv<T, V>(zout + e, o);
     }
     if (part) block_col_reduce<V, T>(acc, red, part, N, col, cv);
+}
+
+// The same sweep with z-marching CTAs for blocks larger than L2: a CTA owns
+// TY consecutive x-points of one y-row and walks a range of z-planes, keeping
+// the z-1, z, z+1 values of its points in registers, so the z-neighbours are
+// read once from memory instead of being re-read from other CTAs' rows.  The
+// six-neighbour sum is formed in the same order with the same zero masks as
+// nbr_sum, so results are bit-identical to k_jacobi.  No partial sums (the
+// sweep that also forms r.z uses k_jacobi).
+template <typename T, int V>
+__global__ void __launch_bounds__(256) k_jacobi_zm(int m, int N, int nseg, int mz,
+                                                   const T *__restrict__ wD, T c, T omw,
+                                                   const T *__restrict__ r,
+                                                   const T *__restrict__ zin,
+                                                   T *__restrict__ zout) {
+    const int TY = blockDim.y;
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    if (col >= N) return;
+    const int b = blockIdx.y;
+    const int seg = b % nseg, rest = b / nseg;
+    const int j = rest % m, zc = rest / m;
+    const int i = seg * TY + threadIdx.y;
+    if (i >= m) return;
+    const int k0 = zc * mz, k1 = min(m, k0 + mz);
+    if (k0 >= k1) return;
+    const size_t sx = (size_t)N, sy = (size_t)m * N, sz = (size_t)m * m * N;
+    long p = i + (long)m * (j + (long)m * k0);
+    size_t e = (size_t)p * N + col;
+    const bool bw = i > 0, be = i < m - 1, bs = j > 0, bn = j < m - 1;
+    VT<T, V> zero;
+#pragma unroll
+    for (int v = 0; v < V; v++) zero.v[v] = T(0);
+    VT<T, V> zcur = ldv<T, V>(zin + e);
+    VT<T, V> zprev = k0 > 0 ? ldv<T, V>(zin + e - sz) : zero;
+    for (int kk = k0; kk < k1; kk++, e += sz, p += (long)m * m) {
+        VT<T, V> znext = kk + 1 < m ? ldv<T, V>(zin + e + sz) : zero;
+        VT<T, V> a0 = ldv<T, V>(zin + (bw ? e - sx : e)), a1 = ldv<T, V>(zin + (be ? e + sx : e));
+        VT<T, V> a2 = ldv<T, V>(zin + (bs ? e - sy : e)), a3 = ldv<T, V>(zin + (bn ? e + sy : e));
+        VT<T, V> rv = ldv<T, V>(r + e);
+        const T w = wD[p];
+        VT<T, V> o;
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            const T sum = (((bw ? a0.v[v] : T(0)) + (be ? a1.v[v] : T(0))) +
+                           ((bs ? a2.v[v] : T(0)) + (bn ? a3.v[v] : T(0)))) +
+                          (zprev.v[v] + znext.v[v]);
+            o.v[v] = omw * zcur.v[v] + w * (rv.v[v] + c * sum);
+        }
+        stv<T, V>(zout + e, o);
+        zprev = zcur;
+        zcur = znext;
+    }
+}
+
+// Residual y = b - A x with the z-marching CTAs of k_jacobi_zm (no partial
+// sums); the neighbour sum and the expression are those of k_stencil<T,V,1>.
+template <typename T, int V>
+__global__ void __launch_bounds__(256) k_resid_zm(int m, int N, int nseg, int mz,
+                                                  const T *__restrict__ D, T c,
+                                                  const T *__restrict__ x,
+                                                  const T *__restrict__ b, T *__restrict__ y) {
+    const int TY = blockDim.y;
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    if (col >= N) return;
+    const int bl = blockIdx.y;
+    const int seg = bl % nseg, rest = bl / nseg;
+    const int j = rest % m, zc = rest / m;
+    const int i = seg * TY + threadIdx.y;
+    if (i >= m) return;
+    const int k0 = zc * mz, k1 = min(m, k0 + mz);
+    if (k0 >= k1) return;
+    const size_t sx = (size_t)N, sy = (size_t)m * N, sz = (size_t)m * m * N;
+    long p = i + (long)m * (j + (long)m * k0);
+    size_t e = (size_t)p * N + col;
+    const bool bw = i > 0, be = i < m - 1, bs = j > 0, bn = j < m - 1;
+    VT<T, V> zero;
+#pragma unroll
+    for (int v = 0; v < V; v++) zero.v[v] = T(0);
+    VT<T, V> xcur = ldv<T, V>(x + e);
+    VT<T, V> xprev = k0 > 0 ? ldv<T, V>(x + e - sz) : zero;
+    for (int kk = k0; kk < k1; kk++, e += sz, p += (long)m * m) {
+        VT<T, V> xnext = kk + 1 < m ? ldv<T, V>(x + e + sz) : zero;
+        VT<T, V> a0 = ldv<T, V>(x + (bw ? e - sx : e)), a1 = ldv<T, V>(x + (be ? e + sx : e));
+        VT<T, V> a2 = ldv<T, V>(x + (bs ? e - sy : e)), a3 = ldv<T, V>(x + (bn ? e + sy : e));
+        VT<T, V> bb = ldv<T, V>(b + e);
+        const T d = D[p];
+        VT<T, V> o;
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            const T sum = (((bw ? a0.v[v] : T(0)) + (be ? a1.v[v] : T(0))) +
+                           ((bs ? a2.v[v] : T(0)) + (bn ? a3.v[v] : T(0)))) +
+                          (xprev.v[v] + xnext.v[v]);
+            o.v[v] = bb.v[v] - (d * xcur.v[v] - c * sum);
+        }
+        stv<T, V>(y + e, o);
+        xprev = xcur;
+        xcur = xnext;
+    }
 }
 
 template <typename T, int V>
@@ -846,9 +952,22 @@ static void run_resid(const GridGeom &g, const T *D, T c, const T *x, const T *b
                       double *p1, double *p2, cudaStream_t s) {
     HQ_LAUNCH_W(HQ_K_RESIDUAL, (double)g.n * g.N, k_stencil<T, V, 1><<<grd(g), blk(g), 0, s>>>(g.m, g.n, g.N, g.ppt, D, c, x, b, y, p1, p2));
 }
+template <typename T, int V>
+static void run_resid_zm(const GridGeom &g, const T *D, T c, const T *x, const T *b, T *y,
+                         cudaStream_t s) {
+    const int nseg = (g.m + g.ty - 1) / g.ty;
+    const int mz = (g.m + g.zch - 1) / g.zch;
+    const dim3 grid(g.gx, (unsigned)(nseg * g.m * g.zch));
+    HQ_LAUNCH_W(HQ_K_RESIDUAL, (double)g.n * g.N,
+                k_resid_zm<T, V><<<grid, blk(g), 0, s>>>(g.m, g.N, nseg, mz, D, c, x, b, y));
+}
 template <typename T>
 void launch_resid(const GridGeom &g, const T *D, T c, const T *x, const T *b, T *y,
                   double *part_yy, double *part_bb, cudaStream_t s) {
+    if (g.zch > 0 && !part_yy && !part_bb) {
+        HQ_VEC_DISPATCH(T, g, run_resid_zm, g, D, c, x, b, y, s);
+        return;
+    }
     HQ_VEC_DISPATCH(T, g, run_resid, g, D, c, x, b, y, part_yy, part_bb, s);
 }
 
@@ -879,10 +998,24 @@ static void run_jacobi(const GridGeom &g, const T *wD, T c, T omw, const T *r, c
     HQ_LAUNCH_W(HQ_K_SMOOTH, (double)g.n * g.N, k_jacobi<T, V><<<grd(g), blk(g), 0, s>>>(g.m, g.n, g.N, g.ppt, wD, c, omw, r, zin, zout,
                                              part));
 }
+template <typename T, int V>
+static void run_jacobi_zm(const GridGeom &g, const T *wD, T c, T omw, const T *r, const T *zin,
+                          T *zout, cudaStream_t s) {
+    const int nseg = (g.m + g.ty - 1) / g.ty;
+    const int mz = (g.m + g.zch - 1) / g.zch;
+    const dim3 grid(g.gx, (unsigned)(nseg * g.m * g.zch));
+    HQ_LAUNCH_W(HQ_K_SMOOTH, (double)g.n * g.N,
+                k_jacobi_zm<T, V><<<grid, blk(g), 0, s>>>(g.m, g.N, nseg, mz, wD, c, omw, r, zin,
+                                                          zout));
+}
 template <typename T>
 void launch_jacobi(const GridGeom &g, const T *D, const T *wD, T c, T omw, const T *r,
                    const T *zin, T *zout, double *part_rz, cudaStream_t s) {
     (void)D;
+    if (g.zch > 0 && !part_rz) {
+        HQ_VEC_DISPATCH(T, g, run_jacobi_zm, g, wD, c, omw, r, zin, zout, s);
+        return;
+    }
     HQ_VEC_DISPATCH(T, g, run_jacobi, g, wD, c, omw, r, zin, zout, part_rz, s);
 }
 

@@ -97,3 +97,26 @@ def test_graphs_follow_a_new_potential():
         s.step(4)
     assert a.info()["sigma"] == b.info()["sigma"] > 0.0
     assert np.array_equal(a.get_state()[0], b.get_state()[0])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_zmarch_smoother_is_bit_identical(precision):
+    """The z-marching smoothing sweeps (used for blocks beyond half of L2)
+    form the same sums in the same order as the linear-order kernel:
+    trajectories with HQ_ZMARCH=1 (forced) and HQ_ZMARCH=0 are identical."""
+    import os
+    out = []
+    for flag in ("1", "0"):
+        old = os.environ.get("HQ_ZMARCH")
+        os.environ["HQ_ZMARCH"] = flag
+        try:
+            s, _, _ = make(20, 12, precision=precision, tau=0.4,
+                           cg_rtol=1e-10 if precision == "fp64" else 1e-6)
+        finally:
+            if old is None:
+                os.environ.pop("HQ_ZMARCH", None)
+            else:
+                os.environ["HQ_ZMARCH"] = old
+        s.step(3)
+        out.append(s.get_state()[0])
+    assert np.array_equal(out[0], out[1])
