@@ -57,9 +57,9 @@ TRAFFIC_PER_ELEMENT = {("smooth", "f64"): (288.253952e6 + 111.722752e6) / 167772
 # FP64, and steps / seconds to a Rayleigh-Ritz eigenvalue error <= 1e-6
 # (against the FP64 result) in FP64 and in mixed precision.  The default run
 # reports them as "recorded" beside a projection from its own ms/step.
-TTR_STEPS = {"wells64_N64": {"command": "python bench.py --ttr", "steps": 15113, "s": 466.7,
-                             "fp64_err1e-6_steps": 6250, "fp64_err1e-6_s": 214.6,
-                             "mixed_err1e-6_steps": 6250, "mixed_err1e-6_s": 49.4}}
+TTR_STEPS = {"wells64_N64": {"command": "python bench.py --ttr", "steps": 15113, "s": 295.8,
+                             "fp64_err1e-6_steps": 6250, "fp64_err1e-6_s": 143.8,
+                             "mixed_err1e-6_steps": 6250, "mixed_err1e-6_s": 25.8}}
 
 
 def peaks():
