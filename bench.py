@@ -368,6 +368,26 @@ def run_ttr(args):
     sm.set_initial(U0)
     hmx = solve_history(torch, sm, 1e-300, chunk, args.ttr_steps, lam_ref=lam_ref, stop_err=1e-7,
                         stall=8)
+    # FP64 PCG with the FP32 preconditioner, to g < 1e-8, and the same after
+    # the mixed leg (state handed over through host memory)
+    s3 = hq.Solver(m, N, tau=w["tau"], cg_rtol=w["cg_rtol"], precision="fp64", adaptive_tau=1,
+                   tau_max=args.tau_max, mg_fp32=1)
+    s3.set_potential(V)
+    s3.set_initial(U0)
+    h32 = solve_history(torch, s3, w["eps"], chunk, args.ttr_steps, lam_ref=lam_ref)
+    del s3
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Um, Zm, stpm = sm.get_state(with_warm_start=True)
+    s4 = hq.Solver(m, N, tau=w["tau"], cg_rtol=w["cg_rtol"], precision="fp64", adaptive_tau=1,
+                   tau_max=args.tau_max, mg_fp32=1)
+    s4.set_potential(V)
+    s4.set_state(Um, stpm, Zm)
+    torch.cuda.synchronize()
+    t_hand4 = time.perf_counter() - t0
+    h4 = solve_history(torch, s4, w["eps"], chunk, args.ttr_steps, lam_ref=lam_ref)
+    del s4
+    torch.cuda.empty_cache()
     hpol, t_hand = None, None
     if args.ttr_pipeline:
         # hand over to FP64 (state through host memory), then to g < 1e-8
@@ -398,8 +418,16 @@ def run_ttr(args):
                "time_to_residual_s": hmx[-1]["s"] + t_hand + hpol[-1]["s"],
                "mixed_s": hmx[-1]["s"], "handover_s": t_hand, "fp64_s": hpol[-1]["s"],
                "fp64_steps": hpol[-1]["steps"], "g": hpol[-1]["g"]},
+           "fp64_mg32": {"time_to_residual_s": h32[-1]["s"], "steps": h32[-1]["steps"],
+                         "g": h32[-1]["g"], "err": h32[-1]["err"]},
+           "mixed_then_fp64_mg32": {
+               "time_to_residual_s": hmx[-1]["s"] + t_hand4 + h4[-1]["s"],
+               "mixed_s": hmx[-1]["s"], "mixed_steps": hmx[-1]["steps"], "handover_s": t_hand4,
+               "fp64_mg32_s": h4[-1]["s"], "fp64_mg32_steps": h4[-1]["steps"], "g": h4[-1]["g"],
+               "err": h4[-1]["err"]},
            "history": {"fp64": pick(h64), "mixed": pick(hmx),
-                       "fp64_after_mixed": hpol and pick(hpol)}}
+                       "fp64_after_mixed": hpol and pick(hpol), "fp64_mg32": pick(h32),
+                       "fp64_mg32_after_mixed": pick(h4)}}
     print(json.dumps(out), flush=True)
 
 
@@ -613,6 +641,26 @@ def run_hq(args):
     del s
     torch.cuda.empty_cache()
 
+    # ---- FP64 PCG with an FP32 multigrid preconditioner (mg_fp32) --------------
+    mg32 = None
+    if not args.no_mixed:
+        s3 = hq.Solver(m, N, tau=w["tau"], cg_rtol=w["cg_rtol"], precision="fp64", mg_fp32=1)
+        s3.set_potential(V)
+        s3.set_initial(U0)
+        for _ in range(W):
+            s3.step(1)
+        s3.profile(timing=False)
+        ms3, _ = time_steps(torch, s3, K, ws)
+        ms3 = max_over_ranks(ws, ms3)
+        sol3, it3 = s3.pcg_stats()
+        mg32 = {"value": job_value(ws, ms3), "unit": "steps/s", "ms_per_step": ms3,
+                "speedup_vs_fp64": ms / ms3, "pcg_iterations_per_solve": it3 / max(sol3, 1),
+                "dtype": "f64 PCG (residuals, updates, stopping test, step algebra); "
+                         "f32 multigrid V-cycle inside the preconditioner",
+                "note": "W = G U solved to the same FP64 rtol 1e-10; not the headline"}
+        del s3
+        torch.cuda.empty_cache()
+
     # ---- mixed-precision path on the same workload -----------------------------
     mixed = None
     if not args.no_mixed:
@@ -688,6 +736,7 @@ def run_hq(args):
                 "how": "hq_set_state from pinned host (U and warm start), hq_step, "
                        "hq_get_state to pinned host, every step"},
         "mixed": mixed,
+        "fp64_fp32_preconditioner": mg32,
         "large": large,
         "batched": batched,
         "cpu_baseline": cpu,

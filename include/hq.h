@@ -91,6 +91,11 @@ typedef struct {
                          /* start) on tensor cores by exact integer slicing of the   */
                          /* FP64 values (error below 2^-53 |row max| |column max|    */
                          /* per term, FP64 results; for 2N <= 128); 0 = FP64 SIMT   */
+    int mg_fp32;         /* HQ_FP64 only: 1 = the multigrid preconditioner of the     */
+                         /* FP64 block PCG runs in FP32 (r rounded to FP32, z widened */
+                         /* back, r.z in FP64); the PCG residuals, updates, stopping  */
+                         /* test and every other step stay FP64, so W = G U is still  */
+                         /* solved to cg_rtol in FP64.  0 (default) = FP64 V-cycle   */
 } hq_config;
 
 /* Defaults: box [-6,6]^3, tau 0.4, automatic shift, FP64, cg_rtol 1e-10,

@@ -23,6 +23,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/hq.h"
@@ -89,6 +90,13 @@ struct hq_ctx {
     long nc = 0;
     double *Acoarse = nullptr, *Ainv = nullptr;
     void *xt1 = nullptr, *xt2 = nullptr;   // transfer-pass scratch
+    // the V-cycle's view of the levels: lev itself, or (mg32: an FP64 context
+    // with an FP32 preconditioner) FP32 copies of D, omega/D, level buffers,
+    // geometries and transfer scratch
+    Level mg[MAXLEV];
+    void *mxt1 = nullptr, *mxt2 = nullptr;
+    bool mg32 = false;
+    float *R32 = nullptr, *Z32 = nullptr, *T32 = nullptr;
     // n x N blocks in the working precision
     void *U = nullptr, *W = nullptr, *Uh = nullptr, *Z = nullptr;
     void *R = nullptr, *Zp = nullptr, *P = nullptr, *Q = nullptr, *Tt = nullptr;
@@ -258,6 +266,7 @@ bool valid_config(const hq_config *c, std::string *why) {
         return fail("grid_block must be 0, 64, 128 or 256");
     if (c->grid_ctas < 0 || c->grid_ctas > 64) return fail("grid_ctas must be in [0, 64]");
     if (c->fp64_tc != 0 && c->fp64_tc != 1) return fail("fp64_tc must be 0 or 1");
+    if (c->mg_fp32 != 0 && c->mg_fp32 != 1) return fail("mg_fp32 must be 0 or 1");
     return true;
 }
 
@@ -344,6 +353,35 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
     const size_t xs2 = (L > 1) ? (size_t)ms[0] * ms[1] * ms[1] : 1;
     void *xt1 = cv.take<char>(xs * N * esz);
     void *xt2 = cv.take<char>(xs2 * N * esz);
+    // FP32 preconditioner of an FP64 context: FP32 level copies and buffers
+    const bool mg32 = !mixed && c->mg_fp32;
+    Level mgv[MAXLEV];
+    void *mxt1 = xt1, *mxt2 = xt2;
+    float *R32 = nullptr, *Z32 = nullptr, *T32 = nullptr;
+    for (int l = 0; l < L; l++) mgv[l] = lev[l];
+    if (mg32) {
+        R32 = cv.take<float>(sizeof(float) * n * N);
+        Z32 = cv.take<float>(sizeof(float) * n * N);
+        T32 = cv.take<float>(sizeof(float) * n * N);
+        for (int l = 0; l < L; l++) {
+            Level &w = mgv[l];
+            w.g = make_geom(ms[l], N, 4, c->grid_block, c->grid_ctas);
+            if (l == 0 && L > 1 && (double)w.n * N * 4 >= 100e6) enable_zmarch(w.g);
+            w.Dt = cv.take<float>(sizeof(float) * w.n);
+            w.wDt = cv.take<float>(sizeof(float) * w.n);
+            if (l > 0) {
+                w.r = cv.take<float>(sizeof(float) * w.n * N);
+                w.z = cv.take<float>(sizeof(float) * w.n * N);
+                w.t = cv.take<float>(sizeof(float) * w.n * N);
+            } else {
+                w.r = R32;
+                w.z = Z32;
+                w.t = T32;
+            }
+        }
+        mxt1 = cv.take<float>(sizeof(float) * xs * N);
+        mxt2 = cv.take<float>(sizeof(float) * xs2 * N);
+    }
     const long nc = lev[L - 1].n;
     double *Acoarse = cv.take<double>(sizeof(double) * nc * nc);
     double *Ainv = cv.take<double>(sizeof(double) * nc * nc);
@@ -424,6 +462,9 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
         x->L = L;
         for (int l = 0; l < L; l++) x->lev[l] = lev[l];
         x->nc = nc; x->Acoarse = Acoarse; x->Ainv = Ainv; x->xt1 = xt1; x->xt2 = xt2;
+        for (int l = 0; l < L; l++) x->mg[l] = mgv[l];
+        x->mxt1 = mxt1; x->mxt2 = mxt2; x->mg32 = mg32;
+        x->R32 = R32; x->Z32 = Z32; x->T32 = T32;
         x->sc = sc; x->part = part; x->part2 = part2;
         x->gplan_uw = guw; x->gplan_max = gmax; x->gpart = gpart; x->tcpart = tcpart; x->tcimg = tcimg;
         x->tplan = tp; x->tpart = tpart;
@@ -512,7 +553,7 @@ T *first_target(hq_ctx *x, int l, T *Zfinal, T *Tbuf) {
 template <typename T>
 hq_status vcycle(hq_ctx *x, int l, const T *r, T *Zf, T *Tb, bool first_done, double *part_final) {
     LevelScope lvl_(l);
-    Level &v = x->lev[l];
+    Level &v = x->mg[l];
     const T c = (T)v.c, omw = (T)(1.0 - x->cfg.mg_omega);
     if (l == x->L - 1) {
         launch_coarse_solve<T>(v.g, x->Ainv, r, Zf, x->st);
@@ -527,10 +568,10 @@ hq_status vcycle(hq_ctx *x, int l, const T *r, T *Zf, T *Tb, bool first_done, do
         std::swap(cur, oth);
     }
     launch_resid<T>(v.g, (const T *)v.Dt, c, cur, r, oth, nullptr, nullptr, x->st);
-    Level &w = x->lev[l + 1];
-    launch_restrict<T>(v.m, w.m, x->N, v.tab, oth, (T *)x->xt1, (T *)x->xt2, (T *)w.r, x->st);
+    Level &w = x->mg[l + 1];
+    launch_restrict<T>(v.m, w.m, x->N, v.tab, oth, (T *)x->mxt1, (T *)x->mxt2, (T *)w.r, x->st);
     HQ_TRY(vcycle<T>(x, l + 1, (const T *)w.r, (T *)w.z, (T *)w.t, false, nullptr));
-    launch_prolong<T>(v.m, w.m, x->N, v.tab, (const T *)w.z, (T *)x->xt1, (T *)x->xt2, cur, oth,
+    launch_prolong<T>(v.m, w.m, x->N, v.tab, (const T *)w.z, (T *)x->mxt1, (T *)x->mxt2, cur, oth,
                       x->st);
     std::swap(cur, oth);
     for (int s = 0; s < x->cfg.mg_nu2; s++) {
@@ -542,6 +583,28 @@ hq_status vcycle(hq_ctx *x, int l, const T *r, T *Zf, T *Tb, bool first_done, do
     if (cur != Zf) HQ_TRY(copy_blk<T>(x, Zf, cur, (size_t)v.n * x->N));
     return HQ_OK;
 }
+
+// z = M r (one V-cycle) and, if part is non-null, the partials of r.z in the
+// finest level's layout.  In mg32 contexts (FP64 PCG, FP32 preconditioner)
+// r is rounded to FP32, the V-cycle runs on the FP32 level copies, and z is
+// widened back to FP64 while r.z is formed in FP64.
+template <typename T>
+hq_status precondition(hq_ctx *x, const T *r, T *z, T *tbuf, bool first_done, double *part) {
+    if constexpr (std::is_same<T, double>::value) {
+        if (x->mg32) {
+            const size_t cnt = (size_t)x->n * x->N;
+            launch_convert_d2f(cnt, r, x->R32, x->st);
+            HQ_TRY(vcycle<float>(x, 0, x->R32, x->Z32, x->T32, false, nullptr));
+            launch_widen_dot(x->lev[0].g, x->Z32, r, z, part, x->st);
+            return HQ_OK;
+        }
+    }
+    return vcycle<T>(x, 0, r, z, tbuf, first_done, part);
+}
+
+// the first damped-Jacobi sweep can be fused into the x / r update when the
+// V-cycle runs on the PCG's own buffers (more than one level, same precision)
+bool fuse_first_sweep(hq_ctx *x) { return x->L > 1 && !x->mg32; }
 
 // ---------------------------------------------------------------------------
 // block PCG: X = G B, per-column stopping ||r_j|| <= rtol ||b_j||
@@ -564,8 +627,7 @@ hq_status pcg_body(hq_ctx *x, T *X, double rtol) {
     const int N = x->N;
     T *R = (T *)x->R, *Zp = (T *)x->Zp, *P = (T *)x->P, *Q = (T *)x->Q, *Tt = (T *)x->Tt;
     PcgScalars sc = x->sc;
-    const bool single = (x->L == 1);
-    HQ_TRY(vcycle<T>(x, 0, R, Zp, Tt, !single, x->part));
+    HQ_TRY(precondition<T>(x, R, Zp, Tt, fuse_first_sweep(x), x->part));
     launch_finalize(FIN_BETA, N, g.gy, x->part, nullptr, sc, rtol, x->st);
     launch_pcg_p<T>(g, sc.beta, Zp, P, x->st);
     return HQ_OK;
@@ -578,12 +640,11 @@ hq_status pcg_half(hq_ctx *x, T *X, double rtol) {
     const int N = x->N;
     T *R = (T *)x->R, *Zp = (T *)x->Zp, *P = (T *)x->P, *Q = (T *)x->Q, *Tt = (T *)x->Tt;
     PcgScalars sc = x->sc;
-    const bool single = (x->L == 1);
     T *zfirst = first_target<T>(x, 0, Zp, Tt);
     launch_apply<T>(g, (const T *)v.Dt, (T)v.c, P, Q, x->part, x->st);
     launch_finalize(FIN_ALPHA, N, g.gy, x->part, nullptr, sc, rtol, x->st);
     launch_pcg_xr<T>(g, sc.alpha, P, Q, X, R, x->part, (const T *)v.wDt,
-                     single ? nullptr : zfirst, x->st);
+                     fuse_first_sweep(x) ? zfirst : nullptr, x->st);
     HQ_CUDA(cudaMemsetAsync(sc.num_active, 0, sizeof(int), x->st));
     launch_finalize(FIN_RR, N, g.gy, x->part, nullptr, sc, rtol, x->st);
     return HQ_OK;
@@ -676,7 +737,7 @@ hq_status pcg(hq_ctx *x, const T *B, T *X, double rtol, int maxit, int *iters_ho
     hq_status st = HQ_OK;
     long it_done = 0;
     if (nact > 0 && maxit > 0) {
-        HQ_TRY(vcycle<T>(x, 0, R, Zp, Tt, false, x->part));
+        HQ_TRY(precondition<T>(x, R, Zp, Tt, false, x->part));
         launch_finalize(FIN_RZ, N, g.gy, x->part, nullptr, sc, rtol, x->st);
         HQ_TRY(copy_blk<T>(x, P, Zp, (size_t)x->n * N));
         HQ_TRY(pcg_half<T>(x, X, rtol));   // iteration 1
@@ -814,7 +875,7 @@ hq_status pcg_device(hq_ctx *x, const T *B, T *X, double rtol, int maxit, StepGr
     HQ_CUDA(cudaMemsetAsync(sc.num_active, 0, 2 * sizeof(int), main));
     launch_resid<T>(g, (const T *)v.Dt, (T)v.c, X, B, R, x->part, x->part2, main);
     launch_finalize(FIN_BNORM_RNORM, N, g.gy, x->part, x->part2, sc, rtol, main);
-    HQ_TRY(vcycle<T>(x, 0, R, Zp, Tt, false, x->part));
+    HQ_TRY(precondition<T>(x, R, Zp, Tt, false, x->part));
     launch_finalize(FIN_RZ, N, g.gy, x->part, nullptr, sc, rtol, main);
     HQ_TRY(copy_blk<T>(x, P, Zp, (size_t)x->n * N));
     cudaGraph_t gmain;
@@ -1432,6 +1493,10 @@ hq_status set_potential_impl(hq_ctx *x, const double *V, int on_device) {
             launch_convert_d2f(v.n, v.D, (float *)v.Dt, x->st);
             launch_convert_d2f(v.n, v.wD, (float *)v.wDt, x->st);
         }
+        if (x->mg32) {
+            launch_convert_d2f(v.n, v.D, (float *)x->mg[l].Dt, x->st);
+            launch_convert_d2f(v.n, v.wD, (float *)x->mg[l].wDt, x->st);
+        }
     }
     Level &vc = x->lev[x->L - 1];
     launch_assemble_dense(vc.m, vc.c, vc.V, x->sigma, x->Acoarse, x->st);
@@ -1760,7 +1825,7 @@ hq_status grad_density_impl(hq_ctx *x, const double *G, const double *rho_target
     HQ_CUDA(cudaMemcpyAsync(&nact, sc.num_active, sizeof(int), cudaMemcpyDeviceToHost, x->st));
     HQ_CUDA(cudaStreamSynchronize(x->st));
     if (nact > 0) {
-        HQ_TRY(vcycle<double>(x, 0, R, Zp, Tt, false, nullptr));
+        HQ_TRY(precondition<double>(x, R, Zp, Tt, false, nullptr));
         HQ_TRY(project(x, Zp));
         launch_dot<double>(g, R, Zp, x->part, x->st);
         launch_finalize(FIN_RZ, N, g.gy, x->part, nullptr, sc, rtol, x->st);
@@ -1777,7 +1842,7 @@ hq_status grad_density_impl(hq_ctx *x, const double *G, const double *rho_target
             HQ_CUDA(cudaMemcpyAsync(&nact, sc.num_active, sizeof(int), cudaMemcpyDeviceToHost, x->st));
             HQ_CUDA(cudaStreamSynchronize(x->st));
             if (nact == 0) break;
-            HQ_TRY(vcycle<double>(x, 0, R, Zp, Tt, false, nullptr));
+            HQ_TRY(precondition<double>(x, R, Zp, Tt, false, nullptr));
             HQ_TRY(project(x, Zp));
             launch_dot<double>(g, R, Zp, x->part, x->st);
             launch_finalize(FIN_BETA, N, g.gy, x->part, nullptr, sc, rtol, x->st);
@@ -1813,7 +1878,7 @@ hq_status apply_impl(hq_ctx *x, const void *in, void *out, int ncol) {
 }
 template <typename T>
 hq_status vcycle_impl(hq_ctx *x, const void *r, void *z) {
-    HQ_TRY(vcycle<T>(x, 0, (const T *)r, (T *)z, (T *)x->Tt, false, nullptr));
+    HQ_TRY(precondition<T>(x, (const T *)r, (T *)z, (T *)x->Tt, false, nullptr));
     return check_launch(x);
 }
 template <typename T>
@@ -1925,6 +1990,7 @@ void hq_default_config(hq_config *c) {
     c->z_warm_start = 1;
     c->adaptive_tau = 0;
     c->fp64_tc = 1;
+    c->mg_fp32 = 0;
     c->tau_max = 0.0;
 }
 

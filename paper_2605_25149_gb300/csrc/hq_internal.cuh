@@ -209,6 +209,9 @@ void launch_gauss_jordan(int nc, double *A, double *Ainv, int *status, cudaStrea
 void launch_minmax(long n, const double *V, double *out2 /* [min, max-abs-nonfinite flag] */,
                    cudaStream_t s);
 void launch_convert_d2f(size_t count, const double *in, float *out, cudaStream_t s);
+// z = (double) z32, partials of r.z per column (nullable) in g's layout (FP64 geometry)
+void launch_widen_dot(const GridGeom &g, const float *z32, const double *r, double *z,
+                      double *part, cudaStream_t s);
 void launch_convert_f2d(size_t count, const float *in, double *out, cudaStream_t s);
 template <typename T>
 void launch_scale(size_t count, const double *factor, T *x, cudaStream_t s);

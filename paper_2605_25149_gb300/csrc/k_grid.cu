@@ -370,6 +370,36 @@ __global__ void __launch_bounds__(256) k_resid_zm(int m, int N, int nseg, int mz
     }
 }
 
+// z = (double) z32 and partial r.z per column (FP64 geometry of the level):
+// the exit of an FP32 preconditioner inside an FP64 block PCG
+template <int V>
+__global__ void __launch_bounds__(256) k_widen_dot(long n, int N, int ppt,
+                                                   const float *__restrict__ z32,
+                                                   const double *__restrict__ r,
+                                                   double *__restrict__ z, double *part) {
+    __shared__ double red[1024];
+    const int TY = blockDim.y;
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    const bool cv = col < N;
+    double acc[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) acc[v] = 0.0;
+    const long base = (long)blockIdx.y * TY * ppt;
+    for (int k = 0; k < ppt; k++) {
+        long p = base + (long)k * TY + threadIdx.y;
+        if (!cv || p >= n) continue;
+        size_t e = (size_t)p * N + col;
+        VT<double, V> rv = ldv<double, V>(r + e), o;
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            o.v[v] = (double)z32[e + v];
+            acc[v] += rv.v[v] * o.v[v];
+        }
+        stv<double, V>(z + e, o);
+    }
+    if (part) block_col_reduce<V, double>(acc, red, part, N, col, cv);
+}
+
 template <typename T, int V>
 __global__ void __launch_bounds__(256) k_jacobi_first(long n, int N, int ppt,
                                                       const T *__restrict__ wD,
@@ -1104,6 +1134,17 @@ template <typename T, int V>
 static void run_dot(const GridGeom &g, const T *x, const T *y, double *part, cudaStream_t s) {
     HQ_LAUNCH_W(HQ_K_VECTOR, (double)g.n * g.N, k_dot<T, V><<<grd(g), blk(g), 0, s>>>(g.n, g.N, g.ppt, x, y, part));
 }
+template <typename T, int V>
+static void run_widen_dot(const GridGeom &g, const float *z32, const double *r, double *z,
+                          double *part, cudaStream_t s) {
+    HQ_LAUNCH_W(HQ_K_VECTOR, (double)g.n * g.N,
+                k_widen_dot<V><<<grd(g), blk(g), 0, s>>>(g.n, g.N, g.ppt, z32, r, z, part));
+}
+void launch_widen_dot(const GridGeom &g, const float *z32, const double *r, double *z,
+                      double *part, cudaStream_t s) {
+    HQ_VEC_DISPATCH(double, g, run_widen_dot, g, z32, r, z, part, s);
+}
+
 template <typename T>
 void launch_dot(const GridGeom &g, const T *x, const T *y, double *part, cudaStream_t s) {
     HQ_VEC_DISPATCH(T, g, run_dot, g, x, y, part, s);

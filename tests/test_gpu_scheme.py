@@ -211,3 +211,34 @@ def test_mixed_predictor_system_is_solved_to_fp64_accuracy(m, N):
     rhs = np.vstack([S, Pwu])
     res = np.abs(Mm @ XY - rhs).max() / np.abs(rhs).max()
     assert res < 1e-13, res
+
+
+def test_fp64_pcg_with_fp32_preconditioner_matches_oracle():
+    """mg_fp32 = 1: the block PCG stays FP64 (residuals, updates, stopping test)
+    and only the V-cycle runs in FP32; W = G U is still solved to cg_rtol, so
+    20 steps follow the oracle's FP64 trajectory."""
+    m, N, tau = 12, 6, 0.4
+    s, V, U0 = make(m, N, tau=tau, cg_rtol=1e-12, cg_maxit=400, mg_fp32=1)
+    sigma = s.info()["sigma"]
+    Uo = s.get_state()[0]
+    for n in range(20):
+        s.step(1)
+        Uo = O.scheme_step(m, V, sigma, Uo, tau)["Unew"]
+        assert rel(s.get_state()[0], Uo) < 1e-8, n
+
+
+def test_fp64_with_fp32_preconditioner_converges_to_closed_form():
+    m, N = 16, 8
+    s, V, U0 = make(m, N, potential="harmonic", useed=1, tau=0.5, cg_rtol=1e-10, mg_fp32=1)
+    steps, g = s.solve(1e-8, 10000)
+    assert g < 1e-8
+    ev = s.eigenpairs(vectors=True)
+    np.testing.assert_allclose(ev["lam_rr"], separable_levels(m, -6.0, 6.0, N), rtol=1e-10)
+    s64, _, _ = make(m, N, potential="harmonic", useed=1, tau=0.5, cg_rtol=1e-10)
+    s64.profile()
+    s.profile()
+    s64.step(5)
+    s.step(5)
+    it64 = s64.pcg_stats()[1]
+    it32 = s.pcg_stats()[1]
+    assert it32 <= 1.5 * it64 + 2
