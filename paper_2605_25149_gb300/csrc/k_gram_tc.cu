@@ -10,12 +10,12 @@
 // FP32 columns), and writes its partial tile; a second kernel reduces the
 // chunk partials in FP64 in a fixed order (deterministic).
 //
-// Per 32-point K-slice the 128 threads load the tile columns of 32 point rows
-// (coalesced along the columns of the point-major block), split them into
-// tf32 hi/lo and store them K-major with the 128-byte swizzle into a
-// double-buffered shared-memory stage; one thread issues 12 MMAs
-// (4 K-steps of 8 x 3 products, M = N = 128) and commits them to the stage's
-// mbarrier, so the loads of the next slice overlap the MMAs of this one.
+// Per 32-point K-slice the 128 threads copy the tile columns of 32 point rows
+// (coalesced along the columns of the point-major block) into a raw
+// shared-memory stage with cp.async, three slices ahead; they split a landed
+// slice into tf32 hi/lo and store it K-major with the 128-byte swizzle into a
+// double-buffered MMA stage; one thread issues 12 MMAs (4 K-steps of 8 x 3
+// products, M = N = 128) and commits them to the stage's mbarrier.
 // Every wait is bounded: on expiry the CTA sets an error flag, stops issuing
 // and still releases its TMEM.
 #include "hq_internal.cuh"
@@ -29,6 +29,8 @@ constexpr int TC_T = 128;        // output tile edge (M = N = 128)
 constexpr int TC_K = 32;         // points per slice (128 bytes of tf32 per row)
 constexpr int TC_THREADS = 128;  // 4 warps: each owns 32 TMEM lanes in the epilogue
 constexpr int TC_TILE_BYTES = TC_T * TC_K * 4;   // 16 KB: one operand, one of hi / lo
+constexpr int TC_RAW = 3;                          // raw FP32 slices in flight (cp.async)
+constexpr int TC_RAW_BYTES = TC_K * TC_T * 4;      // 16 KB: one operand's raw slice
 // instruction descriptor: D f32, A/B tf32, both K-major, M = N = 128
 __host__ __device__ constexpr uint32_t idesc_tf32_128x128() {
     return (1u << 4)                 // D format: F32
@@ -67,7 +69,8 @@ __device__ __forceinline__ float tc_gat(const float *X1, int n1, const float *X2
     return c < n1 ? X1[(size_t)p * n1 + c] : X2[(size_t)p * n2 + (c - n1)];
 }
 
-// Stage layout (bytes): [A_hi | A_lo | B_hi | B_lo], 16 KB each, 1024-aligned.
+// Shared memory (bytes): two MMA stages [A_hi | A_lo | B_hi | B_lo] of 16 KB
+// each (1024-aligned), then TC_RAW raw stages [A | B] of 16 KB each.
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gram_tf32x3(TcPlan P, const float *__restrict__ X1, int n1, const float *__restrict__ X2,
                   int n2, float *__restrict__ partials, int *status) {
@@ -104,43 +107,53 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base_sh;
 
-    // each thread loads column-quads of 32 point rows: 32 rows x 128 cols =
-    // 1024 float4; thread t takes float4 index q = t + 128 j (j = 0..7):
-    // row = q / 32, column quad = q % 32.
-    float4 ra[8], rb[8];
+    // Raw FP32 slices (32 point rows x 128 columns, rows of 512 bytes) are
+    // copied into shared memory with cp.async, three slices ahead of the one
+    // being split, so the global-memory latency overlaps the split and the
+    // MMAs.  Thread t copies 16-byte chunks q = t + 128 j: row = q / 32,
+    // column quad = q % 32; chunks the vector path cannot take (ragged rows
+    // or columns, unaligned blocks) are written with plain loads and stores.
+    unsigned char *raw = smem + 2 * 4 * TC_TILE_BYTES;   // TC_RAW stages x (A | B)
     const bool vec4 = (n1 % 4 == 0) && (n2 % 4 == 0) &&
                       (((uintptr_t)X1 & 15) == 0) && (X2 == nullptr || ((uintptr_t)X2 & 15) == 0);
-    auto load_slice = [&](int s, float4 (&dst)[8], int c0) {
+    auto issue_slice = [&](int sl, unsigned char *dst, int c0) {
 #pragma unroll
         for (int j = 0; j < 8; j++) {
-            int q = tid + TC_THREADS * j;
-            int row = q >> 5, cq = (q & 31) * 4;
-            long p = r0 + (long)s * TC_K + row;
+            const int q = tid + TC_THREADS * j;
+            const int row = q >> 5, cq = (q & 31) * 4;
+            const long p = r0 + (long)sl * TC_K + row;
             const int c = c0 + cq;
+            float *d = reinterpret_cast<float *>(dst + (size_t)row * 512 + cq * 4);
             if (p < r1 && vec4 && c + 3 < P.na) {
                 const float *src = c < n1 ? X1 + (size_t)p * n1 + c : X2 + (size_t)p * n2 + (c - n1);
-                dst[j] = *reinterpret_cast<const float4 *>(src);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(d)),
+                             "l"(src)
+                             : "memory");
             } else {
-                float v[4];
 #pragma unroll
                 for (int u = 0; u < 4; u++)
-                    v[u] = (p < r1 && c + u < P.na) ? tc_gat(X1, n1, X2, n2, p, c + u) : 0.f;
-                dst[j] = make_float4(v[0], v[1], v[2], v[3]);
+                    d[u] = (p < r1 && c + u < P.na) ? tc_gat(X1, n1, X2, n2, p, c + u) : 0.f;
             }
         }
     };
-    // store: element (point row k, column i) -> K-major tile row i, k
-    auto store_slice = [&](unsigned char *hi, unsigned char *lo, const float4 (&src)[8]) {
+    auto issue_raw = [&](int sl) {
+        unsigned char *dst = raw + (size_t)(sl % TC_RAW) * 2 * TC_RAW_BYTES;
+        issue_slice(sl, dst, a0);
+        if (!diag) issue_slice(sl, dst + TC_RAW_BYTES, b0);
+    };
+    // split: raw element (point row k, column i) -> K-major tile row i, k
+    auto split_slice = [&](const unsigned char *src, unsigned char *hi, unsigned char *lo) {
 #pragma unroll
         for (int j = 0; j < 8; j++) {
-            int q = tid + TC_THREADS * j;
-            int k = q >> 5, cq = (q & 31) * 4;
-            float v[4] = {src[j].x, src[j].y, src[j].z, src[j].w};
+            const int q = tid + TC_THREADS * j;
+            const int k = q >> 5, cq = (q & 31) * 4;
+            const float4 v4 = *reinterpret_cast<const float4 *>(src + (size_t)k * 512 + cq * 4);
+            const float v[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
             for (int u = 0; u < 4; u++) {
-                float h = tf32_rna(v[u]);
-                float l = tf32_rna(v[u] - h);
-                uint32_t off = sw128_offset(cq + u, k);
+                const float h = tf32_rna(v[u]);
+                const float l = tf32_rna(v[u] - h);
+                const uint32_t off = sw128_offset(cq + u, k);
                 *reinterpret_cast<float *>(hi + off) = h;
                 *reinterpret_cast<float *>(lo + off) = l;
             }
@@ -148,9 +161,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     };
 
     const uint32_t idesc = idesc_tf32_128x128();
-    if (nslices > 0) {
-        load_slice(0, ra, a0);
-        if (!diag) load_slice(0, rb, b0);
+    for (int sl = 0; sl < TC_RAW; sl++) {
+        if (sl < nslices) issue_raw(sl);
+        asm volatile("cp.async.commit_group;" ::: "memory");
     }
     for (int s = 0; s < nslices; s++) {
         const int st = s & 1;
@@ -158,19 +171,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         unsigned char *Ahi = base, *Alo = base + TC_TILE_BYTES;
         unsigned char *Bhi = diag ? Ahi : base + 2 * TC_TILE_BYTES;
         unsigned char *Blo = diag ? Alo : base + 3 * TC_TILE_BYTES;
+        // slice s has landed once all but the TC_RAW - 1 newest groups are done
+        asm volatile("cp.async.wait_group %0;" ::"n"(TC_RAW - 1) : "memory");
         if (s >= 2) {
             if (!mbar_wait(&mbar[st], (unsigned)(((s - 2) >> 1) & 1))) atomicExch(&abort_sh, 1);
         }
         __syncthreads();
         if (abort_sh) break;
-        store_slice(Ahi, Alo, ra);
-        if (!diag) store_slice(Bhi, Blo, rb);
-        if (s + 1 < nslices) {
-            load_slice(s + 1, ra, a0);
-            if (!diag) load_slice(s + 1, rb, b0);
-        }
+        const unsigned char *rs = raw + (size_t)(s % TC_RAW) * 2 * TC_RAW_BYTES;
+        split_slice(rs, Ahi, Alo);
+        if (!diag) split_slice(rs + TC_RAW_BYTES, Bhi, Blo);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
+        if (s + TC_RAW < nslices) issue_raw(s + TC_RAW);
+        asm volatile("cp.async.commit_group;" ::: "memory");
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t ahi = smem_u32(Ahi), alo = smem_u32(Alo);
@@ -187,6 +201,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mma_commit(&mbar[st]);
         }
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     // wait for the last two commits (they complete in issue order)
     bool ok = !abort_sh;
     if (ok && nslices >= 1) {
@@ -266,7 +281,7 @@ size_t gram_tc_partial_bytes(long n, int na) {
     return sizeof(float) * (size_t)p.chunks * p.ntiles * TC_T * TC_T;
 }
 
-size_t gram_tc_smem_bytes() { return 2 * 4 * TC_TILE_BYTES + 1024; }
+size_t gram_tc_smem_bytes() { return 2 * 4 * TC_TILE_BYTES + TC_RAW * 2 * TC_RAW_BYTES + 1024; }
 
 void launch_gram_tc(long n, const float *X1, int n1, const float *X2, int n2, double w,
                     float *partials, double *out, int *status, cudaStream_t s) {
