@@ -141,22 +141,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         issue_slice(sl, dst, a0);
         if (!diag) issue_slice(sl, dst + TC_RAW_BYTES, b0);
     };
-    // split: raw element (point row k, column i) -> K-major tile row i, k
+    // split: raw element (point row k, column i) -> K-major tile row i, k.
+    // Thread = (tile row i, quad of 4 consecutive points): four 4-byte reads
+    // down a raw column (consecutive i across the lanes: no bank conflicts)
+    // and one 16-byte store per half (a swizzled chunk of row i).
     auto split_slice = [&](const unsigned char *src, unsigned char *hi, unsigned char *lo) {
+        const float *rf = reinterpret_cast<const float *>(src);
 #pragma unroll
         for (int j = 0; j < 8; j++) {
             const int q = tid + TC_THREADS * j;
-            const int k = q >> 5, cq = (q & 31) * 4;
-            const float4 v4 = *reinterpret_cast<const float4 *>(src + (size_t)k * 512 + cq * 4);
-            const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+            const int i = q & (TC_T - 1), kq = q >> 7;
+            float h[4], l[4];
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const float h = tf32_rna(v[u]);
-                const float l = tf32_rna(v[u] - h);
-                const uint32_t off = sw128_offset(cq + u, k);
-                *reinterpret_cast<float *>(hi + off) = h;
-                *reinterpret_cast<float *>(lo + off) = l;
+            for (int t = 0; t < 4; t++) {
+                const float v = rf[(4 * kq + t) * TC_T + i];
+                h[t] = tf32_rna(v);
+                l[t] = tf32_rna(v - h[t]);
             }
+            const uint32_t off = sw128_offset(i, 4 * kq);
+            *reinterpret_cast<float4 *>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<float4 *>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
         }
     };
 
@@ -446,14 +450,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int q = tid + TC_THREADS * j;
             const int row = q >> 3, kq = (q & 7) * 4;
             const float v[4] = {ra[j].x, ra[j].y, ra[j].z, ra[j].w};
+            float h[4], l[4];
 #pragma unroll
             for (int u = 0; u < 4; u++) {
-                const float h = tf32_rna(v[u]);
-                const float l = tf32_rna(v[u] - h);
-                const uint32_t off = sw128_offset(row, kq + u);
-                *reinterpret_cast<float *>(hi + off) = h;
-                *reinterpret_cast<float *>(lo + off) = l;
+                h[u] = tf32_rna(v[u]);
+                l[u] = tf32_rna(v[u] - h[u]);
             }
+            // the four values form one 16-byte chunk of the swizzled row
+            const uint32_t off = sw128_offset(row, kq);
+            *reinterpret_cast<float4 *>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<float4 *>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
         }
     };
     auto copy_b = [&](int s, unsigned char *dst) {

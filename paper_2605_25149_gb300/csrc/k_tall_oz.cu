@@ -379,13 +379,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base_sh;
     const uint32_t idesc = idesc_bf16(OZ_M, OZ_NT);
-    // slice loads: thread t takes column c = t & 127 of points 2 j + (t >> 7)
+    // slice loads: thread t takes column c = t & 127 of the 32 consecutive
+    // points 32 (t >> 7) + j (coalesced across the lanes for each j)
     const int lc = tid & (OZ_M - 1), lh = tid >> 7;
     double xv[OZ_KC / 2];
     auto load_slice = [&](int sl) {
 #pragma unroll
         for (int j = 0; j < OZ_KC / 2; j++) {
-            const long p = p0 + (long)sl * OZ_KC + 2 * j + lh;
+            const long p = p0 + (long)sl * OZ_KC + 32 * lh + j;
             xv[j] = (p < p1 && lc < na)
                         ? (lc < n1 ? X1[(size_t)p * n1 + lc] : X2[(size_t)p * n2 + (lc - n1)])
                         : 0.0;
@@ -422,15 +423,26 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         if (abort_sh) break;
         if (sl > 0 && (sl & 1) == 0) flush();   // 128 points accumulated
         {
+            // eight consecutive points of one column form one 16-byte chunk of
+            // each digit plane
             const int em = cexp[lc];
 #pragma unroll
-            for (int j = 0; j < OZ_KC / 2; j++) {
-                uint16_t dg[OZ_S];
-                oz_digits(xv[j], em, dg);
-                const uint32_t off = sw128_offset16(lc, 2 * j + lh);
+            for (int g8 = 0; g8 < 4; g8++) {
+                uint32_t pk[OZ_S][4];
+#pragma unroll
+                for (int u = 0; u < 8; u += 2) {
+                    uint16_t d0[OZ_S], d1[OZ_S];
+                    oz_digits(xv[8 * g8 + u], em, d0);
+                    oz_digits(xv[8 * g8 + u + 1], em, d1);
+#pragma unroll
+                    for (int i = 0; i < OZ_S; i++)
+                        pk[i][u >> 1] = (uint32_t)d0[i] | ((uint32_t)d1[i] << 16);
+                }
+                const uint32_t off = sw128_offset16(lc, 32 * lh + 8 * g8);
 #pragma unroll
                 for (int i = 0; i < OZ_S; i++)
-                    *reinterpret_cast<uint16_t *>(planes + i * OZ_APLANE + off) = dg[i];
+                    *reinterpret_cast<uint4 *>(planes + i * OZ_APLANE + off) =
+                        make_uint4(pk[i][0], pk[i][1], pk[i][2], pk[i][3]);
             }
         }
         if (sl + 1 < nslices) load_slice(sl + 1);
