@@ -314,6 +314,11 @@ void launch_gram_tc(long n, const float *X1, int n1, const float *X2, int n2, do
 // with plain 16-byte loads.  Accumulators: TMEM, 128 lanes x NT columns.
 // ===========================================================================
 constexpr int TT_M = 128;
+// raw A slices in flight (cp.async) for wide tiles; tiles of NT <= 64 stage A
+// through registers instead, which keeps their shared memory small enough
+// for two CTAs per SM
+template <int NT>
+__host__ __device__ constexpr int tt_raw() { return NT >= 128 ? 2 : 0; }
 
 struct TallTcPlan {
     long n;
@@ -417,6 +422,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const bool vec4 = (P.k1 % 4 == 0) && (P.k2 % 4 == 0) && (((uintptr_t)A1 & 15) == 0) &&
                       (A2 == nullptr || ((uintptr_t)A2 & 15) == 0);
 
+    if constexpr (tt_raw<NT>() == 0) {
     // A slice: 128 points x 32 columns; thread t takes float4 q = t + 128 j:
     // row = q / 8, column quad = (q % 8) * 4
     float4 ra[8];
@@ -502,11 +508,127 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mma_commit(&mbar[st]);
         }
     }
+    } else {
+    // A slices (128 points x 32 columns, rows of 128 bytes) are copied raw
+    // into shared memory with cp.async two slices ahead and split into tf32
+    // hi / lo from there; the B image of slice s + 1 is copied with cp.async
+    // straight into its MMA stage as soon as the MMAs of slice s - 1 that used
+    // the stage have completed.  Thread t copies / splits the 16-byte chunks
+    // q = t + 128 j: row = q / 8, column quad = (q % 8) * 4.
+    constexpr int TT_RAW = tt_raw<NT>();
+    unsigned char *raw = smem + 2 * STAGE;   // TT_RAW slices x 16 KB
+    auto issue_a = [&](int sl) {
+        unsigned char *dst = raw + (size_t)(sl % TT_RAW) * ABYTES;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const int q = tid + TC_THREADS * j;
+            const int row = q >> 3, kq = (q & 7) * 4;
+            const long p = r0 + row;
+            const int k = sl * TC_K + kq;
+            float *d = reinterpret_cast<float *>(dst + row * 128 + kq * 4);
+            if (p < P.n && vec4 && k + 3 < P.k1 + P.k2) {
+                const float *src = k < P.k1 ? A1 + (size_t)p * P.k1 + k
+                                            : A2 + (size_t)p * P.k2 + (k - P.k1);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(d)),
+                             "l"(src)
+                             : "memory");
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int kk = k + u;
+                    float v = 0.f;
+                    if (p < P.n && kk < P.k1) v = A1[(size_t)p * P.k1 + kk];
+                    else if (p < P.n && kk < P.k1 + P.k2) v = A2[(size_t)p * P.k2 + (kk - P.k1)];
+                    d[u] = v;
+                }
+            }
+        }
+    };
+    auto split_a = [&](int sl, unsigned char *hi, unsigned char *lo) {
+        const unsigned char *src = raw + (size_t)(sl % TT_RAW) * ABYTES;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const int q = tid + TC_THREADS * j;
+            const int row = q >> 3, kq = (q & 7) * 4;
+            const float4 v4 = *reinterpret_cast<const float4 *>(src + row * 128 + kq * 4);
+            const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+            float h[4], l[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                h[u] = tf32_rna(v[u]);
+                l[u] = tf32_rna(v[u] - h[u]);
+            }
+            // the four values form one 16-byte chunk of the swizzled row
+            const uint32_t off = sw128_offset(row, kq);
+            *reinterpret_cast<float4 *>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<float4 *>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
+        }
+    };
+    auto issue_b = [&](int sl) {
+        const unsigned char *src =
+            image + ((size_t)ct * P.nslices + sl) * 2 * (size_t)BBYTES;
+        unsigned char *dst = smem + (sl & 1) * STAGE + 2 * ABYTES;
+        for (int i = tid; i < 2 * BBYTES / 16; i += TC_THREADS)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst + 16 * i)),
+                         "l"(src + 16 * (size_t)i)
+                         : "memory");
+    };
+    auto commit = [&]() { asm volatile("cp.async.commit_group;" ::: "memory"); };
+
+    const uint32_t idesc = idesc_tf32(TT_M, NT);
+    // prologue: B(0) | A(0) | A(1)
+    if (P.nslices > 0) issue_b(0);
+    commit();
+    for (int sl = 0; sl < TT_RAW; sl++) {
+        if (sl < P.nslices) issue_a(sl);
+        commit();
+    }
+    for (int s = 0; s < P.nslices; s++) {
+        const int st = s & 1;
+        unsigned char *base = smem + st * STAGE;
+        unsigned char *Ahi = base, *Alo = base + ABYTES, *Bhi = base + 2 * ABYTES,
+                      *Blo = base + 2 * ABYTES + BBYTES;
+        // B(s) and A(s) have landed once only the newest TT_RAW - 1 groups
+        // (A(s + 1)) may still be in flight
+        asm volatile("cp.async.wait_group %0;" ::"n"(TT_RAW - 1) : "memory");
+        __syncthreads();
+        if (abort_sh) break;
+        split_a(s, Ahi, Alo);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ahi = smem_u32(Ahi), alo = smem_u32(Alo);
+            const uint32_t bhi = smem_u32(Bhi), blo = smem_u32(Blo);
+#pragma unroll
+            for (int kk = 0; kk < TC_K / 8; kk++) {
+                const uint32_t ko = kk * 32;
+                const uint64_t dah = make_desc_sw128(ahi + ko), dal = make_desc_sw128(alo + ko);
+                const uint64_t dbh = make_desc_sw128(bhi + ko), dbl = make_desc_sw128(blo + ko);
+                mma_tf32(tmem, dah, dbh, idesc, (s > 0 || kk > 0) ? 1u : 0u);
+                mma_tf32(tmem, dah, dbl, idesc, 1u);
+                mma_tf32(tmem, dal, dbh, idesc, 1u);
+            }
+            mma_commit(&mbar[st]);
+        }
+        // the other stage is free once the MMAs of slice s - 1 are done: copy
+        // B(s + 1) there, and A(s + 2) into the raw slot A(s) just left
+        if (s >= 1) {
+            if (!mbar_wait(&mbar[st ^ 1], (unsigned)(((s - 1) >> 1) & 1))) atomicExch(&abort_sh, 1);
+        }
+        if (s + 1 < P.nslices) issue_b(s + 1);
+        commit();
+        if (s + TT_RAW < P.nslices) issue_a(s + TT_RAW);
+        commit();
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
     bool ok = !abort_sh;
     if (ok && P.nslices >= 1) {
         int s = P.nslices - 1;
         ok = mbar_wait(&mbar[s & 1], (unsigned)((s >> 1) & 1));
-        if (ok && P.nslices >= 2) {
+        // the register-staged variant has not yet waited for slice n - 2
+        if (tt_raw<NT>() == 0 && ok && P.nslices >= 2) {
             s = P.nslices - 2;
             ok = mbar_wait(&mbar[s & 1], (unsigned)((s >> 1) & 1));
         }
@@ -581,7 +703,7 @@ template <int NT>
 static void run_tall_tc(const TallTcPlan &p, const float *A1, const float *A2,
                         const unsigned char *image, const float *Cin, float *Out, double *part_sq,
                         int *status, cudaStream_t s) {
-    const int smem = 2 * (2 * TT_M * 128 + 2 * NT * 128) + 1024;
+    const int smem = 2 * (2 * TT_M * 128 + 2 * NT * 128) + tt_raw<NT>() * TT_M * 128 + 1024;
     tc_prepare();
     const unsigned gx = (unsigned)((p.n + TT_M - 1) / TT_M);
     HQ_LAUNCH(HQ_K_BLOCKGEMM,
@@ -591,7 +713,7 @@ static void run_tall_tc(const TallTcPlan &p, const float *A1, const float *A2,
 
 template <int NT>
 static void prep_tall() {
-    const int smem = 2 * (2 * TT_M * 128 + 2 * NT * 128) + 1024;
+    const int smem = 2 * (2 * TT_M * 128 + 2 * NT * 128) + tt_raw<NT>() * TT_M * 128 + 1024;
     cudaFuncSetAttribute(k_tall_tf32x3<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
