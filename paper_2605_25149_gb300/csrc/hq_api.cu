@@ -280,6 +280,14 @@ int level_sizes(int m, int coarsest, int *ms) {
     return L;
 }
 
+// z-marching CTAs for a finest level whose block reaches 100 MB (beyond
+// about three quarters of L2); HQ_ZMARCH=1 / 0 forces them on / off
+void zmarch_rule(GridGeom &g, double block_bytes) {
+    const char *zm = std::getenv("HQ_ZMARCH");
+    const bool force = zm && zm[0] == '1', off = zm && zm[0] == '0';
+    if (!off && (force || block_bytes >= 100e6)) enable_zmarch(g);
+}
+
 size_t carve(hq_ctx *x, const hq_config *c, char *base) {
     Carver cv{base};
     const int m = c->m, N = c->nev;
@@ -313,11 +321,7 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
         // finest-level blocks of 100 MB or more: z-marching smoothing sweeps
         // (HQ_ZMARCH=0 keeps the linear point order, HQ_ZMARCH=1 forces the
         // z-marching order at any size; both for comparisons)
-        if (l == 0 && L > 1) {
-            const char *zm = std::getenv("HQ_ZMARCH");
-            const bool force = zm && zm[0] == '1', off = zm && zm[0] == '0';
-            if (!off && (force || (double)v.n * N * esz >= 100e6)) enable_zmarch(v.g);
-        }
+        if (l == 0 && L > 1) zmarch_rule(v.g, (double)v.n * N * esz);
         v.V = cv.take<double>(sizeof(double) * v.n);
         v.D = cv.take<double>(sizeof(double) * v.n);
         v.wD = cv.take<double>(sizeof(double) * v.n);
@@ -366,7 +370,7 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
         for (int l = 0; l < L; l++) {
             Level &w = mgv[l];
             w.g = make_geom(ms[l], N, 4, c->grid_block, c->grid_ctas);
-            if (l == 0 && L > 1 && (double)w.n * N * 4 >= 100e6) enable_zmarch(w.g);
+            if (l == 0 && L > 1) zmarch_rule(w.g, (double)w.n * N * 4);
             w.Dt = cv.take<float>(sizeof(float) * w.n);
             w.wDt = cv.take<float>(sizeof(float) * w.n);
             if (l > 0) {
@@ -397,7 +401,7 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
     sc.status = cv.take<int>(sizeof(int) * 4);
     // partial rows: the working-precision geometry of the finest level, or the
     // FP64 geometry used by the FP64 extraction / monitoring kernels
-    const int gy0 = std::max(lev[0].g.gy, make_geom(m, N, 8).gy);
+    const int gy0 = std::max(std::max(lev[0].g.gy, part_rows(lev[0].g)), make_geom(m, N, 8).gy);
     double *part = cv.take<double>(sizeof(double) * (size_t)gy0 * N);
     double *part2 = cv.take<double>(sizeof(double) * (size_t)gy0 * N);
     sc.fpart = cv.take<double>(sizeof(double) * 2 * (size_t)finalize_chunks(gy0) * N);
@@ -606,6 +610,10 @@ hq_status precondition(hq_ctx *x, const T *r, T *z, T *tbuf, bool first_done, do
 // V-cycle runs on the PCG's own buffers (more than one level, same precision)
 bool fuse_first_sweep(hq_ctx *x) { return x->L > 1 && !x->mg32; }
 
+// rows of the r.z partials precondition() leaves: the last smoothing sweep
+// of the finest level, or the FP64 widening kernel of an FP32 V-cycle
+int prec_rows(hq_ctx *x) { return x->mg32 ? x->lev[0].g.gy : part_rows(x->lev[0].g); }
+
 // ---------------------------------------------------------------------------
 // block PCG: X = G B, per-column stopping ||r_j|| <= rtol ||b_j||
 //
@@ -628,7 +636,7 @@ hq_status pcg_body(hq_ctx *x, T *X, double rtol) {
     T *R = (T *)x->R, *Zp = (T *)x->Zp, *P = (T *)x->P, *Q = (T *)x->Q, *Tt = (T *)x->Tt;
     PcgScalars sc = x->sc;
     HQ_TRY(precondition<T>(x, R, Zp, Tt, fuse_first_sweep(x), x->part));
-    launch_finalize(FIN_BETA, N, g.gy, x->part, nullptr, sc, rtol, x->st);
+    launch_finalize(FIN_BETA, N, prec_rows(x), x->part, nullptr, sc, rtol, x->st);
     launch_pcg_p<T>(g, sc.beta, Zp, P, x->st);
     return HQ_OK;
 }
@@ -642,7 +650,7 @@ hq_status pcg_half(hq_ctx *x, T *X, double rtol) {
     PcgScalars sc = x->sc;
     T *zfirst = first_target<T>(x, 0, Zp, Tt);
     launch_apply<T>(g, (const T *)v.Dt, (T)v.c, P, Q, x->part, x->st);
-    launch_finalize(FIN_ALPHA, N, g.gy, x->part, nullptr, sc, rtol, x->st);
+    launch_finalize(FIN_ALPHA, N, part_rows(g), x->part, nullptr, sc, rtol, x->st);
     launch_pcg_xr<T>(g, sc.alpha, P, Q, X, R, x->part, (const T *)v.wDt,
                      fuse_first_sweep(x) ? zfirst : nullptr, x->st);
     HQ_CUDA(cudaMemsetAsync(sc.num_active, 0, sizeof(int), x->st));
@@ -730,7 +738,7 @@ hq_status pcg(hq_ctx *x, const T *B, T *X, double rtol, int maxit, int *iters_ho
     PcgScalars sc = x->sc;
     HQ_CUDA(cudaMemsetAsync(sc.num_active, 0, sizeof(int), x->st));
     launch_resid<T>(g, (const T *)v.Dt, c, X, B, R, x->part, x->part2, x->st);
-    launch_finalize(FIN_BNORM_RNORM, N, g.gy, x->part, x->part2, sc, rtol, x->st);
+    launch_finalize(FIN_BNORM_RNORM, N, part_rows(g), x->part, x->part2, sc, rtol, x->st);
     int nact = 0;
     HQ_CUDA(cudaMemcpyAsync(&nact, sc.num_active, sizeof(int), cudaMemcpyDeviceToHost, x->st));
     HQ_CUDA(cudaStreamSynchronize(x->st));
@@ -738,7 +746,7 @@ hq_status pcg(hq_ctx *x, const T *B, T *X, double rtol, int maxit, int *iters_ho
     long it_done = 0;
     if (nact > 0 && maxit > 0) {
         HQ_TRY(precondition<T>(x, R, Zp, Tt, false, x->part));
-        launch_finalize(FIN_RZ, N, g.gy, x->part, nullptr, sc, rtol, x->st);
+        launch_finalize(FIN_RZ, N, prec_rows(x), x->part, nullptr, sc, rtol, x->st);
         HQ_TRY(copy_blk<T>(x, P, Zp, (size_t)x->n * N));
         HQ_TRY(pcg_half<T>(x, X, rtol));   // iteration 1
         it_done = 1;
@@ -874,9 +882,9 @@ hq_status pcg_device(hq_ctx *x, const T *B, T *X, double rtol, int maxit, StepGr
     cudaStream_t main = x->st;
     HQ_CUDA(cudaMemsetAsync(sc.num_active, 0, 2 * sizeof(int), main));
     launch_resid<T>(g, (const T *)v.Dt, (T)v.c, X, B, R, x->part, x->part2, main);
-    launch_finalize(FIN_BNORM_RNORM, N, g.gy, x->part, x->part2, sc, rtol, main);
+    launch_finalize(FIN_BNORM_RNORM, N, part_rows(g), x->part, x->part2, sc, rtol, main);
     HQ_TRY(precondition<T>(x, R, Zp, Tt, false, x->part));
-    launch_finalize(FIN_RZ, N, g.gy, x->part, nullptr, sc, rtol, main);
+    launch_finalize(FIN_RZ, N, prec_rows(x), x->part, nullptr, sc, rtol, main);
     HQ_TRY(copy_blk<T>(x, P, Zp, (size_t)x->n * N));
     cudaGraph_t gmain;
     if (!capture_graph_of(main, &gmain)) return fail(x, HQ_ERR_CUDA, "capture state");
@@ -1872,7 +1880,8 @@ hq_status grad_density_impl(hq_ctx *x, const double *G, const double *rho_target
 template <typename T>
 hq_status apply_impl(hq_ctx *x, const void *in, void *out, int ncol) {
     Level &v = x->lev[0];
-    GridGeom g = make_geom(x->m, ncol, (int)sizeof(T));
+    // the step's own launch shape for N columns, a plain one otherwise
+    GridGeom g = ncol == x->N ? v.g : make_geom(x->m, ncol, (int)sizeof(T));
     launch_apply<T>(g, (const T *)v.Dt, (T)v.c, (const T *)in, (T *)out, nullptr, x->st);
     return check_launch(x);
 }

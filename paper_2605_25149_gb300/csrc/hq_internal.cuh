@@ -36,8 +36,13 @@ struct GridGeom {
     int zch;        // > 0: smoothing sweeps without partial sums march in z
                     // (zch chunks of planes per x-segment / y-row), see k_jacobi_zm
 };
-// switches the smoother of a level to z-marching CTAs (blocks larger than L2)
+// switches the operator, residual and smoothing sweeps of a level to
+// z-marching CTAs (blocks larger than L2)
 void enable_zmarch(GridGeom &g);
+// rows of per-column partial sums written by the operator, residual and
+// smoothing kernels of geometry g (one row per CTA along y); the vector
+// kernels (launch_pcg_xr, launch_dot, launch_widen_dot) always write g.gy
+int part_rows(const GridGeom &g);
 // block: threads per CTA (0: 256); ctas_per_sm: target CTAs per SM of the
 // grid (0: 16) -- the two launch-shape parameters the autotuner searches
 GridGeom make_geom(int m, int N, int elem_bytes, int block = 0, int ctas_per_sm = 0);

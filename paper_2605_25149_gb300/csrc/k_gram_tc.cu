@@ -10,12 +10,21 @@
 // FP32 columns), and writes its partial tile; a second kernel reduces the
 // chunk partials in FP64 in a fixed order (deterministic).
 //
-// Per 32-point K-slice the 128 threads copy the tile columns of 32 point rows
+// Per 32-point K-slice the 256 threads copy the tile columns of 32 point rows
 // (coalesced along the columns of the point-major block) into a raw
 // shared-memory stage with cp.async, three slices ahead; they split a landed
 // slice into tf32 hi/lo and store it K-major with the 128-byte swizzle into a
 // double-buffered MMA stage; one thread issues 12 MMAs (4 K-steps of 8 x 3
 // products, M = N = 128) and commits them to the stage's mbarrier.
+//
+// Accumulation.  The tensor core's FP32 accumulator truncates each addition
+// relative to its own magnitude (measured on GB300: a 3xTF32 Gram diagonal
+// accumulated over 70,000 points in one TMEM accumulator came out 5.7e-4 too
+// small, the error growing linearly with the points summed).  So every
+// slice accumulates into a fresh TMEM accumulator (two, alternating), the
+// two small cross terms first, and the threads add the slice result into
+// FP32 registers (round to nearest) once its MMAs have completed: the bias
+// is that of one 32-point slice.
 // Every wait is bounded: on expiry the CTA sets an error flag, stops issuing
 // and still releases its TMEM.
 #include "hq_internal.cuh"
@@ -27,7 +36,7 @@ namespace hq {
 
 constexpr int TC_T = 128;        // output tile edge (M = N = 128)
 constexpr int TC_K = 32;         // points per slice (128 bytes of tf32 per row)
-constexpr int TC_THREADS = 128;  // 4 warps: each owns 32 TMEM lanes in the epilogue
+constexpr int TC_THREADS = 256;  // 8 warps; in the epilogue warp w reads TMEM lanes 32 (w % 4)
 constexpr int TC_TILE_BYTES = TC_T * TC_K * 4;   // 16 KB: one operand, one of hi / lo
 constexpr int TC_RAW = 3;                          // raw FP32 slices in flight (cp.async)
 constexpr int TC_RAW_BYTES = TC_K * TC_T * 4;      // 16 KB: one operand's raw slice
@@ -46,6 +55,25 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t da, uint64_t 
         "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
         "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+}
+
+// One 32-deep K slice of the 3xTF32 product hi hi^T + hi lo^T + lo hi^T into
+// a fresh accumulator d (shared-memory addresses of the four swizzled
+// K-major operand halves): the cross terms first, while the accumulator is
+// small, then hi hi^T.
+__device__ __forceinline__ void mma_slice_3xtf32(uint32_t d, uint32_t ahi, uint32_t alo,
+                                                 uint32_t bhi, uint32_t blo, uint32_t idesc) {
+#pragma unroll
+    for (int kk = 0; kk < TC_K / 8; kk++) {
+        const uint32_t ko = kk * 32;   // 8 tf32 = 32 bytes along K
+        mma_tf32(d, make_desc_sw128(ahi + ko), make_desc_sw128(blo + ko), idesc, kk > 0 ? 1u : 0u);
+        mma_tf32(d, make_desc_sw128(alo + ko), make_desc_sw128(bhi + ko), idesc, 1u);
+    }
+#pragma unroll
+    for (int kk = 0; kk < TC_K / 8; kk++) {
+        const uint32_t ko = kk * 32;
+        mma_tf32(d, make_desc_sw128(ahi + ko), make_desc_sw128(bhi + ko), idesc, 1u);
+    }
 }
 
 struct TcPlan {
@@ -98,19 +126,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base_sh)),
-                     "r"(TC_T)
+                     "r"(2 * TC_T)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = tmem_base_sh;
+    const uint32_t tmem = tmem_base_sh;   // accumulator of slice s: columns (s & 1) * 128 + 0..127
+    // this thread's share of the tile: row wl + lane (its TMEM lane), columns
+    // cbeg + 0..63, summed over the slices in FP32 registers
+    const int wl = (warp & 3) * 32, cbeg = (warp >> 2) * (TC_T / 2);
+    const uint32_t tl = tmem + ((uint32_t)wl << 16) + (uint32_t)cbeg;
+    float acc[TC_T / 2];
+#pragma unroll
+    for (int j = 0; j < TC_T / 2; j++) acc[j] = 0.f;
 
     // Raw FP32 slices (32 point rows x 128 columns, rows of 512 bytes) are
     // copied into shared memory with cp.async, three slices ahead of the one
     // being split, so the global-memory latency overlaps the split and the
-    // MMAs.  Thread t copies 16-byte chunks q = t + 128 j: row = q / 32,
+    // MMAs.  Thread t copies 16-byte chunks q = t + 256 j: row = q / 32,
     // column quad = q % 32; chunks the vector path cannot take (ragged rows
     // or columns, unaligned blocks) are written with plain loads and stores.
     unsigned char *raw = smem + 2 * 4 * TC_TILE_BYTES;   // TC_RAW stages x (A | B)
@@ -118,7 +153,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                       (((uintptr_t)X1 & 15) == 0) && (X2 == nullptr || ((uintptr_t)X2 & 15) == 0);
     auto issue_slice = [&](int sl, unsigned char *dst, int c0) {
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
+        for (int j = 0; j < TC_K * TC_T / 4 / TC_THREADS; j++) {
             const int q = tid + TC_THREADS * j;
             const int row = q >> 5, cq = (q & 31) * 4;
             const long p = r0 + (long)sl * TC_K + row;
@@ -148,7 +183,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     auto split_slice = [&](const unsigned char *src, unsigned char *hi, unsigned char *lo) {
         const float *rf = reinterpret_cast<const float *>(src);
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
+        for (int j = 0; j < TC_K * TC_T / 4 / TC_THREADS; j++) {
             const int q = tid + TC_THREADS * j;
             const int i = q & (TC_T - 1), kq = q >> 7;
             float h[4], l[4];
@@ -178,8 +213,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // slice s has landed once all but the TC_RAW - 1 newest groups are done
         asm volatile("cp.async.wait_group %0;" ::"n"(TC_RAW - 1) : "memory");
         if (s >= 2) {
-            if (!mbar_wait(&mbar[st], (unsigned)(((s - 2) >> 1) & 1))) atomicExch(&abort_sh, 1);
+            // the MMAs of slice s - 2 (this stage, this accumulator) are
+            // done: add their result into the registers (a warp-uniform
+            // decision: tcgen05.ld is a whole-warp instruction)
+            const bool done = __all_sync(0xffffffffu, mbar_wait(&mbar[st], (unsigned)(((s - 2) >> 1) & 1)));
+            if (!done) atomicExch(&abort_sh, 1);
+            else {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                tmem_add32<TC_T / 64>(tl + (uint32_t)(st * TC_T), acc);
+            }
         }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         if (abort_sh) break;
         const unsigned char *rs = raw + (size_t)(s % TC_RAW) * 2 * TC_RAW_BYTES;
@@ -191,46 +235,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         asm volatile("cp.async.commit_group;" ::: "memory");
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t ahi = smem_u32(Ahi), alo = smem_u32(Alo);
-            const uint32_t bhi = smem_u32(Bhi), blo = smem_u32(Blo);
-#pragma unroll
-            for (int kk = 0; kk < TC_K / 8; kk++) {
-                const uint32_t ko = kk * 32;   // 8 tf32 = 32 bytes along K
-                const uint64_t dah = make_desc_sw128(ahi + ko), dal = make_desc_sw128(alo + ko);
-                const uint64_t dbh = make_desc_sw128(bhi + ko), dbl = make_desc_sw128(blo + ko);
-                mma_tf32(tmem, dah, dbh, idesc, (s > 0 || kk > 0) ? 1u : 0u);
-                mma_tf32(tmem, dah, dbl, idesc, 1u);
-                mma_tf32(tmem, dal, dbh, idesc, 1u);
-            }
+            mma_slice_3xtf32(tmem + (uint32_t)(st * TC_T), smem_u32(Ahi), smem_u32(Alo),
+                             smem_u32(Bhi), smem_u32(Blo), idesc);
             mma_commit(&mbar[st]);
         }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
-    // wait for the last two commits (they complete in issue order)
+    // the last two slices (their MMAs complete in issue order): add them in
+    // slice order
     bool ok = !abort_sh;
     if (ok && nslices >= 1) {
-        int s = nslices - 1;
-        ok = mbar_wait(&mbar[s & 1], (unsigned)((s >> 1) & 1));
-        if (ok && nslices >= 2) {
-            s = nslices - 2;
-            ok = mbar_wait(&mbar[s & 1], (unsigned)((s >> 1) & 1));
-        }
+        const int s = nslices - 1;
+        ok = __all_sync(0xffffffffu, mbar_wait(&mbar[s & 1], (unsigned)((s >> 1) & 1)));
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (ok && nslices >= 2) tmem_add32<TC_T / 64>(tl + (uint32_t)(((s - 1) & 1) * TC_T), acc);
+        if (ok) tmem_add32<TC_T / 64>(tl + (uint32_t)((s & 1) * TC_T), acc);
     }
     if (!ok) atomicExch(&abort_sh, 1);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (abort_sh) {
         if (tid == 0) atomicOr(status, ST_TC_TIMEOUT);
     } else if (nslices > 0) {
-        // epilogue: warp w reads TMEM lanes 32w..32w+31 (tile rows), 32 columns at a time
-        float *dst = partials + ((size_t)blockIdx.y * P.ntiles + blockIdx.x) * TC_T * TC_T;
-        const int row = warp * 32 + lane;
-        for (int cb = 0; cb < TC_T; cb += 32) {
-            float v[32];
-            tmem_ld32<32>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+        float *dst = partials + ((size_t)blockIdx.y * P.ntiles + blockIdx.x) * TC_T * TC_T +
+                     (size_t)(wl + lane) * TC_T + cbeg;
 #pragma unroll
-            for (int j = 0; j < 32; j++) dst[(size_t)row * TC_T + cb + j] = v[j];
-        }
+        for (int j = 0; j < TC_T / 2; j += 4)
+            *reinterpret_cast<float4 *>(dst + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
     } else {
         float *dst = partials + ((size_t)blockIdx.y * P.ntiles + blockIdx.x) * TC_T * TC_T;
         for (int e = tid; e < TC_T * TC_T; e += TC_THREADS) dst[e] = 0.f;
@@ -238,7 +269,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_T)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(2 * TC_T)
                      : "memory");
 }
 
@@ -319,6 +351,11 @@ constexpr int TT_M = 128;
 // for two CTAs per SM
 template <int NT>
 __host__ __device__ constexpr int tt_raw() { return NT >= 128 ? 2 : 0; }
+// TMEM columns of one accumulator (a power of two, at least 32)
+template <int NT>
+__host__ __device__ constexpr uint32_t tt_cols() {
+    return NT <= 32 ? 32u : (NT <= 64 ? 64u : 128u);
+}
 
 struct TallTcPlan {
     long n;
@@ -333,10 +370,12 @@ TallTcPlan make_tall_tc_plan(long n, int k1, int k2, int ncol) {
     p.kpad = (k1 + k2 + TC_K - 1) / TC_K * TC_K;
     p.nslices = p.kpad / TC_K;
     p.ncol = ncol;
-    // instantiated tile widths (multiples of 16 up to the M = 128 limit of 256)
-    const int widths[6] = {16, 32, 48, 64, 128, 256};
-    p.nt = 256;
-    for (int i = 0; i < 6; i++)
+    // instantiated tile widths (multiples of 16); wider outputs take several
+    // 128-column tiles, whose CTAs run next to each other and share the A
+    // rows through L2 (two accumulators of NT columns per CTA, see the kernel)
+    const int widths[5] = {16, 32, 48, 64, 128};
+    p.nt = 128;
+    for (int i = 0; i < 5; i++)
         if (widths[i] >= ncol) {
             p.nt = widths[i];
             break;
@@ -383,53 +422,159 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
            ((uint32_t)(M >> 4) << 24);
 }
 
+constexpr int TT_THREADS = 256;   // 8 warps; warp w owns TMEM lanes 32 (w % 4) + 0..31
+
+// Out (n x ncol) = [A1 A2] [M1; M2] (+ Cin) for one 128-point row block and
+// one NT-column tile (blockIdx.x = row block x ctiles + column tile).  As in
+// the Gram kernel, each 32-deep K slice accumulates into a fresh TMEM
+// accumulator (two of NT columns, alternating) and the threads add the slice
+// result into FP32 registers: thread = point row (TMEM lane), NT / HALVES
+// columns (HALVES = 2 where NT is a multiple of 64: the two warp quartets
+// take one column half each).
+// two CTAs per SM where a thread sums at most 32 columns (register budget)
 template <int NT>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__host__ __device__ constexpr int tt_min_blocks() {
+    return (tt_raw<NT>() == 0 && (NT % 64 == 0 ? NT / 2 : NT) <= 32) ? 2 : 1;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(TT_THREADS, tt_min_blocks<NT>())
     k_tall_tf32x3(TallTcPlan P, const float *__restrict__ A1, const float *__restrict__ A2,
                   const unsigned char *__restrict__ image, const float *__restrict__ Cin,
                   float *__restrict__ Out, double *part_sq, int *status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t mbar[2];
+    __shared__ uint64_t mbar[2];    // MMAs of the stage completed
+    __shared__ uint64_t bfull[2];   // B image of the stage landed
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh;
-    __shared__ double red[TC_THREADS];
+    __shared__ double red[TT_THREADS / 32];
     constexpr int ABYTES = TT_M * 128;           // one operand half (hi or lo): 16 KB
-    constexpr int BBYTES = NT * 128;             // 32 KB for NT = 256
+    constexpr int BBYTES = NT * 128;             // 16 KB for NT = 128
     constexpr int STAGE = 2 * ABYTES + 2 * BBYTES;
-    constexpr uint32_t TCOLS = NT < 32 ? 32 : (NT <= 32 ? 32 : (NT <= 64 ? 64 : (NT <= 128 ? 128 : 256)));
+    constexpr int AQ = TT_M * TC_K / 4 / TT_THREADS;   // 16-byte A chunks per thread per slice
+    constexpr uint32_t TCOLS = tt_cols<NT>();
+    constexpr int HALVES = (NT % 64 == 0) ? 2 : 1;
+    constexpr int CW = NT / HALVES;                // columns per thread
+    constexpr int NCH = (CW + 31) / 32;            // 32-column TMEM loads per drain
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const long r0 = (long)blockIdx.x * TT_M;
-    const int ct = blockIdx.y;
+    const int ct = (int)(blockIdx.x % (unsigned)P.ctiles);
+    const long r0 = (long)(blockIdx.x / (unsigned)P.ctiles) * TT_M;
     if (tid == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
+        mbar_init(&bfull[0], 1);
+        mbar_init(&bfull[1], 1);
         abort_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base_sh)),
-                     "r"(TCOLS)
+                     "r"(2 * TCOLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = tmem_base_sh;
+    const uint32_t tmem = tmem_base_sh;   // accumulator of slice s: columns (s & 1) * TCOLS + ..
+    const int wl = (warp & 3) * 32, half = warp >> 2;
+    const bool owner = half < HALVES;      // warp-uniform
+    const uint32_t tl = tmem + ((uint32_t)wl << 16) + (uint32_t)(half * CW);
+    float acc[NCH * 32];
+#pragma unroll
+    for (int j = 0; j < NCH * 32; j++) acc[j] = 0.f;
+    // add the accumulator of slice sl (complete, warp-uniform) into acc
+    auto drain = [&](int sl) {
+        if (owner) tmem_add32<NCH>(tl + (uint32_t)((sl & 1) * TCOLS), acc);
+    };
     const bool vec4 = (P.k1 % 4 == 0) && (P.k2 % 4 == 0) && (((uintptr_t)A1 & 15) == 0) &&
                       (A2 == nullptr || ((uintptr_t)A2 & 15) == 0);
 
+    // The B image of a slice (hi | lo, 2 NT rows of 128 bytes, already split
+    // and swizzled) is one contiguous block: thread 0 copies it into the
+    // slice's MMA stage with one bulk (TMA) copy that completes on bfull,
+    // as soon as the MMAs of slice s - 2 that used the stage are done.
+    int b_issued = 0, b_landed = 0;   // thread 0's count of B copies
+    auto issue_b = [&](int sl) {
+        const unsigned char *src = image + ((size_t)ct * P.nslices + sl) * 2 * (size_t)BBYTES;
+        unsigned char *dst = smem + (sl & 1) * STAGE + 2 * ABYTES;
+        mbar_expect_tx(&bfull[sl & 1], 2 * BBYTES);
+        bulk_g2s(dst, src, 2 * BBYTES, &bfull[sl & 1]);
+        b_issued++;
+    };
+    // split four FP32 values into tf32 hi / lo: one 16-byte chunk of each
+    // swizzled row
+    auto put4 = [&](const float4 &v4, int row, int kq, unsigned char *hi, unsigned char *lo) {
+        const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+        float h[4], l[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            h[u] = tf32_rna(v[u]);
+            l[u] = tf32_rna(v[u] - h[u]);
+        }
+        const uint32_t off = sw128_offset(row, kq);
+        *reinterpret_cast<float4 *>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4 *>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
+    };
+    auto a_scalar = [&](long p, int k) {
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int kk = k + u;
+            v[u] = 0.f;
+            if (p < P.n && kk < P.k1) v[u] = A1[(size_t)p * P.k1 + kk];
+            else if (p < P.n && kk < P.k1 + P.k2) v[u] = A2[(size_t)p * P.k2 + (kk - P.k1)];
+        }
+        return make_float4(v[0], v[1], v[2], v[3]);
+    };
+    // thread 0: MMAs of slice s once its B image has landed, then the B copy
+    // of slice s + 1 into the other stage once the MMAs of s - 1 are done
+    const uint32_t idesc = idesc_tf32(TT_M, NT);
+    auto mma_slice = [&](int s, unsigned char *base) {
+        const int st = s & 1;
+        if (!mbar_wait(&bfull[st], (unsigned)((s >> 1) & 1))) {
+            atomicExch(&abort_sh, 1);
+            return;
+        }
+        b_landed++;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        mma_slice_3xtf32(tmem + (uint32_t)(st * TCOLS), smem_u32(base), smem_u32(base + ABYTES),
+                         smem_u32(base + 2 * ABYTES), smem_u32(base + 2 * ABYTES + BBYTES), idesc);
+        mma_commit(&mbar[st]);
+        if (s + 1 < P.nslices) {
+            if (s >= 1 && !mbar_wait(&mbar[st ^ 1], (unsigned)(((s - 1) >> 1) & 1))) {
+                atomicExch(&abort_sh, 1);
+                return;
+            }
+            issue_b(s + 1);
+        }
+    };
+    // every thread, before slice s reuses stage and accumulator s & 1: wait
+    // for the MMAs of slice s - 2 and add their result into the registers
+    auto retire = [&](int s) {
+        if (s < 2) return;
+        const bool done =
+            __all_sync(0xffffffffu, mbar_wait(&mbar[s & 1], (unsigned)(((s - 2) >> 1) & 1)));
+        if (!done) {
+            atomicExch(&abort_sh, 1);
+            return;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        drain(s - 2);
+    };
+
+    if (tid == 0 && P.nslices > 0) issue_b(0);
     if constexpr (tt_raw<NT>() == 0) {
-    // A slice: 128 points x 32 columns; thread t takes float4 q = t + 128 j:
-    // row = q / 8, column quad = (q % 8) * 4
-    float4 ra[8];
+    // A slice: 128 points x 32 columns, staged through registers; thread t
+    // takes the 16-byte chunks q = t + 256 j: row = q / 8, column quad = (q % 8) * 4
+    float4 ra[AQ];
     auto load_a = [&](int s) {
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-            const int q = tid + TC_THREADS * j;
+        for (int j = 0; j < AQ; j++) {
+            const int q = tid + TT_THREADS * j;
             const int row = q >> 3, kq = (q & 7) * 4;
             const long p = r0 + row;
             const int k = s * TC_K + kq;
@@ -438,90 +583,40 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                             : A2 + (size_t)p * P.k2 + (k - P.k1);
                 ra[j] = *reinterpret_cast<const float4 *>(src);
             } else {
-                float v[4];
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const int kk = k + u;
-                    v[u] = 0.f;
-                    if (p < P.n && kk < P.k1) v[u] = A1[(size_t)p * P.k1 + kk];
-                    else if (p < P.n && kk < P.k1 + P.k2) v[u] = A2[(size_t)p * P.k2 + (kk - P.k1)];
-                }
-                ra[j] = make_float4(v[0], v[1], v[2], v[3]);
+                ra[j] = a_scalar(p, k);
             }
         }
     };
-    auto store_a = [&](unsigned char *hi, unsigned char *lo) {
-#pragma unroll
-        for (int j = 0; j < 8; j++) {
-            const int q = tid + TC_THREADS * j;
-            const int row = q >> 3, kq = (q & 7) * 4;
-            const float v[4] = {ra[j].x, ra[j].y, ra[j].z, ra[j].w};
-            float h[4], l[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                h[u] = tf32_rna(v[u]);
-                l[u] = tf32_rna(v[u] - h[u]);
-            }
-            // the four values form one 16-byte chunk of the swizzled row
-            const uint32_t off = sw128_offset(row, kq);
-            *reinterpret_cast<float4 *>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
-            *reinterpret_cast<float4 *>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
-        }
-    };
-    auto copy_b = [&](int s, unsigned char *dst) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(
-            image + ((size_t)ct * P.nslices + s) * 2 * (size_t)BBYTES);
-        uint4 *d = reinterpret_cast<uint4 *>(dst);
-        for (int i = tid; i < 2 * BBYTES / 16; i += TC_THREADS) d[i] = src[i];
-    };
-
-    const uint32_t idesc = idesc_tf32(TT_M, NT);
     if (P.nslices > 0) load_a(0);
     for (int s = 0; s < P.nslices; s++) {
         const int st = s & 1;
         unsigned char *base = smem + st * STAGE;
-        unsigned char *Ahi = base, *Alo = base + ABYTES, *Bhi = base + 2 * ABYTES,
-                      *Blo = base + 2 * ABYTES + BBYTES;
-        if (s >= 2) {
-            if (!mbar_wait(&mbar[st], (unsigned)(((s - 2) >> 1) & 1))) atomicExch(&abort_sh, 1);
-        }
+        retire(s);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         if (abort_sh) break;
-        store_a(Ahi, Alo);
-        copy_b(s, Bhi);
+#pragma unroll
+        for (int j = 0; j < AQ; j++) {
+            const int q = tid + TT_THREADS * j;
+            put4(ra[j], q >> 3, (q & 7) * 4, base, base + ABYTES);
+        }
         if (s + 1 < P.nslices) load_a(s + 1);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t ahi = smem_u32(Ahi), alo = smem_u32(Alo);
-            const uint32_t bhi = smem_u32(Bhi), blo = smem_u32(Blo);
-#pragma unroll
-            for (int kk = 0; kk < TC_K / 8; kk++) {
-                const uint32_t ko = kk * 32;
-                const uint64_t dah = make_desc_sw128(ahi + ko), dal = make_desc_sw128(alo + ko);
-                const uint64_t dbh = make_desc_sw128(bhi + ko), dbl = make_desc_sw128(blo + ko);
-                mma_tf32(tmem, dah, dbh, idesc, (s > 0 || kk > 0) ? 1u : 0u);
-                mma_tf32(tmem, dah, dbl, idesc, 1u);
-                mma_tf32(tmem, dal, dbh, idesc, 1u);
-            }
-            mma_commit(&mbar[st]);
-        }
+        if (tid == 0) mma_slice(s, base);
     }
     } else {
     // A slices (128 points x 32 columns, rows of 128 bytes) are copied raw
-    // into shared memory with cp.async two slices ahead and split into tf32
-    // hi / lo from there; the B image of slice s + 1 is copied with cp.async
-    // straight into its MMA stage as soon as the MMAs of slice s - 1 that used
-    // the stage have completed.  Thread t copies / splits the 16-byte chunks
-    // q = t + 128 j: row = q / 8, column quad = (q % 8) * 4.
+    // into shared memory with cp.async TT_RAW slices ahead and split into
+    // tf32 hi / lo from there; thread t copies / splits the 16-byte chunks
+    // q = t + 256 j: row = q / 8, column quad = (q % 8) * 4.
     constexpr int TT_RAW = tt_raw<NT>();
     unsigned char *raw = smem + 2 * STAGE;   // TT_RAW slices x 16 KB
     auto issue_a = [&](int sl) {
         unsigned char *dst = raw + (size_t)(sl % TT_RAW) * ABYTES;
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-            const int q = tid + TC_THREADS * j;
+        for (int j = 0; j < AQ; j++) {
+            const int q = tid + TT_THREADS * j;
             const int row = q >> 3, kq = (q & 7) * 4;
             const long p = r0 + row;
             const int k = sl * TC_K + kq;
@@ -533,52 +628,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                              "l"(src)
                              : "memory");
             } else {
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const int kk = k + u;
-                    float v = 0.f;
-                    if (p < P.n && kk < P.k1) v = A1[(size_t)p * P.k1 + kk];
-                    else if (p < P.n && kk < P.k1 + P.k2) v = A2[(size_t)p * P.k2 + (kk - P.k1)];
-                    d[u] = v;
-                }
+                *reinterpret_cast<float4 *>(d) = a_scalar(p, k);
             }
         }
-    };
-    auto split_a = [&](int sl, unsigned char *hi, unsigned char *lo) {
-        const unsigned char *src = raw + (size_t)(sl % TT_RAW) * ABYTES;
-#pragma unroll
-        for (int j = 0; j < 8; j++) {
-            const int q = tid + TC_THREADS * j;
-            const int row = q >> 3, kq = (q & 7) * 4;
-            const float4 v4 = *reinterpret_cast<const float4 *>(src + row * 128 + kq * 4);
-            const float v[4] = {v4.x, v4.y, v4.z, v4.w};
-            float h[4], l[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                h[u] = tf32_rna(v[u]);
-                l[u] = tf32_rna(v[u] - h[u]);
-            }
-            // the four values form one 16-byte chunk of the swizzled row
-            const uint32_t off = sw128_offset(row, kq);
-            *reinterpret_cast<float4 *>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
-            *reinterpret_cast<float4 *>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
-        }
-    };
-    auto issue_b = [&](int sl) {
-        const unsigned char *src =
-            image + ((size_t)ct * P.nslices + sl) * 2 * (size_t)BBYTES;
-        unsigned char *dst = smem + (sl & 1) * STAGE + 2 * ABYTES;
-        for (int i = tid; i < 2 * BBYTES / 16; i += TC_THREADS)
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst + 16 * i)),
-                         "l"(src + 16 * (size_t)i)
-                         : "memory");
     };
     auto commit = [&]() { asm volatile("cp.async.commit_group;" ::: "memory"); };
-
-    const uint32_t idesc = idesc_tf32(TT_M, NT);
-    // prologue: B(0) | A(0) | A(1)
-    if (P.nslices > 0) issue_b(0);
-    commit();
     for (int sl = 0; sl < TT_RAW; sl++) {
         if (sl < P.nslices) issue_a(sl);
         commit();
@@ -586,116 +640,112 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int s = 0; s < P.nslices; s++) {
         const int st = s & 1;
         unsigned char *base = smem + st * STAGE;
-        unsigned char *Ahi = base, *Alo = base + ABYTES, *Bhi = base + 2 * ABYTES,
-                      *Blo = base + 2 * ABYTES + BBYTES;
-        // B(s) and A(s) have landed once only the newest TT_RAW - 1 groups
-        // (A(s + 1)) may still be in flight
+        // A(s) has landed once only the newest TT_RAW - 1 groups may still
+        // be in flight
         asm volatile("cp.async.wait_group %0;" ::"n"(TT_RAW - 1) : "memory");
+        retire(s);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         if (abort_sh) break;
-        split_a(s, Ahi, Alo);
+        const unsigned char *src = raw + (size_t)(s % TT_RAW) * ABYTES;
+#pragma unroll
+        for (int j = 0; j < AQ; j++) {
+            const int q = tid + TT_THREADS * j;
+            const int row = q >> 3, kq = (q & 7) * 4;
+            put4(*reinterpret_cast<const float4 *>(src + row * 128 + kq * 4), row, kq, base,
+                 base + ABYTES);
+        }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t ahi = smem_u32(Ahi), alo = smem_u32(Alo);
-            const uint32_t bhi = smem_u32(Bhi), blo = smem_u32(Blo);
-#pragma unroll
-            for (int kk = 0; kk < TC_K / 8; kk++) {
-                const uint32_t ko = kk * 32;
-                const uint64_t dah = make_desc_sw128(ahi + ko), dal = make_desc_sw128(alo + ko);
-                const uint64_t dbh = make_desc_sw128(bhi + ko), dbl = make_desc_sw128(blo + ko);
-                mma_tf32(tmem, dah, dbh, idesc, (s > 0 || kk > 0) ? 1u : 0u);
-                mma_tf32(tmem, dah, dbl, idesc, 1u);
-                mma_tf32(tmem, dal, dbh, idesc, 1u);
-            }
-            mma_commit(&mbar[st]);
-        }
-        // the other stage is free once the MMAs of slice s - 1 are done: copy
-        // B(s + 1) there, and A(s + 2) into the raw slot A(s) just left
-        if (s >= 1) {
-            if (!mbar_wait(&mbar[st ^ 1], (unsigned)(((s - 1) >> 1) & 1))) atomicExch(&abort_sh, 1);
-        }
-        if (s + 1 < P.nslices) issue_b(s + 1);
-        commit();
+        // the raw slot of A(s) is free again: copy A(s + TT_RAW) into it
         if (s + TT_RAW < P.nslices) issue_a(s + TT_RAW);
         commit();
+        if (tid == 0) mma_slice(s, base);
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
+    // the last two slices (their MMAs complete in issue order), in slice order
     bool ok = !abort_sh;
     if (ok && P.nslices >= 1) {
-        int s = P.nslices - 1;
-        ok = mbar_wait(&mbar[s & 1], (unsigned)((s >> 1) & 1));
-        // the register-staged variant has not yet waited for slice n - 2
-        if (tt_raw<NT>() == 0 && ok && P.nslices >= 2) {
-            s = P.nslices - 2;
-            ok = mbar_wait(&mbar[s & 1], (unsigned)((s >> 1) & 1));
-        }
+        const int s = P.nslices - 1;
+        ok = __all_sync(0xffffffffu, mbar_wait(&mbar[s & 1], (unsigned)((s >> 1) & 1)));
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (ok && s >= 1) drain(s - 1);
+        if (ok) drain(s);
     }
     if (!ok) atomicExch(&abort_sh, 1);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // B copies still in flight after an abort: wait for them (bounded)
+    if (tid == 0)
+        for (; b_landed < b_issued; b_landed++)
+            if (!mbar_wait(&bfull[b_landed & 1], (unsigned)((b_landed >> 1) & 1))) break;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     double sq = 0.0;
     if (abort_sh) {
         if (tid == 0) atomicOr(status, ST_TC_TIMEOUT);
-    } else {
-        // epilogue: thread = one point row (TMEM lane), 32 columns per load;
+    } else if (owner) {
+        // epilogue: row r0 + wl + lane, columns ct NT + half CW + 0..CW-1;
         // 16-byte loads / stores where the row segment allows, squares summed
-        // in FP32 per 32 columns and in FP64 across segments (only when the
-        // sum of squares is requested)
-        const long p = r0 + warp * 32 + lane;
+        // in FP32 per 32 columns and in FP64 across them (only when the sum
+        // of squares is requested)
+        const long p = r0 + wl + lane;
         const bool v4 = (P.ncol % 4 == 0) && (((uintptr_t)Out & 15) == 0) &&
                         (((uintptr_t)Cin & 15) == 0);
-        for (int cb = 0; cb < NT; cb += 32) {
-            float v[32];
-            tmem_ld32<32>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
-            if (p >= P.n) continue;
-            const int c0 = ct * NT + cb;
-            float sqf = 0.f;
-            if (v4 && cb + 32 <= NT && c0 + 32 <= P.ncol) {
-                const size_t e0 = (size_t)p * P.ncol + c0;
+        if (p < P.n) {
 #pragma unroll
-                for (int j = 0; j < 32; j += 4) {
-                    float4 o = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-                    if (Cin) {
-                        const float4 ci = *reinterpret_cast<const float4 *>(Cin + e0 + j);
-                        o.x += ci.x;
-                        o.y += ci.y;
-                        o.z += ci.z;
-                        o.w += ci.w;
+            for (int c = 0; c < NCH; c++) {
+                const int cb = half * CW + c * 32;   // column within the tile
+                const int c0 = ct * NT + cb;
+                float sqf = 0.f;
+                if (v4 && c * 32 + 32 <= CW && c0 + 32 <= P.ncol) {
+                    const size_t e0 = (size_t)p * P.ncol + c0;
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4) {
+                        float4 o = make_float4(acc[c * 32 + j], acc[c * 32 + j + 1],
+                                               acc[c * 32 + j + 2], acc[c * 32 + j + 3]);
+                        if (Cin) {
+                            const float4 ci = *reinterpret_cast<const float4 *>(Cin + e0 + j);
+                            o.x += ci.x;
+                            o.y += ci.y;
+                            o.z += ci.z;
+                            o.w += ci.w;
+                        }
+                        if (Out) *reinterpret_cast<float4 *>(Out + e0 + j) = o;
+                        if (part_sq) sqf += (o.x * o.x + o.y * o.y) + (o.z * o.z + o.w * o.w);
                     }
-                    if (Out) *reinterpret_cast<float4 *>(Out + e0 + j) = o;
-                    if (part_sq) sqf += (o.x * o.x + o.y * o.y) + (o.z * o.z + o.w * o.w);
-                }
-            } else {
+                } else {
 #pragma unroll
-                for (int j = 0; j < 32; j++) {
-                    const int c = c0 + j;
-                    if (cb + j >= NT || c >= P.ncol) continue;
-                    const size_t e = (size_t)p * P.ncol + c;
-                    float o = v[j];
-                    if (Cin) o += Cin[e];
-                    if (Out) Out[e] = o;
-                    if (part_sq) sqf += o * o;
+                    for (int j = 0; j < 32; j++) {
+                        const int c1 = c0 + j;
+                        if (c * 32 + j >= CW || c1 >= P.ncol) continue;
+                        const size_t e = (size_t)p * P.ncol + c1;
+                        float o = acc[c * 32 + j];
+                        if (Cin) o += Cin[e];
+                        if (Out) Out[e] = o;
+                        if (part_sq) sqf += o * o;
+                    }
                 }
+                if (part_sq) sq += (double)sqf;
             }
-            if (part_sq) sq += (double)sqf;
         }
     }
     if (part_sq) {
-        red[tid] = sq;
+        // fixed butterfly within each warp, then the warps in order
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if (lane == 0) red[warp] = sq;
         __syncthreads();
-        for (int k = TC_THREADS / 2; k > 0; k >>= 1) {
-            if (tid < k) red[tid] += red[tid + k];
-            __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < TT_THREADS / 32; w++) t += red[w];
+            part_sq[blockIdx.x] = t;
         }
-        if (tid == 0) part_sq[(size_t)blockIdx.x * gridDim.y + blockIdx.y] = red[0];
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(2 * TCOLS)
                      : "memory");
 }
 
@@ -705,9 +755,9 @@ static void run_tall_tc(const TallTcPlan &p, const float *A1, const float *A2,
                         int *status, cudaStream_t s) {
     const int smem = 2 * (2 * TT_M * 128 + 2 * NT * 128) + tt_raw<NT>() * TT_M * 128 + 1024;
     tc_prepare();
-    const unsigned gx = (unsigned)((p.n + TT_M - 1) / TT_M);
+    const unsigned gx = (unsigned)((p.n + TT_M - 1) / TT_M * p.ctiles);
     HQ_LAUNCH(HQ_K_BLOCKGEMM,
-              k_tall_tf32x3<NT><<<dim3(gx, p.ctiles), TC_THREADS, smem, s>>>(p, A1, A2, image, Cin,
+              k_tall_tf32x3<NT><<<gx, TT_THREADS, smem, s>>>(p, A1, A2, image, Cin,
                                                                              Out, part_sq, status));
 }
 
@@ -727,7 +777,6 @@ void tc_prepare() {
     prep_tall<48>();
     prep_tall<64>();
     prep_tall<128>();
-    prep_tall<256>();
     done = true;
 }
 
@@ -749,7 +798,6 @@ void launch_tall_tc(long n, const float *A1, int k1, const double *M1, const flo
     case 48: run_tall_tc<48>(p, A1, A2, image, Cin, Out, part_sq, status, s); break;
     case 64: run_tall_tc<64>(p, A1, A2, image, Cin, Out, part_sq, status, s); break;
     case 128: run_tall_tc<128>(p, A1, A2, image, Cin, Out, part_sq, status, s); break;
-    case 256: run_tall_tc<256>(p, A1, A2, image, Cin, Out, part_sq, status, s); break;
     }
 }
 

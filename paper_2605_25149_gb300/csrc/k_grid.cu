@@ -121,8 +121,10 @@ __device__ __forceinline__ VT<T, V> nbr_sum(const T *__restrict__ x, size_t e, i
 // ---------------------------------------------------------------------------
 // 7-point operator.  MODE 0: y = A x (+ x.y);  MODE 1: y = b - A x (+ y.y, b.b)
 // A x = D x - c (x_w + x_e + x_s + x_n + x_b + x_t),  D = 6c + V + sigma.
+// PART: form the partial sums (a compile-time switch: in FP64 the extra
+// products are a measurable share of the FP64-pipe work of a sweep).
 // ---------------------------------------------------------------------------
-template <typename T, int V, int MODE>
+template <typename T, int V, int MODE, bool PART>
 __global__ void __launch_bounds__(256) k_stencil(int m, long n, int N, int ppt,
                                                  const T *__restrict__ D, T c,
                                                  const T *__restrict__ x,
@@ -155,17 +157,21 @@ __global__ void __launch_bounds__(256) k_stencil(int m, long n, int N, int ppt,
 #pragma unroll
             for (int v = 0; v < V; v++) {
                 o.v[v] = bb.v[v] - o.v[v];
-                a1[v] += o.v[v] * o.v[v];
-                a2[v] += bb.v[v] * bb.v[v];
+                if (PART) {
+                    a1[v] += o.v[v] * o.v[v];
+                    a2[v] += bb.v[v] * bb.v[v];
+                }
             }
-        } else {
+        } else if (PART) {
 #pragma unroll
             for (int v = 0; v < V; v++) a1[v] += xc.v[v] * o.v[v];
         }
         stv<T, V>(y + e, o);
     }
-    if (part1) block_col_reduce<V, T>(a1, red, part1, N, col, cv);
-    if (MODE == 1 && part2) block_col_reduce<V, T>(a2, red, part2, N, col, cv);
+    if (PART) {
+        block_col_reduce<V, T>(a1, red, part1, N, col, cv);
+        if (MODE == 1 && part2) block_col_reduce<V, T>(a2, red, part2, N, col, cv);
+    }
 }
 
 // x += alpha p; r -= alpha q; partial r.r; optional zf = wD r
@@ -236,8 +242,8 @@ __global__ void __launch_bounds__(256) k_pcg_p(long n, int N, int ppt,
 }
 
 // z_out = z_in + wD (r - A z_in) = (1 - omega) z_in + wD (r + c * nbrsum(z_in))
-// (wD = omega / D, so wD * D = omega); optional partial r.z_out.
-template <typename T, int V>
+// (wD = omega / D, so wD * D = omega); PART: partial r.z_out.
+template <typename T, int V, bool PART>
 __global__ void __launch_bounds__(256) k_jacobi(int m, long n, int N, int ppt,
                                                 const T *__restrict__ wD, T c, T omw,
                                                 const T *__restrict__ r,
@@ -265,11 +271,11 @@ __global__ void __launch_bounds__(256) k_jacobi(int m, long n, int N, int ppt,
 #pragma unroll
         for (int v = 0; v < V; v++) {
             o.v[v] = omw * zc.v[v] + w * (rv.v[v] + c * s.v[v]);
-            acc[v] += rv.v[v] * o.v[v];
+            if (PART) acc[v] += rv.v[v] * o.v[v];
         }
         stv<T, V>(zout + e, o);
     }
-    if (part) block_col_reduce<V, T>(acc, red, part, N, col, cv);
+    if (PART) block_col_reduce<V, T>(acc, red, part, N, col, cv);
 }
 
 // The same sweep with z-marching CTAs for blocks larger than L2: a CTA owns
@@ -277,96 +283,126 @@ __global__ void __launch_bounds__(256) k_jacobi(int m, long n, int N, int ppt,
 // the z-1, z, z+1 values of its points in registers, so the z-neighbours are
 // read once from memory instead of being re-read from other CTAs' rows.  The
 // six-neighbour sum is formed in the same order with the same zero masks as
-// nbr_sum, so results are bit-identical to k_jacobi.  No partial sums (the
-// sweep that also forms r.z uses k_jacobi).
-template <typename T, int V>
+// nbr_sum, so the swept values are bit-identical to k_jacobi.  The optional
+// partial r.z is reduced over the CTA's points (one partial row per CTA:
+// part_rows() rows in all), so its summation order differs from k_jacobi's.
+template <typename T, int V, bool PART>
 __global__ void __launch_bounds__(256) k_jacobi_zm(int m, int N, int nseg, int mz,
                                                    const T *__restrict__ wD, T c, T omw,
                                                    const T *__restrict__ r,
                                                    const T *__restrict__ zin,
-                                                   T *__restrict__ zout) {
+                                                   T *__restrict__ zout, double *part) {
+    __shared__ double red[1024];
     const int TY = blockDim.y;
     const int col = (blockIdx.x * blockDim.x + threadIdx.x) * V;
-    if (col >= N) return;
+    const bool cv = col < N;
     const int b = blockIdx.y;
     const int seg = b % nseg, rest = b / nseg;
     const int j = rest % m, zc = rest / m;
     const int i = seg * TY + threadIdx.y;
-    if (i >= m) return;
     const int k0 = zc * mz, k1 = min(m, k0 + mz);
-    if (k0 >= k1) return;
-    const size_t sx = (size_t)N, sy = (size_t)m * N, sz = (size_t)m * m * N;
-    long p = i + (long)m * (j + (long)m * k0);
-    size_t e = (size_t)p * N + col;
-    const bool bw = i > 0, be = i < m - 1, bs = j > 0, bn = j < m - 1;
-    VT<T, V> zero;
+    T acc[V];
 #pragma unroll
-    for (int v = 0; v < V; v++) zero.v[v] = T(0);
-    VT<T, V> zcur = ldv<T, V>(zin + e);
-    VT<T, V> zprev = k0 > 0 ? ldv<T, V>(zin + e - sz) : zero;
-    for (int kk = k0; kk < k1; kk++, e += sz, p += (long)m * m) {
-        VT<T, V> znext = kk + 1 < m ? ldv<T, V>(zin + e + sz) : zero;
-        VT<T, V> a0 = ldv<T, V>(zin + (bw ? e - sx : e)), a1 = ldv<T, V>(zin + (be ? e + sx : e));
-        VT<T, V> a2 = ldv<T, V>(zin + (bs ? e - sy : e)), a3 = ldv<T, V>(zin + (bn ? e + sy : e));
-        VT<T, V> rv = ldv<T, V>(r + e);
-        const T w = wD[p];
-        VT<T, V> o;
+    for (int v = 0; v < V; v++) acc[v] = T(0);
+    if (cv && i < m && k0 < k1) {
+        const size_t sx = (size_t)N, sy = (size_t)m * N, sz = (size_t)m * m * N;
+        long p = i + (long)m * (j + (long)m * k0);
+        size_t e = (size_t)p * N + col;
+        const bool bw = i > 0, be = i < m - 1, bs = j > 0, bn = j < m - 1;
+        VT<T, V> zero;
 #pragma unroll
-        for (int v = 0; v < V; v++) {
-            const T sum = (((bw ? a0.v[v] : T(0)) + (be ? a1.v[v] : T(0))) +
-                           ((bs ? a2.v[v] : T(0)) + (bn ? a3.v[v] : T(0)))) +
-                          (zprev.v[v] + znext.v[v]);
-            o.v[v] = omw * zcur.v[v] + w * (rv.v[v] + c * sum);
+        for (int v = 0; v < V; v++) zero.v[v] = T(0);
+        VT<T, V> zcur = ldv<T, V>(zin + e);
+        VT<T, V> zprev = k0 > 0 ? ldv<T, V>(zin + e - sz) : zero;
+        for (int kk = k0; kk < k1; kk++, e += sz, p += (long)m * m) {
+            VT<T, V> znext = kk + 1 < m ? ldv<T, V>(zin + e + sz) : zero;
+            VT<T, V> a0 = ldv<T, V>(zin + (bw ? e - sx : e)), a1 = ldv<T, V>(zin + (be ? e + sx : e));
+            VT<T, V> a2 = ldv<T, V>(zin + (bs ? e - sy : e)), a3 = ldv<T, V>(zin + (bn ? e + sy : e));
+            VT<T, V> rv = ldv<T, V>(r + e);
+            const T w = wD[p];
+            VT<T, V> o;
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                const T sum = (((bw ? a0.v[v] : T(0)) + (be ? a1.v[v] : T(0))) +
+                               ((bs ? a2.v[v] : T(0)) + (bn ? a3.v[v] : T(0)))) +
+                              (zprev.v[v] + znext.v[v]);
+                o.v[v] = omw * zcur.v[v] + w * (rv.v[v] + c * sum);
+                if (PART) acc[v] += rv.v[v] * o.v[v];
+            }
+            stv<T, V>(zout + e, o);
+            zprev = zcur;
+            zcur = znext;
         }
-        stv<T, V>(zout + e, o);
-        zprev = zcur;
-        zcur = znext;
     }
+    if (PART) block_col_reduce<V, T>(acc, red, part, N, col, cv);
 }
 
-// Residual y = b - A x with the z-marching CTAs of k_jacobi_zm (no partial
-// sums); the neighbour sum and the expression are those of k_stencil<T,V,1>.
-template <typename T, int V>
-__global__ void __launch_bounds__(256) k_resid_zm(int m, int N, int nseg, int mz,
-                                                  const T *__restrict__ D, T c,
-                                                  const T *__restrict__ x,
-                                                  const T *__restrict__ b, T *__restrict__ y) {
+// The 7-point operator of k_stencil (MODE 0: y = A x with partial x.y;
+// MODE 1: y = b - A x with partials y.y and b.b) on the z-marching CTAs of
+// k_jacobi_zm: the same element values, partials reduced per CTA.
+template <typename T, int V, int MODE, bool PART>
+__global__ void __launch_bounds__(256) k_stencil_zm(int m, int N, int nseg, int mz,
+                                                    const T *__restrict__ D, T c,
+                                                    const T *__restrict__ x,
+                                                    const T *__restrict__ b, T *__restrict__ y,
+                                                    double *part1, double *part2) {
+    __shared__ double red[1024];
     const int TY = blockDim.y;
     const int col = (blockIdx.x * blockDim.x + threadIdx.x) * V;
-    if (col >= N) return;
+    const bool cv = col < N;
     const int bl = blockIdx.y;
     const int seg = bl % nseg, rest = bl / nseg;
     const int j = rest % m, zc = rest / m;
     const int i = seg * TY + threadIdx.y;
-    if (i >= m) return;
     const int k0 = zc * mz, k1 = min(m, k0 + mz);
-    if (k0 >= k1) return;
-    const size_t sx = (size_t)N, sy = (size_t)m * N, sz = (size_t)m * m * N;
-    long p = i + (long)m * (j + (long)m * k0);
-    size_t e = (size_t)p * N + col;
-    const bool bw = i > 0, be = i < m - 1, bs = j > 0, bn = j < m - 1;
-    VT<T, V> zero;
+    T s1[V], s2[V];
 #pragma unroll
-    for (int v = 0; v < V; v++) zero.v[v] = T(0);
-    VT<T, V> xcur = ldv<T, V>(x + e);
-    VT<T, V> xprev = k0 > 0 ? ldv<T, V>(x + e - sz) : zero;
-    for (int kk = k0; kk < k1; kk++, e += sz, p += (long)m * m) {
-        VT<T, V> xnext = kk + 1 < m ? ldv<T, V>(x + e + sz) : zero;
-        VT<T, V> a0 = ldv<T, V>(x + (bw ? e - sx : e)), a1 = ldv<T, V>(x + (be ? e + sx : e));
-        VT<T, V> a2 = ldv<T, V>(x + (bs ? e - sy : e)), a3 = ldv<T, V>(x + (bn ? e + sy : e));
-        VT<T, V> bb = ldv<T, V>(b + e);
-        const T d = D[p];
-        VT<T, V> o;
+    for (int v = 0; v < V; v++) s1[v] = s2[v] = T(0);
+    if (cv && i < m && k0 < k1) {
+        const size_t sx = (size_t)N, sy = (size_t)m * N, sz = (size_t)m * m * N;
+        long p = i + (long)m * (j + (long)m * k0);
+        size_t e = (size_t)p * N + col;
+        const bool bw = i > 0, be = i < m - 1, bs = j > 0, bn = j < m - 1;
+        VT<T, V> zero;
 #pragma unroll
-        for (int v = 0; v < V; v++) {
-            const T sum = (((bw ? a0.v[v] : T(0)) + (be ? a1.v[v] : T(0))) +
-                           ((bs ? a2.v[v] : T(0)) + (bn ? a3.v[v] : T(0)))) +
-                          (xprev.v[v] + xnext.v[v]);
-            o.v[v] = bb.v[v] - (d * xcur.v[v] - c * sum);
+        for (int v = 0; v < V; v++) zero.v[v] = T(0);
+        VT<T, V> xcur = ldv<T, V>(x + e);
+        VT<T, V> xprev = k0 > 0 ? ldv<T, V>(x + e - sz) : zero;
+        for (int kk = k0; kk < k1; kk++, e += sz, p += (long)m * m) {
+            VT<T, V> xnext = kk + 1 < m ? ldv<T, V>(x + e + sz) : zero;
+            VT<T, V> a0 = ldv<T, V>(x + (bw ? e - sx : e)), a1 = ldv<T, V>(x + (be ? e + sx : e));
+            VT<T, V> a2 = ldv<T, V>(x + (bs ? e - sy : e)), a3 = ldv<T, V>(x + (bn ? e + sy : e));
+            const T d = D[p];
+            VT<T, V> o;
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                const T sum = (((bw ? a0.v[v] : T(0)) + (be ? a1.v[v] : T(0))) +
+                               ((bs ? a2.v[v] : T(0)) + (bn ? a3.v[v] : T(0)))) +
+                              (xprev.v[v] + xnext.v[v]);
+                o.v[v] = d * xcur.v[v] - c * sum;
+            }
+            if (MODE == 1) {
+                VT<T, V> bb = ldv<T, V>(b + e);
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    o.v[v] = bb.v[v] - o.v[v];
+                    if (PART) {
+                        s1[v] += o.v[v] * o.v[v];
+                        s2[v] += bb.v[v] * bb.v[v];
+                    }
+                }
+            } else if (PART) {
+#pragma unroll
+                for (int v = 0; v < V; v++) s1[v] += xcur.v[v] * o.v[v];
+            }
+            stv<T, V>(y + e, o);
+            xprev = xcur;
+            xcur = xnext;
         }
-        stv<T, V>(y + e, o);
-        xprev = xcur;
-        xcur = xnext;
+    }
+    if (PART) {
+        block_col_reduce<V, T>(s1, red, part1, N, col, cv);
+        if (MODE == 1 && part2) block_col_reduce<V, T>(s2, red, part2, N, col, cv);
     }
 }
 
@@ -965,11 +1001,39 @@ static inline dim3 grd(const GridGeom &g) { return dim3(g.gx, g.gy); }
         else KERNEL<T, 1>(__VA_ARGS__);                                           \
     } while (0)
 
+// z-marching launch shape: nseg x-segments of TY points per y-row, m rows,
+// zch z-chunks of mz planes; one CTA (and one partial row) per (segment,
+// row, chunk)
+static inline int zm_segments(const GridGeom &g) { return (g.m + g.ty - 1) / g.ty; }
+static inline int zm_planes(const GridGeom &g) { return (g.m + g.zch - 1) / g.zch; }
+static inline dim3 zm_grid(const GridGeom &g) {
+    return dim3(g.gx, (unsigned)(zm_segments(g) * g.m * g.zch));
+}
+
+int part_rows(const GridGeom &g) {
+    return g.zch > 0 ? zm_segments(g) * g.m * g.zch : g.gy;
+}
+
 template <typename T, int V>
 static void run_apply(const GridGeom &g, const T *D, T c, const T *x, T *y, double *part,
                       cudaStream_t s) {
-    HQ_LAUNCH_W(HQ_K_STENCIL, (double)g.n * g.N, k_stencil<T, V, 0><<<grd(g), blk(g), 0, s>>>(g.m, g.n, g.N, g.ppt, D, c, x, nullptr, y,
-                                                  part, nullptr));
+    const double el = (double)g.n * g.N;
+    if (g.zch > 0) {
+        const int ns = zm_segments(g), mz = zm_planes(g);
+        if (part)
+            HQ_LAUNCH_W(HQ_K_STENCIL, el, k_stencil_zm<T, V, 0, true><<<zm_grid(g), blk(g), 0, s>>>(
+                                              g.m, g.N, ns, mz, D, c, x, nullptr, y, part, nullptr));
+        else
+            HQ_LAUNCH_W(HQ_K_STENCIL, el, k_stencil_zm<T, V, 0, false><<<zm_grid(g), blk(g), 0, s>>>(
+                                              g.m, g.N, ns, mz, D, c, x, nullptr, y, part, nullptr));
+        return;
+    }
+    if (part)
+        HQ_LAUNCH_W(HQ_K_STENCIL, el, k_stencil<T, V, 0, true><<<grd(g), blk(g), 0, s>>>(
+                                          g.m, g.n, g.N, g.ppt, D, c, x, nullptr, y, part, nullptr));
+    else
+        HQ_LAUNCH_W(HQ_K_STENCIL, el, k_stencil<T, V, 0, false><<<grd(g), blk(g), 0, s>>>(
+                                          g.m, g.n, g.N, g.ppt, D, c, x, nullptr, y, part, nullptr));
 }
 template <typename T>
 void launch_apply(const GridGeom &g, const T *D, T c, const T *x, T *y, double *part_xy,
@@ -980,22 +1044,31 @@ void launch_apply(const GridGeom &g, const T *D, T c, const T *x, T *y, double *
 template <typename T, int V>
 static void run_resid(const GridGeom &g, const T *D, T c, const T *x, const T *b, T *y,
                       double *p1, double *p2, cudaStream_t s) {
-    HQ_LAUNCH_W(HQ_K_RESIDUAL, (double)g.n * g.N, k_stencil<T, V, 1><<<grd(g), blk(g), 0, s>>>(g.m, g.n, g.N, g.ppt, D, c, x, b, y, p1, p2));
+    const double el = (double)g.n * g.N;
+    if (p1)
+        HQ_LAUNCH_W(HQ_K_RESIDUAL, el, k_stencil<T, V, 1, true><<<grd(g), blk(g), 0, s>>>(
+                                           g.m, g.n, g.N, g.ppt, D, c, x, b, y, p1, p2));
+    else
+        HQ_LAUNCH_W(HQ_K_RESIDUAL, el, k_stencil<T, V, 1, false><<<grd(g), blk(g), 0, s>>>(
+                                           g.m, g.n, g.N, g.ppt, D, c, x, b, y, p1, p2));
 }
 template <typename T, int V>
 static void run_resid_zm(const GridGeom &g, const T *D, T c, const T *x, const T *b, T *y,
-                         cudaStream_t s) {
-    const int nseg = (g.m + g.ty - 1) / g.ty;
-    const int mz = (g.m + g.zch - 1) / g.zch;
-    const dim3 grid(g.gx, (unsigned)(nseg * g.m * g.zch));
-    HQ_LAUNCH_W(HQ_K_RESIDUAL, (double)g.n * g.N,
-                k_resid_zm<T, V><<<grid, blk(g), 0, s>>>(g.m, g.N, nseg, mz, D, c, x, b, y));
+                         double *p1, double *p2, cudaStream_t s) {
+    const double el = (double)g.n * g.N;
+    const int ns = zm_segments(g), mz = zm_planes(g);
+    if (p1)
+        HQ_LAUNCH_W(HQ_K_RESIDUAL, el, k_stencil_zm<T, V, 1, true><<<zm_grid(g), blk(g), 0, s>>>(
+                                           g.m, g.N, ns, mz, D, c, x, b, y, p1, p2));
+    else
+        HQ_LAUNCH_W(HQ_K_RESIDUAL, el, k_stencil_zm<T, V, 1, false><<<zm_grid(g), blk(g), 0, s>>>(
+                                           g.m, g.N, ns, mz, D, c, x, b, y, p1, p2));
 }
 template <typename T>
 void launch_resid(const GridGeom &g, const T *D, T c, const T *x, const T *b, T *y,
                   double *part_yy, double *part_bb, cudaStream_t s) {
-    if (g.zch > 0 && !part_yy && !part_bb) {
-        HQ_VEC_DISPATCH(T, g, run_resid_zm, g, D, c, x, b, y, s);
+    if (g.zch > 0) {
+        HQ_VEC_DISPATCH(T, g, run_resid_zm, g, D, c, x, b, y, part_yy, part_bb, s);
         return;
     }
     HQ_VEC_DISPATCH(T, g, run_resid, g, D, c, x, b, y, part_yy, part_bb, s);
@@ -1025,25 +1098,32 @@ void launch_pcg_p(const GridGeom &g, const double *beta, const T *z, T *p, cudaS
 template <typename T, int V>
 static void run_jacobi(const GridGeom &g, const T *wD, T c, T omw, const T *r, const T *zin,
                        T *zout, double *part, cudaStream_t s) {
-    HQ_LAUNCH_W(HQ_K_SMOOTH, (double)g.n * g.N, k_jacobi<T, V><<<grd(g), blk(g), 0, s>>>(g.m, g.n, g.N, g.ppt, wD, c, omw, r, zin, zout,
-                                             part));
+    const double el = (double)g.n * g.N;
+    if (part)
+        HQ_LAUNCH_W(HQ_K_SMOOTH, el, k_jacobi<T, V, true><<<grd(g), blk(g), 0, s>>>(
+                                         g.m, g.n, g.N, g.ppt, wD, c, omw, r, zin, zout, part));
+    else
+        HQ_LAUNCH_W(HQ_K_SMOOTH, el, k_jacobi<T, V, false><<<grd(g), blk(g), 0, s>>>(
+                                         g.m, g.n, g.N, g.ppt, wD, c, omw, r, zin, zout, part));
 }
 template <typename T, int V>
 static void run_jacobi_zm(const GridGeom &g, const T *wD, T c, T omw, const T *r, const T *zin,
-                          T *zout, cudaStream_t s) {
-    const int nseg = (g.m + g.ty - 1) / g.ty;
-    const int mz = (g.m + g.zch - 1) / g.zch;
-    const dim3 grid(g.gx, (unsigned)(nseg * g.m * g.zch));
-    HQ_LAUNCH_W(HQ_K_SMOOTH, (double)g.n * g.N,
-                k_jacobi_zm<T, V><<<grid, blk(g), 0, s>>>(g.m, g.N, nseg, mz, wD, c, omw, r, zin,
-                                                          zout));
+                          T *zout, double *part, cudaStream_t s) {
+    const double el = (double)g.n * g.N;
+    const int ns = zm_segments(g), mz = zm_planes(g);
+    if (part)
+        HQ_LAUNCH_W(HQ_K_SMOOTH, el, k_jacobi_zm<T, V, true><<<zm_grid(g), blk(g), 0, s>>>(
+                                         g.m, g.N, ns, mz, wD, c, omw, r, zin, zout, part));
+    else
+        HQ_LAUNCH_W(HQ_K_SMOOTH, el, k_jacobi_zm<T, V, false><<<zm_grid(g), blk(g), 0, s>>>(
+                                         g.m, g.N, ns, mz, wD, c, omw, r, zin, zout, part));
 }
 template <typename T>
 void launch_jacobi(const GridGeom &g, const T *D, const T *wD, T c, T omw, const T *r,
                    const T *zin, T *zout, double *part_rz, cudaStream_t s) {
     (void)D;
-    if (g.zch > 0 && !part_rz) {
-        HQ_VEC_DISPATCH(T, g, run_jacobi_zm, g, wD, c, omw, r, zin, zout, s);
+    if (g.zch > 0) {
+        HQ_VEC_DISPATCH(T, g, run_jacobi_zm, g, wD, c, omw, r, zin, zout, part_rz, s);
         return;
     }
     HQ_VEC_DISPATCH(T, g, run_jacobi, g, wD, c, omw, r, zin, zout, part_rz, s);

@@ -56,6 +56,25 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
     return false;
 }
 
+// arrive on the barrier and announce `bytes` of asynchronous copies that
+// will complete on the current phase
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// bulk global -> shared copy on the TMA unit (16-byte aligned addresses, size
+// a multiple of 16); completion is signalled on `bar` as transaction bytes
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -82,6 +101,18 @@ __device__ __forceinline__ void tmem_ld32<32>(uint32_t taddr, float (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// acc[c * 32 + j] += TMEM(lane of this warp, column taddr + c * 32 + j)
+template <int NCH>
+__device__ __forceinline__ void tmem_add32(uint32_t taddr, float (&acc)[NCH * 32]) {
+#pragma unroll
+    for (int c = 0; c < NCH; c++) {
+        float v[32];
+        tmem_ld32<32>(taddr + (uint32_t)(c * 32), v);
+#pragma unroll
+        for (int j = 0; j < 32; j++) acc[c * 32 + j] += v[j];
+    }
 }
 
 }  // namespace hq

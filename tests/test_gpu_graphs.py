@@ -99,24 +99,47 @@ def test_graphs_follow_a_new_potential():
     assert np.array_equal(a.get_state()[0], b.get_state()[0])
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_zmarch_smoother_is_bit_identical(precision):
-    """The z-marching smoothing sweeps (used for blocks beyond half of L2)
-    form the same sums in the same order as the linear-order kernel:
-    trajectories with HQ_ZMARCH=1 (forced) and HQ_ZMARCH=0 are identical."""
-    import os
+def _zm_pair(precision, m=20, N=12):
     out = []
     for flag in ("1", "0"):
         old = os.environ.get("HQ_ZMARCH")
         os.environ["HQ_ZMARCH"] = flag
         try:
-            s, _, _ = make(20, 12, precision=precision, tau=0.4,
+            s, _, _ = make(m, N, precision=precision, tau=0.4,
                            cg_rtol=1e-10 if precision == "fp64" else 1e-6)
         finally:
             if old is None:
                 os.environ.pop("HQ_ZMARCH", None)
             else:
                 os.environ["HQ_ZMARCH"] = old
-        s.step(3)
-        out.append(s.get_state()[0])
-    assert np.array_equal(out[0], out[1])
+        out.append(s)
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_zmarch_kernels_match_the_linear_order(precision):
+    """The z-marching CTAs (used for finest-level blocks beyond about three
+    quarters of L2; HQ_ZMARCH=1 forces them) form every element with the
+    same sums in the same order as the linear-order kernels: the operator,
+    a smoothing sweep and a V-cycle are bit-identical.  Their per-column
+    PCG partial sums (p.q, r.z, r.r, b.b) are reduced per CTA, a different
+    order, so PCG solves and trajectories agree to rounding."""
+    from tests.gpu_common import dev, host, rel
+    torch = pytest.importorskip("torch")
+    a, b = _zm_pair(precision)
+    n, N = a.n, a.N
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    rng = np.random.default_rng(5)
+    x = dev(rng.standard_normal((n, N)), dt)
+    r = dev(rng.standard_normal((n, N)), dt)
+    assert np.array_equal(host(a.apply_operator(x)), host(b.apply_operator(x)))
+    assert np.array_equal(host(a.mg_smooth(0, r, x)), host(b.mg_smooth(0, r, x)))
+    assert np.array_equal(host(a.mg_vcycle(r)), host(b.mg_vcycle(r)))
+    tol_x = 1e-8 if precision == "fp64" else 1e-4
+    Xa, ia = a.block_pcg(r, rtol=1e-10 if precision == "fp64" else 1e-6)
+    Xb, ib = b.block_pcg(r, rtol=1e-10 if precision == "fp64" else 1e-6)
+    assert np.abs(ia - ib).max() <= 1
+    assert rel(host(Xa), host(Xb)) < tol_x
+    a.step(3)
+    b.step(3)
+    assert rel(a.get_state()[0], b.get_state()[0]) < (1e-8 if precision == "fp64" else 1e-4)

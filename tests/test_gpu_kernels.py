@@ -129,6 +129,29 @@ def test_tensor_core_gram_matches_oracle(m, N, Na):
     np.testing.assert_array_equal(host(s.gram(Ad, Ad, w)), out)
 
 
+def test_tensor_core_gram_has_no_accumulation_bias():
+    """The tcgen05 FP32 accumulator truncates each addition relative to its
+    own magnitude, so a Gram summed over thousands of points in one TMEM
+    accumulator comes out biased low.  With every 32-point slice in a fresh
+    accumulator and the slices summed in FP32 registers, a positive block
+    (no cancellation: every entry accumulates the bias) of 110,592 points x
+    512 columns (3,686 points per chunk) stays at FP32 level, unbiased."""
+    torch_mod()
+    m, N, Na = 48, 256, 512
+    s, V, _ = make(m, N, precision="mixed", cg_rtol=1e-6)
+    rng = np.random.default_rng(17)
+    A = np.abs(rng.standard_normal((m ** 3, Na))).astype(np.float32)
+    Ad = dev(A)
+    out = host(s.gram(Ad, Ad, 1.0))        # same tensor twice: the tensor-core path
+    A64 = A.astype(np.float64)
+    ref = A64.T @ A64          # FP64 BLAS: its rounding is far below the bound tested
+    relerr = (out - ref) / ref
+    # measured on GB300: max 2.7e-7, mean -1.3e-7 (the bias of one slice);
+    # one TMEM accumulator per chunk gave -5e-5 here
+    assert np.abs(relerr).max() < 1e-6, np.abs(relerr).max()
+    assert abs(relerr.mean()) < 3e-7, relerr.mean()
+
+
 @pytest.mark.parametrize("m,N", [(8, 3), (16, 8)])
 def test_mixed_operator_and_vcycle_match_oracle(m, N):
     s, V, _ = make(m, N, precision="mixed", cg_rtol=1e-6)
@@ -146,7 +169,10 @@ def test_mixed_operator_and_vcycle_match_oracle(m, N):
 @pytest.mark.parametrize("prec,m,N,k1,k2,tol", [("fp64", 12, 8, 8, 8, 1e-13), ("fp64", 13, 17, 5, 0, 1e-13),
                                                ("mixed", 16, 64, 64, 64, 2e-6),
                                                ("mixed", 13, 24, 24, 7, 2e-6),
-                                               ("mixed", 12, 80, 80, 0, 2e-6)])
+                                               ("mixed", 12, 80, 80, 0, 2e-6),
+                                               ("mixed", 10, 9, 9, 9, 2e-6),
+                                               ("mixed", 11, 40, 40, 33, 2e-6),
+                                               ("mixed", 12, 256, 256, 256, 2e-6)])
 def test_block_gemm_matches_numpy(prec, m, N, k1, k2, tol):
     """Out = A1 M1 + A2 M2 + Cin, the products of the predictor / corrector
     updates: SIMT FP64, or tcgen05 3xTF32 in mixed precision (ragged tile
