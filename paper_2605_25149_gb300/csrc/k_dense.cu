@@ -475,7 +475,6 @@ __global__ void __launch_bounds__(512) k_lu_panel(int nn, int k0, int nb, double
         P[r * ld + c] = Mw[(size_t)(k0 + r) * nn + k0 + c];
     }
     __syncthreads();
-    bool singular = false;
     for (int jj = 0; jj < nb; jj++) {
         // pivot: largest |P[i][jj]|, i >= jj, first row on ties
         double best = -1.0;
@@ -510,7 +509,6 @@ __global__ void __launch_bounds__(512) k_lu_panel(int nn, int k0, int nb, double
                 atomicOr(status, ST_SINGULAR);
                 for (int t = jj; t < nb; t++) ipiv[k0 + t] = k0 + t;
             }
-            singular = true;
             break;
         }
         if (tid == 0) ipiv[k0 + jj] = k0 + piv;
@@ -528,7 +526,6 @@ __global__ void __launch_bounds__(512) k_lu_panel(int nn, int k0, int nb, double
         }
         __syncthreads();
     }
-    (void)singular;
     __syncthreads();
     for (int idx = tid; idx < R * nb; idx += T) {
         const int r = idx / nb, c = idx % nb;

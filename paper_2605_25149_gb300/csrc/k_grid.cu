@@ -596,30 +596,39 @@ __global__ void __launch_bounds__(256) k_axis_pass(int o2, int o1, int o0, int i
     }
 }
 
+// z = Ainv r on the coarsest level, one coarse point per CTA: thread (x, y)
+// sums the terms qq = y, y + CS_Y, ... of its column vector x in FP64, then
+// the CS_Y partials are added in y order (fixed order: deterministic)
+constexpr int CS_Y = 8;
 template <typename T, int V>
-__global__ void __launch_bounds__(256) k_coarse_solve(long nc, int N, int ppt,
-                                                      const double *__restrict__ Ainv,
+__global__ void __launch_bounds__(256) k_coarse_solve(long nc, int N, const double *__restrict__ Ainv,
                                                       const T *__restrict__ r,
                                                       T *__restrict__ z) {
-    const int TY = blockDim.y;
+    __shared__ double red[CS_Y][256];
     const int col = (blockIdx.x * blockDim.x + threadIdx.x) * V;
-    if (col >= N) return;
-    const long base = (long)blockIdx.y * TY * ppt;
-    for (int k = 0; k < ppt; k++) {
-        long p = base + (long)k * TY + threadIdx.y;
-        if (p >= nc) continue;
-        double acc[V];
+    const bool cv = col < N;
+    const long p = blockIdx.y;
+    double acc[V];
 #pragma unroll
-        for (int v = 0; v < V; v++) acc[v] = 0.0;
-        for (long qq = 0; qq < nc; qq++) {
-            double a = Ainv[p * nc + qq];
+    for (int v = 0; v < V; v++) acc[v] = 0.0;
+    if (cv)
+        for (long qq = threadIdx.y; qq < nc; qq += CS_Y) {
+            const double a = Ainv[p * nc + qq];
             VT<T, V> rv = ldv<T, V>(r + (size_t)qq * N + col);
 #pragma unroll
             for (int v = 0; v < V; v++) acc[v] += a * (double)rv.v[v];
         }
+#pragma unroll
+    for (int v = 0; v < V; v++) red[threadIdx.y][threadIdx.x * V + v] = acc[v];
+    __syncthreads();
+    if (threadIdx.y == 0 && cv) {
         VT<T, V> o;
 #pragma unroll
-        for (int v = 0; v < V; v++) o.v[v] = (T)acc[v];
+        for (int v = 0; v < V; v++) {
+            double s = 0.0;
+            for (int y = 0; y < CS_Y; y++) s += red[y][threadIdx.x * V + v];
+            o.v[v] = (T)s;
+        }
         stv<T, V>(z + (size_t)p * N + col, o);
     }
 }
@@ -1201,8 +1210,8 @@ static void run_coarse_solve(const GridGeom &g, const double *Ainv, const T *r, 
     // one coarse point per CTA row: the FP64 products of the dense inverse
     // are spread over nc CTAs (GB300's per-SM FP64 rate is low)
     HQ_LAUNCH_W(HQ_K_COARSE, (double)g.n * g.N,
-                k_coarse_solve<T, V><<<dim3(g.gx, (unsigned)g.n), dim3(g.tx, 1), 0, s>>>(
-                    g.n, g.N, 1, Ainv, r, z));
+                k_coarse_solve<T, V><<<dim3(g.gx, (unsigned)g.n), dim3(g.tx, CS_Y), 0, s>>>(
+                    g.n, g.N, Ainv, r, z));
 }
 template <typename T>
 void launch_coarse_solve(const GridGeom &g, const double *Ainv, const T *r, T *z,
