@@ -10,7 +10,7 @@
 // FP32 columns), and writes its partial tile; a second kernel reduces the
 // chunk partials in FP64 in a fixed order (deterministic).
 //
-// Per 32-point K-slice the 256 threads copy the tile columns of 32 point rows
+// Per 32-point K-slice the 512 threads copy the tile columns of 32 point rows
 // (coalesced along the columns of the point-major block) into a raw
 // shared-memory stage with cp.async, three slices ahead; they split a landed
 // slice into tf32 hi/lo and store it K-major with the 128-byte swizzle into a
@@ -36,7 +36,8 @@ namespace hq {
 
 constexpr int TC_T = 128;        // output tile edge (M = N = 128)
 constexpr int TC_K = 32;         // points per slice (128 bytes of tf32 per row)
-constexpr int TC_THREADS = 256;  // 8 warps; in the epilogue warp w reads TMEM lanes 32 (w % 4)
+constexpr int TC_THREADS = 512;  // 16 warps; warp w reads TMEM lanes 32 (w % 4)
+constexpr int TC_CW = TC_T / (TC_THREADS / 128);   // columns of a thread's share (32)
 constexpr int TC_TILE_BYTES = TC_T * TC_K * 4;   // 16 KB: one operand, one of hi / lo
 constexpr int TC_RAW = 3;                          // raw FP32 slices in flight (cp.async)
 constexpr int TC_RAW_BYTES = TC_K * TC_T * 4;      // 16 KB: one operand's raw slice
@@ -135,17 +136,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base_sh;   // accumulator of slice s: columns (s & 1) * 128 + 0..127
     // this thread's share of the tile: row wl + lane (its TMEM lane), columns
-    // cbeg + 0..63, summed over the slices in FP32 registers
-    const int wl = (warp & 3) * 32, cbeg = (warp >> 2) * (TC_T / 2);
+    // cbeg + 0..TC_CW-1, summed over the slices in FP32 registers
+    const int wl = (warp & 3) * 32, cbeg = (warp >> 2) * TC_CW;
     const uint32_t tl = tmem + ((uint32_t)wl << 16) + (uint32_t)cbeg;
-    float acc[TC_T / 2];
+    float acc[TC_CW];
 #pragma unroll
-    for (int j = 0; j < TC_T / 2; j++) acc[j] = 0.f;
+    for (int j = 0; j < TC_CW; j++) acc[j] = 0.f;
 
     // Raw FP32 slices (32 point rows x 128 columns, rows of 512 bytes) are
     // copied into shared memory with cp.async, three slices ahead of the one
     // being split, so the global-memory latency overlaps the split and the
-    // MMAs.  Thread t copies 16-byte chunks q = t + 256 j: row = q / 32,
+    // MMAs.  Thread t copies 16-byte chunks q = t + 512 j: row = q / 32,
     // column quad = q % 32; chunks the vector path cannot take (ragged rows
     // or columns, unaligned blocks) are written with plain loads and stores.
     unsigned char *raw = smem + 2 * 4 * TC_TILE_BYTES;   // TC_RAW stages x (A | B)
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (!done) atomicExch(&abort_sh, 1);
             else {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                tmem_add32<TC_T / 64>(tl + (uint32_t)(st * TC_T), acc);
+                tmem_add32<TC_CW / 32>(tl + (uint32_t)(st * TC_T), acc);
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -248,8 +249,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int s = nslices - 1;
         ok = __all_sync(0xffffffffu, mbar_wait(&mbar[s & 1], (unsigned)((s >> 1) & 1)));
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (ok && nslices >= 2) tmem_add32<TC_T / 64>(tl + (uint32_t)(((s - 1) & 1) * TC_T), acc);
-        if (ok) tmem_add32<TC_T / 64>(tl + (uint32_t)((s & 1) * TC_T), acc);
+        if (ok && nslices >= 2) tmem_add32<TC_CW / 32>(tl + (uint32_t)(((s - 1) & 1) * TC_T), acc);
+        if (ok) tmem_add32<TC_CW / 32>(tl + (uint32_t)((s & 1) * TC_T), acc);
     }
     if (!ok) atomicExch(&abort_sh, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -260,7 +261,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         float *dst = partials + ((size_t)blockIdx.y * P.ntiles + blockIdx.x) * TC_T * TC_T +
                      (size_t)(wl + lane) * TC_T + cbeg;
 #pragma unroll
-        for (int j = 0; j < TC_T / 2; j += 4)
+        for (int j = 0; j < TC_CW; j += 4)
             *reinterpret_cast<float4 *>(dst + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
     } else {
         float *dst = partials + ((size_t)blockIdx.y * P.ntiles + blockIdx.x) * TC_T * TC_T;
@@ -350,7 +351,15 @@ constexpr int TT_M = 128;
 // through registers instead, which keeps their shared memory small enough
 // for two CTAs per SM
 template <int NT>
-__host__ __device__ constexpr int tt_raw() { return NT >= 128 ? 2 : 0; }
+__host__ __device__ constexpr int tt_raw() { return NT >= 128 ? 4 : 0; }
+// stages of the small-matrix image ring (B): 3 let the copy of slice s + 2
+// start as soon as the MMAs of slice s - 1 are done
+template <int NT>
+__host__ __device__ constexpr int tt_bst() { return NT >= 128 ? 3 : 2; }
+template <int NT>
+__host__ __device__ constexpr int tt_smem() {
+    return 2 * (2 * 128 * 128) + tt_bst<NT>() * (2 * NT * 128) + tt_raw<NT>() * 128 * 128 + 1024;
+}
 // TMEM columns of one accumulator (a power of two, at least 32)
 template <int NT>
 __host__ __device__ constexpr uint32_t tt_cols() {
@@ -422,40 +431,47 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
            ((uint32_t)(M >> 4) << 24);
 }
 
-constexpr int TT_THREADS = 256;   // 8 warps; warp w owns TMEM lanes 32 (w % 4) + 0..31
+// threads per CTA: 16 warps for the wide tiles (one CTA per SM), 8 for
+// NT <= 64 (two CTAs per SM); warp w owns TMEM lanes 32 (w % 4) + 0..31
+template <int NT>
+__host__ __device__ constexpr int tt_threads() { return NT >= 128 ? 512 : 256; }
 
 // Out (n x ncol) = [A1 A2] [M1; M2] (+ Cin) for one 128-point row block and
 // one NT-column tile (blockIdx.x = row block x ctiles + column tile).  As in
 // the Gram kernel, each 32-deep K slice accumulates into a fresh TMEM
 // accumulator (two of NT columns, alternating) and the threads add the slice
-// result into FP32 registers: thread = point row (TMEM lane), NT / HALVES
-// columns (HALVES = 2 where NT is a multiple of 64: the two warp quartets
-// take one column half each).
-// two CTAs per SM where a thread sums at most 32 columns (register budget)
+// result into FP32 registers: thread = point row (TMEM lane), NT / G
+// columns (tt_groups: the warp quartets take one column group each).
+// column groups of the read-out: the four warp quartets take one NT / G
+// column group each (G = 4, 2 or 1 as 32-column loads allow)
 template <int NT>
-__host__ __device__ constexpr int tt_min_blocks() {
-    return (tt_raw<NT>() == 0 && (NT % 64 == 0 ? NT / 2 : NT) <= 32) ? 2 : 1;
+__host__ __device__ constexpr int tt_groups() {
+    return (NT % 128 == 0 && tt_threads<NT>() >= 512) ? 4 : (NT % 64 == 0 ? 2 : 1);
 }
 
 template <int NT>
-__global__ void __launch_bounds__(TT_THREADS, tt_min_blocks<NT>())
+__global__ void __launch_bounds__(tt_threads<NT>(),
+                                  (tt_threads<NT>() < 512 && NT / tt_groups<NT>() <= 32) ? 2 : 1)
     k_tall_tf32x3(TallTcPlan P, const float *__restrict__ A1, const float *__restrict__ A2,
                   const unsigned char *__restrict__ image, const float *__restrict__ Cin,
                   float *__restrict__ Out, double *part_sq, int *status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ uint64_t mbar[2];    // MMAs of the stage completed
-    __shared__ uint64_t bfull[2];   // B image of the stage landed
+    __shared__ uint64_t bfull[3];   // B image of the ring slot landed
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh;
+    constexpr int TT_THREADS = tt_threads<NT>();
     __shared__ double red[TT_THREADS / 32];
     constexpr int ABYTES = TT_M * 128;           // one operand half (hi or lo): 16 KB
     constexpr int BBYTES = NT * 128;             // 16 KB for NT = 128
-    constexpr int STAGE = 2 * ABYTES + 2 * BBYTES;
+    constexpr int ASTAGE = 2 * ABYTES;            // A hi | lo of one MMA stage (two stages)
+    constexpr int BST = tt_bst<NT>();             // B ring slots of 2 * BBYTES
+    unsigned char *bring = smem + 2 * ASTAGE;
     constexpr int AQ = TT_M * TC_K / 4 / TT_THREADS;   // 16-byte A chunks per thread per slice
     constexpr uint32_t TCOLS = tt_cols<NT>();
-    constexpr int HALVES = (NT % 64 == 0) ? 2 : 1;
-    constexpr int CW = NT / HALVES;                // columns per thread
+    constexpr int G = tt_groups<NT>();
+    constexpr int CW = NT / G;                     // columns per thread
     constexpr int NCH = (CW + 31) / 32;            // 32-column TMEM loads per drain
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -464,8 +480,7 @@ __global__ void __launch_bounds__(TT_THREADS, tt_min_blocks<NT>())
     if (tid == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
-        mbar_init(&bfull[0], 1);
-        mbar_init(&bfull[1], 1);
+        for (int b = 0; b < BST; b++) mbar_init(&bfull[b], 1);
         abort_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -480,8 +495,8 @@ __global__ void __launch_bounds__(TT_THREADS, tt_min_blocks<NT>())
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base_sh;   // accumulator of slice s: columns (s & 1) * TCOLS + ..
-    const int wl = (warp & 3) * 32, half = warp >> 2;
-    const bool owner = half < HALVES;      // warp-uniform
+    const int wl = (warp & 3) * 32, half = warp >> 2;   // half: the warp's column group
+    const bool owner = half < G;           // warp-uniform
     const uint32_t tl = tmem + ((uint32_t)wl << 16) + (uint32_t)(half * CW);
     float acc[NCH * 32];
 #pragma unroll
@@ -494,15 +509,15 @@ __global__ void __launch_bounds__(TT_THREADS, tt_min_blocks<NT>())
                       (A2 == nullptr || ((uintptr_t)A2 & 15) == 0);
 
     // The B image of a slice (hi | lo, 2 NT rows of 128 bytes, already split
-    // and swizzled) is one contiguous block: thread 0 copies it into the
-    // slice's MMA stage with one bulk (TMA) copy that completes on bfull,
-    // as soon as the MMAs of slice s - 2 that used the stage are done.
+    // and swizzled) is one contiguous block: thread 0 copies it into ring
+    // slot s % BST with one bulk (TMA) copy that completes on bfull, BST - 1
+    // slices ahead (as soon as the MMAs that used the slot are done).
     int b_issued = 0, b_landed = 0;   // thread 0's count of B copies
     auto issue_b = [&](int sl) {
         const unsigned char *src = image + ((size_t)ct * P.nslices + sl) * 2 * (size_t)BBYTES;
-        unsigned char *dst = smem + (sl & 1) * STAGE + 2 * ABYTES;
-        mbar_expect_tx(&bfull[sl & 1], 2 * BBYTES);
-        bulk_g2s(dst, src, 2 * BBYTES, &bfull[sl & 1]);
+        const int b = sl % BST;
+        mbar_expect_tx(&bfull[b], 2 * BBYTES);
+        bulk_g2s(bring + b * 2 * BBYTES, src, 2 * BBYTES, &bfull[b]);
         b_issued++;
     };
     // split four FP32 values into tf32 hi / lo: one 16-byte chunk of each
@@ -534,22 +549,24 @@ __global__ void __launch_bounds__(TT_THREADS, tt_min_blocks<NT>())
     // of slice s + 1 into the other stage once the MMAs of s - 1 are done
     const uint32_t idesc = idesc_tf32(TT_M, NT);
     auto mma_slice = [&](int s, unsigned char *base) {
-        const int st = s & 1;
-        if (!mbar_wait(&bfull[st], (unsigned)((s >> 1) & 1))) {
+        const int st = s & 1, b = s % BST;
+        if (!mbar_wait(&bfull[b], (unsigned)((s / BST) & 1))) {
             atomicExch(&abort_sh, 1);
             return;
         }
         b_landed++;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const unsigned char *bb = bring + b * 2 * BBYTES;
         mma_slice_3xtf32(tmem + (uint32_t)(st * TCOLS), smem_u32(base), smem_u32(base + ABYTES),
-                         smem_u32(base + 2 * ABYTES), smem_u32(base + 2 * ABYTES + BBYTES), idesc);
+                         smem_u32(bb), smem_u32(bb + BBYTES), idesc);
         mma_commit(&mbar[st]);
-        if (s + 1 < P.nslices) {
+        // slot (s - 1) % BST is free once the MMAs of slice s - 1 are done
+        if (s + BST - 1 < P.nslices) {
             if (s >= 1 && !mbar_wait(&mbar[st ^ 1], (unsigned)(((s - 1) >> 1) & 1))) {
                 atomicExch(&abort_sh, 1);
                 return;
             }
-            issue_b(s + 1);
+            issue_b(s + BST - 1);
         }
     };
     // every thread, before slice s reuses stage and accumulator s & 1: wait
@@ -566,10 +583,11 @@ __global__ void __launch_bounds__(TT_THREADS, tt_min_blocks<NT>())
         drain(s - 2);
     };
 
-    if (tid == 0 && P.nslices > 0) issue_b(0);
+    if (tid == 0)
+        for (int sl = 0; sl < BST - 1 && sl < P.nslices; sl++) issue_b(sl);
     if constexpr (tt_raw<NT>() == 0) {
     // A slice: 128 points x 32 columns, staged through registers; thread t
-    // takes the 16-byte chunks q = t + 256 j: row = q / 8, column quad = (q % 8) * 4
+    // takes the 16-byte chunks q = t + 512 j: row = q / 8, column quad = (q % 8) * 4
     float4 ra[AQ];
     auto load_a = [&](int s) {
 #pragma unroll
@@ -590,7 +608,7 @@ __global__ void __launch_bounds__(TT_THREADS, tt_min_blocks<NT>())
     if (P.nslices > 0) load_a(0);
     for (int s = 0; s < P.nslices; s++) {
         const int st = s & 1;
-        unsigned char *base = smem + st * STAGE;
+        unsigned char *base = smem + st * ASTAGE;
         retire(s);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
@@ -609,9 +627,9 @@ __global__ void __launch_bounds__(TT_THREADS, tt_min_blocks<NT>())
     // A slices (128 points x 32 columns, rows of 128 bytes) are copied raw
     // into shared memory with cp.async TT_RAW slices ahead and split into
     // tf32 hi / lo from there; thread t copies / splits the 16-byte chunks
-    // q = t + 256 j: row = q / 8, column quad = (q % 8) * 4.
+    // q = t + 512 j: row = q / 8, column quad = (q % 8) * 4.
     constexpr int TT_RAW = tt_raw<NT>();
-    unsigned char *raw = smem + 2 * STAGE;   // TT_RAW slices x 16 KB
+    unsigned char *raw = bring + BST * 2 * BBYTES;   // TT_RAW slices x 16 KB
     auto issue_a = [&](int sl) {
         unsigned char *dst = raw + (size_t)(sl % TT_RAW) * ABYTES;
 #pragma unroll
@@ -639,7 +657,7 @@ __global__ void __launch_bounds__(TT_THREADS, tt_min_blocks<NT>())
     }
     for (int s = 0; s < P.nslices; s++) {
         const int st = s & 1;
-        unsigned char *base = smem + st * STAGE;
+        unsigned char *base = smem + st * ASTAGE;
         // A(s) has landed once only the newest TT_RAW - 1 groups may still
         // be in flight
         asm volatile("cp.async.wait_group %0;" ::"n"(TT_RAW - 1) : "memory");
@@ -677,14 +695,14 @@ __global__ void __launch_bounds__(TT_THREADS, tt_min_blocks<NT>())
     // B copies still in flight after an abort: wait for them (bounded)
     if (tid == 0)
         for (; b_landed < b_issued; b_landed++)
-            if (!mbar_wait(&bfull[b_landed & 1], (unsigned)((b_landed >> 1) & 1))) break;
+            if (!mbar_wait(&bfull[b_landed % BST], (unsigned)((b_landed / BST) & 1))) break;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     double sq = 0.0;
     if (abort_sh) {
         if (tid == 0) atomicOr(status, ST_TC_TIMEOUT);
     } else if (owner) {
-        // epilogue: row r0 + wl + lane, columns ct NT + half CW + 0..CW-1;
+        // epilogue: row r0 + wl + lane, columns ct NT + group CW + 0..CW-1;
         // 16-byte loads / stores where the row segment allows, squares summed
         // in FP32 per 32 columns and in FP64 across them (only when the sum
         // of squares is requested)
@@ -753,17 +771,17 @@ template <int NT>
 static void run_tall_tc(const TallTcPlan &p, const float *A1, const float *A2,
                         const unsigned char *image, const float *Cin, float *Out, double *part_sq,
                         int *status, cudaStream_t s) {
-    const int smem = 2 * (2 * TT_M * 128 + 2 * NT * 128) + tt_raw<NT>() * TT_M * 128 + 1024;
+    const int smem = tt_smem<NT>();
     tc_prepare();
     const unsigned gx = (unsigned)((p.n + TT_M - 1) / TT_M * p.ctiles);
     HQ_LAUNCH(HQ_K_BLOCKGEMM,
-              k_tall_tf32x3<NT><<<gx, TT_THREADS, smem, s>>>(p, A1, A2, image, Cin,
+              k_tall_tf32x3<NT><<<gx, tt_threads<NT>(), smem, s>>>(p, A1, A2, image, Cin,
                                                                              Out, part_sq, status));
 }
 
 template <int NT>
 static void prep_tall() {
-    const int smem = 2 * (2 * TT_M * 128 + 2 * NT * 128) + tt_raw<NT>() * TT_M * 128 + 1024;
+    const int smem = tt_smem<NT>();
     cudaFuncSetAttribute(k_tall_tf32x3<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
