@@ -412,7 +412,9 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
     GramPlan gmax = make_gram_plan(n, 2 * N, 2 * N, false);
     double *gpart = cv.take<double>(std::max(gram_partial_bytes(guw), gram_partial_bytes(gmax)));
     TallPlan tp = make_tall_plan(n, N, 2 * N, 0);
-    double *tpart = cv.take<double>(sizeof(double) * (size_t)tp.gy * std::max(N, tp.gx));
+    const size_t tparts = std::max((size_t)tp.gy * std::max(N, tp.gx),
+                                   mixed ? (size_t)tall_tc_partials(n, N) : (size_t)0);
+    double *tpart = cv.take<double>(sizeof(double) * tparts);
     const size_t N2 = (size_t)N * N;
     double *G2 = cv.take<double>(sizeof(double) * 4 * N2);
     double *Mw = cv.take<double>(sizeof(double) * 4 * N2);

@@ -337,34 +337,41 @@ void launch_gram_tc(long n, const float *X1, int n1, const float *X2, int n2, do
 // Block x small-matrix products on tcgen05:
 //   Out (n x ncol) = [A1 A2] (n x (k1 + k2)) [M1; M2] (+ Cin), FP32 blocks,
 //   FP64 small matrices, 3xTF32.
-// D = A B with M = 128 grid points per CTA (tile rows), N = NT output columns
-// (NT = min(256, ncol rounded up to 16)), K = the block's columns in slices
-// of 32.  The point rows of a point-major block are already K-major, so an A
-// slice (128 points x 32 columns) is loaded, split into tf32 hi / lo and
-// stored with the 128-byte swizzle exactly as in the Gram kernel.  The small
-// matrix is split once per call by k_split_small into the same swizzled
-// shared-memory image (per column tile and K slice), which each CTA copies
-// with plain 16-byte loads.  Accumulators: TMEM, 128 lanes x NT columns.
+// Work item = 128 grid points (M, the TMEM lanes) x one NT-column tile (N);
+// K = the block's columns in slices of 32.  The point rows of a point-major
+// block are already K-major, so an A slice (128 points x 32 columns) is
+// loaded, split into tf32 hi / lo and stored with the 128-byte swizzle as in
+// the Gram kernel.  The small matrix is split once per call by
+// k_split_small into the same swizzled image (per column tile and K slice),
+// copied into shared memory with one bulk (TMA) copy per slice.
+//
+// Persistent and warp-specialised: one CTA per SM walks the work items.
+// Eight worker warps load and split the A slices into a three-stage ring
+// and add each finished slice accumulator into FP32 registers (per-slice
+// accumulation, see the Gram kernel); one control thread copies the B
+// images and issues the MMAs.  The roles meet only at mbarriers: A stage
+// full (worker warps arrive), B stage full (bulk-copy bytes), stage empty
+// and accumulator full (MMA commits), accumulator empty (worker warps), so
+// the MMAs of one slice overlap the split of the next ones and the write-out
+// of a finished work item.
 // ===========================================================================
 constexpr int TT_M = 128;
-// raw A slices in flight (cp.async) for wide tiles; tiles of NT <= 64 stage A
-// through registers instead, which keeps their shared memory small enough
-// for two CTAs per SM
-template <int NT>
-__host__ __device__ constexpr int tt_raw() { return NT >= 128 ? 4 : 0; }
-// stages of the small-matrix image ring (B): 3 let the copy of slice s + 2
-// start as soon as the MMAs of slice s - 1 are done
-template <int NT>
-__host__ __device__ constexpr int tt_bst() { return NT >= 128 ? 3 : 2; }
-template <int NT>
-__host__ __device__ constexpr int tt_smem() {
-    return 2 * (2 * 128 * 128) + tt_bst<NT>() * (2 * NT * 128) + tt_raw<NT>() * 128 * 128 + 1024;
-}
+constexpr int TT_STAGES = 3;
+constexpr int TT_WORKERS = 8;                       // worker warps
+constexpr int TT_THREADS = 32 * (TT_WORKERS + 1);   // + the control warp
 // TMEM columns of one accumulator (a power of two, at least 32)
 template <int NT>
 __host__ __device__ constexpr uint32_t tt_cols() {
     return NT <= 32 ? 32u : (NT <= 64 ? 64u : 128u);
 }
+template <int NT>
+__host__ __device__ constexpr int tt_smem() {
+    return TT_STAGES * (2 * TT_M * 128 + 2 * NT * 128) + 1024;
+}
+// column groups of the read-out: the two worker-warp quartets take one half
+// each where NT is a multiple of 64, else quartet 0 takes all columns
+template <int NT>
+__host__ __device__ constexpr int tt_groups() { return NT % 64 == 0 ? 2 : 1; }
 
 struct TallTcPlan {
     long n;
@@ -431,56 +438,44 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
            ((uint32_t)(M >> 4) << 24);
 }
 
-// threads per CTA: 16 warps for the wide tiles (one CTA per SM), 8 for
-// NT <= 64 (two CTAs per SM); warp w owns TMEM lanes 32 (w % 4) + 0..31
 template <int NT>
-__host__ __device__ constexpr int tt_threads() { return NT >= 128 ? 512 : 256; }
-
-// Out (n x ncol) = [A1 A2] [M1; M2] (+ Cin) for one 128-point row block and
-// one NT-column tile (blockIdx.x = row block x ctiles + column tile).  As in
-// the Gram kernel, each 32-deep K slice accumulates into a fresh TMEM
-// accumulator (two of NT columns, alternating) and the threads add the slice
-// result into FP32 registers: thread = point row (TMEM lane), NT / G
-// columns (tt_groups: the warp quartets take one column group each).
-// column groups of the read-out: the four warp quartets take one NT / G
-// column group each (G = 4, 2 or 1 as 32-column loads allow)
-template <int NT>
-__host__ __device__ constexpr int tt_groups() {
-    return (NT % 128 == 0 && tt_threads<NT>() >= 512) ? 4 : (NT % 64 == 0 ? 2 : 1);
-}
-
-template <int NT>
-__global__ void __launch_bounds__(tt_threads<NT>(),
-                                  (tt_threads<NT>() < 512 && NT / tt_groups<NT>() <= 32) ? 2 : 1)
-    k_tall_tf32x3(TallTcPlan P, const float *__restrict__ A1, const float *__restrict__ A2,
-                  const unsigned char *__restrict__ image, const float *__restrict__ Cin,
-                  float *__restrict__ Out, double *part_sq, int *status) {
+__global__ void __launch_bounds__(TT_THREADS, 1)
+    k_tall_tf32x3(TallTcPlan P, int nitems, const float *__restrict__ A1,
+                  const float *__restrict__ A2, const unsigned char *__restrict__ image,
+                  const float *__restrict__ Cin, float *__restrict__ Out, double *part_sq,
+                  int *status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t mbar[2];    // MMAs of the stage completed
-    __shared__ uint64_t bfull[3];   // B image of the ring slot landed
-    __shared__ uint32_t tmem_base_sh;
-    __shared__ int abort_sh;
-    constexpr int TT_THREADS = tt_threads<NT>();
-    __shared__ double red[TT_THREADS / 32];
-    constexpr int ABYTES = TT_M * 128;           // one operand half (hi or lo): 16 KB
-    constexpr int BBYTES = NT * 128;             // 16 KB for NT = 128
-    constexpr int ASTAGE = 2 * ABYTES;            // A hi | lo of one MMA stage (two stages)
-    constexpr int BST = tt_bst<NT>();             // B ring slots of 2 * BBYTES
-    unsigned char *bring = smem + 2 * ASTAGE;
-    constexpr int AQ = TT_M * TC_K / 4 / TT_THREADS;   // 16-byte A chunks per thread per slice
+    constexpr int ABYTES = TT_M * 128;           // one A half (hi or lo): 16 KB
+    constexpr int BBYTES = NT * 128;             // one B half
+    constexpr int STAGE = 2 * ABYTES + 2 * BBYTES;
+    constexpr int S = TT_STAGES;
+    constexpr int AQ = TT_M * TC_K / 4 / (32 * TT_WORKERS);   // 16-byte A chunks per thread
     constexpr uint32_t TCOLS = tt_cols<NT>();
     constexpr int G = tt_groups<NT>();
-    constexpr int CW = NT / G;                     // columns per thread
-    constexpr int NCH = (CW + 31) / 32;            // 32-column TMEM loads per drain
+    constexpr int CW = NT / G;                   // columns per worker thread
+    constexpr int NCH = (CW + 31) / 32;          // 32-column TMEM loads per slice
+    constexpr int OWNERS = 4 * G;                // worker warps holding columns
+    __shared__ uint64_t full_a[S], full_b[S], empty[S], accf[2], acce[2];
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int ct = (int)(blockIdx.x % (unsigned)P.ctiles);
-    const long r0 = (long)(blockIdx.x / (unsigned)P.ctiles) * TT_M;
+    const int ns = P.nslices;
+    auto aborted = [&]() { return *(volatile int *)&abort_sh != 0; };
+    // this CTA's work items: blockIdx.x + i gridDim.x; global slice g = i ns + s
+    const int my_items = blockIdx.x < nitems ? (nitems - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const long total = (long)my_items * ns;
     if (tid == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
-        for (int b = 0; b < BST; b++) mbar_init(&bfull[b], 1);
+        for (int b = 0; b < S; b++) {
+            mbar_init(&full_a[b], TT_WORKERS);
+            mbar_init(&full_b[b], 1);
+            mbar_init(&empty[b], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], OWNERS);
+        }
         abort_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -494,269 +489,210 @@ __global__ void __launch_bounds__(tt_threads<NT>(),
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = tmem_base_sh;   // accumulator of slice s: columns (s & 1) * TCOLS + ..
-    const int wl = (warp & 3) * 32, half = warp >> 2;   // half: the warp's column group
-    const bool owner = half < G;           // warp-uniform
-    const uint32_t tl = tmem + ((uint32_t)wl << 16) + (uint32_t)(half * CW);
-    float acc[NCH * 32];
-#pragma unroll
-    for (int j = 0; j < NCH * 32; j++) acc[j] = 0.f;
-    // add the accumulator of slice sl (complete, warp-uniform) into acc
-    auto drain = [&](int sl) {
-        if (owner) tmem_add32<NCH>(tl + (uint32_t)((sl & 1) * TCOLS), acc);
+    const uint32_t tmem = tmem_base_sh;   // accumulator of slice g: columns (g & 1) TCOLS + ..
+    auto item_of = [&](long g, int &rb, int &ct) {
+        const int it = blockIdx.x + (int)(g / ns) * gridDim.x;
+        rb = it / P.ctiles;
+        ct = it % P.ctiles;
     };
-    const bool vec4 = (P.k1 % 4 == 0) && (P.k2 % 4 == 0) && (((uintptr_t)A1 & 15) == 0) &&
-                      (A2 == nullptr || ((uintptr_t)A2 & 15) == 0);
-
-    // The B image of a slice (hi | lo, 2 NT rows of 128 bytes, already split
-    // and swizzled) is one contiguous block: thread 0 copies it into ring
-    // slot s % BST with one bulk (TMA) copy that completes on bfull, BST - 1
-    // slices ahead (as soon as the MMAs that used the slot are done).
-    int b_issued = 0, b_landed = 0;   // thread 0's count of B copies
-    auto issue_b = [&](int sl) {
-        const unsigned char *src = image + ((size_t)ct * P.nslices + sl) * 2 * (size_t)BBYTES;
-        const int b = sl % BST;
-        mbar_expect_tx(&bfull[b], 2 * BBYTES);
-        bulk_g2s(bring + b * 2 * BBYTES, src, 2 * BBYTES, &bfull[b]);
-        b_issued++;
-    };
-    // split four FP32 values into tf32 hi / lo: one 16-byte chunk of each
-    // swizzled row
-    auto put4 = [&](const float4 &v4, int row, int kq, unsigned char *hi, unsigned char *lo) {
-        const float v[4] = {v4.x, v4.y, v4.z, v4.w};
-        float h[4], l[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            h[u] = tf32_rna(v[u]);
-            l[u] = tf32_rna(v[u] - h[u]);
-        }
-        const uint32_t off = sw128_offset(row, kq);
-        *reinterpret_cast<float4 *>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<float4 *>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
-    };
-    auto a_scalar = [&](long p, int k) {
-        float v[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int kk = k + u;
-            v[u] = 0.f;
-            if (p < P.n && kk < P.k1) v[u] = A1[(size_t)p * P.k1 + kk];
-            else if (p < P.n && kk < P.k1 + P.k2) v[u] = A2[(size_t)p * P.k2 + (kk - P.k1)];
-        }
-        return make_float4(v[0], v[1], v[2], v[3]);
-    };
-    // thread 0: MMAs of slice s once its B image has landed, then the B copy
-    // of slice s + 1 into the other stage once the MMAs of s - 1 are done
-    const uint32_t idesc = idesc_tf32(TT_M, NT);
-    auto mma_slice = [&](int s, unsigned char *base) {
-        const int st = s & 1, b = s % BST;
-        if (!mbar_wait(&bfull[b], (unsigned)((s / BST) & 1))) {
-            atomicExch(&abort_sh, 1);
-            return;
-        }
-        b_landed++;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const unsigned char *bb = bring + b * 2 * BBYTES;
-        mma_slice_3xtf32(tmem + (uint32_t)(st * TCOLS), smem_u32(base), smem_u32(base + ABYTES),
-                         smem_u32(bb), smem_u32(bb + BBYTES), idesc);
-        mma_commit(&mbar[st]);
-        // slot (s - 1) % BST is free once the MMAs of slice s - 1 are done
-        if (s + BST - 1 < P.nslices) {
-            if (s >= 1 && !mbar_wait(&mbar[st ^ 1], (unsigned)(((s - 1) >> 1) & 1))) {
-                atomicExch(&abort_sh, 1);
-                return;
-            }
-            issue_b(s + BST - 1);
-        }
-    };
-    // every thread, before slice s reuses stage and accumulator s & 1: wait
-    // for the MMAs of slice s - 2 and add their result into the registers
-    auto retire = [&](int s) {
-        if (s < 2) return;
-        const bool done =
-            __all_sync(0xffffffffu, mbar_wait(&mbar[s & 1], (unsigned)(((s - 2) >> 1) & 1)));
-        if (!done) {
-            atomicExch(&abort_sh, 1);
-            return;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        drain(s - 2);
+    auto fail = [&]() {
+        atomicExch(&abort_sh, 1);
+        atomicOr(status, ST_TC_TIMEOUT);
     };
 
-    if (tid == 0)
-        for (int sl = 0; sl < BST - 1 && sl < P.nslices; sl++) issue_b(sl);
-    if constexpr (tt_raw<NT>() == 0) {
-    // A slice: 128 points x 32 columns, staged through registers; thread t
-    // takes the 16-byte chunks q = t + 512 j: row = q / 8, column quad = (q % 8) * 4
-    float4 ra[AQ];
-    auto load_a = [&](int s) {
-#pragma unroll
-        for (int j = 0; j < AQ; j++) {
-            const int q = tid + TT_THREADS * j;
-            const int row = q >> 3, kq = (q & 7) * 4;
-            const long p = r0 + row;
-            const int k = s * TC_K + kq;
-            if (p < P.n && vec4 && k + 3 < P.k1 + P.k2) {
-                const float *src = k < P.k1 ? A1 + (size_t)p * P.k1 + k
-                                            : A2 + (size_t)p * P.k2 + (k - P.k1);
-                ra[j] = *reinterpret_cast<const float4 *>(src);
-            } else {
-                ra[j] = a_scalar(p, k);
-            }
-        }
-    };
-    if (P.nslices > 0) load_a(0);
-    for (int s = 0; s < P.nslices; s++) {
-        const int st = s & 1;
-        unsigned char *base = smem + st * ASTAGE;
-        retire(s);
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        if (abort_sh) break;
-#pragma unroll
-        for (int j = 0; j < AQ; j++) {
-            const int q = tid + TT_THREADS * j;
-            put4(ra[j], q >> 3, (q & 7) * 4, base, base + ABYTES);
-        }
-        if (s + 1 < P.nslices) load_a(s + 1);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) mma_slice(s, base);
-    }
-    } else {
-    // A slices (128 points x 32 columns, rows of 128 bytes) are copied raw
-    // into shared memory with cp.async TT_RAW slices ahead and split into
-    // tf32 hi / lo from there; thread t copies / splits the 16-byte chunks
-    // q = t + 512 j: row = q / 8, column quad = (q % 8) * 4.
-    constexpr int TT_RAW = tt_raw<NT>();
-    unsigned char *raw = bring + BST * 2 * BBYTES;   // TT_RAW slices x 16 KB
-    auto issue_a = [&](int sl) {
-        unsigned char *dst = raw + (size_t)(sl % TT_RAW) * ABYTES;
-#pragma unroll
-        for (int j = 0; j < AQ; j++) {
-            const int q = tid + TT_THREADS * j;
-            const int row = q >> 3, kq = (q & 7) * 4;
-            const long p = r0 + row;
-            const int k = sl * TC_K + kq;
-            float *d = reinterpret_cast<float *>(dst + row * 128 + kq * 4);
-            if (p < P.n && vec4 && k + 3 < P.k1 + P.k2) {
-                const float *src = k < P.k1 ? A1 + (size_t)p * P.k1 + k
-                                            : A2 + (size_t)p * P.k2 + (k - P.k1);
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(d)),
-                             "l"(src)
-                             : "memory");
-            } else {
-                *reinterpret_cast<float4 *>(d) = a_scalar(p, k);
-            }
-        }
-    };
-    auto commit = [&]() { asm volatile("cp.async.commit_group;" ::: "memory"); };
-    for (int sl = 0; sl < TT_RAW; sl++) {
-        if (sl < P.nslices) issue_a(sl);
-        commit();
-    }
-    for (int s = 0; s < P.nslices; s++) {
-        const int st = s & 1;
-        unsigned char *base = smem + st * ASTAGE;
-        // A(s) has landed once only the newest TT_RAW - 1 groups may still
-        // be in flight
-        asm volatile("cp.async.wait_group %0;" ::"n"(TT_RAW - 1) : "memory");
-        retire(s);
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        if (abort_sh) break;
-        const unsigned char *src = raw + (size_t)(s % TT_RAW) * ABYTES;
-#pragma unroll
-        for (int j = 0; j < AQ; j++) {
-            const int q = tid + TT_THREADS * j;
-            const int row = q >> 3, kq = (q & 7) * 4;
-            put4(*reinterpret_cast<const float4 *>(src + row * 128 + kq * 4), row, kq, base,
-                 base + ABYTES);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        // the raw slot of A(s) is free again: copy A(s + TT_RAW) into it
-        if (s + TT_RAW < P.nslices) issue_a(s + TT_RAW);
-        commit();
-        if (tid == 0) mma_slice(s, base);
-    }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    }
-    // the last two slices (their MMAs complete in issue order), in slice order
-    bool ok = !abort_sh;
-    if (ok && P.nslices >= 1) {
-        const int s = P.nslices - 1;
-        ok = __all_sync(0xffffffffu, mbar_wait(&mbar[s & 1], (unsigned)((s >> 1) & 1)));
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (ok && s >= 1) drain(s - 1);
-        if (ok) drain(s);
-    }
-    if (!ok) atomicExch(&abort_sh, 1);
-    // B copies still in flight after an abort: wait for them (bounded)
-    if (tid == 0)
-        for (; b_landed < b_issued; b_landed++)
-            if (!mbar_wait(&bfull[b_landed % BST], (unsigned)((b_landed / BST) & 1))) break;
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    double sq = 0.0;
-    if (abort_sh) {
-        if (tid == 0) atomicOr(status, ST_TC_TIMEOUT);
-    } else if (owner) {
-        // epilogue: row r0 + wl + lane, columns ct NT + group CW + 0..CW-1;
-        // 16-byte loads / stores where the row segment allows, squares summed
-        // in FP32 per 32 columns and in FP64 across them (only when the sum
-        // of squares is requested)
-        const long p = r0 + wl + lane;
-        const bool v4 = (P.ncol % 4 == 0) && (((uintptr_t)Out & 15) == 0) &&
-                        (((uintptr_t)Cin & 15) == 0);
-        if (p < P.n) {
-#pragma unroll
-            for (int c = 0; c < NCH; c++) {
-                const int cb = half * CW + c * 32;   // column within the tile
-                const int c0 = ct * NT + cb;
-                float sqf = 0.f;
-                if (v4 && c * 32 + 32 <= CW && c0 + 32 <= P.ncol) {
-                    const size_t e0 = (size_t)p * P.ncol + c0;
-#pragma unroll
-                    for (int j = 0; j < 32; j += 4) {
-                        float4 o = make_float4(acc[c * 32 + j], acc[c * 32 + j + 1],
-                                               acc[c * 32 + j + 2], acc[c * 32 + j + 3]);
-                        if (Cin) {
-                            const float4 ci = *reinterpret_cast<const float4 *>(Cin + e0 + j);
-                            o.x += ci.x;
-                            o.y += ci.y;
-                            o.z += ci.z;
-                            o.w += ci.w;
-                        }
-                        if (Out) *reinterpret_cast<float4 *>(Out + e0 + j) = o;
-                        if (part_sq) sqf += (o.x * o.x + o.y * o.y) + (o.z * o.z + o.w * o.w);
+    if (warp == TT_WORKERS) {
+        // ----------------------------------------------------------------- control
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tf32(TT_M, NT);
+            long b_issued = 0, b_landed = 0;
+            auto issue_b = [&](long g) {
+                int rb, ct;
+                item_of(g, rb, ct);
+                const unsigned char *src =
+                    image + ((size_t)ct * ns + (size_t)(g % ns)) * 2 * (size_t)BBYTES;
+                const int st = (int)(g % S);
+                unsigned char *dst = smem + st * STAGE + 2 * ABYTES;
+                mbar_expect_tx(&full_b[st], 2 * BBYTES);
+                bulk_g2s(dst, src, 2 * BBYTES, &full_b[st]);
+                b_issued++;
+            };
+            for (long g = 0; g < S - 1 && g < total; g++) issue_b(g);
+            for (long g = 0; g < total && !aborted(); g++) {
+                const int st = (int)(g % S);
+                const unsigned u = (unsigned)((g / S) & 1);
+                if (!mbar_wait(&full_a[st], u) || !mbar_wait(&full_b[st], u)) { fail(); break; }
+                b_landed++;
+                // the accumulator of slice g - 2 has been read out
+                if (g >= 2 && !mbar_wait(&acce[g & 1], (unsigned)(((g - 2) >> 1) & 1))) { fail(); break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                unsigned char *base = smem + st * STAGE;
+                mma_slice_3xtf32(tmem + (uint32_t)((g & 1) * TCOLS), smem_u32(base),
+                                 smem_u32(base + ABYTES), smem_u32(base + 2 * ABYTES),
+                                 smem_u32(base + 2 * ABYTES + BBYTES), idesc);
+                mma_commit(&empty[st]);
+                mma_commit(&accf[g & 1]);
+                // the B half of stage (g - 1) % S is free once the MMAs of g - 1 are done
+                if (g + S - 1 < total) {
+                    if (g >= 1 && !mbar_wait(&empty[(g - 1) % S], (unsigned)(((g - 1) / S) & 1))) {
+                        fail();
+                        break;
                     }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 32; j++) {
-                        const int c1 = c0 + j;
-                        if (c * 32 + j >= CW || c1 >= P.ncol) continue;
-                        const size_t e = (size_t)p * P.ncol + c1;
-                        float o = acc[c * 32 + j];
-                        if (Cin) o += Cin[e];
-                        if (Out) Out[e] = o;
-                        if (part_sq) sqf += o * o;
-                    }
+                    issue_b(g + S - 1);
                 }
-                if (part_sq) sq += (double)sqf;
+            }
+            // B copies still in flight after an abort: wait for them (bounded)
+            for (; b_landed < b_issued; b_landed++)
+                if (!mbar_wait(&full_b[b_landed % S], (unsigned)((b_landed / S) & 1))) break;
+        }
+    } else {
+        // ----------------------------------------------------------------- workers
+        const int wt = tid;                        // 0 .. 255
+        const int wl = (warp & 3) * 32, grp = warp >> 2;
+        const bool owner = grp < G;                // warp-uniform
+        const uint32_t tl = tmem + ((uint32_t)wl << 16) + (uint32_t)(grp * CW);
+        const bool vec4 = (P.k1 % 4 == 0) && (P.k2 % 4 == 0) && (((uintptr_t)A1 & 15) == 0) &&
+                          (A2 == nullptr || ((uintptr_t)A2 & 15) == 0);
+        const bool v4o = (P.ncol % 4 == 0) && (((uintptr_t)Out & 15) == 0) &&
+                         (((uintptr_t)Cin & 15) == 0);
+        float acc[NCH * 32];
+#pragma unroll
+        for (int j = 0; j < NCH * 32; j++) acc[j] = 0.f;
+        float4 ra[AQ];
+        // A slice g into registers: chunk q = wt + 256 j: row q / 8, column quad (q % 8) * 4
+        auto load_a = [&](long g) {
+            int rb, ct;
+            item_of(g, rb, ct);
+            const long r0 = (long)rb * TT_M;
+            const int k0 = (int)(g % ns) * TC_K;
+#pragma unroll
+            for (int j = 0; j < AQ; j++) {
+                const int q = wt + 32 * TT_WORKERS * j;
+                const int row = q >> 3, kq = (q & 7) * 4;
+                const long p = r0 + row;
+                const int k = k0 + kq;
+                if (p < P.n && vec4 && k + 3 < P.k1 + P.k2) {
+                    const float *src = k < P.k1 ? A1 + (size_t)p * P.k1 + k
+                                                : A2 + (size_t)p * P.k2 + (k - P.k1);
+                    ra[j] = *reinterpret_cast<const float4 *>(src);
+                } else {
+                    float v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const int kk = k + u;
+                        v[u] = 0.f;
+                        if (p < P.n && kk < P.k1) v[u] = A1[(size_t)p * P.k1 + kk];
+                        else if (p < P.n && kk < P.k1 + P.k2) v[u] = A2[(size_t)p * P.k2 + (kk - P.k1)];
+                    }
+                    ra[j] = make_float4(v[0], v[1], v[2], v[3]);
+                }
+            }
+        };
+        // the accumulator of slice h into registers, then release it
+        auto drain = [&](long h) -> bool {
+            if (!owner) return true;
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&accf[h & 1], (unsigned)((h >> 1) & 1)));
+            if (!ok) return false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            tmem_add32<NCH>(tl + (uint32_t)((h & 1) * TCOLS), acc);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[h & 1]);
+            return true;
+        };
+        // write out the finished work item of slice h, reset the sums
+        auto write_item = [&](long h) {
+            int rb, ct;
+            item_of(h, rb, ct);
+            double sq = 0.0;
+            const long p = (long)rb * TT_M + wl + lane;
+            if (owner && p < P.n) {
+#pragma unroll
+                for (int c = 0; c < NCH; c++) {
+                    const int cb = grp * CW + c * 32;   // column within the tile
+                    const int c0 = ct * NT + cb;
+                    float sqf = 0.f;
+                    if (v4o && c * 32 + 32 <= CW && c0 + 32 <= P.ncol) {
+                        const size_t e0 = (size_t)p * P.ncol + c0;
+#pragma unroll
+                        for (int j = 0; j < 32; j += 4) {
+                            float4 o = make_float4(acc[c * 32 + j], acc[c * 32 + j + 1],
+                                                   acc[c * 32 + j + 2], acc[c * 32 + j + 3]);
+                            if (Cin) {
+                                const float4 ci = __ldcs(reinterpret_cast<const float4 *>(Cin + e0 + j));
+                                o.x += ci.x;
+                                o.y += ci.y;
+                                o.z += ci.z;
+                                o.w += ci.w;
+                            }
+                            if (Out) __stcs(reinterpret_cast<float4 *>(Out + e0 + j), o);
+                            if (part_sq) sqf += (o.x * o.x + o.y * o.y) + (o.z * o.z + o.w * o.w);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; j++) {
+                            const int c1 = c0 + j;
+                            if (c * 32 + j >= CW || c1 >= P.ncol) continue;
+                            const size_t e = (size_t)p * P.ncol + c1;
+                            float o = acc[c * 32 + j];
+                            if (Cin) o += Cin[e];
+                            if (Out) Out[e] = o;
+                            if (part_sq) sqf += o * o;
+                        }
+                    }
+                    if (part_sq) sq += (double)sqf;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < NCH * 32; j++) acc[j] = 0.f;
+            if (part_sq) {
+                // fixed butterfly within the warp; one partial per worker warp
+                // and work item (summed in order by the consumer)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+                if (lane == 0) part_sq[((size_t)rb * P.ctiles + ct) * TT_WORKERS + warp] = sq;
+            }
+        };
+        if (total > 0) load_a(0);
+        for (long g = 0; g < total; g++) {
+            const int st = (int)(g % S);
+            unsigned char *base = smem + st * STAGE;
+            // the stage is free once the MMAs of slice g - S are done
+            if (g >= S && !__all_sync(0xffffffffu, mbar_wait(&empty[st], (unsigned)((g / S - 1) & 1)))) {
+                fail();
+                break;
+            }
+            if (aborted()) break;
+#pragma unroll
+            for (int j = 0; j < AQ; j++) {
+                const int q = wt + 32 * TT_WORKERS * j;
+                const int row = q >> 3, kq = (q & 7) * 4;
+                const float v[4] = {ra[j].x, ra[j].y, ra[j].z, ra[j].w};
+                float h[4], l[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    h[u] = tf32_rna(v[u]);
+                    l[u] = tf32_rna(v[u] - h[u]);
+                }
+                const uint32_t off = sw128_offset(row, kq);
+                *reinterpret_cast<float4 *>(base + off) = make_float4(h[0], h[1], h[2], h[3]);
+                *reinterpret_cast<float4 *>(base + ABYTES + off) = make_float4(l[0], l[1], l[2], l[3]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&full_a[st]);
+            if (g + 1 < total) load_a(g + 1);
+            // read out slice g - 1; a work item ends with it: write the item
+            if (g >= 1) {
+                if (!drain(g - 1)) {
+                    fail();
+                    break;
+                }
+                if ((g - 1) % ns == ns - 1) write_item(g - 1);
             }
         }
-    }
-    if (part_sq) {
-        // fixed butterfly within each warp, then the warps in order
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-        if (lane == 0) red[warp] = sq;
-        __syncthreads();
-        if (tid == 0) {
-            double t = 0.0;
-            for (int w = 0; w < TT_THREADS / 32; w++) t += red[w];
-            part_sq[blockIdx.x] = t;
+        if (total > 0 && !aborted()) {
+            if (drain(total - 1)) write_item(total - 1);
+            else fail();
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -767,16 +703,28 @@ __global__ void __launch_bounds__(tt_threads<NT>(),
                      : "memory");
 }
 
+int tall_tc_ctas() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+            n = 152;
+    }
+    return n;
+}
+
 template <int NT>
 static void run_tall_tc(const TallTcPlan &p, const float *A1, const float *A2,
                         const unsigned char *image, const float *Cin, float *Out, double *part_sq,
                         int *status, cudaStream_t s) {
     const int smem = tt_smem<NT>();
     tc_prepare();
-    const unsigned gx = (unsigned)((p.n + TT_M - 1) / TT_M * p.ctiles);
+    const long items = (p.n + TT_M - 1) / TT_M * p.ctiles;
+    const int grid = (int)std::min<long>(items, tall_tc_ctas());
     HQ_LAUNCH(HQ_K_BLOCKGEMM,
-              k_tall_tf32x3<NT><<<gx, tt_threads<NT>(), smem, s>>>(p, A1, A2, image, Cin,
-                                                                             Out, part_sq, status));
+              k_tall_tf32x3<NT><<<grid, TT_THREADS, smem, s>>>(p, (int)items, A1, A2, image, Cin,
+                                                               Out, part_sq, status));
 }
 
 template <int NT>
@@ -800,7 +748,7 @@ void tc_prepare() {
 
 int tall_tc_partials(long n, int ncol) {
     TallTcPlan p = make_tall_tc_plan(n, 4, 0, ncol);
-    return (int)(((n + TT_M - 1) / TT_M) * p.ctiles);
+    return (int)(((n + TT_M - 1) / TT_M) * p.ctiles * TT_WORKERS);
 }
 
 void launch_tall_tc(long n, const float *A1, int k1, const double *M1, const float *A2, int k2,

@@ -40,9 +40,17 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
 
-// bounded wait for completion of the phase with the given parity
+__device__ __forceinline__ unsigned long long tc_now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait for completion of the phase with the given parity: at most
+// TC_WAIT_LIMIT polls and at most 2 s of %globaltimer
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
     uint32_t a = smem_u32(bar);
+    unsigned long long t0 = 0;
     for (unsigned it = 0; it < TC_WAIT_LIMIT; it++) {
         uint32_t ok;
         asm volatile(
@@ -52,8 +60,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
             : "r"(a), "r"(parity)
             : "memory");
         if (ok) return true;
+        if ((it & 1023u) == 0) {
+            const unsigned long long t = tc_now_ns();
+            if (it == 0) t0 = t;
+            else if (t - t0 > 2000000000ull) return false;
+        }
     }
     return false;
+}
+
+// arrive once on the barrier (release at CTA scope)
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // arrive on the barrier and announce `bytes` of asynchronous copies that
