@@ -46,9 +46,10 @@ FP64_PEAK_GFLOPS = 2 * 152 * 2.07 * 2
 ALGO = {"smooth": (10.0, 3.0), "stencil": (8.0, 2.0), "residual": (9.0, 3.0)}
 # DRAM bytes per point-column of the finest-level smooth kernel measured by
 # ncu (dram__bytes_read.sum + dram__bytes_write.sum of one launch / 16.78 M
-# point-columns, profiles/k_jacobi_wells64_N64.md); set to None whenever the
-# kernel changes until it is captured again.
-TRAFFIC_PER_ELEMENT = {("smooth", "f64"): (288.253952e6 + 111.722752e6) / 16777216,
+# point-columns, profiles/k_jacobi_k_jacobi_zm_wells64_N64.md: k_jacobi_zm
+# for the 134 MB FP64 block, k_jacobi for the 67 MB FP32 block); set to None
+# whenever the kernel changes until it is captured again.
+TRAFFIC_PER_ELEMENT = {("smooth", "f64"): (272.131840e6 + 109.167616e6) / 16777216,
                        ("smooth", "f32"): (136.215040e6 + 44.029440e6) / 16777216}
 
 
@@ -243,7 +244,8 @@ def roofline_alone(ms_launch, n_el, dtype_tag, hbm_peak, hbm_kind, in_step):
     t = ms_launch / 1e3
     tr = TRAFFIC_PER_ELEMENT.get(("smooth", dtype_tag))
     traffic = None if tr is None else tr * n_el
-    out = {"kernel": "smooth (k_jacobi, finest level)", "timing": "alone: back-to-back "
+    out = {"kernel": "smooth (finest-level damped-Jacobi sweep: k_jacobi_zm for blocks of "
+           "100 MB or more, else k_jacobi)", "timing": "alone: back-to-back "
            "launches on the step's block shape, CUDA events; inputs exceed L2",
            "ms_per_launch": ms_launch, "elements_per_launch": n_el, "traffic": traffic,
            "algorithmic_bytes": words_e * w * n_el, "algorithmic_flops": flops_e * n_el}
