@@ -77,6 +77,7 @@ def _sig(lib):
         "orc_pcg_mg": (_I, [_P, _I, _P, _P, _D, _I, _P]),
         "orc_gram": (None, [_L, _I, _P, _I, _P, _D, _P]),
         "orc_lu_solve": (_I, [_I, _P, _I, _P]),
+        "orc_predictor": (_I, [_I, _D, _P, _P, _P]),
         "orc_sym_eig": (_I, [_I, _P, _P, _P]),
         "orc_auto_shift": (_D, [_I, _D, _D, _P]),
         "orc_scale_initial": (_D, [_L, _I, _D, _P]),
@@ -270,6 +271,20 @@ def lu_solve(A, B):
     st = lib().orc_lu_solve(A.shape[0], _ptr(A), B2.shape[1], _ptr(B2))
     _check(st, "orc_lu_solve")
     return B2.reshape(B.shape)
+
+
+def predictor(gram, tau):
+    """Step 4 of Eq. (4.1) and the small matrices of its predictor update from
+    the 2N x 2N Gram of [U W] (S, <U,W>, <W,U>, Q): the 2N x 2N predictor
+    system solved by LU with partial pivoting, XY = [X; Y] (2N x N), and
+    C = [I - tau Y; tau X] with Uh = [U W] C.  The routine the oracle's own
+    step uses (orc_scheme_step)."""
+    G = _f64(gram)
+    N = G.shape[0] // 2
+    XY = np.empty((2 * N, N))
+    C = np.empty((2 * N, N))
+    _check(lib().orc_predictor(N, tau, _ptr(G), _ptr(XY), _ptr(C)), "orc_predictor")
+    return XY, C
 
 
 def sym_eig(A):

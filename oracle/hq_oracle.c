@@ -780,6 +780,52 @@ static double adaptive_tau(int N, const double *G2, orc_adapt *ad)
     return tau;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Step 4 and the small matrices of step 5 of Eq. (4.1), from the Gram of   */
+/* [U W] (2N x 2N: S, P_uw / P_wu, Q): the 2N x 2N predictor system         */
+/*   [ I - (tau/2) P_uw   (tau/2) S       ] [X]   [ S    ]                  */
+/*   [ -(tau/2) Q         I + (tau/2) P_wu ] [Y] = [ P_wu ]                 */
+/* solved by LU with partial pivoting (XY = [X; Y], 2N x N), and            */
+/* C = [I - tau Y; tau X] (2N x N) with Uh = [U W] C.                        */
+/* ------------------------------------------------------------------------ */
+static int predictor_impl(int N, double tau, const double *G2, double *XY, double *C)
+{
+    int N2 = 2 * N;
+    double *M = malloc(sizeof(double) * N2 * N2);
+#define S_(i, j)   G2[(long)(i) * N2 + (j)]
+#define PUW(i, j)  G2[(long)(i) * N2 + N + (j)]
+#define PWU(i, j)  G2[(long)(N + (i)) * N2 + (j)]
+#define Q_(i, j)   G2[(long)(N + (i)) * N2 + N + (j)]
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++) {
+            double d = (i == j) ? 1.0 : 0.0;
+            M[(long)i * N2 + j]           = d - 0.5 * tau * PUW(i, j);
+            M[(long)i * N2 + N + j]       = 0.5 * tau * S_(i, j);
+            M[(long)(N + i) * N2 + j]     = -0.5 * tau * Q_(i, j);
+            M[(long)(N + i) * N2 + N + j] = d + 0.5 * tau * PWU(i, j);
+            XY[(long)i * N + j]           = S_(i, j);
+            XY[(long)(N + i) * N + j]     = PWU(i, j);
+        }
+#undef S_
+#undef PUW
+#undef PWU
+#undef Q_
+    int st = orc_lu_solve(N2, M, N, XY);
+    free(M);
+    if (st != ORC_OK) return st;
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++) {
+            C[(long)i * N + j]       = ((i == j) ? 1.0 : 0.0) - tau * XY[(long)(N + i) * N + j];
+            C[(long)(N + i) * N + j] = tau * XY[(long)i * N + j];
+        }
+    return ORC_OK;
+}
+
+int orc_predictor(int N, double tau, const double *gram, double *XY_out, double *C_out)
+{
+    return predictor_impl(N, tau, gram, XY_out, C_out);
+}
+
 static int scheme_step_impl(int m, double lo, double hi, const double *V, double sigma, int N,
                             double tau, orc_adapt *ad, double *tau_used,
                             double cg_rtol, int cg_maxit,
@@ -792,7 +838,7 @@ static int scheme_step_impl(int m, double lo, double hi, const double *V, double
     double h = orc_grid_h(m, lo, hi), h3 = h * h * h;
     int N2 = 2 * N, st;
     double *W = malloc(sizeof(double) * n * N), *UW = malloc(sizeof(double) * n * N2),
-           *G2 = malloc(sizeof(double) * N2 * N2), *M = malloc(sizeof(double) * N2 * N2),
+           *G2 = malloc(sizeof(double) * N2 * N2),
            *XY = malloc(sizeof(double) * N2 * N), *C = malloc(sizeof(double) * N2 * N),
            *Uh = malloc(sizeof(double) * n * N), *Sh = malloc(sizeof(double) * N * N),
            *Z = malloc(sizeof(double) * n * N), *O = malloc(sizeof(double) * N * N),
@@ -829,27 +875,12 @@ static int scheme_step_impl(int m, double lo, double hi, const double *V, double
     /* 4. predictor system (time step fixed, or from the adaptive rule) */
     if (ad) tau = adaptive_tau(N, G2, ad);
     if (tau_used) *tau_used = tau;
-    for (int i = 0; i < N; i++)
-        for (int j = 0; j < N; j++) {
-            double d = (i == j) ? 1.0 : 0.0;
-            M[(long)i * N2 + j]           = d - 0.5 * tau * PUW(i, j);
-            M[(long)i * N2 + N + j]       = 0.5 * tau * S_(i, j);
-            M[(long)(N + i) * N2 + j]     = -0.5 * tau * Q_(i, j);
-            M[(long)(N + i) * N2 + N + j] = d + 0.5 * tau * PWU(i, j);
-            XY[(long)i * N + j]           = S_(i, j);
-            XY[(long)(N + i) * N + j]     = PWU(i, j);
-        }
     if (gram_out) memcpy(gram_out, G2, sizeof(double) * N2 * N2);
-    st = orc_lu_solve(N2, M, N, XY);
+    st = predictor_impl(N, tau, G2, XY, C);
     if (st != ORC_OK) goto done;
     if (XY_out) memcpy(XY_out, XY, sizeof(double) * N2 * N);
 
     /* 5. Uh = U (I - tau Y) + W (tau X) = [U W] C */
-    for (int i = 0; i < N; i++)
-        for (int j = 0; j < N; j++) {
-            C[(long)i * N + j]       = ((i == j) ? 1.0 : 0.0) - tau * XY[(long)(N + i) * N + j];
-            C[(long)(N + i) * N + j] = tau * XY[(long)i * N + j];
-        }
     block_times_small(n, N2, UW, N, C, Uh);
 
     /* 6. Shat = <Uh,Uh> (computed literally), O = Shat - I */
@@ -877,7 +908,7 @@ static int scheme_step_impl(int m, double lo, double hi, const double *V, double
 #undef PWU
 #undef Q_
 done:
-    free(W); free(UW); free(G2); free(M); free(XY); free(C); free(Uh); free(Sh);
+    free(W); free(UW); free(G2); free(XY); free(C); free(Uh); free(Sh);
     free(Z); free(O); free(ZO); free(it);
     return st;
 }

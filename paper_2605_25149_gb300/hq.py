@@ -366,6 +366,14 @@ class Solver:
                     "hq_get_state")
         return U, Z, step.value
 
+    def state_device(self):
+        """The current block as a device FP64 tensor (n x N) and the step count."""
+        U = self._torch.empty((self.n, self.N), dtype=self._torch.float64, device="cuda")
+        step = ctypes.c_long()
+        self._check(self.lib.hq_get_state(self._ctx, _dptr(U), None, 1, ctypes.byref(step)),
+                    "hq_get_state")
+        return U, step.value
+
     def set_state(self, U, step, Z=None):
         U = self._host_f64(U, (self.n, self.N))
         Zh = None if Z is None else self._host_f64(Z, (self.n, self.N))

@@ -1,0 +1,118 @@
+"""Parity at the full workload sizes, in the configuration bench.py times.
+
+One step of Eq. (4.1) on wells64_N64 (FP64: 64^3 grid, N = 64) and on
+wells128_N256 (mixed precision: 128^3 grid, N = 256), from the state after
+two warm-up steps, through the step's own graph-replayed phases
+(hq_step_trace).  The oracle cannot run these steps whole in seconds, so its
+intermediates are checked where the oracle computes them one by one, or by
+properties that hold at any size:
+
+* W = G U and Z = G Uh: the residual (H + sigma) w_j - u_j of sampled columns,
+  with the oracle's operator, against the PCG tolerance;
+* the Gram of [U W] and <Uh, Uh>: sampled entries against the oracle's
+  compensated inner product of the two columns;
+* [X; Y]: the oracle's predictor solve of the same Gram (Eq. (4.1));
+* Uh = [U W] C and U_{n+1} = Uh - tau Z (<Uh, Uh> - I): sampled rows;
+* g = ||W - U <W, U>||_h in full (FP64 only);
+* the traced step equals hq_step on a second context bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2605_25149_gb300 import hq, inputs
+from tests.gpu_common import torch_mod
+
+pytestmark = pytest.mark.gpu
+
+# (workload, W/Z residual bound, Gram bound, row bound): FP64 follows the PCG
+# tolerance 1e-10; mixed stores W, Z in FP32 (their rounding alone, times the
+# operator's condition number ~1e3 at 128^3, allows a residual of ~1e-4) and
+# forms the products with 3xTF32 (2-3e-7 of the largest entry)
+CASES = [("wells64_N64", 1.5e-10, 1e-12, 1e-12),
+         ("wells128_N256", 2e-4, 1e-6, 2e-6)]
+
+
+def _host(t):
+    return t.detach().double().cpu().numpy()
+
+
+@pytest.mark.parametrize("name,res_tol,gram_tol,row_tol", CASES)
+def test_full_size_step_on_samples(name, res_tol, gram_tol, row_tol):
+    torch = torch_mod()
+    V, U0, w = inputs.workload(name)
+    m, N, tau = w["m"], w["N"], w["tau"]
+    n = m ** 3
+    solvers = []
+    for _ in range(2):
+        s = hq.Solver(m, N, tau=tau, cg_rtol=w["cg_rtol"], precision=w["precision"])
+        s.set_potential(V)
+        s.set_initial(U0)
+        s.step(2)
+        solvers.append(s)
+    s, s2 = solvers
+    h = inputs.grid_h(m)
+    h3 = h ** 3
+    sigma = s.info()["sigma"]
+    Ud, _ = s.state_device()
+    tr = s.step_trace()
+    # the traced step is the timed step: hq_step from the same state agrees bit for bit
+    s2.step(1)
+    U2, _ = s2.state_device()
+    assert torch.equal(U2, tr["Unew"].double())
+
+    rng = np.random.default_rng(7)
+    cols = np.sort(rng.choice(N, 6, replace=False))
+    rows = np.sort(rng.choice(n, 64, replace=False))
+    ci = torch.as_tensor(cols, device="cuda")
+    ri = torch.as_tensor(rows, device="cuda")
+
+    def columns(t):
+        return _host(t.index_select(1, ci))
+
+    def rows_of(t):
+        return _host(t.index_select(0, ri))
+
+    # W = G U and Z = G Uh on sampled columns (the oracle's operator)
+    for X, B in ((tr["W"], Ud), (tr["Z"], tr["Uh"])):
+        Xc, Bc = columns(X), columns(B)
+        R = O.apply_h(m, h, V, sigma, Xc) - Bc
+        rel = np.linalg.norm(R, axis=0) / np.linalg.norm(Bc, axis=0)
+        assert rel.max() < res_tol, rel
+
+    # Gram of [U W] and <Uh, Uh>: sampled entries
+    gram = _host(tr["gram"])
+    shat = _host(tr["Shat"])
+    UW = (Ud, tr["W"])
+    pairs = [(int(a), int(b)) for a, b in rng.integers(0, 2 * N, size=(8, 2))]
+    pairs += [(0, 0), (N, N), (2 * N - 1, 0)]
+    for a, b in pairs:
+        xa = _host(UW[a // N][:, a % N])
+        xb = _host(UW[b // N][:, b % N])
+        ref = O.gram(xa[:, None], xb[:, None], h3)[0, 0]
+        scale = np.sqrt(O.gram(xa[:, None], xa[:, None], h3)[0, 0] *
+                        O.gram(xb[:, None], xb[:, None], h3)[0, 0])
+        assert abs(gram[a, b] - ref) <= gram_tol * scale, (a, b)
+    for a, b in [(int(a), int(b)) for a, b in rng.integers(0, N, size=(6, 2))] + [(1, 1)]:
+        xa, xb = _host(tr["Uh"][:, a]), _host(tr["Uh"][:, b])
+        ref = O.gram(xa[:, None], xb[:, None], h3)[0, 0]
+        assert abs(shat[a, b] - ref) <= gram_tol * np.sqrt(shat[a, a] * shat[b, b]), (a, b)
+
+    # [X; Y] from the same Gram by the oracle's predictor solve
+    XY, C = O.predictor(gram, tau)
+    xy = _host(tr["XY"])
+    assert np.abs(xy - XY).max() <= 1e-9 * np.abs(XY).max()
+
+    # Uh = [U W] C and U_{n+1} = Uh - tau Z (Shat - I) on sampled rows
+    Ur, Wr, Uhr, Zr, Unr = (rows_of(t) for t in (Ud, tr["W"], tr["Uh"], tr["Z"], tr["Unew"]))
+    Uh_ref = Ur @ C[:N] + Wr @ C[N:]
+    assert np.abs(Uhr - Uh_ref).max() <= row_tol * np.abs(Uh_ref).max()
+    Un_ref = Uhr - tau * Zr @ (shat - np.eye(N))
+    assert np.abs(Unr - Un_ref).max() <= row_tol * np.abs(Un_ref).max()
+
+    # g = ||W - U <W, U>||_h in full (FP64: 16.8 M entries)
+    if w["precision"] == "fp64":
+        U, W = _host(Ud), _host(tr["W"])
+        Pwu = gram[N:, :N]
+        g_ref = np.sqrt(h3 * np.sum((W - U @ Pwu) ** 2))
+        assert abs(_host(tr["g"])[0] - g_ref) <= 1e-9 * g_ref
