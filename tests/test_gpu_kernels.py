@@ -47,6 +47,26 @@ def test_multigrid_pieces_match_oracle(m, N):
     assert rel(host(s.mg_coarse_solve(dev(r))), mg.coarse_solve(r)) < 1e-11
 
 
+@pytest.mark.parametrize("m,N", [(9, 3), (16, 6), (20, 8), (33, 12)])
+def test_mixed_transfers_match_oracle(m, N):
+    """FP32 restriction and prolongation-with-correction on every level
+    against the oracle's FP64 transfers of the same FP32 data; all three
+    vector widths, nested and non-nested level pairs."""
+    s, V, _ = make(m, N, precision="mixed", cg_rtol=1e-6)
+    levels = s.levels()
+    rng = np.random.default_rng(m * N)
+    for l in range(len(levels) - 1):
+        ml, mc = levels[l], levels[l + 1]
+        r = rng.standard_normal((ml ** 3, N)).astype(np.float32)
+        got = host(s.mg_restrict(l, dev(r)))
+        assert rel(got, O.restrict(ml, mc, r.astype(np.float64))) < 2e-6, l
+        ec = rng.standard_normal((mc ** 3, N)).astype(np.float32)
+        z = rng.standard_normal((ml ** 3, N)).astype(np.float32)
+        got = host(s.mg_prolong(l, dev(ec), dev(z)))
+        ref = O.prolong_add(mc, ml, ec.astype(np.float64), z.astype(np.float64))
+        assert rel(got, ref) < 2e-6, l
+
+
 @pytest.mark.parametrize("m,N", [(3, 2), (16, 4), (21, 9)])
 def test_vcycle_matches_oracle(m, N):
     s, V, _ = make(m, N)
