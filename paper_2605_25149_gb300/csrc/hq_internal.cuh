@@ -47,6 +47,29 @@ int part_rows(const GridGeom &g);
 // grid (0: 16) -- the two launch-shape parameters the autotuner searches
 GridGeom make_geom(int m, int N, int elem_bytes, int block = 0, int ctas_per_sm = 0);
 
+// sum_{c < count} (double) p[c * stride] in index order (deterministic), the
+// loads issued in groups of eight ahead of the additions: an add after each
+// load would serialise the load latencies
+template <typename P>
+__device__ __forceinline__ double ordered_sum(const P *p, long count, size_t stride) {
+    double s = 0.0;
+    for (long c0 = 0; c0 < count; c0 += 8) {
+        double a[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) a[u] = c0 + u < count ? (double)p[(size_t)(c0 + u) * stride] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+            if (c0 + u < count) s += a[u];
+    }
+    return s;
+}
+// the elements i = t, t + step, ... < np of p, in that order
+__device__ __forceinline__ double strided_sum(const double *p, int np, int t, int step,
+                                              size_t stride = 1) {
+    const long cnt = t < np ? (np - 1 - t) / step + 1 : 0;
+    return ordered_sum(p + (size_t)t * stride, cnt, (size_t)step * stride);
+}
+
 // per-column PCG scalars, all device arrays of length N (FP64)
 struct PcgScalars {
     double *rz, *alpha, *beta, *bnorm, *rnorm;

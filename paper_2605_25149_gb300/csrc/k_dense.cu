@@ -118,8 +118,7 @@ __global__ void k_gram_reduce(GramPlan P, const double *partials, double w, doub
     const int la = e / GT, lb = e % GT;
     const int a = ta * GT + la, b = tb * GT + lb;
     if (a >= P.na || b >= P.nb) return;
-    double s = 0.0;
-    for (int c = 0; c < P.chunks; c++) s += partials[((size_t)c * P.ntiles + tile) * GT * GT + e];
+    double s = ordered_sum(partials + (size_t)tile * GT * GT + e, P.chunks, (size_t)P.ntiles * GT * GT);
     s *= w;
     out[(size_t)a * P.nb + b] = s;
     if (P.sym && ta != tb) out[(size_t)b * P.nb + a] = s;
@@ -261,8 +260,7 @@ void launch_tall_gemm_colsq(const TallPlan &p, const T *A1, const double *M1, co
 
 __global__ void k_sum_sqrt(int np, const double *part, double w, double *out) {
     __shared__ double red[256];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < np; i += 256) s += part[i];
+    double s = strided_sum(part, np, threadIdx.x, 256);
     red[threadIdx.x] = s;
     __syncthreads();
     for (int k = 128; k > 0; k >>= 1) {
@@ -278,8 +276,7 @@ void launch_sum_sqrt(int np, const double *part, double w, double *out, cudaStre
 __global__ void k_colsum_sqrt(int np, int ncol, const double *part, double w, double *out) {
     __shared__ double red[128];
     const int c = blockIdx.x;
-    double s = 0.0;
-    for (int i = threadIdx.x; i < np; i += 128) s += part[(size_t)i * ncol + c];
+    double s = strided_sum(part + c, np, threadIdx.x, 128, (size_t)ncol);
     red[threadIdx.x] = s;
     __syncthreads();
     for (int k = 64; k > 0; k >>= 1) {
@@ -1474,8 +1471,7 @@ void launch_scale_cols(int N, const double *Cv, const double *lam, double add, d
 __global__ void k_monitor_finish(int np, const double *part, double w, int N, const double *A,
                                  double *out) {
     __shared__ double red[256];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < np; i += 256) s += part[i];
+    double s = strided_sum(part, np, threadIdx.x, 256);
     red[threadIdx.x] = s;
     __syncthreads();
     for (int k = 128; k > 0; k >>= 1) {

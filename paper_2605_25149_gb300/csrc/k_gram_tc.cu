@@ -289,9 +289,8 @@ __global__ void k_gram_tc_reduce(TcPlan P, const float *partials, double w, doub
     // within a diagonal tile the MMA accumulates (i,j) and (j,i) in different
     // orders: keep the upper entry and mirror it
     if (ta == tb && la > lb) return;
-    double s = 0.0;
-    for (int c = 0; c < P.chunks; c++)
-        s += (double)partials[((size_t)c * P.ntiles + tile) * TC_T * TC_T + e];
+    double s = ordered_sum(partials + (size_t)tile * TC_T * TC_T + e, P.chunks,
+                           (size_t)P.ntiles * TC_T * TC_T);
     s *= w;
     out[(size_t)a * P.na + b] = s;
     if (a != b) out[(size_t)b * P.na + a] = s;

@@ -652,11 +652,23 @@ __global__ void __launch_bounds__(256) k_finalize(int mode, int N, int gy, const
     const int col = blockIdx.x * 32 + lane;
     const int R = gridDim.y, y0 = blockIdx.y * FIN_ROWS;
     const int y1 = min(gy, y0 + FIN_ROWS);
+    // all loads of a thread are issued before the additions (an add after
+    // each load would serialise their latencies); the sums run in row order
+    constexpr int PER = FIN_ROWS / 8;
+    double v1[PER], v2[PER];
+#pragma unroll
+    for (int t = 0; t < PER; t++) {
+        const int i = y0 + warp + 8 * t;
+        const bool in = col < N && i < y1;
+        v1[t] = in ? part[(size_t)i * N + col] : 0.0;
+        v2[t] = (in && part2) ? part2[(size_t)i * N + col] : 0.0;
+    }
     double s = 0.0, s2 = 0.0;
-    if (col < N)
-        for (int i = y0 + warp; i < y1; i += 8) {
-            s += part[(size_t)i * N + col];
-            if (part2) s2 += part2[(size_t)i * N + col];
+#pragma unroll
+    for (int t = 0; t < PER; t++)
+        if (y0 + warp + 8 * t < y1) {
+            s += v1[t];
+            s2 += v2[t];
         }
     red[0][warp][lane] = s;
     red[1][warp][lane] = s2;
@@ -682,9 +694,20 @@ __global__ void __launch_bounds__(256) k_finalize(int mode, int N, int gy, const
     if (col >= N) return;
     s = 0.0;
     s2 = 0.0;
-    for (int c = 0; c < R; c++) {
-        s += __ldcg(&sc.fpart[(size_t)c * N + col]);
-        s2 += __ldcg(&sc.fpart[(size_t)(R + c) * N + col]);
+    for (int c0 = 0; c0 < R; c0 += 8) {
+        double a[8], b[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int c = c0 + u;
+            a[u] = c < R ? __ldcg(&sc.fpart[(size_t)c * N + col]) : 0.0;
+            b[u] = c < R ? __ldcg(&sc.fpart[(size_t)(R + c) * N + col]) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+            if (c0 + u < R) {
+                s += a[u];
+                s2 += b[u];
+            }
     }
     switch (mode) {
     case FIN_BNORM_RNORM: {

@@ -513,9 +513,8 @@ __global__ void k_oz_gram_reduce(int na, int ctiles, int chunks, const double *p
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= na * na) return;
     const int i = e / na, j = e % na, ct = j / OZ_NT, jl = j % OZ_NT;
-    double s = 0.0;
-    for (int c = 0; c < chunks; c++)
-        s += partials[(((size_t)c * ctiles + ct) * OZ_M + i) * OZ_NT + jl];
+    const double s = ordered_sum(partials + ((size_t)ct * OZ_M + i) * OZ_NT + jl, chunks,
+                                 (size_t)ctiles * OZ_M * OZ_NT);
     out[e] = w * s;
 }
 
