@@ -299,11 +299,21 @@ __global__ void k_small_gemm(int M, int Nc, int K, double alpha, const double *A
     for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < (long)M * Nc;
          idx += (long)gridDim.x * blockDim.x) {
         int i = (int)(idx / Nc), j = (int)(idx % Nc);
+        const double *ap = ta ? A + i : A + (size_t)i * lda;
+        const double *bp = tb ? B + (size_t)j * ldb : B + j;
+        const size_t as = ta ? (size_t)lda : 1, bs = tb ? 1 : (size_t)ldb;
+        // k in order; the loads of eight terms issued ahead of their FMAs
         double s = 0.0;
-        for (int k = 0; k < K; k++) {
-            double a = ta ? A[(size_t)k * lda + i] : A[(size_t)i * lda + k];
-            double b = tb ? B[(size_t)j * ldb + k] : B[(size_t)k * ldb + j];
-            s += a * b;
+        for (int k0 = 0; k0 < K; k0 += 8) {
+            double a[8], b[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                a[u] = k0 + u < K ? ap[(size_t)(k0 + u) * as] : 0.0;
+                b[u] = k0 + u < K ? bp[(size_t)(k0 + u) * bs] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                if (k0 + u < K) s += a[u] * b[u];
         }
         double c = beta == 0.0 ? 0.0 : beta * C[(size_t)i * ldc + j];
         C[(size_t)i * ldc + j] = c + alpha * s;
@@ -834,7 +844,18 @@ __global__ void __launch_bounds__(64) k_resid64(int nn, int nr, const double *A,
     if (e >= nn * nr) return;
     const int r = e / nr, c = e % nr;
     double s = B[(size_t)r * ldb + c];
-    for (int k = 0; k < nn; k++) s -= A[(size_t)r * lda + k] * X[(size_t)k * nr + c];
+    // k in order; the loads of eight terms issued ahead of their FMAs
+    for (int k0 = 0; k0 < nn; k0 += 8) {
+        double a[8], x[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            a[u] = k0 + u < nn ? A[(size_t)r * lda + k0 + u] : 0.0;
+            x[u] = k0 + u < nn ? X[(size_t)(k0 + u) * nr + c] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+            if (k0 + u < nn) s -= a[u] * x[u];
+    }
     R[e] = s;
 }
 
