@@ -44,12 +44,17 @@ FP64_PEAK_GFLOPS = 2 * 152 * 2.07 * 2
 #   stencil  y = D x - c s: 5 add + mul + fma = 8 flops; 2 words
 #   residual b - (D x - c s): 9 flops; 3 words
 ALGO = {"smooth": (10.0, 3.0), "stencil": (8.0, 2.0), "residual": (9.0, 3.0)}
+# FP64 V-cycles sweep from the pre-scaled right-hand side rt = omega D^-1 r:
+#   z' = (omega c D^-1) s + ((1 - omega) z + rt): 5 add + 2 fma = 9 flops in 7
+#   FP64-pipe instructions; reads rt, z, writes z': 3 words
+ALGO_F64 = dict(ALGO, smooth=(9.0, 3.0))
+FP64_OPS = {"smooth": 7.0, "stencil": 7.0, "residual": 8.0}
 # DRAM bytes per point-column of the finest-level smooth kernel measured by
 # ncu (dram__bytes_read.sum + dram__bytes_write.sum of one launch / 16.78 M
 # point-columns, profiles/k_jacobi_k_jacobi_zm_wells64_N64.md: k_jacobi_zm
 # for the 134 MB FP64 block, k_jacobi for the 67 MB FP32 block); set to None
 # whenever the kernel changes until it is captured again.
-TRAFFIC_PER_ELEMENT = {("smooth", "f64"): (272.131840e6 + 109.167616e6) / 16777216,
+TRAFFIC_PER_ELEMENT = {("smooth", "f64"): None,
                        ("smooth", "f32"): (136.215040e6 + 44.029440e6) / 16777216}
 
 
@@ -183,7 +188,7 @@ def roofline(prof, dtype_tag, hbm_peak, hbm_kind):
         return None
     k = max(cand, key=lambda c: cand[c][1])
     launches, ms, elems = cand[k]
-    flops_e, words_e = ALGO[k]
+    flops_e, words_e = (ALGO_F64 if dtype_tag == "f64" else ALGO)[k]
     w = 8 if dtype_tag == "f64" else 4
     per_launch_s = ms / 1e3 / launches
     per_launch_elems = elems / launches
@@ -195,7 +200,9 @@ def roofline(prof, dtype_tag, hbm_peak, hbm_kind):
         out = {"bound": "alu", "kernel": k, "achieved": achieved, "peak": peak,
                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz",
-               "hbm_gbs": words_e * w * per_launch_elems / per_launch_s / 1e9}
+               "hbm_gbs": words_e * w * per_launch_elems / per_launch_s / 1e9,
+               "fp64_issue_frac": FP64_OPS[k] * per_launch_elems / per_launch_s
+               / (FP64_PEAK_GFLOPS / 2 * 1e9)}
     else:
         achieved = words_e * w * per_launch_elems / per_launch_s / 1e9
         out = {"bound": "hbm", "kernel": k, "achieved": achieved, "peak": hbm_peak,
@@ -208,8 +215,9 @@ def roofline(prof, dtype_tag, hbm_peak, hbm_kind):
 
 def smooth_alone(torch, hq, s, reps=40):
     """The finest-level damped-Jacobi sweep (the dominant kernel class) timed
-    alone: `reps` back-to-back launches through hq_mg_smooth on n x N blocks
-    of the context's working precision (ping-pong z_in / z_out; the three
+    alone, in the form the context's V-cycle launches it (hq_mg_smooth_prescaled
+    for FP64 contexts, hq_mg_smooth otherwise): `reps` back-to-back launches on
+    n x N blocks of the working precision (ping-pong z_in / z_out; the three
     blocks exceed L2, so every sweep streams from HBM), CUDA events on the
     context's stream around the whole sequence.  Returns ms per launch."""
     import ctypes
@@ -224,14 +232,17 @@ def smooth_alone(torch, hq, s, reps=40):
              ctypes.c_void_p(zb.data_ptr())),
             (ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(zb.data_ptr()),
              ctypes.c_void_p(za.data_ptr()))]
+    fn, name = lib.hq_mg_smooth, "hq_mg_smooth"
+    if s.dtype == torch.float64 and not s.cfg.mg_fp32:
+        fn, name = lib.hq_mg_smooth_prescaled, "hq_mg_smooth_prescaled"
     for i in range(4):
-        s._check(lib.hq_mg_smooth(s._ctx, 0, *args[i & 1]), "hq_mg_smooth")
+        s._check(fn(s._ctx, 0, *args[i & 1]), name)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(st)
     for i in range(reps):
-        s._check(lib.hq_mg_smooth(s._ctx, 0, *args[i & 1]), "hq_mg_smooth")
+        s._check(fn(s._ctx, 0, *args[i & 1]), name)
     e1.record(st)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps
@@ -239,7 +250,7 @@ def smooth_alone(torch, hq, s, reps=40):
 
 def roofline_alone(ms_launch, n_el, dtype_tag, hbm_peak, hbm_kind, in_step):
     """Roofline entry of the smooth kernel from its stand-alone launch time."""
-    flops_e, words_e = ALGO["smooth"]
+    flops_e, words_e = (ALGO_F64 if dtype_tag == "f64" else ALGO)["smooth"]
     w = 8 if dtype_tag == "f64" else 4
     t = ms_launch / 1e3
     tr = TRAFFIC_PER_ELEMENT.get(("smooth", dtype_tag))
@@ -255,7 +266,9 @@ def roofline_alone(ms_launch, n_el, dtype_tag, hbm_peak, hbm_kind, in_step):
         out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak,
                     "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz",
-                    "hbm_gbs": words_e * w * n_el / t / 1e9})
+                    "hbm_gbs": words_e * w * n_el / t / 1e9,
+                    "fp64_issue_frac": FP64_OPS["smooth"] * n_el / t
+                    / (FP64_PEAK_GFLOPS / 2 * 1e9)})
     else:
         achieved = words_e * w * n_el / t / 1e9
         out.update({"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",

@@ -242,6 +242,13 @@ hq_status hq_step_trace(hq_ctx *ctx, void *W, double *gram, double *g, double *X
  * ef_out = ef_in + P ec from level l+1 to l; exact solve on the coarsest
  * level.  ncol must equal N.                                               */
 hq_status hq_mg_smooth(hq_ctx *ctx, int level, const void *r, const void *z_in, void *z_out);
+/* The same sweep as the FP64 V-cycle forms it, from the pre-scaled right-hand
+ * side rt = omega D^{-1} r (device, n_l x N, FP64):
+ * z_out = omega c D^{-1} nbrsum(z_in) + ((1 - omega) z_in + rt), with
+ * c = 1/(2 h_l^2).  FP64 contexts without mg_fp32 only (HQ_ERR_STATE
+ * otherwise) and levels above the coarsest (HQ_ERR_ARG).                   */
+hq_status hq_mg_smooth_prescaled(hq_ctx *ctx, int level, const void *rt, const void *z_in,
+                                 void *z_out);
 hq_status hq_mg_restrict(hq_ctx *ctx, int level, const void *rf, void *rc);
 hq_status hq_mg_prolong(hq_ctx *ctx, int level, const void *ec, const void *ef_in,
                         void *ef_out);

@@ -41,6 +41,10 @@ struct Level {
     double h = 0, c = 0;
     double *V = nullptr, *D = nullptr, *wD = nullptr;   // FP64
     void *Dt = nullptr, *wDt = nullptr;                 // working precision
+    // FP64 V-cycle (FP64 contexts): wD c per point and the pre-scaled
+    // right-hand side rt = wD r of the level (the first sweep from zero)
+    double *wcD = nullptr;
+    void *rt = nullptr;
     void *r = nullptr, *z = nullptr, *t = nullptr;      // level buffers (l >= 1)
     XferTab tab{};                                       // transfer tables to level l + 1
     GridGeom g;
@@ -96,6 +100,8 @@ struct hq_ctx {
     Level mg[MAXLEV];
     void *mxt1 = nullptr, *mxt2 = nullptr;
     bool mg32 = false;
+    // FP64 V-cycle smoothing from the pre-scaled right-hand side (Level::rt)
+    bool rtilde = false;
     float *R32 = nullptr, *Z32 = nullptr, *T32 = nullptr;
     // n x N blocks in the working precision
     void *U = nullptr, *W = nullptr, *Uh = nullptr, *Z = nullptr;
@@ -325,6 +331,10 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
         v.V = cv.take<double>(sizeof(double) * v.n);
         v.D = cv.take<double>(sizeof(double) * v.n);
         v.wD = cv.take<double>(sizeof(double) * v.n);
+        if (!mixed && !c->mg_fp32 && l + 1 < L) {
+            v.wcD = cv.take<double>(sizeof(double) * v.n);
+            v.rt = cv.take<char>((size_t)v.n * N * esz);
+        }
         if (mixed) {
             v.Dt = cv.take<float>(sizeof(float) * v.n);
             v.wDt = cv.take<float>(sizeof(float) * v.n);
@@ -470,6 +480,7 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
         x->nc = nc; x->Acoarse = Acoarse; x->Ainv = Ainv; x->xt1 = xt1; x->xt2 = xt2;
         for (int l = 0; l < L; l++) x->mg[l] = mgv[l];
         x->mxt1 = mxt1; x->mxt2 = mxt2; x->mg32 = mg32;
+        x->rtilde = !mixed && !mg32 && L > 1;
         x->R32 = R32; x->Z32 = Z32; x->T32 = T32;
         x->sc = sc; x->part = part; x->part2 = part2;
         x->gplan_uw = guw; x->gplan_max = gmax; x->gpart = gpart; x->tcpart = tcpart; x->tcimg = tcimg;
@@ -557,6 +568,66 @@ T *first_target(hq_ctx *x, int l, T *Zfinal, T *Tbuf) {
 }
 
 template <typename T>
+hq_status vcycle(hq_ctx *x, int l, const T *r, T *Zf, T *Tb, bool first_done, double *part_final);
+
+// The FP64 V-cycle of level l with the smoothing sweeps from the pre-scaled
+// right-hand side rt = wD r (launch_jacobi_rt): the first sweep from zero is
+// rt itself (written by launch_jacobi_first, or by the PCG update when
+// first_done), so the sweeps read rt instead of r and form
+// wc nbrsum(z) + ((1 - omega) z + rt); rt stays untouched for the post
+// sweeps.  Iterates and the residual alternate between Zf and Tb, starting
+// so that the last write lands in Zf (no copy).
+hq_status vcycle_rt(hq_ctx *x, int l, const double *r, double *Zf, double *Tb, bool first_done,
+                    double *part_final) {
+    Level &v = x->mg[l];
+    const double c = v.c, omw = 1.0 - x->cfg.mg_omega;
+    double *rt = (double *)v.rt;
+    if (!first_done) launch_jacobi_first<double>(v.g, v.wD, r, rt, x->st);
+    // writes after the first sweep: nu1 - 1 pre sweeps, the residual, the
+    // prolongation (into the residual's buffer), nu2 post sweeps
+    const int nu1 = x->cfg.mg_nu1, nu2 = x->cfg.mg_nu2;
+    auto final_is_first = [&]() {
+        // simulate with the first written buffer labelled 0
+        int cur = -1, k = 0;
+        auto next = [&](int c0) { return c0 < 0 ? 0 : 1 - c0; };
+        for (int s = 1; s < nu1; s++) cur = next(cur);
+        k = next(cur);   // residual buffer, the prolongation writes into it
+        cur = k;
+        for (int s = 0; s < nu2; s++) cur = next(cur);
+        return cur == 0;
+    };
+    double *b0 = final_is_first() ? Zf : Tb;
+    auto next = [&](const double *cb) -> double * {
+        return cb == rt ? b0 : (cb == Zf ? Tb : Zf);
+    };
+    double *cur = rt;
+    for (int s = 1; s < nu1; s++) {
+        double *o = next(cur);
+        launch_jacobi_rt<double>(v.g, v.wcD, omw, r, rt, cur, o, nullptr, x->st);
+        cur = o;
+    }
+    double *res = next(cur);
+    launch_resid<double>(v.g, v.D, c, cur, r, res, nullptr, nullptr, x->st);
+    Level &w = x->mg[l + 1];
+    launch_restrict<double>(v.m, w.m, x->N, v.tab, res, (double *)x->mxt1, (double *)x->mxt2,
+                            (double *)w.r, x->st);
+    HQ_TRY(vcycle<double>(x, l + 1, (const double *)w.r, (double *)w.z, (double *)w.t, false,
+                          nullptr));
+    launch_prolong<double>(v.m, w.m, x->N, v.tab, (const double *)w.z, (double *)x->mxt1,
+                           (double *)x->mxt2, cur, res, x->st);
+    cur = res;
+    for (int s = 0; s < nu2; s++) {
+        const bool last = (s == nu2 - 1);
+        double *o = next(cur);
+        launch_jacobi_rt<double>(v.g, v.wcD, omw, r, rt, cur, o, last ? part_final : nullptr,
+                                 x->st);
+        cur = o;
+    }
+    if (cur != Zf) HQ_TRY(copy_blk<double>(x, Zf, cur, (size_t)v.n * x->N));
+    return HQ_OK;
+}
+
+template <typename T>
 hq_status vcycle(hq_ctx *x, int l, const T *r, T *Zf, T *Tb, bool first_done, double *part_final) {
     LevelScope lvl_(l);
     Level &v = x->mg[l];
@@ -565,6 +636,9 @@ hq_status vcycle(hq_ctx *x, int l, const T *r, T *Zf, T *Tb, bool first_done, do
         launch_coarse_solve<T>(v.g, x->Ainv, r, Zf, x->st);
         if (part_final) launch_dot<T>(v.g, r, Zf, part_final, x->st);
         return HQ_OK;
+    }
+    if constexpr (std::is_same<T, double>::value) {
+        if (x->rtilde) return vcycle_rt(x, l, r, Zf, Tb, first_done, part_final);
     }
     T *cur = first_target<T>(x, l, Zf, Tb);
     T *oth = (cur == Zf) ? Tb : Zf;
@@ -650,7 +724,7 @@ hq_status pcg_half(hq_ctx *x, T *X, double rtol) {
     const int N = x->N;
     T *R = (T *)x->R, *Zp = (T *)x->Zp, *P = (T *)x->P, *Q = (T *)x->Q, *Tt = (T *)x->Tt;
     PcgScalars sc = x->sc;
-    T *zfirst = first_target<T>(x, 0, Zp, Tt);
+    T *zfirst = x->rtilde ? (T *)x->mg[0].rt : first_target<T>(x, 0, Zp, Tt);
     launch_apply<T>(g, (const T *)v.Dt, (T)v.c, P, Q, x->part, x->st);
     launch_finalize(FIN_ALPHA, N, part_rows(g), x->part, nullptr, sc, rtol, x->st);
     launch_pcg_xr<T>(g, sc.alpha, P, Q, X, R, x->part, (const T *)v.wDt,
@@ -1498,7 +1572,7 @@ hq_status set_potential_impl(hq_ctx *x, const double *V, int on_device) {
     }
     for (int l = 0; l < x->L; l++) {
         Level &v = x->lev[l];
-        launch_level_diag(v.n, v.V, x->sigma, v.c, x->cfg.mg_omega, v.D, v.wD, x->st);
+        launch_level_diag(v.n, v.V, x->sigma, v.c, x->cfg.mg_omega, v.D, v.wD, v.wcD, x->st);
         if (x->mixed) {
             launch_convert_d2f(v.n, v.D, (float *)v.Dt, x->st);
             launch_convert_d2f(v.n, v.wD, (float *)v.wDt, x->st);
@@ -2256,6 +2330,21 @@ hq_status hq_mg_smooth(hq_ctx *x, int level, const void *r, const void *z_in, vo
     HQ_TRY(HQ_DISPATCH(x, level_check, x, level, false));
     if (!r || !z_in || !z_out || z_in == z_out) return fail(x, HQ_ERR_ARG, "bad operand");
     return HQ_DISPATCH(x, smooth_impl, x, level, r, z_in, z_out);
+    HQ_API_END
+}
+
+hq_status hq_mg_smooth_prescaled(hq_ctx *x, int level, const void *rt, const void *z_in,
+                                 void *z_out) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    if (!x->rtilde) return fail(x, HQ_ERR_STATE, "the context's V-cycle does not pre-scale (mixed or mg_fp32)");
+    HQ_TRY(level_check<double>(x, level, true));
+    if (!rt || !z_in || !z_out || z_in == z_out) return fail(x, HQ_ERR_ARG, "bad operand");
+    Level &v = x->mg[level];
+    launch_jacobi_rt<double>(v.g, v.wcD, 1.0 - x->cfg.mg_omega, nullptr, (const double *)rt,
+                             (const double *)z_in, (double *)z_out, nullptr, x->st);
+    return check_launch(x);
     HQ_API_END
 }
 

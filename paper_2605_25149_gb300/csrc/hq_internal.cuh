@@ -110,6 +110,12 @@ void launch_jacobi(const GridGeom &g, const T *D, const T *wD, T c, T one_minus_
 // z = wD * r
 template <typename T>
 void launch_jacobi_first(const GridGeom &g, const T *wD, const T *r, T *z, cudaStream_t s);
+// the damped-Jacobi sweep from the pre-scaled right-hand side rt = wD r and
+// wc = wD c: z_out = wc nbrsum(z_in) + ((1 - omega) z_in + rt); r is read
+// only for the partial r.z_out (part_rz non-null)
+template <typename T>
+void launch_jacobi_rt(const GridGeom &g, const T *wc, T one_minus_omega, const T *r,
+                      const T *rt, const T *zin, T *zout, double *part_rz, cudaStream_t s);
 // 1-D transfer tables between grids of mf and mc nodes per side:
 // restriction taps (fine node, weight) per coarse node, XFER_RTAPS each;
 // prolongation taps (coarse node, weight) per fine node, 2 each; index -1 =
@@ -229,8 +235,9 @@ int launch_diff_sq(long n, const double *a, const double *b, double *d, double *
 
 // setup
 void launch_coarse_potential(int mf, const double *Vf, int mc, double *Vc, cudaStream_t s);
+// D = 6c + V + sigma, wD = omega / D and (nullable) wcD = wD c per point
 void launch_level_diag(long n, const double *V, double sigma, double c, double omega,
-                       double *D, double *wD, cudaStream_t s);
+                       double *D, double *wD, double *wcD, cudaStream_t s);
 void launch_assemble_dense(int mc, double c, const double *V, double sigma, double *A,
                            cudaStream_t s);
 void launch_gauss_jordan(int nc, double *A, double *Ainv, int *status, cudaStream_t s);

@@ -243,12 +243,18 @@ __global__ void __launch_bounds__(256) k_pcg_p(long n, int N, int ppt,
 
 // z_out = z_in + wD (r - A z_in) = (1 - omega) z_in + wD (r + c * nbrsum(z_in))
 // (wD = omega / D, so wD * D = omega); PART: partial r.z_out.
-template <typename T, int V, bool PART>
+// RT: the same sweep from the pre-scaled right-hand side rt = wD r (the
+// first sweep from zero, kept by the V-cycle) and wc = wD c per point:
+// z_out = wc nbrsum(z_in) + ((1 - omega) z_in + rt), two FMAs after the
+// neighbour sum instead of a multiply and two FMAs (FP64 levels, where the
+// FP64 pipe bounds the sweep).
+template <typename T, int V, bool PART, bool RT = false>
 __global__ void __launch_bounds__(256) k_jacobi(int m, long n, int N, int ppt,
                                                 const T *__restrict__ wD, T c, T omw,
                                                 const T *__restrict__ r,
                                                 const T *__restrict__ zin,
-                                                T *__restrict__ zout, double *part) {
+                                                T *__restrict__ zout, double *part,
+                                                const T *__restrict__ rt = nullptr) {
     __shared__ double red[1024];
     const int TY = blockDim.y;
     const int col = (blockIdx.x * blockDim.x + threadIdx.x) * V;
@@ -264,15 +270,22 @@ __global__ void __launch_bounds__(256) k_jacobi(int m, long n, int N, int ppt,
     for (int k = 0; k < ppt; k++, p += TY, grid_advance(TY, m, i, j, kk)) {
         if (!cv || p >= n) continue;
         size_t e = (size_t)p * N + col;
-        VT<T, V> zc = ldv<T, V>(zin + e), rv = ldv<T, V>(r + e);
+        VT<T, V> zc = ldv<T, V>(zin + e), rv;
+        if (!RT || PART) rv = ldv<T, V>(r + e);
         VT<T, V> s = nbr_sum<T, V>(zin, e, i, j, kk, m, sx, sy, sz);
         T w = wD[p];
         VT<T, V> o;
+        if (RT) {
+            VT<T, V> tv = ldv<T, V>(rt + e);
 #pragma unroll
-        for (int v = 0; v < V; v++) {
-            o.v[v] = omw * zc.v[v] + w * (rv.v[v] + c * s.v[v]);
-            if (PART) acc[v] += rv.v[v] * o.v[v];
+            for (int v = 0; v < V; v++) o.v[v] = w * s.v[v] + (omw * zc.v[v] + tv.v[v]);
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; v++) o.v[v] = omw * zc.v[v] + w * (rv.v[v] + c * s.v[v]);
         }
+#pragma unroll
+        for (int v = 0; v < V; v++)
+            if (PART) acc[v] += rv.v[v] * o.v[v];
         stv<T, V>(zout + e, o);
     }
     if (PART) block_col_reduce<V, T>(acc, red, part, N, col, cv);
@@ -286,12 +299,13 @@ __global__ void __launch_bounds__(256) k_jacobi(int m, long n, int N, int ppt,
 // nbr_sum, so the swept values are bit-identical to k_jacobi.  The optional
 // partial r.z is reduced over the CTA's points (one partial row per CTA:
 // part_rows() rows in all), so its summation order differs from k_jacobi's.
-template <typename T, int V, bool PART>
+template <typename T, int V, bool PART, bool RT = false>
 __global__ void __launch_bounds__(256) k_jacobi_zm(int m, int N, int nseg, int mz,
                                                    const T *__restrict__ wD, T c, T omw,
                                                    const T *__restrict__ r,
                                                    const T *__restrict__ zin,
-                                                   T *__restrict__ zout, double *part) {
+                                                   T *__restrict__ zout, double *part,
+                                                   const T *__restrict__ rt = nullptr) {
     __shared__ double red[1024];
     const int TY = blockDim.y;
     const int col = (blockIdx.x * blockDim.x + threadIdx.x) * V;
@@ -318,7 +332,9 @@ __global__ void __launch_bounds__(256) k_jacobi_zm(int m, int N, int nseg, int m
             VT<T, V> znext = kk + 1 < m ? ldv<T, V>(zin + e + sz) : zero;
             VT<T, V> a0 = ldv<T, V>(zin + (bw ? e - sx : e)), a1 = ldv<T, V>(zin + (be ? e + sx : e));
             VT<T, V> a2 = ldv<T, V>(zin + (bs ? e - sy : e)), a3 = ldv<T, V>(zin + (bn ? e + sy : e));
-            VT<T, V> rv = ldv<T, V>(r + e);
+            VT<T, V> rv, tv;
+            if (!RT || PART) rv = ldv<T, V>(r + e);
+            if (RT) tv = ldv<T, V>(rt + e);
             const T w = wD[p];
             VT<T, V> o;
 #pragma unroll
@@ -326,7 +342,8 @@ __global__ void __launch_bounds__(256) k_jacobi_zm(int m, int N, int nseg, int m
                 const T sum = (((bw ? a0.v[v] : T(0)) + (be ? a1.v[v] : T(0))) +
                                ((bs ? a2.v[v] : T(0)) + (bn ? a3.v[v] : T(0)))) +
                               (zprev.v[v] + znext.v[v]);
-                o.v[v] = omw * zcur.v[v] + w * (rv.v[v] + c * sum);
+                if (RT) o.v[v] = w * sum + (omw * zcur.v[v] + tv.v[v]);
+                else o.v[v] = omw * zcur.v[v] + w * (rv.v[v] + c * sum);
                 if (PART) acc[v] += rv.v[v] * o.v[v];
             }
             stv<T, V>(zout + e, o);
@@ -915,12 +932,13 @@ __global__ void k_coarse_potential(int mf, const double *__restrict__ Vf, int mc
 }
 
 __global__ void k_level_diag(long n, const double *V, double sigma, double c, double omega,
-                             double *D, double *wD) {
+                             double *D, double *wD, double *wcD) {
     for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < n;
          p += (long)gridDim.x * blockDim.x) {
         double d = 6.0 * c + V[p] + sigma;
         D[p] = d;
         wD[p] = omega / d;
+        if (wcD) wcD[p] = (omega / d) * c;
     }
 }
 
@@ -1161,6 +1179,35 @@ void launch_jacobi(const GridGeom &g, const T *D, const T *wD, T c, T omw, const
     HQ_VEC_DISPATCH(T, g, run_jacobi, g, wD, c, omw, r, zin, zout, part_rz, s);
 }
 
+// the sweep from the pre-scaled right-hand side (k_jacobi<..., RT = true>):
+// wc = omega c / D per point, rt = wD r; r is read only with partials
+template <typename T, int V>
+static void run_jacobi_rt(const GridGeom &g, const T *wc, T omw, const T *r, const T *rt,
+                          const T *zin, T *zout, double *part, cudaStream_t s) {
+    const double el = (double)g.n * g.N;
+    if (g.zch > 0) {
+        const int ns = zm_segments(g), mz = zm_planes(g);
+        if (part)
+            HQ_LAUNCH_W(HQ_K_SMOOTH, el, k_jacobi_zm<T, V, true, true><<<zm_grid(g), blk(g), 0, s>>>(
+                                         g.m, g.N, ns, mz, wc, T(0), omw, r, zin, zout, part, rt));
+        else
+            HQ_LAUNCH_W(HQ_K_SMOOTH, el, k_jacobi_zm<T, V, false, true><<<zm_grid(g), blk(g), 0, s>>>(
+                                         g.m, g.N, ns, mz, wc, T(0), omw, r, zin, zout, part, rt));
+        return;
+    }
+    if (part)
+        HQ_LAUNCH_W(HQ_K_SMOOTH, el, k_jacobi<T, V, true, true><<<grd(g), blk(g), 0, s>>>(
+                                     g.m, g.n, g.N, g.ppt, wc, T(0), omw, r, zin, zout, part, rt));
+    else
+        HQ_LAUNCH_W(HQ_K_SMOOTH, el, k_jacobi<T, V, false, true><<<grd(g), blk(g), 0, s>>>(
+                                     g.m, g.n, g.N, g.ppt, wc, T(0), omw, r, zin, zout, part, rt));
+}
+template <typename T>
+void launch_jacobi_rt(const GridGeom &g, const T *wc, T omw, const T *r, const T *rt,
+                      const T *zin, T *zout, double *part_rz, cudaStream_t s) {
+    HQ_VEC_DISPATCH(T, g, run_jacobi_rt, g, wc, omw, r, rt, zin, zout, part_rz, s);
+}
+
 template <typename T, int V>
 static void run_jacobi_first(const GridGeom &g, const T *wD, const T *r, T *z, cudaStream_t s) {
     HQ_LAUNCH_W(HQ_K_VECTOR, (double)g.n * g.N, k_jacobi_first<T, V><<<grd(g), blk(g), 0, s>>>(g.n, g.N, g.ppt, wD, r, z));
@@ -1300,9 +1347,9 @@ void launch_coarse_potential(int mf, const double *Vf, int mc, double *Vc, cudaS
     HQ_LAUNCH(HQ_K_SETUP, k_coarse_potential<<<blocks, 256, 0, s>>>(mf, Vf, mc, Vc));
 }
 void launch_level_diag(long n, const double *V, double sigma, double c, double omega,
-                       double *D, double *wD, cudaStream_t s) {
+                       double *D, double *wD, double *wcD, cudaStream_t s) {
     int blocks = (int)std::min<long>((n + 255) / 256, 4096);
-    HQ_LAUNCH(HQ_K_SETUP, k_level_diag<<<blocks, 256, 0, s>>>(n, V, sigma, c, omega, D, wD));
+    HQ_LAUNCH(HQ_K_SETUP, k_level_diag<<<blocks, 256, 0, s>>>(n, V, sigma, c, omega, D, wD, wcD));
 }
 void launch_assemble_dense(int mc, double c, const double *V, double sigma, double *A,
                            cudaStream_t s) {
@@ -1343,6 +1390,8 @@ void launch_scale(size_t count, const double *factor, T *x, cudaStream_t s) {
                                    const T *, T *, double *, cudaStream_t);                  \
     template void launch_jacobi_first<T>(const GridGeom &, const T *, const T *, T *,         \
                                          cudaStream_t);                                      \
+    template void launch_jacobi_rt<T>(const GridGeom &, const T *, T, const T *, const T *,   \
+                                      const T *, T *, double *, cudaStream_t);               \
     template void launch_restrict<T>(int, int, int, const XferTab &, const T *, T *, T *, T *, \
                                      cudaStream_t);                                          \
     template void launch_prolong<T>(int, int, int, const XferTab &, const T *, T *, T *,      \

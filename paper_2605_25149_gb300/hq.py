@@ -35,7 +35,8 @@ EXPORTED = [
     "hq_grad_eigs", "hq_grad_density", "hq_get_state", "hq_set_state", "hq_problem_info",
     "hq_apply_operator", "hq_mg_vcycle", "hq_block_pcg", "hq_gram", "hq_block_gemm",
     "hq_step_trace",
-    "hq_mg_smooth", "hq_mg_restrict", "hq_mg_prolong", "hq_mg_coarse_solve",
+    "hq_mg_smooth", "hq_mg_smooth_prescaled", "hq_mg_restrict", "hq_mg_prolong",
+    "hq_mg_coarse_solve",
     "hq_mg_level_potential", "hq_gram_static", "hq_profile", "hq_profile_read", "hq_pcg_stats",
     "hq_last_error",
     "hq_status_string", "hq_destroy",
@@ -106,6 +107,7 @@ def load():
         "hq_block_gemm": (_I, [_P, _P, _I, _P, _P, _I, _P, _P, _P]),
         "hq_step_trace": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
         "hq_mg_smooth": (_I, [_P, _I, _P, _P, _P]),
+        "hq_mg_smooth_prescaled": (_I, [_P, _I, _P, _P, _P]),
         "hq_mg_restrict": (_I, [_P, _I, _P, _P]),
         "hq_mg_prolong": (_I, [_P, _I, _P, _P, _P]),
         "hq_mg_coarse_solve": (_I, [_P, _P, _P]),
@@ -476,6 +478,15 @@ class Solver:
         zout = self._torch.empty_like(zin)
         self._check(self.lib.hq_mg_smooth(self._ctx, level, self._dev(r, m ** 3),
                                           self._dev(zin, m ** 3), _dptr(zout)), "hq_mg_smooth")
+        return zout
+
+    def mg_smooth_prescaled(self, level, rt, zin):
+        """The FP64 V-cycle's sweep from rt = omega D^-1 r (FP64 contexts)."""
+        m = self.levels()[level]
+        zout = self._torch.empty_like(zin)
+        self._check(self.lib.hq_mg_smooth_prescaled(self._ctx, level, self._dev(rt, m ** 3),
+                                                    self._dev(zin, m ** 3), _dptr(zout)),
+                    "hq_mg_smooth_prescaled")
         return zout
 
     def mg_restrict(self, level, rf):

@@ -47,6 +47,35 @@ def test_multigrid_pieces_match_oracle(m, N):
     assert rel(host(s.mg_coarse_solve(dev(r))), mg.coarse_solve(r)) < 1e-11
 
 
+@pytest.mark.parametrize("m,N", [(9, 2), (17, 5), (24, 8)])
+def test_prescaled_sweep_matches_oracle_sweep(m, N):
+    """The FP64 V-cycle's sweep from rt = omega D^-1 r (D = 6c + V_l + sigma,
+    c = 1/(2 h_l^2)) equals the damped-Jacobi sweep of r on every level above
+    the coarsest; the coarsest level and FP32 contexts refuse it."""
+    from paper_2605_25149_gb300 import hq
+    s, V, _ = make(m, N)
+    mg = oracle_mg(s, V)
+    om, sigma = s.cfg.mg_omega, s.info()["sigma"]
+    rng = np.random.default_rng(3 * m + N)
+    for l, ml in enumerate(mg.levels[:-1]):
+        D = 6.0 / (2.0 * inputs.grid_h(ml) ** 2) + mg.level_potential(l) + sigma
+        r = rng.standard_normal((ml ** 3, N))
+        z = rng.standard_normal((ml ** 3, N))
+        rt = (om / D)[:, None] * r
+        got = host(s.mg_smooth_prescaled(l, dev(rt), dev(z)))
+        assert rel(got, mg.smooth(l, r, z)) < TOL64, l
+    mc = mg.levels[-1]
+    with pytest.raises(hq.HQError) as ei:
+        s.mg_smooth_prescaled(len(mg.levels) - 1, dev(np.zeros((mc ** 3, N))),
+                              dev(np.zeros((mc ** 3, N))))
+    assert ei.value.status == 1   # HQ_ERR_ARG
+    t, _, _ = make(m, N, precision="mixed", cg_rtol=1e-6)
+    z32 = dev(np.zeros((m ** 3, N), np.float32))
+    with pytest.raises(hq.HQError) as ei:
+        t.mg_smooth_prescaled(0, z32, z32.clone())
+    assert ei.value.status == 2   # HQ_ERR_STATE
+
+
 @pytest.mark.parametrize("m,N", [(9, 3), (16, 6), (20, 8), (33, 12)])
 def test_mixed_transfers_match_oracle(m, N):
     """FP32 restriction and prolongation-with-correction on every level
