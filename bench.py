@@ -51,10 +51,11 @@ ALGO_F64 = dict(ALGO, smooth=(9.0, 3.0))
 FP64_OPS = {"smooth": 7.0, "stencil": 7.0, "residual": 8.0}
 # DRAM bytes per point-column of the finest-level smooth kernel measured by
 # ncu (dram__bytes_read.sum + dram__bytes_write.sum of one launch / 16.78 M
-# point-columns, profiles/k_jacobi_k_jacobi_zm_wells64_N64.md: k_jacobi_zm
-# for the 134 MB FP64 block, k_jacobi for the 67 MB FP32 block); set to None
-# whenever the kernel changes until it is captured again.
-TRAFFIC_PER_ELEMENT = {("smooth", "f64"): None,
+# point-columns, profiles/k_jacobi_k_jacobi_zm_wells64_N64.md: the pre-scaled
+# k_jacobi_zm of a post-smoothing sweep for the 134 MB FP64 block, k_jacobi
+# for the 67 MB FP32 block); set to None whenever the kernel changes until it
+# is captured again.
+TRAFFIC_PER_ELEMENT = {("smooth", "f64"): (272.048896e6 + 107.949824e6) / 16777216,
                        ("smooth", "f32"): (136.215040e6 + 44.029440e6) / 16777216}
 
 
