@@ -42,13 +42,13 @@ FP64_PEAK_GFLOPS = 2 * 152 * 2.07 * 2
 #            (fma), (1-omega) z (mul), + wD (...) (fma): 10 flops; reads r, z,
 #            writes z': 3 words
 #   stencil  y = D x - c s: 5 add + mul + fma = 8 flops; 2 words
-#   residual b - (D x - c s): 9 flops; 3 words
+#   residual (b - D x) + c s: 5 add + 2 fma = 9 flops; 3 words
 ALGO = {"smooth": (10.0, 3.0), "stencil": (8.0, 2.0), "residual": (9.0, 3.0)}
 # FP64 V-cycles sweep from the pre-scaled right-hand side rt = omega D^-1 r:
 #   z' = (omega c D^-1) s + ((1 - omega) z + rt): 5 add + 2 fma = 9 flops in 7
 #   FP64-pipe instructions; reads rt, z, writes z': 3 words
 ALGO_F64 = dict(ALGO, smooth=(9.0, 3.0))
-FP64_OPS = {"smooth": 7.0, "stencil": 7.0, "residual": 8.0}
+FP64_OPS = {"smooth": 7.0, "stencil": 7.0, "residual": 7.0}
 # DRAM bytes per point-column of the finest-level smooth kernel measured by
 # ncu (dram__bytes_read.sum + dram__bytes_write.sum of one launch / 16.78 M
 # point-columns, profiles/k_jacobi_k_jacobi_zm_wells64_N64.md: the pre-scaled

@@ -121,6 +121,8 @@ __device__ __forceinline__ VT<T, V> nbr_sum(const T *__restrict__ x, size_t e, i
 // ---------------------------------------------------------------------------
 // 7-point operator.  MODE 0: y = A x (+ x.y);  MODE 1: y = b - A x (+ y.y, b.b)
 // A x = D x - c (x_w + x_e + x_s + x_n + x_b + x_t),  D = 6c + V + sigma.
+// The residual is formed as (b - D x) + c s: two FMAs after the neighbour
+// sum, one FP64-pipe instruction fewer than b - (D x - c s).
 // PART: form the partial sums (a compile-time switch: in FP64 the extra
 // products are a measurable share of the FP64-pipe work of a sweep).
 // ---------------------------------------------------------------------------
@@ -150,13 +152,14 @@ __global__ void __launch_bounds__(256) k_stencil(int m, long n, int N, int ppt,
         VT<T, V> s = nbr_sum<T, V>(x, e, i, j, kk, m, sx, sy, sz);
         T d = D[p];
         VT<T, V> o;
+        VT<T, V> bb;
+        if (MODE == 1) bb = ldv<T, V>(b + e);
 #pragma unroll
-        for (int v = 0; v < V; v++) o.v[v] = d * xc.v[v] - c * s.v[v];
+        for (int v = 0; v < V; v++)
+            o.v[v] = MODE == 1 ? (bb.v[v] - d * xc.v[v]) + c * s.v[v] : d * xc.v[v] - c * s.v[v];
         if (MODE == 1) {
-            VT<T, V> bb = ldv<T, V>(b + e);
 #pragma unroll
             for (int v = 0; v < V; v++) {
-                o.v[v] = bb.v[v] - o.v[v];
                 if (PART) {
                     a1[v] += o.v[v] * o.v[v];
                     a2[v] += bb.v[v] * bb.v[v];
@@ -391,18 +394,19 @@ __global__ void __launch_bounds__(256) k_stencil_zm(int m, int N, int nseg, int 
             VT<T, V> a2 = ldv<T, V>(x + (bs ? e - sy : e)), a3 = ldv<T, V>(x + (bn ? e + sy : e));
             const T d = D[p];
             VT<T, V> o;
+            VT<T, V> bb;
+            if (MODE == 1) bb = ldv<T, V>(b + e);
 #pragma unroll
             for (int v = 0; v < V; v++) {
                 const T sum = (((bw ? a0.v[v] : T(0)) + (be ? a1.v[v] : T(0))) +
                                ((bs ? a2.v[v] : T(0)) + (bn ? a3.v[v] : T(0)))) +
                               (xprev.v[v] + xnext.v[v]);
-                o.v[v] = d * xcur.v[v] - c * sum;
+                o.v[v] = MODE == 1 ? (bb.v[v] - d * xcur.v[v]) + c * sum
+                                   : d * xcur.v[v] - c * sum;
             }
             if (MODE == 1) {
-                VT<T, V> bb = ldv<T, V>(b + e);
 #pragma unroll
                 for (int v = 0; v < V; v++) {
-                    o.v[v] = bb.v[v] - o.v[v];
                     if (PART) {
                         s1[v] += o.v[v] * o.v[v];
                         s2[v] += bb.v[v] * bb.v[v];
@@ -557,8 +561,13 @@ __device__ __forceinline__ const float *wsel<float>(const double *, const float 
 
 // One 1-D pass along `axis` (0 = x, fastest; 1 = y; 2 = z).  Output dims
 // (o2, o1, o0), input dims equal except along the axis (ilen).  Output index
-// o along the axis takes taps idx[o*NT + t] (input index, -1 = none) with
-// weights w[o*NT + t]:  out = scale * sum_t w in (+ add).
+// o along the axis takes taps idx[o*NT + t] (input index, -1 = none; the
+// valid taps come first) with weights w[o*NT + t]:
+//   out = scale * sum_t w in          (no add)
+//   out = add + sum_t w in            (scale = 1: the sum starts from add)
+// With scale = 1 no multiply is issued (the restriction's x and y passes,
+// every prolongation pass): in FP64 these passes are bound by the FP64 pipe,
+// and a tap costs one FMA.  The taps' loads are issued before their FMAs.
 template <typename T, int V, int NT>
 __global__ void __launch_bounds__(256) k_axis_pass(int o2, int o1, int o0, int ilen, int axis,
                                                    int N, int ppt, const int *__restrict__ idx,
@@ -571,44 +580,48 @@ __global__ void __launch_bounds__(256) k_axis_pass(int o2, int o1, int o0, int i
     const int col = (blockIdx.x * blockDim.x + threadIdx.x) * V;
     if (col >= N) return;
     const T *w = wsel<T>(wd, wf);
-    const long nout = (long)o2 * o1 * o0;
+    const bool unit = scale == T(1);
+    const unsigned nout = (unsigned)o2 * (unsigned)o1 * (unsigned)o0;   // m <= 1024: < 2^30
     const int d0 = axis == 0 ? ilen : o0;
     const int d1 = axis == 1 ? ilen : o1;
     const size_t s0 = (size_t)N, s1 = (size_t)d0 * N, s2 = (size_t)d1 * d0 * N;
     const size_t sa = axis == 0 ? s0 : (axis == 1 ? s1 : s2);
-    const long base = (long)blockIdx.y * TY * ppt;
+    const unsigned base = blockIdx.y * (unsigned)TY * (unsigned)ppt;
     for (int k = 0; k < ppt; k++) {
-        long p = base + (long)k * TY + threadIdx.y;
+        const unsigned p = base + (unsigned)k * TY + threadIdx.y;
         if (p >= nout) continue;
-        const int i0 = (int)(p % o0);
-        const long q = p / o0;
-        const int i1 = (int)(q % o1);
-        const int i2 = (int)(q / o1);
-        const int oa = axis == 0 ? i0 : (axis == 1 ? i1 : i2);
+        const unsigned i0 = p % (unsigned)o0;
+        const unsigned q = p / (unsigned)o0;
+        const unsigned i1 = q % (unsigned)o1;
+        const unsigned i2 = q / (unsigned)o1;
+        const unsigned oa = axis == 0 ? i0 : (axis == 1 ? i1 : i2);
         const size_t ib = (axis == 0 ? 0 : (size_t)i0 * s0) + (axis == 1 ? 0 : (size_t)i1 * s1) +
                           (axis == 2 ? 0 : (size_t)i2 * s2) + col;
-        T acc[V];
-#pragma unroll
-        for (int v = 0; v < V; v++) acc[v] = T(0);
+        const size_t oe = (size_t)p * N + col;
+        int ii[NT];
+        T wt[NT];
+        VT<T, V> a[NT];
 #pragma unroll
         for (int t = 0; t < NT; t++) {
-            const int ii = idx[oa * NT + t];
-            if (ii < 0) continue;
-            const T wt = w[oa * NT + t];
-            VT<T, V> a = ldv<T, V>(in + ib + (size_t)ii * sa);
-#pragma unroll
-            for (int v = 0; v < V; v++) acc[v] += wt * a.v[v];
+            ii[t] = idx[oa * NT + t];
+            wt[t] = w[oa * NT + t];
+            if (ii[t] >= 0) a[t] = ldv<T, V>(in + ib + (size_t)ii[t] * sa);
         }
-        const size_t oe = (size_t)p * N + col;
+        VT<T, V> e;
+        if (add) e = ldv<T, V>(add + oe);
+        T acc[V];
+#pragma unroll
+        for (int v = 0; v < V; v++) acc[v] = (add && unit) ? e.v[v] : T(0);
+#pragma unroll
+        for (int t = 0; t < NT; t++) {
+            if (ii[t] < 0) continue;
+#pragma unroll
+            for (int v = 0; v < V; v++) acc[v] += wt[t] * a[t].v[v];
+        }
         VT<T, V> o;
-        if (add) {
-            VT<T, V> a = ldv<T, V>(add + oe);
 #pragma unroll
-            for (int v = 0; v < V; v++) o.v[v] = a.v[v] + scale * acc[v];
-        } else {
-#pragma unroll
-            for (int v = 0; v < V; v++) o.v[v] = scale * acc[v];
-        }
+        for (int v = 0; v < V; v++)
+            o.v[v] = unit ? acc[v] : (add ? e.v[v] + scale * acc[v] : scale * acc[v]);
         stv<T, V>(out + oe, o);
     }
 }
