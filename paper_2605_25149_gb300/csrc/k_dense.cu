@@ -526,10 +526,15 @@ __global__ void __launch_bounds__(512) k_lu_panel(int nn, int k0, int nb, double
         }
         __syncthreads();
         const double djj = P[jj * ld + jj];
-        for (int r = jj + 1 + tid; r < R; r += T) {
-            const double l = P[r * ld + jj] / djj;
-            P[r * ld + jj] = l;
-            for (int c = jj + 1; c < nb; c++) P[r * ld + c] -= l * P[jj * ld + c];
+        for (int r = jj + 1 + tid; r < R; r += T) P[r * ld + jj] = P[r * ld + jj] / djj;
+        __syncthreads();
+        // trailing part of the panel: lane = column, warps stride the rows, so
+        // all warps share the FP64 work (each element sees the same
+        // multiply-subtract sequence over jj as a row-per-thread loop)
+        const int c = jj + 1 + lane;
+        if (c < nb) {
+            const double u = P[jj * ld + c];
+            for (int r = jj + 1 + warp; r < R; r += (T >> 5)) P[r * ld + c] -= P[r * ld + jj] * u;
         }
         __syncthreads();
     }
@@ -569,17 +574,24 @@ __global__ void __launch_bounds__(128) k_lu_trsm(int nn, int N, int k0, int nb, 
             col[(size_t)piv * ld] = a;
         }
     }
+    // the column's nb entries are loaded together, solved in registers and
+    // stored together (same arithmetic as row-by-row)
     double x[PB];
+#pragma unroll
+    for (int r = 0; r < PB; r++)
+        if (r < nb) x[r] = col[(size_t)(k0 + r) * ld];
 #pragma unroll
     for (int r = 0; r < PB; r++) {
         if (r < nb) {
-            double v = col[(size_t)(k0 + r) * ld];
+            double v = x[r];
 #pragma unroll
             for (int q = 0; q < r; q++) v -= L[r][q] * x[q];
             x[r] = v;
-            col[(size_t)(k0 + r) * ld] = v;
         }
     }
+#pragma unroll
+    for (int r = 0; r < PB; r++)
+        if (r < nb) col[(size_t)(k0 + r) * ld] = x[r];
 }
 
 // trailing update: rows [k0+nb, nn) of every column right of the panel
@@ -633,18 +645,24 @@ __global__ void __launch_bounds__(128) k_lu_back_diag(int nn, int N, int k0, int
     __syncthreads();
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
+    // loads first, the substitution in registers, stores last (same arithmetic)
     double x[PB];
+#pragma unroll
+    for (int r = 0; r < PB; r++)
+        if (r < nb) x[r] = XY[(size_t)(k0 + r) * N + c];
 #pragma unroll
     for (int r = PB - 1; r >= 0; r--) {
         if (r < nb) {
-            double v = XY[(size_t)(k0 + r) * N + c];
+            double v = x[r];
 #pragma unroll
             for (int q = r + 1; q < PB; q++)
                 if (q < nb) v -= Ub[r][q] * x[q];
             x[r] = v / Ub[r][r];
-            XY[(size_t)(k0 + r) * N + c] = x[r];
         }
     }
+#pragma unroll
+    for (int r = 0; r < PB; r++)
+        if (r < nb) XY[(size_t)(k0 + r) * N + c] = x[r];
 }
 
 // rows [0, k0): Y -= U[0:k0, k0:k0+nb] X_b (64 x 64 tiles)
