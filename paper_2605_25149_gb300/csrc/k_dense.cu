@@ -877,50 +877,62 @@ __global__ void __launch_bounds__(64) k_resid64(int nn, int nr, const double *A,
     R[e] = s;
 }
 
-// X += (LU)^-1 P R with the stored FP32 factors
-__global__ void __launch_bounds__(LU32_THREADS) k_lu32_resolve(int nn, int nr, const float *LU,
-                                                             const int *ipiv, const double *R,
-                                                             double *X) {
+// X += (LU)^-1 P R with the stored FP32 factors.  The right-hand sides are
+// independent: each CTA takes RS_COLS of them (RS_THREADS threads: column =
+// tid % RS_COLS, row slot = tid / RS_COLS), so the 2 nn barriers of the two
+// substitutions are barriers of a few warps; every element sees the same
+// operations in the same order as a single-CTA solve.
+constexpr int RS_COLS = 8, RS_THREADS = 256, RS_SLOTS = RS_THREADS / RS_COLS;
+size_t lu32_resolve_smem(int nn) {
+    return sizeof(float) * ((size_t)nn * (nn + 1) + (size_t)nn * RS_COLS);
+}
+__global__ void __launch_bounds__(RS_THREADS) k_lu32_resolve(int nn, int nr, const float *LU,
+                                                           const int *ipiv, const double *R,
+                                                           double *X) {
     extern __shared__ float sm32[];
     float *sA = sm32;
     float *sB = sm32 + (size_t)nn * (nn + 1);
-    const int T = blockDim.x, tid = threadIdx.x, la = nn + 1;
-    const int lx = tid & 31, wy = tid >> 5, NW = T >> 5;
-    for (int r = wy; r < nn; r += NW) {
-        for (int c = lx; c < nn; c += 32) sA[r * la + c] = LU[(size_t)r * nn + c];
-        for (int c = lx; c < nr; c += 32) sB[r * nr + c] = (float)R[(size_t)r * nr + c];
+    const int tid = threadIdx.x, la = nn + 1;
+    const int cc = tid % RS_COLS, slot = tid / RS_COLS;
+    const int c = blockIdx.x * RS_COLS + cc;
+    const bool cv = c < nr;
+    for (int idx = tid; idx < nn * nn; idx += RS_THREADS) {
+        const int r = idx / nn, q = idx - r * nn;
+        sA[r * la + q] = LU[idx];
     }
+    for (int r = slot; r < nn; r += RS_SLOTS)
+        sB[r * RS_COLS + cc] = cv ? (float)R[(size_t)r * nr + c] : 0.f;
     __syncthreads();
     // row swaps in elimination order, one thread per right-hand side
-    for (int c = tid; c < nr; c += T)
+    if (slot == 0)
         for (int k = 0; k < nn; k++) {
             const int p = ipiv[k];
             if (p != k) {
-                const float t = sB[k * nr + c];
-                sB[k * nr + c] = sB[p * nr + c];
-                sB[p * nr + c] = t;
+                const float t = sB[k * RS_COLS + cc];
+                sB[k * RS_COLS + cc] = sB[p * RS_COLS + cc];
+                sB[p * RS_COLS + cc] = t;
             }
         }
     __syncthreads();
     for (int k = 0; k < nn - 1; k++) {
-        for (int r = k + 1 + wy; r < nn; r += NW) {
-            const float l = sA[r * la + k];
-            for (int c = lx; c < nr; c += 32) sB[r * nr + c] -= l * sB[k * nr + c];
-        }
+        const float bk = sB[k * RS_COLS + cc];
+        for (int r = k + 1 + slot; r < nn; r += RS_SLOTS)
+            sB[r * RS_COLS + cc] -= sA[r * la + k] * bk;
         __syncthreads();
     }
     for (int k = nn - 1; k >= 0; k--) {
         const float inv = 1.0f / sA[k * la + k];
-        for (int r = wy; r < k; r += NW) {
+        const float bk = sB[k * RS_COLS + cc];
+        for (int r = slot; r < k; r += RS_SLOTS) {
             const float u = sA[r * la + k] * inv;
-            for (int c = lx; c < nr; c += 32) sB[r * nr + c] -= u * sB[k * nr + c];
+            sB[r * RS_COLS + cc] -= u * bk;
         }
         __syncthreads();
-        for (int c = tid; c < nr; c += T) sB[k * nr + c] *= inv;
+        if (slot == 0) sB[k * RS_COLS + cc] *= inv;
     }
     __syncthreads();
-    for (int r = wy; r < nn; r += NW)
-        for (int c = lx; c < nr; c += 32) X[(size_t)r * nr + c] += (double)sB[r * nr + c];
+    if (cv)
+        for (int r = slot; r < nn; r += RS_SLOTS) X[(size_t)r * nr + c] += (double)sB[r * RS_COLS + cc];
 }
 
 void lu32_prepare() {
@@ -944,7 +956,8 @@ void launch_solve32_refined(int nn, int nr, const double *A, int lda, const doub
     for (int it = 0; it < refine; it++) {
         HQ_LAUNCH(HQ_K_SMALL, k_resid64<<<(nn * nr + 63) / 64, 64, 0, s>>>(nn, nr, A, lda, B, ldb,
                                                                           X, R));
-        HQ_LAUNCH(HQ_K_SMALL, k_lu32_resolve<<<1, LU32_THREADS, shm, s>>>(nn, nr, LU, ipiv, R, X));
+        HQ_LAUNCH(HQ_K_SMALL, k_lu32_resolve<<<(nr + RS_COLS - 1) / RS_COLS, RS_THREADS,
+                                                 lu32_resolve_smem(nn), s>>>(nn, nr, LU, ipiv, R, X));
     }
 }
 
