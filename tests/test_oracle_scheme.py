@@ -43,6 +43,39 @@ def test_step_satisfies_predictor_equation():
     assert res < 1e-12
 
 
+def test_predictor_solve_worked_check_and_step_consistency():
+    """The predictor system of Eq. (4.1) on the Gram of exact eigenvector
+    columns u_j = c_j phi_j, w_j = G u_j = u_j / mu_j (S = diag c^2,
+    P_uw = P_wu = diag c^2/mu, Q = diag c^2/mu^2) has the closed-form
+    solution X = S, Y = P_wu, so that Uh = U (I - tau Y) + W tau X = U.  On a
+    general Gram, the standalone solve equals the one inside the step."""
+    N, tau = 5, 0.7
+    c2 = np.array([0.5, 1.0, 1.5, 2.0, 3.0])
+    mu = np.array([0.9, 0.4, 0.25, 0.1, 0.05])
+    S, P, Q = np.diag(c2), np.diag(c2 / mu), np.diag(c2 / mu ** 2)
+    gram = np.block([[S, P], [P, Q]])
+    XY, C = O.predictor(gram, tau)
+    # each column decouples into a 2 x 2 system of determinant 1 whose
+    # entries reach tau c^2 / (2 mu^2) = 420 (mu = 0.05): condition ~2e5, so
+    # the elimination's rounding allows ~2e5 ulps
+    tol = 1e-10
+    np.testing.assert_allclose(XY[:N], S, rtol=tol, atol=tol)
+    np.testing.assert_allclose(XY[N:], P, rtol=tol, atol=tol)
+    # C1 = I - tau Y, C2 = tau X, and [U W] C = U for W = U diag(1/mu)
+    np.testing.assert_allclose(C[:N], np.eye(N) - tau * P, rtol=tol, atol=tol)
+    np.testing.assert_allclose(C[N:], tau * S, rtol=tol, atol=tol)
+    rng = np.random.default_rng(4)
+    U = rng.standard_normal((40, N))
+    np.testing.assert_allclose(U @ C[:N] + (U / mu) @ C[N:], U, rtol=tol, atol=tol)
+    # general Gram: the step's own [X; Y] is the standalone solve, bit for bit
+    m = 8
+    V, sigma, h3, U = _problem(m, 4, seed_u=3, V=I.wells(8, 5))
+    st = O.scheme_step(m, V, sigma, U, 0.4)
+    XY2, C2 = O.predictor(st["gram"], 0.4)
+    assert np.array_equal(XY2, st["XY"])
+    np.testing.assert_allclose(st["Uh"], np.hstack([U, st["W"]]) @ C2, rtol=1e-13, atol=1e-14)
+
+
 def test_step_satisfies_corrector_equation():
     """(U+ - Uh)/tau = -G Uh (<Uh,Uh> - I), with Z = G Uh checked by residual."""
     m, N, tau = 8, 4, 0.4
