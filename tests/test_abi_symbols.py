@@ -85,3 +85,19 @@ def test_launch_shape_fields_and_tuner_workspace():
     assert hq.workspace_bytes(hq.default_config(32, 16, grid_ctas=65)) == 0
     out = hq.Config()
     assert lib.hq_tune(ctypes.byref(c), None, 0, None, ctypes.byref(out), None) == 4
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """No CPU fallback: without the built libhq.so, loading raises."""
+    monkeypatch.setattr(hq, "_lib", None)
+    monkeypatch.setattr(hq, "LIB_PATH", "/nonexistent/libhq.so")
+    with pytest.raises(RuntimeError, match="not built"):
+        hq.load()
+
+
+def test_device_operands_must_be_cuda_tensors():
+    """Host tensors are refused before any call reaches the library."""
+    import torch
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        hq._dptr(torch.zeros(4, dtype=torch.float64))
+    assert hq._dptr(None) is None
