@@ -778,7 +778,7 @@ __device__ __forceinline__ void lu32_argmax(float v, int i, float *wv, int *wi, 
 
 // A (nn x nn, lda) and B (nn x nr, ldb) in FP64; factors LU (nn x nn FP32,
 // L unit lower below the diagonal, rows permuted) and ipiv to global memory;
-// X (nn x nr, FP64) = the FP32 solution.  Work is mapped row = warp, column =
+// X (nn x nr, FP64) = the FP32 solution (nr = 0: factors only).  Work is mapped row = warp, column =
 // lane (no integer division in the loops).
 __global__ void __launch_bounds__(LU32_THREADS) k_lu32_factor_solve(int nn, int nr, const double *A,
                                                                   int lda, const double *B, int ldb,
@@ -837,17 +837,20 @@ __global__ void __launch_bounds__(LU32_THREADS) k_lu32_factor_solve(int nn, int 
         // (column k below the diagonal is read by no later step of this loop)
     }
     __syncthreads();
-    for (int k = nn - 1; k >= 0; k--) {
-        const float inv = 1.0f / sA[k * la + k];
-        for (int r = wy; r < k; r += NW) {
-            const float u = sA[r * la + k] * inv;
-            for (int c = lx; c < nr; c += 32) sB[r * nr + c] -= u * sB[k * nr + c];
+    // nr == 0: factors only (the solves run in k_lu32_resolve)
+    if (nr > 0) {
+        for (int k = nn - 1; k >= 0; k--) {
+            const float inv = 1.0f / sA[k * la + k];
+            for (int r = wy; r < k; r += NW) {
+                const float u = sA[r * la + k] * inv;
+                for (int c = lx; c < nr; c += 32) sB[r * nr + c] -= u * sB[k * nr + c];
+            }
+            __syncthreads();
+            for (int c = tid; c < nr; c += T) sB[k * nr + c] *= inv;
+            // row k is read by no later step
         }
         __syncthreads();
-        for (int c = tid; c < nr; c += T) sB[k * nr + c] *= inv;
-        // row k is read by no later step
     }
-    __syncthreads();
     for (int r = wy; r < nn; r += NW) {
         for (int c = lx; c < nn; c += 32) LU[(size_t)r * nn + c] = sA[r * la + c];
         for (int c = lx; c < nr; c += 32) X[(size_t)r * nr + c] = (double)sB[r * nr + c];
@@ -877,7 +880,11 @@ __global__ void __launch_bounds__(64) k_resid64(int nn, int nr, const double *A,
     R[e] = s;
 }
 
-// X += (LU)^-1 P R with the stored FP32 factors.  The right-hand sides are
+// X = (LU)^-1 P R, or X += (LU)^-1 P R (accumulate), with the stored FP32
+// factors; R has leading dimension ldr, X is dense nn x nr.  The solves of
+// the first solution and of every refinement step run here (the row swaps
+// applied first, then the eliminations: the same operations per row as
+// swapping during the factorisation).  The right-hand sides are
 // independent: each CTA takes RS_COLS of them (RS_THREADS threads: column =
 // tid % RS_COLS, row slot = tid / RS_COLS), so the 2 nn barriers of the two
 // substitutions are barriers of a few warps; every element sees the same
@@ -888,7 +895,7 @@ size_t lu32_resolve_smem(int nn) {
 }
 __global__ void __launch_bounds__(RS_THREADS) k_lu32_resolve(int nn, int nr, const float *LU,
                                                            const int *ipiv, const double *R,
-                                                           double *X) {
+                                                           int ldr, double *X, int accumulate) {
     extern __shared__ float sm32[];
     float *sA = sm32;
     float *sB = sm32 + (size_t)nn * (nn + 1);
@@ -901,7 +908,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_lu32_resolve(int nn, int nr, con
         sA[r * la + q] = LU[idx];
     }
     for (int r = slot; r < nn; r += RS_SLOTS)
-        sB[r * RS_COLS + cc] = cv ? (float)R[(size_t)r * nr + c] : 0.f;
+        sB[r * RS_COLS + cc] = cv ? (float)R[(size_t)r * ldr + c] : 0.f;
     __syncthreads();
     // row swaps in elimination order, one thread per right-hand side
     if (slot == 0)
@@ -932,7 +939,10 @@ __global__ void __launch_bounds__(RS_THREADS) k_lu32_resolve(int nn, int nr, con
     }
     __syncthreads();
     if (cv)
-        for (int r = slot; r < nn; r += RS_SLOTS) X[(size_t)r * nr + c] += (double)sB[r * RS_COLS + cc];
+        for (int r = slot; r < nn; r += RS_SLOTS) {
+            const double v = (double)sB[r * RS_COLS + cc];
+            X[(size_t)r * nr + c] = accumulate ? X[(size_t)r * nr + c] + v : v;
+        }
 }
 
 void lu32_prepare() {
@@ -944,20 +954,30 @@ void lu32_prepare() {
     done = true;
 }
 
+// FP32 factors of A in one CTA, then X = (LU)^-1 P B over RS_COLS-column CTAs
+static void lu32_factor_then_solve(int nn, int nr, const double *A, int lda, const double *B,
+                                   int ldb, double *X, float *LU, int *ipiv, int *status,
+                                   cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_SMALL, k_lu32_factor_solve<<<1, LU32_THREADS, lu32_smem(nn, 0), s>>>(
+                              nn, 0, A, lda, nullptr, 0, LU, ipiv, nullptr, status));
+    HQ_LAUNCH(HQ_K_SMALL, k_lu32_resolve<<<(nr + RS_COLS - 1) / RS_COLS, RS_THREADS,
+                                             lu32_resolve_smem(nn), s>>>(nn, nr, LU, ipiv, B, ldb,
+                                                                          X, 0));
+}
+
 // X = A^-1 B (A nn x nn, B nn x nr, FP64 in and out) by FP32 elimination and
 // `refine` FP64 refinement steps; LU (nn^2 floats), ipiv (nn) and R (nn x nr
 // doubles) are scratch.  Requires lu32_fits(nn, nr).
 void launch_solve32_refined(int nn, int nr, const double *A, int lda, const double *B, int ldb,
                             double *X, float *LU, int *ipiv, double *R, int refine, int *status,
                             cudaStream_t s) {
-    const size_t shm = lu32_smem(nn, nr);
-    HQ_LAUNCH(HQ_K_SMALL, k_lu32_factor_solve<<<1, LU32_THREADS, shm, s>>>(nn, nr, A, lda, B, ldb,
-                                                                          LU, ipiv, X, status));
+    lu32_factor_then_solve(nn, nr, A, lda, B, ldb, X, LU, ipiv, status, s);
     for (int it = 0; it < refine; it++) {
         HQ_LAUNCH(HQ_K_SMALL, k_resid64<<<(nn * nr + 63) / 64, 64, 0, s>>>(nn, nr, A, lda, B, ldb,
                                                                           X, R));
         HQ_LAUNCH(HQ_K_SMALL, k_lu32_resolve<<<(nr + RS_COLS - 1) / RS_COLS, RS_THREADS,
-                                                 lu32_resolve_smem(nn), s>>>(nn, nr, LU, ipiv, R, X));
+                                                 lu32_resolve_smem(nn), s>>>(nn, nr, LU, ipiv, R,
+                                                                              nr, X, 1));
     }
 }
 
@@ -1006,8 +1026,7 @@ void launch_spd_solve(int N, const double *A, int lda, const double *B, int ldb,
                       double *L, double *X, int *ipiv, int *status, cudaStream_t s, float *lu32) {
     if (lu32 && ipiv && lu32_fits(N, N)) {
         // mixed-precision path (a warm start only needs FP32 accuracy)
-        HQ_LAUNCH(HQ_K_SMALL, k_lu32_factor_solve<<<1, LU32_THREADS, lu32_smem(N, N), s>>>(
-                                  N, N, A, lda, B, ldb, lu32, ipiv, X, status));
+        lu32_factor_then_solve(N, N, A, lda, B, ldb, X, lu32, ipiv, status, s);
         return;
     }
     if (N <= 32 || !ipiv) {
