@@ -110,7 +110,12 @@ size_t hq_workspace_bytes(const hq_config *cfg);
 /* Creates a context on the current CUDA device.  d_workspace: device buffer
  * of at least hq_workspace_bytes(cfg) bytes, 256-byte aligned, owned by the
  * caller and kept alive until hq_destroy.  cuda_stream: a cudaStream_t (NULL
- * = default stream).                                                        */
+ * = default stream).  Two environment switches are read here, for tests and
+ * profiling: HQ_NO_GRAPHS=1 runs hq_step / hq_solve host-driven instead of
+ * replaying captured graphs (same kernels in the same order, bit-identical
+ * results); HQ_ZMARCH=1 / 0 forces the z-marching finest-level sweeps on / off
+ * (by default they run for finest-level blocks of 100 MB or more; same
+ * element values, PCG dot products summed in another order).              */
 hq_status hq_init(const hq_config *cfg, void *d_workspace, size_t bytes,
                   void *cuda_stream, hq_ctx **out);
 
