@@ -157,6 +157,43 @@ def test_exact_eigenvectors_are_fixed_points():
     assert s1["g"] < 1e-12
 
 
+def test_grad_norm_alone_closed_form_rotation_and_dense():
+    """orc_grad_norm (g = ||G U - U <G U,U>||, Remark 3.1, without a step):
+    on exact eigenvector columns U = Phi diag(c) it equals the closed form
+    sqrt(sum_i (c_i (1 - c_i^2) / lambda_i)^2) and vanishes for c = 1; it is
+    invariant under U -> U Q for orthogonal Q (the gradient transforms as
+    R -> R Q); on a wells potential it equals the definition evaluated with a
+    dense solve of (H_h + sigma) W = U."""
+    m = 8
+    mu, phi = np.linalg.eigh(harmonic_1d(m, -6.0, 6.0))
+    h3 = O.grid_h(m) ** 3
+    cols, lam = [], []
+    for a, b, c in [(0, 0, 0), (1, 0, 0), (0, 1, 1), (2, 0, 1)]:
+        cols.append(np.einsum("k,j,i->kji", phi[:, c], phi[:, b], phi[:, a]).ravel() / np.sqrt(h3))
+        lam.append(mu[a] + mu[b] + mu[c])
+    lam = np.array(lam)
+    cvec = np.array([0.7, 1.0, 1.2, 1.45])
+    V = I.harmonic(m)
+    U = np.stack(cols, 1) * cvec
+    g, W = O.grad_norm(m, V, 0.0, U)
+    assert g == pytest.approx(np.sqrt(np.sum((cvec * (1 - cvec ** 2) / lam) ** 2)), rel=1e-10)
+    np.testing.assert_allclose(W, U / lam, rtol=1e-10, atol=1e-12)
+    g1, _ = O.grad_norm(m, V, 0.0, U / cvec)
+    assert g1 < 1e-12
+    Qr, _ = np.linalg.qr(np.random.default_rng(5).standard_normal((4, 4)))
+    gq, _ = O.grad_norm(m, V, 0.0, U @ Qr)
+    assert gq == pytest.approx(g, rel=1e-10)
+    # wells, general U: the definition with a dense solve
+    m = 6
+    V, sigma, h3, U = _problem(m, 3, seed_u=13, V=I.wells(6, 4))
+    gw, Ww = O.grad_norm(m, V, sigma, U)
+    A = dense_h(m, O.grid_h(m), V, sigma)
+    Wd = np.linalg.solve(A, U)
+    R = Wd - U @ (h3 * Wd.T @ U)
+    assert gw == pytest.approx(np.sqrt(h3 * np.sum(R * R)), rel=1e-10)
+    np.testing.assert_allclose(Ww, Wd, rtol=1e-10, atol=1e-12)
+
+
 def test_invariants_along_trajectory():
     """Theorem 4.5 (monotone energy of the shifted form) and Theorem 4.6
     (orthogonality error decreases) hold step by step for tau below the
