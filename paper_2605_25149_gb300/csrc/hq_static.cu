@@ -14,7 +14,9 @@
 // The host never uses the array's name as a device address (in host code
 // that name is only a stand-in): the first call on each device, with that
 // device current, asks the runtime for the array's device address with
-// cudaGetSymbolAddress, checks the result and caches it for that device.
+// cudaGetSymbolAddress, checks the result and caches it for that device.  The
+// cached address belongs to that device's context: after cudaDeviceReset the
+// entry point must not be called again in the same process.
 #include <mutex>
 
 #include "../../include/hq.h"
@@ -66,11 +68,19 @@ extern "C" hq_status hq_gram_static(const double *A, int Na, const double *B, in
         p.chunks = (int)((n + rows - 1) / rows);
     }
     if ((size_t)p.chunks * per_chunk > HQ_GRAM_STATIC_SCRATCH) return HQ_ERR_ARG;
+    // an error left pending by the caller's earlier work is not this call's:
+    // report it without launching and without clearing it
+    if (cudaPeekAtLastError() != cudaSuccess) return HQ_ERR_CUDA;
     double *scratch = nullptr;
     hq_status st = static_scratch(&scratch);
     if (st != HQ_OK) return st;
     // every partial tile is written before it is read: nothing to clear
     launch_gram<double>(p, A, Na, nullptr, 0, B, Nb, nullptr, 0, w, scratch, out,
                         (cudaStream_t)cuda_stream);
-    return cudaGetLastError() == cudaSuccess ? HQ_OK : HQ_ERR_CUDA;
+    // the slate was clean on entry, so an error now comes from these launches
+    if (cudaPeekAtLastError() != cudaSuccess) {
+        cudaGetLastError();
+        return HQ_ERR_CUDA;
+    }
+    return HQ_OK;
 }

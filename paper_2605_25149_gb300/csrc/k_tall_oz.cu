@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     __shared__ uint64_t mbar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int erow[OZ_M];
-    __shared__ int abort_sh;
+    __shared__ int abort_sh, pend_sh, tmem_free_sh;
     __shared__ double red[OZ_THREADS];
     constexpr uint32_t TCOLS = OZ_S * OZ_NT;   // 512
 
@@ -161,6 +161,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     if (tid == 0) {
         mbar_init(&mbar, 1);
         abort_sh = 0;
+        pend_sh = 0;
+        tmem_free_sh = 1;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -182,7 +184,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 
     for (int ch = 0; ch < kchunks; ch++) {
         if (ch > 0 && tid == 0) {
-            if (!mbar_wait(&mbar, (unsigned)((ch - 1) & 1))) abort_sh = 1;
+            if (!mbar_wait(&mbar, (unsigned)((ch - 1) & 1))) {
+                abort_sh = 1;
+                pend_sh = (ch - 1) & 1;
+            }
         }
         __syncthreads();
         if (abort_sh) break;
@@ -247,8 +252,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         }
     }
     if (!abort_sh && tid == 0) {
-        if (!mbar_wait(&mbar, (unsigned)((kchunks - 1) & 1))) abort_sh = 1;
+        if (!mbar_wait(&mbar, (unsigned)((kchunks - 1) & 1))) {
+            abort_sh = 1;
+            pend_sh = (kchunks - 1) & 1;
+        }
     }
+    // after a wait that gave up, the MMAs of the last commit may still be
+    // writing TMEM: one more bounded wait for them before the columns are
+    // released; if they are still running, the columns stay allocated (only
+    // the status word is meaningful after a timeout)
+    if (abort_sh && tid == 0) tmem_free_sh = mbar_wait(&mbar, (unsigned)pend_sh) ? 1 : 0;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -316,7 +329,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0)
+    if (warp == 0 && tmem_free_sh)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS)
                      : "memory");
 }
@@ -354,7 +367,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     __shared__ uint64_t mbar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int cexp[OZ_M];
-    __shared__ int abort_sh;
+    __shared__ int abort_sh, pend_sh, tmem_free_sh;
     constexpr uint32_t TCOLS = OZ_S * OZ_NT;   // 512
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int na = n1 + n2, ct = blockIdx.x;
@@ -364,6 +377,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     if (tid == 0) {
         mbar_init(&mbar, 1);
         abort_sh = 0;
+        pend_sh = 0;
+        tmem_free_sh = 1;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int c = tid; c < OZ_M; c += OZ_THREADS) cexp[c] = c < na ? colexp[c] : 0;
@@ -415,7 +430,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     if (nslices > 0) load_slice(0);
     for (int sl = 0; sl < nslices; sl++) {
         if (sl > 0 && tid == 0) {
-            if (!mbar_wait(&mbar, (unsigned)((sl - 1) & 1))) abort_sh = 1;
+            if (!mbar_wait(&mbar, (unsigned)((sl - 1) & 1))) {
+                abort_sh = 1;
+                pend_sh = (sl - 1) & 1;
+            }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
@@ -473,8 +491,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         }
     }
     if (!abort_sh && nslices > 0 && tid == 0) {
-        if (!mbar_wait(&mbar, (unsigned)((nslices - 1) & 1))) abort_sh = 1;
+        if (!mbar_wait(&mbar, (unsigned)((nslices - 1) & 1))) {
+            abort_sh = 1;
+            pend_sh = (nslices - 1) & 1;
+        }
     }
+    // as in k_tall_oz: drain the last commit (bounded) before releasing TMEM
+    if (abort_sh && tid == 0) tmem_free_sh = mbar_wait(&mbar, (unsigned)pend_sh) ? 1 : 0;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -502,7 +525,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0)
+    if (warp == 0 && tmem_free_sh)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS)
                      : "memory");
 }

@@ -61,3 +61,27 @@ def test_static_gram_rejects_sizes_beyond_its_limit():
     st = lib.hq_gram_static(ctypes.c_void_p(A.data_ptr()), 513, ctypes.c_void_p(A.data_ptr()), 513,
                             8, 1.0, ctypes.c_void_p(out.data_ptr()), None)
     assert st == 1   # HQ_ERR_ARG
+
+
+def test_static_gram_resplits_points_to_fit_its_array():
+    """Shapes whose planned split over grid points would not fit the fixed
+    array are re-split into fewer, longer point chunks: n = 32^3 with 48 x 17
+    columns (one 64 x 64 tile, 304 planned chunks against room for 128) and
+    the symmetric 512 x 512 Gram (36 tiles per chunk, room for 3 chunks).
+    Both are checked against hq_gram on the same inputs, twice in a row."""
+    import torch
+    lib = hq.load()
+    m, N = 32, 256
+    s = hq.Solver(m, N)
+    s.set_potential(inputs.harmonic(m))
+    w = inputs.grid_h(m) ** 3
+    stream = s.stream.cuda_stream
+    rng = np.random.default_rng(77)
+    for Na, Nb, same in [(48, 17, False), (512, 512, True), (48, 17, False)]:
+        A = torch.from_numpy(rng.standard_normal((m ** 3, Na))).cuda()
+        B = A if same else torch.from_numpy(rng.standard_normal((m ** 3, Nb))).cuda()
+        got = _static_gram(lib, A, B, w, stream)
+        ref = s.gram(A, B, w)
+        torch.cuda.synchronize()
+        got, ref = got.cpu().numpy(), ref.cpu().numpy()
+        assert np.abs(got - ref).max() <= TOL64 * np.abs(ref).max()
