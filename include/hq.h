@@ -26,7 +26,10 @@
  * After any status other than HQ_ERR_CUDA the context stays usable.  No C++
  * exception crosses this boundary.  Device-side failures (CG breakdown, a
  * singular small system) are reported through a status word read at the
- * next synchronisation point; no kernel traps.
+ * next synchronisation point; no kernel traps.  Waits inside the tensor-core
+ * kernels are bounded (2 s of %globaltimer); a wait that gives up reports
+ * HQ_ERR_TIMEOUT ("tensor-core wait expired"), and then only that status is
+ * meaningful: the blocks and matrices the call was writing are undefined.
  *
  * Determinism: reductions run in a fixed order; identical inputs give
  * bit-identical outputs.
@@ -184,6 +187,27 @@ hq_status hq_grad_eigs(hq_ctx *ctx, const double *w, double *dV, int on_device);
 hq_status hq_grad_density(hq_ctx *ctx, const double *G, const double *rho_target, int on_device,
                           double rtol, int maxit, double *dV, double *loss, int *iters);
 
+/* ---- FP64 residual refinement (not in the paper; HQ_FP64 contexts) ----
+ * Refines span(U) of the current iterate in FP64, e.g. after the state of an
+ * HQ_MIXED context was handed over with hq_set_state.  Each of `rounds`
+ * rounds: Rayleigh-Ritz pairs (theta_i, u_i) of H on span(U); residuals
+ * r_i = H u_i - theta_i u_i; corrections t_i in the complement of span(u)
+ * from P (H - theta_i) P t_i = -r_i with P = I - u (h^3 u^T) (Newton's
+ * equation for an invariant subspace, one equation per Ritz vector), solved
+ * together by block PCG with the multigrid V-cycle of H + sigma as
+ * preconditioner, each to ||res_i|| <= rtol ||r_i|| within maxit
+ * iterations; U <- u + t.  P (H - theta_i) P is positive definite on the
+ * complement when every theta_i lies below the spectrum of H there (U close
+ * enough to the N lowest eigenvectors, lambda_N < lambda_{N+1}).  A last
+ * Rayleigh-Ritz leaves U = the Ritz vectors (<u_i,u_j> = delta_ij).  The
+ * step counter is kept; the inner solver's warm start is dropped.
+ * resid (N, host, nullable): ||H u_i - theta_i u_i|| of the final Ritz
+ * pairs; iters (host, nullable): PCG iterations over all rounds.  Errors:
+ * HQ_ERR_STATE (HQ_MIXED context, or no iterate), HQ_ERR_ARG (rounds < 0,
+ * maxit < 1, rtol <= 0), HQ_ERR_NOT_CONVERGED (a correction reached maxit;
+ * U keeps the last completed round), HQ_ERR_BREAKDOWN.                     */
+hq_status hq_refine(hq_ctx *ctx, int rounds, double rtol, int maxit, double *resid, int *iters);
+
 /* Checkpoint: copy U_n (n x N, FP64) and the step counter out / in.  Zwarm
  * (nullable, n x N) is the inner solver's warm start, G Uh of the last step;
  * restoring U together with Zwarm continues bit-identically to the
@@ -279,8 +303,14 @@ hq_status hq_mg_level_potential(hq_ctx *ctx, int level, double *V_out);
  * (every partial is written before it is read, so nothing needs clearing):
  * calls that can overlap on the GPU -- on different streams, or from
  * different host threads -- race and must be serialised by the caller.
+ * The cached address belongs to the device's context at the first call: after
+ * cudaDeviceReset of that device this entry point must not be called again in
+ * the same process.
  * cuda_stream: a cudaStream_t (NULL = default stream); the call is
- * asynchronous on it.  Returns HQ_ERR_CUDA on a runtime error.             */
+ * asynchronous on it.  Returns HQ_ERR_CUDA on a runtime error: a launch error
+ * already pending on the calling thread (left by earlier work) is reported
+ * before anything is launched and left in place for the caller; an error of
+ * this call's own launches is reported and cleared.                        */
 hq_status hq_gram_static(const double *A, int Na, const double *B, int Nb, long n, double w,
                          double *out, void *cuda_stream);
 

@@ -93,6 +93,7 @@ def _sig(lib):
         "orc_energy": (_D, [_I, _D, _D, _P, _D, _I, _P]),
         "orc_grad_eigs": (_I, [_I, _D, _D, _I, _P, _P, _P]),
         "orc_grad_density": (_I, [_I, _D, _D, _P, _I, _P, _P, _P, _D, _I, _P, _P, _P]),
+        "orc_refine": (_I, [_I, _D, _D, _P, _I, _P, _I, _D, _I, _P, _P, _P]),
     }
     for name, (res, args) in spec.items():
         f = getattr(lib, name)
@@ -442,3 +443,22 @@ def grad_density(m, V, U, lam, rho_target, rtol=1e-12, maxit=20000, lo=-6.0, hi=
                                 _ptr(dV), ctypes.byref(L), ctypes.byref(its))
     _check(st, "orc_grad_density")
     return dV, L.value, its.value
+
+
+def refine(m, V, U, rounds, rtol=1e-12, maxit=20000, lo=-6.0, hi=6.0):
+    """FP64 residual refinement of span(U) (not in the paper; the final FP64
+    refinement of a lower-precision result): per round, Rayleigh-Ritz pairs
+    (theta_i, u_i), then Newton corrections t_i in the complement of span(U)
+    from Q (H - theta_i) Q t_i = -(H u_i - theta_i u_i) by CG, U <- u + t; a
+    last Rayleigh-Ritz returns (Ritz vectors, Ritz values, residual norms,
+    largest CG count per round)."""
+    V = _f64(V).ravel()
+    U = np.array(_f64(U), copy=True)
+    n, N = U.shape
+    lam = np.zeros(N)
+    res = np.zeros(N)
+    its = np.zeros(max(rounds, 1), dtype=np.int32)
+    st = lib().orc_refine(m, lo, hi, _ptr(V), N, _ptr(U), rounds, rtol, maxit, _ptr(lam),
+                          _ptr(res), _ptr(its))
+    _check(st, "orc_refine")
+    return U, lam, res, its[:rounds]

@@ -1222,3 +1222,80 @@ int orc_grad_density(int m, double lo, double hi, const double *V, int N, const 
     free(g); free(xi);
     return status;
 }
+
+/* ------------------------------------------------------------------------ */
+/* FP64 residual refinement of an approximate eigen-subspace (not in the    */
+/* paper: the final refinement, in FP64, of a result computed in lower      */
+/* precision).  One round, from the current U (n x N):                      */
+/*   1. Rayleigh-Ritz on span(U): Ritz pairs (theta_i, u_i) of H with        */
+/*      <u_i, u_j> = delta_ij (orc_extract);                                 */
+/*   2. residuals r_i = H u_i - theta_i u_i, which are orthogonal to span(U) */
+/*      by the Ritz conditions;                                             */
+/*   3. corrections t_i in range(Q), Q = I - sum_j u_j <u_j, .>, from        */
+/*        Q (H - theta_i) Q t_i = -r_i,                                     */
+/*      by CG on range(Q) from t_i = 0 to ||res|| <= rtol ||r_i|| (Q applied */
+/*      after every operator application).  This is Newton's equation for   */
+/*      an invariant subspace written in the Ritz basis, where it decouples */
+/*      into one equation per column; Q (H - theta_i) Q is positive definite */
+/*      on range(Q) when every theta_i lies below the spectrum of H on the  */
+/*      complement of span(U);                                              */
+/*   4. U <- u + t.                                                          */
+/* After `rounds` rounds a last Rayleigh-Ritz returns U = the Ritz vectors,  */
+/* lam = the Ritz values (ascending) and res_i = ||H u_i - lam_i u_i||.      */
+/* cg_iters (nullable) receives the largest CG count of each round.          */
+/* ------------------------------------------------------------------------ */
+int orc_refine(int m, double lo, double hi, const double *V, int N, double *U, int rounds,
+               double rtol, int maxit, double *lam, double *res, int *cg_iters)
+{
+    long n = cube(m);
+    double h = orc_grid_h(m, lo, hi), h3 = h * h * h;
+    double *u = malloc(sizeof(double) * n * N);
+    int status = ORC_OK;
+    for (int k = 0; k < rounds && status == ORC_OK; k++) {
+        status = orc_extract(m, lo, hi, V, 0.0, N, U, NULL, NULL, lam, u, NULL);
+        if (status != ORC_OK) break;
+        int itmax = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int i = 0; i < N; i++) {
+            double *ui = malloc(sizeof(double) * n), *b = malloc(sizeof(double) * n),
+                   *t = calloc(n, sizeof(double)), *r = malloc(sizeof(double) * n),
+                   *pp = malloc(sizeof(double) * n), *q = malloc(sizeof(double) * n);
+            for (long p = 0; p < n; p++) ui[p] = u[p * N + i];
+            apply_col(m, h, V, -lam[i], ui, b);          /* r_i = (H - theta_i) u_i */
+            for (long p = 0; p < n; p++) b[p] = -b[p];
+            project_out(n, N, h3, u, b);
+            double bn = sqrt(dot(n, b, b));
+            for (long p = 0; p < n; p++) { r[p] = b[p]; pp[p] = b[p]; }
+            double rr = dot(n, r, r);
+            int st = (sqrt(rr) <= rtol * bn) ? ORC_OK : ORC_ERR_NOT_CONVERGED, it = 0;
+            while (st != ORC_OK && it < maxit) {
+                apply_col(m, h, V, -lam[i], pp, q);
+                project_out(n, N, h3, u, q);
+                double pq = dot(n, pp, q);
+                if (!(pq > 0.0)) { st = ORC_ERR_BREAKDOWN; break; }
+                double alpha = rr / pq;
+                for (long p = 0; p < n; p++) { t[p] += alpha * pp[p]; r[p] -= alpha * q[p]; }
+                double rr1 = dot(n, r, r);
+                it++;
+                if (sqrt(rr1) <= rtol * bn) { st = ORC_OK; break; }
+                double beta = rr1 / rr;
+                for (long p = 0; p < n; p++) pp[p] = r[p] + beta * pp[p];
+                rr = rr1;
+            }
+            for (long p = 0; p < n; p++) U[p * N + i] = ui[p] + t[p];
+#pragma omp critical
+            {
+                if (st != ORC_OK && status == ORC_OK) status = st;
+                if (it > itmax) itmax = it;
+            }
+            free(ui); free(b); free(t); free(r); free(pp); free(q);
+        }
+        if (cg_iters) cg_iters[k] = itmax;
+    }
+    if (status == ORC_OK) {
+        status = orc_extract(m, lo, hi, V, 0.0, N, U, NULL, NULL, lam, u, res);
+        if (status == ORC_OK) memcpy(U, u, sizeof(double) * n * N);
+    }
+    free(u);
+    return status;
+}

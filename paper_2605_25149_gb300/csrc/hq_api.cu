@@ -1867,33 +1867,19 @@ hq_status grad_eigs_impl(hq_ctx *x, const double *w, double *dV, int on_device) 
     return check_launch(x);
 }
 
-hq_status grad_density_impl(hq_ctx *x, const double *G, const double *rho_target, int on_device,
-                            double rtol, int maxit, double *dV, double *loss, int *iters) {
-    HQ_TRY(need_fp64(x));
-    HQ_TRY(clear_status(x));
-    HQ_TRY(ritz(x));
+// Projected, column-shifted block PCG (FP64 contexts): xi_i in range(P) with
+//   P (A - s_i) P xi_i = b_i,   b_i in range(P),   A = H + sigma,
+// P = I - u (h^3 u^T) the projector onto the complement of the Ritz vectors u
+// (in Uh), shifts s (device, N values), preconditioner P M P with M the
+// V-cycle of A, xi_0 = 0, column i stopped at ||r_i|| <= rtol ||b_i||.  b is
+// kept; the PCG blocks R, Zp, P, Q, Tt are overwritten.  P (A - s_i) P is
+// positive definite on range(P) when s_i lies below the spectrum of A on the
+// complement of span(u).  *iters: iterations run.
+hq_status projected_pcg(hq_ctx *x, const double *b, double *xi, const double *shifts, double rtol,
+                        int maxit, int *iters, const char *what) {
     const int N = x->N;
     const long n = x->n;
     const size_t cnt = (size_t)n * N;
-    const double *u = (const double *)x->Uh;
-    double *Gd = x->vn[1];
-    if (rho_target) {
-        // G = h^3 (rho - rho_target), L = (1/2) h^3 sum (rho - rho_target)^2
-        launch_rowreduce(0, n, N, u, nullptr, nullptr, 1.0, x->vn[0], x->st);
-        HQ_CUDA(cudaMemcpyAsync(x->vn[2], rho_target, sizeof(double) * n, kind_in(on_device), x->st));
-        int np = launch_diff_sq(n, x->vn[0], x->vn[2], Gd, x->tpart, x->st);
-        launch_monitor_finish(np, x->tpart, 0.5 * x->h3, 0, nullptr, x->scal + 6, x->st);
-        launch_dscale((int)n, x->h3, Gd, Gd, x->st);
-    } else {
-        if (!G) return fail(x, HQ_ERR_ARG, "G and rho_target are both null");
-        HQ_CUDA(cudaMemcpyAsync(Gd, G, sizeof(double) * n, kind_in(on_device), x->st));
-    }
-    // right-hand sides b_i = P (G o u_i) in Z; shifts s_i = lambda_i + sigma
-    double *b = (double *)x->Z, *xi = (double *)x->W;
-    launch_scale_rows(n, N, Gd, u, b, x->st);
-    HQ_TRY(project(x, b));
-    launch_add_scalar(N, x->lam_r, x->sigma, x->mu, x->st);
-    // projected block PCG on (A - s_i) with preconditioner P M P
     Level &v = x->lev[0];
     const GridGeom &g = v.g;
     double *R = (double *)x->R, *Zp = (double *)x->Zp, *P = (double *)x->P, *Q = (double *)x->Q,
@@ -1916,7 +1902,7 @@ hq_status grad_density_impl(hq_ctx *x, const double *G, const double *rho_target
         HQ_TRY(copy_blk<double>(x, P, Zp, cnt));
         for (it = 1; it <= maxit; it++) {
             launch_apply<double>(g, v.D, v.c, P, Q, nullptr, x->st);
-            launch_shift_cols(n, N, x->mu, P, Q, x->st);
+            launch_shift_cols(n, N, shifts, P, Q, x->st);
             HQ_TRY(project(x, Q));
             launch_dot<double>(g, P, Q, x->part, x->st);
             launch_finalize(FIN_ALPHA, N, g.gy, x->part, nullptr, sc, rtol, x->st);
@@ -1933,8 +1919,44 @@ hq_status grad_density_impl(hq_ctx *x, const double *G, const double *rho_target
             launch_pcg_p<double>(g, sc.beta, Zp, P, x->st);
         }
     }
-    HQ_TRY(sync_status(x, sc.status, "adjoint PCG"));
-    if (nact > 0) return fail(x, HQ_ERR_NOT_CONVERGED, "adjoint PCG reached maxit");
+    if (iters) *iters = it > maxit ? maxit : it;
+    HQ_TRY(sync_status(x, sc.status, what));
+    if (nact > 0) return fail(x, HQ_ERR_NOT_CONVERGED, std::string(what) + " reached maxit");
+    return HQ_OK;
+}
+
+hq_status grad_density_impl(hq_ctx *x, const double *G, const double *rho_target, int on_device,
+                            double rtol, int maxit, double *dV, double *loss, int *iters) {
+    HQ_TRY(need_fp64(x));
+    HQ_TRY(clear_status(x));
+    HQ_TRY(ritz(x));
+    const int N = x->N;
+    const long n = x->n;
+    const double *u = (const double *)x->Uh;
+    double *Gd = x->vn[1];
+    if (rho_target) {
+        // G = h^3 (rho - rho_target), L = (1/2) h^3 sum (rho - rho_target)^2
+        launch_rowreduce(0, n, N, u, nullptr, nullptr, 1.0, x->vn[0], x->st);
+        HQ_CUDA(cudaMemcpyAsync(x->vn[2], rho_target, sizeof(double) * n, kind_in(on_device), x->st));
+        int np = launch_diff_sq(n, x->vn[0], x->vn[2], Gd, x->tpart, x->st);
+        launch_monitor_finish(np, x->tpart, 0.5 * x->h3, 0, nullptr, x->scal + 6, x->st);
+        launch_dscale((int)n, x->h3, Gd, Gd, x->st);
+    } else {
+        if (!G) return fail(x, HQ_ERR_ARG, "G and rho_target are both null");
+        HQ_CUDA(cudaMemcpyAsync(Gd, G, sizeof(double) * n, kind_in(on_device), x->st));
+    }
+    // right-hand sides b_i = P (G o u_i) in Z; shifts s_i = lambda_i + sigma
+    double *b = (double *)x->Z, *xi = (double *)x->W;
+    launch_scale_rows(n, N, Gd, u, b, x->st);
+    HQ_TRY(project(x, b));
+    launch_add_scalar(N, x->lam_r, x->sigma, x->mu, x->st);
+    int it = 0;
+    hq_status st = projected_pcg(x, b, xi, x->mu, rtol, maxit, &it, "adjoint PCG");
+    // the step buffers W and Z now hold adjoint data
+    x->w_valid = false;
+    x->z_valid = false;
+    if (iters) *iters = it;
+    HQ_TRY(st);
     // dL/dV = -2 sum_i u_i o xi_i
     launch_rowreduce(1, n, N, u, xi, nullptr, -2.0, x->vn[0], x->st);
     HQ_CUDA(cudaMemcpyAsync(dV, x->vn[0], sizeof(double) * n, kind_out(on_device), x->st));
@@ -1943,11 +1965,89 @@ hq_status grad_density_impl(hq_ctx *x, const double *G, const double *rho_target
         if (rho_target)
             HQ_CUDA(cudaMemcpyAsync(loss, x->scal + 6, sizeof(double), cudaMemcpyDeviceToHost, x->st));
     }
-    if (iters) *iters = it;
     HQ_CUDA(cudaStreamSynchronize(x->st));
-    // the step buffers W and Z now hold adjoint data
+    return check_launch(x);
+}
+
+// FP64 Rayleigh-Ritz of H on span(U) without the phase-A solve that
+// hq_eigenpairs runs for Section 5's values: Ritz values (ascending) into
+// lam_r, <.,.>-orthonormal, sign-fixed Ritz vectors into Uh.  FP64 contexts.
+hq_status rayleigh_ritz_vectors(hq_ctx *x) {
+    const int N = x->N;
+    double *U64 = (double *)x->U;
+    Level &v0 = x->lev[0];
+    launch_apply<double>(v0.g, v0.D, v0.c, U64, x->E2, nullptr, x->st);   // (H + sigma) U
+    GramPlan gk = make_gram_plan(x->n, N, N, false);
+    GramPlan gs = make_gram_plan(x->n, N, N, true);
+    launch_gram<double>(gk, U64, N, nullptr, 0, x->E2, N, nullptr, 0, x->h3, x->gpart, x->Ksm, x->st);
+    launch_gram<double>(gs, U64, N, nullptr, 0, U64, N, nullptr, 0, x->h3, x->gpart, x->Ssm, x->st);
+    launch_axpy_small(N * N, -x->sigma, x->Ssm, x->Ksm, x->st);   // <U, H U>
+    launch_rr_reduce(N, x->Ksm, x->Ssm, x->Lm, x->Cm, x->status, x->st);
+    HQ_TRY(sync_status(x, x->status, "Rayleigh-Ritz (Cholesky of <U,U>)"));
+    launch_sym_eig(N, x->Cm, x->eigwork, x->lam_r, x->Ym, x->st);
+    launch_rr_back(N, x->Lm, x->Ym, x->Cv, x->st);
+    TallPlan tp = make_tall_plan(x->n, N, N, N);
+    launch_tall_gemm<double>(tp, U64, x->Cv, nullptr, nullptr, nullptr, (double *)x->Uh, nullptr,
+                             x->st);
+    launch_fix_signs<double>(x->n, N, (double *)x->Uh, x->signwork, x->st);
+    return check_launch(x);
+}
+
+// FP64 residual refinement (not in the paper; the final FP64 refinement of a
+// lower-precision result).  Each round: Ritz pairs (theta_i, u_i) of span(U);
+// r_i = H u_i - theta_i u_i; corrections t_i in the complement of span(u)
+// from P (A - s_i) P t_i = -r_i, s_i = theta_i + sigma (Newton's equation for
+// an invariant subspace in the Ritz basis, one equation per column), by the
+// projected PCG; U <- u + t.  A last Rayleigh-Ritz leaves U = the Ritz
+// vectors.  The warm start of the next inner solve is dropped.
+hq_status refine_impl(hq_ctx *x, int rounds, double rtol, int maxit, double *resid,
+                      int *iters_out) {
+    HQ_TRY(need_ready(x));
+    if (x->mixed) return fail(x, HQ_ERR_STATE, "hq_refine needs an HQ_FP64 context");
+    if (rounds < 0 || maxit < 1 || !(rtol > 0.0)) return fail(x, HQ_ERR_ARG, "rounds >= 0, maxit >= 1, rtol > 0");
+    HQ_TRY(clear_status(x));
+    const int N = x->N;
+    const long n = x->n;
+    const size_t cnt = (size_t)n * N;
+    Level &v = x->lev[0];
+    double *u = (double *)x->Uh, *b = (double *)x->Z, *t = (double *)x->W;
+    int total = 0;
+    hq_status st = HQ_OK;
+    for (int k = 0; k < rounds && st == HQ_OK; k++) {
+        st = rayleigh_ritz_vectors(x);
+        if (st != HQ_OK) break;
+        launch_add_scalar(N, x->lam_r, x->sigma, x->mu, x->st);
+        // b = -(A u - s u) = -(H u_i - theta_i u_i), projected
+        launch_apply<double>(v.g, v.D, v.c, u, b, nullptr, x->st);
+        launch_shift_cols(n, N, x->mu, u, b, x->st);
+        launch_axpby(cnt, -1.0, b, 0.0, b, b, x->st);
+        st = project(x, b);
+        if (st != HQ_OK) break;
+        int it = 0;
+        st = projected_pcg(x, b, t, x->mu, rtol, maxit, &it, "refinement PCG");
+        total += it;
+        if (st != HQ_OK) break;
+        launch_axpby(cnt, 1.0, u, 1.0, t, (double *)x->U, x->st);
+    }
     x->w_valid = false;
     x->z_valid = false;
+    if (iters_out) *iters_out = total;
+    HQ_TRY(st);
+    HQ_TRY(rayleigh_ritz_vectors(x));
+    HQ_TRY(copy_blk<double>(x, (double *)x->U, u, cnt));
+    if (resid) {
+        // ||H u_i - theta_i u_i|| of the final Ritz pairs
+        launch_add_scalar(N, x->lam_r, x->sigma, x->mu, x->st);
+        launch_apply<double>(v.g, v.D, v.c, u, b, nullptr, x->st);
+        launch_shift_cols(n, N, x->mu, u, b, x->st);
+        GramPlan gp = make_gram_plan(n, N, N, true);
+        launch_gram<double>(gp, b, N, nullptr, 0, b, N, nullptr, 0, x->h3, x->gpart, x->Ksm, x->st);
+        std::vector<double> K((size_t)N * N);
+        HQ_CUDA(cudaMemcpyAsync(K.data(), x->Ksm, sizeof(double) * N * N, cudaMemcpyDeviceToHost, x->st));
+        HQ_CUDA(cudaStreamSynchronize(x->st));
+        for (int i = 0; i < N; i++) resid[i] = std::sqrt(std::max(0.0, K[(size_t)i * N + i]));
+    }
+    HQ_CUDA(cudaStreamSynchronize(x->st));
     return check_launch(x);
 }
 
@@ -2212,6 +2312,14 @@ hq_status hq_grad_density(hq_ctx *x, const double *G, const double *rho_target, 
     ProfScope ps_(x);
     if (!dV || !(rtol > 0.0) || maxit < 1) return fail(x, HQ_ERR_ARG, "bad argument");
     return grad_density_impl(x, G, rho_target, on_device, rtol, maxit, dV, loss, iters);
+    HQ_API_END
+}
+
+hq_status hq_refine(hq_ctx *x, int rounds, double rtol, int maxit, double *resid, int *iters) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    return refine_impl(x, rounds, rtol, maxit, resid, iters);
     HQ_API_END
 }
 

@@ -229,6 +229,9 @@ void launch_rowreduce(int mode, long n, int N, const double *u, const double *v,
 void launch_scale_rows(long n, int N, const double *g, const double *u, double *y, cudaStream_t s);
 void launch_shift_cols(long n, int N, const double *sft, const double *x, double *y,
                        cudaStream_t s);
+// out = a x + b y over count FP64 values (out may alias x or y)
+void launch_axpby(size_t count, double a, const double *x, double b, const double *y, double *out,
+                  cudaStream_t s);
 // d = a - b, returns the number of partial sums of d^2 written to part
 int launch_diff_sq(long n, const double *a, const double *b, double *d, double *part,
                    cudaStream_t s);

@@ -839,6 +839,19 @@ void launch_shift_cols(long n, int N, const double *sft, const double *x, double
     HQ_LAUNCH(HQ_K_VECTOR, k_shift_cols<<<blocks, 256, 0, s>>>(n, N, sft, x, y));
 }
 
+//   out[e] = a * x[e] + b * y[e]            (whole blocks, FP64)
+__global__ void k_axpby(size_t count, double a, const double *x, double b, const double *y,
+                        double *out) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count;
+         e += (size_t)gridDim.x * blockDim.x)
+        out[e] = a * x[e] + b * y[e];
+}
+void launch_axpby(size_t count, double a, const double *x, double b, const double *y, double *out,
+                  cudaStream_t s) {
+    int blocks = (int)std::min<size_t>((count + 255) / 256, 152 * 16);
+    HQ_LAUNCH(HQ_K_VECTOR, k_axpby<<<blocks, 256, 0, s>>>(count, a, x, b, y, out));
+}
+
 // d[p] = a[p] - b[p]; part[block] = sum of d^2 (one partial per block)
 __global__ void k_diff_sq(long n, const double *a, const double *b, double *d, double *part) {
     __shared__ double red[256];

@@ -32,7 +32,7 @@ FP64, MIXED = 0, 1
 EXPORTED = [
     "hq_default_config", "hq_workspace_bytes", "hq_init", "hq_set_potential", "hq_set_initial",
     "hq_step", "hq_solve", "hq_eigenpairs", "hq_monitor", "hq_time_step", "hq_density",
-    "hq_grad_eigs", "hq_grad_density", "hq_get_state", "hq_set_state", "hq_problem_info",
+    "hq_grad_eigs", "hq_grad_density", "hq_refine", "hq_get_state", "hq_set_state", "hq_problem_info",
     "hq_apply_operator", "hq_mg_vcycle", "hq_block_pcg", "hq_gram", "hq_block_gemm",
     "hq_step_trace",
     "hq_mg_smooth", "hq_mg_smooth_prescaled", "hq_mg_restrict", "hq_mg_prolong",
@@ -97,6 +97,7 @@ def load():
         "hq_density": (_I, [_P, _P, _I]),
         "hq_grad_eigs": (_I, [_P, _P, _P, _I]),
         "hq_grad_density": (_I, [_P, _P, _P, _I, _D, _I, _P, _P, _P]),
+        "hq_refine": (_I, [_P, _I, _D, _I, _P, _P]),
         "hq_get_state": (_I, [_P, _P, _P, _I, _P]),
         "hq_set_state": (_I, [_P, _P, _P, _I, _L]),
         "hq_problem_info": (_I, [_P, _P, _P, _P, _P]),
@@ -339,6 +340,16 @@ class Solver:
                     "hq_grad_density")
         return dV, loss.value, its.value
 
+    def refine(self, rounds=2, rtol=1e-8, maxit=500):
+        """FP64 residual refinement of span(U) (hq_refine): `rounds` Newton
+        corrections of the Ritz pairs; returns (final residual norms
+        ||H u_i - theta_i u_i|| as a host array, PCG iterations)."""
+        res = np.empty(self.N)
+        its = ctypes.c_int()
+        self._check(self.lib.hq_refine(self._ctx, rounds, rtol, maxit, _hptr(res),
+                                       ctypes.byref(its)), "hq_refine")
+        return res, its.value
+
     def time_step(self):
         """tau_n of the last step taken."""
         t = ctypes.c_double()
@@ -381,6 +392,16 @@ class Solver:
         Zh = None if Z is None else self._host_f64(Z, (self.n, self.N))
         self._check(self.lib.hq_set_state(self._ctx, _hptr(U), _hptr(Zh), 0, step),
                     "hq_set_state")
+
+    def set_state_device(self, U, step, Z=None):
+        """hq_set_state from device FP64 tensors (n x N), e.g. the state of
+        another context read with state_device()."""
+        for t in (U, Z):
+            if t is not None and (t.dtype != self._torch.float64 or not t.is_cuda or
+                                  not t.is_contiguous() or t.numel() != self.n * self.N):
+                raise ValueError("expected a contiguous CUDA float64 tensor of n x N values")
+        self._check(self.lib.hq_set_state(self._ctx, _dptr(U), None if Z is None else _dptr(Z), 1,
+                                          step), "hq_set_state")
 
     def info(self):
         h, s, L = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()

@@ -6,7 +6,7 @@ import pytest
 import oracle as O
 from paper_2605_25149_gb300 import hq, inputs
 from tests.gpu_common import dev, host, make, rel, torch_mod
-from tests.helpers import separable_levels
+from tests.helpers import clusters, lowest_eigenpairs, separable_levels, subspace_sin
 
 pytestmark = pytest.mark.gpu
 
@@ -24,7 +24,9 @@ def _oracle_from_gpu_start(s, U0):
 def test_step_intermediates_match_oracle(m, N, pot):
     tau = 0.4
     s, V, U0 = make(m, N, potential=pot, tau=tau, cg_rtol=1e-13, cg_maxit=400)
-    sigma = s.info()["sigma"]
+    # the oracle runs with its own shift rule (Garding shift, Section 2.2)
+    sigma = O.auto_shift(m, V)
+    assert s.info()["sigma"] == sigma
     Ug0, _, _ = s.get_state()
     Uo = _oracle_from_gpu_start(s, U0)
     assert rel(Ug0, Uo) < 1e-13
@@ -242,3 +244,109 @@ def test_fp64_with_fp32_preconditioner_converges_to_closed_form():
     it64 = s64.pcg_stats()[1]
     it32 = s.pcg_stats()[1]
     assert it32 <= 1.5 * it64 + 2
+
+
+@pytest.mark.parametrize("m,pot,shift", [(16, "harmonic", None), (20, "wells", None),
+                                         (13, "wells", None), (12, "wells", 2.5),
+                                         (11, "harmonic", -0.25)])
+def test_shift_equals_oracle_rule(m, pot, shift):
+    """The shift of G = (H + sigma)^-1 (Garding shift of Section 2.2; automatic
+    rule sigma = 0 if lambda_min(-Delta_h/2) + min V > 0, else 1 - that bound)
+    equals the oracle's rule bit for bit; a shift given in the configuration is
+    used as given."""
+    kw = {} if shift is None else {"shift": shift}
+    s, V, U0 = make(m, 4, potential=pot, **kw)
+    sig = s.info()["sigma"]
+    want = O.auto_shift(m, V) if shift is None else shift
+    assert sig == want, (sig, want)
+    if pot == "wells" and shift is None:
+        assert sig > 1.0
+
+
+def _solve_to_floor(s, chunk, cap):
+    """Algorithm 1 in chunks until g stops dropping by 10% per chunk (the
+    rounding floor of the working precision) or `cap` steps."""
+    steps, prev = 0, np.inf
+    while steps < cap:
+        n, g = s.solve(1e-30, chunk, raise_on_unconverged=False)
+        steps += n
+        if g > 0.9 * prev:
+            break
+        prev = g
+    return steps, g
+
+
+def test_mixed_wells_eigenpairs_meet_stated_tolerances():
+    """Mixed precision (FP32 blocks, FP32 PCG rtol 1e-6, 3xTF32 tensor-core
+    products, FP64 small solves) run to its floor on a wells potential (24^3,
+    N = 20: the lowest 20 levels end at a gap of 0.51), then FP64 Rayleigh-Ritz
+    (Section 5's extraction): every eigenvalue within 1e-6 (relative) of the N
+    lowest eigenpairs of H_h (sparse shift-invert Lanczos on the assembled
+    operator: the definition of the converged result).  The state is then
+    handed to an FP64 context for the final FP64 residual refinement
+    (hq_refine): eigenvalues within 1e-10, and every eigenvector whose level is
+    separated by more than 1e-3 from its neighbours within a subspace angle of
+    1e-5 (reached: below 1e-8).  The FP32 floor alone leaves angles of ~2e-5
+    here, below 1e-4.  The FP64 path on the same problem reaches the same
+    eigenvalues to 1e-10."""
+    torch = torch_mod()
+    m, N, seed = 24, 20, 7
+    lam_ref, vec_ref = lowest_eigenpairs(m, inputs.wells(m, seed), N + 1)
+    groups = clusters(lam_ref, N, 1e-3)
+    assert sum(len(g) for g in groups) == N
+    s, V, U0 = make(m, N, seed=seed, useed=107, precision="mixed", tau=0.4, cg_rtol=1e-6)
+    steps, g = _solve_to_floor(s, 250, 20000)
+    ev = s.eigenpairs(vectors=True)
+    err = np.abs(ev["lam_rr"] - lam_ref[:N]) / np.abs(lam_ref[:N])
+    assert err.max() <= 1e-6, (err.max(), steps, g)
+    raw = max(subspace_sin(ev["vectors"][:, grp], vec_ref[:, grp]) for grp in groups)
+    assert raw <= 1e-4, (raw, steps, g)
+    # hand-over to FP64 (device to device) and the FP64 residual refinement
+    U, st = s.state_device()
+    s64 = hq.Solver(m, N, tau=0.4, cg_rtol=1e-10, mg_fp32=1)
+    s64.set_potential(V)
+    s64.set_state_device(U, st)
+    res, its = s64.refine(rounds=2, rtol=1e-8, maxit=500)
+    ev64 = s64.eigenpairs(vectors=True)
+    np.testing.assert_allclose(ev64["lam_rr"], lam_ref[:N], rtol=1e-10)
+    worst = max(subspace_sin(ev64["vectors"][:, grp], vec_ref[:, grp]) for grp in groups)
+    assert worst <= 1e-8, (worst, raw, its)
+    assert res.max() < 1e-7, res
+    # the refined state satisfies Algorithm 1's stopping test with an FP64 solve
+    n0, g0 = s64.solve(1e-8, 0, raise_on_unconverged=False)
+    assert n0 == 0 and g0 < 1e-8, g0
+    s2, _, _ = make(m, N, seed=seed, useed=107, tau=0.4, cg_rtol=1e-10)
+    s2.solve(1e-9, 20000)
+    np.testing.assert_allclose(s2.eigenpairs()["lam_rr"], lam_ref[:N], rtol=1e-10)
+
+
+@pytest.mark.parametrize("m,N,seed", [(10, 5, 2), (12, 6, 5)])
+def test_refine_matches_oracle_refinement(m, N, seed):
+    """hq_refine (Rayleigh-Ritz, then Newton corrections of the Ritz pairs on
+    the complement of span(U), solved by the projected multigrid PCG) from
+    the same iterate as the oracle's orc_refine (plain CG on each projected
+    system): the same Ritz values and vectors after two rounds."""
+    s, V, U0 = make(m, N, seed=seed, tau=0.4, cg_rtol=1e-12, cg_maxit=400)
+    s.solve(2e-4, 20000)
+    U = s.get_state()[0]
+    Uo, lo_, reso, _ = O.refine(m, V, U, 2, rtol=1e-12)
+    res, its = s.refine(rounds=2, rtol=1e-12, maxit=400)
+    Ug, _, _ = s.get_state()
+    ev = s.eigenpairs(vectors=True)
+    np.testing.assert_allclose(ev["lam_rr"], lo_, rtol=1e-12)
+    gaps = np.minimum(np.diff(np.r_[-np.inf, lo_]), np.diff(np.r_[lo_, np.inf]))
+    for i in np.nonzero(gaps > 1e-3)[0]:
+        assert rel(Ug[:, i], Uo[:, i]) < 1e-9, i
+    np.testing.assert_allclose(res, reso, rtol=1e-3, atol=1e-12)
+    assert its > 0
+
+
+def test_refine_rejects_mixed_contexts_and_bad_arguments():
+    s, V, U0 = make(8, 3, precision="mixed", cg_rtol=1e-6)
+    with pytest.raises(hq.HQError) as e:
+        s.refine()
+    assert e.value.status == 2
+    s64, _, _ = make(8, 3)
+    with pytest.raises(hq.HQError) as e:
+        s64.refine(rounds=1, rtol=0.0)
+    assert e.value.status == 1
