@@ -41,34 +41,22 @@ FP64_PEAK_GFLOPS = 2 * 152 * 2.07 * 2
 #   smooth   z' = z + omega D^-1 (r - A z): 6-neighbour sum (5 add), r + c s
 #            (fma), (1-omega) z (mul), + wD (...) (fma): 10 flops; reads r, z,
 #            writes z': 3 words
-#   stencil  y = D x - c s: 5 add + mul + fma = 8 flops; 2 words
+#   stencil  y = D x - c s: 5 add + mul + fma = 8 flops, + the per-column
+#            partial x.y of the PCG operator (fma): 10 flops; reads x, writes
+#            y: 2 words
 #   residual (b - D x) + c s: 5 add + 2 fma = 9 flops; 3 words
-ALGO = {"smooth": (10.0, 3.0), "stencil": (8.0, 2.0), "residual": (9.0, 3.0)}
+ALGO = {"smooth": (10.0, 3.0), "stencil": (10.0, 2.0), "residual": (9.0, 3.0)}
 # FP64 V-cycles sweep from the pre-scaled right-hand side rt = omega D^-1 r:
 #   z' = (omega c D^-1) s + ((1 - omega) z + rt): 5 add + 2 fma = 9 flops in 7
 #   FP64-pipe instructions; reads rt, z, writes z': 3 words
 ALGO_F64 = dict(ALGO, smooth=(9.0, 3.0))
-FP64_OPS = {"smooth": 7.0, "stencil": 7.0, "residual": 7.0}
-# DRAM bytes per point-column of the finest-level smooth kernel measured by
-# ncu (dram__bytes_read.sum + dram__bytes_write.sum of one launch / 16.78 M
-# point-columns, profiles/k_jacobi_k_jacobi_zm_wells64_N64.md: the pre-scaled
-# k_jacobi_zm of a post-smoothing sweep for the 134 MB FP64 block, k_jacobi
-# for the 67 MB FP32 block); set to None whenever the kernel changes until it
-# is captured again.
-TRAFFIC_PER_ELEMENT = {("smooth", "f64"): (272.048896e6 + 107.949824e6) / 16777216,
-                       ("smooth", "f32"): (136.215040e6 + 44.029440e6) / 16777216}
-
-
-# Recorded by `python bench.py --ttr` on a GB300 (profiles/ttr_wells64_N64.md):
-# Algorithm 1 with the adaptive time step, steps and seconds to g < 1e-8 in
-# FP64, and steps / seconds to a Rayleigh-Ritz eigenvalue error <= 1e-6
-# (against the FP64 result) in FP64 and in mixed precision.  The default run
-# reports them as "recorded" beside a projection from its own ms/step.
-TTR_STEPS = {"wells64_N64": {"command": "python bench.py --ttr", "steps": 15113, "s": 288.3,
-                             "fp64_err1e-6_steps": 6250, "fp64_err1e-6_s": 140.0,
-                             "mixed_err1e-6_steps": 6250, "mixed_err1e-6_s": 25.7,
-                             "fp64_mg32_s": 171.8, "mixed_then_fp64_mg32_s": 105.5,
-                             "mixed_then_fp64_mg32_steps": 7750 + 7379}}
+# FP64-pipe instructions per point-column (an add takes an issue slot as an FMA does)
+FP64_OPS = {"smooth": 7.0, "stencil": 8.0, "residual": 7.0}
+# DRAM bytes per point-column of the roofline kernels from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch / point-columns
+# of that launch): keys (class, dtype); an entry is removed whenever its
+# kernel changes, until it is captured again.
+TRAFFIC_PER_ELEMENT = {("smooth", "f32"): (136.215040e6 + 44.029440e6) / 16777216}
 
 
 def peaks():
@@ -182,45 +170,42 @@ def time_steps(torch, s, K, ws, label=None):
     return e0.elapsed_time(e1) / max(K, 1), g
 
 
-def roofline(prof, dtype_tag, hbm_peak, hbm_kind):
-    """Dominant grid kernel class of an instrumented region."""
-    cand = {k: v for k, v in prof.items() if k in ALGO and v[1] > 0}
-    if not cand:
+GRID_CLASSES = ("stencil", "smooth", "residual")
+KERNEL_NAME = {"stencil": "finest-level operator y = (H + sigma) x with per-column x.y partials "
+                          "(k_stencil_zm for blocks of 100 MB or more, else k_stencil)",
+               "smooth": "finest-level damped-Jacobi sweep (k_jacobi_zm for blocks of 100 MB or "
+                         "more, else k_jacobi)",
+               "residual": "finest-level residual sweep (k_stencil_zm / k_stencil, mode 1)"}
+
+
+def dominant(prof):
+    """The finest-level grid kernel class with the most in-step time."""
+    cand = {k: v for k, v in prof.items() if k in GRID_CLASSES and v[1] > 0}
+    return max(cand, key=lambda c: cand[c][1]) if cand else None
+
+
+def roofline(prof, kind, dtype_tag):
+    """In-step figures of kernel class `kind` from an instrumented region."""
+    if kind not in prof or prof[kind][0] == 0:
         return None
-    k = max(cand, key=lambda c: cand[c][1])
-    launches, ms, elems = cand[k]
-    flops_e, words_e = (ALGO_F64 if dtype_tag == "f64" else ALGO)[k]
+    launches, ms, elems = prof[kind]
+    flops_e, words_e = (ALGO_F64 if dtype_tag == "f64" else ALGO)[kind]
     w = 8 if dtype_tag == "f64" else 4
-    per_launch_s = ms / 1e3 / launches
-    per_launch_elems = elems / launches
-    tr = TRAFFIC_PER_ELEMENT.get((k, dtype_tag))
-    traffic = None if tr is None else tr * per_launch_elems
-    if dtype_tag == "f64":
-        achieved = flops_e * per_launch_elems / per_launch_s / 1e12
-        peak = FP64_PEAK_GFLOPS / 1e3
-        out = {"bound": "alu", "kernel": k, "achieved": achieved, "peak": peak,
-               "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-               "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz",
-               "hbm_gbs": words_e * w * per_launch_elems / per_launch_s / 1e9,
-               "fp64_issue_frac": FP64_OPS[k] * per_launch_elems / per_launch_s
-               / (FP64_PEAK_GFLOPS / 2 * 1e9)}
-    else:
-        achieved = words_e * w * per_launch_elems / per_launch_s / 1e9
-        out = {"bound": "hbm", "kernel": k, "achieved": achieved, "peak": hbm_peak,
-               "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
-               "peak_source": hbm_kind}
-    out.update({"launches": launches, "ms_per_launch": ms / launches,
-                "elements_per_launch": per_launch_elems, "share": ms / sum(v[1] for v in prof.values())})
-    return out
+    t = ms / 1e3 / launches
+    el = elems / launches
+    return {"kernel": kind, "launches": launches, "ms_per_launch": ms / launches,
+            "elements_per_launch": el, "share": ms / sum(v[1] for v in prof.values()),
+            "gbs": words_e * w * el / t / 1e9, "tflops": flops_e * el / t / 1e12}
 
 
-def smooth_alone(torch, hq, s, reps=40):
-    """The finest-level damped-Jacobi sweep (the dominant kernel class) timed
-    alone, in the form the context's V-cycle launches it (hq_mg_smooth_prescaled
-    for FP64 contexts, hq_mg_smooth otherwise): `reps` back-to-back launches on
-    n x N blocks of the working precision (ping-pong z_in / z_out; the three
-    blocks exceed L2, so every sweep streams from HBM), CUDA events on the
-    context's stream around the whole sequence.  Returns ms per launch."""
+def kernel_alone(torch, s, kind, mg_prescaled, reps=40):
+    """One finest-level kernel of the step timed alone: `reps` back-to-back
+    launches through the C ABI on n x N blocks of the context's working
+    precision (ping-pong between two blocks; the blocks exceed L2, so every
+    launch streams from HBM), CUDA events on the context's stream around the
+    whole sequence.  kind "stencil": hq_apply_operator with ncol = N (the PCG's
+    operator launch); "smooth": hq_mg_smooth_prescaled for FP64 V-cycles, else
+    hq_mg_smooth.  Returns ms per launch."""
     import ctypes
     n, N = s.n, s.N
     g = torch.Generator(device="cuda").manual_seed(7)
@@ -229,36 +214,42 @@ def smooth_alone(torch, hq, s, reps=40):
     zb = torch.empty_like(za)
     st = s.stream
     lib = s.lib
-    args = [(ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(za.data_ptr()),
-             ctypes.c_void_p(zb.data_ptr())),
-            (ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(zb.data_ptr()),
-             ctypes.c_void_p(za.data_ptr()))]
-    fn, name = lib.hq_mg_smooth, "hq_mg_smooth"
-    if s.dtype == torch.float64 and not s.cfg.mg_fp32:
-        fn, name = lib.hq_mg_smooth_prescaled, "hq_mg_smooth_prescaled"
+    P = lambda t: ctypes.c_void_p(t.data_ptr())
+    if kind == "stencil":
+        calls = [lambda: lib.hq_apply_operator(s._ctx, P(za), P(zb), N),
+                 lambda: lib.hq_apply_operator(s._ctx, P(zb), P(za), N)]
+        name = "hq_apply_operator"
+    else:
+        fn, name = lib.hq_mg_smooth, "hq_mg_smooth"
+        if mg_prescaled:
+            fn, name = lib.hq_mg_smooth_prescaled, "hq_mg_smooth_prescaled"
+        calls = [lambda: fn(s._ctx, 0, P(r), P(za), P(zb)),
+                 lambda: fn(s._ctx, 0, P(r), P(zb), P(za))]
     for i in range(4):
-        s._check(fn(s._ctx, 0, *args[i & 1]), name)
+        s._check(calls[i & 1](), name)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(st)
     for i in range(reps):
-        s._check(fn(s._ctx, 0, *args[i & 1]), name)
+        s._check(calls[i & 1](), name)
     e1.record(st)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps
 
 
-def roofline_alone(ms_launch, n_el, dtype_tag, hbm_peak, hbm_kind, in_step):
-    """Roofline entry of the smooth kernel from its stand-alone launch time."""
-    flops_e, words_e = (ALGO_F64 if dtype_tag == "f64" else ALGO)["smooth"]
+def roofline_alone(kind, ms_launch, n_el, dtype_tag, hbm_peak, hbm_kind, in_step):
+    """Roofline entry of kernel class `kind` from its stand-alone launch time:
+    FP64 kernels against the derived FP64 issue peak ("alu"), FP32 kernels
+    against the measured HBM copy bandwidth."""
+    flops_e, words_e = (ALGO_F64 if dtype_tag == "f64" else ALGO)[kind]
     w = 8 if dtype_tag == "f64" else 4
     t = ms_launch / 1e3
-    tr = TRAFFIC_PER_ELEMENT.get(("smooth", dtype_tag))
+    tr = TRAFFIC_PER_ELEMENT.get((kind, dtype_tag))
     traffic = None if tr is None else tr * n_el
-    out = {"kernel": "smooth (finest-level damped-Jacobi sweep: k_jacobi_zm for blocks of "
-           "100 MB or more, else k_jacobi)", "timing": "alone: back-to-back "
-           "launches on the step's block shape, CUDA events; inputs exceed L2",
+    out = {"kernel": "%s: %s" % (kind, KERNEL_NAME[kind]),
+           "timing": "alone: back-to-back launches on the step's block shape, CUDA events; "
+                     "inputs exceed L2",
            "ms_per_launch": ms_launch, "elements_per_launch": n_el, "traffic": traffic,
            "algorithmic_bytes": words_e * w * n_el, "algorithmic_flops": flops_e * n_el}
     if dtype_tag == "f64":
@@ -268,8 +259,7 @@ def roofline_alone(ms_launch, n_el, dtype_tag, hbm_peak, hbm_kind, in_step):
                     "frac": achieved / peak,
                     "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz",
                     "hbm_gbs": words_e * w * n_el / t / 1e9,
-                    "fp64_issue_frac": FP64_OPS["smooth"] * n_el / t
-                    / (FP64_PEAK_GFLOPS / 2 * 1e9)})
+                    "fp64_issue_frac": FP64_OPS[kind] * n_el / t / (FP64_PEAK_GFLOPS / 2 * 1e9)})
     else:
         achieved = words_e * w * n_el / t / 1e9
         out.update({"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -358,10 +348,12 @@ def first_below(hist, key, thr):
 
 
 def run_ttr(args):
-    """Time to residual and to eigenvalue error on the 64^3, N = 64 wells
-    workload with the adaptive time step: FP64 to g < 1e-8 (its Rayleigh-Ritz
-    values are the reference), the mixed path to eigenvalue error <= 1e-6,
-    and the mixed path followed by FP64 to g < 1e-8."""
+    """The long time-to-residual legs on the 64^3, N = 64 wells workload,
+    scheme only (no refinement), adaptive time step, SM clocks sampled:
+    the FP64 scheme (FP64 PCG, FP32 V-cycle) from U0 to g < 1e-8 (its
+    Rayleigh-Ritz values are the reference), the mixed scheme to g < 2e-6
+    handed device to device to the FP64 scheme and continued to g < 1e-8, and
+    the steps and seconds each needs to eigenvalue error 1e-6."""
     import numpy as np
     import torch
     import __graft_entry__ as ge
@@ -370,8 +362,10 @@ def run_ttr(args):
     V, U0, w = inputs.workload(WORKLOAD)
     m, N = w["m"], w["N"]
     chunk = args.ttr_chunk
-    s = hq.Solver(m, N, tau=w["tau"], cg_rtol=w["cg_rtol"], precision="fp64", adaptive_tau=1,
-                  tau_max=args.tau_max)
+    common = dict(tau=w["tau"], adaptive_tau=1, tau_max=args.tau_max)
+    clk = ClockSampler(0)
+    clk.start()
+    s = hq.Solver(m, N, cg_rtol=w["cg_rtol"], precision="fp64", mg_fp32=1, **common)
     s.set_potential(V)
     s.set_initial(U0)
     h64 = solve_history(torch, s, w["eps"], chunk, args.ttr_steps)
@@ -380,72 +374,38 @@ def run_ttr(args):
         h["err"] = float(np.max(np.abs(h["lam"] - lam_ref) / np.abs(lam_ref)))
     del s
     torch.cuda.empty_cache()
-    sm = hq.Solver(m, N, tau=w["tau"], cg_rtol=args.mixed_rtol, precision="mixed", adaptive_tau=1,
-                   tau_max=args.tau_max)
+    sm = hq.Solver(m, N, cg_rtol=args.mixed_rtol, precision="mixed", **common)
     sm.set_potential(V)
     sm.set_initial(U0)
-    hmx = solve_history(torch, sm, 1e-300, chunk, args.ttr_steps, lam_ref=lam_ref, stop_err=1e-7,
-                        stall=8)
-    # FP64 PCG with the FP32 preconditioner, to g < 1e-8, and the same after
-    # the mixed leg (state handed over through host memory)
-    s3 = hq.Solver(m, N, tau=w["tau"], cg_rtol=w["cg_rtol"], precision="fp64", adaptive_tau=1,
-                   tau_max=args.tau_max, mg_fp32=1)
-    s3.set_potential(V)
-    s3.set_initial(U0)
-    h32 = solve_history(torch, s3, w["eps"], chunk, args.ttr_steps, lam_ref=lam_ref)
-    del s3
+    hmx = solve_history(torch, sm, 2e-6, chunk, args.ttr_steps, lam_ref=lam_ref)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    Um, Zm, stpm = sm.get_state(with_warm_start=True)
-    s4 = hq.Solver(m, N, tau=w["tau"], cg_rtol=w["cg_rtol"], precision="fp64", adaptive_tau=1,
-                   tau_max=args.tau_max, mg_fp32=1)
+    U, st = sm.state_device()
+    s4 = hq.Solver(m, N, cg_rtol=w["cg_rtol"], precision="fp64", mg_fp32=1, **common)
     s4.set_potential(V)
-    s4.set_state(Um, stpm, Zm)
+    s4.set_state_device(U, st)
     torch.cuda.synchronize()
-    t_hand4 = time.perf_counter() - t0
+    t_hand = time.perf_counter() - t0
     h4 = solve_history(torch, s4, w["eps"], chunk, args.ttr_steps, lam_ref=lam_ref)
-    del s4
-    torch.cuda.empty_cache()
-    hpol, t_hand = None, None
-    if args.ttr_pipeline:
-        # hand over to FP64 (state through host memory), then to g < 1e-8
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        U, Z, stp = sm.get_state(with_warm_start=True)
-        s2 = hq.Solver(m, N, tau=w["tau"], cg_rtol=w["cg_rtol"], precision="fp64",
-                       adaptive_tau=1, tau_max=args.tau_max)
-        s2.set_potential(V)
-        s2.set_state(U, stp, Z)
-        torch.cuda.synchronize()
-        t_hand = time.perf_counter() - t0
-        hpol = solve_history(torch, s2, w["eps"], chunk, args.ttr_steps, lam_ref=lam_ref)
-    del sm
+    clocks = clk.stop()
 
     def pick(hh):
         return [{k: v for k, v in h.items() if k != "lam"} for h in hh]
 
     a64, amx = first_below(h64, "err", 1e-6), first_below(hmx, "err", 1e-6)
     out = {"workload": WORKLOAD, "tau_rule": "adaptive, tau_max %g" % args.tau_max,
-           "chunk": chunk, "eps": w["eps"],
+           "chunk": chunk, "eps": w["eps"], "clocks": clocks,
            "fp64": {"time_to_residual_s": h64[-1]["s"], "steps": h64[-1]["steps"],
                     "g": h64[-1]["g"], "to_err_1e-6": a64 and {"s": a64["s"], "steps": a64["steps"]}},
            "mixed": {"to_err_1e-6": amx and {"s": amx["s"], "steps": amx["steps"]},
                      "last": pick(hmx[-1:])[0], "cg_rtol": args.mixed_rtol},
            "speedup_mixed_vs_fp64_at_err_1e-6": (a64["s"] / amx["s"]) if (a64 and amx) else None,
-           "mixed_then_fp64": hpol and {
-               "time_to_residual_s": hmx[-1]["s"] + t_hand + hpol[-1]["s"],
-               "mixed_s": hmx[-1]["s"], "handover_s": t_hand, "fp64_s": hpol[-1]["s"],
-               "fp64_steps": hpol[-1]["steps"], "g": hpol[-1]["g"]},
-           "fp64_mg32": {"time_to_residual_s": h32[-1]["s"], "steps": h32[-1]["steps"],
-                         "g": h32[-1]["g"], "err": h32[-1]["err"]},
-           "mixed_then_fp64_mg32": {
-               "time_to_residual_s": hmx[-1]["s"] + t_hand4 + h4[-1]["s"],
-               "mixed_s": hmx[-1]["s"], "mixed_steps": hmx[-1]["steps"], "handover_s": t_hand4,
-               "fp64_mg32_s": h4[-1]["s"], "fp64_mg32_steps": h4[-1]["steps"], "g": h4[-1]["g"],
+           "mixed_then_fp64": {
+               "time_to_residual_s": hmx[-1]["s"] + t_hand + h4[-1]["s"],
+               "mixed_s": hmx[-1]["s"], "mixed_steps": hmx[-1]["steps"], "handover_s": t_hand,
+               "fp64_s": h4[-1]["s"], "fp64_steps": h4[-1]["steps"], "g": h4[-1]["g"],
                "err": h4[-1]["err"]},
-           "history": {"fp64": pick(h64), "mixed": pick(hmx),
-                       "fp64_after_mixed": hpol and pick(hpol), "fp64_mg32": pick(h32),
-                       "fp64_mg32_after_mixed": pick(h4)}}
+           "history": {"fp64": pick(h64), "mixed": pick(hmx), "fp64_after_mixed": pick(h4)}}
     print(json.dumps(out), flush=True)
 
 
@@ -574,8 +534,9 @@ def bench_large(torch, hq, inputs, K, W, hbm_peak, hbm_kind, shape=(128, 256)):
     time_steps(torch, s, 1, 1)
     prof = s.profile_read()
     s.profile(timing=False)
-    ms_sm = smooth_alone(torch, hq, s, reps=10)
-    roof = roofline_alone(ms_sm, m ** 3 * N, "f32", hbm_peak, hbm_kind, None)
+    kind = dominant(prof) or "smooth"
+    roof = roofline_alone(kind, kernel_alone(torch, s, kind, False, reps=10), m ** 3 * N, "f32",
+                          hbm_peak, hbm_kind, roofline(prof, kind, "f32"))
     roof["traffic"] = None
     out = {"workload": "wells: %d^3 grid, V=|x|^2/2 + 8 wells (default_rng(3)), "
                        "N=%d, tau=0.4, mixed, PCG rtol 1e-6" % (m, N),
@@ -584,6 +545,123 @@ def bench_large(torch, hq, inputs, K, W, hbm_peak, hbm_kind, shape=(128, 256)):
            "workspace_gb": s.workspace.numel() / 1e9}
     del s
     torch.cuda.empty_cache()
+    return out
+
+
+def solver_kw(w):
+    """Solver options of a workload."""
+    kw = dict(tau=w["tau"], cg_rtol=w["cg_rtol"], precision=w["precision"])
+    if w.get("mg_fp32"):
+        kw["mg_fp32"] = 1
+    return kw
+
+
+def refine_to(torch, s, eps, max_rounds=6, rtol=1e-6, maxit=1000):
+    """FP64 residual refinement rounds (hq_refine) until the state passes
+    Algorithm 1's stopping test g < eps (evaluated with an FP64 inner solve:
+    hq_solve with max_steps = 0).  Returns (rounds, PCG iterations, g)."""
+    rounds, its, g = 0, 0, float("inf")
+    while rounds < max_rounds:
+        _, k = s.refine(rounds=1, rtol=rtol, maxit=maxit)
+        rounds += 1
+        its += k
+        _, g = s.solve(eps, 0, raise_on_unconverged=False)
+        if g < eps:
+            break
+    return rounds, its, g
+
+
+def ttr_live(torch, hq, inputs, args):
+    """Time to residual 1e-8 on the 64^3, N = 64 wells workload, measured in
+    this run (host wall clock between synchronisations, from hq_solve entry
+    with the potential and U0 uploaded, to the state that passes Algorithm 1's
+    stopping test g < 1e-8 in FP64).  Adaptive time step (tau_max 10) in every
+    leg.
+
+    mixed_refined: the mixed-precision scheme until g < g_hand, the state
+      handed device to device to an FP64 context (FP32 multigrid
+      preconditioner), then FP64 residual refinement rounds (hq_refine) until
+      g < 1e-8.  The refined eigenvalues are the FP64 reference of this run.
+    mixed_to_err: the mixed scheme continued from the hand-over state until
+      its own Rayleigh-Ritz eigenvalues are within 1e-6 of the reference (the
+      mixed form's stated accuracy), in chunks of 500 steps.
+    fp64_refined: the same with the FP64 scheme (FP64 PCG, FP32 V-cycle)
+      until g < g_hand, then refinement.  Its ms per step gives the FP64
+      scheme's time to eigenvalue error 1e-6 at the mixed leg's step count
+      (the two trajectories agree to rounding, so the step counts are equal;
+      labelled projected)."""
+    import numpy as np
+    V, U0, w = inputs.workload(WORKLOAD)
+    m, N, eps = w["m"], w["N"], w["eps"]
+    g_hand = args.ttr_handoff
+    common = dict(tau=w["tau"], adaptive_tau=1, tau_max=args.tau_max)
+    out = {"workload": "%s: %d^3 wells, N=%d" % (WORKLOAD, m, N), "eps": eps,
+           "tau_rule": "adaptive, tau_max %g" % args.tau_max, "handoff_g": g_hand}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def leg(prec_kw, label):
+        s = hq.Solver(m, N, **common, **prec_kw)
+        s.set_potential(V)
+        s.set_initial(U0)
+        s64 = hq.Solver(m, N, cg_rtol=w["cg_rtol"], precision="fp64", mg_fp32=1, **common)
+        s64.set_potential(V)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push(label)
+        t0 = time.perf_counter()
+        e0.record(s.stream)
+        n1, g1 = s.solve(g_hand, 60000)
+        e1.record(s.stream)
+        U, st = s.state_device()
+        s64.set_state_device(U, st)
+        t_hand = time.perf_counter()
+        rounds, its, g = refine_to(torch, s64, eps)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        torch.cuda.nvtx.range_pop()
+        scheme_s = e0.elapsed_time(e1) / 1e3
+        return s, s64, {"value": t1 - t0, "unit": "s", "how": "measured", "scheme_steps": n1,
+                        "scheme_s": scheme_s, "scheme_ms_per_step": 1e3 * scheme_s / max(n1, 1),
+                        "g_at_handoff": g1, "handoff_and_refine_s": t1 - t_hand,
+                        "refine_rounds": rounds, "refine_pcg_iterations": its, "g": g,
+                        "converged": bool(g < eps)}
+
+    sm, sr, res_m = leg(dict(precision="mixed", cg_rtol=args.mixed_rtol), "ttr_mixed")
+    lam_ref = sr.eigenpairs()["lam_rr"]
+    lam_hand = sm.eigenpairs()["lam_rr"]
+    res_m["eig_err_at_handoff"] = float(np.max(np.abs(lam_hand - lam_ref) / np.abs(lam_ref)))
+    out["mixed_refined"] = res_m
+    del sr
+    # mixed scheme continued to eigenvalue error 1e-6 against the refined values
+    t, steps, err = res_m["scheme_s"], res_m["scheme_steps"], res_m["eig_err_at_handoff"]
+    while err > 1e-6 and steps < res_m["scheme_steps"] + 20000:
+        torch.cuda.synchronize()
+        e0.record(sm.stream)
+        n, _ = sm.solve(1e-300, 500, raise_on_unconverged=False)
+        e1.record(sm.stream)
+        torch.cuda.synchronize()
+        t += e0.elapsed_time(e1) / 1e3
+        steps += n
+        lam = sm.eigenpairs()["lam_rr"]
+        err = float(np.max(np.abs(lam - lam_ref) / np.abs(lam_ref)))
+    out["mixed_to_eig_err_1e-6"] = {"s": t, "steps": steps, "err": err, "how": "measured",
+                                    "reached": bool(err <= 1e-6)}
+    del sm
+    torch.cuda.empty_cache()
+    s64, sr64, res_f = leg(dict(precision="fp64", cg_rtol=w["cg_rtol"], mg_fp32=1), "ttr_fp64")
+    lam64 = sr64.eigenpairs()["lam_rr"]
+    res_f["eig_agreement_with_mixed_refined"] = float(np.max(np.abs(lam64 - lam_ref) /
+                                                             np.abs(lam_ref)))
+    out["fp64_refined"] = res_f
+    del s64, sr64
+    torch.cuda.empty_cache()
+    st = out["mixed_to_eig_err_1e-6"]["steps"]
+    out["fp64_to_eig_err_1e-6"] = {"s": st * res_f["scheme_ms_per_step"] / 1e3, "steps": st,
+                                   "how": "projected: the mixed leg's step count x the FP64 "
+                                          "scheme's ms/step measured above"}
+    out["speedup_mixed_vs_fp64_at_eig_err_1e-6"] = (out["fp64_to_eig_err_1e-6"]["s"] /
+                                                    out["mixed_to_eig_err_1e-6"]["s"])
+    out["speedup_mixed_refined_vs_fp64_refined"] = res_f["value"] / res_m["value"]
     return out
 
 
@@ -607,10 +685,9 @@ def run_hq(args):
     m, N = w["m"], w["N"]
     K, W = args.steps, args.warmup
     hbm_peak, hbm_kind = peaks()
-    result = {}
 
     # ---- FP64 path: headline ------------------------------------------------
-    s = hq.Solver(m, N, tau=w["tau"], cg_rtol=w["cg_rtol"], precision="fp64")
+    s = hq.Solver(m, N, **solver_kw(w))
     s.set_potential(V)
     s.set_initial(U0)
     for _ in range(W):
@@ -628,8 +705,9 @@ def run_hq(args):
     prof = s.profile_read()
     pcg_solves, pcg_iters = s.pcg_stats()
     s.profile(timing=False)
-    roof = roofline_alone(smooth_alone(torch, hq, s), m ** 3 * N, "f64", hbm_peak, hbm_kind,
-                          roofline(prof, "f64", hbm_peak, hbm_kind))
+    kind = dominant(prof)
+    roof = roofline_alone(kind, kernel_alone(torch, s, kind, not w.get("mg_fp32")), m ** 3 * N,
+                          "f64", hbm_peak, hbm_kind, roofline(prof, kind, "f64"))
     brk = breakdown(prof, K)
     # end to end through host buffers: state in from pinned host memory,
     # step, state and gradient norm back to pinned host memory
@@ -648,26 +726,23 @@ def run_hq(args):
     barrier(ws)
     e2e_s = max_over_ranks(ws, e2e_s)
     blk_bytes = m ** 3 * N * 8
-    ttr = {} if args.no_ttr else {"harmonic16_N8": ttr_small(torch, hq, inputs)}
-    if WORKLOAD in TTR_STEPS:
-        rec = TTR_STEPS[WORKLOAD]
-        ttr[WORKLOAD] = {"value": rec["s"], "unit": "s", "how": "recorded (%s)" % rec["command"],
-                         "steps": rec["steps"], "eps": w["eps"], "tau": "adaptive",
-                         "projected_s": rec["steps"] * ms / 1e3,
-                         "projected_basis": "recorded steps x this run's fixed-tau ms/step "
-                                            "(early steps cost more PCG iterations than late ones)",
-                         "fp64_fp32_preconditioner_s": rec["fp64_mg32_s"],
-                         "mixed_then_fp64_fp32_preconditioner_s": rec["mixed_then_fp64_mg32_s"],
-                         "mixed_then_fp64_steps": rec["mixed_then_fp64_mg32_steps"],
-                         "note": "all three end at g < 1e-8 with FP64 blocks; eigenvalues agree "
-                                 "with the plain FP64 run to 1e-14"}
     del s
     torch.cuda.empty_cache()
 
-    # ---- FP64 PCG with an FP32 multigrid preconditioner (mg_fp32) --------------
-    mg32 = None
+    # ---- time to residual (rank 0 of a single-GPU run) ---------------------------
+    ttr = {}
+    if not args.no_ttr:
+        ttr["harmonic16_N8"] = ttr_small(torch, hq, inputs)
+        if ws == 1:
+            clk2 = ClockSampler(local)
+            clk2.start()
+            ttr[WORKLOAD] = ttr_live(torch, hq, inputs, args)
+            ttr[WORKLOAD]["clocks"] = clk2.stop()
+
+    # ---- FP64 with the FP64 V-cycle (mg_fp32 = 0) ---------------------------------
+    v64 = None
     if not args.no_mixed:
-        s3 = hq.Solver(m, N, tau=w["tau"], cg_rtol=w["cg_rtol"], precision="fp64", mg_fp32=1)
+        s3 = hq.Solver(m, N, tau=w["tau"], cg_rtol=w["cg_rtol"], precision="fp64")
         s3.set_potential(V)
         s3.set_initial(U0)
         for _ in range(W):
@@ -676,11 +751,11 @@ def run_hq(args):
         ms3, _ = time_steps(torch, s3, K, ws)
         ms3 = max_over_ranks(ws, ms3)
         sol3, it3 = s3.pcg_stats()
-        mg32 = {"value": job_value(ws, ms3), "unit": "steps/s", "ms_per_step": ms3,
-                "speedup_vs_fp64": ms / ms3, "pcg_iterations_per_solve": it3 / max(sol3, 1),
-                "dtype": "f64 PCG (residuals, updates, stopping test, step algebra); "
-                         "f32 multigrid V-cycle inside the preconditioner",
-                "note": "W = G U solved to the same FP64 rtol 1e-10; not the headline"}
+        v64 = {"value": job_value(ws, ms3), "unit": "steps/s", "ms_per_step": ms3,
+               "headline_speedup_over_this": ms3 / ms,
+               "pcg_iterations_per_solve": it3 / max(sol3, 1),
+               "dtype": "f64 throughout (FP64 multigrid V-cycle)",
+               "note": "the same solve with an FP64 preconditioner; not the headline"}
         del s3
         torch.cuda.empty_cache()
 
@@ -699,21 +774,13 @@ def run_hq(args):
         time_steps(torch, sm, K, ws)
         prof_m = sm.profile_read()
         sm.profile(timing=False)
+        kind_m = dominant(prof_m) or "smooth"
         mixed = {"value": job_value(ws, ms_m), "unit": "steps/s", "ms_per_step": ms_m,
                  "speedup_vs_fp64": ms / ms_m, "dtype": "f32 (FP64 small solve / extraction)",
-                 "to_eig_err_1e-6": None if WORKLOAD not in TTR_STEPS else {
-                     "recorded_fp64_s": TTR_STEPS[WORKLOAD]["fp64_err1e-6_s"],
-                     "recorded_mixed_s": TTR_STEPS[WORKLOAD]["mixed_err1e-6_s"],
-                     "recorded_speedup": TTR_STEPS[WORKLOAD]["fp64_err1e-6_s"] /
-                                         TTR_STEPS[WORKLOAD]["mixed_err1e-6_s"],
-                     "steps_fp64": TTR_STEPS[WORKLOAD]["fp64_err1e-6_steps"],
-                     "steps_mixed": TTR_STEPS[WORKLOAD]["mixed_err1e-6_steps"],
-                     "how": "recorded (%s); same step count, so the speedup at error 1e-6 "
-                            "equals the per-step ratio" % TTR_STEPS[WORKLOAD]["command"]},
                  "cg_rtol": args.mixed_rtol,
-                 "roofline": roofline_alone(smooth_alone(torch, hq, sm), m ** 3 * N, "f32",
-                                            hbm_peak, hbm_kind,
-                                            roofline(prof_m, "f32", hbm_peak, hbm_kind)),
+                 "roofline": roofline_alone(kind_m, kernel_alone(torch, sm, kind_m, False),
+                                            m ** 3 * N, "f32", hbm_peak, hbm_kind,
+                                            roofline(prof_m, kind_m, "f32")),
                  "breakdown": breakdown(prof_m, K)}
         del sm
         torch.cuda.empty_cache()
@@ -743,7 +810,9 @@ def run_hq(args):
         "warmup": W, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "%s: %d^3 grid on [-6,6]^3, V=|x|^2/2 + 8 seeded Gaussian wells, "
-                               "N=%d, tau=%g, PCG rtol %g, FP64" % (WORKLOAD, m, N, w["tau"], w["cg_rtol"]),
+                               "N=%d, tau=%g, FP64 block PCG to rtol %g with an FP32 multigrid "
+                               "preconditioner, FP64 step algebra"
+                               % (WORKLOAD, m, N, w["tau"], w["cg_rtol"]),
                    "n_points": m ** 3, "nev": N, "parallelism": "replicas (one problem per GPU)",
                    "l2": "working set %.2f GB per GPU > 126 MB L2; no flush needed" %
                          (9 * blk_bytes / 1e9)},
@@ -759,7 +828,7 @@ def run_hq(args):
                 "how": "hq_set_state from pinned host (U and warm start), hq_step, "
                        "hq_get_state to pinned host, every step"},
         "mixed": mixed,
-        "fp64_fp32_preconditioner": mg32,
+        "fp64_fp64_vcycle": v64,
         "large": large,
         "batched": batched,
         "cpu_baseline": cpu,
@@ -834,22 +903,38 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def _free_port():
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
+def spawn_command(argv, n, port):
+    """torchrun command that runs this script on n local ranks (one per GPU)
+    with the same arguments; rendezvous on 127.0.0.1."""
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+            "--nproc-per-node", str(n), "--master-addr", "127.0.0.1", "--master-port", str(port),
+            os.path.join(ROOT, "bench.py")] + list(argv)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=25)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["hq", "reference"], default="hq")
     ap.add_argument("--ttr", action="store_true",
-                    help="only measure time to residual / eigenvalue error on %s "
+                    help="only the long scheme-only time-to-residual legs on %s "
                          "(adaptive tau; several minutes)" % WORKLOAD)
     ap.add_argument("--no-ttr", action="store_true",
-                    help="skip the time-to-residual run of the 16^3 workload")
+                    help="skip the time-to-residual legs")
     ap.add_argument("--ttr-steps", type=int, default=40000, help="step cap of each --ttr leg")
     ap.add_argument("--ttr-chunk", type=int, default=250)
-    ap.add_argument("--ttr-pipeline", action="store_true",
-                    help="with --ttr: also hand the mixed state to FP64 and run to 1e-8")
     ap.add_argument("--tau-max", type=float, default=10.0)
+    ap.add_argument("--ttr-handoff", type=float, default=1e-4,
+                    help="g at which the time-to-residual legs hand the scheme's state to "
+                         "the FP64 residual refinement")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
     ap.add_argument("--no-large", action="store_true", help="skip the 128^3, N = 256 workload")
@@ -860,8 +945,18 @@ def main():
     ap.add_argument("--mixed-rtol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    if args.warmup < 0 or args.steps < 1:
-        ap.error("need --steps >= 1 and --warmup >= 0")
+    if args.warmup < 0 or args.steps < 1 or args.gpus < 1:
+        ap.error("need --steps >= 1, --warmup >= 0 and --gpus >= 1")
+    ws = int(os.environ.get("WORLD_SIZE", "0"))
+    if ws == 0 and args.gpus > 1:
+        # launched without torchrun: start one rank per GPU ourselves
+        cmd = spawn_command(sys.argv[1:], args.gpus, _free_port())
+        sys.exit(subprocess.call(cmd, cwd=ROOT))
+    if ws and ws != args.gpus:
+        ap.error("--gpus %d but WORLD_SIZE=%d" % (args.gpus, ws))
+    if ws > 1:
+        # replicas: the timed headline step only (the other legs hold every GPU for minutes)
+        args.no_ttr = args.no_mixed = args.no_large = args.no_batch = True
     if args.impl == "reference":
         run_reference(args)
     elif args.ttr:

@@ -89,11 +89,13 @@ typedef struct {
     int grid_block;      /* threads per CTA of the grid kernels: 0 (= 256), 64, 128, 256 */
     int grid_ctas;       /* target CTAs per SM of the grid kernels: 0 (= 16) .. 64;     */
                          /* both set the launch shape only (hq_tune picks them)      */
-    int fp64_tc;         /* HQ_FP64 only: 1 = the Gram of [U W] and the n x N block   */
+    int fp64_tc;         /* HQ_FP64 only: 2 = the Gram of [U W] and the n x N block   */
                          /* products (Uh, U_{n+1}, the gradient residual, the warm   */
                          /* start) on tensor cores by exact integer slicing of the   */
                          /* FP64 values (error below 2^-53 |row max| |column max|    */
-                         /* per term, FP64 results; for 2N <= 128); 0 = FP64 SIMT   */
+                         /* per term, FP64 results; for 2N <= 128); 1 (default) =    */
+                         /* the same for products of at least 2^25 multiply-adds,    */
+                         /* FP64 SIMT below; 0 = FP64 SIMT                          */
     int mg_fp32;         /* HQ_FP64 only: 1 = the multigrid preconditioner of the     */
                          /* FP64 block PCG runs in FP32 (r rounded to FP32, z widened */
                          /* back, r.z in FP64); the PCG residuals, updates, stopping  */
@@ -103,7 +105,7 @@ typedef struct {
 
 /* Defaults: box [-6,6]^3, tau 0.4, automatic shift, FP64, cg_rtol 1e-10,
  * cg_maxit 200, nu1 = nu2 = 2, coarsest 4, omega 0.8, no timeout, warm start
- * of the corrector solve on, fp64_tc on.  m and nev are left 0 and must be
+ * of the corrector solve on, fp64_tc 1.  m and nev are left 0 and must be
  * set.                                                                      */
 void hq_default_config(hq_config *cfg);
 
@@ -118,7 +120,11 @@ size_t hq_workspace_bytes(const hq_config *cfg);
  * replaying captured graphs (same kernels in the same order, bit-identical
  * results); HQ_ZMARCH=1 / 0 forces the z-marching finest-level sweeps on / off
  * (by default they run for finest-level blocks of 100 MB or more; same
- * element values, PCG dot products summed in another order).              */
+ * element values, PCG dot products summed in another order);
+ * HQ_FUSED_COARSE=0 runs every level of the FP32 V-cycles (HQ_MIXED, mg_fp32)
+ * as separate kernels (by default the levels from the first one whose
+ * vectors fit one CTA's shared memory, about 16^3 points, down to the
+ * coarsest run as one launch, one CTA per column).                        */
 hq_status hq_init(const hq_config *cfg, void *d_workspace, size_t bytes,
                   void *cuda_stream, hq_ctx **out);
 
@@ -227,7 +233,10 @@ hq_status hq_problem_info(hq_ctx *ctx, double *h, double *sigma, int *levels,
 /* ---- operations of one step, on caller device buffers (point-major,
  * ncol columns, FP64 in HQ_FP64 contexts, FP32 in HQ_MIXED contexts). ---- */
 
-/* y = (H + sigma) x on the finest grid (the operator G inverts). */
+/* y = (H + sigma) x on the finest grid (the operator G inverts).  With
+ * ncol == N this is the block PCG's own operator launch (same kernel and
+ * launch shape, its per-column x.y partial sums formed into the context's
+ * scratch). */
 hq_status hq_apply_operator(hq_ctx *ctx, const void *x, void *y, int ncol);
 
 /* z = M r: one multigrid V-cycle for (H + sigma) (symmetric when nu1 == nu2),
@@ -321,7 +330,8 @@ typedef enum {
     HQ_K_RESIDUAL,      /* residual r - (H + sigma) z                      */
     HQ_K_SMOOTH,        /* damped-Jacobi sweeps                            */
     HQ_K_TRANSFER,      /* restriction / prolongation                      */
-    HQ_K_COARSE,        /* coarsest-level solve                            */
+    HQ_K_COARSE,        /* coarsest-level solve, or the coarse levels of an */
+                        /* FP32 V-cycle in one launch                      */
     HQ_K_VECTOR,        /* PCG vector updates, dots, conversions           */
     HQ_K_REDUCE,        /* per-column / global finalising reductions       */
     HQ_K_GRAM,          /* inner-product matrices <A,B>                    */

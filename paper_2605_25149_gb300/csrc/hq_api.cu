@@ -102,6 +102,8 @@ struct hq_ctx {
     bool mg32 = false;
     // FP64 V-cycle smoothing from the pre-scaled right-hand side (Level::rt)
     bool rtilde = false;
+    // FP32 V-cycles: levels fuse_l0 .. L-1 run as one launch (k_vcoarse); -1: off
+    int fuse_l0 = -1;
     float *R32 = nullptr, *Z32 = nullptr, *T32 = nullptr;
     // n x N blocks in the working precision
     void *U = nullptr, *W = nullptr, *Uh = nullptr, *Z = nullptr;
@@ -160,6 +162,11 @@ struct hq_ctx {
     StepGraph bsg[2];
     long long bseen[4] = {0, 0, 0, 0};
     int gen = 0;   // incremented whenever the captured graphs are dropped
+    // hq_solve's device-side time loop: a one-member batch graph on this
+    // context's stream (created at the first graph-replayed hq_solve; freed by
+    // hq_destroy); solo_failed: its capture failed, use the host loop
+    hq_batch *solo = nullptr;
+    bool solo_failed = false;
     ~hq_ctx() {
         for (cudaEvent_t e : evpool) cudaEventDestroy(e);
         for (int i = 0; i < npgraph; i++) {
@@ -271,7 +278,7 @@ bool valid_config(const hq_config *c, std::string *why) {
     if (c->grid_block != 0 && c->grid_block != 64 && c->grid_block != 128 && c->grid_block != 256)
         return fail("grid_block must be 0, 64, 128 or 256");
     if (c->grid_ctas < 0 || c->grid_ctas > 64) return fail("grid_ctas must be in [0, 64]");
-    if (c->fp64_tc != 0 && c->fp64_tc != 1) return fail("fp64_tc must be 0 or 1");
+    if (c->fp64_tc < 0 || c->fp64_tc > 2) return fail("fp64_tc must be 0, 1 or 2");
     if (c->mg_fp32 != 0 && c->mg_fp32 != 1) return fail("mg_fp32 must be 0 or 1");
     return true;
 }
@@ -627,9 +634,56 @@ hq_status vcycle_rt(hq_ctx *x, int l, const double *r, double *Zf, double *Tb, b
     return HQ_OK;
 }
 
+// the FP32 V-cycle of levels l .. L-1 as one launch's description
+VCoarse make_vcoarse(const hq_ctx *x, int l) {
+    VCoarse vc;
+    std::memset(&vc, 0, sizeof(vc));
+    vc.levels = x->L - l;
+    for (int k = 0; k < vc.levels; k++) {
+        const Level &v = x->mg[l + k];
+        vc.m[k] = v.m;
+        vc.c[k] = (float)v.c;
+        vc.D[k] = (const float *)v.Dt;
+        vc.wD[k] = (const float *)v.wDt;
+        if (k + 1 < vc.levels) {
+            vc.ridx[k] = v.tab.ridx;
+            vc.rw[k] = v.tab.rwf;
+            vc.pidx[k] = v.tab.pidx;
+            vc.pw[k] = v.tab.pwf;
+            const double q = (double)(x->mg[l + k + 1].m + 1) / (double)(v.m + 1);
+            vc.rscale[k] = (float)(q * q * q);
+        }
+    }
+    vc.Ainv = x->Ainv;
+    vc.nc = (int)x->nc;
+    vc.omw = (float)(1.0 - x->cfg.mg_omega);
+    vc.nu1 = x->cfg.mg_nu1;
+    vc.nu2 = x->cfg.mg_nu2;
+    return vc;
+}
+
+// first level from which the FP32 V-cycle fits one launch (-1: none), or -1
+// when HQ_FUSED_COARSE=0 (the multi-kernel V-cycle, for comparisons)
+int fuse_level(const hq_ctx *x) {
+    const char *e = std::getenv("HQ_FUSED_COARSE");
+    if (e && e[0] == '0') return -1;
+    if (!x->mixed && !x->mg32) return -1;
+    for (int l = 0; l + 1 < x->L; l++) {
+        if (x->L - l > VC_MAXLEV) continue;
+        if (vcoarse_smem_bytes(make_vcoarse(x, l)) <= (size_t)VC_MAX_SMEM) return l;
+    }
+    return -1;
+}
+
 template <typename T>
 hq_status vcycle(hq_ctx *x, int l, const T *r, T *Zf, T *Tb, bool first_done, double *part_final) {
     LevelScope lvl_(l);
+    if constexpr (std::is_same<T, float>::value) {
+        if (x->fuse_l0 >= 0 && l >= x->fuse_l0 && l + 1 < x->L && !first_done && !part_final) {
+            launch_vcoarse(make_vcoarse(x, l), x->N, r, Zf, x->st);
+            return HQ_OK;
+        }
+    }
     Level &v = x->mg[l];
     const T c = (T)v.c, omw = (T)(1.0 - x->cfg.mg_omega);
     if (l == x->L - 1) {
@@ -865,9 +919,19 @@ hq_status pcg(hq_ctx *x, const T *B, T *X, double rtol, int maxit, int *iters_ho
 // tcgen05 3xTF32 in HQ_MIXED contexts.
 template <typename T>
 void gram_sym(hq_ctx *x, const T *X1, int n1, const T *X2, int n2, double *out);
+// fp64_tc = 1 sends an FP64 product to the digit-sliced tensor-core kernels
+// only from this many multiply-adds on: below it their splitting passes and
+// one-CTA-per-SM schedule cost more than the SIMT FP64 kernels (a 4096 x 8
+// block: 23 us per product on tensor cores against a few us in SIMT)
+constexpr double OZ_MIN_MACS = 33554432.0;
+bool use_oz(const hq_ctx *x, double macs) {
+    return x->cfg.fp64_tc == 2 || (x->cfg.fp64_tc == 1 && macs >= OZ_MIN_MACS);
+}
+
 template <>
 void gram_sym<double>(hq_ctx *x, const double *X1, int n1, const double *X2, int n2, double *out) {
-    if (x->ozgram && gram_oz_supported(n1 + n2)) {
+    const double na = n1 + n2;
+    if (x->ozgram && gram_oz_supported(n1 + n2) && use_oz(x, 0.5 * (double)x->n * na * na)) {
         launch_gram_oz(x->n, X1, n1, X2, n2, x->h3, x->ozgram, out, x->status, x->st);
         return;
     }
@@ -888,7 +952,8 @@ void block_gemm(hq_ctx *x, const T *A1, int k1, const double *M1, const T *A2, i
 template <>
 void block_gemm<double>(hq_ctx *x, const double *A1, int k1, const double *M1, const double *A2,
                         int k2, const double *M2, const double *Cin, double *Out, bool sq, int *np) {
-    if (x->ozimg && tall_oz_supported(k1, A2 ? k2 : 0)) {
+    const double K = k1 + (A2 ? k2 : 0);
+    if (x->ozimg && tall_oz_supported(k1, A2 ? k2 : 0) && use_oz(x, (double)x->n * K * x->N)) {
         launch_tall_oz(x->n, A1, k1, M1, A2, k2, M2, x->N, Cin, Out, sq ? x->tpart : nullptr,
                        x->ozimg, x->status, x->st);
         if (np) *np = tall_oz_partials(x->n, x->N);
@@ -1661,10 +1726,50 @@ hq_status step_impl(hq_ctx *x, int nsteps, double *resid_out) {
     return HQ_OK;
 }
 
+// Algorithm 1 on the device: the time loop of a one-member batch graph (the
+// batched form's WHILE node, stopping test g < eps and step cap decided on
+// the device), one graph launch and one host synchronisation per call.  The
+// trajectory equals the host loop's bit for bit.  Returns false (nothing
+// launched) when the graph cannot be captured; the caller then runs the host
+// loop.
+bool solve_device(hq_ctx *x, double eps, long max_steps, long *steps_out, double *resid_out,
+                  hq_status *st_out) {
+    if (x->solo_failed || !x->use_graphs || x->timing) return false;
+    if (!x->solo) {
+        x->solo = new hq_batch();
+        x->solo->ctx.assign(1, x);
+        x->solo->gen.assign(1, -1);
+        x->solo->st = x->st;
+    }
+    hq_batch *b = x->solo;
+    if (!b->exec || b->gen[0] != x->gen) {
+        if (cudaStreamSynchronize(x->st) != cudaSuccess) return false;
+        if (batch_build(b) != HQ_OK) {
+            x->solo_failed = true;
+            cudaGetLastError();
+            x->err.clear();
+            return false;
+        }
+    }
+    long steps = 0;
+    double g = NAN;
+    int stk = HQ_OK;
+    const double tmo = x->cfg.timeout_s > 0 ? x->cfg.timeout_s : 0.0;
+    hq_status st = batch_run(b, 0, &eps, max_steps, tmo, &steps, &g, &stk);
+    if (st == HQ_OK || stk != HQ_OK) st = (hq_status)stk;
+    else if (x->err.empty()) x->err = b->err;
+    if (steps_out) *steps_out = steps;
+    if (resid_out) *resid_out = g;
+    *st_out = st;
+    return true;
+}
+
 template <typename T>
 hq_status solve_impl(hq_ctx *x, double eps, long max_steps, long *steps_out, double *resid_out) {
     HQ_TRY(need_ready(x));
     HQ_TRY(clear_status(x));
+    hq_status dst = HQ_OK;
+    if (solve_device(x, eps, max_steps, steps_out, resid_out, &dst)) return dst;
     auto t0 = std::chrono::steady_clock::now();
     long taken = 0;
     double g = NAN;
@@ -2056,9 +2161,13 @@ hq_status refine_impl(hq_ctx *x, int rounds, double rtol, int maxit, double *res
 template <typename T>
 hq_status apply_impl(hq_ctx *x, const void *in, void *out, int ncol) {
     Level &v = x->lev[0];
-    // the step's own launch shape for N columns, a plain one otherwise
-    GridGeom g = ncol == x->N ? v.g : make_geom(x->m, ncol, (int)sizeof(T));
-    launch_apply<T>(g, (const T *)v.Dt, (T)v.c, (const T *)in, (T *)out, nullptr, x->st);
+    // N columns: the block PCG's own operator launch (its launch shape, the
+    // per-column x.y partial sums formed into the PCG scratch); a plain launch
+    // otherwise
+    const bool own = ncol == x->N;
+    GridGeom g = own ? v.g : make_geom(x->m, ncol, (int)sizeof(T));
+    launch_apply<T>(g, (const T *)v.Dt, (T)v.c, (const T *)in, (T *)out, own ? x->part : nullptr,
+                    x->st);
     return check_launch(x);
 }
 template <typename T>
@@ -2080,9 +2189,20 @@ hq_status gram_impl(hq_ctx *x, const void *A, int Na, const void *B, int Nb, dou
         return sync_status(x, x->status, "tensor-core Gram");
     }
     GramPlan gp = make_gram_plan(x->n, Na, Nb, A == B && Na == Nb);
-    if (gram_partial_bytes(gp) > gram_partial_bytes(x->gplan_max) &&
-        gram_partial_bytes(gp) > gram_partial_bytes(x->gplan_uw))
-        return fail(x, HQ_ERR_ARG, "Gram shape exceeds the workspace plan");
+    // the split over grid points must fit the workspace's partial sums (sized
+    // for the step's own Gram shapes): otherwise fewer, longer point chunks
+    const size_t avail = std::max(gram_partial_bytes(x->gplan_max), gram_partial_bytes(x->gplan_uw));
+    if (gram_partial_bytes(gp) > avail) {
+        const size_t per_chunk = sizeof(double) * (size_t)gp.ntiles * 64 * 64;
+        const long max_chunks = (long)(avail / per_chunk);
+        if (max_chunks < 1) return fail(x, HQ_ERR_ARG, "Gram shape exceeds the workspace plan");
+        long rows = (x->n + max_chunks - 1) / max_chunks;
+        rows = (rows + 15) / 16 * 16;
+        gp.chunk_rows = rows;
+        gp.chunks = (int)((x->n + rows - 1) / rows);
+        if (gram_partial_bytes(gp) > avail)
+            return fail(x, HQ_ERR_ARG, "Gram shape exceeds the workspace plan");
+    }
     launch_gram<T>(gp, (const T *)A, Na, nullptr, 0, (const T *)B, Nb, nullptr, 0, w, x->gpart, out, x->st);
     return check_launch(x);
 }
@@ -2215,6 +2335,7 @@ hq_status hq_init(const hq_config *cfg, void *d_workspace, size_t bytes, void *c
         x->use_graphs = !(e && e[0] == '1');
     }
     carve(x, cfg, x->ws);
+    x->fuse_l0 = fuse_level(x);
     // the status words and counters start cleared
     cudaError_t e = cudaMemsetAsync(x->sc.status, 0, sizeof(int), x->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(x->status, 0, sizeof(int), x->st);
@@ -2223,6 +2344,7 @@ hq_status hq_init(const hq_config *cfg, void *d_workspace, size_t bytes, void *c
     if (e == cudaSuccess) e = cudaStreamSynchronize(x->st);
     if (x->mixed) hq::tc_prepare();
     hq::lu_prepare();
+    hq::vcoarse_prepare();
     if (x->mixed) hq::lu32_prepare();
     if (x->ozimg || x->ozgram) hq::oz_prepare();
     if (e != cudaSuccess) {
@@ -2559,7 +2681,11 @@ const char *hq_status_string(hq_status s) {
     return "unknown status";
 }
 
-void hq_destroy(hq_ctx *x) { delete x; }
+void hq_destroy(hq_ctx *x) {
+    if (!x) return;
+    delete x->solo;
+    delete x;
+}
 
 // ---------------------------------------------------------------------------
 // launch-shape autotuner

@@ -10,43 +10,51 @@ import bench
 from tests.helpers import dense_h
 
 
-def test_roofline_alone_fp64_is_alu_bound_with_issue_fraction():
+@pytest.mark.parametrize("kind,ops", [("smooth", 7), ("stencil", 8)])
+def test_roofline_alone_fp64_is_alu_bound_with_issue_fraction(kind, ops):
     n, ms = 16777216, 0.24
-    r = bench.roofline_alone(ms, n, "f64", 6778.7, "measured", None)
+    r = bench.roofline_alone(kind, ms, n, "f64", 6778.7, "measured", None)
     t = ms / 1e3
-    flops, words = bench.ALGO_F64["smooth"]
+    flops, words = bench.ALGO_F64[kind]
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["kernel"].startswith(kind)
     assert r["achieved"] == pytest.approx(flops * n / t / 1e12)
     assert r["peak"] == pytest.approx(2 * 152 * 2.07 * 2 / 1e3)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
-    # 7 FP64-pipe instructions per point-column against 2 per clock per SM
-    assert r["fp64_issue_frac"] == pytest.approx(7 * n / t / (2 * 152 * 2.07e9))
+    # FP64-pipe instructions per point-column against 2 per clock per SM
+    assert r["fp64_issue_frac"] == pytest.approx(ops * n / t / (2 * 152 * 2.07e9))
     assert r["hbm_gbs"] == pytest.approx(words * 8 * n / t / 1e9)
     assert r["algorithmic_bytes"] == words * 8 * n
-    tr = bench.TRAFFIC_PER_ELEMENT[("smooth", "f64")]
+    tr = bench.TRAFFIC_PER_ELEMENT.get((kind, "f64"))
     assert r["traffic"] == (None if tr is None else pytest.approx(tr * n))
 
 
 def test_roofline_alone_fp32_is_hbm_bound():
     n, ms = 16777216, 0.04
-    r = bench.roofline_alone(ms, n, "f32", 6778.7, "measured", None)
+    r = bench.roofline_alone("smooth", ms, n, "f32", 6778.7, "measured", None)
     flops, words = bench.ALGO["smooth"]
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert r["achieved"] == pytest.approx(words * 4 * n / (ms / 1e3) / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / 6778.7)
+    assert r["traffic"] == pytest.approx(bench.TRAFFIC_PER_ELEMENT[("smooth", "f32")] * n)
 
 
 def test_roofline_picks_the_dominant_grid_class():
     # (launches, ms, point-columns) per class; "vector" is not a grid class
     prof = {"smooth": (45, 12.0, 45 * 1e6), "stencil": (15, 4.0, 15 * 1e6),
             "residual": (17, 4.4, 17 * 1e6), "vector": (30, 30.0, 30 * 1e6)}
-    r = bench.roofline(prof, "f64", 6778.7, "measured")
+    assert bench.dominant(prof) == "smooth"
+    r = bench.roofline(prof, "smooth", "f64")
     assert r["kernel"] == "smooth"
     assert r["launches"] == 45
     assert r["ms_per_launch"] == pytest.approx(12.0 / 45)
     assert r["elements_per_launch"] == pytest.approx(1e6)
     assert r["share"] == pytest.approx(12.0 / 50.4)
-    assert bench.roofline({"vector": (1, 1.0, 1.0)}, "f64", 1.0, "x") is None
+    assert r["tflops"] == pytest.approx(9.0 * 1e6 / (12.0 / 45 / 1e3) / 1e12)
+    prof["stencil"] = (16, 20.0, 16 * 1e6)
+    assert bench.dominant(prof) == "stencil"
+    assert bench.dominant({"vector": (1, 1.0, 1.0)}) is None
+    assert bench.roofline({"vector": (1, 1.0, 1.0)}, "smooth", "f64") is None
 
 
 def test_job_value_counts_every_replica_at_the_slowest_time():

@@ -201,7 +201,7 @@ def test_tensor_core_gram_has_no_accumulation_bias():
     assert abs(relerr.mean()) < 3e-7, relerr.mean()
 
 
-@pytest.mark.parametrize("m,N", [(8, 3), (16, 8)])
+@pytest.mark.parametrize("m,N", [(8, 3), (16, 8), (33, 5)])
 def test_mixed_operator_and_vcycle_match_oracle(m, N):
     s, V, _ = make(m, N, precision="mixed", cg_rtol=1e-6)
     torch = torch_mod()
@@ -262,7 +262,7 @@ def test_fp64_tensor_core_products_match_fp64(m, N, k1, k2):
     Cin = rng.standard_normal((n, N))
     ref = A1 @ M1 + Cin + (A2 @ M2 if k2 else 0.0)
     outs = []
-    for tc in (1, 0):
+    for tc in (2, 0):
         s, _, _ = make(m, N, fp64_tc=tc)
         outs.append(host(s.block_gemm(dev(A1), dev(M1), None if A2 is None else dev(A2),
                                       None if M2 is None else dev(M2), dev(Cin))))
@@ -280,11 +280,11 @@ def test_fp64_tensor_core_products_match_fp64(m, N, k1, k2):
 @pytest.mark.parametrize("m,N", [(16, 64), (13, 9)])
 def test_fp64_tensor_core_gram_matches_simt(m, N):
     """The Gram of [U W] of one step by digit slicing on tensor cores
-    (fp64_tc = 1) against the FP64 SIMT Gram (fp64_tc = 0) on the same state:
+    (fp64_tc = 2) against the FP64 SIMT Gram (fp64_tc = 0) on the same state:
     exactly symmetric, and equal to within 2^-50 |col max_i| |col max_j| n h^3."""
     torch_mod()
     grams, Ws = [], []
-    for tc in (1, 0):
+    for tc in (2, 0):
         s, V, U0 = make(m, N, fp64_tc=tc, cg_rtol=1e-12)
         tr = s.step_trace()
         grams.append(host(tr["gram"]))
@@ -294,3 +294,36 @@ def test_fp64_tensor_core_gram_matches_simt(m, N):
     scale = np.sqrt(np.abs(np.diag(g_ref)))
     bound = 2.0 ** -44 * np.outer(scale, scale) * (m ** 3)
     assert np.all(np.abs(g_tc - g_ref) <= bound + 1e-14 * np.abs(g_ref).max())
+
+
+@pytest.mark.parametrize("m,N,prec", [(16, 8, "mg32"), (8, 3, "mixed"), (20, 6, "mixed"),
+                                      (33, 5, "mixed"), (48, 4, "mixed"), (24, 3, "mg32")])
+def test_fused_coarse_vcycle_matches_separate_kernels(m, N, prec, monkeypatch):
+    """The coarse levels of an FP32 V-cycle as one launch (one CTA per column,
+    every level from about 16^3 points down in shared memory) against the
+    same V-cycle as separate kernels (HQ_FUSED_COARSE=0): each operation
+    repeats its separate kernel's expression, so the V-cycle and three steps
+    of the scheme agree bit for bit.  Cases: the whole V-cycle fused (m <= 20),
+    fused from level 1 (33, 48), FP64 contexts with the FP32 preconditioner."""
+    torch_mod()
+    kw = dict(precision="mixed", cg_rtol=1e-6) if prec == "mixed" else dict(mg_fp32=1)
+    outs = []
+    for fused in (True, False):
+        if fused:
+            monkeypatch.delenv("HQ_FUSED_COARSE", raising=False)
+        else:
+            monkeypatch.setenv("HQ_FUSED_COARSE", "0")
+        s, V, _ = make(m, N, **kw)
+        rng = np.random.default_rng(m + N)
+        X = rng.standard_normal((m ** 3, N))
+        if prec == "mixed":
+            X = X.astype(np.float32)
+        z = host(s.mg_vcycle(dev(X)))
+        s.profile()
+        s.step(3)
+        launches = s.profile_read()
+        outs.append((z, s.get_state()[0], launches))
+    (zf, uf, lf), (zs, us, ls) = outs
+    np.testing.assert_array_equal(zf, zs)
+    np.testing.assert_array_equal(uf, us)
+    assert sum(v[0] for v in lf.values()) < sum(v[0] for v in ls.values())

@@ -51,3 +51,19 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(1, 7.0) == 7.0
     assert bench.job_value(1, 10.0) == 100.0
+
+
+def test_bench_spawns_one_rank_per_gpu_without_torchrun():
+    """bench.py --gpus N started without WORLD_SIZE re-launches itself under
+    torch.distributed.run with N local ranks, the same arguments and a
+    127.0.0.1 rendezvous."""
+    import sys
+
+    import bench
+    cmd = bench.spawn_command(["--gpus", "4", "--steps", "5"], 4, 29512)
+    assert cmd[:3] == [sys.executable, "-m", "torch.distributed.run"]
+    i = cmd.index("--nproc-per-node")
+    assert cmd[i + 1] == "4"
+    assert cmd[cmd.index("--master-addr") + 1] == "127.0.0.1"
+    assert cmd[cmd.index("--master-port") + 1] == "29512"
+    assert cmd[-5].endswith("bench.py") and cmd[-4:] == ["--gpus", "4", "--steps", "5"]
