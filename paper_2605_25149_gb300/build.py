@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhq.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["k_grid.cu", "k_dense.cu", "k_gram_tc.cu", "k_batch.cu", "k_tall_oz.cu", "hq_api.cu", "hq_static.cu"]
+SOURCES = ["k_grid.cu", "k_dense.cu", "k_gram_tc.cu", "k_batch.cu", "k_tall_oz.cu", "k_vcoarse.cu",
+           "hq_api.cu", "hq_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "-I" + INCLUDE]

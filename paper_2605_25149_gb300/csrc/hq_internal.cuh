@@ -147,6 +147,32 @@ void launch_coarse_solve(const GridGeom &g, const double *Ainv, const T *r, T *z
 template <typename T>
 void launch_dot(const GridGeom &g, const T *x, const T *y, double *part, cudaStream_t s);
 
+// The coarse levels l0 .. L-1 of an FP32 V-cycle in one launch (k_vcoarse.cu):
+// one CTA per column, every level's vectors in shared memory.  Arrays are
+// indexed from l0 (entry 0 = level l0); the last entry is the coarsest level.
+constexpr int VC_MAXLEV = 8;
+constexpr int VC_MAX_SMEM = 200 * 1024;
+struct VCoarse {
+    int levels;                       // levels in the launch (>= 2)
+    int m[VC_MAXLEV];                 // nodes per side
+    float c[VC_MAXLEV];               // 1 / (2 h_l^2)
+    const float *D[VC_MAXLEV], *wD[VC_MAXLEV];
+    const int *ridx[VC_MAXLEV];       // transfer tables of level l to l + 1
+    const float *rw[VC_MAXLEV];
+    const int *pidx[VC_MAXLEV];
+    const float *pw[VC_MAXLEV];
+    float rscale[VC_MAXLEV];          // ((m_{l+1} + 1) / (m_l + 1))^3
+    const double *Ainv;               // dense inverse of the coarsest operator
+    int nc;
+    float omw;                        // 1 - omega
+    int nu1, nu2;
+};
+size_t vcoarse_smem_bytes(const VCoarse &v);
+// sets the dynamic shared-memory limit (call once, outside any stream capture)
+void vcoarse_prepare();
+// z = V-cycle(r) from level l0 for all N columns (point-major n_l0 x N FP32 blocks)
+void launch_vcoarse(const VCoarse &v, int N, const float *r, float *z, cudaStream_t s);
+
 // per-column reduction of gy partials + PCG scalar logic
 enum FinMode { FIN_BNORM_RNORM = 0, FIN_ALPHA = 1, FIN_RR = 2, FIN_BETA = 3, FIN_RZ = 4 };
 // row chunks of the finalisation for gy partial rows (sizes PcgScalars::fpart)

@@ -1,0 +1,242 @@
+// The coarse levels of the FP32 multigrid V-cycle in one launch.
+//
+// Below a few thousand points per level the V-cycle's kernels are bound by
+// launch latency: on a 16^3 level each of its ~20 launches (sweeps, residual,
+// three restriction and three prolongation passes per level, the coarsest
+// solve) runs for about as long as it takes to start.  The V-cycle acts on
+// every column independently, so here one CTA carries one column through all
+// levels from l0 down to the coarsest and back, with every level's right-hand
+// side, iterates and transfer temporaries in shared memory: no grid-wide
+// synchronisation, one launch per V-cycle.
+//
+// Each operation repeats the expression of its multi-kernel counterpart in
+// k_grid.cu (damped-Jacobi sweep, residual, the 1-D transfer passes with the
+// same tap tables in the same order, the coarsest solve's FP64 sums in the
+// same grouping), so a column's values follow the same roundings.
+#include "hq_internal.cuh"
+
+#include <algorithm>
+
+namespace hq {
+
+namespace {
+
+constexpr int VC_THREADS = 512;
+
+// sum of the six neighbours of point p = i + m (j + m k) in one column stored
+// contiguously (zero outside the grid), grouped as nbr_sum groups them
+__device__ __forceinline__ float nbr6(const float *x, int p, int i, int j, int k, int m) {
+    const int sy = m, sz = m * m;
+    const bool bw = i > 0, be = i < m - 1, bs = j > 0, bn = j < m - 1, bb = k > 0, bt = k < m - 1;
+    const float a0 = bw ? x[p - 1] : 0.f, a1 = be ? x[p + 1] : 0.f;
+    const float a2 = bs ? x[p - sy] : 0.f, a3 = bn ? x[p + sy] : 0.f;
+    const float a4 = bb ? x[p - sz] : 0.f, a5 = bt ? x[p + sz] : 0.f;
+    return ((a0 + a1) + (a2 + a3)) + (a4 + a5);
+}
+
+__device__ __forceinline__ void decomp(int p, int m, int &i, int &j, int &k) {
+    const int q = p / m;
+    i = p - q * m;
+    k = q / m;
+    j = q - k * m;
+}
+
+// z = wD r (the first sweep from zero)
+__device__ void sm_first(int m, const float *__restrict__ wD, const float *r, float *z) {
+    const int n = m * m * m;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        const float w = __ldg(wD + p);
+        z[p] = w * r[p];
+    }
+}
+
+// zout = (1 - omega) zin + wD (r + c nbrsum(zin))
+__device__ void sm_jacobi(int m, const float *__restrict__ wD, float c, float omw, const float *r,
+                          const float *zin, float *zout) {
+    const int n = m * m * m;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        int i, j, k;
+        decomp(p, m, i, j, k);
+        const float s = nbr6(zin, p, i, j, k, m);
+        const float w = __ldg(wD + p);
+        const float zc = zin[p], rv = r[p];
+        zout[p] = omw * zc + w * (rv + c * s);
+    }
+}
+
+// y = (b - D x) + c nbrsum(x)
+__device__ void sm_resid(int m, const float *__restrict__ D, float c, const float *x, const float *b,
+                         float *y) {
+    const int n = m * m * m;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        int i, j, k;
+        decomp(p, m, i, j, k);
+        const float s = nbr6(x, p, i, j, k, m);
+        const float d = __ldg(D + p);
+        const float xc = x[p], bb = b[p];
+        y[p] = (bb - d * xc) + c * s;
+    }
+}
+
+// one 1-D transfer pass on a single column (k_axis_pass with N = 1): output
+// dims (o2, o1, o0), input dims equal except along `axis` (ilen); output
+// index o along the axis takes taps idx[o NT + t] (-1 = none) with weights
+// w[o NT + t]; out = scale sum (no add) or add + sum (scale = 1)
+template <int NT>
+__device__ void sm_axis(int o2, int o1, int o0, int ilen, int axis, const int *__restrict__ idx,
+                        const float *__restrict__ w, float scale, const float *in, const float *add,
+                        float *out) {
+    const int nout = o2 * o1 * o0;
+    const int d0 = axis == 0 ? ilen : o0;
+    const int d1 = axis == 1 ? ilen : o1;
+    const int s1 = d0, s2 = d1 * d0;
+    const int sa = axis == 0 ? 1 : (axis == 1 ? s1 : s2);
+    const bool unit = scale == 1.f;
+    for (int p = threadIdx.x; p < nout; p += blockDim.x) {
+        const int i0 = p % o0;
+        const int q = p / o0;
+        const int i1 = q % o1;
+        const int i2 = q / o1;
+        const int oa = axis == 0 ? i0 : (axis == 1 ? i1 : i2);
+        const int ib = (axis == 0 ? 0 : i0) + (axis == 1 ? 0 : i1 * s1) + (axis == 2 ? 0 : i2 * s2);
+        int ii[NT];
+        float wt[NT], a[NT];
+#pragma unroll
+        for (int t = 0; t < NT; t++) {
+            ii[t] = __ldg(idx + oa * NT + t);
+            wt[t] = __ldg(w + oa * NT + t);
+            a[t] = ii[t] >= 0 ? in[ib + ii[t] * sa] : 0.f;
+        }
+        float e = 0.f;
+        if (add) e = add[p];
+        float acc = (add && unit) ? e : 0.f;
+#pragma unroll
+        for (int t = 0; t < NT; t++) {
+            if (ii[t] < 0) continue;
+            acc += wt[t] * a[t];
+        }
+        out[p] = unit ? acc : (add ? e + scale * acc : scale * acc);
+    }
+}
+
+// z = Ainv r on the coarsest level: per point, eight FP64 partial sums over
+// the terms qq = y, y + 8, ... (y = 0..7), added in y order (the grouping of
+// k_coarse_solve), rounded to FP32
+__device__ void sm_coarse(int nc, const double *__restrict__ Ainv, const float *r, float *z) {
+    for (int p = threadIdx.x; p < nc; p += blockDim.x) {
+        double s = 0.0;
+        for (int y = 0; y < 8; y++) {
+            double acc = 0.0;
+            for (int qq = y; qq < nc; qq += 8) acc += __ldg(Ainv + (size_t)p * nc + qq) * (double)r[qq];
+            s += acc;
+        }
+        z[p] = (float)s;
+    }
+}
+
+struct LevelSmem {
+    float *r, *a, *b;
+};
+
+__global__ void __launch_bounds__(VC_THREADS) k_vcoarse(VCoarse v, int N, const float *__restrict__ rin,
+                                                        float *__restrict__ zout) {
+    extern __shared__ __align__(16) float vsm[];
+    const int col = blockIdx.x;
+    const int Lf = v.levels;   // levels in this launch: l0 .. l0 + Lf - 1 (last = coarsest)
+    LevelSmem lv[VC_MAXLEV];
+    float *q = vsm;
+    for (int l = 0; l < Lf; l++) {
+        const int n = v.m[l] * v.m[l] * v.m[l];
+        lv[l].r = q;
+        lv[l].a = q + n;
+        lv[l].b = q + 2 * n;
+        q += 3 * n;
+    }
+    float *tmp1 = q;
+    float *tmp2 = q + (Lf > 1 ? v.m[0] * v.m[0] * v.m[1] : 0);
+    // right-hand side of level l0 (column `col` of a point-major n0 x N block)
+    {
+        const int n0 = v.m[0] * v.m[0] * v.m[0];
+        for (int p = threadIdx.x; p < n0; p += blockDim.x) lv[0].r[p] = rin[(size_t)p * N + col];
+    }
+    __syncthreads();
+    // down: pre-smoothing, residual, restriction
+    float *cur[VC_MAXLEV];
+    for (int l = 0; l + 1 < Lf; l++) {
+        const int m = v.m[l], mc = v.m[l + 1];
+        float *c0 = lv[l].a, *o0 = lv[l].b;
+        sm_first(m, v.wD[l], lv[l].r, c0);
+        __syncthreads();
+        for (int s = 1; s < v.nu1; s++) {
+            sm_jacobi(m, v.wD[l], v.c[l], v.omw, lv[l].r, c0, o0);
+            __syncthreads();
+            float *t = c0;
+            c0 = o0;
+            o0 = t;
+        }
+        sm_resid(m, v.D[l], v.c[l], c0, lv[l].r, o0);
+        __syncthreads();
+        sm_axis<XFER_RTAPS>(m, m, mc, m, 0, v.ridx[l], v.rw[l], 1.f, o0, nullptr, tmp1);
+        __syncthreads();
+        sm_axis<XFER_RTAPS>(m, mc, mc, m, 1, v.ridx[l], v.rw[l], 1.f, tmp1, nullptr, tmp2);
+        __syncthreads();
+        sm_axis<XFER_RTAPS>(mc, mc, mc, m, 2, v.ridx[l], v.rw[l], v.rscale[l], tmp2, nullptr,
+                            lv[l + 1].r);
+        __syncthreads();
+        cur[l] = c0;
+    }
+    // coarsest solve
+    sm_coarse(v.nc, v.Ainv, lv[Lf - 1].r, lv[Lf - 1].a);
+    __syncthreads();
+    float *zc = lv[Lf - 1].a;   // the finished correction of the level below
+    // up: prolongation added to the pre-smoothed iterate, post-smoothing
+    for (int l = Lf - 2; l >= 0; l--) {
+        const int m = v.m[l], mc = v.m[l + 1];
+        float *c0 = cur[l];
+        float *o0 = (c0 == lv[l].a) ? lv[l].b : lv[l].a;
+        sm_axis<2>(m, mc, mc, mc, 2, v.pidx[l], v.pw[l], 1.f, zc, nullptr, tmp2);
+        __syncthreads();
+        sm_axis<2>(m, m, mc, mc, 1, v.pidx[l], v.pw[l], 1.f, tmp2, nullptr, tmp1);
+        __syncthreads();
+        sm_axis<2>(m, m, m, mc, 0, v.pidx[l], v.pw[l], 1.f, tmp1, c0, o0);
+        __syncthreads();
+        {
+            float *t = c0;
+            c0 = o0;
+            o0 = t;
+        }
+        for (int s = 0; s < v.nu2; s++) {
+            sm_jacobi(m, v.wD[l], v.c[l], v.omw, lv[l].r, c0, o0);
+            __syncthreads();
+            float *t = c0;
+            c0 = o0;
+            o0 = t;
+        }
+        zc = c0;
+    }
+    {
+        const int n0 = v.m[0] * v.m[0] * v.m[0];
+        for (int p = threadIdx.x; p < n0; p += blockDim.x) zout[(size_t)p * N + col] = zc[p];
+    }
+}
+
+}  // namespace
+
+size_t vcoarse_smem_bytes(const VCoarse &v) {
+    size_t f = 0;
+    for (int l = 0; l < v.levels; l++) f += 3 * (size_t)v.m[l] * v.m[l] * v.m[l];
+    if (v.levels > 1) f += (size_t)v.m[0] * v.m[0] * v.m[1] + (size_t)v.m[0] * v.m[1] * v.m[1];
+    return f * sizeof(float);
+}
+
+void vcoarse_prepare() {
+    cudaFuncSetAttribute(k_vcoarse, cudaFuncAttributeMaxDynamicSharedMemorySize, VC_MAX_SMEM);
+}
+
+void launch_vcoarse(const VCoarse &v, int N, const float *r, float *z, cudaStream_t s) {
+    const size_t bytes = vcoarse_smem_bytes(v);
+    HQ_LAUNCH_W(HQ_K_COARSE, (double)v.m[0] * v.m[0] * v.m[0] * N,
+                k_vcoarse<<<N, VC_THREADS, bytes, s>>>(v, N, r, z));
+}
+
+}  // namespace hq

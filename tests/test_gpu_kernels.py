@@ -326,4 +326,10 @@ def test_fused_coarse_vcycle_matches_separate_kernels(m, N, prec, monkeypatch):
     (zf, uf, lf), (zs, us, ls) = outs
     np.testing.assert_array_equal(zf, zs)
     np.testing.assert_array_equal(uf, us)
-    assert sum(v[0] for v in lf.values()) < sum(v[0] for v in ls.values())
+    # the steps' V-cycles fuse below the finest level (mixed: the finest sweep
+    # forms the PCG's dot products) once there are three levels or more
+    nl, nf = sum(v[0] for v in ls.values()), sum(v[0] for v in lf.values())
+    if len(s.levels()) >= 3:
+        assert nf < nl, (nf, nl)
+    else:
+        assert nf == nl
