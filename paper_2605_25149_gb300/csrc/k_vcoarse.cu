@@ -21,7 +21,7 @@ namespace hq {
 
 namespace {
 
-constexpr int VC_THREADS = 512;
+constexpr int VC_THREADS = 1024;
 
 // sum of the six neighbours of point p = i + m (j + m k) in one column stored
 // contiguously (zero outside the grid), grouped as nbr_sum groups them
@@ -42,37 +42,37 @@ __device__ __forceinline__ void decomp(int p, int m, int &i, int &j, int &k) {
 }
 
 // z = wD r (the first sweep from zero)
-__device__ void sm_first(int m, const float *__restrict__ wD, const float *r, float *z) {
+__device__ void sm_first(int m, const float *wD, const float *r, float *z) {
     const int n = m * m * m;
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        const float w = __ldg(wD + p);
+        const float w = wD[p];
         z[p] = w * r[p];
     }
 }
 
 // zout = (1 - omega) zin + wD (r + c nbrsum(zin))
-__device__ void sm_jacobi(int m, const float *__restrict__ wD, float c, float omw, const float *r,
+__device__ void sm_jacobi(int m, const float *wD, float c, float omw, const float *r,
                           const float *zin, float *zout) {
     const int n = m * m * m;
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
         int i, j, k;
         decomp(p, m, i, j, k);
         const float s = nbr6(zin, p, i, j, k, m);
-        const float w = __ldg(wD + p);
+        const float w = wD[p];
         const float zc = zin[p], rv = r[p];
         zout[p] = omw * zc + w * (rv + c * s);
     }
 }
 
 // y = (b - D x) + c nbrsum(x)
-__device__ void sm_resid(int m, const float *__restrict__ D, float c, const float *x, const float *b,
+__device__ void sm_resid(int m, const float *D, float c, const float *x, const float *b,
                          float *y) {
     const int n = m * m * m;
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
         int i, j, k;
         decomp(p, m, i, j, k);
         const float s = nbr6(x, p, i, j, k, m);
-        const float d = __ldg(D + p);
+        const float d = D[p];
         const float xc = x[p], bb = b[p];
         y[p] = (bb - d * xc) + c * s;
     }
@@ -83,9 +83,8 @@ __device__ void sm_resid(int m, const float *__restrict__ D, float c, const floa
 // index o along the axis takes taps idx[o NT + t] (-1 = none) with weights
 // w[o NT + t]; out = scale sum (no add) or add + sum (scale = 1)
 template <int NT>
-__device__ void sm_axis(int o2, int o1, int o0, int ilen, int axis, const int *__restrict__ idx,
-                        const float *__restrict__ w, float scale, const float *in, const float *add,
-                        float *out) {
+__device__ void sm_axis(int o2, int o1, int o0, int ilen, int axis, const int *idx, const float *w,
+                        float scale, const float *in, const float *add, float *out) {
     const int nout = o2 * o1 * o0;
     const int d0 = axis == 0 ? ilen : o0;
     const int d1 = axis == 1 ? ilen : o1;
@@ -103,8 +102,8 @@ __device__ void sm_axis(int o2, int o1, int o0, int ilen, int axis, const int *_
         float wt[NT], a[NT];
 #pragma unroll
         for (int t = 0; t < NT; t++) {
-            ii[t] = __ldg(idx + oa * NT + t);
-            wt[t] = __ldg(w + oa * NT + t);
+            ii[t] = idx[oa * NT + t];
+            wt[t] = w[oa * NT + t];
             a[t] = ii[t] >= 0 ? in[ib + ii[t] * sa] : 0.f;
         }
         float e = 0.f;
@@ -120,18 +119,36 @@ __device__ void sm_axis(int o2, int o1, int o0, int ilen, int axis, const int *_
 }
 
 // z = Ainv r on the coarsest level: per point, eight FP64 partial sums over
-// the terms qq = y, y + 8, ... (y = 0..7), added in y order (the grouping of
-// k_coarse_solve), rounded to FP32
-__device__ void sm_coarse(int nc, const double *__restrict__ Ainv, const float *r, float *z) {
+// the terms qq = y, y + 8, ... (y = 0..7; one thread each), added in y order
+// (the grouping of k_coarse_solve), rounded to FP32; part: 8 nc doubles
+__device__ void sm_coarse(int nc, const double *__restrict__ Ainv, const float *r, float *z,
+                          double *part) {
+    for (int t = threadIdx.x; t < 8 * nc; t += blockDim.x) {
+        const int p = t >> 3, y = t & 7;
+        double acc = 0.0;
+        for (int qq = y; qq < nc; qq += 8) acc += __ldg(Ainv + (size_t)p * nc + qq) * (double)r[qq];
+        part[t] = acc;
+    }
+    __syncthreads();
     for (int p = threadIdx.x; p < nc; p += blockDim.x) {
         double s = 0.0;
-        for (int y = 0; y < 8; y++) {
-            double acc = 0.0;
-            for (int qq = y; qq < nc; qq += 8) acc += __ldg(Ainv + (size_t)p * nc + qq) * (double)r[qq];
-            s += acc;
-        }
+        for (int y = 0; y < 8; y++) s += part[p * 8 + y];
         z[p] = (float)s;
     }
+}
+
+// shared-memory layout of one column (floats unless stated): per level l the
+// right-hand side r, two iterates a, b (3 n_l), then per level D and wD
+// (2 n_l), the transfer temporaries (m0^2 m1 + m0 m1^2), per level pair the
+// restriction taps (ridx: 6 m_{l+1} ints, rw: 6 m_{l+1}) and prolongation
+// taps (pidx: 2 m_l ints, pw: 2 m_l), padding to 8 bytes, and 8 nc doubles of
+// coarse-solve partials
+__host__ __device__ inline size_t vc_floats(const VCoarse &v) {
+    size_t f = 0;
+    for (int l = 0; l < v.levels; l++) f += 5 * (size_t)v.m[l] * v.m[l] * v.m[l];
+    if (v.levels > 1) f += (size_t)v.m[0] * v.m[0] * v.m[1] + (size_t)v.m[0] * v.m[1] * v.m[1];
+    for (int l = 0; l + 1 < v.levels; l++) f += 12 * (size_t)v.m[l + 1] + 4 * (size_t)v.m[l];
+    return (f + 1) & ~(size_t)1;
 }
 
 struct LevelSmem {
@@ -144,6 +161,9 @@ __global__ void __launch_bounds__(VC_THREADS) k_vcoarse(VCoarse v, int N, const 
     const int col = blockIdx.x;
     const int Lf = v.levels;   // levels in this launch: l0 .. l0 + Lf - 1 (last = coarsest)
     LevelSmem lv[VC_MAXLEV];
+    const float *Ds[VC_MAXLEV], *wDs[VC_MAXLEV];
+    const int *rid[VC_MAXLEV], *pid[VC_MAXLEV];
+    const float *rws[VC_MAXLEV], *pws[VC_MAXLEV];
     float *q = vsm;
     for (int l = 0; l < Lf; l++) {
         const int n = v.m[l] * v.m[l] * v.m[l];
@@ -152,8 +172,41 @@ __global__ void __launch_bounds__(VC_THREADS) k_vcoarse(VCoarse v, int N, const 
         lv[l].b = q + 2 * n;
         q += 3 * n;
     }
+    for (int l = 0; l < Lf; l++) {
+        const int n = v.m[l] * v.m[l] * v.m[l];
+        float *d = q, *w = q + n;
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+            d[p] = __ldg(v.D[l] + p);
+            w[p] = __ldg(v.wD[l] + p);
+        }
+        Ds[l] = d;
+        wDs[l] = w;
+        q += 2 * n;
+    }
     float *tmp1 = q;
     float *tmp2 = q + (Lf > 1 ? v.m[0] * v.m[0] * v.m[1] : 0);
+    q = tmp2 + (Lf > 1 ? v.m[0] * v.m[1] * v.m[1] : 0);
+    for (int l = 0; l + 1 < Lf; l++) {
+        const int mf = v.m[l], mc = v.m[l + 1];
+        int *ri = reinterpret_cast<int *>(q);
+        float *rw = q + XFER_RTAPS * mc;
+        int *pi = reinterpret_cast<int *>(q + 2 * XFER_RTAPS * mc);
+        float *pw = q + 2 * XFER_RTAPS * mc + 2 * mf;
+        for (int t = threadIdx.x; t < XFER_RTAPS * mc; t += blockDim.x) {
+            ri[t] = __ldg(v.ridx[l] + t);
+            rw[t] = __ldg(v.rw[l] + t);
+        }
+        for (int t = threadIdx.x; t < 2 * mf; t += blockDim.x) {
+            pi[t] = __ldg(v.pidx[l] + t);
+            pw[t] = __ldg(v.pw[l] + t);
+        }
+        rid[l] = ri;
+        rws[l] = rw;
+        pid[l] = pi;
+        pws[l] = pw;
+        q += 2 * XFER_RTAPS * mc + 4 * mf;
+    }
+    double *cpart = reinterpret_cast<double *>(vsm + vc_floats(v));
     // right-hand side of level l0 (column `col` of a point-major n0 x N block)
     {
         const int n0 = v.m[0] * v.m[0] * v.m[0];
@@ -165,28 +218,28 @@ __global__ void __launch_bounds__(VC_THREADS) k_vcoarse(VCoarse v, int N, const 
     for (int l = 0; l + 1 < Lf; l++) {
         const int m = v.m[l], mc = v.m[l + 1];
         float *c0 = lv[l].a, *o0 = lv[l].b;
-        sm_first(m, v.wD[l], lv[l].r, c0);
+        sm_first(m, wDs[l], lv[l].r, c0);
         __syncthreads();
         for (int s = 1; s < v.nu1; s++) {
-            sm_jacobi(m, v.wD[l], v.c[l], v.omw, lv[l].r, c0, o0);
+            sm_jacobi(m, wDs[l], v.c[l], v.omw, lv[l].r, c0, o0);
             __syncthreads();
             float *t = c0;
             c0 = o0;
             o0 = t;
         }
-        sm_resid(m, v.D[l], v.c[l], c0, lv[l].r, o0);
+        sm_resid(m, Ds[l], v.c[l], c0, lv[l].r, o0);
         __syncthreads();
-        sm_axis<XFER_RTAPS>(m, m, mc, m, 0, v.ridx[l], v.rw[l], 1.f, o0, nullptr, tmp1);
+        sm_axis<XFER_RTAPS>(m, m, mc, m, 0, rid[l], rws[l], 1.f, o0, nullptr, tmp1);
         __syncthreads();
-        sm_axis<XFER_RTAPS>(m, mc, mc, m, 1, v.ridx[l], v.rw[l], 1.f, tmp1, nullptr, tmp2);
+        sm_axis<XFER_RTAPS>(m, mc, mc, m, 1, rid[l], rws[l], 1.f, tmp1, nullptr, tmp2);
         __syncthreads();
-        sm_axis<XFER_RTAPS>(mc, mc, mc, m, 2, v.ridx[l], v.rw[l], v.rscale[l], tmp2, nullptr,
+        sm_axis<XFER_RTAPS>(mc, mc, mc, m, 2, rid[l], rws[l], v.rscale[l], tmp2, nullptr,
                             lv[l + 1].r);
         __syncthreads();
         cur[l] = c0;
     }
     // coarsest solve
-    sm_coarse(v.nc, v.Ainv, lv[Lf - 1].r, lv[Lf - 1].a);
+    sm_coarse(v.nc, v.Ainv, lv[Lf - 1].r, lv[Lf - 1].a, cpart);
     __syncthreads();
     float *zc = lv[Lf - 1].a;   // the finished correction of the level below
     // up: prolongation added to the pre-smoothed iterate, post-smoothing
@@ -194,11 +247,11 @@ __global__ void __launch_bounds__(VC_THREADS) k_vcoarse(VCoarse v, int N, const 
         const int m = v.m[l], mc = v.m[l + 1];
         float *c0 = cur[l];
         float *o0 = (c0 == lv[l].a) ? lv[l].b : lv[l].a;
-        sm_axis<2>(m, mc, mc, mc, 2, v.pidx[l], v.pw[l], 1.f, zc, nullptr, tmp2);
+        sm_axis<2>(m, mc, mc, mc, 2, pid[l], pws[l], 1.f, zc, nullptr, tmp2);
         __syncthreads();
-        sm_axis<2>(m, m, mc, mc, 1, v.pidx[l], v.pw[l], 1.f, tmp2, nullptr, tmp1);
+        sm_axis<2>(m, m, mc, mc, 1, pid[l], pws[l], 1.f, tmp2, nullptr, tmp1);
         __syncthreads();
-        sm_axis<2>(m, m, m, mc, 0, v.pidx[l], v.pw[l], 1.f, tmp1, c0, o0);
+        sm_axis<2>(m, m, m, mc, 0, pid[l], pws[l], 1.f, tmp1, c0, o0);
         __syncthreads();
         {
             float *t = c0;
@@ -206,7 +259,7 @@ __global__ void __launch_bounds__(VC_THREADS) k_vcoarse(VCoarse v, int N, const 
             o0 = t;
         }
         for (int s = 0; s < v.nu2; s++) {
-            sm_jacobi(m, v.wD[l], v.c[l], v.omw, lv[l].r, c0, o0);
+            sm_jacobi(m, wDs[l], v.c[l], v.omw, lv[l].r, c0, o0);
             __syncthreads();
             float *t = c0;
             c0 = o0;
@@ -223,10 +276,7 @@ __global__ void __launch_bounds__(VC_THREADS) k_vcoarse(VCoarse v, int N, const 
 }  // namespace
 
 size_t vcoarse_smem_bytes(const VCoarse &v) {
-    size_t f = 0;
-    for (int l = 0; l < v.levels; l++) f += 3 * (size_t)v.m[l] * v.m[l] * v.m[l];
-    if (v.levels > 1) f += (size_t)v.m[0] * v.m[0] * v.m[1] + (size_t)v.m[0] * v.m[1] * v.m[1];
-    return f * sizeof(float);
+    return vc_floats(v) * sizeof(float) + 8 * sizeof(double) * (size_t)v.nc;
 }
 
 void vcoarse_prepare() {

@@ -303,8 +303,8 @@ def test_fused_coarse_vcycle_matches_separate_kernels(m, N, prec, monkeypatch):
     every level from about 16^3 points down in shared memory) against the
     same V-cycle as separate kernels (HQ_FUSED_COARSE=0): each operation
     repeats its separate kernel's expression, so the V-cycle and three steps
-    of the scheme agree bit for bit.  Cases: the whole V-cycle fused (m <= 20),
-    fused from level 1 (33, 48), FP64 contexts with the FP32 preconditioner."""
+    of the scheme agree bit for bit.  Cases: the whole V-cycle fused (m <= 16),
+    fused from level 1 (20, 33, 48), FP64 contexts with the FP32 preconditioner."""
     torch_mod()
     kw = dict(precision="mixed", cg_rtol=1e-6) if prec == "mixed" else dict(mg_fp32=1)
     outs = []
