@@ -56,7 +56,8 @@ FP64_OPS = {"smooth": 7.0, "stencil": 8.0, "residual": 7.0}
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch / point-columns
 # of that launch): keys (class, dtype); an entry is removed whenever its
 # kernel changes, until it is captured again.
-TRAFFIC_PER_ELEMENT = {("smooth", "f32"): (136.215040e6 + 44.029440e6) / 16777216}
+TRAFFIC_PER_ELEMENT = {("smooth", "f32"): (136.215040e6 + 44.029440e6) / 16777216,
+                       ("stencil", "f64"): (136.483584e6 + 96.978432e6) / 16777216}
 
 
 def peaks():
@@ -665,6 +666,79 @@ def ttr_live(torch, hq, inputs, args):
     return out
 
 
+def bench_grad(torch, hq, inputs, n_fd=4):
+    """The differentiation workload (64^3, N = 32, wells default_rng(5), FP64):
+    converged eigenpairs (mixed scheme to g < 1e-4, then FP64 residual
+    refinement to g < 1e-10 in an FP64 context), the target density of a second
+    potential (default_rng(6)) the same way, then timed: d(sum lambda)/dV
+    (hq_grad_eigs) and the adjoint of the density loss (hq_grad_density, rtol
+    1e-11).  Central finite differences (h = 1e-6) of the refined eigenpairs of
+    V +- h e_p at the first n_fd of the 20 points drawn by default_rng(505)
+    check both gradients."""
+    import numpy as np
+    V, U0, w = inputs.workload("wells64_N32")
+    m, N = w["m"], w["N"]
+    h3 = inputs.grid_h(m) ** 3
+
+    def converged(Vx, U0x):
+        sm = hq.Solver(m, N, tau=0.4, cg_rtol=1e-6, precision="mixed", adaptive_tau=1, tau_max=10.0)
+        sm.set_potential(Vx)
+        sm.set_initial(U0x)
+        sm.solve(1e-4, 60000)
+        U, st = sm.state_device()
+        s = hq.Solver(m, N, tau=0.4, cg_rtol=1e-10, mg_fp32=1)
+        s.set_potential(Vx)
+        s.set_state_device(U, st)
+        refine_to(torch, s, 1e-10, rtol=1e-8, maxit=2000)
+        return s
+
+    t0 = time.perf_counter()
+    s = converged(V, U0)
+    s6 = converged(inputs.wells(m, 6), inputs.initial_block(m, N, 106))
+    rho_t = s6.density()
+    del s6
+    torch.cuda.synchronize()
+    t_conv = time.perf_counter() - t0
+    Ud, st = s.state_device()
+    _, g = s.solve(1e-10, 0, raise_on_unconverged=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ge = s.grad_eigs()
+    torch.cuda.synchronize()
+    t_eigs = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    dV, L, its = s.grad_density(rho_target=rho_t, rtol=1e-11, maxit=4000)
+    torch.cuda.synchronize()
+    t_dens = time.perf_counter() - t0
+    f = hq.Solver(m, N, tau=0.4, cg_rtol=1e-10, mg_fp32=1)
+    pts = np.random.default_rng(505).choice(m ** 3, 20, replace=False)[:n_fd]
+    err_s, err_l = [], []
+    for p in pts:
+        vals = []
+        for sgn in (1.0, -1.0):
+            Vx = V.copy()
+            Vx[p] += sgn * 1e-6
+            f.set_potential(Vx)
+            f.set_state_device(Ud, st)
+            f.refine(rounds=2, rtol=1e-12, maxit=4000)
+            rho = f.density()
+            vals.append((np.sum(f.eigenpairs()["lam_rr"]), 0.5 * h3 * np.sum((rho - rho_t) ** 2)))
+        fs = (vals[0][0] - vals[1][0]) / 2e-6
+        fl = (vals[0][1] - vals[1][1]) / 2e-6
+        err_s.append(abs(ge[p] - fs) / max(abs(fs), 1e-300))
+        err_l.append(abs(dV[p] - fl) / max(abs(fl), 1e-300))
+    return {"workload": "wells64_N32: 64^3 grid, V=|x|^2/2 + 8 wells (default_rng(5)), N=32, FP64",
+            "g_converged": g, "converge_s": t_conv,
+            "grad_eigs_s": t_eigs, "grad_density_s": t_dens, "grad_density_pcg_iterations": its,
+            "loss": L, "fd_points": int(len(pts)),
+            "fd_rel_err_grad_eigs_max": float(max(err_s)),
+            "fd_rel_err_grad_density_max": float(max(err_l)),
+            "how": "converged eigenpairs: mixed scheme to g < 1e-4, FP64 refinement to g < "
+                   "1e-10; gradients timed with synchronisation on both sides; finite "
+                   "differences h = 1e-6 of refined eigenpairs (all 20 points: "
+                   "tests/test_gpu_adjoint_fullsize.py)"}
+
+
 def run_hq(args):
     import numpy as np
     import torch
@@ -797,6 +871,12 @@ def run_hq(args):
         batched = bench_batched(torch, hq, inputs, max(1, min(K, 3)), max(1, min(W, 1)),
                                 tune=not args.no_tune)
 
+    # ---- differentiation workload (64^3, N = 32) ------------------------------
+    grad = None
+    if not args.no_grad:
+        grad = bench_grad(torch, hq, inputs)
+        torch.cuda.empty_cache()
+
     # ---- CPU oracle on the host cores (rank 0, N = 1) ------------------------
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
@@ -831,6 +911,7 @@ def run_hq(args):
         "fp64_fp64_vcycle": v64,
         "large": large,
         "batched": batched,
+        "differentiation": grad,
         "cpu_baseline": cpu,
         "gradient_norm_last": g,
     }
@@ -937,6 +1018,7 @@ def main():
                          "the FP64 residual refinement")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
+    ap.add_argument("--no-grad", action="store_true", help="skip the differentiation workload")
     ap.add_argument("--no-large", action="store_true", help="skip the 128^3, N = 256 workload")
     ap.add_argument("--large-shape", type=int, nargs=2, default=[128, 256], metavar=("M", "N"),
                     help="grid side and block width of the large mixed workload")
@@ -956,7 +1038,7 @@ def main():
         ap.error("--gpus %d but WORLD_SIZE=%d" % (args.gpus, ws))
     if ws > 1:
         # replicas: the timed headline step only (the other legs hold every GPU for minutes)
-        args.no_ttr = args.no_mixed = args.no_large = args.no_batch = True
+        args.no_ttr = args.no_mixed = args.no_large = args.no_batch = args.no_grad = True
     if args.impl == "reference":
         run_reference(args)
     elif args.ttr:
