@@ -582,7 +582,9 @@ def ttr_live(torch, hq, inputs, args):
     mixed_refined: the mixed-precision scheme until g < g_hand, the state
       handed device to device to an FP64 context (FP32 multigrid
       preconditioner), then FP64 residual refinement rounds (hq_refine) until
-      g < 1e-8.  The refined eigenvalues are the FP64 reference of this run.
+      g < 1e-8 (a hand-over whose refinement breaks down continues the scheme
+      to a 3x lower g first; that time counts).  The refined eigenvalues are
+      the FP64 reference of this run.
     mixed_to_err: the mixed scheme continued from the hand-over state until
       its own Rayleigh-Ritz eigenvalues are within 1e-6 of the reference (the
       mixed form's stated accuracy), in chunks of 500 steps.
@@ -610,22 +612,35 @@ def ttr_live(torch, hq, inputs, args):
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push(label)
         t0 = time.perf_counter()
-        e0.record(s.stream)
-        n1, g1 = s.solve(g_hand, 60000)
-        e1.record(s.stream)
-        U, st = s.state_device()
-        s64.set_state_device(U, st)
-        t_hand = time.perf_counter()
-        rounds, its, g = refine_to(torch, s64, eps)
+        n1, scheme_s, failed = 0, 0.0, []
+        # hand over at g_hand; if the refinement's inner solve breaks down (the
+        # Ritz values not yet below the rest of the spectrum), continue the
+        # scheme to a 3x lower g and hand over again (all time counted)
+        for tgt in (g_hand, g_hand / 3, g_hand / 10, g_hand / 30):
+            e0.record(s.stream)
+            n, g1 = s.solve(tgt, 60000)
+            e1.record(s.stream)
+            e1.synchronize()
+            n1 += n
+            scheme_s += e0.elapsed_time(e1) / 1e3
+            U, st = s.state_device()
+            s64.set_state_device(U, st)
+            t_hand = time.perf_counter()
+            try:
+                rounds, its, g = refine_to(torch, s64, eps)
+                break
+            except hq.HQError as err:
+                if err.status not in (5, 7):   # breakdown / not converged
+                    raise
+                failed.append({"g_at_handoff": g1, "status": err.status})
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         torch.cuda.nvtx.range_pop()
-        scheme_s = e0.elapsed_time(e1) / 1e3
         return s, s64, {"value": t1 - t0, "unit": "s", "how": "measured", "scheme_steps": n1,
                         "scheme_s": scheme_s, "scheme_ms_per_step": 1e3 * scheme_s / max(n1, 1),
                         "g_at_handoff": g1, "handoff_and_refine_s": t1 - t_hand,
                         "refine_rounds": rounds, "refine_pcg_iterations": its, "g": g,
-                        "converged": bool(g < eps)}
+                        "converged": bool(g < eps), "failed_handoffs": failed}
 
     sm, sr, res_m = leg(dict(precision="mixed", cg_rtol=args.mixed_rtol), "ttr_mixed")
     lam_ref = sr.eigenpairs()["lam_rr"]
@@ -666,7 +681,7 @@ def ttr_live(torch, hq, inputs, args):
     return out
 
 
-def bench_grad(torch, hq, inputs, n_fd=4):
+def bench_grad(torch, hq, inputs, n_fd=6):
     """The differentiation workload (64^3, N = 32, wells default_rng(5), FP64):
     converged eigenpairs (mixed scheme to g < 1e-4, then FP64 residual
     refinement to g < 1e-10 in an FP64 context), the target density of a second
@@ -712,7 +727,7 @@ def bench_grad(torch, hq, inputs, n_fd=4):
     t_dens = time.perf_counter() - t0
     f = hq.Solver(m, N, tau=0.4, cg_rtol=1e-10, mg_fp32=1)
     pts = np.random.default_rng(505).choice(m ** 3, 20, replace=False)[:n_fd]
-    err_s, err_l = [], []
+    fds, fdl = [], []
     for p in pts:
         vals = []
         for sgn in (1.0, -1.0):
@@ -723,16 +738,26 @@ def bench_grad(torch, hq, inputs, n_fd=4):
             f.refine(rounds=2, rtol=1e-12, maxit=4000)
             rho = f.density()
             vals.append((np.sum(f.eigenpairs()["lam_rr"]), 0.5 * h3 * np.sum((rho - rho_t) ** 2)))
-        fs = (vals[0][0] - vals[1][0]) / 2e-6
-        fl = (vals[0][1] - vals[1][1]) / 2e-6
-        err_s.append(abs(ge[p] - fs) / max(abs(fs), 1e-300))
-        err_l.append(abs(dV[p] - fl) / max(abs(fl), 1e-300))
+        fds.append((vals[0][0] - vals[1][0]) / 2e-6)
+        fdl.append((vals[0][1] - vals[1][1]) / 2e-6)
+    fds, fdl = np.array(fds), np.array(fdl)
+
+    def errs(g_all, fd):
+        # max |g - fd| over the points, relative to the gradient's largest
+        # entry, and the largest relative error where |g| > 1e-3 max |g|
+        scale = float(np.abs(g_all).max())
+        gp = g_all[pts]
+        big = np.abs(gp) > 1e-3 * scale
+        rel = float(np.max(np.abs(gp - fd)[big] / np.abs(gp)[big])) if big.any() else None
+        return float(np.abs(gp - fd).max() / scale), rel
     return {"workload": "wells64_N32: 64^3 grid, V=|x|^2/2 + 8 wells (default_rng(5)), N=32, FP64",
             "g_converged": g, "converge_s": t_conv,
             "grad_eigs_s": t_eigs, "grad_density_s": t_dens, "grad_density_pcg_iterations": its,
             "loss": L, "fd_points": int(len(pts)),
-            "fd_rel_err_grad_eigs_max": float(max(err_s)),
-            "fd_rel_err_grad_density_max": float(max(err_l)),
+            "fd_err_grad_eigs": dict(zip(("max_abs_over_max_grad", "max_rel_where_large"),
+                                         errs(ge, fds))),
+            "fd_err_grad_density": dict(zip(("max_abs_over_max_grad", "max_rel_where_large"),
+                                            errs(dV, fdl))),
             "how": "converged eigenpairs: mixed scheme to g < 1e-4, FP64 refinement to g < "
                    "1e-10; gradients timed with synchronisation on both sides; finite "
                    "differences h = 1e-6 of refined eigenpairs (all 20 points: "
@@ -1013,7 +1038,7 @@ def main():
     ap.add_argument("--ttr-steps", type=int, default=40000, help="step cap of each --ttr leg")
     ap.add_argument("--ttr-chunk", type=int, default=250)
     ap.add_argument("--tau-max", type=float, default=10.0)
-    ap.add_argument("--ttr-handoff", type=float, default=1e-4,
+    ap.add_argument("--ttr-handoff", type=float, default=3e-4,
                     help="g at which the time-to-residual legs hand the scheme's state to "
                          "the FP64 residual refinement")
     ap.add_argument("--no-mixed", action="store_true")

@@ -102,8 +102,11 @@ struct hq_ctx {
     bool mg32 = false;
     // FP64 V-cycle smoothing from the pre-scaled right-hand side (Level::rt)
     bool rtilde = false;
-    // FP32 V-cycles: levels fuse_l0 .. L-1 run as one launch (k_vcoarse); -1: off
+    // FP32 V-cycles: levels fuse_l0 .. L-1 run as one launch (k_vcoarse); -1: off.
+    // no_fuse: set while a batch graph of several problems is captured (their
+    // separate small kernels interleave better across concurrent problems)
     int fuse_l0 = -1;
+    bool no_fuse = false;
     float *R32 = nullptr, *Z32 = nullptr, *T32 = nullptr;
     // n x N blocks in the working precision
     void *U = nullptr, *W = nullptr, *Uh = nullptr, *Z = nullptr;
@@ -679,7 +682,8 @@ template <typename T>
 hq_status vcycle(hq_ctx *x, int l, const T *r, T *Zf, T *Tb, bool first_done, double *part_final) {
     LevelScope lvl_(l);
     if constexpr (std::is_same<T, float>::value) {
-        if (x->fuse_l0 >= 0 && l >= x->fuse_l0 && l + 1 < x->L && !first_done && !part_final) {
+        if (x->fuse_l0 >= 0 && !x->no_fuse && l >= x->fuse_l0 && l + 1 < x->L && !first_done &&
+            !part_final) {
             launch_vcoarse(make_vcoarse(x, l), x->N, r, Zf, x->st);
             return HQ_OK;
         }
@@ -1457,7 +1461,11 @@ hq_status batch_build(hq_batch *b) {
     hq_status st = HQ_OK;
     for (int k = 0; k < K && ok; k++) {
         hq_ctx *x = b->ctx[k];
+        // several concurrent problems: the coarse levels as separate kernels
+        // (the same values bit for bit, see k_vcoarse.cu)
+        x->no_fuse = K > 1;
         st = x->mixed ? capture_problem<float>(x, bodies[k]) : capture_problem<double>(x, bodies[k]);
+        x->no_fuse = false;
         if (st != HQ_OK) {
             ok = false;
             b->err = "problem " + std::to_string(k) + ": " + x->err;
