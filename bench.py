@@ -296,7 +296,7 @@ def ttr_small(torch, hq, inputs):
     against the separable closed form."""
     import numpy as np
     V, U0, w = inputs.workload("harmonic16_N8")
-    s = hq.Solver(w["m"], w["N"], tau=w["tau"], cg_rtol=w["cg_rtol"], precision="fp64")
+    s = hq.Solver(w["m"], w["N"], **solver_kw(w))
     s.set_potential(V)
     s.set_initial(U0)
     torch.cuda.synchronize()
@@ -307,7 +307,8 @@ def ttr_small(torch, hq, inputs):
     lam = s.eigenpairs()["lam_rr"]
     ref = fd_harmonic_levels(w["m"], w["N"])
     return {"value": el, "unit": "s", "steps": steps, "g": g, "eps": w["eps"], "how": "measured",
-            "workload": "harmonic16_N8: 16^3, V=|x|^2/2, N=8, tau=0.5, FP64",
+            "workload": "harmonic16_N8: 16^3, V=|x|^2/2, N=8, tau=0.5, FP64 block PCG with the "
+                        "FP32 multigrid preconditioner",
             "eig_rel_err_vs_closed_form": float(np.max(np.abs(lam - ref) / np.abs(ref)))}
 
 

@@ -107,6 +107,10 @@ struct hq_ctx {
     // separate small kernels interleave better across concurrent problems)
     int fuse_l0 = -1;
     bool no_fuse = false;
+    // whether level 0 of an FP32 V-cycle fits one launch, whatever
+    // HQ_FUSED_COARSE says (selects the FP64 <-> FP32 interface of mg_fp32,
+    // so the switch leaves every value unchanged)
+    bool level0_fits = false;
     float *R32 = nullptr, *Z32 = nullptr, *T32 = nullptr;
     // n x N blocks in the working precision
     void *U = nullptr, *W = nullptr, *Uh = nullptr, *Z = nullptr;
@@ -421,7 +425,11 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
     sc.status = cv.take<int>(sizeof(int) * 4);
     // partial rows: the working-precision geometry of the finest level, or the
     // FP64 geometry used by the FP64 extraction / monitoring kernels
-    const int gy0 = std::max(std::max(lev[0].g.gy, part_rows(lev[0].g)), make_geom(m, N, 8).gy);
+    int gy0 = std::max(std::max(lev[0].g.gy, part_rows(lev[0].g)), make_geom(m, N, 8).gy);
+    if (!mixed && c->mg_fp32) {
+        GridGeom g32 = make_geom(m, N, 4, c->grid_block, c->grid_ctas);
+        gy0 = std::max(gy0, std::max(g32.gy, part_rows(g32)));
+    }
     double *part = cv.take<double>(sizeof(double) * (size_t)gy0 * N);
     double *part2 = cv.take<double>(sizeof(double) * (size_t)gy0 * N);
     sc.fpart = cv.take<double>(sizeof(double) * 2 * (size_t)finalize_chunks(gy0) * N);
@@ -578,7 +586,8 @@ T *first_target(hq_ctx *x, int l, T *Zfinal, T *Tbuf) {
 }
 
 template <typename T>
-hq_status vcycle(hq_ctx *x, int l, const T *r, T *Zf, T *Tb, bool first_done, double *part_final);
+hq_status vcycle(hq_ctx *x, int l, const T *r, T *Zf, T *Tb, bool first_done, double *part_final,
+                 const double *r64dot = nullptr);
 
 // The FP64 V-cycle of level l with the smoothing sweeps from the pre-scaled
 // right-hand side rt = wD r (launch_jacobi_rt): the first sweep from zero is
@@ -667,9 +676,9 @@ VCoarse make_vcoarse(const hq_ctx *x, int l) {
 
 // first level from which the FP32 V-cycle fits one launch (-1: none), or -1
 // when HQ_FUSED_COARSE=0 (the multi-kernel V-cycle, for comparisons)
-int fuse_level(const hq_ctx *x) {
+int fuse_level(const hq_ctx *x, bool honour_switch = true) {
     const char *e = std::getenv("HQ_FUSED_COARSE");
-    if (e && e[0] == '0') return -1;
+    if (honour_switch && e && e[0] == '0') return -1;
     if (!x->mixed && !x->mg32) return -1;
     for (int l = 0; l + 1 < x->L; l++) {
         if (x->L - l > VC_MAXLEV) continue;
@@ -678,8 +687,11 @@ int fuse_level(const hq_ctx *x) {
     return -1;
 }
 
+// r64dot (FP32 V-cycle of an FP64 PCG, level 0, linear point order only):
+// the last sweep forms part_final as the FP64 partials of r64dot . z
 template <typename T>
-hq_status vcycle(hq_ctx *x, int l, const T *r, T *Zf, T *Tb, bool first_done, double *part_final) {
+hq_status vcycle(hq_ctx *x, int l, const T *r, T *Zf, T *Tb, bool first_done, double *part_final,
+                 const double *r64dot) {
     LevelScope lvl_(l);
     if constexpr (std::is_same<T, float>::value) {
         if (x->fuse_l0 >= 0 && !x->no_fuse && l >= x->fuse_l0 && l + 1 < x->L && !first_done &&
@@ -714,6 +726,14 @@ hq_status vcycle(hq_ctx *x, int l, const T *r, T *Zf, T *Tb, bool first_done, do
     std::swap(cur, oth);
     for (int s = 0; s < x->cfg.mg_nu2; s++) {
         bool last = (s == x->cfg.mg_nu2 - 1);
+        if constexpr (std::is_same<T, float>::value) {
+            if (last && part_final && r64dot) {
+                launch_jacobi_dot64(v.g, (const float *)v.wDt, c, omw, r, r64dot, cur, oth,
+                                    part_final, x->st);
+                std::swap(cur, oth);
+                continue;
+            }
+        }
         launch_jacobi<T>(v.g, (const T *)v.Dt, (const T *)v.wDt, c, omw, r, cur, oth,
                          last ? part_final : nullptr, x->st);
         std::swap(cur, oth);
@@ -744,9 +764,30 @@ hq_status precondition(hq_ctx *x, const T *r, T *z, T *tbuf, bool first_done, do
 // V-cycle runs on the PCG's own buffers (more than one level, same precision)
 bool fuse_first_sweep(hq_ctx *x) { return x->L > 1 && !x->mg32; }
 
+// FP64 block PCG with an FP32 V-cycle whose finest level runs as separate
+// kernels in linear point order: the FP64 <-> FP32 interface is fused into the
+// PCG's passes (k_pcg_xr_mg writes r32 and the first sweep, the last sweep
+// forms r.z in FP64, k_pcg_p_mg reads z in FP32) instead of k_d2f,
+// k_jacobi_first and k_widen_dot
+bool mgf(const hq_ctx *x) {
+    return x->mg32 && x->L > 1 && !x->level0_fits && x->mg[0].g.zch == 0;
+}
+
 // rows of the r.z partials precondition() leaves: the last smoothing sweep
-// of the finest level, or the FP64 widening kernel of an FP32 V-cycle
-int prec_rows(hq_ctx *x) { return x->mg32 ? x->lev[0].g.gy : part_rows(x->lev[0].g); }
+// of the finest level, or the FP64 widening kernel of an FP32 V-cycle, or the
+// fused FP32 sweep
+int prec_rows(hq_ctx *x) {
+    if (mgf(x)) return x->mg[0].g.gy;
+    return x->mg32 ? x->lev[0].g.gy : part_rows(x->lev[0].g);
+}
+
+// the block PCG's preconditioner in mgf contexts: z (FP32, in Z32) = M r with
+// r32 written here (first_done false) or by k_pcg_xr_mg together with the
+// first sweep (first_done true); part: the FP64 partials of r.z
+hq_status precondition_mgf(hq_ctx *x, const double *r, bool first_done, double *part) {
+    if (!first_done) launch_convert_d2f((size_t)x->n * x->N, r, x->R32, x->st);
+    return vcycle<float>(x, 0, x->R32, x->Z32, x->T32, first_done, part, r);
+}
 
 // ---------------------------------------------------------------------------
 // block PCG: X = G B, per-column stopping ||r_j|| <= rtol ||b_j||
@@ -762,6 +803,25 @@ int prec_rows(hq_ctx *x) { return x->mg32 ? x->lev[0].g.gy : part_rows(x->lev[0]
 // a whole solve costs two host round trips.  With per-launch event timing on,
 // the same body is launched from the host instead.
 // ---------------------------------------------------------------------------
+// PCG start: z = M r, rz = r.z, p = z
+template <typename T>
+hq_status pcg_first_direction(hq_ctx *x, double rtol) {
+    const int N = x->N;
+    T *R = (T *)x->R, *Zp = (T *)x->Zp, *P = (T *)x->P, *Tt = (T *)x->Tt;
+    PcgScalars sc = x->sc;
+    if constexpr (std::is_same<T, double>::value) {
+        if (mgf(x)) {
+            HQ_TRY(precondition_mgf(x, R, false, x->part));
+            launch_finalize(FIN_RZ, N, prec_rows(x), x->part, nullptr, sc, rtol, x->st);
+            launch_convert_f2d((size_t)x->n * N, x->Z32, P, x->st);
+            return HQ_OK;
+        }
+    }
+    HQ_TRY(precondition<T>(x, R, Zp, Tt, false, x->part));
+    launch_finalize(FIN_RZ, N, prec_rows(x), x->part, nullptr, sc, rtol, x->st);
+    return copy_blk<T>(x, P, Zp, (size_t)x->n * N);
+}
+
 template <typename T>
 hq_status pcg_body(hq_ctx *x, T *X, double rtol) {
     Level &v = x->lev[0];
@@ -769,6 +829,14 @@ hq_status pcg_body(hq_ctx *x, T *X, double rtol) {
     const int N = x->N;
     T *R = (T *)x->R, *Zp = (T *)x->Zp, *P = (T *)x->P, *Q = (T *)x->Q, *Tt = (T *)x->Tt;
     PcgScalars sc = x->sc;
+    if constexpr (std::is_same<T, double>::value) {
+        if (mgf(x)) {
+            HQ_TRY(precondition_mgf(x, R, true, x->part));
+            launch_finalize(FIN_BETA, N, prec_rows(x), x->part, nullptr, sc, rtol, x->st);
+            launch_pcg_p_mg(g, sc.beta, x->Z32, P, x->st);
+            return HQ_OK;
+        }
+    }
     HQ_TRY(precondition<T>(x, R, Zp, Tt, fuse_first_sweep(x), x->part));
     launch_finalize(FIN_BETA, N, prec_rows(x), x->part, nullptr, sc, rtol, x->st);
     launch_pcg_p<T>(g, sc.beta, Zp, P, x->st);
@@ -785,8 +853,17 @@ hq_status pcg_half(hq_ctx *x, T *X, double rtol) {
     T *zfirst = x->rtilde ? (T *)x->mg[0].rt : first_target<T>(x, 0, Zp, Tt);
     launch_apply<T>(g, (const T *)v.Dt, (T)v.c, P, Q, x->part, x->st);
     launch_finalize(FIN_ALPHA, N, part_rows(g), x->part, nullptr, sc, rtol, x->st);
-    launch_pcg_xr<T>(g, sc.alpha, P, Q, X, R, x->part, (const T *)v.wDt,
-                     fuse_first_sweep(x) ? zfirst : nullptr, x->st);
+    bool done = false;
+    if constexpr (std::is_same<T, double>::value) {
+        if (mgf(x)) {
+            launch_pcg_xr_mg(g, sc.alpha, P, Q, X, R, x->part, (const float *)x->mg[0].wDt,
+                             x->R32, first_target<float>(x, 0, x->Z32, x->T32), x->st);
+            done = true;
+        }
+    }
+    if (!done)
+        launch_pcg_xr<T>(g, sc.alpha, P, Q, X, R, x->part, (const T *)v.wDt,
+                         fuse_first_sweep(x) ? zfirst : nullptr, x->st);
     HQ_CUDA(cudaMemsetAsync(sc.num_active, 0, sizeof(int), x->st));
     launch_finalize(FIN_RR, N, g.gy, x->part, nullptr, sc, rtol, x->st);
     return HQ_OK;
@@ -879,9 +956,7 @@ hq_status pcg(hq_ctx *x, const T *B, T *X, double rtol, int maxit, int *iters_ho
     hq_status st = HQ_OK;
     long it_done = 0;
     if (nact > 0 && maxit > 0) {
-        HQ_TRY(precondition<T>(x, R, Zp, Tt, false, x->part));
-        launch_finalize(FIN_RZ, N, prec_rows(x), x->part, nullptr, sc, rtol, x->st);
-        HQ_TRY(copy_blk<T>(x, P, Zp, (size_t)x->n * N));
+        HQ_TRY(pcg_first_direction<T>(x, rtol));
         HQ_TRY(pcg_half<T>(x, X, rtol));   // iteration 1
         it_done = 1;
         HQ_CUDA(cudaMemcpyAsync(&nact, sc.num_active, sizeof(int), cudaMemcpyDeviceToHost, x->st));
@@ -1028,9 +1103,7 @@ hq_status pcg_device(hq_ctx *x, const T *B, T *X, double rtol, int maxit, StepGr
     HQ_CUDA(cudaMemsetAsync(sc.num_active, 0, 2 * sizeof(int), main));
     launch_resid<T>(g, (const T *)v.Dt, (T)v.c, X, B, R, x->part, x->part2, main);
     launch_finalize(FIN_BNORM_RNORM, N, part_rows(g), x->part, x->part2, sc, rtol, main);
-    HQ_TRY(precondition<T>(x, R, Zp, Tt, false, x->part));
-    launch_finalize(FIN_RZ, N, prec_rows(x), x->part, nullptr, sc, rtol, main);
-    HQ_TRY(copy_blk<T>(x, P, Zp, (size_t)x->n * N));
+    HQ_TRY(pcg_first_direction<T>(x, rtol));
     cudaGraph_t gmain;
     if (!capture_graph_of(main, &gmain)) return fail(x, HQ_ERR_CUDA, "capture state");
     cudaGraphConditionalHandle hw, hif;
@@ -2344,6 +2417,7 @@ hq_status hq_init(const hq_config *cfg, void *d_workspace, size_t bytes, void *c
     }
     carve(x, cfg, x->ws);
     x->fuse_l0 = fuse_level(x);
+    x->level0_fits = fuse_level(x, false) == 0;
     // the status words and counters start cleared
     cudaError_t e = cudaMemsetAsync(x->sc.status, 0, sizeof(int), x->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(x->status, 0, sizeof(int), x->st);

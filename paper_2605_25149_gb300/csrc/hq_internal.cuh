@@ -255,6 +255,21 @@ void launch_rowreduce(int mode, long n, int N, const double *u, const double *v,
 void launch_scale_rows(long n, int N, const double *g, const double *u, double *y, cudaStream_t s);
 void launch_shift_cols(long n, int N, const double *sft, const double *x, double *y,
                        cudaStream_t s);
+// An FP32 preconditioner inside an FP64 block PCG, its interface fused into
+// the PCG passes (g: the FP64 geometry of the finest level for the PCG
+// kernels, the FP32 one for the sweep):
+// x += alpha p, r -= alpha q, partial r.r, r32 = (float) r, z32 = wD32 r32
+void launch_pcg_xr_mg(const GridGeom &g, const double *alpha, const double *p, const double *q,
+                      double *x, double *r, double *part_rr, const float *wD32, float *r32,
+                      float *z32, cudaStream_t s);
+// the damped-Jacobi sweep of launch_jacobi<float> with the partial
+// r64 . (double) z_out per column (FP64), in g's partial rows (g.gy)
+void launch_jacobi_dot64(const GridGeom &g, const float *wD, float c, float omw, const float *r,
+                         const double *r64, const float *zin, float *zout, double *part,
+                         cudaStream_t s);
+// p = (double) z32 + beta p
+void launch_pcg_p_mg(const GridGeom &g, const double *beta, const float *z32, double *p,
+                     cudaStream_t s);
 // out = a x + b y over count FP64 values (out may alias x or y)
 void launch_axpby(size_t count, double a, const double *x, double b, const double *y, double *out,
                   cudaStream_t s);

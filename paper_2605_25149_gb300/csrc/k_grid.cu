@@ -1056,6 +1056,125 @@ __global__ void k_f2d(size_t count, const float *in, double *out) {
          i += (size_t)gridDim.x * blockDim.x)
         out[i] = (double)in[i];
 }
+// The interface of an FP32 preconditioner inside an FP64 block PCG, fused
+// into the PCG's own passes:
+// k_pcg_xr_mg: x += alpha p, r -= alpha q, partial r.r (all FP64, the
+// geometry of the FP64 level), and the V-cycle's entry: r32 = (float) r and
+// its first damped-Jacobi sweep from zero z32 = wD32 r32 -- the values
+// k_d2f and k_jacobi_first<float> would write.
+template <int V>
+__global__ void __launch_bounds__(256) k_pcg_xr_mg(long n, int N, int ppt,
+                                                   const double *__restrict__ alpha,
+                                                   const double *__restrict__ p_,
+                                                   const double *__restrict__ q_,
+                                                   double *__restrict__ x, double *__restrict__ r,
+                                                   double *part, const float *__restrict__ wD32,
+                                                   float *__restrict__ r32,
+                                                   float *__restrict__ z32) {
+    __shared__ double red[1024];
+    const int TY = blockDim.y;
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    const bool cv = col < N;
+    double acc[V], a[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+        acc[v] = 0.0;
+        a[v] = cv ? alpha[col + v] : 0.0;
+    }
+    const long base = (long)blockIdx.y * TY * ppt;
+    for (int k = 0; k < ppt; k++) {
+        long p = base + (long)k * TY + threadIdx.y;
+        if (!cv || p >= n) continue;
+        size_t e = (size_t)p * N + col;
+        VT<double, V> pv = ldv<double, V>(p_ + e), qv = ldv<double, V>(q_ + e),
+                      xv = ldv<double, V>(x + e), rv = ldv<double, V>(r + e);
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            xv.v[v] += a[v] * pv.v[v];
+            rv.v[v] -= a[v] * qv.v[v];
+            acc[v] += rv.v[v] * rv.v[v];
+        }
+        stv<double, V>(x + e, xv);
+        stv<double, V>(r + e, rv);
+        const float w = wD32[p];
+        VT<float, V> rf, zf;
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            rf.v[v] = (float)rv.v[v];
+            zf.v[v] = w * rf.v[v];
+        }
+        stv<float, V>(r32 + e, rf);
+        stv<float, V>(z32 + e, zf);
+    }
+    block_col_reduce<V, double>(acc, red, part, N, col, cv);
+}
+
+// the V-cycle's last sweep on the finest FP32 level (k_jacobi<float>'s
+// update) with the PCG's dot product formed in FP64 from the FP64 residual:
+// partial sum of r64 . (double) z_out per column (the values k_widen_dot
+// would add; its per-thread order differs)
+template <int V>
+__global__ void __launch_bounds__(256) k_jacobi_dot64(int m, long n, int N, int ppt,
+                                                      const float *__restrict__ wD, float c,
+                                                      float omw, const float *__restrict__ r,
+                                                      const double *__restrict__ r64,
+                                                      const float *__restrict__ zin,
+                                                      float *__restrict__ zout, double *part) {
+    __shared__ double red[1024];
+    const int TY = blockDim.y;
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    const bool cv = col < N;
+    double acc[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) acc[v] = 0.0;
+    const size_t sx = (size_t)N, sy = (size_t)m * N, sz = (size_t)m * m * N;
+    const long base = (long)blockIdx.y * TY * ppt;
+    long p = base + threadIdx.y;
+    int i, j, kk;
+    grid_decomp((unsigned)p, (unsigned)m, i, j, kk);
+    for (int k = 0; k < ppt; k++, p += TY, grid_advance(TY, m, i, j, kk)) {
+        if (!cv || p >= n) continue;
+        size_t e = (size_t)p * N + col;
+        VT<float, V> zc = ldv<float, V>(zin + e), rv = ldv<float, V>(r + e);
+        VT<float, V> sm = nbr_sum<float, V>(zin, e, i, j, kk, m, sx, sy, sz);
+        VT<double, V> r8 = ldv<double, V>(r64 + e);
+        const float w = wD[p];
+        VT<float, V> o;
+#pragma unroll
+        for (int v = 0; v < V; v++) o.v[v] = omw * zc.v[v] + w * (rv.v[v] + c * sm.v[v]);
+#pragma unroll
+        for (int v = 0; v < V; v++) acc[v] += r8.v[v] * (double)o.v[v];
+        stv<float, V>(zout + e, o);
+    }
+    block_col_reduce<V, double>(acc, red, part, N, col, cv);
+}
+
+// p = (double) z32 + beta p: the PCG's direction update from the FP32
+// preconditioned residual (the value k_widen_dot then k_pcg_p would give)
+template <int V>
+__global__ void __launch_bounds__(256) k_pcg_p_mg(long n, int N, int ppt,
+                                                  const double *__restrict__ beta,
+                                                  const float *__restrict__ z32,
+                                                  double *__restrict__ p_) {
+    const int TY = blockDim.y;
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    if (col >= N) return;
+    double bt[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) bt[v] = beta[col + v];
+    const long base = (long)blockIdx.y * TY * ppt;
+    for (int k = 0; k < ppt; k++) {
+        long p = base + (long)k * TY + threadIdx.y;
+        if (p >= n) continue;
+        size_t e = (size_t)p * N + col;
+        VT<float, V> zv = ldv<float, V>(z32 + e);
+        VT<double, V> pv = ldv<double, V>(p_ + e);
+#pragma unroll
+        for (int v = 0; v < V; v++) pv.v[v] = (double)zv.v[v] + bt[v] * pv.v[v];
+        stv<double, V>(p_ + e, pv);
+    }
+}
+
 template <typename T>
 __global__ void k_scale(size_t count, const double *factor, T *x) {
     T f = (T)factor[0];
@@ -1232,6 +1351,43 @@ template <typename T>
 void launch_jacobi_rt(const GridGeom &g, const T *wc, T omw, const T *r, const T *rt,
                       const T *zin, T *zout, double *part_rz, cudaStream_t s) {
     HQ_VEC_DISPATCH(T, g, run_jacobi_rt, g, wc, omw, r, rt, zin, zout, part_rz, s);
+}
+
+template <typename T, int V>
+static void run_pcg_xr_mg(const GridGeom &g, const double *alpha, const double *p, const double *q,
+                          double *x, double *r, double *part, const float *wD32, float *r32,
+                          float *z32, cudaStream_t s) {
+    HQ_LAUNCH_W(HQ_K_VECTOR, (double)g.n * g.N,
+                k_pcg_xr_mg<V><<<grd(g), blk(g), 0, s>>>(g.n, g.N, g.ppt, alpha, p, q, x, r, part,
+                                                         wD32, r32, z32));
+}
+void launch_pcg_xr_mg(const GridGeom &g, const double *alpha, const double *p, const double *q,
+                      double *x, double *r, double *part_rr, const float *wD32, float *r32,
+                      float *z32, cudaStream_t s) {
+    HQ_VEC_DISPATCH(double, g, run_pcg_xr_mg, g, alpha, p, q, x, r, part_rr, wD32, r32, z32, s);
+}
+template <typename T, int V>
+static void run_jacobi_dot64(const GridGeom &g, const float *wD, float c, float omw,
+                             const float *r, const double *r64, const float *zin, float *zout,
+                             double *part, cudaStream_t s) {
+    HQ_LAUNCH_W(HQ_K_SMOOTH, (double)g.n * g.N,
+                k_jacobi_dot64<V><<<grd(g), blk(g), 0, s>>>(g.m, g.n, g.N, g.ppt, wD, c, omw, r,
+                                                            r64, zin, zout, part));
+}
+void launch_jacobi_dot64(const GridGeom &g, const float *wD, float c, float omw, const float *r,
+                         const double *r64, const float *zin, float *zout, double *part,
+                         cudaStream_t s) {
+    HQ_VEC_DISPATCH(float, g, run_jacobi_dot64, g, wD, c, omw, r, r64, zin, zout, part, s);
+}
+template <typename T, int V>
+static void run_pcg_p_mg(const GridGeom &g, const double *beta, const float *z32, double *p,
+                         cudaStream_t s) {
+    HQ_LAUNCH_W(HQ_K_VECTOR, (double)g.n * g.N,
+                k_pcg_p_mg<V><<<grd(g), blk(g), 0, s>>>(g.n, g.N, g.ppt, beta, z32, p));
+}
+void launch_pcg_p_mg(const GridGeom &g, const double *beta, const float *z32, double *p,
+                     cudaStream_t s) {
+    HQ_VEC_DISPATCH(double, g, run_pcg_p_mg, g, beta, z32, p, s);
 }
 
 template <typename T, int V>

@@ -64,7 +64,7 @@ def initial_block(m: int, N: int, seed: int) -> np.ndarray:
 # mg_fp32 = 1: FP64 block PCG with the multigrid preconditioner in FP32)
 WORKLOADS = {
     "harmonic16_N8": dict(m=16, N=8, potential=("harmonic", None), u0_seed=1, tau=0.5,
-                          precision="fp64", cg_rtol=1e-10, eps=1e-8),
+                          precision="fp64", cg_rtol=1e-10, eps=1e-8, mg_fp32=1),
     "wells64_N64": dict(m=64, N=64, potential=("wells", 2), u0_seed=102, tau=0.4,
                         precision="fp64", cg_rtol=1e-10, eps=1e-8, mg_fp32=1),
     "wells128_N256": dict(m=128, N=256, potential=("wells", 3), u0_seed=103, tau=0.4,

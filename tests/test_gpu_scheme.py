@@ -215,11 +215,16 @@ def test_mixed_predictor_system_is_solved_to_fp64_accuracy(m, N):
     assert res < 1e-13, res
 
 
-def test_fp64_pcg_with_fp32_preconditioner_matches_oracle():
+@pytest.mark.parametrize("m", [12, 20])
+def test_fp64_pcg_with_fp32_preconditioner_matches_oracle(m):
     """mg_fp32 = 1: the block PCG stays FP64 (residuals, updates, stopping test)
     and only the V-cycle runs in FP32; W = G U is still solved to cg_rtol, so
-    20 steps follow the oracle's FP64 trajectory."""
-    m, N, tau = 12, 6, 0.4
+    20 steps follow the oracle's FP64 trajectory.  m = 12: the whole V-cycle
+    in one launch between the FP64 <-> FP32 conversions; m = 20: the finest
+    level as separate kernels with the interface fused into the PCG passes
+    (r32 and the first sweep written by the x / r update, r.z formed in FP64
+    by the last sweep, p updated from the FP32 z)."""
+    N, tau = 6, 0.4
     s, V, U0 = make(m, N, tau=tau, cg_rtol=1e-12, cg_maxit=400, mg_fp32=1)
     sigma = s.info()["sigma"]
     Uo = s.get_state()[0]
