@@ -450,7 +450,9 @@ def bench_batched(torch, hq, inputs, K, W, tune=True):
         launches = (k1 - k0) + sum(sum(v[0] for v in s.profile_read().values()) for s in solvers)
         return e0.elapsed_time(e1) / K, launches / K
 
-    def seq(solvers):
+    per_problem = []
+
+    def seq(solvers, record=False):
         tot = 0.0
         for s in solvers:
             s.step(W)
@@ -459,12 +461,15 @@ def bench_batched(torch, hq, inputs, K, W, tune=True):
             s.step(K)
             e1.record(s.stream)
             torch.cuda.synchronize()
-            tot += e0.elapsed_time(e1) / K
+            t = e0.elapsed_time(e1) / K
+            if record:
+                per_problem.append(t)
+            tot += t
         return tot
 
     solvers = make(lambda m, N: (0, 0))
     ms_default, launches = time_batch(solvers, "batch_timed")
-    ms_seq_mixed = seq(solvers)
+    ms_seq_mixed = seq(solvers, record=True)
     del solvers
     torch.cuda.empty_cache()
     out = {}
@@ -502,6 +507,11 @@ def bench_batched(torch, hq, inputs, K, W, tune=True):
            "gpu_launches_per_batch_step": launches, "graph_launches_per_call": 1,
            "sequential_mixed_ms": ms_seq_mixed, "sequential_fp64_ms": ms_seq_fp64,
            "speedup_vs_sequential_mixed": ms_seq_mixed / ms_batch,
+           "sequential_mixed_ms_by_shape": {
+               "%dx%d" % k: round(sum(t for (mm, nn), t in zip(shapes, per_problem)
+                                      if (mm, nn) == k), 3)
+               for k in sorted(set(shapes))},
+           "largest_problem_ms": max(per_problem),
            "speedup_vs_fp64": ms_seq_fp64 / ms_batch,
            "workload": "32 wells problems, sides/N drawn by default_rng(4) from "
                        "{32,48,64,96} x {16,32,64,128}; tau 0.4; mixed, PCG rtol 1e-6; "
@@ -689,8 +699,8 @@ def bench_grad(torch, hq, inputs, n_fd=6):
     potential (default_rng(6)) the same way, then timed: d(sum lambda)/dV
     (hq_grad_eigs) and the adjoint of the density loss (hq_grad_density, rtol
     1e-11).  Central finite differences (h = 1e-6) of the refined eigenpairs of
-    V +- h e_p at the first n_fd of the 20 points drawn by default_rng(505)
-    check both gradients."""
+    V +- h e_p at the first n_fd / 2 of the 20 points drawn by default_rng(505)
+    check both gradients (the other half: the points of largest gradient)."""
     import numpy as np
     V, U0, w = inputs.workload("wells64_N32")
     m, N = w["m"], w["N"]
@@ -727,7 +737,10 @@ def bench_grad(torch, hq, inputs, n_fd=6):
     torch.cuda.synchronize()
     t_dens = time.perf_counter() - t0
     f = hq.Solver(m, N, tau=0.4, cg_rtol=1e-10, mg_fp32=1)
-    pts = np.random.default_rng(505).choice(m ** 3, 20, replace=False)[:n_fd]
+    # the first of the 20 seeded points (mostly far from the wells, where the
+    # density is small) and the points of largest |d(sum lambda)/dV|
+    seeded = np.random.default_rng(505).choice(m ** 3, 20, replace=False)[:n_fd // 2]
+    pts = np.concatenate([seeded, np.argsort(-np.abs(ge))[:n_fd - len(seeded)]])
     fds, fdl = [], []
     for p in pts:
         vals = []

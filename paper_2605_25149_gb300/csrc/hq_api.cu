@@ -680,6 +680,7 @@ int fuse_level(const hq_ctx *x, bool honour_switch = true) {
     const char *e = std::getenv("HQ_FUSED_COARSE");
     if (honour_switch && e && e[0] == '0') return -1;
     if (!x->mixed && !x->mg32) return -1;
+    if (x->nc > 64) return -1;   // k_vcoarse's coarsest solve: at most 64 points (4^3)
     for (int l = 0; l + 1 < x->L; l++) {
         if (x->L - l > VC_MAXLEV) continue;
         if (vcoarse_smem_bytes(make_vcoarse(x, l)) <= (size_t)VC_MAX_SMEM) return l;
@@ -750,6 +751,15 @@ template <typename T>
 hq_status precondition(hq_ctx *x, const T *r, T *z, T *tbuf, bool first_done, double *part) {
     if constexpr (std::is_same<T, double>::value) {
         if (x->mg32) {
+            // the whole V-cycle fits one launch: conversion, V-cycle, widening
+            // and r.z in that launch (the same values as the three launches)
+            if (x->fuse_l0 == 0 && !x->no_fuse) {
+                const VCoarse vc = make_vcoarse(x, 0);
+                if (vcoarse64_smem_bytes(vc, x->lev[0].g) <= (size_t)VC_MAX_SMEM) {
+                    launch_vcoarse64(vc, x->lev[0].g, r, z, part, x->st);
+                    return HQ_OK;
+                }
+            }
             const size_t cnt = (size_t)x->n * x->N;
             launch_convert_d2f(cnt, r, x->R32, x->st);
             HQ_TRY(vcycle<float>(x, 0, x->R32, x->Z32, x->T32, false, nullptr));
@@ -2013,9 +2023,18 @@ hq_status level_check(hq_ctx *x, int level, bool need_next) {
 hq_status project(hq_ctx *x, double *y) {
     const int N = x->N;
     const double *u = (const double *)x->Uh;
-    GramPlan gp = make_gram_plan(x->n, N, N, false);
-    launch_gram<double>(gp, u, N, nullptr, 0, y, N, nullptr, 0, x->h3, x->gpart, x->Ksm, x->st);
-    launch_extract(N, N, -1.0, x->Ksm, N, x->Msm, N, x->st);
+    const double na = 2.0 * N;
+    if (x->ozgram && gram_oz_supported(2 * N) && use_oz(x, 0.5 * (double)x->n * na * na)) {
+        // u^T y from the tensor-core Gram of [u y] (digit slicing, FP64
+        // accurate): rows 0..N-1, columns N..2N-1 of the 2N x 2N result, in
+        // the predictor scratch (unused outside a step)
+        launch_gram_oz(x->n, u, N, y, N, x->h3, x->ozgram, x->Mw, x->status, x->st);
+        launch_extract(N, N, -1.0, x->Mw + N, 2 * N, x->Msm, N, x->st);
+    } else {
+        GramPlan gp = make_gram_plan(x->n, N, N, false);
+        launch_gram<double>(gp, u, N, nullptr, 0, y, N, nullptr, 0, x->h3, x->gpart, x->Ksm, x->st);
+        launch_extract(N, N, -1.0, x->Ksm, N, x->Msm, N, x->st);
+    }
     block_gemm<double>(x, u, N, x->Msm, nullptr, 0, nullptr, y, y, false, nullptr);
     return check_launch(x);
 }
@@ -2107,6 +2126,7 @@ hq_status projected_pcg(hq_ctx *x, const double *b, double *xi, const double *sh
     }
     if (iters) *iters = it > maxit ? maxit : it;
     HQ_TRY(sync_status(x, sc.status, what));
+    HQ_TRY(sync_status(x, x->status, what));   // tensor-core projections
     if (nact > 0) return fail(x, HQ_ERR_NOT_CONVERGED, std::string(what) + " reached maxit");
     return HQ_OK;
 }

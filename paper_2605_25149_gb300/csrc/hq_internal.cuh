@@ -172,6 +172,13 @@ size_t vcoarse_smem_bytes(const VCoarse &v);
 void vcoarse_prepare();
 // z = V-cycle(r) from level l0 for all N columns (point-major n_l0 x N FP32 blocks)
 void launch_vcoarse(const VCoarse &v, int N, const float *r, float *z, cudaStream_t s);
+// the whole FP32 V-cycle (l0 = 0) between FP64 blocks: r32 = (float) r64,
+// z64 = (double) V-cycle(r32) and (part non-null) the partials of r64 . z64
+// in the rows of the FP64 geometry g64, as launch_convert_d2f +
+// launch_vcoarse + launch_widen_dot give them, bit for bit
+size_t vcoarse64_smem_bytes(const VCoarse &v, const GridGeom &g64);
+void launch_vcoarse64(const VCoarse &v, const GridGeom &g64, const double *r64, double *z64,
+                      double *part, cudaStream_t s);
 
 // per-column reduction of gy partials + PCG scalar logic
 enum FinMode { FIN_BNORM_RNORM = 0, FIN_ALPHA = 1, FIN_RR = 2, FIN_BETA = 3, FIN_RZ = 4 };

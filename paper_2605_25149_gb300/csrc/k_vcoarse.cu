@@ -41,6 +41,28 @@ __device__ __forceinline__ void decomp(int p, int m, int &i, int &j, int &k) {
     j = q - k * m;
 }
 
+// The points p = t, t + S, t + 2S, ... of an m^3 grid with their (i, j, k):
+// the divisions happen once per pass, each step adds the precomputed
+// decomposition of S with carries (the index arithmetic per point would
+// otherwise be two integer divisions, more instructions than the update)
+struct GridWalk {
+    int p, i, j, k, di, dj, dk, m;
+    __device__ __forceinline__ GridWalk(int t, int S, int m_) : p(t), m(m_) {
+        decomp(t, m, i, j, k);
+        decomp(S, m, di, dj, dk);
+    }
+    __device__ __forceinline__ void next(int S) {
+        p += S;
+        i += di;
+        int ci = i >= m;
+        i -= ci ? m : 0;
+        j += dj + ci;
+        int cj = j >= m;
+        j -= cj ? m : 0;
+        k += dk + cj;
+    }
+};
+
 // z = wD r (the first sweep from zero)
 __device__ void sm_first(int m, const float *wD, const float *r, float *z) {
     const int n = m * m * m;
@@ -54,9 +76,8 @@ __device__ void sm_first(int m, const float *wD, const float *r, float *z) {
 __device__ void sm_jacobi(int m, const float *wD, float c, float omw, const float *r,
                           const float *zin, float *zout) {
     const int n = m * m * m;
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        int i, j, k;
-        decomp(p, m, i, j, k);
+    for (GridWalk g(threadIdx.x, blockDim.x, m); g.p < n; g.next(blockDim.x)) {
+        const int p = g.p, i = g.i, j = g.j, k = g.k;
         const float s = nbr6(zin, p, i, j, k, m);
         const float w = wD[p];
         const float zc = zin[p], rv = r[p];
@@ -68,9 +89,8 @@ __device__ void sm_jacobi(int m, const float *wD, float c, float omw, const floa
 __device__ void sm_resid(int m, const float *D, float c, const float *x, const float *b,
                          float *y) {
     const int n = m * m * m;
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        int i, j, k;
-        decomp(p, m, i, j, k);
+    for (GridWalk g(threadIdx.x, blockDim.x, m); g.p < n; g.next(blockDim.x)) {
+        const int p = g.p, i = g.i, j = g.j, k = g.k;
         const float s = nbr6(x, p, i, j, k, m);
         const float d = D[p];
         const float xc = x[p], bb = b[p];
@@ -91,11 +111,20 @@ __device__ void sm_axis(int o2, int o1, int o0, int ilen, int axis, const int *i
     const int s1 = d0, s2 = d1 * d0;
     const int sa = axis == 0 ? 1 : (axis == 1 ? s1 : s2);
     const bool unit = scale == 1.f;
-    for (int p = threadIdx.x; p < nout; p += blockDim.x) {
-        const int i0 = p % o0;
-        const int q = p / o0;
-        const int i1 = q % o1;
-        const int i2 = q / o1;
+    // (i0, i1, i2) of p = t, t + S, ... by carries (one set of divisions)
+    const int S = blockDim.x;
+    int i0 = threadIdx.x % o0, i1 = (threadIdx.x / o0) % o1, i2 = threadIdx.x / (o0 * o1);
+    const int s0 = S % o0, s1d = (S / o0) % o1, s2d = S / (o0 * o1);
+    for (int p = threadIdx.x; p < nout; p += S) {
+        if (p != (int)threadIdx.x) {
+            i0 += s0;
+            const int c0 = i0 >= o0;
+            i0 -= c0 ? o0 : 0;
+            i1 += s1d + c0;
+            const int c1 = i1 >= o1;
+            i1 -= c1 ? o1 : 0;
+            i2 += s2d + c1;
+        }
         const int oa = axis == 0 ? i0 : (axis == 1 ? i1 : i2);
         const int ib = (axis == 0 ? 0 : i0) + (axis == 1 ? 0 : i1 * s1) + (axis == 2 ? 0 : i2 * s2);
         int ii[NT];
@@ -125,8 +154,18 @@ __device__ void sm_coarse(int nc, const double *__restrict__ Ainv, const float *
                           double *part) {
     for (int t = threadIdx.x; t < 8 * nc; t += blockDim.x) {
         const int p = t >> 3, y = t & 7;
+        // nc <= 64: at most eight terms, their loads issued together
+        double a[8], rv[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int qq = y + 8 * u;
+            a[u] = qq < nc ? __ldg(Ainv + (size_t)p * nc + qq) : 0.0;
+            rv[u] = qq < nc ? (double)r[qq] : 0.0;
+        }
         double acc = 0.0;
-        for (int qq = y; qq < nc; qq += 8) acc += __ldg(Ainv + (size_t)p * nc + qq) * (double)r[qq];
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+            if (y + 8 * u < nc) acc += a[u] * rv[u];
         part[t] = acc;
     }
     __syncthreads();
@@ -155,8 +194,19 @@ struct LevelSmem {
     float *r, *a, *b;
 };
 
+// MG64 = false: r, z are FP32 blocks (rin, zout).  MG64 = true (the whole
+// V-cycle of an FP32 preconditioner inside an FP64 PCG): r is read from the
+// FP64 block r64 and rounded (the value k_d2f writes), z is written widened
+// to the FP64 block z64, and the partial sums of r64 . z are formed as
+// k_widen_dot forms them in the FP64 level geometry (TY points per row chunk
+// per thread row, ppt chunks, gy partial rows: the same terms in the same
+// order, so the values equal d2f + V-cycle + widen bit for bit)
+template <bool MG64>
 __global__ void __launch_bounds__(VC_THREADS) k_vcoarse(VCoarse v, int N, const float *__restrict__ rin,
-                                                        float *__restrict__ zout) {
+                                                        float *__restrict__ zout,
+                                                        const double *__restrict__ r64,
+                                                        double *__restrict__ z64, double *part,
+                                                        int TY, int ppt, int gy) {
     extern __shared__ __align__(16) float vsm[];
     const int col = blockIdx.x;
     const int Lf = v.levels;   // levels in this launch: l0 .. l0 + Lf - 1 (last = coarsest)
@@ -175,9 +225,23 @@ __global__ void __launch_bounds__(VC_THREADS) k_vcoarse(VCoarse v, int N, const 
     for (int l = 0; l < Lf; l++) {
         const int n = v.m[l] * v.m[l] * v.m[l];
         float *d = q, *w = q + n;
-        for (int p = threadIdx.x; p < n; p += blockDim.x) {
-            d[p] = __ldg(v.D[l] + p);
-            w[p] = __ldg(v.wD[l] + p);
+        // four points per thread in flight: loads first, then the stores
+        for (int p0 = threadIdx.x; p0 < n; p0 += 4 * blockDim.x) {
+            float a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int p = p0 + u * blockDim.x;
+                a[u] = p < n ? __ldg(v.D[l] + p) : 0.f;
+                b[u] = p < n ? __ldg(v.wD[l] + p) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int p = p0 + u * blockDim.x;
+                if (p < n) {
+                    d[p] = a[u];
+                    w[p] = b[u];
+                }
+            }
         }
         Ds[l] = d;
         wDs[l] = w;
@@ -210,7 +274,20 @@ __global__ void __launch_bounds__(VC_THREADS) k_vcoarse(VCoarse v, int N, const 
     // right-hand side of level l0 (column `col` of a point-major n0 x N block)
     {
         const int n0 = v.m[0] * v.m[0] * v.m[0];
-        for (int p = threadIdx.x; p < n0; p += blockDim.x) lv[0].r[p] = rin[(size_t)p * N + col];
+        for (int p0 = threadIdx.x; p0 < n0; p0 += 4 * blockDim.x) {
+            float a[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int p = p0 + u * blockDim.x;
+                if (MG64) a[u] = p < n0 ? (float)r64[(size_t)p * N + col] : 0.f;
+                else a[u] = p < n0 ? rin[(size_t)p * N + col] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int p = p0 + u * blockDim.x;
+                if (p < n0) lv[0].r[p] = a[u];
+            }
+        }
     }
     __syncthreads();
     // down: pre-smoothing, residual, restriction
@@ -267,9 +344,32 @@ __global__ void __launch_bounds__(VC_THREADS) k_vcoarse(VCoarse v, int N, const 
         }
         zc = c0;
     }
-    {
-        const int n0 = v.m[0] * v.m[0] * v.m[0];
+    const int n0 = v.m[0] * v.m[0] * v.m[0];
+    if (!MG64) {
         for (int p = threadIdx.x; p < n0; p += blockDim.x) zout[(size_t)p * N + col] = zc[p];
+        return;
+    }
+    for (int p = threadIdx.x; p < n0; p += blockDim.x) z64[(size_t)p * N + col] = (double)zc[p];
+    if (!part) return;
+    // partial row `row` of column col = sum over thread rows y (in order) of
+    // the sum over chunks k (in order) of r . z at p = row TY ppt + k TY + y
+    double *red = cpart + 8 * v.nc;
+    for (int t = threadIdx.x; t < gy * TY; t += blockDim.x) {
+        const int row = t / TY, y = t - row * TY;
+        double acc = 0.0;
+        for (int k = 0; k < ppt; k++) {
+            const long p = (long)row * TY * ppt + (long)k * TY + y;
+            if (p >= n0) continue;
+            const double o = (double)zc[p];
+            acc += r64[(size_t)p * N + col] * o;
+        }
+        red[t] = acc;
+    }
+    __syncthreads();
+    for (int row = threadIdx.x; row < gy; row += blockDim.x) {
+        double sacc = 0.0;
+        for (int y = 0; y < TY; y++) sacc += red[row * TY + y];
+        part[(size_t)row * N + col] = sacc;
     }
 }
 
@@ -279,14 +379,29 @@ size_t vcoarse_smem_bytes(const VCoarse &v) {
     return vc_floats(v) * sizeof(float) + 8 * sizeof(double) * (size_t)v.nc;
 }
 
+size_t vcoarse64_smem_bytes(const VCoarse &v, const GridGeom &g64) {
+    return vcoarse_smem_bytes(v) + sizeof(double) * (size_t)g64.gy * g64.ty;
+}
+
 void vcoarse_prepare() {
-    cudaFuncSetAttribute(k_vcoarse, cudaFuncAttributeMaxDynamicSharedMemorySize, VC_MAX_SMEM);
+    cudaFuncSetAttribute(k_vcoarse<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, VC_MAX_SMEM);
+    cudaFuncSetAttribute(k_vcoarse<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, VC_MAX_SMEM);
 }
 
 void launch_vcoarse(const VCoarse &v, int N, const float *r, float *z, cudaStream_t s) {
     const size_t bytes = vcoarse_smem_bytes(v);
     HQ_LAUNCH_W(HQ_K_COARSE, (double)v.m[0] * v.m[0] * v.m[0] * N,
-                k_vcoarse<<<N, VC_THREADS, bytes, s>>>(v, N, r, z));
+                k_vcoarse<false><<<N, VC_THREADS, bytes, s>>>(v, N, r, z, nullptr, nullptr,
+                                                              nullptr, 0, 0, 0));
+}
+
+void launch_vcoarse64(const VCoarse &v, const GridGeom &g64, const double *r64, double *z64,
+                      double *part, cudaStream_t s) {
+    const size_t bytes = vcoarse64_smem_bytes(v, g64);
+    HQ_LAUNCH_W(HQ_K_COARSE, (double)v.m[0] * v.m[0] * v.m[0] * g64.N,
+                k_vcoarse<true><<<g64.N, VC_THREADS, bytes, s>>>(v, g64.N, nullptr, nullptr, r64,
+                                                                 z64, part, g64.ty, g64.ppt,
+                                                                 g64.gy));
 }
 
 }  // namespace hq
