@@ -411,6 +411,57 @@ def run_ttr(args):
     print(json.dumps(out), flush=True)
 
 
+def run_large_accuracy(args):
+    """The 128^3, N = 256 mixed workload run for accuracy (not part of the
+    default run): Algorithm 1 in mixed precision with the adaptive time step
+    (tau_max 10) in chunks of 500 steps timed with CUDA events, until g <
+    --large-g or --large-steps steps; after every 1000 steps (untimed) the
+    FP64 Rayleigh-Ritz eigenpairs with their FP64 residual norms
+    r_i = ||H u_i - lambda_i u_i||.  H is symmetric, so an eigenvalue lies
+    within r_i of each Ritz value lambda_i (and lambda_i is an upper bound of
+    the i-th eigenvalue): max_i r_i / |lambda_i| bounds the relative
+    eigenvalue error without an FP64 reference run.  SM clocks sampled."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2605_25149_gb300 import hq, inputs
+    V, U0, w = inputs.workload("wells128_N256")
+    m, N = w["m"], w["N"]
+    clk = ClockSampler(0)
+    clk.start()
+    s = hq.Solver(m, N, tau=w["tau"], cg_rtol=w["cg_rtol"], precision="mixed", adaptive_tau=1,
+                  tau_max=args.tau_max)
+    s.set_potential(V)
+    s.set_initial(U0)
+    del U0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    hist, steps, t, g = [], 0, 0.0, float("inf")
+    while steps < args.large_steps and g >= args.large_g:
+        torch.cuda.synchronize()
+        e0.record(s.stream)
+        n, g = s.solve(args.large_g, min(500, args.large_steps - steps),
+                       raise_on_unconverged=False)
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        t += e0.elapsed_time(e1) / 1e3
+        steps += n
+        row = {"steps": steps, "s": t, "g": g, "tau": s.time_step()}
+        if steps % 1000 == 0 or g < args.large_g or steps >= args.large_steps:
+            ev = s.eigenpairs()
+            lam, res = ev["lam_rr"], ev["residuals"]
+            row.update({"max_rel_resid": float(np.max(res / np.abs(lam))),
+                        "lam_first": lam[:3].tolist(), "lam_last": lam[-3:].tolist()})
+        hist.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    clocks = clk.stop()
+    print(json.dumps({"workload": "wells128_N256: 128^3 grid, V=|x|^2/2 + 8 wells "
+                                  "(default_rng(3)), N=256, mixed, PCG rtol 1e-6, adaptive tau",
+                      "steps": steps, "scheme_s": t, "g": g, "clocks": clocks,
+                      "history": hist}), flush=True)
+
+
 def bench_batched(torch, hq, inputs, K, W, tune=True):
     """The batched workload: 32 wells problems, grid sides in {32,48,64,96}^3
     and N in {16,32,64,128} (seeded), tau = 0.4, mixed precision, advanced
@@ -499,6 +550,25 @@ def bench_batched(torch, hq, inputs, K, W, tune=True):
         ms_seq_fp64 += seq([s])
         del s
     torch.cuda.empty_cache()
+    # many small problems: 32 problems of the 16^3, N = 8 harmonic workload
+    # (U0 from default_rng(3000 + k)) in one batch, against one of them alone
+    Vh, _, wh = inputs.workload("harmonic16_N8")
+    small = []
+    for k in range(32):
+        sh = hq.Solver(wh["m"], wh["N"], **solver_kw(wh))
+        sh.set_potential(Vh)
+        sh.set_initial(inputs.initial_block(wh["m"], wh["N"], 3000 + k))
+        small.append(sh)
+    ms_small_one = seq(small[:1])
+    ms_small_batch, _ = time_batch(small, "batch_small_timed")
+    del small
+    torch.cuda.empty_cache()
+    out["small_problems"] = {
+        "problems": 32, "workload": "harmonic16_N8 (16^3, N = 8, FP64 PCG, FP32 multigrid "
+                                    "preconditioner), U0 from default_rng(3000 + k)",
+        "ms_per_batch_step": ms_small_batch, "ms_per_step_one_problem": ms_small_one,
+        "problem_steps_per_s": 32 * 1000.0 / ms_small_batch,
+        "speedup_vs_one_at_a_time": 32 * ms_small_one / ms_small_batch}
     ms_batch = min(ms_default, ms_tuned)
     pc = sum(m ** 3 * N for m, N in shapes)
     res = {"value": len(shapes) * 1000.0 / ms_batch, "unit": "problem-steps/s",
@@ -1055,6 +1125,10 @@ def main():
     ap.add_argument("--ttr-handoff", type=float, default=3e-4,
                     help="g at which the time-to-residual legs hand the scheme's state to "
                          "the FP64 residual refinement")
+    ap.add_argument("--large-accuracy", action="store_true",
+                    help="only the accuracy run of the 128^3, N = 256 mixed workload (minutes)")
+    ap.add_argument("--large-g", type=float, default=1e-4)
+    ap.add_argument("--large-steps", type=int, default=4000)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
     ap.add_argument("--no-grad", action="store_true", help="skip the differentiation workload")
@@ -1082,6 +1156,8 @@ def main():
         run_reference(args)
     elif args.ttr:
         run_ttr(args)
+    elif args.large_accuracy:
+        run_large_accuracy(args)
     else:
         run_hq(args)
 

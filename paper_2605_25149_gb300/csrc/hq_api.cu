@@ -1544,9 +1544,10 @@ hq_status batch_build(hq_batch *b) {
     hq_status st = HQ_OK;
     for (int k = 0; k < K && ok; k++) {
         hq_ctx *x = b->ctx[k];
-        // several concurrent problems: the coarse levels as separate kernels
-        // (the same values bit for bit, see k_vcoarse.cu)
-        x->no_fuse = K > 1;
+        // several concurrent problems: the coarse levels of a larger grid as
+        // separate kernels (the same values bit for bit, see k_vcoarse.cu);
+        // a V-cycle that fits one launch whole stays one launch
+        x->no_fuse = K > 1 && x->fuse_l0 > 0;
         st = x->mixed ? capture_problem<float>(x, bodies[k]) : capture_problem<double>(x, bodies[k]);
         x->no_fuse = false;
         if (st != HQ_OK) {
