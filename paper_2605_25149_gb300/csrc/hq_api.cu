@@ -2024,18 +2024,14 @@ hq_status level_check(hq_ctx *x, int level, bool need_next) {
 hq_status project(hq_ctx *x, double *y) {
     const int N = x->N;
     const double *u = (const double *)x->Uh;
-    const double na = 2.0 * N;
-    if (x->ozgram && gram_oz_supported(2 * N) && use_oz(x, 0.5 * (double)x->n * na * na)) {
-        // u^T y from the tensor-core Gram of [u y] (digit slicing, FP64
-        // accurate): rows 0..N-1, columns N..2N-1 of the 2N x 2N result, in
-        // the predictor scratch (unused outside a step)
-        launch_gram_oz(x->n, u, N, y, N, x->h3, x->ozgram, x->Mw, x->status, x->st);
-        launch_extract(N, N, -1.0, x->Mw + N, 2 * N, x->Msm, N, x->st);
-    } else {
-        GramPlan gp = make_gram_plan(x->n, N, N, false);
-        launch_gram<double>(gp, u, N, nullptr, 0, y, N, nullptr, 0, x->h3, x->gpart, x->Ksm, x->st);
-        launch_extract(N, N, -1.0, x->Ksm, N, x->Msm, N, x->st);
-    }
+    // u^T y by the SIMT FP64 Gram: y is kept in range(P), so u^T y is at the
+    // rounding level of |u| |y|; the digit-sliced tensor-core Gram, whose
+    // error is bounded by the columns' largest entries times the number of
+    // points (~3e-11 of |u| |y| at 64^3 for localised u), let the Krylov
+    // space of a 1e-11 adjoint solve leak into span(u) and stall
+    GramPlan gp = make_gram_plan(x->n, N, N, false);
+    launch_gram<double>(gp, u, N, nullptr, 0, y, N, nullptr, 0, x->h3, x->gpart, x->Ksm, x->st);
+    launch_extract(N, N, -1.0, x->Ksm, N, x->Msm, N, x->st);
     block_gemm<double>(x, u, N, x->Msm, nullptr, 0, nullptr, y, y, false, nullptr);
     return check_launch(x);
 }
