@@ -94,6 +94,7 @@ def _sig(lib):
         "orc_grad_eigs": (_I, [_I, _D, _D, _I, _P, _P, _P]),
         "orc_grad_density": (_I, [_I, _D, _D, _P, _I, _P, _P, _P, _D, _I, _P, _P, _P]),
         "orc_refine": (_I, [_I, _D, _D, _P, _I, _P, _I, _D, _I, _P, _P, _P]),
+        "orc_block_pcg_mg": (_I, [_P, _I, _P, _P, _D, _I, _P]),
     }
     for name, (res, args) in spec.items():
         f = getattr(lib, name)
@@ -240,6 +241,19 @@ class MG:
         Z = np.empty_like(R)
         lib().orc_mg_coarse_solve(self._h, R.shape[1], _ptr(R), _ptr(Z))
         return Z
+
+    def block_pcg(self, B, X0=None, rtol=1e-13, maxit=1000):
+        """O'Leary's block PCG with this V-cycle (an alternative inner solver,
+        not in the paper): N x N step matrices alpha = (P^T A P)^-1 Z^T R,
+        beta = (Z^T R)^-1 Z'^T R'.  rtol = 0 runs exactly maxit iterations.
+        Returns (X, iterations)."""
+        B = _f64(B)
+        X = np.zeros_like(B) if X0 is None else np.array(_f64(X0), copy=True)
+        its = ctypes.c_int()
+        st = lib().orc_block_pcg_mg(self._h, B.shape[1], _ptr(B), _ptr(X), rtol, maxit,
+                                    ctypes.byref(its))
+        _check(st, "orc_block_pcg_mg")
+        return X, its.value
 
     def pcg(self, B, X0=None, rtol=1e-13, maxit=1000):
         """MG-preconditioned CG per column; rtol = 0 runs exactly maxit steps."""

@@ -1299,3 +1299,116 @@ int orc_refine(int m, double lo, double hi, const double *V, int N, double *U, i
     free(u);
     return status;
 }
+
+/* ------------------------------------------------------------------------ */
+/* O'Leary's block preconditioned CG (not in the paper; an alternative inner */
+/* solver for W = G U): all N columns share one block Krylov space, with    */
+/* N x N step matrices instead of per-column scalars.                        */
+/*   R = B - A X, Z = M R, P = Z                                             */
+/*   repeat: Q = A P, alpha = (P^T Q)^{-1} (Z^T R), X += P alpha,            */
+/*           R -= Q alpha, stop if every ||r_j|| <= rtol ||b_j||,            */
+/*           Z' = M R, beta = (Z^T R)^{-1} (Z'^T R'), P = Z' + P beta.        */
+/* P^T Q and Z^T R are symmetric positive definite while the block keeps full */
+/* rank; their systems are solved by Cholesky (ORC_ERR_SINGULAR otherwise).  */
+/* For N = 1 this is pcg_col.  rtol = 0 runs exactly maxit iterations.       */
+/* ------------------------------------------------------------------------ */
+static void apply_block(const orc_mg *mg, int N, const double *X, double *Y)
+{
+    orc_apply_h(mg->m[0], mg->h[0], mg->V[0], mg->sigma, N, X, Y);
+}
+
+/* C (N x N) = X^T Y, plain sums over the n points (the PCG's inner products) */
+static void block_dot(long n, int N, const double *X, const double *Y, double *C)
+{
+    for (int a = 0; a < N; a++)
+        for (int b = 0; b < N; b++) {
+            double s = 0.0;
+            for (long p = 0; p < n; p++) s += X[p * N + a] * Y[p * N + b];
+            C[a * N + b] = s;
+        }
+}
+
+/* S (N x N) <- A^{-1} S for SPD A (N x N), via its Cholesky factor L */
+static int spd_solve_cols(int N, const double *A, double *S, double *L, double *tmp)
+{
+    memcpy(L, A, sizeof(double) * N * N);
+    int st = cholesky(N, L);
+    if (st != ORC_OK) return st;
+    for (int c = 0; c < N; c++) {
+        for (int i = 0; i < N; i++) tmp[i] = S[i * N + c];
+        chol_solve(N, L, tmp, tmp + N);
+        for (int i = 0; i < N; i++) S[i * N + c] = tmp[N + i];
+    }
+    return ORC_OK;
+}
+
+/* every column's residual within tolerance: ||r_c|| <= rtol ||b_c|| */
+static int block_done(long n, int N, const double *R, double rtol, const double *bn)
+{
+    for (int c = 0; c < N; c++) {
+        double s = 0.0;
+        for (long p = 0; p < n; p++) s += R[p * N + c] * R[p * N + c];
+        if (!(sqrt(s) <= rtol * bn[c])) return 0;
+    }
+    return 1;
+}
+
+int orc_block_pcg_mg(const orc_mg *mg, int N, const double *B, double *X, double rtol,
+                     int maxit, int *iters)
+{
+    long n = cube(mg->m[0]);
+    size_t blk = sizeof(double) * n * N, sq = sizeof(double) * N * N;
+    double *R = malloc(blk), *Z = malloc(blk), *P = malloc(blk), *Q = malloc(blk), *T = malloc(blk);
+    double *PQ = malloc(sq), *ZR = malloc(sq), *ZR1 = malloc(sq), *al = malloc(sq),
+           *be = malloc(sq), *L = malloc(sq), *tmp = malloc(sizeof(double) * 2 * N);
+    double *bn = malloc(sizeof(double) * N);
+    int st = ORC_ERR_NOT_CONVERGED, it = 0;
+    apply_block(mg, N, X, Q);
+    for (long i = 0; i < n * N; i++) R[i] = B[i] - Q[i];
+    for (int c = 0; c < N; c++) {
+        double s = 0.0;
+        for (long p = 0; p < n; p++) s += B[p * N + c] * B[p * N + c];
+        bn[c] = sqrt(s);
+    }
+    if (rtol > 0.0 && block_done(n, N, R, rtol, bn)) st = ORC_OK;
+    if (st != ORC_OK) {
+        orc_mg_vcycle(mg, N, R, Z);
+        memcpy(P, Z, blk);
+        block_dot(n, N, Z, R, ZR);
+    }
+    while (st != ORC_OK && it < maxit) {
+        apply_block(mg, N, P, Q);
+        block_dot(n, N, P, Q, PQ);
+        memcpy(al, ZR, sq);
+        if (spd_solve_cols(N, PQ, al, L, tmp) != ORC_OK) { st = ORC_ERR_BREAKDOWN; break; }
+        for (long p = 0; p < n; p++)
+            for (int j = 0; j < N; j++) {
+                double sx = 0.0, sr = 0.0;
+                for (int k = 0; k < N; k++) {
+                    sx += P[p * N + k] * al[k * N + j];
+                    sr += Q[p * N + k] * al[k * N + j];
+                }
+                X[p * N + j] += sx;
+                R[p * N + j] -= sr;
+            }
+        it++;
+        if (rtol > 0.0 && block_done(n, N, R, rtol, bn)) { st = ORC_OK; break; }
+        orc_mg_vcycle(mg, N, R, Z);
+        block_dot(n, N, Z, R, ZR1);
+        memcpy(be, ZR1, sq);
+        if (spd_solve_cols(N, ZR, be, L, tmp) != ORC_OK) { st = ORC_ERR_BREAKDOWN; break; }
+        for (long p = 0; p < n; p++)
+            for (int j = 0; j < N; j++) {
+                double s = 0.0;
+                for (int k = 0; k < N; k++) s += P[p * N + k] * be[k * N + j];
+                T[p * N + j] = Z[p * N + j] + s;
+            }
+        memcpy(P, T, blk);
+        memcpy(ZR, ZR1, sq);
+    }
+    if (rtol == 0.0 && st == ORC_ERR_NOT_CONVERGED && it == maxit) st = ORC_OK;
+    if (iters) *iters = it;
+    free(R); free(Z); free(P); free(Q); free(T); free(PQ); free(ZR); free(ZR1); free(al);
+    free(be); free(L); free(tmp); free(bn);
+    return st;
+}

@@ -185,3 +185,32 @@ def test_pcg_fixed_iteration_mode():
     assert (its == 3).all()
     x2, _ = mg.pcg(b, rtol=0.0, maxit=2)
     assert not np.array_equal(x2, x3)
+
+
+def test_block_pcg_single_column_is_pcg_and_solves_the_system():
+    """O'Leary's block PCG (N x N alpha, beta) with one column is the
+    per-column PCG iterate by iterate; with several columns it converges to
+    the dense solve of (H + sigma) X = B in no more iterations than the
+    slowest column of the per-column PCG (its block Krylov space contains
+    every column's Krylov space)."""
+    m = 9
+    V = I.wells(m, 6)
+    sigma = O.auto_shift(m, V)
+    mg = O.MG(m, V, sigma)
+    rng = np.random.default_rng(21)
+    b = rng.standard_normal((m ** 3, 1))
+    for k in (1, 2, 5):
+        xb, _ = mg.block_pcg(b, rtol=0.0, maxit=k)
+        xc, _ = mg.pcg(b, rtol=0.0, maxit=k)
+        np.testing.assert_allclose(xb, xc, rtol=1e-12, atol=1e-14 * np.abs(xc).max())
+    N = 6
+    B = rng.standard_normal((m ** 3, N))
+    Xb, itb = mg.block_pcg(B, rtol=1e-12, maxit=500)
+    Xc, itc = mg.pcg(B, rtol=1e-12, maxit=500)
+    A = dense_h(m, O.grid_h(m), V, sigma)
+    Xd = np.linalg.solve(A, B)
+    np.testing.assert_allclose(Xb, Xd, rtol=1e-10, atol=1e-12 * np.abs(Xd).max())
+    assert itb <= itc.max()
+    # the block residual is below the tolerance in every column
+    R = B - A @ Xb
+    assert np.all(np.linalg.norm(R, axis=0) <= 1e-12 * np.linalg.norm(B, axis=0) * 1.0001)
