@@ -762,6 +762,41 @@ def ttr_live(torch, hq, inputs, args):
     return out
 
 
+def bench_inner(torch, hq, V, U0, w, reps=3):
+    """The inner solve (H + sigma) X = U of the step, from a zero start to the
+    workload's rtol, with the per-column block PCG the step uses and with
+    O'Leary's block PCG (N x N step matrices, one block Krylov space): time,
+    iterations and launches of each.  Both host-driven (one synchronisation
+    per iteration), so wall time brackets each solve."""
+    import numpy as np
+    m, N = w["m"], w["N"]
+    s = hq.Solver(m, N, **solver_kw(w))
+    s.set_potential(V)
+    s.set_initial(U0)
+    B = torch.from_numpy(np.ascontiguousarray(U0)).cuda()
+    rt = w["cg_rtol"]
+    out = {"rtol": rt, "start": "zero", "rhs": "the initial block U_0"}
+    for name, solve in (("per_column", lambda: s.block_pcg(B, rtol=rt, maxit=1000)),
+                        ("oleary_block", lambda: s.block_pcg_coupled(B, rtol=rt, maxit=1000))):
+        solve()
+        s.profile(timing=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            X, its = solve()
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) / reps * 1e3
+        launches = sum(v[0] for v in s.profile_read().values()) / reps
+        its = np.asarray(its)
+        out[name] = {"ms": ms, "iterations_max": int(its.max()),
+                     "iterations_mean": float(its.mean()), "launches": launches}
+        del X
+    out["oleary_speedup"] = out["per_column"]["ms"] / out["oleary_block"]["ms"]
+    del s
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_grad(torch, hq, inputs, n_fd=6):
     """The differentiation workload (64^3, N = 32, wells default_rng(5), FP64):
     converged eigenpairs (mixed scheme to g < 1e-4, then FP64 residual
@@ -980,6 +1015,11 @@ def run_hq(args):
         batched = bench_batched(torch, hq, inputs, max(1, min(K, 3)), max(1, min(W, 1)),
                                 tune=not args.no_tune)
 
+    # ---- inner solver: per-column against O'Leary's block PCG --------------------
+    inner = None
+    if not args.no_inner:
+        inner = bench_inner(torch, hq, V, U0, w)
+
     # ---- differentiation workload (64^3, N = 32) ------------------------------
     grad = None
     if not args.no_grad:
@@ -1021,6 +1061,7 @@ def run_hq(args):
         "large": large,
         "batched": batched,
         "differentiation": grad,
+        "inner_solvers": inner,
         "cpu_baseline": cpu,
         "gradient_norm_last": g,
     }
@@ -1133,6 +1174,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
     ap.add_argument("--no-grad", action="store_true", help="skip the differentiation workload")
     ap.add_argument("--no-large", action="store_true", help="skip the 128^3, N = 256 workload")
+    ap.add_argument("--no-inner", action="store_true",
+                    help="skip the per-column / O'Leary block PCG comparison")
     ap.add_argument("--large-shape", type=int, nargs=2, default=[128, 256], metavar=("M", "N"),
                     help="grid side and block width of the large mixed workload")
     ap.add_argument("--no-tune", action="store_true",
@@ -1152,6 +1195,7 @@ def main():
     if ws > 1:
         # replicas: the timed headline step only (the other legs hold every GPU for minutes)
         args.no_ttr = args.no_mixed = args.no_large = args.no_batch = args.no_grad = True
+        args.no_inner = True
     if args.impl == "reference":
         run_reference(args)
     elif args.ttr:

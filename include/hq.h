@@ -249,6 +249,19 @@ hq_status hq_mg_vcycle(hq_ctx *ctx, const void *r, void *z);
 hq_status hq_block_pcg(hq_ctx *ctx, const void *B, void *X, double rtol, int maxit,
                        int *iters);
 
+/* O'Leary's block PCG (not in the paper; an alternative to hq_block_pcg's
+ * per-column recurrences): X = G B with all N columns in one block Krylov
+ * space and N x N step matrices, alpha = (P^T A P)^{-1} (Z^T R),
+ * beta = (Z^T R)^{-1} (Z'^T R') (Z = M R, the multigrid V-cycle), the inner
+ * products plain sums over the grid points.  X holds the initial guess on
+ * entry; stops when every column has ||r_j|| <= rtol ||b_j|| (rtol = 0: after
+ * exactly maxit iterations).  iters (host, nullable): iterations run.
+ * Errors: HQ_ERR_NOT_CONVERGED at maxit, HQ_ERR_SINGULAR when P^T A P or
+ * Z^T R lost positive definiteness (the block lost rank: a column converged
+ * far ahead of the others).  Uses the context's PCG blocks as scratch.    */
+hq_status hq_block_pcg_coupled(hq_ctx *ctx, const void *B, void *X, double rtol, int maxit,
+                               int *iters);
+
 /* out = w A^T B (Na x Nb, row-major, FP64, device) for point-major blocks
  * A (n x Na) and B (n x Nb) on the finest grid: the inner-product matrices
  * <A,B> of Section 2.1 with w = h^3.  Na, Nb <= 2N.                        */

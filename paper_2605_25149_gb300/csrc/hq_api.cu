@@ -2278,6 +2278,103 @@ hq_status pcg_impl(hq_ctx *x, const void *B, void *X, double rtol, int maxit, in
     HQ_TRY(clear_status(x));
     return pcg<T>(x, (const T *)B, (T *)X, rtol, maxit, iters);
 }
+// The split over grid points of a Gram must fit the workspace's partial sums
+// (sized for the step's own Gram shapes): otherwise fewer, longer point chunks.
+hq_status fit_gram_plan(hq_ctx *x, GramPlan &gp) {
+    const size_t avail = std::max(gram_partial_bytes(x->gplan_max), gram_partial_bytes(x->gplan_uw));
+    if (gram_partial_bytes(gp) <= avail) return HQ_OK;
+    const size_t per_chunk = sizeof(double) * (size_t)gp.ntiles * 64 * 64;
+    const long max_chunks = (long)(avail / per_chunk);
+    if (max_chunks < 1) return fail(x, HQ_ERR_ARG, "Gram shape exceeds the workspace plan");
+    long rows = (x->n + max_chunks - 1) / max_chunks;
+    rows = (rows + 15) / 16 * 16;
+    gp.chunk_rows = rows;
+    gp.chunks = (int)((x->n + rows - 1) / rows);
+    if (gram_partial_bytes(gp) > avail)
+        return fail(x, HQ_ERR_ARG, "Gram shape exceeds the workspace plan");
+    return HQ_OK;
+}
+
+// O'Leary's block PCG (not in the paper; an alternative to the per-column
+// recurrences of pcg()): X = G B with all N columns in one block Krylov space,
+// N x N step matrices alpha = (P^T Q)^-1 (Z^T R), beta = (Z^T R)^-1 (Z'^T R'):
+//   R = B - A X, Z = M R, P = Z
+//   repeat: Q = A P, X += P alpha, R -= Q alpha, stop when every column has
+//           ||r_j|| <= rtol ||b_j||, Z' = M R, P = Z' + P beta.
+// The inner products are plain sums over the points (as the per-column
+// PCG's), formed by the SIMT Gram with FP64 accumulation; the N x N systems
+// by the FP64 SPD solves; the block updates by the step's block products.
+// Host-driven (one synchronisation per iteration for the stopping test).
+// rtol = 0 runs exactly maxit iterations.
+template <typename T>
+hq_status coupled_pcg_impl(hq_ctx *x, const T *B, T *X, double rtol, int maxit, int *iters_out) {
+    HQ_TRY(clear_status(x));
+    const int N = x->N;
+    const long n = x->n;
+    Level &v = x->lev[0];
+    const GridGeom &g = v.g;
+    T *R = (T *)x->R, *Z = (T *)x->Zp, *P = (T *)x->P, *Q = (T *)x->Q, *Tt = (T *)x->Tt;
+    GramPlan gp = make_gram_plan(n, N, N, false);
+    HQ_TRY(fit_gram_plan(x, gp));
+    auto inner = [&](const T *A, const T *Bm, double *out) {
+        launch_gram<T>(gp, A, N, nullptr, 0, Bm, N, nullptr, 0, 1.0, x->gpart, out, x->st);
+    };
+    std::vector<double> rn(N), bn(N);
+    // R = B - A X with the partial sums of r.r and b.b
+    launch_resid<T>(g, (const T *)v.Dt, (T)v.c, X, B, R, x->part, x->part2, x->st);
+    launch_colsum_sqrt(part_rows(g), N, x->part, 1.0, x->resn, x->st);
+    launch_colsum_sqrt(part_rows(g), N, x->part2, 1.0, x->mu, x->st);
+    HQ_CUDA(cudaMemcpyAsync(rn.data(), x->resn, sizeof(double) * N, cudaMemcpyDeviceToHost, x->st));
+    HQ_CUDA(cudaMemcpyAsync(bn.data(), x->mu, sizeof(double) * N, cudaMemcpyDeviceToHost, x->st));
+    HQ_CUDA(cudaStreamSynchronize(x->st));
+    auto done = [&]() {
+        if (!(rtol > 0.0)) return false;
+        for (int c = 0; c < N; c++)
+            if (!(rn[c] <= rtol * bn[c])) return false;
+        return true;
+    };
+    int it = 0;
+    if (!done() && maxit > 0) {
+        HQ_TRY(precondition<T>(x, R, Z, Tt, false, nullptr));
+        HQ_TRY(copy_blk<T>(x, P, Z, (size_t)n * N));
+        inner(Z, R, x->Ssm);   // Z^T R
+        for (it = 1; it <= maxit; it++) {
+            launch_apply<T>(g, (const T *)v.Dt, (T)v.c, P, Q, nullptr, x->st);
+            inner(P, Q, x->Ksm);   // P^T A P
+            launch_spd_solve(N, x->Ksm, N, x->Ssm, N, x->Mw, x->Lm, x->Ym, x->ipiv, x->status,
+                             x->st);   // alpha
+            // X and R in place: the block products' epilogues read Cin and
+            // write Out element by element in the same thread
+            block_gemm<T>(x, P, N, x->Ym, nullptr, 0, nullptr, X, X, false, nullptr);
+            launch_dscale(N * N, -1.0, x->Ym, x->Cm, x->st);
+            block_gemm<T>(x, Q, N, x->Cm, nullptr, 0, nullptr, R, R, false, nullptr);
+            launch_dot<T>(g, R, R, x->part, x->st);
+            launch_colsum_sqrt(g.gy, N, x->part, 1.0, x->resn, x->st);
+            HQ_CUDA(cudaMemcpyAsync(rn.data(), x->resn, sizeof(double) * N, cudaMemcpyDeviceToHost,
+                                    x->st));
+            HQ_TRY(sync_status(x, x->status, "block PCG (P^T A P)"));
+            if (done()) break;
+            HQ_TRY(precondition<T>(x, R, Z, Tt, false, nullptr));
+            inner(Z, R, x->Msm);   // Z'^T R'
+            launch_spd_solve(N, x->Ssm, N, x->Msm, N, x->Mw, x->Lm, x->Cv, x->ipiv, x->status,
+                             x->st);   // beta
+            // P' = Z' + P beta into Q's buffer (P is read while P' is written),
+            // then the two buffers swap roles
+            block_gemm<T>(x, P, N, x->Cv, nullptr, 0, nullptr, Z, Q, false, nullptr);
+            std::swap(P, Q);
+            HQ_CUDA(cudaMemcpyAsync(x->Ssm, x->Msm, sizeof(double) * N * N,
+                                    cudaMemcpyDeviceToDevice, x->st));
+        }
+        if (it > maxit) it = maxit;
+    }
+    if (iters_out) *iters_out = it;
+    HQ_TRY(sync_status(x, x->status, "block PCG"));
+    // the step's warm starts refer to the PCG buffers no longer
+    x->w_valid = false;
+    if (rtol > 0.0 && !done()) return fail(x, HQ_ERR_NOT_CONVERGED, "block PCG reached maxit");
+    return check_launch(x);
+}
+
 template <typename T>
 hq_status gram_impl(hq_ctx *x, const void *A, int Na, const void *B, int Nb, double w, double *out) {
     if (x->mixed && A == B && Na == Nb) {
@@ -2287,20 +2384,7 @@ hq_status gram_impl(hq_ctx *x, const void *A, int Na, const void *B, int Nb, dou
         return sync_status(x, x->status, "tensor-core Gram");
     }
     GramPlan gp = make_gram_plan(x->n, Na, Nb, A == B && Na == Nb);
-    // the split over grid points must fit the workspace's partial sums (sized
-    // for the step's own Gram shapes): otherwise fewer, longer point chunks
-    const size_t avail = std::max(gram_partial_bytes(x->gplan_max), gram_partial_bytes(x->gplan_uw));
-    if (gram_partial_bytes(gp) > avail) {
-        const size_t per_chunk = sizeof(double) * (size_t)gp.ntiles * 64 * 64;
-        const long max_chunks = (long)(avail / per_chunk);
-        if (max_chunks < 1) return fail(x, HQ_ERR_ARG, "Gram shape exceeds the workspace plan");
-        long rows = (x->n + max_chunks - 1) / max_chunks;
-        rows = (rows + 15) / 16 * 16;
-        gp.chunk_rows = rows;
-        gp.chunks = (int)((x->n + rows - 1) / rows);
-        if (gram_partial_bytes(gp) > avail)
-            return fail(x, HQ_ERR_ARG, "Gram shape exceeds the workspace plan");
-    }
+    HQ_TRY(fit_gram_plan(x, gp));
     launch_gram<T>(gp, (const T *)A, Na, nullptr, 0, (const T *)B, Nb, nullptr, 0, w, x->gpart, out, x->st);
     return check_launch(x);
 }
@@ -2618,6 +2702,18 @@ hq_status hq_block_pcg(hq_ctx *x, const void *B, void *X, double rtol, int maxit
     if (!x->have_V) return fail(x, HQ_ERR_STATE, "hq_set_potential has not been called");
     if (!B || !X || maxit < 0 || !(rtol >= 0.0)) return fail(x, HQ_ERR_ARG, "bad operand");
     return HQ_DISPATCH(x, pcg_impl, x, B, X, rtol, maxit, iters);
+    HQ_API_END
+}
+
+hq_status hq_block_pcg_coupled(hq_ctx *x, const void *B, void *X, double rtol, int maxit,
+                               int *iters) {
+    HQ_API_BEGIN
+    HQ_TRY(guard(x));
+    ProfScope ps_(x);
+    if (!x->have_V) return fail(x, HQ_ERR_STATE, "hq_set_potential has not been called");
+    if (!B || !X || maxit < 0 || !(rtol >= 0.0)) return fail(x, HQ_ERR_ARG, "bad operand");
+    if (x->mixed) return coupled_pcg_impl<float>(x, (const float *)B, (float *)X, rtol, maxit, iters);
+    return coupled_pcg_impl<double>(x, (const double *)B, (double *)X, rtol, maxit, iters);
     HQ_API_END
 }
 

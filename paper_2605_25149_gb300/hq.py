@@ -33,7 +33,8 @@ EXPORTED = [
     "hq_default_config", "hq_workspace_bytes", "hq_init", "hq_set_potential", "hq_set_initial",
     "hq_step", "hq_solve", "hq_eigenpairs", "hq_monitor", "hq_time_step", "hq_density",
     "hq_grad_eigs", "hq_grad_density", "hq_refine", "hq_get_state", "hq_set_state", "hq_problem_info",
-    "hq_apply_operator", "hq_mg_vcycle", "hq_block_pcg", "hq_gram", "hq_block_gemm",
+    "hq_apply_operator", "hq_mg_vcycle", "hq_block_pcg", "hq_block_pcg_coupled", "hq_gram",
+    "hq_block_gemm",
     "hq_step_trace",
     "hq_mg_smooth", "hq_mg_smooth_prescaled", "hq_mg_restrict", "hq_mg_prolong",
     "hq_mg_coarse_solve",
@@ -104,6 +105,7 @@ def load():
         "hq_apply_operator": (_I, [_P, _P, _P, _I]),
         "hq_mg_vcycle": (_I, [_P, _P, _P]),
         "hq_block_pcg": (_I, [_P, _P, _P, _D, _I, _P]),
+        "hq_block_pcg_coupled": (_I, [_P, _P, _P, _D, _I, _P]),
         "hq_gram": (_I, [_P, _P, _I, _P, _I, _D, _P]),
         "hq_block_gemm": (_I, [_P, _P, _I, _P, _P, _I, _P, _P, _P]),
         "hq_step_trace": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
@@ -436,6 +438,15 @@ class Solver:
         self._check(self.lib.hq_block_pcg(self._ctx, self._dev(B, self.n), _dptr(X), rtol, maxit,
                                           _hptr(its)), "hq_block_pcg")
         return X, its
+
+    def block_pcg_coupled(self, B, X0=None, rtol=1e-10, maxit=200):
+        """O'Leary's block PCG (N x N step matrices): (X, iterations)."""
+        X = self._torch.zeros_like(B) if X0 is None else X0.clone()
+        its = ctypes.c_int()
+        self._check(self.lib.hq_block_pcg_coupled(self._ctx, self._dev(B, self.n), self._dev(X, self.n),
+                                                  rtol, maxit, ctypes.byref(its)),
+                    "hq_block_pcg_coupled")
+        return X, its.value
 
     def gram(self, A, B, w):
         Na, Nb = A.shape[1], B.shape[1]

@@ -132,6 +132,61 @@ def test_pcg_converges_to_inverse_operator():
     np.testing.assert_array_equal(its, itso)
 
 
+@pytest.mark.parametrize("m,N,k", [(12, 1, 4), (12, 3, 1), (16, 8, 3), (19, 5, 6), (17, 40, 2)])
+def test_coupled_block_pcg_matches_oracle_iteration_by_iteration(m, N, k):
+    """O'Leary's block PCG, rtol = 0: both sides run exactly k iterations with
+    the N x N step matrices (N = 40: the blocked elimination of the small
+    solves instead of the one-CTA Cholesky)."""
+    s, V, _ = make(m, N)
+    mg = oracle_mg(s, V)
+    B = np.random.default_rng(11 + N).standard_normal((m ** 3, N))
+    X0 = np.random.default_rng(12).standard_normal((m ** 3, N)) * 1e-2
+    X, its = s.block_pcg_coupled(dev(B), dev(X0), rtol=0.0, maxit=k)
+    Xo, itso = mg.block_pcg(B, X0, rtol=0.0, maxit=k)
+    assert its == k and itso == k
+    assert rel(host(X), Xo) < 1e-10
+
+
+def test_coupled_block_pcg_converges_with_the_oracle_count():
+    m, N = 24, 12
+    s, V, _ = make(m, N)
+    sigma = s.info()["sigma"]
+    B = np.random.default_rng(9).standard_normal((m ** 3, N))
+    X, its = s.block_pcg_coupled(dev(B), rtol=1e-11, maxit=200)
+    X = host(X)
+    res = np.linalg.norm(B - O.apply_h(m, inputs.grid_h(m), V, sigma, X), axis=0)
+    assert (res <= 2e-11 * np.linalg.norm(B, axis=0)).all()
+    _, itso = oracle_mg(s, V).block_pcg(B, rtol=1e-11, maxit=200)
+    assert abs(its - itso) <= 1
+    # the block Krylov space holds every column's: no more iterations than
+    # the slowest column of the per-column PCG
+    _, itc = s.block_pcg(dev(B), rtol=1e-11, maxit=200)
+    assert its <= itc.max()
+
+
+def test_coupled_block_pcg_mixed_and_errors():
+    from paper_2605_25149_gb300 import hq
+    torch = torch_mod()
+    m, N = 20, 8
+    s, V, _ = make(m, N, precision="mixed", cg_rtol=1e-6)
+    sigma = s.info()["sigma"]
+    B = np.random.default_rng(4).standard_normal((m ** 3, N)).astype(np.float32)
+    X, its = s.block_pcg_coupled(dev(B), rtol=1e-5, maxit=100)
+    assert 0 < its < 100
+    res = np.linalg.norm(B - O.apply_h(m, inputs.grid_h(m), V, sigma, host(X)), axis=0)
+    assert (res <= 2e-5 * np.linalg.norm(B.astype(np.float64), axis=0)).all()
+    with pytest.raises(hq.HQError) as ei:
+        s.block_pcg_coupled(dev(B), rtol=1e-12, maxit=2)
+    assert ei.value.status == 7   # HQ_ERR_NOT_CONVERGED
+    with pytest.raises(hq.HQError) as ei:
+        s.block_pcg_coupled(dev(B), rtol=-1.0, maxit=2)
+    assert ei.value.status == 1   # HQ_ERR_ARG
+    # a zero right-hand side is solved before the first iteration
+    Z = torch.zeros((m ** 3, N), dtype=torch.float32, device="cuda")
+    X, its = s.block_pcg_coupled(Z, rtol=1e-6, maxit=5)
+    assert its == 0 and float(X.abs().max()) == 0.0
+
+
 @pytest.mark.parametrize("m,Na,Nb", [(10, 3, 3), (16, 16, 9), (17, 70, 128), (12, 1, 5)])
 def test_gram_matches_oracle(m, Na, Nb):
     N = max(Na, Nb)
