@@ -367,7 +367,7 @@ def run_ttr(args):
     common = dict(tau=w["tau"], adaptive_tau=1, tau_max=args.tau_max)
     clk = ClockSampler(0)
     clk.start()
-    s = hq.Solver(m, N, cg_rtol=w["cg_rtol"], precision="fp64", mg_fp32=1, **common)
+    s = hq.Solver(m, N, cg_rtol=w["cg_rtol"], precision="fp64", mg_fp32=1, **common, **nu_kw(w))
     s.set_potential(V)
     s.set_initial(U0)
     h64 = solve_history(torch, s, w["eps"], chunk, args.ttr_steps)
@@ -383,7 +383,7 @@ def run_ttr(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     U, st = sm.state_device()
-    s4 = hq.Solver(m, N, cg_rtol=w["cg_rtol"], precision="fp64", mg_fp32=1, **common)
+    s4 = hq.Solver(m, N, cg_rtol=w["cg_rtol"], precision="fp64", mg_fp32=1, **common, **nu_kw(w))
     s4.set_potential(V)
     s4.set_state_device(U, st)
     torch.cuda.synchronize()
@@ -630,9 +630,14 @@ def bench_large(torch, hq, inputs, K, W, hbm_peak, hbm_kind, shape=(128, 256)):
     return out
 
 
+def nu_kw(w):
+    """Damped-Jacobi sweeps per level of a workload's V-cycle (default 2)."""
+    return {"mg_nu1": w["mg_nu"], "mg_nu2": w["mg_nu"]} if w.get("mg_nu") else {}
+
+
 def solver_kw(w):
     """Solver options of a workload."""
-    kw = dict(tau=w["tau"], cg_rtol=w["cg_rtol"], precision=w["precision"])
+    kw = dict(tau=w["tau"], cg_rtol=w["cg_rtol"], precision=w["precision"], **nu_kw(w))
     if w.get("mg_fp32"):
         kw["mg_fp32"] = 1
     return kw
@@ -688,7 +693,7 @@ def ttr_live(torch, hq, inputs, args):
         s = hq.Solver(m, N, **common, **prec_kw)
         s.set_potential(V)
         s.set_initial(U0)
-        s64 = hq.Solver(m, N, cg_rtol=w["cg_rtol"], precision="fp64", mg_fp32=1, **common)
+        s64 = hq.Solver(m, N, cg_rtol=w["cg_rtol"], precision="fp64", mg_fp32=1, **common, **nu_kw(w))
         s64.set_potential(V)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push(label)
@@ -745,7 +750,7 @@ def ttr_live(torch, hq, inputs, args):
                                     "reached": bool(err <= 1e-6)}
     del sm
     torch.cuda.empty_cache()
-    s64, sr64, res_f = leg(dict(precision="fp64", cg_rtol=w["cg_rtol"], mg_fp32=1), "ttr_fp64")
+    s64, sr64, res_f = leg(dict(precision="fp64", cg_rtol=w["cg_rtol"], mg_fp32=1, **nu_kw(w)), "ttr_fp64")
     lam64 = sr64.eigenpairs()["lam_rr"]
     res_f["eig_agreement_with_mixed_refined"] = float(np.max(np.abs(lam64 - lam_ref) /
                                                              np.abs(lam_ref)))

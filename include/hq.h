@@ -124,7 +124,11 @@ size_t hq_workspace_bytes(const hq_config *cfg);
  * HQ_FUSED_COARSE=0 runs every level of the FP32 V-cycles (HQ_MIXED, mg_fp32)
  * as separate kernels (by default the levels from the first one whose
  * vectors fit one CTA's shared memory, about 16^3 points, down to the
- * coarsest run as one launch, one CTA per column).                        */
+ * coarsest run as one launch, one CTA per column).  HQ_LOG=<path> appends
+ * one JSON line per hq_step call to <path> (context, step counter, steps
+ * taken, g, inner PCG solves and iterations, wall ms, status); it makes
+ * every hq_step call synchronise.  Every public call is an NVTX range named
+ * after the call.                                                          */
 hq_status hq_init(const hq_config *cfg, void *d_workspace, size_t bytes,
                   void *cuda_stream, hq_ctx **out);
 

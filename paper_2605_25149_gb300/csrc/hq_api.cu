@@ -15,6 +15,7 @@
 // host reads back one scalar per PCG iteration (number of active columns) and
 // one per step (g) and never allocates device memory after hq_init.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <chrono>
@@ -22,6 +23,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -2448,7 +2450,35 @@ hq_status set_state_impl(hq_ctx *x, const double *U, const double *Zw, int on_de
 
 }  // namespace
 
-#define HQ_API_BEGIN try {
+// HQ_LOG=<path>: every hq_step call appends one JSON line to <path> (the
+// context, its step counter, the steps taken, the gradient norm g, the inner
+// PCG solves and iterations of the call, its wall time in ms, the status).
+struct StepLog {
+    FILE *f = nullptr;
+    std::mutex mu;
+    StepLog() {
+        const char *p = std::getenv("HQ_LOG");
+        if (p && *p) f = std::fopen(p, "a");
+    }
+    ~StepLog() {
+        if (f) std::fclose(f);
+    }
+};
+StepLog &step_log() {
+    static StepLog l;
+    return l;
+}
+
+// Every public call is an NVTX range named after the call (header-only NVTX:
+// a no-op unless a profiler is attached), so a timeline shows the library's
+// calls around their kernels.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+#define HQ_API_BEGIN      \
+    NvtxRange nvtx_(__func__); \
+    try {
 #define HQ_API_END                                                   \
     }                                                                \
     catch (...) {                                                    \
@@ -2562,7 +2592,27 @@ hq_status hq_step(hq_ctx *x, int nsteps, double *resid_out) {
     HQ_TRY(guard(x));
     ProfScope ps_(x);
     if (nsteps < 0) return fail(x, HQ_ERR_ARG, "nsteps < 0");
-    return HQ_DISPATCH(x, step_impl, x, nsteps, resid_out);
+    StepLog &lg = step_log();
+    if (!lg.f) return HQ_DISPATCH(x, step_impl, x, nsteps, resid_out);
+    // per-call record: the gradient norm is read back (one synchronisation)
+    HQ_TRY(fold_graph_counts(x));
+    const long s0 = x->stat_solves, i0 = x->stat_iters;
+    const auto t0 = std::chrono::steady_clock::now();
+    double g = NAN;
+    const hq_status st = HQ_DISPATCH(x, step_impl, x, nsteps, &g);
+    if (st == HQ_OK) HQ_CUDA(cudaStreamSynchronize(x->st));
+    const double ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (st == HQ_OK) HQ_TRY(fold_graph_counts(x));
+    if (resid_out) *resid_out = g;
+    std::lock_guard<std::mutex> lk(lg.mu);
+    std::fprintf(lg.f,
+                 "{\"ctx\": \"%p\", \"step\": %ld, \"nsteps\": %d, \"g\": %.17g, "
+                 "\"pcg_solves\": %ld, \"pcg_iterations\": %ld, \"ms\": %.4f, \"status\": %d}\n",
+                 (void *)x, x->step, nsteps, std::isfinite(g) ? g : -1.0, x->stat_solves - s0,
+                 x->stat_iters - i0, ms, (int)st);
+    std::fflush(lg.f);
+    return st;
     HQ_API_END
 }
 

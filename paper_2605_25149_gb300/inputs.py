@@ -66,7 +66,7 @@ WORKLOADS = {
     "harmonic16_N8": dict(m=16, N=8, potential=("harmonic", None), u0_seed=1, tau=0.5,
                           precision="fp64", cg_rtol=1e-10, eps=1e-8, mg_fp32=1),
     "wells64_N64": dict(m=64, N=64, potential=("wells", 2), u0_seed=102, tau=0.4,
-                        precision="fp64", cg_rtol=1e-10, eps=1e-8, mg_fp32=1),
+                        precision="fp64", cg_rtol=1e-10, eps=1e-8, mg_fp32=1, mg_nu=3),
     "wells128_N256": dict(m=128, N=256, potential=("wells", 3), u0_seed=103, tau=0.4,
                           precision="mixed", cg_rtol=1e-6, eps=1e-5),
     "wells64_N32": dict(m=64, N=32, potential=("wells", 5), u0_seed=105, tau=0.4,

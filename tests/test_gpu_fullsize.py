@@ -45,8 +45,9 @@ def test_full_size_step_on_samples(name, res_tol, gram_tol, row_tol):
     n = m ** 3
     solvers = []
     for _ in range(2):
+        nu = {"mg_nu1": w["mg_nu"], "mg_nu2": w["mg_nu"]} if w.get("mg_nu") else {}
         s = hq.Solver(m, N, tau=tau, cg_rtol=w["cg_rtol"], precision=w["precision"],
-                      mg_fp32=w.get("mg_fp32", 0))
+                      mg_fp32=w.get("mg_fp32", 0), **nu)
         s.set_potential(V)
         s.set_initial(U0)
         s.step(2)

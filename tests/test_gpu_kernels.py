@@ -276,11 +276,16 @@ def test_mixed_operator_and_vcycle_match_oracle(m, N):
                                                ("mixed", 12, 80, 80, 0, 2e-6),
                                                ("mixed", 10, 9, 9, 9, 2e-6),
                                                ("mixed", 11, 40, 40, 33, 2e-6),
-                                               ("mixed", 12, 256, 256, 256, 2e-6)])
+                                               ("mixed", 12, 256, 256, 256, 2e-6),
+                                               ("mixed", 13, 128, 128, 128, 2e-6),
+                                               ("mixed", 11, 128, 128, 0, 2e-6),
+                                               ("mixed", 9, 256, 256, 40, 2e-6),
+                                               ("mixed", 10, 128, 128, 7, 2e-6)])
 def test_block_gemm_matches_numpy(prec, m, N, k1, k2, tol):
     """Out = A1 M1 + A2 M2 + Cin, the products of the predictor / corrector
     updates: SIMT FP64, or tcgen05 3xTF32 in mixed precision (ragged tile
-    widths and K not a multiple of 32 included)."""
+    widths and K not a multiple of 32 included; 128 and 256 output columns
+    with ragged point blocks)."""
     torch = torch_mod()
     s, V, _ = make(m, N, precision=prec, cg_rtol=1e-10 if prec == "fp64" else 1e-6)
     rng = np.random.default_rng(N + k1 + k2)

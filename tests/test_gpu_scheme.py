@@ -135,8 +135,12 @@ def test_solve_reports_not_converged_and_keeps_state():
     s.step(1)
 
 
-def test_mixed_step_tracks_fp64_oracle():
-    m, N, tau = 12, 6, 0.4
+@pytest.mark.parametrize("m,N", [(12, 6), (12, 128)])
+def test_mixed_step_tracks_fp64_oracle(m, N):
+    """One mixed step against the FP64 oracle's step; N = 128 takes full
+    128-column tiles in the tensor-core block products (the gradient
+    residual with its fused sum of squares included)."""
+    tau = 0.4
     s, V, U0 = make(m, N, precision="mixed", tau=tau, cg_rtol=1e-7, cg_maxit=400)
     sigma = s.info()["sigma"]
     Ug0 = s.get_state()[0]
