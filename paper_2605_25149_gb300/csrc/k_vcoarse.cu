@@ -34,10 +34,21 @@ __device__ __forceinline__ float nbr6(const float *x, int p, int i, int j, int k
     return ((a0 + a1) + (a2 + a3)) + (a4 + a5);
 }
 
+// a / d for 0 <= a < 2^22 and 1 <= d < 2^12: the quotient through the FP32
+// reciprocal (relative error below 2^-23, so at most one off) and one
+// correction step; a few instructions instead of an integer division's
+// sequence, which dominated this kernel's index set-up per pass
+__device__ __forceinline__ int fdiv(int a, int d) {
+    int q = __float2int_rz(__int2float_rn(a) * __frcp_rn(__int2float_rn(d)));
+    const int r = a - q * d;
+    q += r < 0 ? -1 : (r >= d ? 1 : 0);
+    return q;
+}
+
 __device__ __forceinline__ void decomp(int p, int m, int &i, int &j, int &k) {
-    const int q = p / m;
+    const int q = fdiv(p, m);
     i = p - q * m;
-    k = q / m;
+    k = fdiv(q, m);
     j = q - k * m;
 }
 
@@ -113,8 +124,10 @@ __device__ void sm_axis(int o2, int o1, int o0, int ilen, int axis, const int *i
     const bool unit = scale == 1.f;
     // (i0, i1, i2) of p = t, t + S, ... by carries (one set of divisions)
     const int S = blockDim.x;
-    int i0 = threadIdx.x % o0, i1 = (threadIdx.x / o0) % o1, i2 = threadIdx.x / (o0 * o1);
-    const int s0 = S % o0, s1d = (S / o0) % o1, s2d = S / (o0 * o1);
+    const int t = threadIdx.x;
+    const int tq = fdiv(t, o0), sq = fdiv(S, o0);
+    int i0 = t - tq * o0, i2 = fdiv(tq, o1), i1 = tq - i2 * o1;
+    const int s0 = S - sq * o0, s2d = fdiv(sq, o1), s1d = sq - s2d * o1;
     for (int p = threadIdx.x; p < nout; p += S) {
         if (p != (int)threadIdx.x) {
             i0 += s0;
@@ -355,7 +368,7 @@ __global__ void __launch_bounds__(VC_THREADS) k_vcoarse(VCoarse v, int N, const 
     // the sum over chunks k (in order) of r . z at p = row TY ppt + k TY + y
     double *red = cpart + 8 * v.nc;
     for (int t = threadIdx.x; t < gy * TY; t += blockDim.x) {
-        const int row = t / TY, y = t - row * TY;
+        const int row = fdiv(t, TY), y = t - row * TY;
         double acc = 0.0;
         for (int k = 0; k < ppt; k++) {
             const long p = (long)row * TY * ppt + (long)k * TY + y;
