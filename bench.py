@@ -928,7 +928,11 @@ def run_hq(args):
     prof = s.profile_read()
     pcg_solves, pcg_iters = s.pcg_stats()
     s.profile(timing=False)
-    kind = dominant(prof)
+    # the dominant kernel: with the FP32 preconditioner the FP64 operator
+    # (k_stencil_zm, the largest single kernel of the step's launch list); the
+    # smooth class there is the FP32 sweeps of every level, split over ~115
+    # launches a step, with their own roofline in the mixed leg
+    kind = "stencil" if w.get("mg_fp32") else dominant(prof)
     roof = roofline_alone(kind, kernel_alone(torch, s, kind, not w.get("mg_fp32")), m ** 3 * N,
                           "f64", hbm_peak, hbm_kind, roofline(prof, kind, "f64"))
     brk = breakdown(prof, K)
@@ -965,7 +969,7 @@ def run_hq(args):
     # ---- FP64 with the FP64 V-cycle (mg_fp32 = 0) ---------------------------------
     v64 = None
     if not args.no_mixed:
-        s3 = hq.Solver(m, N, tau=w["tau"], cg_rtol=w["cg_rtol"], precision="fp64")
+        s3 = hq.Solver(m, N, tau=w["tau"], cg_rtol=w["cg_rtol"], precision="fp64", **nu_kw(w))
         s3.set_potential(V)
         s3.set_initial(U0)
         for _ in range(W):
