@@ -57,7 +57,10 @@ FP64_OPS = {"smooth": 7.0, "stencil": 8.0, "residual": 7.0}
 # of that launch): keys (class, dtype); an entry is removed whenever its
 # kernel changes, until it is captured again.
 TRAFFIC_PER_ELEMENT = {("smooth", "f32"): (136.215040e6 + 44.029440e6) / 16777216,
-                       ("stencil", "f64"): (136.483584e6 + 96.978432e6) / 16777216}
+                       ("stencil", "f64"): (136.483584e6 + 96.978432e6) / 16777216,
+                       # the z-marching FP32 sweep (blocks of 100 MB or more),
+                       # captured on 64^3 x 256 and scaled by point-columns
+                       ("smooth_zm", "f32"): (553.649408e6 + 240.579328e6) / 67108864}
 
 
 def peaks():
@@ -619,7 +622,9 @@ def bench_large(torch, hq, inputs, K, W, hbm_peak, hbm_kind, shape=(128, 256)):
     kind = dominant(prof) or "smooth"
     roof = roofline_alone(kind, kernel_alone(torch, s, kind, False, reps=10), m ** 3 * N, "f32",
                           hbm_peak, hbm_kind, roofline(prof, kind, "f32"))
-    roof["traffic"] = None
+    # the block (>= 100 MB) runs the z-marching sweep: its own capture
+    zm = TRAFFIC_PER_ELEMENT.get((kind + "_zm", "f32"))
+    roof["traffic"] = zm * m ** 3 * N if (zm is not None and 4 * m ** 3 * N >= 100e6) else None
     out = {"workload": "wells: %d^3 grid, V=|x|^2/2 + 8 wells (default_rng(3)), "
                        "N=%d, tau=0.4, mixed, PCG rtol 1e-6" % (m, N),
            "ms_per_step": ms, "value": 1000.0 / ms, "unit": "steps/s", "roofline": roof,
