@@ -203,9 +203,40 @@ __host__ __device__ inline size_t vc_floats(const VCoarse &v) {
     return (f + 1) & ~(size_t)1;
 }
 
-struct LevelSmem {
-    float *r, *a, *b;
-};
+// Shared-memory offsets (floats) of the layout above, computed where they
+// are used: the pointers the sweeps get are then visibly derived from the
+// shared array (shared-memory loads and stores, no per-level pointer tables
+// in local memory)
+__device__ __forceinline__ int vc_n(const VCoarse &v, int l) { return v.m[l] * v.m[l] * v.m[l]; }
+__device__ __forceinline__ int vc_ntot(const VCoarse &v) {
+    int s = 0;
+    for (int l = 0; l < v.levels; l++) s += vc_n(v, l);
+    return s;
+}
+// r, a, b of level l: 3 sum_{i<l} n_i + {0, n_l, 2 n_l}
+__device__ __forceinline__ int vc_rab(const VCoarse &v, int l) {
+    int s = 0;
+    for (int i = 0; i < l; i++) s += vc_n(v, i);
+    return 3 * s;
+}
+// D, wD of level l: 3 n_tot + 2 sum_{i<l} n_i + {0, n_l}
+__device__ __forceinline__ int vc_dw(const VCoarse &v, int l, int ntot) {
+    int s = 0;
+    for (int i = 0; i < l; i++) s += vc_n(v, i);
+    return 3 * ntot + 2 * s;
+}
+// transfer temporaries
+__device__ __forceinline__ int vc_tmp1(int ntot) { return 5 * ntot; }
+__device__ __forceinline__ int vc_tmp2(const VCoarse &v, int ntot) {
+    return 5 * ntot + (v.levels > 1 ? v.m[0] * v.m[0] * v.m[1] : 0);
+}
+// taps of level pair l -> l + 1: ridx (6 m_{l+1} ints), rw (6 m_{l+1}),
+// pidx (2 m_l ints), pw (2 m_l)
+__device__ __forceinline__ int vc_taps(const VCoarse &v, int l, int ntot) {
+    int s = vc_tmp2(v, ntot) + (v.levels > 1 ? v.m[0] * v.m[1] * v.m[1] : 0);
+    for (int i = 0; i < l; i++) s += 2 * XFER_RTAPS * v.m[i + 1] + 4 * v.m[i];
+    return s;
+}
 
 // MG64 = false: r, z are FP32 blocks (rin, zout).  MG64 = true (the whole
 // V-cycle of an FP32 preconditioner inside an FP64 PCG): r is read from the
@@ -215,29 +246,19 @@ struct LevelSmem {
 // per thread row, ppt chunks, gy partial rows: the same terms in the same
 // order, so the values equal d2f + V-cycle + widen bit for bit)
 template <bool MG64>
-__global__ void __launch_bounds__(VC_THREADS) k_vcoarse(VCoarse v, int N, const float *__restrict__ rin,
-                                                        float *__restrict__ zout,
-                                                        const double *__restrict__ r64,
-                                                        double *__restrict__ z64, double *part,
-                                                        int TY, int ppt, int gy) {
+__global__ void __launch_bounds__(VC_THREADS)
+    k_vcoarse(const __grid_constant__ VCoarse v, int N, const float *__restrict__ rin,
+              float *__restrict__ zout, const double *__restrict__ r64, double *__restrict__ z64,
+              double *part, int TY, int ppt, int gy) {
     extern __shared__ __align__(16) float vsm[];
     const int col = blockIdx.x;
     const int Lf = v.levels;   // levels in this launch: l0 .. l0 + Lf - 1 (last = coarsest)
-    LevelSmem lv[VC_MAXLEV];
-    const float *Ds[VC_MAXLEV], *wDs[VC_MAXLEV];
-    const int *rid[VC_MAXLEV], *pid[VC_MAXLEV];
-    const float *rws[VC_MAXLEV], *pws[VC_MAXLEV];
-    float *q = vsm;
+    const int ntot = vc_ntot(v);
+    int *const vsi = reinterpret_cast<int *>(vsm);
+    // level tables: D and omega / D of every level, the transfer taps
     for (int l = 0; l < Lf; l++) {
-        const int n = v.m[l] * v.m[l] * v.m[l];
-        lv[l].r = q;
-        lv[l].a = q + n;
-        lv[l].b = q + 2 * n;
-        q += 3 * n;
-    }
-    for (int l = 0; l < Lf; l++) {
-        const int n = v.m[l] * v.m[l] * v.m[l];
-        float *d = q, *w = q + n;
+        const int n = vc_n(v, l);
+        float *d = vsm + vc_dw(v, l, ntot), *w = d + n;
         // four points per thread in flight: loads first, then the stores
         for (int p0 = threadIdx.x; p0 < n; p0 += 4 * blockDim.x) {
             float a[4], b[4];
@@ -256,19 +277,14 @@ __global__ void __launch_bounds__(VC_THREADS) k_vcoarse(VCoarse v, int N, const 
                 }
             }
         }
-        Ds[l] = d;
-        wDs[l] = w;
-        q += 2 * n;
     }
-    float *tmp1 = q;
-    float *tmp2 = q + (Lf > 1 ? v.m[0] * v.m[0] * v.m[1] : 0);
-    q = tmp2 + (Lf > 1 ? v.m[0] * v.m[1] * v.m[1] : 0);
     for (int l = 0; l + 1 < Lf; l++) {
         const int mf = v.m[l], mc = v.m[l + 1];
-        int *ri = reinterpret_cast<int *>(q);
-        float *rw = q + XFER_RTAPS * mc;
-        int *pi = reinterpret_cast<int *>(q + 2 * XFER_RTAPS * mc);
-        float *pw = q + 2 * XFER_RTAPS * mc + 2 * mf;
+        const int o = vc_taps(v, l, ntot);
+        int *ri = vsi + o;
+        float *rw = vsm + o + XFER_RTAPS * mc;
+        int *pi = vsi + o + 2 * XFER_RTAPS * mc;
+        float *pw = vsm + o + 2 * XFER_RTAPS * mc + 2 * mf;
         for (int t = threadIdx.x; t < XFER_RTAPS * mc; t += blockDim.x) {
             ri[t] = __ldg(v.ridx[l] + t);
             rw[t] = __ldg(v.rw[l] + t);
@@ -277,16 +293,14 @@ __global__ void __launch_bounds__(VC_THREADS) k_vcoarse(VCoarse v, int N, const 
             pi[t] = __ldg(v.pidx[l] + t);
             pw[t] = __ldg(v.pw[l] + t);
         }
-        rid[l] = ri;
-        rws[l] = rw;
-        pid[l] = pi;
-        pws[l] = pw;
-        q += 2 * XFER_RTAPS * mc + 4 * mf;
     }
     double *cpart = reinterpret_cast<double *>(vsm + vc_floats(v));
+    float *const tmp1 = vsm + vc_tmp1(ntot);
+    float *const tmp2 = vsm + vc_tmp2(v, ntot);
     // right-hand side of level l0 (column `col` of a point-major n0 x N block)
     {
-        const int n0 = v.m[0] * v.m[0] * v.m[0];
+        const int n0 = vc_n(v, 0);
+        float *r0 = vsm + vc_rab(v, 0);
         for (int p0 = threadIdx.x; p0 < n0; p0 += 4 * blockDim.x) {
             float a[4];
 #pragma unroll
@@ -298,50 +312,66 @@ __global__ void __launch_bounds__(VC_THREADS) k_vcoarse(VCoarse v, int N, const 
 #pragma unroll
             for (int u = 0; u < 4; u++) {
                 const int p = p0 + u * blockDim.x;
-                if (p < n0) lv[0].r[p] = a[u];
+                if (p < n0) r0[p] = a[u];
             }
         }
     }
     __syncthreads();
-    // down: pre-smoothing, residual, restriction
-    float *cur[VC_MAXLEV];
+    // down: pre-smoothing, residual, restriction.  in_b: bit l set when
+    // level l's pre-smoothed iterate ended in b (else in a)
+    unsigned in_b = 0;
     for (int l = 0; l + 1 < Lf; l++) {
-        const int m = v.m[l], mc = v.m[l + 1];
-        float *c0 = lv[l].a, *o0 = lv[l].b;
-        sm_first(m, wDs[l], lv[l].r, c0);
+        const int m = v.m[l], mc = v.m[l + 1], n = vc_n(v, l);
+        const int orab = vc_rab(v, l), odw = vc_dw(v, l, ntot), ot = vc_taps(v, l, ntot);
+        const float *r = vsm + orab, *D = vsm + odw, *wD = vsm + odw + n;
+        float *c0 = vsm + orab + n, *o0 = vsm + orab + 2 * n;
+        bool cb = false;
+        sm_first(m, wD, r, c0);
         __syncthreads();
         for (int s = 1; s < v.nu1; s++) {
-            sm_jacobi(m, wDs[l], v.c[l], v.omw, lv[l].r, c0, o0);
+            sm_jacobi(m, wD, v.c[l], v.omw, r, c0, o0);
             __syncthreads();
             float *t = c0;
             c0 = o0;
             o0 = t;
+            cb = !cb;
         }
-        sm_resid(m, Ds[l], v.c[l], c0, lv[l].r, o0);
+        sm_resid(m, D, v.c[l], c0, r, o0);
         __syncthreads();
-        sm_axis<XFER_RTAPS>(m, m, mc, m, 0, rid[l], rws[l], 1.f, o0, nullptr, tmp1);
+        const int *ri = vsi + ot;
+        const float *rw = vsm + ot + XFER_RTAPS * mc;
+        sm_axis<XFER_RTAPS>(m, m, mc, m, 0, ri, rw, 1.f, o0, nullptr, tmp1);
         __syncthreads();
-        sm_axis<XFER_RTAPS>(m, mc, mc, m, 1, rid[l], rws[l], 1.f, tmp1, nullptr, tmp2);
+        sm_axis<XFER_RTAPS>(m, mc, mc, m, 1, ri, rw, 1.f, tmp1, nullptr, tmp2);
         __syncthreads();
-        sm_axis<XFER_RTAPS>(mc, mc, mc, m, 2, rid[l], rws[l], v.rscale[l], tmp2, nullptr,
-                            lv[l + 1].r);
+        sm_axis<XFER_RTAPS>(mc, mc, mc, m, 2, ri, rw, v.rscale[l], tmp2, nullptr,
+                            vsm + vc_rab(v, l + 1));
         __syncthreads();
-        cur[l] = c0;
+        if (cb) in_b |= 1u << l;
     }
     // coarsest solve
-    sm_coarse(v.nc, v.Ainv, lv[Lf - 1].r, lv[Lf - 1].a, cpart);
+    {
+        const int oc = vc_rab(v, Lf - 1), nc = vc_n(v, Lf - 1);
+        sm_coarse(v.nc, v.Ainv, vsm + oc, vsm + oc + nc, cpart);
+    }
     __syncthreads();
-    float *zc = lv[Lf - 1].a;   // the finished correction of the level below
+    // the finished correction of the level below
+    float *zc = vsm + vc_rab(v, Lf - 1) + vc_n(v, Lf - 1);
     // up: prolongation added to the pre-smoothed iterate, post-smoothing
     for (int l = Lf - 2; l >= 0; l--) {
-        const int m = v.m[l], mc = v.m[l + 1];
-        float *c0 = cur[l];
-        float *o0 = (c0 == lv[l].a) ? lv[l].b : lv[l].a;
-        sm_axis<2>(m, mc, mc, mc, 2, pid[l], pws[l], 1.f, zc, nullptr, tmp2);
+        const int m = v.m[l], mc = v.m[l + 1], n = vc_n(v, l);
+        const int orab = vc_rab(v, l), odw = vc_dw(v, l, ntot), ot = vc_taps(v, l, ntot);
+        const float *r = vsm + orab, *wD = vsm + odw + n;
+        float *a = vsm + orab + n, *b = vsm + orab + 2 * n;
+        float *c0 = ((in_b >> l) & 1u) ? b : a;
+        float *o0 = ((in_b >> l) & 1u) ? a : b;
+        const int *pi = vsi + ot + 2 * XFER_RTAPS * mc;
+        const float *pw = vsm + ot + 2 * XFER_RTAPS * mc + 2 * m;
+        sm_axis<2>(m, mc, mc, mc, 2, pi, pw, 1.f, zc, nullptr, tmp2);
         __syncthreads();
-        sm_axis<2>(m, m, mc, mc, 1, pid[l], pws[l], 1.f, tmp2, nullptr, tmp1);
+        sm_axis<2>(m, m, mc, mc, 1, pi, pw, 1.f, tmp2, nullptr, tmp1);
         __syncthreads();
-        sm_axis<2>(m, m, m, mc, 0, pid[l], pws[l], 1.f, tmp1, c0, o0);
+        sm_axis<2>(m, m, m, mc, 0, pi, pw, 1.f, tmp1, c0, o0);
         __syncthreads();
         {
             float *t = c0;
@@ -349,7 +379,7 @@ __global__ void __launch_bounds__(VC_THREADS) k_vcoarse(VCoarse v, int N, const 
             o0 = t;
         }
         for (int s = 0; s < v.nu2; s++) {
-            sm_jacobi(m, wDs[l], v.c[l], v.omw, lv[l].r, c0, o0);
+            sm_jacobi(m, wD, v.c[l], v.omw, r, c0, o0);
             __syncthreads();
             float *t = c0;
             c0 = o0;
@@ -357,7 +387,7 @@ __global__ void __launch_bounds__(VC_THREADS) k_vcoarse(VCoarse v, int N, const 
         }
         zc = c0;
     }
-    const int n0 = v.m[0] * v.m[0] * v.m[0];
+    const int n0 = vc_n(v, 0);
     if (!MG64) {
         for (int p = threadIdx.x; p < n0; p += blockDim.x) zout[(size_t)p * N + col] = zc[p];
         return;
