@@ -2022,18 +2022,28 @@ hq_status level_check(hq_ctx *x, int level, bool need_next) {
 // ---------------------------------------------------------------------------
 // differentiation (FP64 contexts)
 // ---------------------------------------------------------------------------
-// y <- P y = y - u (h^3 u^T y), u = Ritz vectors (in Uh)
-hq_status project(hq_ctx *x, double *y) {
+// y <- P y = y - u (h^3 u^T y), u = Ritz vectors (in Uh).  u^T y by the
+// SIMT FP64 Gram for solves to rtol below 1e-8: y is kept in range(P), so
+// u^T y is at the rounding level of |u| |y|, while the digit-sliced
+// tensor-core Gram's error is bounded by the columns' largest entries times
+// the number of points (~3e-11 of |u| |y| at 64^3 for localised u), which let
+// the Krylov space of a 1e-11 adjoint solve leak into span(u) and stall.  A
+// looser solve (the refinement's inexact Newton steps) takes the tensor-core
+// Gram of [u y] (rows 0..N-1, columns N..2N-1 of the 2N x 2N result, in the
+// predictor scratch, unused outside a step).
+hq_status project(hq_ctx *x, double *y, double rtol = 0.0) {
     const int N = x->N;
     const double *u = (const double *)x->Uh;
-    // u^T y by the SIMT FP64 Gram: y is kept in range(P), so u^T y is at the
-    // rounding level of |u| |y|; the digit-sliced tensor-core Gram, whose
-    // error is bounded by the columns' largest entries times the number of
-    // points (~3e-11 of |u| |y| at 64^3 for localised u), let the Krylov
-    // space of a 1e-11 adjoint solve leak into span(u) and stall
-    GramPlan gp = make_gram_plan(x->n, N, N, false);
-    launch_gram<double>(gp, u, N, nullptr, 0, y, N, nullptr, 0, x->h3, x->gpart, x->Ksm, x->st);
-    launch_extract(N, N, -1.0, x->Ksm, N, x->Msm, N, x->st);
+    const double na = 2.0 * N;
+    if (rtol >= 1e-8 && x->ozgram && gram_oz_supported(2 * N) &&
+        use_oz(x, 0.5 * (double)x->n * na * na)) {
+        launch_gram_oz(x->n, u, N, y, N, x->h3, x->ozgram, x->Mw, x->status, x->st);
+        launch_extract(N, N, -1.0, x->Mw + N, 2 * N, x->Msm, N, x->st);
+    } else {
+        GramPlan gp = make_gram_plan(x->n, N, N, false);
+        launch_gram<double>(gp, u, N, nullptr, 0, y, N, nullptr, 0, x->h3, x->gpart, x->Ksm, x->st);
+        launch_extract(N, N, -1.0, x->Ksm, N, x->Msm, N, x->st);
+    }
     block_gemm<double>(x, u, N, x->Msm, nullptr, 0, nullptr, y, y, false, nullptr);
     return check_launch(x);
 }
@@ -2100,14 +2110,14 @@ hq_status projected_pcg(hq_ctx *x, const double *b, double *xi, const double *sh
     HQ_CUDA(cudaStreamSynchronize(x->st));
     if (nact > 0) {
         HQ_TRY(precondition<double>(x, R, Zp, Tt, false, nullptr));
-        HQ_TRY(project(x, Zp));
+        HQ_TRY(project(x, Zp, rtol));
         launch_dot<double>(g, R, Zp, x->part, x->st);
         launch_finalize(FIN_RZ, N, g.gy, x->part, nullptr, sc, rtol, x->st);
         HQ_TRY(copy_blk<double>(x, P, Zp, cnt));
         for (it = 1; it <= maxit; it++) {
             launch_apply<double>(g, v.D, v.c, P, Q, nullptr, x->st);
             launch_shift_cols(n, N, shifts, P, Q, x->st);
-            HQ_TRY(project(x, Q));
+            HQ_TRY(project(x, Q, rtol));
             launch_dot<double>(g, P, Q, x->part, x->st);
             launch_finalize(FIN_ALPHA, N, g.gy, x->part, nullptr, sc, rtol, x->st);
             launch_pcg_xr<double>(g, sc.alpha, P, Q, xi, R, x->part, v.wD, nullptr, x->st);
@@ -2117,7 +2127,7 @@ hq_status projected_pcg(hq_ctx *x, const double *b, double *xi, const double *sh
             HQ_CUDA(cudaStreamSynchronize(x->st));
             if (nact == 0) break;
             HQ_TRY(precondition<double>(x, R, Zp, Tt, false, nullptr));
-            HQ_TRY(project(x, Zp));
+            HQ_TRY(project(x, Zp, rtol));
             launch_dot<double>(g, R, Zp, x->part, x->st);
             launch_finalize(FIN_BETA, N, g.gy, x->part, nullptr, sc, rtol, x->st);
             launch_pcg_p<double>(g, sc.beta, Zp, P, x->st);
@@ -2226,7 +2236,7 @@ hq_status refine_impl(hq_ctx *x, int rounds, double rtol, int maxit, double *res
         launch_apply<double>(v.g, v.D, v.c, u, b, nullptr, x->st);
         launch_shift_cols(n, N, x->mu, u, b, x->st);
         launch_axpby(cnt, -1.0, b, 0.0, b, b, x->st);
-        st = project(x, b);
+        st = project(x, b, rtol);
         if (st != HQ_OK) break;
         int it = 0;
         st = projected_pcg(x, b, t, x->mu, rtol, maxit, &it, "refinement PCG");
