@@ -398,7 +398,8 @@ def run_ttr(args):
     V, U0, w = inputs.workload(WORKLOAD)
     m, N = w["m"], w["N"]
     chunk = args.ttr_chunk
-    common = dict(tau=w["tau"], adaptive_tau=1, tau_max=args.tau_max)
+    common = dict(tau=w["tau"], adaptive_tau=1, tau_max=args.tau_max,
+                  tau_safety=args.tau_safety)
     clk = ClockSampler(0)
     clk.start()
     s = hq.Solver(m, N, cg_rtol=w["cg_rtol"], precision="fp64", mg_fp32=1, **common, **nu_kw(w))
@@ -429,7 +430,8 @@ def run_ttr(args):
         return [{k: v for k, v in h.items() if k != "lam"} for h in hh]
 
     a64, amx = first_below(h64, "err", 1e-6), first_below(hmx, "err", 1e-6)
-    out = {"workload": WORKLOAD, "tau_rule": "adaptive, tau_max %g" % args.tau_max,
+    out = {"workload": WORKLOAD,
+           "tau_rule": "adaptive, tau_max %g, safety factor %g" % (args.tau_max, args.tau_safety),
            "chunk": chunk, "eps": w["eps"], "clocks": clocks,
            "fp64": {"time_to_residual_s": h64[-1]["s"], "steps": h64[-1]["steps"],
                     "g": h64[-1]["g"], "to_err_1e-6": a64 and {"s": a64["s"], "steps": a64["steps"]}},
@@ -725,9 +727,11 @@ def ttr_live(torch, hq, inputs, args):
     V, U0, w = inputs.workload(WORKLOAD)
     m, N, eps = w["m"], w["N"], w["eps"]
     g_hand = args.ttr_handoff
-    common = dict(tau=w["tau"], adaptive_tau=1, tau_max=args.tau_max)
+    common = dict(tau=w["tau"], adaptive_tau=1, tau_max=args.tau_max,
+                  tau_safety=args.tau_safety)
     out = {"workload": "%s: %d^3 wells, N=%d" % (WORKLOAD, m, N), "eps": eps,
-           "tau_rule": "adaptive, tau_max %g" % args.tau_max, "handoff_g": g_hand}
+           "tau_rule": "adaptive, tau_max %g, safety factor %g" % (args.tau_max, args.tau_safety),
+           "handoff_g": g_hand}
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
 
@@ -1243,6 +1247,9 @@ def main():
     ap.add_argument("--ttr-steps", type=int, default=40000, help="step cap of each --ttr leg")
     ap.add_argument("--ttr-chunk", type=int, default=250)
     ap.add_argument("--tau-max", type=float, default=10.0)
+    ap.add_argument("--tau-safety", type=float, default=0.9,
+                    help="safety factor c of the adaptive time step in the time-to-residual "
+                         "legs (tau_n <= c lam / s_max)")
     ap.add_argument("--ttr-mixed-rtol", type=float, default=1e-4,
                     help="inner PCG rtol of the mixed scheme in the time-to-residual leg that "
                          "hands over to the FP64 refinement")

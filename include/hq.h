@@ -80,7 +80,7 @@ typedef struct {
     double timeout_s;    /* hq_solve wall-clock limit (<= 0: none)                 */
     int z_warm_start;    /* 1: start the corrector solve G Uh from W (C1 + S^-1 Puw C2), */
                          /* exact when span(U) is G-invariant; 0: from zero          */
-    int adaptive_tau;    /* 0: tau_n = tau.  1: tau_n = min(tau_max, 0.8 lam / s_max,  */
+    int adaptive_tau;    /* 0: tau_n = tau.  1: tau_n = min(tau_max, c lam / s_max,    */
                          /* 1.05 tau_{n-1}) with lam = 1/(largest Ritz value of G on  */
                          /* span(U)), s_max = max_i sum_j |<U,U>_ij| (a bound on its  */
                          /* largest eigenvalue); the first step starts from the       */
@@ -101,12 +101,17 @@ typedef struct {
                          /* back, r.z in FP64); the PCG residuals, updates, stopping  */
                          /* test and every other step stay FP64, so W = G U is still  */
                          /* solved to cg_rtol in FP64.  0 (default) = FP64 V-cycle   */
+    double tau_safety;   /* c of the adaptive time step (adaptive_tau = 1): tau_n    */
+                         /* <= c lam / s_max; 0 < c <= 1, default 0.8.  Near          */
+                         /* convergence tau < lambda_1(H + sigma) keeps the           */
+                         /* orthogonality error contracting, and lam overestimates    */
+                         /* lambda_1 until the Ritz value has converged               */
 } hq_config;
 
 /* Defaults: box [-6,6]^3, tau 0.4, automatic shift, FP64, cg_rtol 1e-10,
  * cg_maxit 200, nu1 = nu2 = 2, coarsest 4, omega 0.8, no timeout, warm start
- * of the corrector solve on, fp64_tc 1.  m and nev are left 0 and must be
- * set.                                                                      */
+ * of the corrector solve on, fp64_tc 1, tau_safety 0.8.  m and nev are left 0
+ * and must be set.                                                          */
 void hq_default_config(hq_config *cfg);
 
 /* Bytes of device workspace hq_init needs for cfg (0 if cfg is invalid). */

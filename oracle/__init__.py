@@ -88,8 +88,8 @@ def _sig(lib):
                            _P, _P, _P]),
         "orc_extract": (_I, [_I, _D, _D, _P, _D, _I, _P, _P, _P, _P, _P, _P]),
         "orc_lambda1_lower_bound": (_D, [_I, _D, _D, _P, _D]),
-        "orc_solve_adaptive": (_I, [_I, _D, _D, _P, _D, _I, _D, _D, _I, _D, _L, _P, _P, _P,
-                                    _P, _P, _P]),
+        "orc_solve_adaptive": (_I, [_I, _D, _D, _P, _D, _I, _D, _D, _D, _I, _D, _L, _P, _P,
+                                    _P, _P, _P, _P]),
         "orc_energy": (_D, [_I, _D, _D, _P, _D, _I, _P]),
         "orc_grad_eigs": (_I, [_I, _D, _D, _I, _P, _P, _P]),
         "orc_grad_density": (_I, [_I, _D, _D, _P, _I, _P, _P, _P, _D, _I, _P, _P, _P]),
@@ -382,9 +382,9 @@ def lambda1_lower_bound(m, V, sigma, lo=-6.0, hi=6.0):
 
 
 def solve_adaptive(m, V, sigma, U0, tau_max, eps, max_steps, lo=-6.0, hi=6.0, cg_rtol=1e-13,
-                   cg_maxit=20000, allow_unconverged=False):
+                   cg_maxit=20000, allow_unconverged=False, c=0.8):
     """Algorithm 1 with the adaptive time step (tau_n <= tau_max = delta_T):
-    tau_n = min(delta_T, 0.8 lam_hat / lambda_max<U,U>, 1.05 tau_{n-1}).
+    tau_n = min(delta_T, c lam_hat / lambda_max<U,U>, 1.05 tau_{n-1}), 0 < c <= 1.
     Returns (U_end, W_end, steps, g_end, g_history, tau_history)."""
     V = _f64(V).ravel()
     U = _f64(U0).copy()
@@ -393,7 +393,7 @@ def solve_adaptive(m, V, sigma, U0, tau_max, eps, max_steps, lo=-6.0, hi=6.0, cg
     g = ctypes.c_double()
     hist = np.full(max_steps + 1, np.nan)
     th = np.full(max_steps + 1, np.nan)
-    st = lib().orc_solve_adaptive(m, lo, hi, _ptr(V), sigma, U.shape[1], tau_max, cg_rtol,
+    st = lib().orc_solve_adaptive(m, lo, hi, _ptr(V), sigma, U.shape[1], tau_max, c, cg_rtol,
                                   cg_maxit, eps, max_steps, _ptr(U), _ptr(W), ctypes.byref(steps),
                                   ctypes.byref(g), _ptr(hist), _ptr(th))
     if not (allow_unconverged and st == ERR_NOT_CONVERGED):

@@ -718,7 +718,8 @@ double orc_scale_initial(long n, int N, double h3, double *U)
  *             upper estimate of the smallest eigenvalue lambda'_1 of H + sigma;
  *   s_max   = max_i sum_j |<U,U>_ij| (Gershgorin bound on lambda_max(<U,U>));
  *   tau_n   = min(delta_T, c lam_hat / s_max, gamma tau_{n-1}),
- * with c = 0.8, gamma = 1.05 and, for the first step, tau_{-1} chosen so that
+ * with 0 < c <= 1 (0.8 by default), gamma = 1.05 and, for the first step,
+ * tau_{-1} chosen so that
  * tau_0 <= c lb / s_max where lb <= lambda'_1 is the closed-form lower bound.
  * Near convergence the orthogonality error of eigenpair 1 is multiplied by
  * 1 - 2 tau / lambda'_1 per step, so tau < lambda'_1 keeps it contracting.  */
@@ -995,13 +996,14 @@ int orc_solve(int m, double lo, double hi, const double *V, double sigma, int N,
 /* Algorithm 1 with the adaptive time step above (delta_T = tau_max).
  * tau_hist (max_steps entries or NULL) receives tau_0, tau_1, ...            */
 int orc_solve_adaptive(int m, double lo, double hi, const double *V, double sigma, int N,
-                       double tau_max, double cg_rtol, int cg_maxit, double eps, long max_steps,
-                       double *U, double *W, long *steps_out, double *g_out, double *g_hist,
-                       double *tau_hist)
+                       double tau_max, double c, double cg_rtol, int cg_maxit, double eps,
+                       long max_steps, double *U, double *W, long *steps_out, double *g_out,
+                       double *g_hist, double *tau_hist)
 {
     long n = cube(m);
+    if (!(c > 0.0 && c <= 1.0)) return ORC_ERR_ARG;
     double *Z = malloc(sizeof(double) * n * N), *Un = malloc(sizeof(double) * n * N);
-    orc_adapt ad = {tau_max, 0.8, 1.05, orc_lambda1_lower_bound(m, lo, hi, V, sigma), 0.0, 1};
+    orc_adapt ad = {tau_max, c, 1.05, orc_lambda1_lower_bound(m, lo, hi, V, sigma), 0.0, 1};
     int have_z = 0, st = ORC_OK;
     long step = 0;
     double g = INFINITY, tau_used = 0.0;

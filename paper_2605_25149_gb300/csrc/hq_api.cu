@@ -289,6 +289,7 @@ bool valid_config(const hq_config *c, std::string *why) {
     if (c->grid_ctas < 0 || c->grid_ctas > 64) return fail("grid_ctas must be in [0, 64]");
     if (c->fp64_tc < 0 || c->fp64_tc > 2) return fail("fp64_tc must be 0, 1 or 2");
     if (c->mg_fp32 != 0 && c->mg_fp32 != 1) return fail("mg_fp32 must be 0 or 1");
+    if (!(c->tau_safety > 0.0 && c->tau_safety <= 1.0)) return fail("tau_safety must be in (0, 1]");
     return true;
 }
 
@@ -1199,7 +1200,8 @@ hq_status enqueue_b(hq_ctx *x, StepGraph *sgr, long long *counters) {
         launch_top_eig(N, x->Cm, N, x->pvec, x->scal + 12, x->st);
         launch_gersh(N, x->Ssm, N, x->scal + 13, x->st);
         const double tmax = x->cfg.tau_max > 0.0 ? x->cfg.tau_max : 1e300;
-        launch_adapt_tau(x->scal + 12, x->scal + 13, tmax, 0.8, 1.05, x->lambda1_lb, x->scal + 8,
+        launch_adapt_tau(x->scal + 12, x->scal + 13, tmax, x->cfg.tau_safety, 1.05, x->lambda1_lb,
+                         x->scal + 8,
                          x->st);
         tau_dev = x->scal + 8;
     }
@@ -2518,6 +2520,7 @@ void hq_default_config(hq_config *c) {
     c->adaptive_tau = 0;
     c->fp64_tc = 1;
     c->mg_fp32 = 0;
+    c->tau_safety = 0.8;
     c->tau_max = 0.0;
 }
 

@@ -64,7 +64,7 @@ class Config(ctypes.Structure):
         ("mg_omega", ctypes.c_double), ("timeout_s", ctypes.c_double),
         ("z_warm_start", ctypes.c_int), ("adaptive_tau", ctypes.c_int),
         ("tau_max", ctypes.c_double), ("grid_block", ctypes.c_int), ("grid_ctas", ctypes.c_int),
-        ("fp64_tc", ctypes.c_int), ("mg_fp32", ctypes.c_int),
+        ("fp64_tc", ctypes.c_int), ("mg_fp32", ctypes.c_int), ("tau_safety", ctypes.c_double),
     ]
 
 

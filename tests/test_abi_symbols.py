@@ -32,6 +32,7 @@ def test_config_struct_layout_and_defaults():
     assert (c.m, c.nev, c.lo, c.hi) == (16, 8, -6.0, 6.0)
     assert c.precision == hq.FP64 and c.mg_nu1 == 2 and c.mg_coarsest == 4
     assert c.shift != c.shift  # NaN: automatic shift
+    assert c.tau_safety == 0.8  # last field: the struct layouts agree to the end
 
 
 def test_workspace_sizing_and_config_validation():
@@ -43,6 +44,9 @@ def test_workspace_sizing_and_config_validation():
     assert hq.workspace_bytes(hq.default_config(4, 65)) == 0         # N > n
     assert hq.workspace_bytes(hq.default_config(8, 4, tau=-1.0)) == 0
     assert hq.workspace_bytes(hq.default_config(8, 4, mg_nu1=0)) == 0
+    for c in (0.0, -0.5, 1.5):
+        assert hq.workspace_bytes(hq.default_config(8, 4, tau_safety=c)) == 0
+    assert hq.workspace_bytes(hq.default_config(8, 4, tau_safety=1.0)) > 0
 
 
 def test_status_strings():

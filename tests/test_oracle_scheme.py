@@ -354,21 +354,28 @@ def test_harmonic16_N8_converges_to_closed_form():
     assert g < 1e-8
 
 
-def test_adaptive_time_step_converges_faster_to_same_eigenvalues():
+@pytest.mark.parametrize("c", [0.8, 0.95])
+def test_adaptive_time_step_converges_faster_to_same_eigenvalues(c):
     """Algorithm 1 allows tau_n <= delta_T; the adaptive rule reaches the same
     closed-form eigenvalues in fewer steps, and its tau grows from the
-    lower-bound start to 0.8 lambda_1 (below the linear stability limit
-    tau < lambda_1 of the orthogonality error of eigenpair 1)."""
+    lower-bound start to c lambda_1 (below the linear stability limit
+    tau < lambda_1 of the orthogonality error of eigenpair 1); a larger
+    safety factor c takes no more steps."""
     m, N = 8, 4
     V, sigma, h3, U = _problem(m, N, seed_u=17)
     _, _, steps_fixed, _, _ = O.solve(m, V, sigma, U, 0.5, 1e-10, 5000)
-    Ue, We, steps, g, hist, taus = O.solve_adaptive(m, V, sigma, U, 10.0, 1e-10, 5000)
+    Ue, We, steps, g, hist, taus = O.solve_adaptive(m, V, sigma, U, 10.0, 1e-10, 5000, c=c)
     assert steps < steps_fixed
     lv = separable_levels(m, -6.0, 6.0, N)
     np.testing.assert_allclose(O.extract(m, V, sigma, Ue, We)["lam_rr"], lv, rtol=1e-12)
     lam1 = lv[0] + sigma
     lb = O.lambda1_lower_bound(m, V, sigma)
     assert 0 < lb <= lam1
-    assert taus[0] <= 0.8 * lb / 1.0 + 1e-12
+    assert taus[0] <= c * lb / 1.0 + 1e-12
     assert np.all(np.diff(taus) <= 0.05 * taus[:-1] + 1e-15)      # growth at most 5%
-    assert taus[-1] == pytest.approx(0.8 * lam1, rel=1e-6)
+    assert taus[-1] == pytest.approx(c * lam1, rel=1e-6)
+    if c > 0.8:
+        _, _, steps08, _, _, _ = O.solve_adaptive(m, V, sigma, U, 10.0, 1e-10, 5000)
+        assert steps <= steps08
+    with pytest.raises(O.OracleError):
+        O.solve_adaptive(m, V, sigma, U, 10.0, 1e-10, 5, c=1.5)
