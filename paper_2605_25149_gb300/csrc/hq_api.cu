@@ -1196,8 +1196,12 @@ hq_status enqueue_b(hq_ctx *x, StepGraph *sgr, long long *counters) {
         // tau_n from the Gram of step n (Ritz estimate of lambda_1, bound on lambda_max<U,U>)
         launch_extract(N, N, 1.0, x->G2, 2 * N, x->Ssm, N, x->st);
         launch_extract(N, N, 1.0, x->G2 + (size_t)N * 2 * N, 2 * N, x->Ksm, N, x->st);
-        launch_rr_reduce(N, x->Ksm, x->Ssm, x->Lm, x->Cm, x->status, x->st);
-        launch_top_eig(N, x->Cm, N, x->pvec, x->scal + 12, x->st);
+        if (x->mixed && lam_hat32_fits(N)) {
+            launch_lam_hat32(N, x->Ksm, x->Ssm, x->pvec, x->scal + 12, x->status, x->st);
+        } else {
+            launch_rr_reduce(N, x->Ksm, x->Ssm, x->Lm, x->Cm, x->status, x->st);
+            launch_top_eig(N, x->Cm, N, x->pvec, x->scal + 12, x->st);
+        }
         launch_gersh(N, x->Ssm, N, x->scal + 13, x->st);
         const double tmax = x->cfg.tau_max > 0.0 ? x->cfg.tau_max : 1e300;
         launch_adapt_tau(x->scal + 12, x->scal + 13, tmax, x->cfg.tau_safety, 1.05, x->lambda1_lb,

@@ -394,6 +394,11 @@ void lu32_prepare();
 // largest eigenvalue of sym(A) (N x N, leading dimension lda) -> out[0];
 // vec (N): warm-start vector, updated (all zero: fixed start)
 void launch_top_eig(int N, const double *A, int lda, double *vec, double *out, cudaStream_t s);
+// the same estimate of the pencil (sym(K), S) in FP32 in one launch (mixed
+// contexts): out[0] = largest eigenvalue to ~1e-6, vec the warm vector
+bool lam_hat32_fits(int N);
+void launch_lam_hat32(int N, const double *K, const double *S, double *vec, double *out,
+                      int *status, cudaStream_t s);
 // out[0] = max_i sum_j |A_ij|
 void launch_gersh(int N, const double *A, int lda, double *out, cudaStream_t s);
 // adaptive time step (see hq_config.adaptive_tau): st[0] = tau_n, st[1] = tau_{n-1},

@@ -706,9 +706,12 @@ __global__ void k_pred_c(int N, double tau_arg, const double *tau_dev, const dou
     }
 }
 
+void small_prepare();   // shared-memory limits of the staged small kernels (below)
+
 void lu_prepare() {
     static bool done = false;
     if (done) return;
+    small_prepare();
     cudaFuncSetAttribute(k_lu_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)lu_panel_smem(768, PB));
     done = true;
@@ -1096,7 +1099,88 @@ __global__ void __launch_bounds__(256) k_top_eig(int N, const double *A, int lda
     for (int i = tid; i < N; i += blockDim.x) vec[i] = v[i];
     if (tid == 0) out[0] = mu;
 }
+// The same power iteration with the symmetric part B = (A + A^T) / 2 staged
+// in shared memory (N <= TE_SMEM_N): each product reads B from shared memory
+// instead of A and A^T from L2 (the transposed reads uncoalesced), and the
+// three inner products of an iteration are reduced by warp butterflies and
+// one pass over the warps (three barriers instead of ten).
+constexpr int TE_SMEM_N = 120;
+size_t te_smem_bytes(int N) { return sizeof(double) * ((size_t)N * N + 2 * N + 768); }
+__global__ void __launch_bounds__(256) k_top_eig_sm(int N, const double *A, int lda, double *vec,
+                                                    double *out) {
+    extern __shared__ double sh[];
+    double *B = sh, *v = sh + (size_t)N * N, *w = v + N, *red = w + N;   // red: 3 x 8 warps
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ int fresh;
+    __shared__ double mu_sh, nw_sh;
+    for (long idx = tid; idx < (long)N * N; idx += blockDim.x) {
+        const int i = (int)(idx / N), j = (int)(idx % N);
+        B[idx] = 0.5 * (A[(size_t)i * lda + j] + A[(size_t)j * lda + i]);
+    }
+    if (tid == 0) {
+        double nv = 0.0;
+        for (int i = 0; i < N; i++) nv += vec[i] * vec[i];
+        fresh = !(nv > 0.0);
+    }
+    __syncthreads();
+    for (int i = tid; i < N; i += blockDim.x) v[i] = fresh ? 1.0 + 0.125 * (double)(i % 7) : vec[i];
+    __syncthreads();
+    double mu = 0.0, mu_prev = 0.0;
+    for (int it = 0; it < 1000; it++) {
+        for (int i = tid; i < N; i += blockDim.x) {
+            double acc = 0.0;
+            for (int j = 0; j < N; j++) acc += B[(size_t)i * N + j] * v[j];
+            w[i] = acc;
+        }
+        __syncthreads();
+        // v.w, v.v, w.w: per-warp butterflies, then the eight warps in order
+        double vw = 0.0, vv = 0.0, ww = 0.0;
+        for (int i = tid; i < N; i += blockDim.x) {
+            vw += v[i] * w[i];
+            vv += v[i] * v[i];
+            ww += w[i] * w[i];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            vw += __shfl_xor_sync(0xffffffffu, vw, o);
+            vv += __shfl_xor_sync(0xffffffffu, vv, o);
+            ww += __shfl_xor_sync(0xffffffffu, ww, o);
+        }
+        if (lane == 0) {
+            red[warp] = vw;
+            red[8 + warp] = vv;
+            red[16 + warp] = ww;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double a = 0.0, b = 0.0, c = 0.0;
+            for (int q = 0; q < 8; q++) {
+                a += red[q];
+                b += red[8 + q];
+                c += red[16 + q];
+            }
+            mu_sh = a / b;
+            nw_sh = sqrt(c);
+        }
+        __syncthreads();
+        mu = mu_sh;
+        const double nw = nw_sh;
+        if (!(nw > 0.0)) break;
+        const double rnw = 1.0 / nw;
+        for (int i = tid; i < N; i += blockDim.x) v[i] = w[i] * rnw;
+        __syncthreads();
+        if (it > 1 && fabs(mu - mu_prev) <= 1e-14 * fabs(mu)) break;
+        mu_prev = mu;
+    }
+    for (int i = tid; i < N; i += blockDim.x) vec[i] = v[i];
+    if (tid == 0) out[0] = mu;
+}
+
 void launch_top_eig(int N, const double *A, int lda, double *vec, double *out, cudaStream_t s) {
+    if (N <= TE_SMEM_N) {
+        HQ_LAUNCH(HQ_K_SMALL, k_top_eig_sm<<<1, 256, te_smem_bytes(N), s>>>(N, A, lda, vec, out));
+        return;
+    }
     size_t shm = sizeof(double) * (2 * N + 768);
     HQ_LAUNCH(HQ_K_SMALL, k_top_eig<<<1, 256, shm, s>>>(N, A, lda, vec, out));
 }
@@ -1365,8 +1449,227 @@ __global__ void __launch_bounds__(1024) k_rr_reduce(int N, const double *K, cons
         }
     }
 }
+// The same reduction in three launches for N <= RR_SMEM_N.  GB300 retires
+// about two FP64 operations per clock per SM, so one CTA doing the whole
+// reduction (N^3/6 for the Cholesky, N^3 for the two triangular solves, N^2
+// divisions) is bound by that single SM's FP64 pipe and by its dependency
+// chains (~0.5 ms at N = 64).  Here one CTA factors S = L L^T in shared
+// memory (reciprocal of each pivot once), and the two triangular solves
+// run one column per CTA on N SMs, each row's dot product split over the
+// warp's lanes: T1 = L^{-1} sym(K) stored transposed, then Cm = L^{-1} T1^T.
+// Same quantities as k_rr_reduce; rounded in a different order.
+constexpr int RR_SMEM_N = 96;
+size_t rr_chol_smem(int N) { return sizeof(double) * (size_t)N * N; }
+// Cholesky S = L L^T in shared memory by one CTA of 1024 threads (the
+// pivot's reciprocal once per step; the trailing update with rows across the
+// warps and columns across the lanes).  A one-warp form took twice as long:
+// GB300's FP64 latency needs the warps in flight more than the barriers cost.
+__global__ void __launch_bounds__(1024) k_chol_sm(int N, const double *S, double *Lg, int *status) {
+    extern __shared__ double L[];
+    __shared__ double d_sh, rd_sh;
+    const int tid = threadIdx.x, T = blockDim.x;
+    for (long idx = tid; idx < (long)N * N; idx += T) L[idx] = S[idx];
+    __syncthreads();
+    for (int k = 0; k < N; k++) {
+        const double dk = L[(size_t)k * N + k];
+        if (!(dk > 0.0)) {
+            if (tid == 0) atomicOr(status, ST_SINGULAR);
+            return;
+        }
+        if (tid == 0) {
+            d_sh = sqrt(dk);
+            rd_sh = 1.0 / d_sh;
+        }
+        __syncthreads();
+        const double d = d_sh, rd = rd_sh;
+        for (int i = k + tid; i < N; i += T) L[(size_t)i * N + k] = (i == k) ? d : L[(size_t)i * N + k] * rd;
+        __syncthreads();
+        for (int i = k + 1 + (tid >> 5); i < N; i += (T >> 5)) {
+            const double lik = L[(size_t)i * N + k];
+            for (int j = k + 1 + (tid & 31); j <= i; j += 32)
+                L[(size_t)i * N + j] -= lik * L[(size_t)j * N + k];
+        }
+        __syncthreads();
+    }
+    for (long idx = tid; idx < (long)N * N; idx += T) {
+        const int i = (int)(idx / N), j = (int)(idx % N);
+        Lg[idx] = j > i ? 0.0 : L[idx];
+    }
+}
+// x = L^{-1} b for column j = blockIdx.x (one warp, L staged in shared
+// memory), each row's dot product split over the lanes: mode 0:
+// b_i = (K_ij + K_ji) / 2, x stored as row j of Out (the transpose); mode 1:
+// b_i = In_ij, x stored as column j of Out
+__global__ void __launch_bounds__(32) k_trsv_col(int N, const double *L, const double *In,
+                                                 int mode, double *Out) {
+    extern __shared__ double tsm[];
+    double *Ls = tsm, *x = tsm + (size_t)N * N;
+    const int j = blockIdx.x, lane = threadIdx.x;
+    for (long idx = lane; idx < (long)N * N; idx += 32) Ls[idx] = L[idx];
+    for (int i = lane; i < N; i += 32)
+        x[i] = mode == 0 ? 0.5 * (In[(size_t)i * N + j] + In[(size_t)j * N + i]) : In[(size_t)i * N + j];
+    __syncwarp();
+    for (int i = 0; i < N; i++) {
+        double part = 0.0;
+        for (int k = lane; k < i; k += 32) part += Ls[(size_t)i * N + k] * x[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) x[i] = (x[i] - part) / Ls[(size_t)i * N + i];
+        __syncwarp();
+    }
+    for (int i = lane; i < N; i += 32) {
+        if (mode == 0) Out[(size_t)j * N + i] = x[i];
+        else Out[(size_t)i * N + j] = x[i];
+    }
+}
+
+// The largest eigenvalue mu of the pencil (sym(K), S) in FP32, one CTA, for
+// the adaptive time step of mixed-precision contexts (a step-size estimate
+// needs ~1e-6, not FP64's 1e-14): C = L^{-1} sym(K) L^{-T} from the FP32
+// Cholesky S = L L^T, then the power iteration of k_top_eig_sm on C from
+// the warm vector vec (FP64, updated), stopped when mu changes by less than
+// 1e-6 of itself.  FP32 runs about sixty times FP64's lane rate here, and
+// the whole estimate is one launch instead of four.  N <= LH_MAX_N.
+constexpr int LH_MAX_N = 96;
+size_t lam_hat32_smem(int N) { return sizeof(float) * (2 * (size_t)N * N + 2 * N + 64); }
+__global__ void __launch_bounds__(1024) k_lam_hat32(int N, const double *K, const double *S,
+                                                   double *vec, double *out, int *status) {
+    extern __shared__ float lsm[];
+    float *L = lsm, *C = lsm + (size_t)N * N, *v = C + (size_t)N * N, *w = v + N, *red = w + N;
+    __shared__ float d_sh, rd_sh, mu_sh, nw_sh;
+    __shared__ int fresh;
+    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    for (long idx = tid; idx < (long)N * N; idx += T) {
+        const int i = (int)(idx / N), j = (int)(idx % N);
+        L[idx] = (float)S[idx];
+        C[idx] = (float)(0.5 * (K[(size_t)i * N + j] + K[(size_t)j * N + i]));
+    }
+    if (tid == 0) {
+        double nv = 0.0;
+        for (int i = 0; i < N; i++) nv += vec[i] * vec[i];
+        fresh = !(nv > 0.0);
+    }
+    __syncthreads();
+    for (int k = 0; k < N; k++) {
+        const float dk = L[(size_t)k * N + k];
+        if (!(dk > 0.f)) {
+            if (tid == 0) atomicOr(status, ST_SINGULAR);
+            return;
+        }
+        if (tid == 0) {
+            d_sh = sqrtf(dk);
+            rd_sh = 1.f / d_sh;
+        }
+        __syncthreads();
+        const float d = d_sh, rd = rd_sh;
+        for (int i = k + tid; i < N; i += T) L[(size_t)i * N + k] = (i == k) ? d : L[(size_t)i * N + k] * rd;
+        __syncthreads();
+        for (int i = k + 1 + (tid >> 5); i < N; i += (T >> 5)) {
+            const float lik = L[(size_t)i * N + k];
+            for (int j = k + 1 + lane; j <= i; j += 32) L[(size_t)i * N + j] -= lik * L[(size_t)j * N + k];
+        }
+        __syncthreads();
+    }
+    // C <- L^{-1} C (column j by thread), transpose, and again: L^{-1} C L^{-T}
+    for (int pass = 0; pass < 2; pass++) {
+        for (int j = tid; j < N; j += T)
+            for (int i = 0; i < N; i++) {
+                float acc = C[(size_t)i * N + j];
+                for (int k = 0; k < i; k++) acc -= L[(size_t)i * N + k] * C[(size_t)k * N + j];
+                C[(size_t)i * N + j] = acc / L[(size_t)i * N + i];
+            }
+        __syncthreads();
+        for (long idx = tid; idx < (long)N * N; idx += T) {
+            const int i = (int)(idx / N), j = (int)(idx % N);
+            if (i < j) {
+                const float a = C[idx], b = C[(size_t)j * N + i];
+                C[idx] = b;
+                C[(size_t)j * N + i] = a;
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < N; i += T) v[i] = fresh ? 1.f + 0.125f * (float)(i % 7) : (float)vec[i];
+    __syncthreads();
+    float mu = 0.f, mu_prev = 0.f;
+    for (int it = 0; it < 500; it++) {
+        for (int i = tid; i < N; i += T) {
+            float acc = 0.f;
+            for (int j = 0; j < N; j++) acc += C[(size_t)i * N + j] * v[j];
+            w[i] = acc;
+        }
+        __syncthreads();
+        float vw = 0.f, vv = 0.f, ww = 0.f;
+        for (int i = tid; i < N; i += T) {
+            vw += v[i] * w[i];
+            vv += v[i] * v[i];
+            ww += w[i] * w[i];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            vw += __shfl_xor_sync(0xffffffffu, vw, o);
+            vv += __shfl_xor_sync(0xffffffffu, vv, o);
+            ww += __shfl_xor_sync(0xffffffffu, ww, o);
+        }
+        if (lane == 0 && warp < 4) {   // the N <= 96 values live in the first warps
+            red[warp] = vw;
+            red[4 + warp] = vv;
+            red[8 + warp] = ww;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            float a = 0.f, b = 0.f, c = 0.f;
+            for (int q = 0; q < 4; q++) {
+                a += red[q];
+                b += red[4 + q];
+                c += red[8 + q];
+            }
+            mu_sh = a / b;
+            nw_sh = sqrtf(c);
+        }
+        __syncthreads();
+        mu = mu_sh;
+        const float nw = nw_sh;
+        if (!(nw > 0.f)) break;
+        for (int i = tid; i < N; i += T) v[i] = w[i] / nw;
+        __syncthreads();
+        if (it > 1 && fabsf(mu - mu_prev) <= 1e-6f * fabsf(mu)) break;
+        mu_prev = mu;
+    }
+    for (int i = tid; i < N; i += T) vec[i] = (double)v[i];
+    if (tid == 0) out[0] = (double)mu;
+}
+
+bool lam_hat32_fits(int N) { return N <= LH_MAX_N; }
+void launch_lam_hat32(int N, const double *K, const double *S, double *vec, double *out,
+                      int *status, cudaStream_t s) {
+    HQ_LAUNCH(HQ_K_SMALL, k_lam_hat32<<<1, 1024, lam_hat32_smem(N), s>>>(N, K, S, vec, out, status));
+}
+
+void small_prepare() {
+    cudaFuncSetAttribute(k_lam_hat32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)lam_hat32_smem(LH_MAX_N));
+    cudaFuncSetAttribute(k_chol_sm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)rr_chol_smem(RR_SMEM_N));
+    cudaFuncSetAttribute(k_trsv_col, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(rr_chol_smem(RR_SMEM_N) + sizeof(double) * RR_SMEM_N));
+
+    cudaFuncSetAttribute(k_top_eig_sm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)te_smem_bytes(TE_SMEM_N));
+}
+
 void launch_rr_reduce(int N, const double *K, const double *S, double *L, double *Cm,
                       int *status, cudaStream_t s) {
+    if (N <= RR_SMEM_N) {
+        // T1^T into Cm, then Cm = L^{-1} T1^T in place: CTA j of the second
+        // solve reads only column j of Cm (into shared memory, before any
+        // write) and writes only column j
+        const size_t tsm = rr_chol_smem(N) + sizeof(double) * N;
+        HQ_LAUNCH(HQ_K_SMALL, k_chol_sm<<<1, 1024, rr_chol_smem(N), s>>>(N, S, L, status));
+        HQ_LAUNCH(HQ_K_SMALL, k_trsv_col<<<N, 32, tsm, s>>>(N, L, K, 0, Cm));
+        HQ_LAUNCH(HQ_K_SMALL, k_trsv_col<<<N, 32, tsm, s>>>(N, L, Cm, 1, Cm));
+        return;
+    }
     HQ_LAUNCH(HQ_K_SMALL, k_rr_reduce<<<1, 1024, 0, s>>>(N, K, S, L, Cm, status));
 }
 
