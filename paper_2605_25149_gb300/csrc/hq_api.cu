@@ -451,9 +451,9 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
     double *Mw = cv.take<double>(sizeof(double) * 4 * N2);
     double *XY = cv.take<double>(sizeof(double) * 2 * N2);
     int *ipiv = cv.take<int>(sizeof(int) * 2 * N);
-    // mixed-precision small solves: FP32 factors and FP64 right-hand side /
-    // residual of the predictor system
-    float *lu32 = mixed ? cv.take<float>(sizeof(float) * 4 * N2) : nullptr;
+    // the predictor system by FP32 elimination and FP64 refinement (both
+    // precisions): FP32 factors and FP64 right-hand side / residual
+    float *lu32 = cv.take<float>(sizeof(float) * 4 * N2);
     // digit planes of the small matrices of the FP64 tensor-core block products
     unsigned char *ozimg = (!mixed && c->fp64_tc && tall_oz_supported(2 * N, 0))
                                ? cv.take<unsigned char>(tall_oz_image_bytes(n, 2 * N, N))
@@ -461,8 +461,8 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
     double *ozgram = (!mixed && c->fp64_tc && gram_oz_supported(2 * N))
                          ? cv.take<double>(gram_oz_scratch_bytes(n, 2 * N))
                          : nullptr;
-    double *pB = mixed ? cv.take<double>(sizeof(double) * 2 * N2) : nullptr;
-    double *pR = mixed ? cv.take<double>(sizeof(double) * 2 * N2) : nullptr;
+    double *pB = cv.take<double>(sizeof(double) * 2 * N2);
+    double *pR = cv.take<double>(sizeof(double) * 2 * N2);
     double *Cc = cv.take<double>(sizeof(double) * 2 * N2);
     double *T1 = cv.take<double>(sizeof(double) * 2 * N2);
     double *Shat = cv.take<double>(sizeof(double) * N2);
@@ -1221,7 +1221,7 @@ hq_status enqueue_b(hq_ctx *x, StepGraph *sgr, long long *counters) {
         // G Uh = W C1 + G W C2 and G W ~ W M with M = S^{-1} Puw (exact when
         // span(U) is G-invariant): start from Z0 = W (C1 + M C2)
         launch_spd_solve(N, x->G2, 2 * N, x->G2 + N, 2 * N, x->Mw, x->Lm, x->Ym, x->ipiv,
-                         x->status, x->st, x->lu32);
+                         x->status, x->st, x->mixed ? x->lu32 : nullptr);
         launch_extract(N, N, 1.0, x->C, N, x->Cm, N, x->st);
         launch_small_gemm(N, N, N, 1.0, x->Ym, N, false, x->C + (size_t)N * N, N, false, 1.0,
                           x->Cm, N, x->st);
@@ -2575,7 +2575,7 @@ hq_status hq_init(const hq_config *cfg, void *d_workspace, size_t bytes, void *c
     if (x->mixed) hq::tc_prepare();
     hq::lu_prepare();
     hq::vcoarse_prepare();
-    if (x->mixed) hq::lu32_prepare();
+    hq::lu32_prepare();
     if (x->ozimg || x->ozgram) hq::oz_prepare();
     if (e != cudaSuccess) {
         delete x;

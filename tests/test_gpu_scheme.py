@@ -203,14 +203,18 @@ def test_adaptive_tau_trajectory_matches_oracle(c):
     assert rel(s.get_state()[0], Ue) < 1e-8
 
 
-@pytest.mark.parametrize("m,N", [(12, 8), (12, 40), (14, 90)])
-def test_mixed_predictor_system_is_solved_to_fp64_accuracy(m, N):
-    """Mixed precision solves the 2N x 2N predictor system of Eq. (4.1) by FP32
-    elimination plus FP64 iterative refinement: the FP64 residual of the
-    equations, re-evaluated from the step's Gram G2 and its X, Y, is at the
-    FP64 rounding level (FP32 alone would leave ~1e-7)."""
+@pytest.mark.parametrize("prec,m,N", [("mixed", 12, 8), ("mixed", 12, 40), ("mixed", 14, 90),
+                                      ("fp64", 12, 8), ("fp64", 12, 40), ("fp64", 14, 90),
+                                      ("fp64", 14, 100)])
+def test_predictor_system_is_solved_to_fp64_accuracy(prec, m, N):
+    """Both precisions solve the 2N x 2N predictor system of Eq. (4.1) by FP32
+    elimination plus FP64 iterative refinement where the FP32 factors fit one
+    CTA's shared memory (2N up to ~180; N = 100 takes the FP64 blocked
+    elimination): the FP64 residual of the equations, re-evaluated from the
+    step's Gram G2 and its X, Y, is at the FP64 rounding level (FP32 alone
+    would leave ~1e-7)."""
     tau = 0.4
-    s, V, U0 = make(m, N, precision="mixed", tau=tau, cg_rtol=1e-6)
+    s, V, U0 = make(m, N, precision=prec, tau=tau, cg_rtol=1e-6 if prec == "mixed" else 1e-10)
     tr = s.step_trace()
     G2, XY = host(tr["gram"]), host(tr["XY"])
     S, Puw = G2[:N, :N], G2[:N, N:]
