@@ -807,6 +807,7 @@ def ttr_live(torch, hq, inputs, args):
     lam64 = sr64.eigenpairs()["lam_rr"]
     res_f["eig_agreement_with_mixed_refined"] = float(np.max(np.abs(lam64 - lam_ref) /
                                                              np.abs(lam_ref)))
+    res_f["fp64_cg_rtol"] = w["cg_rtol"]
     out["fp64_refined"] = res_f
     del s64, sr64
     torch.cuda.empty_cache()

@@ -203,6 +203,39 @@ def test_adaptive_tau_trajectory_matches_oracle(c):
     assert rel(s.get_state()[0], Ue) < 1e-8
 
 
+@pytest.mark.parametrize("prec,N,tol", [("fp64", 8, 1e-10), ("fp64", 40, 1e-10), ("mixed", 8, 1e-5),
+                                        ("mixed", 40, 1e-5), ("mixed", 100, 1e-5)])
+def test_adaptive_tau_follows_the_pencil_of_the_step_gram(prec, N, tol):
+    """The adaptive step from the Gram of the traced step, re-evaluated in
+    FP64 by numpy: tau_n = min(delta_T, c / mu_max / s_max, 1.05 tau_{n-1})
+    with mu_max the largest eigenvalue of the pencil (sym <W,U>, <U,U>) and
+    s_max the Gershgorin bound of <U,U>.  FP64 contexts estimate mu_max in
+    FP64 (Cholesky, column-parallel solves, power iteration), mixed ones in
+    FP32 in one launch (N <= 96) or in FP64 (N = 100)."""
+    import scipy.linalg
+    m, c, tmax = 12, 0.9, 10.0
+    s, V, U0 = make(m, N, precision=prec, cg_rtol=1e-6 if prec == "mixed" else 1e-10,
+                    adaptive_tau=1, tau_max=tmax, tau_safety=c)
+    # past the 5% growth limit of tau_n
+    tau_prev = 0.0
+    for _ in range(400):
+        s.step(1)
+        tau = s.time_step()
+        if tau < 1.04 * tau_prev:
+            break
+        tau_prev = tau
+    tau_prev = s.time_step()
+    tr = s.step_trace()
+    tau = s.time_step()
+    G2 = host(tr["gram"])
+    S, K = G2[:N, :N], G2[N:, :N]
+    mu = scipy.linalg.eigh(0.5 * (K + K.T), S, eigvals_only=True).max()
+    smax = np.abs(S).sum(axis=1).max()
+    est = c / mu / smax
+    assert est < 1.05 * tau_prev and est < tmax
+    assert tau == pytest.approx(est, rel=tol)
+
+
 @pytest.mark.parametrize("prec,m,N", [("mixed", 12, 8), ("mixed", 12, 40), ("mixed", 14, 90),
                                       ("fp64", 12, 8), ("fp64", 12, 40), ("fp64", 14, 90),
                                       ("fp64", 14, 100)])
