@@ -42,6 +42,8 @@ constexpr int OZ_BPLANE = OZ_NT * 128;    // one digit plane of the small matrix
 constexpr int OZ_SMEM = OZ_S * (OZ_APLANE + OZ_BPLANE) + 1024;
 constexpr int OZ_EBAD = 0x7FF;            // biased exponent of Inf / NaN
 constexpr int OZ_FRAC = 40;               // fraction bits of the fixed-point combination
+constexpr int OZ_SLD = OZ_NT + 1;         // row stride (doubles) of the staged output tile
+static_assert(OZ_M * OZ_SLD * 8 <= OZ_S * OZ_APLANE, "output tile fits the digit planes");
 
 // byte offset of 16-bit element (row r, k) in a K-major tile of 64-element
 // rows with the 128-byte swizzle (16-byte chunk c of row r at c ^ (r & 7))
@@ -86,6 +88,37 @@ __device__ __forceinline__ void oz_digits(double x, int emax, uint16_t (&dg)[OZ_
         // float(d) exactly, via the 2^23 bias; bf16 = its upper 16 bits
         const float fd = __uint_as_float(0x4B000000u | d) - 8388608.0f;
         dg[i] = (uint16_t)(__float_as_uint(fd) >> 16) | (d ? sgn : (uint16_t)0);
+    }
+}
+
+// |x| / 2^(emax - 1022) with 62 fraction bits (0 for zero, subnormal, Inf,
+// NaN), and the sign bit of x in bit 31
+__device__ __forceinline__ unsigned long long oz_fixed(double x, int emax, uint32_t &sgn) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    sgn = (uint32_t)(b >> 32) & 0x80000000u;
+    if (ex == 0 || ex == OZ_EBAD || emax == OZ_EBAD) return 0ull;
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = 9 + ex - emax;
+    return sh >= 0 ? (m << sh) : (sh > -64 ? (m >> (-sh)) : 0ull);
+}
+
+// the digits of two values of one row / column, plane by plane as bf16 pairs
+// (x0 in the low half): the same bit patterns as oz_digits.  The signed
+// integer +-d comes from one float addition, (2^23 + d) - 2^23 with the sign
+// of x on both terms (+0 for d = 0), and its bf16 pattern is the upper half.
+__device__ __forceinline__ void oz_digits2(double x0, double x1, int emax, uint32_t (&pk)[OZ_S]) {
+    uint32_t s0, s1;
+    const unsigned long long f0 = oz_fixed(x0, emax, s0), f1 = oz_fixed(x1, emax, s1);
+    const uint32_t c0 = 0x4B000000u | s0, c1 = 0x4B000000u | s1;
+    const float a0 = s0 ? 8388608.0f : -8388608.0f, a1 = s1 ? 8388608.0f : -8388608.0f;
+#pragma unroll
+    for (int i = 0; i < OZ_S; i++) {
+        const uint32_t d0 = (uint32_t)(f0 >> (62 - OZ_BITS * (i + 1))) & 127u;
+        const uint32_t d1 = (uint32_t)(f1 >> (62 - OZ_BITS * (i + 1))) & 127u;
+        const float v0 = __uint_as_float(c0 | d0) + a0;
+        const float v1 = __uint_as_float(c1 | d1) + a1;
+        pk[i] = __byte_perm(__float_as_uint(v0), __float_as_uint(v1), 0x7632);
     }
 }
 
@@ -192,7 +225,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         __syncthreads();
         if (abort_sh) break;
         // digit planes of the point rows for K = ch*64 .. ch*64+63: a warp owns
-        // 16 rows; all 32 loads of a batch of 16 are issued before converting
+        // 16 rows, a lane the pair k = 2 lane, 2 lane + 1 of each (one 32-bit
+        // store per plane; a warp's stores fill one 128-byte row); all 32
+        // loads of a batch of 16 rows are issued before converting
         {
             constexpr int RPW = OZ_M / (OZ_THREADS / 32);   // rows per warp
             double xv[RPW][2];
@@ -202,23 +237,19 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 const long p = r0 + r;
 #pragma unroll
                 for (int h = 0; h < 2; h++) {
-                    const int kg = ch * OZ_KC + lane + 32 * h;
+                    const int kg = ch * OZ_KC + 2 * lane + h;
                     xv[q][h] = (p < n && kg < K) ? aval(p, kg) : 0.0;
                 }
             }
 #pragma unroll
             for (int q = 0; q < RPW; q++) {
                 const int r = warp * RPW + q;
-                const int em = erow[r];
+                uint32_t pk[OZ_S];
+                oz_digits2(xv[q][0], xv[q][1], erow[r], pk);
+                const uint32_t off = sw128_offset16(r, 2 * lane);
 #pragma unroll
-                for (int h = 0; h < 2; h++) {
-                    uint16_t dg[OZ_S];
-                    oz_digits(xv[q][h], em, dg);
-                    const uint32_t off = sw128_offset16(r, lane + 32 * h);
-#pragma unroll
-                    for (int i = 0; i < OZ_S; i++)
-                        *reinterpret_cast<uint16_t *>(planesA + i * OZ_APLANE + off) = dg[i];
-                }
+                for (int i = 0; i < OZ_S; i++)
+                    *reinterpret_cast<uint32_t *>(planesA + i * OZ_APLANE + off) = pk[i];
             }
         }
         // digit planes of the small matrix (prepared by k_oz_split)
@@ -251,6 +282,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             mma_commit(&mbar);
         }
     }
+    // the tile's rows and columns; Cin's tile is loaded (coalesced: a warp
+    // reads 32 consecutive columns of one row) while the last MMAs run
+    const int ncl = min(OZ_NT, ncol - ct * OZ_NT);
+    const long nrw = min((long)OZ_M, n - r0);
+    constexpr int EPT = OZ_M * OZ_NT / OZ_THREADS;   // tile elements per thread
+    double cpre[EPT];
+    if (Cin) {
+#pragma unroll
+        for (int u = 0; u < EPT; u++) {
+            const int idx = tid + u * OZ_THREADS, rr = idx / OZ_NT, jj = idx % OZ_NT;
+            cpre[u] = (rr < nrw && jj < ncl) ? Cin[(size_t)(r0 + rr) * ncol + ct * OZ_NT + jj]
+                                             : 0.0;
+        }
+    }
     if (!abort_sh && tid == 0) {
         if (!mbar_wait(&mbar, (unsigned)((kchunks - 1) & 1))) {
             abort_sh = 1;
@@ -269,6 +314,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     if (abort_sh) {
         if (tid == 0) atomicOr(status, ST_TC_TIMEOUT);
     } else {
+        // the digit planes are free once the MMAs are done: the output tile is
+        // staged there (row stride OZ_SLD doubles: a half-warp's 8-byte
+        // accesses to one column of 16 rows, or to 16 columns of one row,
+        // fall in distinct banks), so Cin is read and Out written in whole
+        // rows
+        double *stg = reinterpret_cast<double *>(planesA);
+        if (Cin) {
+#pragma unroll
+            for (int u = 0; u < EPT; u++) {
+                const int idx = tid + u * OZ_THREADS;
+                stg[(idx / OZ_NT) * OZ_SLD + idx % OZ_NT] = cpre[u];
+            }
+        }
+        __syncthreads();
         // epilogue: thread = one point row (TMEM lane 32 (warp % 4) + lane) and
         // one half of the 64 output columns (warp / 4)
         const int r = (warp & 3) * 32 + lane;
@@ -310,11 +369,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                     o = a * __longlong_as_double((long long)(es + 1023) << 52);
                 else
                     o = a * pow2(es);
-                const size_t e = (size_t)p * ncol + c;
-                if (Cin) o += Cin[e];
-                if (Out) Out[e] = o;
+                double *sl = stg + r * OZ_SLD + cb + j;
+                if (Cin) o += *sl;
+                *sl = o;
                 if (part_sq) sq = fma(o, o, sq);
             }
+            }
+        }
+        if (Out) {
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < EPT; u++) {
+                const int idx = tid + u * OZ_THREADS, rr = idx / OZ_NT, jj = idx % OZ_NT;
+                if (rr < nrw && jj < ncl)
+                    Out[(size_t)(r0 + rr) * ncol + ct * OZ_NT + jj] = stg[rr * OZ_SLD + jj];
             }
         }
     }
@@ -449,12 +517,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 uint32_t pk[OZ_S][4];
 #pragma unroll
                 for (int u = 0; u < 8; u += 2) {
-                    uint16_t d0[OZ_S], d1[OZ_S];
-                    oz_digits(xv[8 * g8 + u], em, d0);
-                    oz_digits(xv[8 * g8 + u + 1], em, d1);
+                    uint32_t pp[OZ_S];
+                    oz_digits2(xv[8 * g8 + u], xv[8 * g8 + u + 1], em, pp);
 #pragma unroll
-                    for (int i = 0; i < OZ_S; i++)
-                        pk[i][u >> 1] = (uint32_t)d0[i] | ((uint32_t)d1[i] << 16);
+                    for (int i = 0; i < OZ_S; i++) pk[i][u >> 1] = pp[i];
                 }
                 const uint32_t off = sw128_offset16(lc, 32 * lh + 8 * g8);
 #pragma unroll
