@@ -70,27 +70,6 @@ __device__ __forceinline__ int biased_exp(double x) {
     return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
 }
 
-// the 8 digits of x relative to the biased exponent emax of its row / column,
-// as bf16 bit patterns of the signed integers
-__device__ __forceinline__ void oz_digits(double x, int emax, uint16_t (&dg)[OZ_S]) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int ex = (int)((b >> 52) & 0x7FF);
-    unsigned long long f = 0ull;   // |x| / 2^(emax - 1022) with 62 fraction bits
-    if (ex != 0 && ex != OZ_EBAD && emax != OZ_EBAD) {
-        const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-        const int sh = 9 + ex - emax;   // <= 9 since ex <= emax
-        f = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> (-sh)) : 0ull);
-    }
-    const uint16_t sgn = (uint16_t)((b >> 48) & 0x8000u);
-#pragma unroll
-    for (int i = 0; i < OZ_S; i++) {
-        const unsigned d = (unsigned)(f >> (62 - OZ_BITS * (i + 1))) & 127u;
-        // float(d) exactly, via the 2^23 bias; bf16 = its upper 16 bits
-        const float fd = __uint_as_float(0x4B000000u | d) - 8388608.0f;
-        dg[i] = (uint16_t)(__float_as_uint(fd) >> 16) | (d ? sgn : (uint16_t)0);
-    }
-}
-
 // |x| / 2^(emax - 1022) with 62 fraction bits (0 for zero, subnormal, Inf,
 // NaN), and the sign bit of x in bit 31
 __device__ __forceinline__ unsigned long long oz_fixed(double x, int emax, uint32_t &sgn) {
@@ -99,14 +78,16 @@ __device__ __forceinline__ unsigned long long oz_fixed(double x, int emax, uint3
     sgn = (uint32_t)(b >> 32) & 0x80000000u;
     if (ex == 0 || ex == OZ_EBAD || emax == OZ_EBAD) return 0ull;
     const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = 9 + ex - emax;
+    const int sh = 9 + ex - emax;   // <= 9 since ex <= emax
     return sh >= 0 ? (m << sh) : (sh > -64 ? (m >> (-sh)) : 0ull);
 }
 
-// the digits of two values of one row / column, plane by plane as bf16 pairs
-// (x0 in the low half): the same bit patterns as oz_digits.  The signed
-// integer +-d comes from one float addition, (2^23 + d) - 2^23 with the sign
-// of x on both terms (+0 for d = 0), and its bf16 pattern is the upper half.
+// the 8 digits of two values of one row / column relative to the biased
+// exponent emax, as bf16 bit patterns of the signed integers, packed in
+// pairs plane by plane (x0 in the low half).  Digit i is bits
+// 55 - 7i .. 61 - 7i of the fixed-point magnitude; the signed integer +-d
+// comes from one float addition, (2^23 + d) - 2^23 with the sign of x on both
+// terms (+0 for d = 0), and its bf16 pattern is the upper half of the float.
 __device__ __forceinline__ void oz_digits2(double x0, double x1, int emax, uint32_t (&pk)[OZ_S]) {
     uint32_t s0, s1;
     const unsigned long long f0 = oz_fixed(x0, emax, s0), f1 = oz_fixed(x1, emax, s1);
@@ -132,28 +113,40 @@ __device__ __forceinline__ double pow2(int e) {
 // Digit planes of the small matrix [M1; M2] (K x ncol) in the layout the MMA
 // reads: image[((ct * kchunks + ch) * 8 + j) * 8 KB] holds digit j of rows =
 // output columns ct*64 .. +63 and K = ch*64 .. +63; fexp[c] = the column's
-// largest biased exponent.  One thread per output column of a tile.
-__global__ void __launch_bounds__(OZ_NT) k_oz_split(int K, int k1, int ncol, int kchunks,
-                                                    const double *M1, const double *M2,
-                                                    unsigned char *image, int *fexp) {
-    const int ct = blockIdx.x, cl = threadIdx.x, c = ct * OZ_NT + cl;
+// largest biased exponent.  CTA = one column tile; thread (kg, cl) takes
+// column cl and the pairs k = 2 (kg + SPL_G i), 2 (kg + SPL_G i) + 1 (the
+// column maxima are reduced over the SPL_G groups in shared memory first).
+constexpr int SPL_G = 16;
+
+__global__ void __launch_bounds__(OZ_NT * SPL_G) k_oz_split(int K, int k1, int ncol, int kchunks,
+                                                            const double *M1, const double *M2,
+                                                            unsigned char *image, int *fexp) {
+    __shared__ int emx[SPL_G][OZ_NT];
+    const int ct = blockIdx.x, cl = threadIdx.x % OZ_NT, kg = threadIdx.x / OZ_NT;
+    const int c = ct * OZ_NT + cl;
     auto val = [&](int k) -> double {
         if (c >= ncol || k >= K) return 0.0;
         return k < k1 ? M1[(size_t)k * ncol + c] : M2[(size_t)(k - k1) * ncol + c];
     };
+    const int npairs = kchunks * OZ_KC / 2;
     int em = 0;
-    for (int k = 0; k < K; k++) em = max(em, biased_exp(val(k)));
-    if (c < ncol) fexp[c] = em;
-    for (int ch = 0; ch < kchunks; ch++) {
-        unsigned char *base = image + (size_t)(ct * kchunks + ch) * OZ_S * OZ_BPLANE;
-        for (int kl = 0; kl < OZ_KC; kl++) {
-            uint16_t dg[OZ_S];
-            oz_digits(val(ch * OZ_KC + kl), em, dg);
-            const uint32_t off = sw128_offset16(cl, kl);
+    for (int q = kg; q < npairs; q += SPL_G)
+        em = max(em, max(biased_exp(val(2 * q)), biased_exp(val(2 * q + 1))));
+    emx[kg][cl] = em;
+    __syncthreads();
+    em = 0;
 #pragma unroll
-            for (int j = 0; j < OZ_S; j++)
-                *reinterpret_cast<uint16_t *>(base + (size_t)j * OZ_BPLANE + off) = dg[j];
-        }
+    for (int g = 0; g < SPL_G; g++) em = max(em, emx[g][cl]);
+    if (kg == 0 && c < ncol) fexp[c] = em;
+    for (int q = kg; q < npairs; q += SPL_G) {
+        const int k = 2 * q, ch = k / OZ_KC, kl = k % OZ_KC;
+        unsigned char *base = image + (size_t)(ct * kchunks + ch) * OZ_S * OZ_BPLANE;
+        uint32_t pk[OZ_S];
+        oz_digits2(val(k), val(k + 1), em, pk);
+        const uint32_t off = sw128_offset16(cl, kl);
+#pragma unroll
+        for (int j = 0; j < OZ_S; j++)
+            *reinterpret_cast<uint32_t *>(base + (size_t)j * OZ_BPLANE + off) = pk[j];
     }
 }
 
@@ -180,7 +173,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *planesA = smem;
     unsigned char *planesB = smem + OZ_S * OZ_APLANE;
-    __shared__ uint64_t mbar;
+    __shared__ uint64_t mbar, bbar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int erow[OZ_M];
     __shared__ int abort_sh, pend_sh, tmem_free_sh;
@@ -193,6 +186,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const int K = k1 + k2;
     if (tid == 0) {
         mbar_init(&mbar, 1);
+        mbar_init(&bbar, 1);
         abort_sh = 0;
         pend_sh = 0;
         tmem_free_sh = 1;
@@ -208,7 +202,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     auto aval = [&](long p, int k) -> double {
         return k < k1 ? A1[(size_t)p * k1 + k] : A2[(size_t)p * k2 + (k - k1)];
     };
-    for (int r = tid; r < OZ_M; r += OZ_THREADS) erow[r] = (r0 + r < n) ? erow_g[r0 + r] : 0;
+    // row exponents: from k_oz_rowexp when K spans several chunks, else
+    // formed below from the chunk's values (erow_g null)
+    if (erow_g)
+        for (int r = tid; r < OZ_M; r += OZ_THREADS) erow[r] = (r0 + r < n) ? erow_g[r0 + r] : 0;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -221,6 +218,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 abort_sh = 1;
                 pend_sh = (ch - 1) & 1;
             }
+        }
+        // the chunk's digit planes of the small matrix (prepared by
+        // k_oz_split) arrive by bulk copies while the threads convert A;
+        // the previous chunk's MMAs, which read them, are complete here
+        if (tid == 0 && !abort_sh) {
+            const unsigned char *src = image + (size_t)(ct * kchunks + ch) * OZ_S * OZ_BPLANE;
+            mbar_expect_tx(&bbar, (uint32_t)(OZ_S * OZ_BPLANE));
+#pragma unroll
+            for (int j = 0; j < OZ_S; j++)
+                bulk_g2s(planesB + j * OZ_BPLANE, src + j * OZ_BPLANE, OZ_BPLANE, &bbar);
         }
         __syncthreads();
         if (abort_sh) break;
@@ -244,24 +251,30 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 #pragma unroll
             for (int q = 0; q < RPW; q++) {
                 const int r = warp * RPW + q;
+                int em;
+                if (erow_g) {
+                    em = erow[r];
+                } else {
+                    em = __reduce_max_sync(0xffffffffu, (unsigned)max(biased_exp(xv[q][0]),
+                                                                      biased_exp(xv[q][1])));
+                    if (lane == 0) erow[r] = em;
+                }
                 uint32_t pk[OZ_S];
-                oz_digits2(xv[q][0], xv[q][1], erow[r], pk);
+                oz_digits2(xv[q][0], xv[q][1], em, pk);
                 const uint32_t off = sw128_offset16(r, 2 * lane);
 #pragma unroll
                 for (int i = 0; i < OZ_S; i++)
                     *reinterpret_cast<uint32_t *>(planesA + i * OZ_APLANE + off) = pk[i];
             }
         }
-        // digit planes of the small matrix (prepared by k_oz_split)
-        {
-            const uint4 *src = reinterpret_cast<const uint4 *>(
-                image + (size_t)(ct * kchunks + ch) * OZ_S * OZ_BPLANE);
-            uint4 *dst = reinterpret_cast<uint4 *>(planesB);
-            for (int i = tid; i < OZ_S * OZ_BPLANE / 16; i += OZ_THREADS) dst[i] = src[i];
-        }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && !mbar_wait(&bbar, (unsigned)(ch & 1))) {
+            // no MMA of this chunk is issued; the last commit (if any) was
+            // waited for above
+            abort_sh = 1;
+            pend_sh = (ch + 1) & 1;
+        } else if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
             for (int ks = 0; ks < OZ_KC / 16; ks++) {
@@ -681,14 +694,18 @@ void launch_tall_oz(long n, const double *A1, int k1, const double *M1, const do
     const int ctiles = (ncol + OZ_NT - 1) / OZ_NT;
     int *fexp = reinterpret_cast<int *>(image + (size_t)ctiles * kchunks * OZ_S * OZ_BPLANE);
     int *erow = fexp + ncol + 64;
-    HQ_LAUNCH(HQ_K_BLOCKGEMM, k_oz_split<<<ctiles, OZ_NT, 0, s>>>(K, k1, ncol, kchunks, M1,
+    HQ_LAUNCH(HQ_K_BLOCKGEMM, k_oz_split<<<ctiles, OZ_NT * SPL_G, 0, s>>>(K, k1, ncol, kchunks, M1,
                                                                    k2 ? M2 : nullptr, image, fexp));
-    HQ_LAUNCH(HQ_K_BLOCKGEMM, k_oz_rowexp<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(
-                                  n, k1, k2, A1, k2 ? A2 : nullptr, erow));
+    // one K chunk: the product kernel forms the row exponents from the values
+    // it converts; more: a pass over the rows first
+    if (kchunks > 1)
+        HQ_LAUNCH(HQ_K_BLOCKGEMM, k_oz_rowexp<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(
+                                      n, k1, k2, A1, k2 ? A2 : nullptr, erow));
     const unsigned gx = (unsigned)((n + OZ_M - 1) / OZ_M);
     HQ_LAUNCH(HQ_K_BLOCKGEMM,
               k_tall_oz<<<dim3(gx, ctiles), OZ_THREADS, OZ_SMEM, s>>>(
-                  n, k1, k2, ncol, kchunks, A1, k2 ? A2 : nullptr, image, fexp, erow, Cin, Out,
+                  n, k1, k2, ncol, kchunks, A1, k2 ? A2 : nullptr, image, fexp,
+                  kchunks > 1 ? erow : nullptr, Cin, Out,
                   part_sq, status));
 }
 
