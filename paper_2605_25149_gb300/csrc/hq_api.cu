@@ -1220,8 +1220,15 @@ hq_status enqueue_b(hq_ctx *x, StepGraph *sgr, long long *counters) {
     if (x->cfg.z_warm_start) {
         // G Uh = W C1 + G W C2 and G W ~ W M with M = S^{-1} Puw (exact when
         // span(U) is G-invariant): start from Z0 = W (C1 + M C2)
-        launch_spd_solve(N, x->G2, 2 * N, x->G2 + N, 2 * N, x->Mw, x->Lm, x->Ym, x->ipiv,
-                         x->status, x->st, x->mixed ? x->lu32 : nullptr);
+        // mixed: FP32 elimination (a warm start needs no more); FP64: FP32
+        // elimination and two FP64 refinement steps where the factors fit
+        // shared memory (the FP64 solution to rounding level)
+        if (!x->mixed && x->lu32 && x->pR && x->ipiv && lu32_fits(N, N))
+            launch_solve32_refined(N, N, x->G2, 2 * N, x->G2 + N, 2 * N, x->Ym, x->lu32, x->ipiv,
+                                   x->pR, 2, x->status, x->st);
+        else
+            launch_spd_solve(N, x->G2, 2 * N, x->G2 + N, 2 * N, x->Mw, x->Lm, x->Ym, x->ipiv,
+                             x->status, x->st, x->mixed ? x->lu32 : nullptr);
         launch_extract(N, N, 1.0, x->C, N, x->Cm, N, x->st);
         launch_small_gemm(N, N, N, 1.0, x->Ym, N, false, x->C + (size_t)N * N, N, false, 1.0,
                           x->Cm, N, x->st);

@@ -384,6 +384,15 @@ void launch_small_gemm(int M, int Ncol, int K, double alpha, const double *A, in
 // lu32 (4N^2 floats), pB, pR (2N x N doubles): scratch of the mixed-precision
 // variant (FP32 elimination + FP64 iterative refinement), used when all are
 // non-null and the system fits one CTA's shared memory
+// true when the FP32 elimination of an nn x nn system with nr right-hand
+// sides fits one CTA's shared memory
+bool lu32_fits(int nn, int nr);
+// X = A^-1 B (nn x nn, nn x nr, FP64) by FP32 elimination with partial
+// pivoting and `refine` FP64 residual-correction steps; LU (nn^2 floats),
+// ipiv (nn) and R (nn x nr doubles) are scratch; requires lu32_fits(nn, nr)
+void launch_solve32_refined(int nn, int nr, const double *A, int lda, const double *B, int ldb,
+                            double *X, float *LU, int *ipiv, double *R, int refine, int *status,
+                            cudaStream_t s);
 void launch_predictor_solve(int N, double tau, const double *G2, double *Mwork, double *XY,
                             double *C, int *status, cudaStream_t s,
                             const double *tau_dev = nullptr, int *ipiv = nullptr,

@@ -419,15 +419,40 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 // FP64 Gram <X, X> = w X^T X of X = [X1 X2] (n x na, na <= 128) by the same
 // digit slicing, with per-column exponents over all points (k_oz_colexp).
 // CTA = all na rows x 64 output columns over a chunk of points; the digit
-// planes of a 64-point slice serve as both operands (the B operand is rows
-// ct*64.. of the A planes).  The exact-sum bound holds for 128 points, so
-// every two slices the eight accumulators are read and added into 64-bit
-// fixed-point registers (OZ_GFRAC fraction bits); the chunk's FP64 partial
-// tile is summed over chunks in a fixed order by k_oz_gram_reduce.  D_t(i,j)
-// and D_t(j,i) are the same integers, so the result is exactly symmetric.
+// planes of a 32-point slice serve as both operands (the B operand is rows
+// ct*64.. of the A planes; 64-byte rows, 64-byte swizzle).  The planes of
+// OZ_GST slices are in flight: the converter warps fill slice s while the MMAs
+// of slice s-1 run.  The exact-sum bound holds for 128 points, so every four
+// slices the eight accumulators are read and added into 64-bit fixed-point
+// registers (OZ_GFRAC fraction bits); the chunk's FP64 partial tile is
+// summed over chunks in a fixed order by k_oz_gram_reduce.  D_t(i,j) and
+// D_t(j,i) are the same integers, so the result is exactly symmetric.
 // ---------------------------------------------------------------------------
 constexpr int OZ_GFRAC = 32;
-constexpr int OZ_GSMEM = OZ_S * OZ_APLANE + 1024;
+constexpr int OZ_GKC = 32;                       // points per slice: 64-byte rows
+constexpr int OZ_GPLANE = OZ_M * 64;             // one digit plane of a slice: 8 KB
+constexpr int OZ_GSTAGE = OZ_S * OZ_GPLANE;      // the eight planes: 64 KB
+constexpr int OZ_GST = 3;                        // slices in flight
+constexpr int OZ_GFLUSH = 128 / OZ_GKC;          // slices per exact accumulation
+constexpr int OZ_GSMEM = OZ_GST * OZ_GSTAGE + 2048;   // + alignment slack
+
+// byte offset of 16-bit element (row r, k) in a K-major tile of 32-element
+// rows with the 64-byte swizzle (16-byte chunk c of row r at c ^ ((r >> 1) & 3))
+__device__ __forceinline__ uint32_t sw64_offset16(int r, int k) {
+    return (uint32_t)((r >> 3) * 512 + (r & 7) * 64 + ((((k >> 3) ^ (r >> 1)) & 3) << 4) +
+                      ((k & 7) << 1));
+}
+
+// shared-memory matrix descriptor: K-major, 64-byte swizzle, SBO = 512 B
+__device__ __forceinline__ uint64_t make_desc_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);   // start address
+    d |= (uint64_t)(1) << 16;                  // leading byte offset (unused, swizzled K-major)
+    d |= (uint64_t)(512 >> 4) << 32;           // stride byte offset: 8 rows x 64 B
+    d |= (uint64_t)1 << 46;                    // descriptor version (sm_100 family)
+    d |= (uint64_t)4 << 61;                    // swizzle mode: 64 B
+    return d;
+}
 
 __global__ void __launch_bounds__(128) k_oz_colexp(long n, int n1, int n2, const double *X1,
                                                    const double *X2, int *colexp) {
@@ -439,30 +464,42 @@ __global__ void __launch_bounds__(128) k_oz_colexp(long n, int n1, int n2, const
     atomicMax(&colexp[c], em);
 }
 
-__global__ void __launch_bounds__(OZ_THREADS, 1)
+// 16 converter warps (digit planes, TMEM read-out, epilogue) and one warp
+// whose first lane issues the MMAs; they meet only at mbarriers: full[st]
+// (the planes of a slice are written), done[st] (its MMAs completed, the
+// stage is free) and tfree (the accumulators were read out at a flush)
+constexpr int OZ_GCONV = 512;
+constexpr int OZ_GTHREADS = OZ_GCONV + 32;
+
+__global__ void __launch_bounds__(OZ_GTHREADS, 1)
     k_gram_oz(long n, int n1, int n2, long chunk_rows, const double *__restrict__ X1,
               const double *__restrict__ X2, const int *__restrict__ colexp,
               double *__restrict__ partials, int *status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *planes = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t mbar;
+    __shared__ uint64_t full[OZ_GST], done[OZ_GST], tfree;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int cexp[OZ_M];
-    __shared__ int abort_sh, pend_sh, tmem_free_sh;
+    __shared__ volatile int abort_sh;
+    __shared__ int last_sh, tmem_free_sh;
     constexpr uint32_t TCOLS = OZ_S * OZ_NT;   // 512
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int na = n1 + n2, ct = blockIdx.x;
     const long p0 = (long)blockIdx.y * chunk_rows;
     const long p1 = (n < p0 + chunk_rows) ? n : p0 + chunk_rows;
-    const int nslices = p1 > p0 ? (int)((p1 - p0 + OZ_KC - 1) / OZ_KC) : 0;
+    const int nslices = p1 > p0 ? (int)((p1 - p0 + OZ_GKC - 1) / OZ_GKC) : 0;
     if (tid == 0) {
-        mbar_init(&mbar, 1);
+        for (int i = 0; i < OZ_GST; i++) {
+            mbar_init(&full[i], OZ_GCONV);
+            mbar_init(&done[i], 1);
+        }
+        mbar_init(&tfree, OZ_GCONV);
         abort_sh = 0;
-        pend_sh = 0;
+        last_sh = -1;   // last slice whose MMAs were committed
         tmem_free_sh = 1;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int c = tid; c < OZ_M; c += OZ_THREADS) cexp[c] = c < na ? colexp[c] : 0;
+    for (int c = tid; c < OZ_M; c += OZ_GTHREADS) cexp[c] = c < na ? colexp[c] : 0;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base_sh)),
@@ -474,120 +511,146 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base_sh;
-    const uint32_t idesc = idesc_bf16(OZ_M, OZ_NT);
-    // slice loads: thread t takes column c = t & 127 of the 32 consecutive
-    // points 32 (t >> 7) + j (coalesced across the lanes for each j)
-    const int lc = tid & (OZ_M - 1), lh = tid >> 7;
-    double xv[OZ_KC / 2];
-    auto load_slice = [&](int sl) {
-#pragma unroll
-        for (int j = 0; j < OZ_KC / 2; j++) {
-            const long p = p0 + (long)sl * OZ_KC + 32 * lh + j;
-            xv[j] = (p < p1 && lc < na)
-                        ? (lc < n1 ? X1[(size_t)p * n1 + lc] : X2[(size_t)p * n2 + (lc - n1)])
-                        : 0.0;
-        }
+    // completion of the MMAs of slice q: the (q / OZ_GST)-th commit on
+    // done[q % OZ_GST].  No role can run a phase ahead of the one another
+    // role waits for (each next arrival needs the awaited phase), so every
+    // parity below is unambiguous.
+    auto wait_done = [&](int q) -> bool {
+        return mbar_wait(&done[q % OZ_GST], (unsigned)((q / OZ_GST) & 1));
     };
-    // fixed-point sums: thread = TMEM lane 32 (warp % 4) + lane (Gram row),
-    // 32 output columns (warp / 4)
-    const int grow = (warp & 3) * 32 + lane, gcb = (warp >> 2) * 32;
-    long long facc[32];
+    // fixed-point sums: converter thread = TMEM lane 32 (warp % 4) + lane
+    // (Gram row), 16 output columns (warp / 4)
+    const int grow = (warp & 3) * 32 + lane, gcb = (warp >> 2) * 16;
+    long long facc[16];
 #pragma unroll
-    for (int j = 0; j < 32; j++) facc[j] = 0;
+    for (int j = 0; j < 16; j++) facc[j] = 0;
     auto flush = [&]() {
 #pragma unroll
         for (int t = 2; t <= OZ_S + 1; t++) {
-            float v[32];
-            tmem_ld32<32>(tmem + ((uint32_t)((warp & 3) * 32) << 16) +
+            float v[16];
+            tmem_ld32<16>(tmem + ((uint32_t)((warp & 3) * 32) << 16) +
                               (uint32_t)((t - 2) * OZ_NT + gcb), v);
             const int sh = OZ_GFRAC - OZ_BITS * (t - 2);
 #pragma unroll
-            for (int j = 0; j < 32; j++) {
+            for (int j = 0; j < 16; j++) {
                 const long long d = (long long)__float2int_rn(v[j]);
                 facc[j] += sh >= 0 ? (d << sh) : (d >> (-sh));
             }
         }
     };
-    if (nslices > 0) load_slice(0);
-    for (int sl = 0; sl < nslices; sl++) {
-        if (sl > 0 && tid == 0) {
-            if (!mbar_wait(&mbar, (unsigned)((sl - 1) & 1))) {
-                abort_sh = 1;
-                pend_sh = (sl - 1) & 1;
+    if (warp == OZ_GCONV / 32) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(OZ_M, OZ_NT);
+            for (int sl = 0; sl < nslices; sl++) {
+                if (abort_sh) break;
+                const int st = sl % OZ_GST;
+                const bool fresh = sl % OZ_GFLUSH == 0;
+                if (!mbar_wait(&full[st], (unsigned)((sl / OZ_GST) & 1)) ||
+                    (fresh && sl > 0 && !mbar_wait(&tfree, (unsigned)((sl / OZ_GFLUSH - 1) & 1)))) {
+                    abort_sh = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                unsigned char *stage = planes + st * OZ_GSTAGE;
+#pragma unroll
+                for (int ks = 0; ks < OZ_GKC / 16; ks++) {
+                    const uint32_t ko = ks * 32;
+#pragma unroll
+                    for (int t = 2; t <= OZ_S + 1; t++) {
+                        const int ilo = t - OZ_S > 1 ? t - OZ_S : 1;
+                        const int ihi = t - 1 < OZ_S ? t - 1 : OZ_S;
+#pragma unroll
+                        for (int i = ilo; i <= ihi; i++) {
+                            const int j = t - i;
+                            const uint64_t da =
+                                make_desc_sw64(smem_u32(stage + (i - 1) * OZ_GPLANE) + ko);
+                            const uint64_t db = make_desc_sw64(
+                                smem_u32(stage + (j - 1) * OZ_GPLANE + ct * OZ_NT * 64) + ko);
+                            const uint32_t acc = (!fresh || ks > 0 || i > ilo) ? 1u : 0u;
+                            mma_bf16(tmem + (uint32_t)((t - 2) * OZ_NT), da, db, idesc, acc);
+                        }
+                    }
+                }
+                mma_commit(&done[st]);
+                last_sh = sl;
             }
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (abort_sh) break;
-        if (sl > 0 && (sl & 1) == 0) flush();   // 128 points accumulated
-        {
-            // eight consecutive points of one column form one 16-byte chunk of
-            // each digit plane
-            const int em = cexp[lc];
+    } else {
+        // slice loads: thread t takes column c = t & 127 of the 8 consecutive
+        // points 8 (t >> 7) + j (coalesced across the lanes for each j)
+        const int lc = tid & (OZ_M - 1), lq = tid >> 7;
+        double xv[8];
+        auto load_slice = [&](int sl) {
 #pragma unroll
-            for (int g8 = 0; g8 < 4; g8++) {
+            for (int j = 0; j < 8; j++) {
+                const long p = p0 + (long)sl * OZ_GKC + 8 * lq + j;
+                xv[j] = (p < p1 && lc < na)
+                            ? (lc < n1 ? X1[(size_t)p * n1 + lc] : X2[(size_t)p * n2 + (lc - n1)])
+                            : 0.0;
+            }
+        };
+        const int em = cexp[lc];
+        if (nslices > 0) load_slice(0);
+        for (int sl = 0; sl < nslices; sl++) {
+            if (abort_sh) break;
+            const int st = sl % OZ_GST;
+            const bool fresh = sl % OZ_GFLUSH == 0;
+            // the stage's previous slice is consumed
+            if (sl >= OZ_GST && !wait_done(sl - OZ_GST)) {
+                abort_sh = 1;
+                break;
+            }
+            if (fresh && sl > 0) {
+                // 128 points accumulated: every MMA so far is complete
+                if (!wait_done(sl - 1)) {
+                    abort_sh = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                flush();
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                mbar_arrive(&tfree);
+            }
+            // eight consecutive points of one column: one 16-byte chunk of
+            // each digit plane
+            {
                 uint32_t pk[OZ_S][4];
 #pragma unroll
                 for (int u = 0; u < 8; u += 2) {
                     uint32_t pp[OZ_S];
-                    oz_digits2(xv[8 * g8 + u], xv[8 * g8 + u + 1], em, pp);
+                    oz_digits2(xv[u], xv[u + 1], em, pp);
 #pragma unroll
                     for (int i = 0; i < OZ_S; i++) pk[i][u >> 1] = pp[i];
                 }
-                const uint32_t off = sw128_offset16(lc, 32 * lh + 8 * g8);
+                unsigned char *stage = planes + st * OZ_GSTAGE;
+                const uint32_t off = sw64_offset16(lc, 8 * lq);
 #pragma unroll
                 for (int i = 0; i < OZ_S; i++)
-                    *reinterpret_cast<uint4 *>(planes + i * OZ_APLANE + off) =
+                    *reinterpret_cast<uint4 *>(stage + i * OZ_GPLANE + off) =
                         make_uint4(pk[i][0], pk[i][1], pk[i][2], pk[i][3]);
             }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&full[st]);
+            if (sl + 1 < nslices) load_slice(sl + 1);
         }
-        if (sl + 1 < nslices) load_slice(sl + 1);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const bool fresh = (sl & 1) == 0;
-#pragma unroll
-            for (int ks = 0; ks < OZ_KC / 16; ks++) {
-                const uint32_t ko = ks * 32;
-#pragma unroll
-                for (int t = 2; t <= OZ_S + 1; t++) {
-                    const int ilo = t - OZ_S > 1 ? t - OZ_S : 1;
-                    const int ihi = t - 1 < OZ_S ? t - 1 : OZ_S;
-                    for (int i = ilo; i <= ihi; i++) {
-                        const int j = t - i;
-                        const uint64_t da = make_desc_sw128(smem_u32(planes + (i - 1) * OZ_APLANE) + ko);
-                        const uint64_t db = make_desc_sw128(
-                            smem_u32(planes + (j - 1) * OZ_APLANE + ct * OZ_NT * 128) + ko);
-                        const uint32_t acc = (!fresh || ks > 0 || i > ilo) ? 1u : 0u;
-                        mma_bf16(tmem + (uint32_t)((t - 2) * OZ_NT), da, db, idesc, acc);
-                    }
-                }
-            }
-            mma_commit(&mbar);
-        }
+        if (!abort_sh && nslices > 0 && !wait_done(nslices - 1)) abort_sh = 1;
     }
-    if (!abort_sh && nslices > 0 && tid == 0) {
-        if (!mbar_wait(&mbar, (unsigned)((nslices - 1) & 1))) {
-            abort_sh = 1;
-            pend_sh = (nslices - 1) & 1;
-        }
-    }
-    // as in k_tall_oz: drain the last commit (bounded) before releasing TMEM
-    if (abort_sh && tid == 0) tmem_free_sh = mbar_wait(&mbar, (unsigned)pend_sh) ? 1 : 0;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // after a wait that gave up, one more bounded wait for the last commit
+    // before the columns are released (if it fails too they stay allocated,
+    // and only the status word is meaningful)
+    if (tid == OZ_GCONV && abort_sh && last_sh >= 0) tmem_free_sh = wait_done(last_sh) ? 1 : 0;
+    __syncthreads();
     if (abort_sh) {
         if (tid == 0) atomicOr(status, ST_TC_TIMEOUT);
-    } else {
+    } else if (tid < OZ_GCONV) {
         if (nslices > 0) flush();
         double *dst = partials + ((size_t)blockIdx.y * gridDim.x + ct) * OZ_M * OZ_NT;
         const int ea = cexp[grow];
 #pragma unroll
-        for (int j = 0; j < 32; j++) {
+        for (int j = 0; j < 16; j++) {
             const int gc = ct * OZ_NT + gcb + j;
             double o = 0.0;
             if (grow < na && gc < na) {
@@ -678,7 +741,7 @@ void launch_gram_oz(long n, const double *X1, int n1, const double *X2, int n2, 
     int *colexp = reinterpret_cast<int *>(scratch + (size_t)g.chunks * g.ctiles * OZ_M * OZ_NT);
     cudaMemsetAsync(colexp, 0, sizeof(int) * OZ_M, s);
     HQ_LAUNCH(HQ_K_GRAM, k_oz_colexp<<<1024, 128, 0, s>>>(n, n1, n2, X1, n2 ? X2 : nullptr, colexp));
-    HQ_LAUNCH(HQ_K_GRAM, k_gram_oz<<<dim3(g.ctiles, g.chunks), OZ_THREADS, OZ_GSMEM, s>>>(
+    HQ_LAUNCH(HQ_K_GRAM, k_gram_oz<<<dim3(g.ctiles, g.chunks), OZ_GTHREADS, OZ_GSMEM, s>>>(
                              n, n1, n2, g.chunk_rows, X1, n2 ? X2 : nullptr, colexp, partials,
                              status));
     HQ_LAUNCH(HQ_K_GRAM, k_oz_gram_reduce<<<(na * na + 255) / 256, 256, 0, s>>>(
