@@ -374,10 +374,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 if (c >= ncol) continue;
                 const int fc = fexp[c];
                 const int es = (em - 1022) + (fc - 1022) - 2 * OZ_BITS - OZ_FRAC;
+                // the integer converts exactly or rounds once; the scaling by
+                // 2^es is an add to the exponent field when the result stays
+                // normal (one FP64 operation fewer per output), else a multiply
                 const double a = (double)acc[j];
+                const long long ab = __double_as_longlong(a);
+                const int ea = (int)((ab >> 52) & 0x7FF) + es;
                 double o;
                 if (em == OZ_EBAD || fc == OZ_EBAD)
                     o = __longlong_as_double(0x7FF8000000000000ll);
+                else if (ea - es != 0 && ea >= 1 && ea <= 2046)
+                    o = __longlong_as_double(ab + (long long)es * (1ll << 52));
                 else if (es >= -1022 && es <= 1023)
                     o = a * __longlong_as_double((long long)(es + 1023) << 52);
                 else
