@@ -138,6 +138,13 @@ struct hq_ctx {
     unsigned char *ozimg = nullptr;   // FP64 tensor-core block products: digit planes
     double *ozgram = nullptr;         // FP64 tensor-core Gram: chunk partials, exponents
     double *pB = nullptr, *pR = nullptr;   // predictor right-hand side / residual
+    // the warm-start solve's own FP32 factors, pivots and residual: it runs
+    // on `side`, beside the predictor system (fork / join by the two events)
+    int *ipivw = nullptr;
+    float *lu32w = nullptr;
+    double *pRw = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t evside[2] = {nullptr, nullptr};
     double *vn[3] = {nullptr, nullptr, nullptr};   // FP64 n-vectors (density, adjoint)
     double *pvec = nullptr;                        // power-iteration vector (N)
     // host state
@@ -191,6 +198,9 @@ struct hq_ctx {
         if (capB) cudaStreamDestroy(capB);
         if (capC) cudaStreamDestroy(capC);
         if (capD) cudaStreamDestroy(capD);
+        if (side) cudaStreamDestroy(side);
+        for (cudaEvent_t e : evside)
+            if (e) cudaEventDestroy(e);
     }
 };
 
@@ -463,6 +473,9 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
                          : nullptr;
     double *pB = cv.take<double>(sizeof(double) * 2 * N2);
     double *pR = cv.take<double>(sizeof(double) * 2 * N2);
+    int *ipivw = cv.take<int>(sizeof(int) * N);
+    float *lu32w = cv.take<float>(sizeof(float) * N2);
+    double *pRw = cv.take<double>(sizeof(double) * N2);
     double *Cc = cv.take<double>(sizeof(double) * 2 * N2);
     double *T1 = cv.take<double>(sizeof(double) * 2 * N2);
     double *Shat = cv.take<double>(sizeof(double) * N2);
@@ -512,6 +525,9 @@ size_t carve(hq_ctx *x, const hq_config *c, char *base) {
         x->ozgram = ozgram;
         x->pB = pB;
         x->pR = pR;
+        x->ipivw = ipivw;
+        x->lu32w = lu32w;
+        x->pRw = pRw;
         x->G2 = G2; x->Mw = Mw; x->XY = XY; x->C = Cc; x->T1 = T1; x->Shat = Shat; x->Om = Om;
         x->Msm = Msm; x->Ksm = Ksm; x->Ssm = Ssm; x->Lm = Lm; x->Cm = Cm; x->Ym = Ym;
         x->Cv = Cvv; x->Cv2 = Cv2; x->eigwork = eigwork; x->evals = evals; x->mu = mu;
@@ -1184,6 +1200,20 @@ hq_status enqueue_a(hq_ctx *x, StepGraph *sgr, long long *counters) {
     return HQ_OK;
 }
 
+// the side stream and fork / join events of phase B
+bool ensure_side(hq_ctx *x) {
+    if (!x->side && cudaStreamCreateWithFlags(&x->side, cudaStreamNonBlocking) != cudaSuccess) {
+        x->side = nullptr;
+        return false;
+    }
+    for (cudaEvent_t &e : x->evside)
+        if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            e = nullptr;
+            return false;
+        }
+    return true;
+}
+
 // B1-B5: predictor system, Uh, Shat, Z = G Uh, corrector (U <- U_{n+1}).
 template <typename T>
 hq_status enqueue_b(hq_ctx *x, StepGraph *sgr, long long *counters) {
@@ -1192,6 +1222,22 @@ hq_status enqueue_b(hq_ctx *x, StepGraph *sgr, long long *counters) {
     const double tau = x->cfg.tau;
     T *U = (T *)x->U, *W = (T *)x->W, *Uh = (T *)x->Uh, *Z = (T *)x->Z;
     const double *tau_dev = nullptr;
+    // the warm start's N x N solve needs only the Gram: it runs on the side
+    // stream beside the step size and the predictor system (not in the
+    // per-launch timing mode, whose events are on the main stream)
+    const bool ws_fork = x->cfg.z_warm_start && x->lu32w && x->ipivw && x->pRw &&
+                         lu32_fits(N, N) && !x->timing && ensure_side(x);
+    if (ws_fork) {
+        HQ_CUDA(cudaEventRecord(x->evside[0], x->st));
+        HQ_CUDA(cudaStreamWaitEvent(x->side, x->evside[0], 0));
+        if (x->mixed)
+            launch_spd_solve(N, x->G2, 2 * N, x->G2 + N, 2 * N, x->Mw, x->Lm, x->Ym, x->ipivw,
+                             x->status, x->side, x->lu32w);
+        else
+            launch_solve32_refined(N, N, x->G2, 2 * N, x->G2 + N, 2 * N, x->Ym, x->lu32w,
+                                   x->ipivw, x->pRw, 2, x->status, x->side);
+        HQ_CUDA(cudaEventRecord(x->evside[1], x->side));
+    }
     if (x->cfg.adaptive_tau) {
         // tau_n from the Gram of step n (Ritz estimate of lambda_1, bound on lambda_max<U,U>)
         launch_extract(N, N, 1.0, x->G2, 2 * N, x->Ssm, N, x->st);
@@ -1223,7 +1269,9 @@ hq_status enqueue_b(hq_ctx *x, StepGraph *sgr, long long *counters) {
         // mixed: FP32 elimination (a warm start needs no more); FP64: FP32
         // elimination and two FP64 refinement steps where the factors fit
         // shared memory (the FP64 solution to rounding level)
-        if (!x->mixed && x->lu32 && x->pR && x->ipiv && lu32_fits(N, N))
+        if (ws_fork)
+            HQ_CUDA(cudaStreamWaitEvent(x->st, x->evside[1], 0));
+        else if (!x->mixed && x->lu32 && x->pR && x->ipiv && lu32_fits(N, N))
             launch_solve32_refined(N, N, x->G2, 2 * N, x->G2 + N, 2 * N, x->Ym, x->lu32, x->ipiv,
                                    x->pR, 2, x->status, x->st);
         else
