@@ -58,20 +58,31 @@ void enable_zmarch(GridGeom &g) {
 }
 
 // Per-column partial sums: each thread holds acc[V] for its columns; reduce
-// over threadIdx.y in order and store one row of the partial array.
+// over threadIdx.y in order and store one row of the partial array.  One
+// thread per output (column group, slot) sums the thread rows, so the chains
+// run side by side.  FP64 partials are summed in FP64 (row order as ever);
+// FP32 partials in FP32 and widened once per output (the thread partials
+// are FP32 sums already; widening each one made the reduction an FP64-pipe
+// cost comparable to the sweep itself at GB300's FP64 rate).
 template <int V, typename A>
 __device__ __forceinline__ void block_col_reduce(A (&acc)[V], double *red, double *part,
                                                  int N, int col, bool cv) {
+    (void)col;
+    (void)cv;
     const int tx = threadIdx.x, ty = threadIdx.y, TX = blockDim.x, TY = blockDim.y;
+    A *ra = reinterpret_cast<A *>(red);
 #pragma unroll
-    for (int v = 0; v < V; v++) red[(ty * TX + tx) * V + v] = (double)acc[v];
+    for (int v = 0; v < V; v++) ra[(ty * TX + tx) * V + v] = acc[v];
     __syncthreads();
-    if (ty == 0 && cv && part) {
-#pragma unroll
-        for (int v = 0; v < V; v++) {
-            double s = 0.0;
-            for (int y = 0; y < TY; y++) s += red[(y * TX + tx) * V + v];
-            part[(size_t)blockIdx.y * N + col + v] = s;
+    const int t = ty * TX + tx;
+    if (t < TX * V && part) {
+        const int cx = t / V, vv = t - cx * V;
+        const int c = (blockIdx.x * TX + cx) * V;   // the column group's first column
+        if (c < N) {
+            A s = A(0);
+#pragma unroll 4
+            for (int y = 0; y < TY; y++) s += ra[(y * TX + cx) * V + vv];
+            part[(size_t)blockIdx.y * N + c + vv] = (double)s;
         }
     }
     __syncthreads();
