@@ -860,92 +860,132 @@ __global__ void __launch_bounds__(LU32_THREADS) k_lu32_factor_solve(int nn, int 
     }
 }
 
-// R = B - A X in FP64 (one thread per entry of R, 64-thread CTAs)
-__global__ void __launch_bounds__(64) k_resid64(int nn, int nr, const double *A, int lda,
-                                                const double *B, int ldb, const double *X,
-                                                double *R) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nn * nr) return;
-    const int r = e / nr, c = e % nr;
-    double s = B[(size_t)r * ldb + c];
-    // k in order; the loads of eight terms issued ahead of their FMAs
-    for (int k0 = 0; k0 < nn; k0 += 8) {
-        double a[8], x[8];
+// R = B - A X in FP64.  CTA = one row r of R and 64 of its columns; the
+// four threads of a column (one per 64-thread group) split k into four
+// contiguous ranges (each a chain of nn/4 FMAs in k order), whose sums are
+// added in range order.
+constexpr int RES_COLS = 64, RES_KG = 4;
+__global__ void __launch_bounds__(RES_COLS * RES_KG) k_resid64(int nn, int nr, const double *A,
+                                                              int lda, const double *B, int ldb,
+                                                              const double *X, double *R) {
+    __shared__ double ps[RES_KG][RES_COLS];
+    const int r = blockIdx.x, cl = threadIdx.x % RES_COLS, kg = threadIdx.x / RES_COLS;
+    const int c = blockIdx.y * RES_COLS + cl;
+    const int kc = (nn + RES_KG - 1) / RES_KG, k0 = kg * kc, k1 = min(nn, k0 + kc);
+    double s = 0.0;
+    if (c < nr)
+        for (int k = k0; k < k1; k++) s += A[(size_t)r * lda + k] * X[(size_t)k * nr + c];
+    ps[kg][cl] = s;
+    __syncthreads();
+    if (kg == 0 && c < nr) {
+        double t = ps[0][cl];
 #pragma unroll
-        for (int u = 0; u < 8; u++) {
-            a[u] = k0 + u < nn ? A[(size_t)r * lda + k0 + u] : 0.0;
-            x[u] = k0 + u < nn ? X[(size_t)(k0 + u) * nr + c] : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; u++)
-            if (k0 + u < nn) s -= a[u] * x[u];
+        for (int g = 1; g < RES_KG; g++) t += ps[g][cl];
+        R[(size_t)r * nr + c] = B[(size_t)r * ldb + c] - t;
     }
-    R[e] = s;
 }
 
 // X = (LU)^-1 P R, or X += (LU)^-1 P R (accumulate), with the stored FP32
 // factors; R has leading dimension ldr, X is dense nn x nr.  The solves of
-// the first solution and of every refinement step run here (the row swaps
-// applied first, then the eliminations: the same operations per row as
-// swapping during the factorisation).  The right-hand sides are
-// independent: each CTA takes RS_COLS of them (RS_THREADS threads: column =
-// tid % RS_COLS, row slot = tid / RS_COLS), so the 2 nn barriers of the two
-// substitutions are barriers of a few warps; every element sees the same
-// operations in the same order as a single-CTA solve.
-constexpr int RS_COLS = 8, RS_THREADS = 256, RS_SLOTS = RS_THREADS / RS_COLS;
+// the first solution and of every refinement step run here.  One warp per
+// right-hand side (the CTA's warps share the factors in shared memory):
+// lane l holds rows l + 32 i in registers, the pivot value of step k comes
+// by a shuffle from its owner, so the 2 nn steps of the two substitutions
+// need no barrier.  P R is gathered through the composed row permutation
+// (the swaps of the elimination applied in reverse to each row index), and
+// every element sees the same operations in the same order as the
+// elimination with the swaps applied in place.
+constexpr int RS_WARPS = 8, RS_THREADS = 32 * RS_WARPS;
 size_t lu32_resolve_smem(int nn) {
-    return sizeof(float) * ((size_t)nn * (nn + 1) + (size_t)nn * RS_COLS);
+    return sizeof(float) * (size_t)nn * (nn + 1) + sizeof(int) * (size_t)nn * 2;
 }
+template <int NI>
 __global__ void __launch_bounds__(RS_THREADS) k_lu32_resolve(int nn, int nr, const float *LU,
                                                            const int *ipiv, const double *R,
                                                            int ldr, double *X, int accumulate) {
     extern __shared__ float sm32[];
     float *sA = sm32;
-    float *sB = sm32 + (size_t)nn * (nn + 1);
-    const int tid = threadIdx.x, la = nn + 1;
-    const int cc = tid % RS_COLS, slot = tid / RS_COLS;
-    const int c = blockIdx.x * RS_COLS + cc;
-    const bool cv = c < nr;
+    int *piv = reinterpret_cast<int *>(sm32 + (size_t)nn * (nn + 1));
+    int *perm = piv + nn;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, la = nn + 1;
     for (int idx = tid; idx < nn * nn; idx += RS_THREADS) {
         const int r = idx / nn, q = idx - r * nn;
         sA[r * la + q] = LU[idx];
     }
-    for (int r = slot; r < nn; r += RS_SLOTS)
-        sB[r * RS_COLS + cc] = cv ? (float)R[(size_t)r * ldr + c] : 0.f;
+    for (int k = tid; k < nn; k += RS_THREADS) piv[k] = ipiv[k];
     __syncthreads();
-    // row swaps in elimination order, one thread per right-hand side
-    if (slot == 0)
-        for (int k = 0; k < nn; k++) {
-            const int p = ipiv[k];
-            if (p != k) {
-                const float t = sB[k * RS_COLS + cc];
-                sB[k * RS_COLS + cc] = sB[p * RS_COLS + cc];
-                sB[p * RS_COLS + cc] = t;
+    for (int i = tid; i < nn; i += RS_THREADS) {
+        int idx = i;
+        for (int k = nn - 1; k >= 0; k--) {
+            const int p = piv[k];
+            idx = idx == k ? p : (idx == p ? k : idx);
+        }
+        perm[i] = idx;
+    }
+    __syncthreads();
+    const int c = blockIdx.x * RS_WARPS + warp;
+    if (c >= nr) return;
+    float x[NI];
+#pragma unroll
+    for (int i = 0; i < NI; i++) {
+        const int row = lane + 32 * i;
+        x[i] = row < nn ? (float)R[(size_t)perm[row] * ldr + c] : 0.f;
+    }
+    // forward substitution with the unit lower factor
+#pragma unroll
+    for (int kb = 0; kb < NI; kb++)
+        for (int kk = 0; kk < 32; kk++) {
+            const int k = 32 * kb + kk;
+            if (k >= nn - 1) break;
+            const float bk = __shfl_sync(0xffffffffu, x[kb], kk);
+#pragma unroll
+            for (int i = kb; i < NI; i++) {
+                const int row = lane + 32 * i;
+                if (row > k && row < nn) x[i] -= sA[row * la + k] * bk;
             }
         }
-    __syncthreads();
-    for (int k = 0; k < nn - 1; k++) {
-        const float bk = sB[k * RS_COLS + cc];
-        for (int r = k + 1 + slot; r < nn; r += RS_SLOTS)
-            sB[r * RS_COLS + cc] -= sA[r * la + k] * bk;
-        __syncthreads();
-    }
-    for (int k = nn - 1; k >= 0; k--) {
-        const float inv = 1.0f / sA[k * la + k];
-        const float bk = sB[k * RS_COLS + cc];
-        for (int r = slot; r < k; r += RS_SLOTS) {
-            const float u = sA[r * la + k] * inv;
-            sB[r * RS_COLS + cc] -= u * bk;
+    // backward substitution with the upper factor
+#pragma unroll
+    for (int kb = NI - 1; kb >= 0; kb--)
+        for (int kk = 31; kk >= 0; kk--) {
+            const int k = 32 * kb + kk;
+            if (k >= nn) continue;
+            const float inv = 1.0f / sA[k * la + k];
+            const float bk = __shfl_sync(0xffffffffu, x[kb], kk);
+#pragma unroll
+            for (int i = 0; i <= kb; i++) {
+                const int row = lane + 32 * i;
+                if (row < k) {
+                    const float u = sA[row * la + k] * inv;
+                    x[i] -= u * bk;
+                }
+            }
+            if (lane == kk) x[kb] *= inv;
         }
-        __syncthreads();
-        if (slot == 0) sB[k * RS_COLS + cc] *= inv;
-    }
-    __syncthreads();
-    if (cv)
-        for (int r = slot; r < nn; r += RS_SLOTS) {
-            const double v = (double)sB[r * RS_COLS + cc];
-            X[(size_t)r * nr + c] = accumulate ? X[(size_t)r * nr + c] + v : v;
+#pragma unroll
+    for (int i = 0; i < NI; i++) {
+        const int row = lane + 32 * i;
+        if (row < nn) {
+            const double v = (double)x[i];
+            X[(size_t)row * nr + c] = accumulate ? X[(size_t)row * nr + c] + v : v;
         }
+    }
+}
+
+static void launch_resolve(int nn, int nr, const float *LU, const int *ipiv, const double *R,
+                           int ldr, double *X, int accumulate, cudaStream_t s) {
+    const dim3 grid((nr + RS_WARPS - 1) / RS_WARPS);
+    const size_t sm = lu32_resolve_smem(nn);
+    switch ((nn + 31) / 32) {
+#define RS_CASE(K)                                                                                 \
+    case K:                                                                                        \
+        HQ_LAUNCH(HQ_K_SMALL, k_lu32_resolve<K><<<grid, RS_THREADS, sm, s>>>(nn, nr, LU, ipiv, R,  \
+                                                                            ldr, X, accumulate));  \
+        break;
+        RS_CASE(1) RS_CASE(2) RS_CASE(3) RS_CASE(4) RS_CASE(5) RS_CASE(6) RS_CASE(7) RS_CASE(8)
+#undef RS_CASE
+    default: break;   // lu32_fits bounds nn well below 256
+    }
 }
 
 void lu32_prepare() {
@@ -953,19 +993,24 @@ void lu32_prepare() {
     if (done) return;
     const int lim = 200 * 1024;
     cudaFuncSetAttribute(k_lu32_factor_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    cudaFuncSetAttribute(k_lu32_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_lu32_resolve<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_lu32_resolve<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_lu32_resolve<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_lu32_resolve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_lu32_resolve<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_lu32_resolve<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_lu32_resolve<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_lu32_resolve<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     done = true;
 }
 
-// FP32 factors of A in one CTA, then X = (LU)^-1 P B over RS_COLS-column CTAs
+// FP32 factors of A in one CTA, then X = (LU)^-1 P B over RS_WARPS-column CTAs
 static void lu32_factor_then_solve(int nn, int nr, const double *A, int lda, const double *B,
                                    int ldb, double *X, float *LU, int *ipiv, int *status,
                                    cudaStream_t s) {
     HQ_LAUNCH(HQ_K_SMALL, k_lu32_factor_solve<<<1, LU32_THREADS, lu32_smem(nn, 0), s>>>(
                               nn, 0, A, lda, nullptr, 0, LU, ipiv, nullptr, status));
-    HQ_LAUNCH(HQ_K_SMALL, k_lu32_resolve<<<(nr + RS_COLS - 1) / RS_COLS, RS_THREADS,
-                                             lu32_resolve_smem(nn), s>>>(nn, nr, LU, ipiv, B, ldb,
-                                                                          X, 0));
+    launch_resolve(nn, nr, LU, ipiv, B, ldb, X, 0, s);
 }
 
 // X = A^-1 B (A nn x nn, B nn x nr, FP64 in and out) by FP32 elimination and
@@ -976,11 +1021,9 @@ void launch_solve32_refined(int nn, int nr, const double *A, int lda, const doub
                             cudaStream_t s) {
     lu32_factor_then_solve(nn, nr, A, lda, B, ldb, X, LU, ipiv, status, s);
     for (int it = 0; it < refine; it++) {
-        HQ_LAUNCH(HQ_K_SMALL, k_resid64<<<(nn * nr + 63) / 64, 64, 0, s>>>(nn, nr, A, lda, B, ldb,
-                                                                          X, R));
-        HQ_LAUNCH(HQ_K_SMALL, k_lu32_resolve<<<(nr + RS_COLS - 1) / RS_COLS, RS_THREADS,
-                                                 lu32_resolve_smem(nn), s>>>(nn, nr, LU, ipiv, R,
-                                                                              nr, X, 1));
+        HQ_LAUNCH(HQ_K_SMALL, k_resid64<<<dim3(nn, (nr + RES_COLS - 1) / RES_COLS), RES_COLS * RES_KG,
+                                           0, s>>>(nn, nr, A, lda, B, ldb, X, R));
+        launch_resolve(nn, nr, LU, ipiv, R, nr, X, 1, s);
     }
 }
 
