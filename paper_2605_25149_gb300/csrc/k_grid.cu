@@ -74,17 +74,19 @@ __device__ __forceinline__ void block_col_reduce(A (&acc)[V], double *red, doubl
 #pragma unroll
     for (int v = 0; v < V; v++) ra[(ty * TX + tx) * V + v] = acc[v];
     __syncthreads();
-    const int t = ty * TX + tx;
-    if (t < TX * V && part) {
-        const int cx = t / V, vv = t - cx * V;
-        const int c = (blockIdx.x * TX + cx) * V;   // the column group's first column
-        if (c < N) {
-            A s = A(0);
+    // TX V outputs over TX TY threads (64-thread CTAs of 32 column groups of
+    // four: two outputs per thread)
+    if (part)
+        for (int o = ty * TX + tx; o < TX * V; o += TX * TY) {
+            const int cx = o / V, vv = o - cx * V;
+            const int c = (blockIdx.x * TX + cx) * V;   // the column group's first column
+            if (c < N) {
+                A s = A(0);
 #pragma unroll 4
-            for (int y = 0; y < TY; y++) s += ra[(y * TX + cx) * V + vv];
-            part[(size_t)blockIdx.y * N + c + vv] = (double)s;
+                for (int y = 0; y < TY; y++) s += ra[(y * TX + cx) * V + vv];
+                part[(size_t)blockIdx.y * N + c + vv] = (double)s;
+            }
         }
-    }
     __syncthreads();
 }
 

@@ -128,6 +128,23 @@ def test_batch_wall_clock_limit():
     assert list(steps) == [1, 1]              # the limit is tested after each loop iteration
 
 
+@pytest.mark.parametrize("prec,N,gb", [("mixed", 128, 64), ("mixed", 128, 128), ("fp64", 64, 64)])
+def test_small_blocks_form_every_partial_sum(prec, N, gb):
+    """Grid kernels of 64- and 128-thread CTAs with 32 column groups (N = 128
+    in FP32, vector width 4: more per-column outputs of a CTA's reduction
+    than threads) follow the default shape's trajectory to rounding."""
+    torch_mod()
+    m = 10
+    kw = dict(precision="mixed", cg_rtol=1e-6) if prec == "mixed" else dict(cg_rtol=1e-12)
+    sd, _, _ = make(m, N, tau=0.4, **kw)
+    st, _, _ = make(m, N, tau=0.4, grid_block=gb, grid_ctas=8, **kw)
+    sd.step(3)
+    st.step(3)
+    Ud, Ut = sd.get_state()[0], st.get_state()[0]
+    tol = 1e-4 if prec == "mixed" else 1e-10
+    assert np.abs(Ud - Ut).max() <= tol * np.abs(Ud).max()
+
+
 def test_tuned_launch_shape_keeps_the_trajectory(tmp_path):
     """hq_tune picks a candidate launch shape; a context using it follows the
     default-shape trajectory to rounding (only reduction orders change) and a
