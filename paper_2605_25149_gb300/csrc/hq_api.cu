@@ -2098,7 +2098,9 @@ hq_status project(hq_ctx *x, double *y, double rtol = 0.0) {
     const double na = 2.0 * N;
     if (rtol >= 1e-8 && x->ozgram && gram_oz_supported(2 * N) &&
         use_oz(x, 0.5 * (double)x->n * na * na)) {
-        launch_gram_oz(x->n, u, N, y, N, x->h3, x->ozgram, x->Mw, x->status, x->st);
+        // only the block <u, y> is used: the Gram's columns of y (the column
+        // tiles from y's first column on)
+        launch_gram_oz(x->n, u, N, y, N, x->h3, x->ozgram, x->Mw, x->status, x->st, N);
         launch_extract(N, N, -1.0, x->Mw + N, 2 * N, x->Msm, N, x->st);
     } else {
         GramPlan gp = make_gram_plan(x->n, N, N, false);

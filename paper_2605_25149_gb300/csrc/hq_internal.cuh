@@ -212,11 +212,13 @@ size_t tall_oz_image_bytes(long n, int K, int ncol);
 int tall_oz_partials(long n, int ncol);
 void oz_prepare();
 // FP64 Gram w [X1 X2]^T [X1 X2] (n x na, na <= 128) by the same slicing;
-// scratch: gram_oz_scratch_bytes(n, na); out: na x na row-major
+// scratch: gram_oz_scratch_bytes(n, na); out: na x na row-major.  col0 > 0:
+// only the output columns from the 64-column tile that holds col0 on are
+// formed and written (a cross block X1^T X2 with n1 a multiple of 64)
 bool gram_oz_supported(int na);
 size_t gram_oz_scratch_bytes(long n, int na);
 void launch_gram_oz(long n, const double *X1, int n1, const double *X2, int n2, double w,
-                    double *scratch, double *out, int *status, cudaStream_t s);
+                    double *scratch, double *out, int *status, cudaStream_t s, int col0 = 0);
 void launch_tall_oz(long n, const double *A1, int k1, const double *M1, const double *A2, int k2,
                     const double *M2, int ncol, const double *Cin, double *Out, double *part_sq,
                     unsigned char *image, int *status, cudaStream_t s);

@@ -1574,18 +1574,19 @@ __global__ void __launch_bounds__(32) k_trsv_col(int N, const double *L, const d
 // 1e-6 of itself.  FP32 runs about sixty times FP64's lane rate here, and
 // the whole estimate is one launch instead of four.  N <= LH_MAX_N.
 constexpr int LH_MAX_N = 96;
-size_t lam_hat32_smem(int N) { return sizeof(float) * (2 * (size_t)N * N + 2 * N + 64); }
+size_t lam_hat32_smem(int N) { return sizeof(float) * (2 * (size_t)N * (N + 1) + 2 * N + 64); }
 __global__ void __launch_bounds__(1024) k_lam_hat32(int N, const double *K, const double *S,
                                                    double *vec, double *out, int *status) {
     extern __shared__ float lsm[];
-    float *L = lsm, *C = lsm + (size_t)N * N, *v = C + (size_t)N * N, *w = v + N, *red = w + N;
+    const int LD = N + 1;   // row stride: a column read by consecutive threads spans all banks
+    float *L = lsm, *C = lsm + (size_t)N * LD, *v = C + (size_t)N * LD, *w = v + N, *red = w + N;
     __shared__ float d_sh, rd_sh, mu_sh, nw_sh;
     __shared__ int fresh;
     const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
     for (long idx = tid; idx < (long)N * N; idx += T) {
         const int i = (int)(idx / N), j = (int)(idx % N);
-        L[idx] = (float)S[idx];
-        C[idx] = (float)(0.5 * (K[(size_t)i * N + j] + K[(size_t)j * N + i]));
+        L[i * LD + j] = (float)S[idx];
+        C[i * LD + j] = (float)(0.5 * (K[(size_t)i * N + j] + K[(size_t)j * N + i]));
     }
     if (tid == 0) {
         double nv = 0.0;
@@ -1594,7 +1595,7 @@ __global__ void __launch_bounds__(1024) k_lam_hat32(int N, const double *K, cons
     }
     __syncthreads();
     for (int k = 0; k < N; k++) {
-        const float dk = L[(size_t)k * N + k];
+        const float dk = L[k * LD + k];
         if (!(dk > 0.f)) {
             if (tid == 0) atomicOr(status, ST_SINGULAR);
             return;
@@ -1605,11 +1606,11 @@ __global__ void __launch_bounds__(1024) k_lam_hat32(int N, const double *K, cons
         }
         __syncthreads();
         const float d = d_sh, rd = rd_sh;
-        for (int i = k + tid; i < N; i += T) L[(size_t)i * N + k] = (i == k) ? d : L[(size_t)i * N + k] * rd;
+        for (int i = k + tid; i < N; i += T) L[i * LD + k] = (i == k) ? d : L[i * LD + k] * rd;
         __syncthreads();
         for (int i = k + 1 + (tid >> 5); i < N; i += (T >> 5)) {
-            const float lik = L[(size_t)i * N + k];
-            for (int j = k + 1 + lane; j <= i; j += 32) L[(size_t)i * N + j] -= lik * L[(size_t)j * N + k];
+            const float lik = L[i * LD + k];
+            for (int j = k + 1 + lane; j <= i; j += 32) L[i * LD + j] -= lik * L[j * LD + k];
         }
         __syncthreads();
     }
@@ -1617,17 +1618,17 @@ __global__ void __launch_bounds__(1024) k_lam_hat32(int N, const double *K, cons
     for (int pass = 0; pass < 2; pass++) {
         for (int j = tid; j < N; j += T)
             for (int i = 0; i < N; i++) {
-                float acc = C[(size_t)i * N + j];
-                for (int k = 0; k < i; k++) acc -= L[(size_t)i * N + k] * C[(size_t)k * N + j];
-                C[(size_t)i * N + j] = acc / L[(size_t)i * N + i];
+                float acc = C[i * LD + j];
+                for (int k = 0; k < i; k++) acc -= L[i * LD + k] * C[k * LD + j];
+                C[i * LD + j] = acc / L[i * LD + i];
             }
         __syncthreads();
         for (long idx = tid; idx < (long)N * N; idx += T) {
             const int i = (int)(idx / N), j = (int)(idx % N);
             if (i < j) {
-                const float a = C[idx], b = C[(size_t)j * N + i];
-                C[idx] = b;
-                C[(size_t)j * N + i] = a;
+                const float a = C[i * LD + j], b = C[j * LD + i];
+                C[i * LD + j] = b;
+                C[j * LD + i] = a;
             }
         }
         __syncthreads();
@@ -1638,7 +1639,7 @@ __global__ void __launch_bounds__(1024) k_lam_hat32(int N, const double *K, cons
     for (int it = 0; it < 500; it++) {
         for (int i = tid; i < N; i += T) {
             float acc = 0.f;
-            for (int j = 0; j < N; j++) acc += C[(size_t)i * N + j] * v[j];
+            for (int j = 0; j < N; j++) acc += C[i * LD + j] * v[j];
             w[i] = acc;
         }
         __syncthreads();

@@ -479,7 +479,7 @@ constexpr int OZ_GCONV = 512;
 constexpr int OZ_GTHREADS = OZ_GCONV + 32;
 
 __global__ void __launch_bounds__(OZ_GTHREADS, 1)
-    k_gram_oz(long n, int n1, int n2, long chunk_rows, const double *__restrict__ X1,
+    k_gram_oz(long n, int n1, int n2, long chunk_rows, int ct0, const double *__restrict__ X1,
               const double *__restrict__ X2, const int *__restrict__ colexp,
               double *__restrict__ partials, int *status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(OZ_GTHREADS, 1)
     __shared__ int last_sh, tmem_free_sh;
     constexpr uint32_t TCOLS = OZ_S * OZ_NT;   // 512
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int na = n1 + n2, ct = blockIdx.x;
+    const int na = n1 + n2, ct = ct0 + blockIdx.x;   // output column tile
     const long p0 = (long)blockIdx.y * chunk_rows;
     const long p1 = (n < p0 + chunk_rows) ? n : p0 + chunk_rows;
     const int nslices = p1 > p0 ? (int)((p1 - p0 + OZ_GKC - 1) / OZ_GKC) : 0;
@@ -654,7 +654,7 @@ __global__ void __launch_bounds__(OZ_GTHREADS, 1)
         if (tid == 0) atomicOr(status, ST_TC_TIMEOUT);
     } else if (tid < OZ_GCONV) {
         if (nslices > 0) flush();
-        double *dst = partials + ((size_t)blockIdx.y * gridDim.x + ct) * OZ_M * OZ_NT;
+        double *dst = partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * OZ_M * OZ_NT;
         const int ea = cexp[grow];
 #pragma unroll
         for (int j = 0; j < 16; j++) {
@@ -679,12 +679,14 @@ __global__ void __launch_bounds__(OZ_GTHREADS, 1)
                      : "memory");
 }
 
-// out[i][j] = w * sum over chunks (in order) of the chunk partials
-__global__ void k_oz_gram_reduce(int na, int ctiles, int chunks, const double *partials, double w,
-                                 double *out) {
+// out[i][j] = w * sum over chunks (in order) of the chunk partials, for the
+// columns of the ctiles tiles from tile ct0 on (the others are not written)
+__global__ void k_oz_gram_reduce(int na, int ct0, int ctiles, int chunks, const double *partials,
+                                 double w, double *out) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= na * na) return;
-    const int i = e / na, j = e % na, ct = j / OZ_NT, jl = j % OZ_NT;
+    const int i = e / na, j = e % na, ct = j / OZ_NT - ct0, jl = j % OZ_NT;
+    if (ct < 0) return;
     const double s = ordered_sum(partials + ((size_t)ct * OZ_M + i) * OZ_NT + jl, chunks,
                                  (size_t)ctiles * OZ_M * OZ_NT);
     out[e] = w * s;
@@ -740,19 +742,21 @@ size_t gram_oz_scratch_bytes(long n, int na) {
 }
 
 void launch_gram_oz(long n, const double *X1, int n1, const double *X2, int n2, double w,
-                    double *scratch, double *out, int *status, cudaStream_t s) {
+                    double *scratch, double *out, int *status, cudaStream_t s, int col0) {
     if (!X2) n2 = 0;
     const int na = n1 + n2;
     OzGramPlan g = make_oz_gram_plan(n, na);
+    // output columns from the tile holding column col0 on
+    const int ct0 = std::min(std::max(col0, 0) / OZ_NT, g.ctiles - 1), nt = g.ctiles - ct0;
     double *partials = scratch;
     int *colexp = reinterpret_cast<int *>(scratch + (size_t)g.chunks * g.ctiles * OZ_M * OZ_NT);
     cudaMemsetAsync(colexp, 0, sizeof(int) * OZ_M, s);
     HQ_LAUNCH(HQ_K_GRAM, k_oz_colexp<<<1024, 128, 0, s>>>(n, n1, n2, X1, n2 ? X2 : nullptr, colexp));
-    HQ_LAUNCH(HQ_K_GRAM, k_gram_oz<<<dim3(g.ctiles, g.chunks), OZ_GTHREADS, OZ_GSMEM, s>>>(
-                             n, n1, n2, g.chunk_rows, X1, n2 ? X2 : nullptr, colexp, partials,
+    HQ_LAUNCH(HQ_K_GRAM, k_gram_oz<<<dim3(nt, g.chunks), OZ_GTHREADS, OZ_GSMEM, s>>>(
+                             n, n1, n2, g.chunk_rows, ct0, X1, n2 ? X2 : nullptr, colexp, partials,
                              status));
     HQ_LAUNCH(HQ_K_GRAM, k_oz_gram_reduce<<<(na * na + 255) / 256, 256, 0, s>>>(
-                             na, g.ctiles, g.chunks, partials, w, out));
+                             na, ct0, nt, g.chunks, partials, w, out));
 }
 
 void launch_tall_oz(long n, const double *A1, int k1, const double *M1, const double *A2, int k2,
