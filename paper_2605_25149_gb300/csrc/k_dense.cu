@@ -1637,10 +1637,14 @@ __global__ void __launch_bounds__(1024) k_lam_hat32(int N, const double *K, cons
     __syncthreads();
     float mu = 0.f, mu_prev = 0.f;
     for (int it = 0; it < 500; it++) {
-        for (int i = tid; i < N; i += T) {
+        // w = C v: a warp per row, the lanes split the row and a butterfly
+        // of shuffles adds their sums
+        for (int i = warp; i < N; i += (T >> 5)) {
             float acc = 0.f;
-            for (int j = 0; j < N; j++) acc += C[i * LD + j] * v[j];
-            w[i] = acc;
+            for (int j = lane; j < N; j += 32) acc += C[i * LD + j] * v[j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) w[i] = acc;
         }
         __syncthreads();
         float vw = 0.f, vv = 0.f, ww = 0.f;
