@@ -17,11 +17,13 @@
 // per term).  The epilogue combines D_2..D_9 in 64-bit fixed point, converts
 // once to FP64, applies 2^(e_p + f_c), adds Cin and optionally sums squares.
 //
-// CTA = 128 points x 64 output columns, all K; per 64-wide K chunk the 128
+// CTA = 128 points x 64 output columns, all K; per 64-wide K chunk the 256
 // threads convert the FP64 rows into 8 digit planes (K-major, 128-byte
-// swizzle) and copy the 8 digit planes of the small matrix prepared once per
-// call by k_oz_split; one thread issues 36 MMAs per K step of 16.  TMEM:
-// 8 accumulators x 64 columns = 512 columns.  Every wait is bounded.
+// swizzle) while bulk copies bring the 8 digit planes of the small matrix
+// (prepared once per call by k_oz_split); one thread issues 36 MMAs per K
+// step of 16.  TMEM: 8 accumulators x 64 columns = 512 columns.  The output
+// tile is staged in the freed digit planes for whole-row Cin reads and Out
+// writes.  Every wait is bounded.
 #include "hq_internal.cuh"
 #include "tc_common.cuh"
 
