@@ -18,6 +18,9 @@
  * Ownership: the caller allocates one device workspace of
  * hq_workspace_bytes() bytes and passes a CUDA stream; the library never
  * allocates device memory after hq_init and every kernel runs on that
+ * stream, or on a private stream forked from it and joined back to it within
+ * the same call (the warm start's N x N solve of a step, beside the
+ * predictor system), so the work of each call stays ordered on the caller's
  * stream.  Pointers passed to a call are borrowed for the duration of the
  * call only.  Arrays flagged on_device are device pointers, otherwise host
  * pointers.  All arrays are FP64 unless stated.
