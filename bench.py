@@ -57,7 +57,7 @@ FP64_OPS = {"smooth": 7.0, "stencil": 8.0, "residual": 7.0}
 # of that launch): keys (class, dtype); an entry is removed whenever its
 # kernel changes, until it is captured again.
 TRAFFIC_PER_ELEMENT = {("smooth", "f32"): (136.215040e6 + 44.029440e6) / 16777216,
-                       ("stencil", "f64"): (136.483584e6 + 96.978432e6) / 16777216,
+                       ("stencil", "f64"): (136.446208e6 + 96.011008e6) / 16777216,
                        # the z-marching FP32 sweep (blocks of 100 MB or more),
                        # captured on 64^3 x 256 and scaled by point-columns
                        ("smooth_zm", "f32"): (553.649408e6 + 240.579328e6) / 67108864}
